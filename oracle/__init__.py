@@ -1,0 +1,134 @@
+"""FP64 CPU oracle for the e+e- pair-process rate kernel -- TEST INFRASTRUCTURE ONLY.
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may import
+this package. The product library never calls it, and it shares no code with the GPU path:
+the arithmetic lives in ``vx_oracle.c`` (plain C, FP64, OpenMP over zones, no FMA contraction),
+built by :func:`build` with gcc. This module only marshals numpy arrays through ctypes.
+
+The kernel definition, the discrete rule and every reading of the paper the oracle adopts are
+stated in the header comment of ``vx_oracle.c``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "vx_oracle.c")
+_SO = os.path.join(_HERE, "libvx_oracle.so")
+_lib = None
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+
+
+def build(force: bool = False) -> str:
+    """Compile vx_oracle.c into libvx_oracle.so (gcc, -O2, OpenMP when available)."""
+    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(_SRC):
+        return _SO
+    base = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-std=c11",
+            "-o", _SO + ".tmp", _SRC, "-lm"]
+    try:
+        subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True, capture_output=True)  # serial build without OpenMP
+    os.replace(_SO + ".tmp", _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_SO)
+        lib.vxo_gauss_legendre.argtypes = [ctypes.c_int, _dp, _dp]
+        lib.vxo_energy_weights.argtypes = [ctypes.c_int, _dp, _dp]
+        lib.vxo_kernel_point.argtypes = [ctypes.c_double] * 5 + [ctypes.c_int, ctypes.c_int, _dp, _dp,
+                                                                 _dp, _dp]
+        lib.vxo_kernel_point.restype = None
+        lib.vxo_phi_zone.argtypes = [ctypes.c_int, _dp, ctypes.c_int, _dp, _dp, ctypes.c_int, _dp, _dp,
+                                     ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                     _dp, _dp]
+        lib.vxo_phi_zone.restype = None
+        lib.vxo_eval.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _ip,
+                                 ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_long,
+                                 _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, ctypes.c_int]
+        lib.vxo_eval.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(_dp)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def gauss_legendre(n: int):
+    """Gauss-Legendre nodes (ascending) and weights on [-1, 1]."""
+    x, w = np.empty(n), np.empty(n)
+    if _load().vxo_gauss_legendre(n, _p(x), _p(w)) != 0:
+        raise ValueError("bad node count")
+    return x, w
+
+
+def energy_weights(eps) -> np.ndarray:
+    """w_i = eps_i^2 d(eps_i) for bin centres eps (edges at geometric midpoints)."""
+    eps = _f64(eps)
+    w = np.empty_like(eps)
+    if _load().vxo_energy_weights(len(eps), _p(eps), _p(w)) != 0:
+        raise ValueError("need at least two bins")
+    return w
+
+
+def kernel_point(eps, epsp, y, T, eta, n_e, boltzmann=False, grad=False):
+    """K^X_dir(eps, eps', y) with G2 = 1: array [dir][X] (dir 0 = production, 1 = annihilation;
+    X 0 = I, 1 = II); with grad=True also dK [dir][X][(d/dT, d/deta)]."""
+    tE, wE = gauss_legendre(n_e)
+    K = np.empty(4)
+    dK = np.empty(8) if grad else None
+    _load().vxo_kernel_point(float(eps), float(epsp), float(y), float(T), float(eta), int(boltzmann),
+                             n_e, _p(tE), _p(wE), _p(K), _p(dK))
+    return (K.reshape(2, 2), dK.reshape(2, 2, 2)) if grad else K.reshape(2, 2)
+
+
+def phi_zone(eps, n_mu, n_e, T, eta, g2=1.0, boltzmann=False, grad=False):
+    """Phi^dir_{l,X}(i,j) of one zone: array [dir][X][l][i][j] (and [.., 2] gradients)."""
+    eps = _f64(eps)
+    n = len(eps)
+    tmu, wmu = gauss_legendre(n_mu)
+    tE, wE = gauss_legendre(n_e)
+    phi = np.empty(8 * n * n)
+    dphi = np.empty(16 * n * n) if grad else None
+    _load().vxo_phi_zone(n, _p(eps), n_mu, _p(tmu), _p(wmu), n_e, _p(tE), _p(wE), float(g2), float(T),
+                         float(eta), int(boltzmann), _p(phi), _p(dphi))
+    phi = phi.reshape(2, 2, 2, n, n)
+    return (phi, dphi.reshape(2, 2, 2, n, n, 2)) if grad else phi
+
+
+def evaluate(eps, n_mu, n_e, species, state, J, H, weights=None, sin2w=0.23, g2=1.0, norm=1.0,
+             phi=False, jac=False, threads=0) -> dict:
+    """Rates j0, chi0, j1, chi1 [Z][S][N] for every zone; optionally the K^I dump
+    phi [Z][dir][l][N][N] and the Jacobian jac [Z][S][N][4 outputs][3 inputs T, eta, Y_e]."""
+    eps = _f64(eps)
+    state = _f64(state)
+    J, H = _f64(J), _f64(H)
+    species = np.ascontiguousarray(species, dtype=np.int32)
+    n, S, Z = len(eps), len(species), state.shape[0]
+    if J.shape != (Z, S, n) or H.shape != (Z, S, n) or state.shape != (Z, 4):
+        raise ValueError("shape mismatch")
+    out = {k: np.empty((Z, S, n)) for k in ("j0", "chi0", "j1", "chi1")}
+    out["phi"] = np.empty((Z, 2, 2, n, n)) if phi else None
+    out["jac"] = np.empty((Z, S, n, 4, 3)) if jac else None
+    w = None if weights is None else _f64(weights)
+    used = _load().vxo_eval(n, _p(eps), _p(w), n_mu, n_e, S, species.ctypes.data_as(_ip), sin2w, g2, norm,
+                            Z, _p(state), _p(J), _p(H), _p(out["j0"]), _p(out["chi0"]), _p(out["j1"]),
+                            _p(out["chi1"]), _p(out["phi"]), _p(out["jac"]), int(threads))
+    if used < 0:
+        raise ValueError("oracle rejected the arguments")
+    out["threads"] = used
+    return out
