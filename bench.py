@@ -1,0 +1,292 @@
+#!/usr/bin/env python
+"""Benchmark: pair-kernel entries/s of the mixed-precision forward + Jacobian pass on one GB300.
+
+A step is one pass of the whole hot path over the batch: persistent scheduling of all zones,
+zone set-up, the (eps, eps', omega, E) quadrature, the spectral contraction and the T / eta_e
+tangents (forward rates and the full Jacobian d(j0, chi0, j1, chi1)/d(T, eta_e, Y_e) from one
+launch). Workload: 4096 rays x 400 zones, 21 bins, 32 x 64 quadrature, 3 species (seeded
+synthetic rays). One entry = one Phi_l(eps_i, eps_j) of one zone and one l: Z N^2 2 per step.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank runs its own independent copy of the workload (weak scaling, no
+collective on the data path); the time is the max over ranks. `--impl reference` times the FP64
+CPU oracle on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import vx_inputs  # noqa: E402
+
+WORKLOAD = 4
+METRIC = "pair-kernel entries/s (zone*eps*eps'*l), FP32+adj vs FP64 fwd, % FP peak"
+UNIT = "entries/s"
+
+
+def entries(Z, N):
+    return Z * N * N * 2
+
+
+def algorithmic_flops_per_node(adj: bool) -> int:
+    """FP32 operations the method needs per (zone, unordered bin pair, omega, E) node, counting an
+    FMA as 2 and an exp or reciprocal as 1: forward 16, tangents 36 more."""
+    return 52 if adj else 16
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while active."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm = [float(r[0]) for r in self.rows if len(r) >= 7 and r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if len(r) >= 7 and r[1].replace(".", "").isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({n for r in self.rows if len(r) >= 7 for n, v in zip(names, r[3:7]) if v == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(sm)}
+
+
+def oracle_sample_rate(b, n_zones: int, jac: bool):
+    """Entries/s of the FP64 oracle on the first n_zones zones of a batch (all host threads)."""
+    import oracle
+    oracle.build()
+    sl = slice(0, n_zones)
+    t0 = time.perf_counter()
+    out = oracle.evaluate(b["eps"], b["n_mu"], b["n_e"], b["species"], b["state"][sl], b["J"][sl], b["H"][sl],
+                          jac=jac)
+    dt = time.perf_counter() - t0
+    return entries(n_zones, len(b["eps"])) / dt, out["threads"], dt
+
+
+def cpu_baseline(target_s: float = 15.0):
+    b = vx_inputs.make_batch(WORKLOAD, rays=[0, 1, 2, 3])
+    rate, thr, dt = oracle_sample_rate(b, 16, True)
+    n = int(min(len(b["state"]), max(16, 16 * target_s / max(dt, 1e-3))))
+    rate, thr, dt = oracle_sample_rate(b, n, True)
+    return {"value": rate, "unit": UNIT, "cores": thr, "kind": "oracle",
+            "sample": f"first {n} zones of workload {WORKLOAD} (rays 0-3), forward + Jacobian, FP64, {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    b = vx_inputs.make_batch(WORKLOAD, rays=[0, 1])
+    # per step: a bounded sample sized to a few seconds of all host cores
+    _, thr, dt = oracle_sample_rate(b, 8, True)
+    n = int(min(len(b["state"]), max(8, 8 * 4.0 / max(dt, 1e-3))))
+    for _ in range(args.warmup):
+        oracle_sample_rate(b, min(n, 8), True)
+    t = []
+    for _ in range(args.steps):
+        r, thr, dt = oracle_sample_rate(b, n, True)
+        t.append(dt)
+    ms = 1000 * float(np.mean(t))
+    value = entries(n, len(b["eps"])) / (ms / 1000)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": vx_inputs.WORKLOADS[WORKLOAD]["name"] + " forward+jacobian",
+                       "zones_per_step": n, "bins": 21, "quadrature": "32x64", "species": 3},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": thr, "kind": "oracle",
+                             "sample": f"first {n} zones of workload {WORKLOAD} per step, forward + Jacobian"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    from paper_1404_1719_gb300 import PairRates, _build
+    _build.build()
+
+    b = vx_inputs.make_batch(WORKLOAD, seed=rank)
+    Z, N, S = b["state"].shape[0], len(b["eps"]), len(b["species"])
+    host = {k: torch.from_numpy(np.ascontiguousarray(b[k])).pin_memory() for k in ("state", "J", "H")}
+    d = {k: v.to(dev) for k, v in host.items()}
+    rates = PairRates(b["eps"], b["n_mu"], b["n_e"], species=b["species"], graph=True)
+    stream = torch.cuda.current_stream()
+    out = {k: torch.empty((Z, S, N), dtype=torch.float64, device=dev) for k in ("j0", "chi0", "j1", "chi1")}
+    jac = torch.empty((Z, S, N, 4, 3), dtype=torch.float64, device=dev)
+    from paper_1404_1719_gb300 import capi
+    bt = rates._batch(d["state"], d["J"], d["H"], b["ray_offsets"])
+    fwd = capi.vx_out(*(out[k].data_ptr() for k in ("j0", "chi0", "j1", "chi1")), None)
+
+    def step():
+        capi.vx_rates_adjoint(rates.handle, bt, None, jac.data_ptr(), None, fwd, stream.cuda_stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    assert rates.check(), "numeric flag raised during warm-up"
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms_local = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        dist.barrier()
+    t = torch.tensor([ms_local], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    ok = rates.check()
+
+    # ---- end-to-end: pinned host inputs -> device -> fused pass -> host rates + Jacobian
+    e2e_steps = max(1, min(3, args.steps))
+    h_out = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in out.items()}
+    h_jac = torch.empty(jac.shape, dtype=jac.dtype, pin_memory=True)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for _ in range(e2e_steps):
+        for k in ("state", "J", "H"):
+            d[k].copy_(host[k], non_blocking=True)
+        step()
+        for k in out:
+            h_out[k].copy_(out[k], non_blocking=True)
+        h_jac.copy_(jac, non_blocking=True)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = a0.elapsed_time(a1) / e2e_steps
+    te = torch.tensor([ms_e2e], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    ms_e2e = float(te.item())
+    h2d = sum(v.numel() * v.element_size() for v in host.values())
+    d2h = sum(v.numel() * v.element_size() for v in out.values()) + jac.numel() * jac.element_size()
+
+    line = None
+    if rank == 0:
+        ent = entries(Z, N) * world
+        value = ent / (ms / 1000)
+        # roofline of the one kernel of the step (FP32 pipe peak from the unit counts and clock)
+        c = clk.summary()
+        nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+        mhz = c["sm_mhz"] or 2070.0
+        peak = nsm * 128 * 2 * mhz * 1e6 / 1e12
+        npair = N * (N + 1) // 2
+        nodes = Z * npair * b["n_mu"] * b["n_e"]
+        achieved = nodes * algorithmic_flops_per_node(True) / (ms_local / 1000) / 1e12
+        # FP64 forward-only comparison on a sample of the same workload
+        sub = 48 * 400
+        r64 = PairRates(b["eps"], b["n_mu"], b["n_e"], species=b["species"], precision="fp64")
+        o64 = {k: torch.empty((sub, S, N), dtype=torch.float64, device=dev) for k in out}
+        args64 = (d["state"][:sub], d["J"][:sub], d["H"][:sub])
+        r64.evaluate(*args64, out=o64)
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        r64.evaluate(*args64, out=o64)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        v64 = entries(sub, N) / (f0.elapsed_time(f1) / 1000)
+        r64.close()
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": vx_inputs.WORKLOADS[WORKLOAD]["name"] + " forward+jacobian (mixed)",
+                       "zones": Z, "rays": int(len(b["ray_offsets"]) - 1), "bins": N,
+                       "quadrature": f"{b['n_mu']}x{b['n_e']}", "species": S,
+                       "l2": "inputs larger than L2 (J, H: %.2f GB)" % (2 * b["J"].nbytes / 1e9),
+                       "graph": True},
+            "e2e": {"value": entries(Z, N) * world / (ms_e2e / 1000), "unit": UNIT,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": args.steps,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "peak_note": f"FP32 {nsm} SMs x 128 FMA x 2 x {mhz:.0f} MHz (median SM clock in the run)",
+                         "kernel": "k_pair_mixed<64,true>"},
+            "fp64_fwd": {"value": v64, "unit": UNIT, "sample": f"first {sub} zones, plain FP64 forward only",
+                         "ratio_mixed_fwd_adj_over_fp64_fwd": value / world / v64},
+            "clocks": c,
+            "numeric_ok": bool(ok),
+        }
+        if not args.no_cpu:
+            line["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(line))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    rates.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU-baseline leg")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

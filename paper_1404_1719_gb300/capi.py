@@ -1,0 +1,126 @@
+"""ctypes binding of the C ABI in include/vx_rates.h: same names, argument marshalling only.
+
+The shared library is built in-tree by ``paper_1404_1719_gb300._build.build()``. There is no
+fallback: if it is missing or cannot be loaded, :func:`lib` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import _build
+
+VX_OK, VX_ERR_INVALID_ARG, VX_ERR_CUDA, VX_ERR_OOM, VX_ERR_NUMERIC, VX_ERR_UNSUPPORTED, VX_ERR_TIMEOUT = range(7)
+VX_PREC_FP64, VX_PREC_MIXED = 0, 1
+VX_NU_E, VX_NU_EBAR, VX_NU_X = 0, 1, 2
+VX_USE_GRAPH, VX_AUTOTUNE = 1, 2
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+
+
+class vx_config(ctypes.Structure):
+    _fields_ = [("n_bins", ctypes.c_int), ("eps", _dp), ("weights", _dp), ("n_mu", ctypes.c_int),
+                ("n_e", ctypes.c_int), ("n_species", ctypes.c_int), ("species", _ip),
+                ("sin2w", ctypes.c_double), ("g2", ctypes.c_double), ("norm", ctypes.c_double),
+                ("eta_fp64", ctypes.c_double), ("prec", ctypes.c_int), ("flags", ctypes.c_uint)]
+
+
+class vx_batch(ctypes.Structure):
+    _fields_ = [("n_rays", ctypes.c_int), ("n_zones", ctypes.c_longlong), ("ray_offsets", _ip),
+                ("state", ctypes.c_void_p), ("J", ctypes.c_void_p), ("H", ctypes.c_void_p)]
+
+
+class vx_out(ctypes.Structure):
+    _fields_ = [("j0", ctypes.c_void_p), ("chi0", ctypes.c_void_p), ("j1", ctypes.c_void_p),
+                ("chi1", ctypes.c_void_p), ("phi", ctypes.c_void_p)]
+
+
+class VxError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {vx_status_string(status)}: {vx_last_error()}")
+
+
+SYMBOLS = ("vx_rates_create", "vx_rates_eval", "vx_rates_adjoint", "vx_rates_check",
+           "vx_rates_entries_per_zone", "vx_rates_destroy", "vx_status_string", "vx_last_error")
+
+_lib = None
+
+
+def lib(path: str | None = None):
+    """Load libvx_rates.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_1404_1719_gb300._build.build() "
+                           "(there is no CPU fallback)")
+    L = ctypes.CDLL(path)
+    L.vx_rates_create.argtypes = [ctypes.POINTER(vx_config), ctypes.POINTER(ctypes.c_void_p)]
+    L.vx_rates_create.restype = ctypes.c_int
+    L.vx_rates_eval.argtypes = [ctypes.c_void_p, ctypes.POINTER(vx_batch), ctypes.POINTER(vx_out), ctypes.c_void_p]
+    L.vx_rates_eval.restype = ctypes.c_int
+    L.vx_rates_adjoint.argtypes = [ctypes.c_void_p, ctypes.POINTER(vx_batch), ctypes.POINTER(vx_out), ctypes.c_void_p,
+                                   ctypes.c_void_p, ctypes.POINTER(vx_out), ctypes.c_void_p]
+    L.vx_rates_adjoint.restype = ctypes.c_int
+    L.vx_rates_check.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    L.vx_rates_check.restype = ctypes.c_int
+    L.vx_rates_entries_per_zone.argtypes = [ctypes.c_void_p]
+    L.vx_rates_entries_per_zone.restype = ctypes.c_longlong
+    L.vx_rates_destroy.argtypes = [ctypes.c_void_p]
+    L.vx_rates_destroy.restype = None
+    L.vx_status_string.argtypes = [ctypes.c_int]
+    L.vx_status_string.restype = ctypes.c_char_p
+    L.vx_last_error.argtypes = []
+    L.vx_last_error.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def vx_status_string(s: int) -> str:
+    return lib().vx_status_string(int(s)).decode()
+
+
+def vx_last_error() -> str:
+    return lib().vx_last_error().decode()
+
+
+def _check(status: int, where: str):
+    if status != VX_OK:
+        raise VxError(status, where)
+
+
+def vx_rates_create(cfg: vx_config) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(lib().vx_rates_create(ctypes.byref(cfg), ctypes.byref(h)), "vx_rates_create")
+    return h
+
+
+def vx_rates_eval(h, batch: vx_batch, out: vx_out, stream: int = 0) -> None:
+    _check(lib().vx_rates_eval(h, ctypes.byref(batch), ctypes.byref(out), ctypes.c_void_p(stream)), "vx_rates_eval")
+
+
+def vx_rates_adjoint(h, batch: vx_batch, grad_out: vx_out | None, jac: int | None, grad_state: int | None,
+                     fwd: vx_out | None, stream: int = 0) -> None:
+    st = lib().vx_rates_adjoint(h, ctypes.byref(batch), ctypes.byref(grad_out) if grad_out is not None else None,
+                                ctypes.c_void_p(jac or 0), ctypes.c_void_p(grad_state or 0),
+                                ctypes.byref(fwd) if fwd is not None else None, ctypes.c_void_p(stream))
+    _check(st, "vx_rates_adjoint")
+
+
+def vx_rates_check(h, stream: int = 0) -> int:
+    """Returns the status (VX_OK or VX_ERR_NUMERIC) instead of raising on a numeric flag."""
+    st = lib().vx_rates_check(h, ctypes.c_void_p(stream))
+    if st not in (VX_OK, VX_ERR_NUMERIC):
+        raise VxError(st, "vx_rates_check")
+    return st
+
+
+def vx_rates_entries_per_zone(h) -> int:
+    return int(lib().vx_rates_entries_per_zone(h))
+
+
+def vx_rates_destroy(h) -> None:
+    lib().vx_rates_destroy(h)

@@ -1,0 +1,467 @@
+// vx_kernel_mixed.cuh -- mixed-precision pair-process kernel: quadrature, Legendre projection,
+// spectral contraction and (optionally) the T / eta tangents, fused in one persistent launch.
+//
+// Work decomposition. One CTA owns one zone at a time and pulls the next zone from a global
+// atomic counter (zones of all rays are concatenated; every zone costs the same node count, so
+// ragged rays need no special handling). Thread slot = (unordered bin pair (i <= j), chunk of
+// cos(omega) nodes). A thread loops over its omega nodes and, inside, over the n_e electron-
+// energy nodes with compile-time indices, so the node constants are constant-bank operands.
+//
+// Kernel algebra (exact rewrites of the definition; see the oracle for the definition itself).
+// With d = eps - eps', g = eps eps' (1 + cos w), |q|^2 = d^2 + 2 g, h = |q|/2, the electron energy
+// on the Gauss-Legendre node tau is E = E- + h (1 + tau) and the positron's Ebar = E- + h (1 - tau).
+// The azimuth-averaged squared matrix element of term I is, per node,
+//     (s^2 / (16 |q|^2)) [ (|q| + d tau)^2 + g (1 - tau^2) ]
+//   = (s^2 / (16 |q|^2)) [ (|q|+d)^2 (1+tau)^2 / 4 + (|q|-d)^2 (1-tau)^2 / 4 + 2 g (1 - tau^2) ],
+// a sum of non-negative terms; term II is the same with d -> -d. So per (pair, omega) the node
+// loop only accumulates three non-negative moments M+, M-, M0 of the blocking factor against
+// w_k (1+tau)^2, w_k (1-tau)^2, w_k (1-tau^2), and K_I, K_II follow from three coefficients each
+// (no cancellation anywhere). Terms I and II of (i,j) are terms II and I of (j,i), so only i <= j
+// is integrated. Production follows from annihilation by detailed balance, e^{-(eps+eps')/T},
+// applied in FP64 at the contraction.
+//
+// Blocking factor (1 - f_e)(1 - f_ebar) = 1 / ((1 + e1)(1 + e2)), e1 = exp(-x_e), e2 = exp(-x_p),
+// x_e = (E - mu)/T, x_p = (Ebar + mu)/T, evaluated with MUFU ex2 / rcp. The zone is mapped to
+// eta >= 0 (eta -> -eta exchanges e- and e+, i.e. tau -> -tau, i.e. M+ <-> M-).
+//  * fast path (|eta| <= eta_sw): x arguments anchored at E- in FP32, two reciprocals per rcp.
+//  * degenerate path (|eta| > eta_sw): the electron argument B (1 + tau) + P is formed exactly:
+//    B, P and 1 + tau are split into a high part on a power-of-two grid (chosen per zone so that
+//    fma(B_hi, u_hi, P_hi) is exact in FP32) and a remainder, and exp2 of the exact high part and
+//    of the small remainder are multiplied. The l = 1 projections, whose omega sum cancels by up
+//    to ~300x at high degeneracy, are accumulated in FP32-pair (double-float) arithmetic.
+#pragma once
+#include "vx_internal.h"
+
+namespace vx {
+
+__device__ __forceinline__ float ex2a(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcpa(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// (h, l) += (ah + al) * M : error-free product and two-sum in FP32 (no contraction).
+__device__ __forceinline__ void df_fma(float &h, float &l, float ah, float al, float M) {
+    float p = __fmul_rn(ah, M);
+    float pe = fmaf(ah, M, -p);
+    float s = __fadd_rn(h, p);
+    float bb = __fsub_rn(s, h);
+    float err = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    h = s;
+    l = __fadd_rn(l, __fadd_rn(err, fmaf(al, M, pe)));
+}
+// (h, l) += (bh, bl)
+__device__ __forceinline__ void df_add(float &h, float &l, float bh, float bl) {
+    float s = __fadd_rn(h, bh);
+    float bb = __fsub_rn(s, h);
+    float err = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(bh, bb));
+    h = s;
+    l = __fadd_rn(l, __fadd_rn(err, bl));
+}
+// (ph, pl) = (ah, al) * (bh, bl) to ~2^-44
+__device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, float &ph, float &pl) {
+    ph = __fmul_rn(ah, bh);
+    pl = __fadd_rn(fmaf(ah, bh, -ph), __fadd_rn(__fmul_rn(ah, bl), __fmul_rn(al, bh)));
+}
+
+// Projections of one quantity (blocking factor or one of its tangents) onto l = 0, 1 for
+// coupling terms I and II.
+struct Proj {
+    float o0I, o0II, o1Ih, o1Il, o1IIh, o1IIl;
+    __device__ __forceinline__ void zero() { o0I = o0II = o1Ih = o1Il = o1IIh = o1IIl = 0.f; }
+};
+
+struct ZoneSh {
+    double T, eta;
+    float il_h, il_l;  // log2(e)/T
+    float el_h, el_l;  // |eta| log2(e)
+    float sB, sP;      // 2^kb and 2^(kb+11): grids of the exact split (degenerate path)
+    float iB, iP;      // their inverses
+    int deg, neg, bad;
+};
+
+// Moments of one quantity against the three non-negative basis weights.
+struct Mom {
+    float p, m, z;
+    __device__ __forceinline__ void zero() { p = m = z = 0.f; }
+};
+
+// One (pair, omega) node loop. Fills the moments of the blocking factor O and, with ADJ, of
+// GTa = O (f_e E + f_ebar Ebar), GTp = O ((1-f_e) E + (1-f_ebar) Ebar), GEt = O (f_ebar - f_e).
+template <int NE, bool ADJ, bool DEG>
+__device__ __forceinline__ void node_loop(const Nodes32 &nd, int ne, float B, float Pe, float Pp,
+                                          float Bq, float Bl, float Pq, float Pl, float h, float Em,
+                                          Mom &mo, Mom &ta, Mom &tp, Mom &et) {
+    const int n = NE > 0 ? NE : ne;
+    auto accum = [&](int k, float e1, float e2, float t, float r) {
+        mo.p = fmaf(nd.cp[k], r, mo.p);
+        mo.m = fmaf(nd.cm[k], r, mo.m);
+        mo.z = fmaf(nd.c0[k], r, mo.z);
+        if (ADJ) {
+            float se = (1.f + e2) * r;   // 1 - f_e
+            float sp = t * r;            // 1 - f_ebar
+            float fe = e1 * se, fp = e2 * sp;
+            float E = fmaf(h, nd.u[k], Em), Eb = fmaf(h, nd.v[k], Em);
+            float ga = fmaf(fe, E, fp * Eb) * r;
+            float gp = fmaf(se, E, sp * Eb) * r;
+            float ge = (fp - fe) * r;
+            ta.p = fmaf(nd.cp[k], ga, ta.p); ta.m = fmaf(nd.cm[k], ga, ta.m); ta.z = fmaf(nd.c0[k], ga, ta.z);
+            tp.p = fmaf(nd.cp[k], gp, tp.p); tp.m = fmaf(nd.cm[k], gp, tp.m); tp.z = fmaf(nd.c0[k], gp, tp.z);
+            et.p = fmaf(nd.cp[k], ge, et.p); et.m = fmaf(nd.cm[k], ge, et.m); et.z = fmaf(nd.c0[k], ge, et.z);
+        }
+    };
+    if (!DEG) {
+        // |eta| <= eta_sw: d = (1+e1)(1+e2) <= 2 (1 + e^{eta_sw}), so a product of two stays finite.
+        int k = 0;
+#pragma unroll
+        for (; k + 1 < (NE > 0 ? NE : VX_MAX_NE); k += 2) {
+            if (NE == 0 && k + 1 >= n) break;
+            float xa = fmaf(B, nd.u[k], Pe), ya = fmaf(B, nd.v[k], Pp);
+            float xb = fmaf(B, nd.u[k + 1], Pe), yb = fmaf(B, nd.v[k + 1], Pp);
+            float e1a = ex2a(-xa), e2a = ex2a(-ya), e1b = ex2a(-xb), e2b = ex2a(-yb);
+            float ta_ = 1.f + e1a, tb_ = 1.f + e1b;
+            float da = fmaf(ta_, e2a, ta_), db = fmaf(tb_, e2b, tb_);
+            float R = rcpa(da * db);
+            accum(k, e1a, e2a, ta_, R * db);
+            accum(k + 1, e1b, e2b, tb_, R * da);
+        }
+        if (NE == 0 || (NE & 1)) {
+            for (; k < n; ++k) {
+                float x = fmaf(B, nd.u[k], Pe), y = fmaf(B, nd.v[k], Pp);
+                float e1 = ex2a(-x), e2 = ex2a(-y);
+                float t = 1.f + e1;
+                accum(k, e1, e2, t, rcpa(fmaf(t, e2, t)));
+            }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < (NE > 0 ? NE : VX_MAX_NE); ++k) {
+            if (NE == 0 && k >= n) break;
+            float s = fmaf(Bq, nd.uh[k], Pq);                      // exact by the grid choice
+            float lo = fmaf(Bq, nd.ul[k], fmaf(Bl, nd.u[k], Pl));  // small remainder
+            float e1 = ex2a(-s) * ex2a(-lo);
+            float e2 = ex2a(-fmaf(B, nd.v[k], Pp));
+            float t = 1.f + e1;
+            accum(k, e1, e2, t, rcpa(fmaf(t, e2, t)));
+        }
+    }
+}
+
+// Projection of one quantity's moments onto l = 0, 1 for terms I and II. (kp, km) are already
+// exchanged for eta < 0.
+template <bool DEG>
+__device__ __forceinline__ void project(Proj &P, const Mom &M, float kp, float km, float k0, float kpl,
+                                        float kml, float k0l, float th, float tl) {
+    float KI = fmaf(kp, M.p, fmaf(km, M.m, k0 * M.z));
+    float KII = fmaf(km, M.p, fmaf(kp, M.m, k0 * M.z));
+    P.o0I += KI;
+    P.o0II += KII;
+    if (!DEG) {
+        P.o1Ih = fmaf(th, KI, P.o1Ih);
+        P.o1IIh = fmaf(th, KII, P.o1IIh);
+    } else {
+        float lph, lpl, lmh, lml, l0h, l0l;
+        df_mul(th, tl, kp, kpl, lph, lpl);
+        df_mul(th, tl, km, kml, lmh, lml);
+        df_mul(th, tl, k0, k0l, l0h, l0l);
+        df_fma(P.o1Ih, P.o1Il, lph, lpl, M.p);
+        df_fma(P.o1Ih, P.o1Il, lmh, lml, M.m);
+        df_fma(P.o1Ih, P.o1Il, l0h, l0l, M.z);
+        df_fma(P.o1IIh, P.o1IIl, lmh, lml, M.p);
+        df_fma(P.o1IIh, P.o1IIl, lph, lpl, M.m);
+        df_fma(P.o1IIh, P.o1IIl, l0h, l0l, M.z);
+    }
+}
+
+// Writes (chunk 0) or adds (later chunks) one thread's projections into the zone matrices:
+// term I of pair (i,j) is Phi_I(i,j), term II is Phi_I(j,i).
+__device__ __forceinline__ void store_proj(float *q3, int N2, int N, int pi, int pj, int c, const Proj &P) {
+    float *M0 = q3, *M1h = q3 + N2, *M1l = q3 + 2 * N2;
+    const int a = pi * N + pj, b = pj * N + pi;
+    if (c == 0) {
+        M0[a] = P.o0I; M1h[a] = P.o1Ih; M1l[a] = P.o1Il;
+        if (pi != pj) { M0[b] = P.o0II; M1h[b] = P.o1IIh; M1l[b] = P.o1IIl; }
+    } else {
+        M0[a] += P.o0I;
+        df_add(M1h[a], M1l[a], P.o1Ih, P.o1Il);
+        if (pi != pj) { M0[b] += P.o0II; df_add(M1h[b], M1l[b], P.o1IIh, P.o1IIl); }
+    }
+}
+
+// Shared-memory layout (floats unless noted), N2 = N*N:
+//   mats[q][3][N2]: for each quantity q, l0, l1 hi, l1 lo of Phi_I(i,j) (term II = transpose)
+//   vec[4][S][N]  : contraction vectors per output (j0, chi0, j1, chi1) and species
+//   sc[N] (double): exp(-(eps_i + eps_0)/T);  em[N] (double): exp(-eps_i/T)
+__host__ __device__ inline size_t smem_mixed_bytes(int N, int S, bool adj) {
+    size_t nq = adj ? 4 : 1;
+    size_t f = nq * 3 * (size_t)N * N + 4 * (size_t)S * N;
+    f = (f + 1) & ~(size_t)1;
+    return f * 4 + 2 * (size_t)N * 8 + 64 * 8;
+}
+
+template <int NE, bool ADJ>
+__global__ void __launch_bounds__(VX_TPB_MAX, 1) k_pair_mixed(const __grid_constant__ Launch L) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ ZoneSh zs;
+    __shared__ long long s_zone;
+    const Common &C = L.c;
+    const int N = C.N, S = C.S, N2 = N * N, npair = C.npair, ms = C.ms;
+    const int nq = ADJ ? 4 : 1;
+    float *mats = reinterpret_cast<float *>(smraw);
+    float *vec = mats + (size_t)nq * 3 * N2;
+    size_t foff = ((size_t)nq * 3 * N2 + 4 * (size_t)S * N + 1) & ~(size_t)1;
+    double *sc = reinterpret_cast<double *>(smraw + foff * 4);
+    double *em = sc + N;
+    double *red = em + N;  // 64 doubles for block reductions
+    const int tid = threadIdx.x;
+    const int nslot = npair * ms;
+    const bool active = tid < nslot;
+    const int chunk = active ? tid / npair : 0;
+    const int p = active ? tid % npair : 0;
+    const int pi = C.pij[p] >> 8, pj = C.pij[p] & 0xff;
+    const int m0 = chunk * C.n_mu / ms, m1 = (chunk + 1) * C.n_mu / ms;
+
+    for (;;) {
+        if (tid == 0) s_zone = (long long)atomicAdd(L.counter, 1ull);
+        __syncthreads();
+        const long long z = s_zone;
+        if (z >= L.Z) break;
+
+        // ---- zone set-up (FP64, one thread) --------------------------------------------------
+        if (tid == 0) {
+            double T = L.state[4 * z + 0], eta = L.state[4 * z + 1];
+            int bad = !(T > 0.0) || !isfinite(T) || !isfinite(eta) || fabs(eta) > VX_ETA_MAX;
+            zs.bad = bad;
+            zs.T = T;
+            zs.eta = eta;
+            if (!bad) {
+                const double LOG2E = 1.4426950408889634;
+                double ae = fabs(eta);
+                double il = LOG2E / T, el = ae * LOG2E;
+                zs.il_h = (float)il;
+                zs.il_l = (float)(il - (double)zs.il_h);
+                zs.el_h = (float)el;
+                zs.el_l = (float)(el - (double)zs.el_h);
+                zs.neg = eta < 0.0;
+                zs.deg = ae > C.eta_sw;
+                // grid of the exact split: B_hi on 2^-kb with < 2^11 steps, P_hi and the sum on
+                // 2^-(kb+11) with |sum| < 2^24 steps
+                double Bmax = C.h_max * il * 1.0001 + 1e-30;
+                double Pmax = C.q0h_max * il + el + 1.0;
+                int kb = (int)floor(fmin(11.0 - log2(Bmax), 13.0 - log2(Pmax + 2.0 * Bmax))) - 1;
+                kb = kb < -60 ? -60 : (kb > 60 ? 60 : kb);
+                zs.sB = ldexpf(1.f, kb);
+                zs.iB = ldexpf(1.f, -kb);
+                zs.sP = ldexpf(1.f, kb + 11);
+                zs.iP = ldexpf(1.f, -(kb + 11));
+            }
+        }
+        __syncthreads();
+        const double T = zs.T;
+        if (zs.bad) {
+            // invalid state: NaN outputs, raise the flag, skip the work
+            const double nan = __longlong_as_double(0x7ff8000000000000ll);
+            for (int e = tid; e < S * N; e += blockDim.x) {
+                size_t o = (size_t)z * S * N + e;
+                if (L.j0) { L.j0[o] = nan; L.chi0[o] = nan; L.j1[o] = nan; L.chi1[o] = nan; }
+                if (ADJ && L.jac)
+                    for (int q = 0; q < 12; ++q) L.jac[o * 12 + q] = nan;
+            }
+            if (L.phi)
+                for (int e = tid; e < 4 * N2; e += blockDim.x) L.phi[(size_t)z * 4 * N2 + e] = nan;
+            if (ADJ && L.grad_state && tid < 4) L.grad_state[4 * z + tid] = nan;
+            if (tid == 0) atomicOr(L.flag, VX_FLAG_BAD_STATE);
+            __syncthreads();
+            continue;
+        }
+
+        // ---- per-zone vectors and FP64 scales (overlap with the node loops) --------------------
+        for (int e = tid; e < 4 * S * N; e += blockDim.x) {
+            int o = e / (S * N), s = (e / N) % S, j = e % N;
+            int pk = C.partner[s];
+            size_t a = ((size_t)z * S + pk) * N + j;
+            float sh = ex2a(-(float)(C.eps[j] - C.eps[0]) * zs.il_h);  // exp(-(eps_j-eps_0)/T)
+            float wj = (float)C.w[j];
+            float v;
+            if (o == 0) v = wj * (float)(1.0 - L.J[a]) * sh;
+            else if (o == 1) v = wj * (float)L.J[a];
+            else if (o == 2) v = wj * (float)L.H[a] * sh;
+            else v = wj * (float)L.H[a];
+            vec[e] = v;
+        }
+        for (int i = tid; i < N; i += blockDim.x) {
+            sc[i] = exp(-(C.eps[i] + C.eps[0]) / T);
+            em[i] = exp(-C.eps[i] / T);
+        }
+
+        // ---- quadrature ------------------------------------------------------------------------
+        Proj PO, PTa, PTp, PEt;
+        PO.zero();
+        if (ADJ) { PTa.zero(); PTp.zero(); PEt.zero(); }
+        if (active) {
+            const float il_h = zs.il_h, el_h = zs.el_h;
+            const bool deg = zs.deg, neg = zs.neg;
+            for (int m = m0; m < m1; ++m) {
+                const float4 *rec = L.tab32 + ((size_t)m * npair + p) * 3;
+                float4 R0 = __ldg(rec), R1 = __ldg(rec + 1), R2 = __ldg(rec + 2);
+                const float h = R0.x, h_lo = R0.y, Em = R0.z, Em_lo = R0.w;
+                float kp = R1.x, km = R1.y, k0 = R1.z, kpl = R2.x, kml = R2.y, k0l = R2.z;
+                if (neg) {  // eta < 0: electron and positron exchange roles, M+ <-> M-
+                    float t = kp; kp = km; km = t;
+                    t = kpl; kpl = kml; kml = t;
+                }
+                Mom mo, ta, tp, et;
+                mo.zero();
+                if (ADJ) { ta.zero(); tp.zero(); et.zero(); }
+                const float B = h * il_h;
+                const float Pp = fmaf(Em, il_h, el_h);
+                if (!deg) {
+                    const float Pe = fmaf(Em, il_h, -el_h);
+                    node_loop<NE, ADJ, false>(L.n32, C.n_e, B, Pe, Pp, 0.f, 0.f, 0.f, 0.f, h, Em, mo, ta, tp, et);
+                    project<false>(PO, mo, kp, km, k0, kpl, kml, k0l, C.t_hi[m], C.t_lo[m]);
+                    if (ADJ) {
+                        project<false>(PTa, ta, kp, km, k0, kpl, kml, k0l, C.t_hi[m], C.t_lo[m]);
+                        project<false>(PTp, tp, kp, km, k0, kpl, kml, k0l, C.t_hi[m], C.t_lo[m]);
+                        project<false>(PEt, et, kp, km, k0, kpl, kml, k0l, C.t_hi[m], C.t_lo[m]);
+                    }
+                } else {
+                    const float il_l = zs.il_l, el_l = zs.el_l;
+                    // B = h * log2e/T as a double-float, split onto the 2^-kb grid
+                    float bh = __fmul_rn(h, il_h);
+                    float bl = __fadd_rn(fmaf(h, il_h, -bh), __fadd_rn(__fmul_rn(h, il_l), __fmul_rn(h_lo, il_h)));
+                    float Bq = __fmul_rn(rintf(__fmul_rn(bh, zs.sB)), zs.iB);
+                    float Bl = __fadd_rn(__fsub_rn(bh, Bq), bl);
+                    // P = (E- log2e/T - |eta| log2e) as a double-float, split onto 2^-(kb+11)
+                    float ph = __fmul_rn(Em, il_h);
+                    float pl = __fadd_rn(fmaf(Em, il_h, -ph), __fadd_rn(__fmul_rn(Em, il_l), __fmul_rn(Em_lo, il_h)));
+                    float s = __fsub_rn(ph, el_h);
+                    float bb = __fsub_rn(s, ph);
+                    float err = __fadd_rn(__fsub_rn(ph, __fsub_rn(s, bb)), __fsub_rn(-el_h, bb));
+                    float slo = __fsub_rn(__fadd_rn(err, pl), el_l);
+                    float Pq = __fmul_rn(rintf(__fmul_rn(s, zs.sP)), zs.iP);
+                    float Pl = __fadd_rn(__fsub_rn(s, Pq), slo);
+                    node_loop<NE, ADJ, true>(L.n32, C.n_e, B, 0.f, Pp, Bq, Bl, Pq, Pl, h, Em, mo, ta, tp, et);
+                    project<true>(PO, mo, kp, km, k0, kpl, kml, k0l, C.t_hi[m], C.t_lo[m]);
+                    if (ADJ) {
+                        project<true>(PTa, ta, kp, km, k0, kpl, kml, k0l, C.t_hi[m], C.t_lo[m]);
+                        project<true>(PTp, tp, kp, km, k0, kpl, kml, k0l, C.t_hi[m], C.t_lo[m]);
+                        project<true>(PEt, et, kp, km, k0, kpl, kml, k0l, C.t_hi[m], C.t_lo[m]);
+                    }
+                }
+            }
+        }
+        // ---- combine the omega chunks into Phi_I(i,j) matrices, in chunk order (deterministic)
+        for (int c = 0; c < ms; ++c) {
+            if (active && chunk == c) {
+                store_proj(mats + 0 * 3 * (size_t)N2, N2, N, pi, pj, c, PO);
+                if (ADJ) {
+                    store_proj(mats + 1 * 3 * (size_t)N2, N2, N, pi, pj, c, PTa);
+                    store_proj(mats + 2 * 3 * (size_t)N2, N2, N, pi, pj, c, PTp);
+                    store_proj(mats + 3 * 3 * (size_t)N2, N2, N, pi, pj, c, PEt);
+                }
+            }
+            __syncthreads();
+        }
+
+        // ---- contraction (and tangents) --------------------------------------------------------
+        const double two_pi = 6.283185307179586;
+        const double c0 = two_pi * C.norm * C.g2, c1 = 3.0 * c0;
+        const double iT2 = 1.0 / (T * T);
+        const double sgn = zs.neg ? -1.0 : 1.0;  // d/deta of the eta >= 0 mapping
+        const int nout = 4 * S * N;
+        double gT = 0.0, gE = 0.0;
+        const bool want_fwd = L.j0 != nullptr;
+        for (int e = tid; e < nout; e += blockDim.x) {
+            const int o = e / (S * N), s = (e / N) % S, i = e % N;
+            const int l = o >> 1;                 // j0, chi0: l = 0; j1, chi1: l = 1
+            const bool prod = (o & 1) == 0;       // j0, j1 come from production
+            const float bI = C.bI[s], bII = C.bII[s];
+            const float *v = vec + (size_t)(o * S + s) * N;
+            const double cl = l ? c1 : c0;
+            const double scal = prod ? sc[i] : 1.0;
+            double res[3];  // contraction of: the kernel, its T tangent, its eta tangent
+            const int nres = ADJ ? 3 : 1;
+#pragma unroll
+            for (int r = 0; r < nres; ++r) {
+                const int q = r == 0 ? 0 : r == 2 ? 3 : (prod ? 2 : 1);
+                const float *M0 = mats + (size_t)(q * 3 + 0) * N2;
+                const float *M1h = mats + (size_t)(q * 3 + 1) * N2;
+                const float *M1l = mats + (size_t)(q * 3 + 2) * N2;
+                if (l == 0) {
+                    float acc = 0.f;
+                    for (int j = 0; j < N; ++j)
+                        acc = fmaf(fmaf(bI, M0[i * N + j], bII * M0[j * N + i]), v[j], acc);
+                    res[r] = (double)acc;
+                } else {
+                    float ah = 0.f, al = 0.f;
+                    for (int j = 0; j < N; ++j) {
+                        float kh, kl, th, tl;
+                        df_mul(bI, 0.f, M1h[i * N + j], M1l[i * N + j], kh, kl);
+                        df_mul(bII, 0.f, M1h[j * N + i], M1l[j * N + i], th, tl);
+                        df_add(kh, kl, th, tl);
+                        df_fma(ah, al, kh, kl, v[j]);
+                    }
+                    res[r] = (double)ah + (double)al;
+                }
+            }
+            const size_t oi = ((size_t)z * S + s) * N + i;
+            const double fwd = cl * scal * res[0];
+            if (want_fwd) {
+                double *dst = o == 0 ? L.j0 : o == 1 ? L.chi0 : o == 2 ? L.j1 : L.chi1;
+                dst[oi] = fwd;
+                if (!isfinite(fwd)) atomicOr(L.flag, VX_FLAG_NONFINITE);
+            }
+            if (ADJ) {
+                // production: d/dT = e^{-q0/T} GTp / T^2 ; annihilation: d/dT = -GTa / T^2
+                const double dT = cl * scal * (prod ? 1.0 : -1.0) * res[1] * iT2;
+                const double dE = cl * scal * sgn * res[2];
+                if (L.jac) {
+                    L.jac[oi * 12 + o * 3 + 0] = dT;
+                    L.jac[oi * 12 + o * 3 + 1] = dE;
+                    L.jac[oi * 12 + o * 3 + 2] = 0.0;
+                    if (!isfinite(dT) || !isfinite(dE)) atomicOr(L.flag, VX_FLAG_NONFINITE);
+                }
+                const double *g = o == 0 ? L.g_j0 : o == 1 ? L.g_chi0 : o == 2 ? L.g_j1 : L.g_chi1;
+                if (g) {
+                    const double gv = g[oi];
+                    gT += gv * dT;
+                    gE += gv * dE;
+                }
+            }
+        }
+        if (ADJ && L.grad_state) {
+            // deterministic block reduction: fixed shuffle tree, then warps in order
+            for (int off = 16; off > 0; off >>= 1) {
+                gT += __shfl_down_sync(0xffffffffu, gT, off);
+                gE += __shfl_down_sync(0xffffffffu, gE, off);
+            }
+            const int nw = (blockDim.x + 31) >> 5;
+            if ((tid & 31) == 0) { red[2 * (tid >> 5)] = gT; red[2 * (tid >> 5) + 1] = gE; }
+            __syncthreads();
+            if (tid == 0) {
+                double a = 0.0, b = 0.0;
+                for (int w = 0; w < nw; ++w) { a += red[2 * w]; b += red[2 * w + 1]; }
+                L.grad_state[4 * z + 0] = a;
+                L.grad_state[4 * z + 1] = b;
+                L.grad_state[4 * z + 2] = 0.0;
+                L.grad_state[4 * z + 3] = 0.0;
+            }
+        }
+        if (L.phi) {  // raw kernel of term I, G2 applied: [dir][l][i][j]
+            for (int e = tid; e < 4 * N2; e += blockDim.x) {
+                const int d = e / (2 * N2), l = (e / N2) & 1, ij = e % N2, i = ij / N, j = ij % N;
+                double a = l ? (double)mats[N2 + ij] + (double)mats[2 * N2 + ij] : (double)mats[ij];
+                double v = C.g2 * (d == 0 ? em[i] * em[j] * a : a);
+                L.phi[(size_t)z * 4 * N2 + e] = v;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace vx

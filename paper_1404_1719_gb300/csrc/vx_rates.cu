@@ -1,0 +1,529 @@
+// vx_rates.cu -- host side of the C ABI declared in include/vx_rates.h.
+//
+// create(): validates the config and builds, in FP64 on the host, everything that does not depend
+// on the zone state: Gauss-Legendre nodes in cos(omega) and electron energy, the energy weights,
+// and per (unordered bin pair, omega node) the half-width |q|/2, the lower electron energy E-, and
+// the three coefficients that turn the node moments into K_I and K_II. These are uploaded once.
+// eval()/adjoint(): host-side argument checks, then one persistent launch (optionally replayed from
+// a cached CUDA graph: work-counter reset + kernel).
+#include "../../include/vx_rates.h"
+#include "vx_internal.h"
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+namespace {
+
+thread_local std::string g_err = "";
+
+vx_status fail(vx_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+#define VX_CU(call)                                                                      \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return fail(e_ == cudaErrorMemoryAllocation ? VX_ERR_OOM : VX_ERR_CUDA,      \
+                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+// Gauss-Legendre nodes (ascending, exactly antisymmetric) and weights on [-1, 1]: Newton's method
+// on P_n from the asymptotic first guess cos(pi (k - 1/4) / (n + 1/2)).
+void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w) {
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    const double pi = 3.14159265358979323846;
+    for (int k = 1; k <= n / 2 + (n & 1); ++k) {
+        double r = std::cos(pi * (k - 0.25) / (n + 0.5));
+        double dP = 1.0;
+        for (int it = 0; it < 60; ++it) {
+            double Pm = 1.0, P = r;  // P_0, P_1
+            for (int m = 2; m <= n; ++m) {
+                double Pn = ((2 * m - 1) * r * P - (m - 1) * Pm) / m;
+                Pm = P;
+                P = Pn;
+            }
+            if (n == 1) { P = r; Pm = 1.0; }
+            dP = n * (Pm - r * P) / (1.0 - r * r);
+            double step = P / dP;
+            r -= step;
+            if (std::fabs(step) <= 1e-17) {
+                // one more evaluation of the derivative at the converged root
+                Pm = 1.0; P = r;
+                for (int m = 2; m <= n; ++m) {
+                    double Pn = ((2 * m - 1) * r * P - (m - 1) * Pm) / m;
+                    Pm = P;
+                    P = Pn;
+                }
+                if (n == 1) { P = r; Pm = 1.0; }
+                dP = n * (Pm - r * P) / (1.0 - r * r);
+                break;
+            }
+        }
+        double wk = 2.0 / ((1.0 - r * r) * dP * dP);
+        x[n - k] = r;
+        x[k - 1] = -r;
+        w[n - k] = wk;
+        w[k - 1] = wk;
+    }
+    if (n & 1) x[n / 2] = 0.0;
+}
+
+int round_up(int a, int b) { return (a + b - 1) / b * b; }
+
+}  // namespace
+
+struct vx_rates {
+    int device = 0;
+    int nsm = 0;
+    vx_config cfg{};
+    std::vector<double> eps, w;
+    std::vector<int> species;
+    vx::Common common{};
+    vx::Nodes32 n32{};
+    vx::Nodes64 n64{};
+    float4 *d_tab32 = nullptr;
+    double *d_tab64 = nullptr;
+    unsigned long long *d_counter = nullptr;
+    int *d_flag = nullptr;
+    // launch shapes (ms = omega chunks per pair)
+    int ms = 1, block = 32;
+    int grid_fwd = 0, grid_adj = 0, grid_64 = 0;
+    size_t smem_fwd = 0, smem_adj = 0, smem_64 = 0;
+    // graph of the last eval launch
+    cudaGraphExec_t gexec = nullptr;
+};
+
+extern "C" {
+
+const char *vx_status_string(vx_status s) {
+    switch (s) {
+        case VX_OK: return "VX_OK";
+        case VX_ERR_INVALID_ARG: return "VX_ERR_INVALID_ARG";
+        case VX_ERR_CUDA: return "VX_ERR_CUDA";
+        case VX_ERR_OOM: return "VX_ERR_OOM";
+        case VX_ERR_NUMERIC: return "VX_ERR_NUMERIC";
+        case VX_ERR_UNSUPPORTED: return "VX_ERR_UNSUPPORTED";
+        case VX_ERR_TIMEOUT: return "VX_ERR_TIMEOUT";
+    }
+    return "VX_ERR_UNKNOWN";
+}
+
+const char *vx_last_error(void) { return g_err.c_str(); }
+
+static vx_status validate_config(const vx_config *c) {
+    if (!c) return fail(VX_ERR_INVALID_ARG, "config is NULL");
+    if (c->n_bins < 2 || c->n_bins > VX_MAX_BINS - 1)  // N (N+1)/2 bin pairs must fit one CTA
+        return fail(VX_ERR_INVALID_ARG, "n_bins %d outside 2..%d", c->n_bins, VX_MAX_BINS - 1);
+    if (!c->eps) return fail(VX_ERR_INVALID_ARG, "eps is NULL");
+    for (int i = 0; i < c->n_bins; ++i) {
+        if (!(c->eps[i] > 0.0) || !std::isfinite(c->eps[i]))
+            return fail(VX_ERR_INVALID_ARG, "eps[%d] must be finite and > 0", i);
+        if (i && !(c->eps[i] > c->eps[i - 1]))
+            return fail(VX_ERR_INVALID_ARG, "eps must be strictly increasing (index %d)", i);
+        if (c->weights && (!(c->weights[i] > 0.0) || !std::isfinite(c->weights[i])))
+            return fail(VX_ERR_INVALID_ARG, "weights[%d] must be finite and > 0", i);
+    }
+    if (c->n_mu < 2 || c->n_mu > VX_MAX_MU) return fail(VX_ERR_INVALID_ARG, "n_mu %d outside 2..%d", c->n_mu, VX_MAX_MU);
+    if (c->n_e < 2 || c->n_e > VX_MAX_NE) return fail(VX_ERR_INVALID_ARG, "n_e %d outside 2..%d", c->n_e, VX_MAX_NE);
+    if (c->n_species < 1 || c->n_species > VX_MAX_SPECIES || !c->species)
+        return fail(VX_ERR_INVALID_ARG, "n_species must be 1..3 with a species list");
+    for (int s = 0; s < c->n_species; ++s) {
+        int sp = c->species[s];
+        if (sp < 0 || sp > 2) return fail(VX_ERR_INVALID_ARG, "species[%d] = %d is not a vx_species", s, sp);
+        for (int t = 0; t < s; ++t)
+            if (c->species[t] == sp) return fail(VX_ERR_INVALID_ARG, "species %d listed twice", sp);
+    }
+    for (int s = 0; s < c->n_species; ++s) {
+        int want = c->species[s] == VX_NU_E ? VX_NU_EBAR : c->species[s] == VX_NU_EBAR ? VX_NU_E : VX_NU_X;
+        bool ok = false;
+        for (int t = 0; t < c->n_species; ++t) ok |= c->species[t] == want;
+        if (!ok) return fail(VX_ERR_INVALID_ARG, "species %d needs its partner %d in the list", c->species[s], want);
+    }
+    if (!std::isfinite(c->sin2w) || !std::isfinite(c->g2) || !std::isfinite(c->norm))
+        return fail(VX_ERR_INVALID_ARG, "sin2w, g2 and norm must be finite");
+    if (!(c->eta_fp64 >= 0.0) || !std::isfinite(c->eta_fp64))
+        return fail(VX_ERR_INVALID_ARG, "eta_fp64 must be finite and >= 0");
+    if (c->eta_fp64 > 40.0)  // keeps two paired denominators below the FP32 range
+        return fail(VX_ERR_INVALID_ARG, "eta_fp64 must be <= 40");
+    if (c->prec != VX_PREC_FP64 && c->prec != VX_PREC_MIXED) return fail(VX_ERR_INVALID_ARG, "unknown precision");
+    if (c->flags & ~(VX_USE_GRAPH | VX_AUTOTUNE)) return fail(VX_ERR_INVALID_ARG, "unknown flag bits");
+    return VX_OK;
+}
+
+vx_status vx_rates_create(const vx_config *cfg, vx_rates **out) {
+    if (!out) return fail(VX_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    vx_status st = validate_config(cfg);
+    if (st != VX_OK) return st;
+    vx_rates *h = new vx_rates();
+    h->cfg = *cfg;
+    const int N = cfg->n_bins, S = cfg->n_species, nmu = cfg->n_mu, ne = cfg->n_e;
+    h->eps.assign(cfg->eps, cfg->eps + N);
+    h->species.assign(cfg->species, cfg->species + S);
+    h->cfg.eps = h->eps.data();
+    h->cfg.species = h->species.data();
+    // energy weights eps^2 d(eps): edges at geometric midpoints, outer edges half a log step out
+    h->w.resize(N);
+    for (int i = 0; i < N; ++i) {
+        if (cfg->weights) { h->w[i] = cfg->weights[i]; continue; }
+        double lo = i ? std::sqrt(h->eps[i - 1] * h->eps[i]) : h->eps[0] * std::sqrt(h->eps[0] / h->eps[1]);
+        double hi = i < N - 1 ? std::sqrt(h->eps[i] * h->eps[i + 1]) : h->eps[N - 1] * std::sqrt(h->eps[N - 1] / h->eps[N - 2]);
+        h->w[i] = h->eps[i] * h->eps[i] * (hi - lo);
+    }
+    h->cfg.weights = h->w.data();
+    if (h->cfg.eta_fp64 == 0.0) h->cfg.eta_fp64 = 10.0;
+
+    vx::Common &C = h->common;
+    C.N = N; C.n_mu = nmu; C.n_e = ne; C.S = S;
+    C.npair = N * (N + 1) / 2;
+    C.g2 = cfg->g2; C.norm = cfg->norm; C.eta_sw = h->cfg.eta_fp64;
+    for (int i = 0; i < N; ++i) { C.eps[i] = h->eps[i]; C.w[i] = h->w[i]; }
+    for (int s = 0; s < S; ++s) {
+        int sp = h->species[s];
+        int want = sp == VX_NU_E ? VX_NU_EBAR : sp == VX_NU_EBAR ? VX_NU_E : VX_NU_X;
+        for (int t = 0; t < S; ++t) if (h->species[t] == want) C.partner[s] = t;
+        C.species[s] = sp;
+        // couplings: (C_V +- C_A)^2, C_V = +-1/2 + 2 sin^2(theta_W), C_A = +-1/2 (nu_e / nu_x);
+        // anti-nu_e sees the transposed kernel, so its two terms swap
+        double cv = (sp == VX_NU_X ? -0.5 : 0.5) + 2.0 * cfg->sin2w, ca = sp == VX_NU_X ? -0.5 : 0.5;
+        double b1 = (cv + ca) * (cv + ca), b2 = (cv - ca) * (cv - ca);
+        if (sp == VX_NU_EBAR) std::swap(b1, b2);
+        C.bI64[s] = b1; C.bII64[s] = b2;
+        C.bI[s] = (float)b1; C.bII[s] = (float)b2;
+    }
+    {
+        int p = 0;
+        for (int i = 0; i < N; ++i)
+            for (int j = i; j < N; ++j) C.pij[p++] = (uint16_t)((i << 8) | j);
+    }
+    std::vector<double> tm, wm, tk, wk;
+    gauss_legendre(nmu, tm, wm);
+    gauss_legendre(ne, tk, wk);
+    for (int m = 0; m < nmu; ++m) {
+        C.t64[m] = tm[m];
+        C.t_hi[m] = (float)tm[m];
+        C.t_lo[m] = (float)(tm[m] - (double)C.t_hi[m]);
+    }
+    for (int k = 0; k < ne; ++k) {
+        double u = 1.0 + tk[k], v = 1.0 - tk[k];
+        h->n64.u[k] = u; h->n64.v[k] = v;
+        h->n64.cp[k] = wk[k] * u * u; h->n64.cm[k] = wk[k] * v * v; h->n64.c0[k] = wk[k] * u * v;
+        h->n32.u[k] = (float)u; h->n32.v[k] = (float)v;
+        h->n32.cp[k] = (float)h->n64.cp[k]; h->n32.cm[k] = (float)h->n64.cm[k]; h->n32.c0[k] = (float)h->n64.c0[k];
+        double uh = std::nearbyint(u * 2048.0) / 2048.0;
+        h->n32.uh[k] = (float)uh;
+        h->n32.ul[k] = (float)(u - uh);
+    }
+    // per (omega node m, unordered pair p) tables
+    const int np = C.npair;
+    std::vector<float4> t32((size_t)nmu * np * 3);
+    std::vector<double> t64((size_t)nmu * np * 5);
+    const double pi = 3.14159265358979323846;
+    double hmax = 0.0, q0hmax = 0.0;
+    for (int m = 0; m < nmu; ++m) {
+        const double t = tm[m], y = 1.0 - t;
+        for (int p = 0; p < np; ++p) {
+            const int i = C.pij[p] >> 8, j = C.pij[p] & 0xff;
+            const double e = h->eps[i], ep = h->eps[j];
+            const double d = e - ep, g = e * ep * (1.0 + t);
+            const double q2 = d * d + 2.0 * g, q = std::sqrt(q2), hh = 0.5 * q;
+            const double q0 = e + ep, s = 2.0 * e * ep * y;
+            const double Em = s / (2.0 * (q0 + q));
+            // K = G2 pi eps eps' y^2 / (16 |q|^2) sum_k w_k O_k P(tau_k), with the omega weight folded in
+            const double pref = wm[m] * pi * e * ep * y * y / (16.0 * q2);
+            const double kp = pref * 0.25 * (q + d) * (q + d), km = pref * 0.25 * (q - d) * (q - d), k0 = pref * 2.0 * g;
+            hmax = std::fmax(hmax, hh);
+            q0hmax = std::fmax(q0hmax, 0.5 * q0);
+            float4 *r = &t32[((size_t)m * np + p) * 3];
+            float fh = (float)hh, fEm = (float)Em, fkp = (float)kp, fkm = (float)km, fk0 = (float)k0;
+            r[0] = make_float4(fh, (float)(hh - fh), fEm, (float)(Em - fEm));
+            r[1] = make_float4(fkp, fkm, fk0, 0.f);
+            r[2] = make_float4((float)(kp - fkp), (float)(km - fkm), (float)(k0 - fk0), 0.f);
+            double *r64 = &t64[((size_t)m * np + p) * 5];
+            r64[0] = hh; r64[1] = Em; r64[2] = kp; r64[3] = km; r64[4] = k0;
+        }
+    }
+    C.h_max = hmax;
+    C.q0h_max = q0hmax;
+
+    // launch shape: omega chunks per pair so that pairs x chunks fills <= VX_TPB_MAX threads
+    int ms = 1;
+    for (int cand : {4, 2}) {
+        if (np * cand <= VX_TPB_MAX && nmu / cand >= 4) { ms = cand; break; }
+    }
+    if (np * ms > VX_TPB_MAX) {
+        delete h;
+        return fail(VX_ERR_UNSUPPORTED, "%d bin pairs exceed one CTA of %d threads", np, VX_TPB_MAX);
+    }
+    C.ms = ms;
+    h->ms = ms;
+    h->block = round_up(np * ms, 32);
+
+    auto cleanup = [&](vx_status s) { vx_rates_destroy(h); return s; };
+    cudaError_t ce = cudaGetDevice(&h->device);
+    if (ce != cudaSuccess) { vx_status s = fail(VX_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(ce)); delete h; return s; }
+    cudaDeviceProp prop;
+    if ((ce = cudaGetDeviceProperties(&prop, h->device)) != cudaSuccess) {
+        vx_status s = fail(VX_ERR_CUDA, "cudaGetDeviceProperties: %s", cudaGetErrorString(ce));
+        delete h;
+        return s;
+    }
+    h->nsm = prop.multiProcessorCount;
+#define VX_CUC(call)                                                                                   \
+    do {                                                                                               \
+        cudaError_t e_ = (call);                                                                       \
+        if (e_ != cudaSuccess)                                                                         \
+            return cleanup(fail(e_ == cudaErrorMemoryAllocation ? VX_ERR_OOM : VX_ERR_CUDA, "%s: %s", #call, \
+                                cudaGetErrorString(e_)));                                              \
+    } while (0)
+    VX_CUC(cudaMalloc(&h->d_tab32, t32.size() * sizeof(float4)));
+    VX_CUC(cudaMalloc(&h->d_tab64, t64.size() * sizeof(double)));
+    VX_CUC(cudaMalloc(&h->d_counter, sizeof(unsigned long long)));
+    VX_CUC(cudaMalloc(&h->d_flag, sizeof(int)));
+    VX_CUC(cudaMemcpy(h->d_tab32, t32.data(), t32.size() * sizeof(float4), cudaMemcpyHostToDevice));
+    VX_CUC(cudaMemcpy(h->d_tab64, t64.data(), t64.size() * sizeof(double), cudaMemcpyHostToDevice));
+    VX_CUC(cudaMemset(h->d_flag, 0, sizeof(int)));
+
+    h->smem_fwd = vx::smem_mixed(C, false);
+    h->smem_adj = vx::smem_mixed(C, true);
+    h->smem_64 = vx::smem_fp64(C);
+    struct K { const void *fn; size_t smem; int *grid; };
+    K ks[3] = {{vx::kernel_mixed_fwd(ne), h->smem_fwd, &h->grid_fwd},
+               {vx::kernel_mixed_adj(ne), h->smem_adj, &h->grid_adj},
+               {vx::kernel_fp64_fwd(ne), h->smem_64, &h->grid_64}};
+    for (K &k : ks) {
+        if (k.smem > 48 * 1024)
+            VX_CUC(cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem));
+        int occ = 0;
+        VX_CUC(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k.fn, h->block, k.smem));
+        if (occ < 1) return cleanup(fail(VX_ERR_UNSUPPORTED, "kernel does not fit on an SM (block %d, smem %zu)", h->block, k.smem));
+        *k.grid = occ * h->nsm;
+    }
+#undef VX_CUC
+    *out = h;
+    return VX_OK;
+}
+
+long long vx_rates_entries_per_zone(const vx_rates *h) {
+    return h ? (long long)h->common.N * h->common.N : 0;
+}
+
+static vx_status check_device_ptr(const void *p, const char *name) {
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(VX_ERR_INVALID_ARG, "%s: not a CUDA pointer", name);
+    }
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+        return fail(VX_ERR_INVALID_ARG, "%s must be device memory", name);
+    if (((uintptr_t)p) % 8) return fail(VX_ERR_INVALID_ARG, "%s must be 8-byte aligned", name);
+    return VX_OK;
+}
+
+static vx_status validate_batch(const vx_rates *h, const vx_batch *b) {
+    if (!h) return fail(VX_ERR_INVALID_ARG, "handle is NULL");
+    if (!b) return fail(VX_ERR_INVALID_ARG, "batch is NULL");
+    if (b->n_zones < 0) return fail(VX_ERR_INVALID_ARG, "n_zones < 0");
+    if (b->n_rays < 0) return fail(VX_ERR_INVALID_ARG, "n_rays < 0");
+    if (b->ray_offsets) {
+        if (b->ray_offsets[0] != 0) return fail(VX_ERR_INVALID_ARG, "ray_offsets[0] must be 0");
+        for (int r = 0; r < b->n_rays; ++r)
+            if (b->ray_offsets[r + 1] < b->ray_offsets[r])
+                return fail(VX_ERR_INVALID_ARG, "ray_offsets must be non-decreasing (ray %d)", r);
+        if ((long long)b->ray_offsets[b->n_rays] != b->n_zones)
+            return fail(VX_ERR_INVALID_ARG, "ray_offsets[n_rays] = %d but n_zones = %lld", b->ray_offsets[b->n_rays], b->n_zones);
+    }
+    if (b->n_zones == 0) return VX_OK;
+    vx_status s;
+    if ((s = check_device_ptr(b->state, "state")) != VX_OK) return s;
+    if ((s = check_device_ptr(b->J, "J")) != VX_OK) return s;
+    if ((s = check_device_ptr(b->H, "H")) != VX_OK) return s;
+    return VX_OK;
+}
+
+static vx_status validate_out(const vx_out *o, bool allow_phi) {
+    if (!o) return fail(VX_ERR_INVALID_ARG, "out is NULL");
+    vx_status s;
+    if ((s = check_device_ptr(o->j0, "out.j0")) != VX_OK) return s;
+    if ((s = check_device_ptr(o->chi0, "out.chi0")) != VX_OK) return s;
+    if ((s = check_device_ptr(o->j1, "out.j1")) != VX_OK) return s;
+    if ((s = check_device_ptr(o->chi1, "out.chi1")) != VX_OK) return s;
+    if (o->phi) {
+        if (!allow_phi) return fail(VX_ERR_INVALID_ARG, "phi output is not produced by this call");
+        if ((s = check_device_ptr(o->phi, "out.phi")) != VX_OK) return s;
+    }
+    return VX_OK;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard() { if (prev >= 0) cudaSetDevice(prev); }
+};
+
+// Launch through a graph (memset node + kernel node), re-using the executable graph when the
+// topology is unchanged and only the parameters differ.
+static vx_status launch_graph(vx_rates *h, const void *fn, void *param, int grid, size_t smem, cudaStream_t s) {
+    cudaGraph_t g = nullptr;
+    cudaGraphNode_t nm = nullptr, nk = nullptr;
+    VX_CU(cudaGraphCreate(&g, 0));
+    cudaMemsetParams mp{};
+    mp.dst = h->d_counter;
+    mp.value = 0;
+    mp.elementSize = 4;
+    mp.width = 2;
+    mp.height = 1;
+    mp.pitch = 0;
+    cudaError_t e = cudaGraphAddMemsetNode(&nm, g, nullptr, 0, &mp);
+    cudaKernelNodeParams kp{};
+    kp.func = (void *)fn;
+    kp.gridDim = dim3(grid);
+    kp.blockDim = dim3(h->block);
+    kp.sharedMemBytes = (unsigned)smem;
+    void *args[1] = {param};
+    kp.kernelParams = args;
+    if (e == cudaSuccess) e = cudaGraphAddKernelNode(&nk, g, &nm, 1, &kp);
+    if (e == cudaSuccess) {
+        bool fresh = true;
+        if (h->gexec) {
+            cudaGraphExecUpdateResultInfo info;
+            if (cudaGraphExecUpdate(h->gexec, g, &info) == cudaSuccess) fresh = false;
+            else {
+                cudaGetLastError();
+                cudaGraphExecDestroy(h->gexec);
+                h->gexec = nullptr;
+            }
+        }
+        if (fresh) e = cudaGraphInstantiate(&h->gexec, g, 0);
+        if (e == cudaSuccess) e = cudaGraphLaunch(h->gexec, s);
+    }
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(VX_ERR_CUDA, "graph launch: %s", cudaGetErrorString(e));
+    return VX_OK;
+}
+
+static void fill_launch(const vx_rates *h, const vx_batch *b, vx::Launch &L) {
+    L.c = h->common;
+    L.n32 = h->n32;
+    L.tab32 = h->d_tab32;
+    L.tab64 = h->d_tab64;
+    L.Z = b->n_zones;
+    L.state = b->state; L.J = b->J; L.H = b->H;
+    L.j0 = L.chi0 = L.j1 = L.chi1 = L.phi = nullptr;
+    L.jac = L.grad_state = nullptr;
+    L.g_j0 = L.g_chi0 = L.g_j1 = L.g_chi1 = nullptr;
+    L.counter = h->d_counter;
+    L.flag = h->d_flag;
+}
+
+vx_status vx_rates_eval(vx_rates *h, const vx_batch *b, const vx_out *out, vx_stream stream) {
+    vx_status st = validate_batch(h, b);
+    if (st != VX_OK) return st;
+    if (b->n_zones == 0) return VX_OK;
+    if ((st = validate_out(out, true)) != VX_OK) return st;
+    DeviceGuard dg(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool graph = (h->cfg.flags & VX_USE_GRAPH) != 0;
+    if (h->cfg.prec == VX_PREC_MIXED) {
+        vx::Launch L;
+        fill_launch(h, b, L);
+        L.j0 = out->j0; L.chi0 = out->chi0; L.j1 = out->j1; L.chi1 = out->chi1; L.phi = out->phi;
+        int grid = (int)std::min<long long>(h->grid_fwd, b->n_zones);
+        if (graph) return launch_graph(h, vx::kernel_mixed_fwd(h->common.n_e), &L, grid, h->smem_fwd, s);
+        VX_CU(cudaMemsetAsync(h->d_counter, 0, sizeof(unsigned long long), s));
+        VX_CU(vx::launch_mixed_fwd(L, grid, h->block, h->smem_fwd, s));
+    } else {
+        vx::Launch64 L;
+        L.c = h->common;
+        L.n64 = h->n64;
+        L.tab64 = h->d_tab64;
+        L.Z = b->n_zones;
+        L.state = b->state; L.J = b->J; L.H = b->H;
+        L.j0 = out->j0; L.chi0 = out->chi0; L.j1 = out->j1; L.chi1 = out->chi1; L.phi = out->phi;
+        L.counter = h->d_counter;
+        L.flag = h->d_flag;
+        int grid = (int)std::min<long long>(h->grid_64, b->n_zones);
+        if (graph) return launch_graph(h, vx::kernel_fp64_fwd(h->common.n_e), &L, grid, h->smem_64, s);
+        VX_CU(cudaMemsetAsync(h->d_counter, 0, sizeof(unsigned long long), s));
+        VX_CU(vx::launch_fp64_fwd(L, grid, h->block, h->smem_64, s));
+    }
+    return VX_OK;
+}
+
+vx_status vx_rates_adjoint(vx_rates *h, const vx_batch *b, const vx_out *grad_out, double *jac,
+                           double *grad_state, const vx_out *fwd, vx_stream stream) {
+    vx_status st = validate_batch(h, b);
+    if (st != VX_OK) return st;
+    if (h->cfg.prec != VX_PREC_MIXED) return fail(VX_ERR_UNSUPPORTED, "the adjoint is provided for the mixed form");
+    if (!jac && !grad_state && !fwd) return fail(VX_ERR_INVALID_ARG, "no output requested");
+    if (grad_state && !grad_out) return fail(VX_ERR_INVALID_ARG, "grad_state needs grad_out");
+    if (b->n_zones == 0) return VX_OK;
+    if (jac && (st = check_device_ptr(jac, "jac")) != VX_OK) return st;
+    if (grad_state && (st = check_device_ptr(grad_state, "grad_state")) != VX_OK) return st;
+    if (fwd && (st = validate_out(fwd, false)) != VX_OK) return st;
+    if (grad_state) {
+        const double *g[4] = {grad_out->j0, grad_out->chi0, grad_out->j1, grad_out->chi1};
+        const char *nm[4] = {"grad_out.j0", "grad_out.chi0", "grad_out.j1", "grad_out.chi1"};
+        for (int k = 0; k < 4; ++k)
+            if (g[k] && (st = check_device_ptr(g[k], nm[k])) != VX_OK) return st;
+    }
+    DeviceGuard dg(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    vx::Launch L;
+    fill_launch(h, b, L);
+    if (fwd) { L.j0 = fwd->j0; L.chi0 = fwd->chi0; L.j1 = fwd->j1; L.chi1 = fwd->chi1; }
+    L.jac = jac;
+    L.grad_state = grad_state;
+    if (grad_state) { L.g_j0 = grad_out->j0; L.g_chi0 = grad_out->chi0; L.g_j1 = grad_out->j1; L.g_chi1 = grad_out->chi1; }
+    int grid = (int)std::min<long long>(h->grid_adj, b->n_zones);
+    if (h->cfg.flags & VX_USE_GRAPH) return launch_graph(h, vx::kernel_mixed_adj(h->common.n_e), &L, grid, h->smem_adj, s);
+    VX_CU(cudaMemsetAsync(h->d_counter, 0, sizeof(unsigned long long), s));
+    VX_CU(vx::launch_mixed_adj(L, grid, h->block, h->smem_adj, s));
+    return VX_OK;
+}
+
+vx_status vx_rates_check(vx_rates *h, vx_stream stream) {
+    if (!h) return fail(VX_ERR_INVALID_ARG, "handle is NULL");
+    DeviceGuard dg(h->device);
+    VX_CU(cudaStreamSynchronize((cudaStream_t)stream));
+    int flag = 0;
+    VX_CU(cudaMemcpy(&flag, h->d_flag, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+        VX_CU(cudaMemset(h->d_flag, 0, sizeof(int)));
+        return fail(VX_ERR_NUMERIC, "device numeric flag 0x%x (%s%s)", flag,
+                    (flag & VX_FLAG_BAD_STATE) ? "invalid zone state; " : "",
+                    (flag & VX_FLAG_NONFINITE) ? "non-finite result" : "");
+    }
+    return VX_OK;
+}
+
+void vx_rates_destroy(vx_rates *h) {
+    if (!h) return;
+    DeviceGuard dg(h->device);
+    cudaDeviceSynchronize();
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    cudaFree(h->d_tab32);
+    cudaFree(h->d_tab64);
+    cudaFree(h->d_counter);
+    cudaFree(h->d_flag);
+    delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,164 @@
+"""PyTorch-facing wrapper of the C ABI: device buffers and streams come from torch, every step of
+the computation runs in libvx_rates.
+
+    rates = PairRates(eps, n_mu=32, n_e=64)                    # one handle per device/stream
+    out = rates.evaluate(state, J, H)                           # dict of [Z][S][N] float64 tensors
+    jac = rates.jacobian(state, J, H)                           # [Z][S][N][4][3]
+    j0, chi0, j1, chi1 = VxRatesFn.apply(rates, state, J, H)    # differentiable in `state`
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import capi
+
+_OUT_KEYS = ("j0", "chi0", "j1", "chi1")
+
+
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+class PairRates:
+    """Handle of the pair-process rate library for one energy grid and quadrature."""
+
+    def __init__(self, eps, n_mu: int, n_e: int, species=(0, 1, 2), weights=None, sin2w: float = 0.23,
+                 g2: float = 1.0, norm: float = 1.0, eta_fp64: float = 0.0, precision: str = "mixed",
+                 graph: bool = False, device=None):
+        self.eps = np.ascontiguousarray(eps, dtype=np.float64)
+        self.weights = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64)
+        self.species = np.ascontiguousarray(species, dtype=np.int32)
+        self.N, self.S = len(self.eps), len(self.species)
+        self.n_mu, self.n_e = int(n_mu), int(n_e)
+        self.precision = precision
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else torch.device(device).index)
+        prec = {"mixed": capi.VX_PREC_MIXED, "fp64": capi.VX_PREC_FP64}[precision]
+        cfg = capi.vx_config(
+            n_bins=self.N, eps=self.eps.ctypes.data_as(capi._dp),
+            weights=None if self.weights is None else self.weights.ctypes.data_as(capi._dp),
+            n_mu=self.n_mu, n_e=self.n_e, n_species=self.S, species=self.species.ctypes.data_as(capi._ip),
+            sin2w=sin2w, g2=g2, norm=norm, eta_fp64=eta_fp64, prec=prec,
+            flags=capi.VX_USE_GRAPH if graph else 0)
+        with torch.cuda.device(self.device):
+            self._h = capi.vx_rates_create(cfg)
+
+    # ------------------------------------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            capi.vx_rates_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def entries_per_zone(self) -> int:
+        """Kernel entries per zone and l: N^2."""
+        return capi.vx_rates_entries_per_zone(self._h)
+
+    def _batch(self, state, J, H, ray_offsets):
+        Z = state.shape[0]
+        for name, t, shape in (("state", state, (Z, 4)), ("J", J, (Z, self.S, self.N)), ("H", H, (Z, self.S, self.N))):
+            if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous() or tuple(t.shape) != shape:
+                raise ValueError(f"{name} must be a contiguous CUDA float64 tensor of shape {shape}")
+        offs = None
+        nr = 1
+        if ray_offsets is not None:
+            offs = np.ascontiguousarray(ray_offsets, dtype=np.int32)
+            nr = len(offs) - 1
+        b = capi.vx_batch(n_rays=nr, n_zones=Z, ray_offsets=None if offs is None else offs.ctypes.data_as(capi._ip),
+                          state=state.data_ptr(), J=J.data_ptr(), H=H.data_ptr())
+        b._keep = offs
+        return b
+
+    def _alloc(self, Z):
+        return {k: torch.empty((Z, self.S, self.N), dtype=torch.float64, device=self.device) for k in _OUT_KEYS}
+
+    @staticmethod
+    def _stream(stream):
+        s = stream if stream is not None else torch.cuda.current_stream()
+        return s.cuda_stream
+
+    def evaluate(self, state, J, H, ray_offsets=None, phi: bool = False, out=None, stream=None) -> dict:
+        """Rates j0, chi0, j1, chi1 of every zone ([Z][S][N] float64); phi=True adds the raw kernel
+        of term I, [Z][2 dir][2 l][N][N]."""
+        Z = state.shape[0]
+        b = self._batch(state, J, H, ray_offsets)
+        res = out if out is not None else self._alloc(Z)
+        if phi and "phi" not in res:
+            res["phi"] = torch.empty((Z, 2, 2, self.N, self.N), dtype=torch.float64, device=self.device)
+        o = capi.vx_out(*(_ptr(res[k]) for k in _OUT_KEYS), _ptr(res.get("phi")) if phi else None)
+        capi.vx_rates_eval(self._h, b, o, self._stream(stream))
+        return res
+
+    def adjoint(self, state, J, H, grad_out=None, jacobian: bool = True, forward: bool = False,
+                ray_offsets=None, stream=None) -> dict:
+        """One pass giving the Jacobian [Z][S][N][4][3] (d(j0,chi0,j1,chi1)/d(T,eta_e,Y_e)), the
+        vector-Jacobian product grad_state [Z][4] for grad_out (dict of [Z][S][N] tensors) and/or
+        the forward rates."""
+        Z = state.shape[0]
+        b = self._batch(state, J, H, ray_offsets)
+        res = {}
+        if jacobian:
+            res["jac"] = torch.empty((Z, self.S, self.N, 4, 3), dtype=torch.float64, device=self.device)
+        g = None
+        if grad_out is not None:
+            g = capi.vx_out(*(_ptr(grad_out.get(k)) for k in _OUT_KEYS), None)
+            res["grad_state"] = torch.empty((Z, 4), dtype=torch.float64, device=self.device)
+        fwd = None
+        if forward:
+            res.update(self._alloc(Z))
+            fwd = capi.vx_out(*(_ptr(res[k]) for k in _OUT_KEYS), None)
+        capi.vx_rates_adjoint(self._h, b, g, _ptr(res.get("jac")), _ptr(res.get("grad_state")), fwd,
+                              self._stream(stream))
+        return res
+
+    def jacobian(self, state, J, H, **kw):
+        return self.adjoint(state, J, H, jacobian=True, **kw)["jac"]
+
+    def check(self, stream=None) -> bool:
+        """Synchronise and read the device numeric flag: True if clean."""
+        return capi.vx_rates_check(self._h, self._stream(stream)) == capi.VX_OK
+
+    # ------------------------------------------------------------------------------------------
+    def evaluate_host(self, state, J, H, ray_offsets=None, stream=None) -> dict:
+        """End-to-end call with host (numpy or pinned torch) inputs: host->device copies, the rate
+        evaluation and device->host copies of the four rate arrays, all on one stream."""
+        s = stream if stream is not None else torch.cuda.current_stream()
+        with torch.cuda.stream(s):
+            dev = [torch.as_tensor(x).to(self.device, non_blocking=True) for x in (state, J, H)]
+            res = self.evaluate(*dev, ray_offsets=ray_offsets, stream=s)
+            host = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in res.items()}
+            for k in res:
+                host[k].copy_(res[k], non_blocking=True)
+        s.synchronize()
+        return host
+
+
+class VxRatesFn(torch.autograd.Function):
+    """(j0, chi0, j1, chi1) = f(state; J, H): forward through vx_rates_eval, backward through the
+    adjoint kernel in vector-Jacobian mode. Gradients flow to `state` (T, eta_e; the Y_e and rho
+    entries are zero for this process); J and H are treated as constants."""
+
+    @staticmethod
+    def forward(ctx, rates: PairRates, state, J, H):
+        out = rates.evaluate(state, J, H)
+        ctx.rates = rates
+        ctx.save_for_backward(state, J, H)
+        return tuple(out[k] for k in _OUT_KEYS)
+
+    @staticmethod
+    def backward(ctx, *grads):
+        state, J, H = ctx.saved_tensors
+        g = {k: (gr.contiguous() if gr is not None else None) for k, gr in zip(_OUT_KEYS, grads)}
+        res = ctx.rates.adjoint(state, J, H, grad_out=g, jacobian=False)
+        return None, res["grad_state"], None, None

@@ -1,0 +1,180 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle on the same seeded inputs.
+
+Tolerances: 1e-12 for the plain FP64 form, 1e-5 for the mixed form, measured per output row
+(zone, species) over the energy bins, normwise and elementwise on entries >= 1e-3 of the row max.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import vx_inputs
+from _metrics import row_errors, worst
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+KEYS = ("j0", "chi0", "j1", "chi1")
+TOL = {"fp64": 1e-12, "mixed": 1e-5}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1404_1719_gb300 import _build
+    _build.build()
+    oracle.build()
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).cuda()
+
+
+def make(b, precision, **kw):
+    from paper_1404_1719_gb300 import PairRates
+    return PairRates(b["eps"], b["n_mu"], b["n_e"], species=b["species"], precision=precision, **kw)
+
+
+def run_pair(b, precision, zones=None, **kw):
+    st, J, H = b["state"], b["J"], b["H"]
+    if zones is not None:
+        st, J, H = st[zones], J[zones], H[zones]
+    rates = make(b, precision, **kw)
+    out = rates.evaluate(dev(st), dev(J), dev(H), phi=True)
+    ok = rates.check()
+    got = {k: v.cpu().numpy() for k, v in out.items()}
+    rates.close()
+    ref = oracle.evaluate(b["eps"], b["n_mu"], b["n_e"], b["species"], st, J, H, phi=True)
+    return got, ref, ok
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("workload", [1, 2])
+def test_parity_small_workloads(workload, precision):
+    b = vx_inputs.make_batch(workload)
+    got, ref, ok = run_pair(b, precision)
+    assert ok
+    tol = TOL[precision]
+    for k in KEYS:
+        e = worst(got[k], ref[k])
+        assert e <= tol, f"{k}: {e:.3e} > {tol}"
+    # raw kernel dump: rows (zone, dir, l, i) over j
+    assert worst(got["phi"], ref["phi"]) <= tol
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_parity_degenerate_ray(precision):
+    """One ray of the 3-D-scale workload: eta_e up to ~63, 16 x 48 quadrature."""
+    b = vx_inputs.make_batch(5, rays=[7])
+    got, ref, ok = run_pair(b, precision)
+    assert ok
+    for k in KEYS:
+        assert worst(got[k], ref[k]) <= TOL[precision], k
+
+
+def _edge_batch():
+    eps = vx_inputs.energy_centres(13, 1.0, 300.0)
+    rows = []
+    for T in (0.3, 1.0, 7.0, 40.0):
+        for eta in (-45.0, -12.0, -3.0, 0.0, 2.5, 9.999, 10.001, 25.0, 60.0, 79.5):
+            rows.append((T, eta))
+    st, J, H = vx_inputs.random_zones(len(rows), 21, n_bins=13)
+    st[:, 0] = [r[0] for r in rows]
+    st[:, 1] = [r[1] for r in rows]
+    return dict(eps=eps, n_mu=8, n_e=20, species=np.array([0, 1, 2], np.int32), state=st, J=J, H=H)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_parity_edge_states(precision):
+    """Negative and large degeneracy, both sides of the precision switch, cold and hot zones,
+    an electron-energy node count without an unrolled instantiation."""
+    b = _edge_batch()
+    got, ref, ok = run_pair(b, precision)
+    assert ok
+    for k in KEYS:
+        assert worst(got[k], ref[k]) <= TOL[precision], k
+    assert worst(got["phi"], ref["phi"]) <= TOL[precision]
+
+
+@pytest.mark.parametrize("species", [[2], [1, 0], [0, 2, 1]])
+def test_species_subsets_and_order(species):
+    b = vx_inputs.make_batch(1, rays=[0])
+    sp = np.array(species, np.int32)
+    st, J, H = vx_inputs.random_zones(24, 3, n_bins=17, n_species=len(sp))
+    bb = dict(eps=b["eps"], n_mu=8, n_e=16, species=sp, state=st, J=J, H=H)
+    got, ref, ok = run_pair(bb, "mixed")
+    assert ok
+    for k in KEYS:
+        assert worst(got[k], ref[k]) <= 1e-5
+
+
+def test_invalid_state_raises_flag_and_spares_other_zones():
+    from paper_1404_1719_gb300 import capi
+    b = vx_inputs.make_batch(1, rays=[0])
+    st = b["state"][:6].copy()
+    st[2, 0] = -1.0        # T <= 0
+    st[4, 1] = 95.0        # |eta| beyond the supported range
+    rates = make(b, "mixed")
+    out = rates.evaluate(dev(st), dev(b["J"][:6]), dev(b["H"][:6]))
+    assert capi.vx_rates_check(rates.handle, torch.cuda.current_stream().cuda_stream) == capi.VX_ERR_NUMERIC
+    assert rates.check()  # the flag is cleared by the read
+    j0 = out["j0"].cpu().numpy()
+    assert np.all(np.isnan(j0[[2, 4]])) and np.all(np.isfinite(j0[[0, 1, 3, 5]]))
+    ref = oracle.evaluate(b["eps"], b["n_mu"], b["n_e"], b["species"], st[[0, 1, 3, 5]], b["J"][[0, 1, 3, 5]],
+                          b["H"][[0, 1, 3, 5]])
+    assert worst(j0[[0, 1, 3, 5]], ref["j0"]) <= 1e-5
+    rates.close()
+
+
+def test_host_argument_checks():
+    from paper_1404_1719_gb300 import capi
+    b = vx_inputs.make_batch(1, rays=[0])
+    rates = make(b, "mixed")
+    st, J, H = dev(b["state"]), dev(b["J"]), dev(b["H"])
+    with pytest.raises(capi.VxError) as e:  # ray offsets that do not cover the zones
+        rates.evaluate(st, J, H, ray_offsets=[0, 10, 20])
+    assert e.value.status == capi.VX_ERR_INVALID_ARG
+    bt = capi.vx_batch(n_rays=1, n_zones=st.shape[0], ray_offsets=None, state=st.data_ptr(), J=J.data_ptr(),
+                       H=H.data_ptr())
+    host = np.zeros(st.shape[0] * 3 * 17)
+    o = capi.vx_out(host.ctypes.data, host.ctypes.data, host.ctypes.data, host.ctypes.data, None)
+    with pytest.raises(capi.VxError) as e:  # host memory as an output
+        capi.vx_rates_eval(rates.handle, bt, o, 0)
+    assert e.value.status == capi.VX_ERR_INVALID_ARG
+    empty = torch.empty((0, 4), dtype=torch.float64, device="cuda")
+    rates.evaluate(empty, torch.empty((0, 3, 17), dtype=torch.float64, device="cuda"),
+                   torch.empty((0, 3, 17), dtype=torch.float64, device="cuda"))
+    assert rates.check()
+    rates.close()
+
+
+def test_graph_replay_is_bitwise_deterministic():
+    b = vx_inputs.make_batch(2)
+    st, J, H = dev(b["state"]), dev(b["J"]), dev(b["H"])
+    ra = make(b, "mixed", graph=True)
+    rb = make(b, "mixed", graph=False)
+    a1 = ra.evaluate(st, J, H)
+    a1 = {k: v.clone() for k, v in a1.items()}
+    a2 = ra.evaluate(st, J, H)
+    c = rb.evaluate(st, J, H)
+    torch.cuda.synchronize()
+    for k in KEYS:
+        assert torch.equal(a1[k], a2[k]) and torch.equal(a1[k], c[k]), k
+    ra.close()
+    rb.close()
+
+
+def test_ragged_rays_full_size_sampled():
+    """2048 rays of 300..550 zones in one launch, graph-captured; sampled zones against the oracle."""
+    b = vx_inputs.make_batch(3)
+    Z = b["state"].shape[0]
+    rates = make(b, "mixed", graph=True)
+    out = rates.evaluate(dev(b["state"]), dev(b["J"]), dev(b["H"]), ray_offsets=b["ray_offsets"])
+    assert rates.check()
+    rng = np.random.default_rng(3)
+    offs = b["ray_offsets"]
+    pick = np.unique(np.concatenate([rng.integers(0, Z, 24), offs[1:-1][:4], offs[1:][-3:] - 1, [0, Z - 1]]))
+    ref = oracle.evaluate(b["eps"], b["n_mu"], b["n_e"], b["species"], b["state"][pick], b["J"][pick], b["H"][pick])
+    for k in KEYS:
+        assert worst(out[k][torch.as_tensor(pick, device="cuda")].cpu().numpy(), ref[k]) <= 1e-5, k
+    rates.close()
