@@ -154,7 +154,7 @@ def run_ours(args):
     from paper_1404_1719_gb300 import PairRates, _build
     _build.build()
 
-    b = vx_inputs.make_batch(WORKLOAD, seed=rank)
+    b = vx_inputs.make_batch(WORKLOAD, seed=rank, rays=None if args.rays is None else range(args.rays))
     Z, N, S = b["state"].shape[0], len(b["eps"]), len(b["species"])
     host = {k: torch.from_numpy(np.ascontiguousarray(b[k])).pin_memory() for k in ("state", "J", "H")}
     d = {k: v.to(dev) for k, v in host.items()}
@@ -231,7 +231,7 @@ def run_ours(args):
         nodes = Z * npair * b["n_mu"] * b["n_e"]
         achieved = nodes * algorithmic_flops_per_node(True) / (ms_local / 1000) / 1e12
         # FP64 forward-only comparison on a sample of the same workload
-        sub = 48 * 400
+        sub = min(48 * 400, Z)
         r64 = PairRates(b["eps"], b["n_mu"], b["n_e"], species=b["species"], precision="fp64")
         o64 = {k: torch.empty((sub, S, N), dtype=torch.float64, device=dev) for k in out}
         args64 = (d["state"][:sub], d["J"][:sub], d["H"][:sub])
@@ -248,7 +248,8 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": vx_inputs.WORKLOADS[WORKLOAD]["name"] + " forward+jacobian (mixed)",
+            "config": {"workload": vx_inputs.WORKLOADS[WORKLOAD]["name"] + " forward+jacobian (mixed)"
+                       + ("" if args.rays is None else f" [first {args.rays} rays]"),
                        "zones": Z, "rays": int(len(b["ray_offsets"]) - 1), "bins": N,
                        "quadrature": f"{b['n_mu']}x{b['n_e']}", "species": S,
                        "l2": "inputs larger than L2 (J, H: %.2f GB)" % (2 * b["J"].nbytes / 1e9),
@@ -282,6 +283,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU-baseline leg")
+    ap.add_argument("--rays", type=int, default=None,
+                    help="use only the first R rays of the workload (small cases for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -203,12 +203,15 @@ void vxo_kernel_point(double eps, double epsp, double y, double T, double eta, i
 /* ---------------------------------------------------------------------------------------- */
 /* Phi^dir_{l,X}(i,j) of one zone for all ordered bin pairs (i = nu bin, j = nubar bin).       */
 /* phi layout [dir][X][l][i][j]; dphi (optional) [dir][X][l][i][j][2] with d/dT, d/deta.        */
+/* phiabs (optional): the same sums with |P_l|, i.e. the magnitude that bounds the rounding of   */
+/* the l = 1 projection (whose terms change sign with cos(omega)); equal to phi for l = 0.       */
 void vxo_phi_zone(int n, const double *eps, int n_mu, const double *tmu, const double *wmu,
                   int n_e, const double *tE, const double *wE, double g2, double T, double eta,
-                  int occ, double *phi, double *dphi)
+                  int occ, double *phi, double *dphi, double *phiabs)
 {
     size_t NN = (size_t)n * n;
     memset(phi, 0, 8 * NN * sizeof(double));
+    if (phiabs) memset(phiabs, 0, 8 * NN * sizeof(double));
     if (dphi) memset(dphi, 0, 16 * NN * sizeof(double));
     for (int i = 0; i < n; i++)
         for (int j = 0; j < n; j++)
@@ -222,6 +225,7 @@ void vxo_phi_zone(int n, const double *eps, int n_mu, const double *tmu, const d
                             double Pl = (l == 0) ? 1.0 : tmu[m];
                             size_t o = (((size_t)(d * 2 + X) * 2 + l) * n + i) * n + j;
                             phi[o] += wmu[m] * Pl * g2 * K[2 * d + X];
+                            if (phiabs) phiabs[o] += wmu[m] * fabs(Pl) * g2 * K[2 * d + X];
                             if (dphi) {
                                 dphi[2 * o + 0] += wmu[m] * Pl * g2 * dK[(2 * d + X) * 2 + 0];
                                 dphi[2 * o + 1] += wmu[m] * Pl * g2 * dK[(2 * d + X) * 2 + 1];
@@ -250,12 +254,15 @@ static int partner_index(int S, const int *species, int si)
 /* sec. 2.2). Arrays: state [Z][4] = (T, eta, Y_e, rho); J, H, j0, chi0, j1, chi1 [Z][S][N].   */
 /* weights: NULL -> vxo_energy_weights. phi_out: NULL or [Z][2 dir][2 l][N][N] for K^I.       */
 /* jac: NULL or [Z][S][N][4 outputs j0,chi0,j1,chi1][3 inputs T,eta,Y_e].                      */
+/* j1abs, chi1abs [Z][S][N], phiabs_out [Z][2][2][N][N] (optional): the same results with every   */
+/* term replaced by its absolute value (|P_l|, |H|), which bound the rounding of a sum whose      */
+/* terms cancel; for the l = 0 outputs the terms never change sign.                               */
 /* Returns the number of threads used (>= 1), or -1 on a bad argument.                         */
 int vxo_eval(int n, const double *eps, const double *weights, int n_mu, int n_e,
              int n_species, const int *species, double sin2w, double g2, double norm,
              long Z, const double *state, const double *J, const double *H,
              double *j0, double *chi0, double *j1, double *chi1, double *phi_out, double *jac,
-             int n_threads)
+             double *j1abs, double *chi1abs, double *phiabs_out, int n_threads)
 {
     if (n < 2 || n_mu < 1 || n_e < 1 || n_species < 1 || Z < 0 || !eps || !species) return -1;
     for (int k = 0; k < n_species; k++)
@@ -281,10 +288,17 @@ int vxo_eval(int n, const double *eps, const double *weights, int n_mu, int n_e,
 #endif
         double *phi = (double *)malloc(8 * NN * sizeof(double));
         double *dphi = jac ? (double *)malloc(16 * NN * sizeof(double)) : NULL;
+        int want_abs = j1abs || chi1abs || phiabs_out;
+        double *pabs = want_abs ? (double *)malloc(8 * NN * sizeof(double)) : NULL;
 #pragma omp for schedule(dynamic, 1)
         for (long z = 0; z < Z; z++) {
             double T = state[4 * z + 0], eta = state[4 * z + 1];
-            vxo_phi_zone(N, eps, n_mu, tmu, wmu, n_e, tE, wE, g2, T, eta, 0, phi, dphi);
+            vxo_phi_zone(N, eps, n_mu, tmu, wmu, n_e, tE, wE, g2, T, eta, 0, phi, dphi, pabs);
+            if (phiabs_out)
+                for (int d = 0; d < 2; d++)
+                    for (int l = 0; l < 2; l++)
+                        memcpy(phiabs_out + (((size_t)z * 2 + d) * 2 + l) * NN, &PHI(pabs, d, 0, l, 0),
+                               NN * sizeof(double));
             if (phi_out) /* K^I only: [dir][l][i][j] */
                 for (int d = 0; d < 2; d++)
                     for (int l = 0; l < 2; l++)
@@ -298,7 +312,7 @@ int vxo_eval(int n, const double *eps, const double *weights, int n_mu, int n_e,
                 const double *Jp = J + ((size_t)z * S + pk) * N;
                 const double *Hp = H + ((size_t)z * S + pk) * N;
                 for (int i = 0; i < N; i++) {
-                    double a_j0 = 0, a_c0 = 0, a_j1 = 0, a_c1 = 0;
+                    double a_j0 = 0, a_c0 = 0, a_j1 = 0, a_c1 = 0, m_j1 = 0, m_c1 = 0;
                     double g[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
                     for (int j = 0; j < N; j++) {
                         size_t ij = (size_t)i * N + j;
@@ -311,6 +325,10 @@ int vxo_eval(int n, const double *eps, const double *weights, int n_mu, int n_e,
                         a_c0 += w[j] * pa0 * Jp[j];
                         a_j1 += w[j] * pp1 * Hp[j];
                         a_c1 += w[j] * pa1 * Hp[j];
+                        if (pabs) {
+                            m_j1 += w[j] * (bI * PHI(pabs, 0, 0, 1, ij) + bII * PHI(pabs, 0, 1, 1, ij)) * fabs(Hp[j]);
+                            m_c1 += w[j] * (bI * PHI(pabs, 1, 0, 1, ij) + bII * PHI(pabs, 1, 1, 1, ij)) * fabs(Hp[j]);
+                        }
                         if (jac)
                             for (int v = 0; v < 2; v++) {
                                 double dpp0 = bI * DPHI(dphi, 0, 0, 0, ij, v) + bII * DPHI(dphi, 0, 1, 0, ij, v);
@@ -329,6 +347,8 @@ int vxo_eval(int n, const double *eps, const double *weights, int n_mu, int n_e,
                     chi0[o] = c0 * a_c0;
                     j1[o] = c1 * a_j1;
                     chi1[o] = c1 * a_c1;
+                    if (j1abs) j1abs[o] = c1 * m_j1;
+                    if (chi1abs) chi1abs[o] = c1 * m_c1;
                     if (jac) {
                         double c[4] = {c0, c0, c1, c1};
                         for (int out = 0; out < 4; out++) {
@@ -342,6 +362,7 @@ int vxo_eval(int n, const double *eps, const double *weights, int n_mu, int n_e,
         }
         free(phi);
         free(dphi);
+        free(pabs);
     }
     free(w); free(tmu); free(wmu); free(tE); free(wE);
     return used;

@@ -82,6 +82,9 @@ struct ZoneSh {
     float el_h, el_l;  // |eta| log2(e)
     float sB, sP;      // 2^kb and 2^(kb+11): grids of the exact split (degenerate path)
     float iB, iP;      // their inverses
+    float sc;          // degenerate path: blocking factor carried as O 2^sc (keeps the deepest-
+    float c1;          //   blocked nodes of the zone far from the FP32 underflow); c1 = 2^-sc
+    double unsc;       // 2^-sc, applied in FP64 to every result of the zone
     int deg, neg, bad;
 };
 
@@ -93,19 +96,22 @@ struct Mom {
 
 // One (pair, omega) node loop. Fills the moments of the blocking factor O and, with ADJ, of
 // GTa = O (f_e E + f_ebar Ebar), GTp = O ((1-f_e) E + (1-f_ebar) Ebar), GEt = O (f_ebar - f_e).
+// With the zone scale (degenerate path) e1 and the "1" of 1 + e1 carry the factor 2^-sc, so
+// r = 2^sc O; c1 = 2^-sc recovers 1 - f_e, while f_e, f_ebar and 1 - f_ebar need no correction.
 template <int NE, bool ADJ, bool DEG>
 __device__ __forceinline__ void node_loop(const Nodes32 &nd, int ne, float B, float Pe, float Pp,
                                           float Bq, float Bl, float Pq, float Pl, float h, float Em,
-                                          Mom &mo, Mom &ta, Mom &tp, Mom &et) {
+                                          float c1, Mom &mo, Mom &ta, Mom &tp, Mom &et) {
     const int n = NE > 0 ? NE : ne;
     auto accum = [&](int k, float e1, float e2, float t, float r) {
         mo.p = fmaf(nd.cp[k], r, mo.p);
         mo.m = fmaf(nd.cm[k], r, mo.m);
         mo.z = fmaf(nd.c0[k], r, mo.z);
         if (ADJ) {
-            float se = (1.f + e2) * r;   // 1 - f_e
-            float sp = t * r;            // 1 - f_ebar
-            float fe = e1 * se, fp = e2 * sp;
+            float qv = (1.f + e2) * r;
+            float se = DEG ? c1 * qv : qv;  // 1 - f_e
+            float sp = t * r;               // 1 - f_ebar
+            float fe = e1 * qv, fp = e2 * sp;
             float E = fmaf(h, nd.u[k], Em), Eb = fmaf(h, nd.v[k], Em);
             float ga = fmaf(fe, E, fp * Eb) * r;
             float gp = fmaf(se, E, sp * Eb) * r;
@@ -146,7 +152,7 @@ __device__ __forceinline__ void node_loop(const Nodes32 &nd, int ne, float B, fl
             float lo = fmaf(Bq, nd.ul[k], fmaf(Bl, nd.u[k], Pl));  // small remainder
             float e1 = ex2a(-s) * ex2a(-lo);
             float e2 = ex2a(-fmaf(B, nd.v[k], Pp));
-            float t = 1.f + e1;
+            float t = c1 + e1;
             accum(k, e1, e2, t, rcpa(fmaf(t, e2, t)));
         }
     }
@@ -249,12 +255,22 @@ __global__ void __launch_bounds__(VX_TPB_MAX, 1) k_pair_mixed(const __grid_const
                 zs.el_l = (float)(el - (double)zs.el_h);
                 zs.neg = eta < 0.0;
                 zs.deg = ae > C.eta_sw;
+                // zone scale: centre O in [e^-|eta|, 1] on the FP32 exponent range
+                int sc = zs.deg ? (int)floor(0.5 * el) : 0;
+                zs.sc = (float)sc;
+                zs.c1 = ldexpf(1.f, -sc);
+                zs.unsc = ldexp(1.0, -sc);
                 // grid of the exact split: B_hi on 2^-kb with < 2^11 steps, P_hi and the sum on
                 // 2^-(kb+11) with |sum| < 2^24 steps
                 double Bmax = C.h_max * il * 1.0001 + 1e-30;
-                double Pmax = C.q0h_max * il + el + 1.0;
+                double Pmax = C.q0h_max * il + el + sc + 1.0;
                 int kb = (int)floor(fmin(11.0 - log2(Bmax), 13.0 - log2(Pmax + 2.0 * Bmax))) - 1;
                 kb = kb < -60 ? -60 : (kb > 60 ? 60 : kb);
+                if (kb + 11 < 0) {  // grid coarser than 1: the integer shift would not be exact
+                    zs.sc = 0.f;
+                    zs.c1 = 1.f;
+                    zs.unsc = 1.0;
+                }
                 zs.sB = ldexpf(1.f, kb);
                 zs.iB = ldexpf(1.f, -kb);
                 zs.sP = ldexpf(1.f, kb + 11);
@@ -322,7 +338,7 @@ __global__ void __launch_bounds__(VX_TPB_MAX, 1) k_pair_mixed(const __grid_const
                 const float Pp = fmaf(Em, il_h, el_h);
                 if (!deg) {
                     const float Pe = fmaf(Em, il_h, -el_h);
-                    node_loop<NE, ADJ, false>(L.n32, C.n_e, B, Pe, Pp, 0.f, 0.f, 0.f, 0.f, h, Em, mo, ta, tp, et);
+                    node_loop<NE, ADJ, false>(L.n32, C.n_e, B, Pe, Pp, 0.f, 0.f, 0.f, 0.f, h, Em, 1.f, mo, ta, tp, et);
                     project<false>(PO, mo, kp, km, k0, kpl, kml, k0l, C.t_hi[m], C.t_lo[m]);
                     if (ADJ) {
                         project<false>(PTa, ta, kp, km, k0, kpl, kml, k0l, C.t_hi[m], C.t_lo[m]);
@@ -345,7 +361,8 @@ __global__ void __launch_bounds__(VX_TPB_MAX, 1) k_pair_mixed(const __grid_const
                     float slo = __fsub_rn(__fadd_rn(err, pl), el_l);
                     float Pq = __fmul_rn(rintf(__fmul_rn(s, zs.sP)), zs.iP);
                     float Pl = __fadd_rn(__fsub_rn(s, Pq), slo);
-                    node_loop<NE, ADJ, true>(L.n32, C.n_e, B, 0.f, Pp, Bq, Bl, Pq, Pl, h, Em, mo, ta, tp, et);
+                    Pq = __fadd_rn(Pq, zs.sc);  // exact: an integer on the same grid
+                    node_loop<NE, ADJ, true>(L.n32, C.n_e, B, 0.f, Pp, Bq, Bl, Pq, Pl, h, Em, zs.c1, mo, ta, tp, et);
                     project<true>(PO, mo, kp, km, k0, kpl, kml, k0l, C.t_hi[m], C.t_lo[m]);
                     if (ADJ) {
                         project<true>(PTa, ta, kp, km, k0, kpl, kml, k0l, C.t_hi[m], C.t_lo[m]);
@@ -370,7 +387,7 @@ __global__ void __launch_bounds__(VX_TPB_MAX, 1) k_pair_mixed(const __grid_const
 
         // ---- contraction (and tangents) --------------------------------------------------------
         const double two_pi = 6.283185307179586;
-        const double c0 = two_pi * C.norm * C.g2, c1 = 3.0 * c0;
+        const double c0 = two_pi * C.norm * C.g2 * zs.unsc, c1 = 3.0 * c0;
         const double iT2 = 1.0 / (T * T);
         const double sgn = zs.neg ? -1.0 : 1.0;  // d/deta of the eta >= 0 mapping
         const int nout = 4 * S * N;
@@ -456,7 +473,7 @@ __global__ void __launch_bounds__(VX_TPB_MAX, 1) k_pair_mixed(const __grid_const
             for (int e = tid; e < 4 * N2; e += blockDim.x) {
                 const int d = e / (2 * N2), l = (e / N2) & 1, ij = e % N2, i = ij / N, j = ij % N;
                 double a = l ? (double)mats[N2 + ij] + (double)mats[2 * N2 + ij] : (double)mats[ij];
-                double v = C.g2 * (d == 0 ? em[i] * em[j] * a : a);
+                double v = C.g2 * zs.unsc * (d == 0 ? em[i] * em[j] * a : a);
                 L.phi[(size_t)z * 4 * N2 + e] = v;
             }
         }

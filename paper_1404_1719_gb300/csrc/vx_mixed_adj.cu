@@ -6,7 +6,7 @@ namespace vx {
 
 template <int NE>
 static cudaError_t go(const Launch &L, int grid, int block, size_t smem, cudaStream_t s) {
-    k_pair_mixed<NE, false><<<grid, block, smem, s>>>(L);
+    k_pair_mixed<NE, true><<<grid, block, smem, s>>>(L);
     return cudaGetLastError();
 }
 

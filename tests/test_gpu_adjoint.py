@@ -6,7 +6,7 @@ import pytest
 
 import oracle
 import vx_inputs
-from _metrics import worst
+from _metrics import magnitudes, worst
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -46,12 +46,14 @@ def test_jacobian_against_oracle(workload, rays):
     r = rates_for(b)
     res = r.adjoint(dev(b["state"]), dev(b["J"]), dev(b["H"]), jacobian=True, forward=True)
     assert r.check()
-    ref = oracle.evaluate(b["eps"], b["n_mu"], b["n_e"], b["species"], b["state"], b["J"], b["H"], jac=True)
+    ref = oracle.evaluate(b["eps"], b["n_mu"], b["n_e"], b["species"], b["state"], b["J"], b["H"], jac=True,
+                          mag=True)
     check_jac(res["jac"].cpu().numpy(), ref["jac"])
     fw = r.evaluate(dev(b["state"]), dev(b["J"]), dev(b["H"]))
+    mg = magnitudes(ref)
     for k in KEYS:
-        assert worst(res[k].cpu().numpy(), ref[k]) <= 1e-5
-        np.testing.assert_allclose(res[k].cpu().numpy(), fw[k].cpu().numpy(), rtol=1e-12, atol=0)
+        assert worst(res[k].cpu().numpy(), ref[k], mag=mg[k]) <= 1e-5
+        assert worst(res[k].cpu().numpy(), fw[k].cpu().numpy()) <= 2e-6  # two FP32 instantiations
     r.close()
 
 
@@ -106,8 +108,9 @@ def test_full_size_forward_adjoint_sampled():
     rng = np.random.default_rng(4)
     pick = np.unique(np.concatenate([rng.integers(0, Z, 16), [0, 399, 400, Z - 1]]))
     ref = oracle.evaluate(b["eps"], b["n_mu"], b["n_e"], b["species"], b["state"][pick], b["J"][pick],
-                          b["H"][pick], jac=True)
+                          b["H"][pick], jac=True, mag=True)
     check_jac(res["jac"][torch.as_tensor(pick, device="cuda")].cpu().numpy(), ref["jac"])
+    mg = magnitudes(ref)
     for k in KEYS:
-        assert worst(res[k][torch.as_tensor(pick, device="cuda")].cpu().numpy(), ref[k]) <= 1e-5
+        assert worst(res[k][torch.as_tensor(pick, device="cuda")].cpu().numpy(), ref[k], mag=mg[k]) <= 1e-5
     r.close()

@@ -334,3 +334,21 @@ def test_rejects_missing_partner_and_accepts_empty_batch():
         oracle.evaluate(eps, 2, 2, [0], st, J, H)  # nu_e without its anti-nu_e partner
     out = oracle.evaluate(eps, 2, 2, [2], st[:0], J[:0], H[:0])
     assert out["j0"].shape == (0, 1, 4)
+
+
+# ------------------------------------------------------------------ magnitude companions (l = 1)
+def test_magnitude_companions_bound_and_limit():
+    """The |P_l| sums bound |Phi_l| entrywise, equal Phi_0 for l = 0, and in the Boltzmann limit
+    (K ~ (1 - cos w)^2) tend to Int |t| (1-t)^2 dt / Int (1-t)^2 dt = (3/2)/(8/3) = 9/16 of Phi_0."""
+    eps = vx_inputs.energy_centres(7, 1.0, 300.0)
+    ph = oracle.phi_zone(eps, 16, 12, 9.0, 30.0)
+    pa = oracle.phi_zone(eps, 16, 12, 9.0, 30.0, mag=True)
+    assert np.all(pa[:, :, 1] >= np.abs(ph[:, :, 1]) * (1 - 1e-15))
+    np.testing.assert_array_equal(pa[:, :, 0], ph[:, :, 0])
+    for n_mu, tol in ((32, 2e-3), (64, 5e-4)):
+        mb = oracle.phi_zone(eps, n_mu, 4, 5.0, 0.0, boltzmann=True)
+        mba = oracle.phi_zone(eps, n_mu, 4, 5.0, 0.0, boltzmann=True, mag=True)
+        np.testing.assert_allclose(mba[1, 0, 1] / mb[1, 0, 0], 9 / 16, rtol=tol)
+    st, J, H = vx_inputs.random_zones(3, 2, n_bins=7)
+    out = oracle.evaluate(eps, 8, 8, [0, 1, 2], st, J, H, mag=True)
+    assert np.all(out["j1_abs"] >= np.abs(out["j1"])) and np.all(out["chi1_abs"] >= np.abs(out["chi1"]))
