@@ -46,15 +46,15 @@ def _load():
         lib.vxo_gauss_legendre.argtypes = [ctypes.c_int, _dp, _dp]
         lib.vxo_energy_weights.argtypes = [ctypes.c_int, _dp, _dp]
         lib.vxo_kernel_point.argtypes = [ctypes.c_double] * 5 + [ctypes.c_int, ctypes.c_int, _dp, _dp,
-                                                                 _dp, _dp]
+                                                                 _dp, _dp, _dp]
         lib.vxo_kernel_point.restype = None
         lib.vxo_phi_zone.argtypes = [ctypes.c_int, _dp, ctypes.c_int, _dp, _dp, ctypes.c_int, _dp, _dp,
                                      ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
-                                     _dp, _dp, _dp]
+                                     _dp, _dp, _dp, _dp]
         lib.vxo_phi_zone.restype = None
         lib.vxo_eval.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _ip,
                                  ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_long,
-                                 _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, ctypes.c_int]
+                                 _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, ctypes.c_int]
         lib.vxo_eval.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -92,7 +92,7 @@ def kernel_point(eps, epsp, y, T, eta, n_e, boltzmann=False, grad=False):
     K = np.empty(4)
     dK = np.empty(8) if grad else None
     _load().vxo_kernel_point(float(eps), float(epsp), float(y), float(T), float(eta), int(boltzmann),
-                             n_e, _p(tE), _p(wE), _p(K), _p(dK))
+                             n_e, _p(tE), _p(wE), _p(K), _p(dK), None)
     return (K.reshape(2, 2), dK.reshape(2, 2, 2)) if grad else K.reshape(2, 2)
 
 
@@ -107,7 +107,7 @@ def phi_zone(eps, n_mu, n_e, T, eta, g2=1.0, boltzmann=False, grad=False, mag=Fa
     dphi = np.empty(16 * n * n) if grad else None
     pabs = np.empty(8 * n * n) if mag else None
     _load().vxo_phi_zone(n, _p(eps), n_mu, _p(tmu), _p(wmu), n_e, _p(tE), _p(wE), float(g2), float(T),
-                         float(eta), int(boltzmann), _p(phi), _p(dphi), _p(pabs))
+                         float(eta), int(boltzmann), _p(phi), _p(dphi), _p(pabs), None)
     if mag:
         return pabs.reshape(2, 2, 2, n, n)
     phi = phi.reshape(2, 2, 2, n, n)
@@ -118,8 +118,9 @@ def evaluate(eps, n_mu, n_e, species, state, J, H, weights=None, sin2w=0.23, g2=
              phi=False, jac=False, mag=False, threads=0) -> dict:
     """Rates j0, chi0, j1, chi1 [Z][S][N] for every zone; optionally the K^I dump
     phi [Z][dir][l][N][N], the Jacobian jac [Z][S][N][4 outputs][3 inputs T, eta, Y_e], and with
-    mag=True the magnitudes j1_abs, chi1_abs (and phi_abs with phi=True): the same sums with every
-    term replaced by its absolute value, which bound the rounding of the l = 1 results."""
+    mag=True the magnitudes j1_abs, chi1_abs (phi_abs with phi=True, jac_abs with jac=True): the
+    same sums with every term replaced by its absolute value, which bound the rounding of results
+    whose terms change sign (the l = 1 projections and the derivatives)."""
     eps = _f64(eps)
     state = _f64(state)
     J, H = _f64(J), _f64(H)
@@ -133,11 +134,12 @@ def evaluate(eps, n_mu, n_e, species, state, J, H, weights=None, sin2w=0.23, g2=
     for k in ("j1_abs", "chi1_abs"):
         out[k] = np.empty((Z, S, n)) if mag else None
     out["phi_abs"] = np.empty((Z, 2, 2, n, n)) if (mag and phi) else None
+    out["jac_abs"] = np.empty((Z, S, n, 4, 3)) if (mag and jac) else None
     w = None if weights is None else _f64(weights)
     used = _load().vxo_eval(n, _p(eps), _p(w), n_mu, n_e, S, species.ctypes.data_as(_ip), sin2w, g2, norm,
                             Z, _p(state), _p(J), _p(H), _p(out["j0"]), _p(out["chi0"]), _p(out["j1"]),
                             _p(out["chi1"]), _p(out["phi"]), _p(out["jac"]), _p(out["j1_abs"]),
-                            _p(out["chi1_abs"]), _p(out["phi_abs"]), int(threads))
+                            _p(out["chi1_abs"]), _p(out["phi_abs"]), _p(out["jac_abs"]), int(threads))
     if used < 0:
         raise ValueError("oracle rejected the arguments")
     out["threads"] = used

@@ -140,7 +140,8 @@ static void species_betas(int species, double sin2w, double *bI, double *bII)
 /* occ selects the statistics: 0 = Fermi-Dirac (the kernel); 1 = Boltzmann limit (O_p =        */
 /* exp(-q0/T), O_a = 1), used only to check the kinematics against the closed form.           */
 void vxo_kernel_point(double eps, double epsp, double y, double T, double eta, int occ,
-                      int n_e, const double *tE, const double *wE, double *K, double *dK)
+                      int n_e, const double *tE, const double *wE, double *K, double *dK,
+                      double *dKabs)
 {
     double q0 = eps + epsp;
     double s = 2.0 * eps * epsp * y;
@@ -153,6 +154,7 @@ void vxo_kernel_point(double eps, double epsp, double y, double T, double eta, i
     double Qk = 0.5 * s;                  /* Q.k = Q.k' */
     double sum[2][2] = {{0, 0}, {0, 0}};
     double dsum[2][2][2] = {{{0, 0}, {0, 0}}, {{0, 0}, {0, 0}}};
+    double dabs[2][2][2] = {{{0, 0}, {0, 0}}, {{0, 0}, {0, 0}}};
     for (int k = 0; k < n_e; k++) {
         double E = 0.5 * (Ep + Em) + 0.5 * (Ep - Em) * tE[k];
         double W = 0.5 * (Ep - Em) * wE[k];
@@ -187,6 +189,12 @@ void vxo_kernel_point(double eps, double epsp, double y, double T, double eta, i
             dsum[0][1][0] += W * dOpT * MII; dsum[0][1][1] += W * dOpe * MII;
             dsum[1][0][0] += W * dOaT * MI;  dsum[1][0][1] += W * dOae * MI;
             dsum[1][1][0] += W * dOaT * MII; dsum[1][1][1] += W * dOae * MII;
+            if (dKabs) { /* the same sums of absolute values: the rounding bound of each derivative */
+                dabs[0][0][0] += W * fabs(dOpT * MI);  dabs[0][0][1] += W * fabs(dOpe * MI);
+                dabs[0][1][0] += W * fabs(dOpT * MII); dabs[0][1][1] += W * fabs(dOpe * MII);
+                dabs[1][0][0] += W * fabs(dOaT * MI);  dabs[1][0][1] += W * fabs(dOae * MI);
+                dabs[1][1][0] += W * fabs(dOaT * MII); dabs[1][1][1] += W * fabs(dOae * MII);
+            }
         }
     }
     double pref = 2.0 * VXO_PI / (4.0 * q * eps * epsp);
@@ -196,6 +204,10 @@ void vxo_kernel_point(double eps, double epsp, double y, double T, double eta, i
             if (dK) {
                 dK[(2 * d + X) * 2 + 0] = pref * dsum[d][X][0];
                 dK[(2 * d + X) * 2 + 1] = pref * dsum[d][X][1];
+            }
+            if (dKabs) {
+                dKabs[(2 * d + X) * 2 + 0] = pref * dabs[d][X][0];
+                dKabs[(2 * d + X) * 2 + 1] = pref * dabs[d][X][1];
             }
         }
 }
@@ -207,18 +219,20 @@ void vxo_kernel_point(double eps, double epsp, double y, double T, double eta, i
 /* the l = 1 projection (whose terms change sign with cos(omega)); equal to phi for l = 0.       */
 void vxo_phi_zone(int n, const double *eps, int n_mu, const double *tmu, const double *wmu,
                   int n_e, const double *tE, const double *wE, double g2, double T, double eta,
-                  int occ, double *phi, double *dphi, double *phiabs)
+                  int occ, double *phi, double *dphi, double *phiabs, double *dphiabs)
 {
     size_t NN = (size_t)n * n;
     memset(phi, 0, 8 * NN * sizeof(double));
     if (phiabs) memset(phiabs, 0, 8 * NN * sizeof(double));
+    if (dphiabs) memset(dphiabs, 0, 16 * NN * sizeof(double));
     if (dphi) memset(dphi, 0, 16 * NN * sizeof(double));
     for (int i = 0; i < n; i++)
         for (int j = 0; j < n; j++)
             for (int m = 0; m < n_mu; m++) {
                 double y = 1.0 - tmu[m];
-                double K[4], dK[8];
-                vxo_kernel_point(eps[i], eps[j], y, T, eta, occ, n_e, tE, wE, K, dphi ? dK : NULL);
+                double K[4], dK[8], dKa[8];
+                vxo_kernel_point(eps[i], eps[j], y, T, eta, occ, n_e, tE, wE, K, dphi ? dK : NULL,
+                                 dphiabs ? dKa : NULL);
                 for (int d = 0; d < 2; d++)
                     for (int X = 0; X < 2; X++)
                         for (int l = 0; l < 2; l++) {
@@ -229,6 +243,10 @@ void vxo_phi_zone(int n, const double *eps, int n_mu, const double *tmu, const d
                             if (dphi) {
                                 dphi[2 * o + 0] += wmu[m] * Pl * g2 * dK[(2 * d + X) * 2 + 0];
                                 dphi[2 * o + 1] += wmu[m] * Pl * g2 * dK[(2 * d + X) * 2 + 1];
+                            }
+                            if (dphiabs) {
+                                dphiabs[2 * o + 0] += wmu[m] * fabs(Pl) * g2 * dKa[(2 * d + X) * 2 + 0];
+                                dphiabs[2 * o + 1] += wmu[m] * fabs(Pl) * g2 * dKa[(2 * d + X) * 2 + 1];
                             }
                         }
             }
@@ -256,13 +274,14 @@ static int partner_index(int S, const int *species, int si)
 /* jac: NULL or [Z][S][N][4 outputs j0,chi0,j1,chi1][3 inputs T,eta,Y_e].                      */
 /* j1abs, chi1abs [Z][S][N], phiabs_out [Z][2][2][N][N] (optional): the same results with every   */
 /* term replaced by its absolute value (|P_l|, |H|), which bound the rounding of a sum whose      */
-/* terms cancel; for the l = 0 outputs the terms never change sign.                               */
+/* terms cancel; for the l = 0 outputs the terms never change sign. jacabs, like jac: the same    */
+/* for the derivatives, whose node terms can change sign as well.                                 */
 /* Returns the number of threads used (>= 1), or -1 on a bad argument.                         */
 int vxo_eval(int n, const double *eps, const double *weights, int n_mu, int n_e,
              int n_species, const int *species, double sin2w, double g2, double norm,
              long Z, const double *state, const double *J, const double *H,
              double *j0, double *chi0, double *j1, double *chi1, double *phi_out, double *jac,
-             double *j1abs, double *chi1abs, double *phiabs_out, int n_threads)
+             double *j1abs, double *chi1abs, double *phiabs_out, double *jacabs, int n_threads)
 {
     if (n < 2 || n_mu < 1 || n_e < 1 || n_species < 1 || Z < 0 || !eps || !species) return -1;
     for (int k = 0; k < n_species; k++)
@@ -290,10 +309,11 @@ int vxo_eval(int n, const double *eps, const double *weights, int n_mu, int n_e,
         double *dphi = jac ? (double *)malloc(16 * NN * sizeof(double)) : NULL;
         int want_abs = j1abs || chi1abs || phiabs_out;
         double *pabs = want_abs ? (double *)malloc(8 * NN * sizeof(double)) : NULL;
+        double *dpabs = (jac && jacabs) ? (double *)malloc(16 * NN * sizeof(double)) : NULL;
 #pragma omp for schedule(dynamic, 1)
         for (long z = 0; z < Z; z++) {
             double T = state[4 * z + 0], eta = state[4 * z + 1];
-            vxo_phi_zone(N, eps, n_mu, tmu, wmu, n_e, tE, wE, g2, T, eta, 0, phi, dphi, pabs);
+            vxo_phi_zone(N, eps, n_mu, tmu, wmu, n_e, tE, wE, g2, T, eta, 0, phi, dphi, pabs, dpabs);
             if (phiabs_out)
                 for (int d = 0; d < 2; d++)
                     for (int l = 0; l < 2; l++)
@@ -314,6 +334,7 @@ int vxo_eval(int n, const double *eps, const double *weights, int n_mu, int n_e,
                 for (int i = 0; i < N; i++) {
                     double a_j0 = 0, a_c0 = 0, a_j1 = 0, a_c1 = 0, m_j1 = 0, m_c1 = 0;
                     double g[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+                    double ga[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
                     for (int j = 0; j < N; j++) {
                         size_t ij = (size_t)i * N + j;
                         /* species kernel = beta_I Phi_I + beta_II Phi_II, per direction and l */
@@ -339,6 +360,12 @@ int vxo_eval(int n, const double *eps, const double *weights, int n_mu, int n_e,
                                 g[1][v] += w[j] * dpa0 * Jp[j];
                                 g[2][v] += w[j] * dpp1 * Hp[j];
                                 g[3][v] += w[j] * dpa1 * Hp[j];
+                                if (dpabs) {
+                                    ga[0][v] += w[j] * (bI * DPHI(dpabs, 0, 0, 0, ij, v) + bII * DPHI(dpabs, 0, 1, 0, ij, v)) * fabs(1.0 - Jp[j]);
+                                    ga[1][v] += w[j] * (bI * DPHI(dpabs, 1, 0, 0, ij, v) + bII * DPHI(dpabs, 1, 1, 0, ij, v)) * fabs(Jp[j]);
+                                    ga[2][v] += w[j] * (bI * DPHI(dpabs, 0, 0, 1, ij, v) + bII * DPHI(dpabs, 0, 1, 1, ij, v)) * fabs(Hp[j]);
+                                    ga[3][v] += w[j] * (bI * DPHI(dpabs, 1, 0, 1, ij, v) + bII * DPHI(dpabs, 1, 1, 1, ij, v)) * fabs(Hp[j]);
+                                }
                             }
                     }
                     size_t o = ((size_t)z * S + si) * N + i;
@@ -355,6 +382,11 @@ int vxo_eval(int n, const double *eps, const double *weights, int n_mu, int n_e,
                             jac[o * 12 + out * 3 + 0] = c[out] * g[out][0];
                             jac[o * 12 + out * 3 + 1] = c[out] * g[out][1];
                             jac[o * 12 + out * 3 + 2] = 0.0; /* Y_e: no dependence */
+                            if (dpabs) {
+                                jacabs[o * 12 + out * 3 + 0] = c[out] * ga[out][0];
+                                jacabs[o * 12 + out * 3 + 1] = c[out] * ga[out][1];
+                                jacabs[o * 12 + out * 3 + 2] = 0.0;
+                            }
                         }
                     }
                 }
@@ -363,6 +395,7 @@ int vxo_eval(int n, const double *eps, const double *weights, int n_mu, int n_e,
         free(phi);
         free(dphi);
         free(pabs);
+        free(dpabs);
     }
     free(w); free(tmu); free(wmu); free(tE); free(wE);
     return used;

@@ -85,6 +85,8 @@ struct ZoneSh {
     float sc;          // degenerate path: blocking factor carried as O 2^sc (keeps the deepest-
     float c1;          //   blocked nodes of the zone far from the FP32 underflow); c1 = 2^-sc
     double unsc;       // 2^-sc, applied in FP64 to every result of the zone
+    int sv;            // production vectors carried as v 2^sv (degenerate zones); the two scales
+                       //   share the FP32 exponent headroom so no product can overflow
     int deg, neg, bad;
 };
 
@@ -202,12 +204,12 @@ __device__ __forceinline__ void store_proj(float *q3, int N2, int N, int pi, int
 // Shared-memory layout (floats unless noted), N2 = N*N:
 //   mats[q][3][N2]: for each quantity q, l0, l1 hi, l1 lo of Phi_I(i,j) (term II = transpose)
 //   vec[4][S][N]  : contraction vectors per output (j0, chi0, j1, chi1) and species
-//   sc[N] (double): exp(-(eps_i + eps_0)/T);  em[N] (double): exp(-eps_i/T)
+//   sc[N] (double): exp(-(eps_i + eps_0)/T);  em[N]: exp(-eps_i/T);  shv[N]: exp(-(eps_i-eps_0)/T) 2^sv
 __host__ __device__ inline size_t smem_mixed_bytes(int N, int S, bool adj) {
     size_t nq = adj ? 4 : 1;
     size_t f = nq * 3 * (size_t)N * N + 4 * (size_t)S * N;
     f = (f + 1) & ~(size_t)1;
-    return f * 4 + 2 * (size_t)N * 8 + 64 * 8;
+    return f * 4 + 3 * (size_t)N * 8 + 64 * 8;
 }
 
 template <int NE, bool ADJ>
@@ -223,7 +225,8 @@ __global__ void __launch_bounds__(VX_TPB_MAX, 1) k_pair_mixed(const __grid_const
     size_t foff = ((size_t)nq * 3 * N2 + 4 * (size_t)S * N + 1) & ~(size_t)1;
     double *sc = reinterpret_cast<double *>(smraw + foff * 4);
     double *em = sc + N;
-    double *red = em + N;  // 64 doubles for block reductions
+    double *shv = em + N;  // exp(-(eps_j - eps_0)/T) 2^sv
+    double *red = shv + N;  // 64 doubles for block reductions
     const int tid = threadIdx.x;
     const int nslot = npair * ms;
     const bool active = tid < nslot;
@@ -255,8 +258,10 @@ __global__ void __launch_bounds__(VX_TPB_MAX, 1) k_pair_mixed(const __grid_const
                 zs.el_l = (float)(el - (double)zs.el_h);
                 zs.neg = eta < 0.0;
                 zs.deg = ae > C.eta_sw;
-                // zone scale: centre O in [e^-|eta|, 1] on the FP32 exponent range
-                int sc = zs.deg ? (int)floor(0.5 * el) : 0;
+                // zone scales: with O in [e^-|eta|, 1] and production vectors whose relevant
+                // entries reach e^-|eta| times their row's largest, lift both off the FP32 floor
+                int sc = zs.deg ? (int)floor(0.3 * el) : 0;
+                zs.sv = zs.deg ? (int)floor(0.4 * el) : 0;
                 zs.sc = (float)sc;
                 zs.c1 = ldexpf(1.f, -sc);
                 zs.unsc = ldexp(1.0, -sc);
@@ -296,23 +301,21 @@ __global__ void __launch_bounds__(VX_TPB_MAX, 1) k_pair_mixed(const __grid_const
             continue;
         }
 
-        // ---- per-zone vectors and FP64 scales (overlap with the node loops) --------------------
-        for (int e = tid; e < 4 * S * N; e += blockDim.x) {
-            int o = e / (S * N), s = (e / N) % S, j = e % N;
-            int pk = C.partner[s];
-            size_t a = ((size_t)z * S + pk) * N + j;
-            float sh = ex2a(-(float)(C.eps[j] - C.eps[0]) * zs.il_h);  // exp(-(eps_j-eps_0)/T)
-            float wj = (float)C.w[j];
-            float v;
-            if (o == 0) v = wj * (float)(1.0 - L.J[a]) * sh;
-            else if (o == 1) v = wj * (float)L.J[a];
-            else if (o == 2) v = wj * (float)L.H[a] * sh;
-            else v = wj * (float)L.H[a];
-            vec[e] = v;
-        }
+        // ---- per-zone FP64 scales and contraction vectors -------------------------------------
         for (int i = tid; i < N; i += blockDim.x) {
             sc[i] = exp(-(C.eps[i] + C.eps[0]) / T);
             em[i] = exp(-C.eps[i] / T);
+            shv[i] = exp(-(C.eps[i] - C.eps[0]) / T + zs.sv * 0.6931471805599453);
+        }
+        __syncthreads();
+        for (int e = tid; e < 4 * S * N; e += blockDim.x) {
+            int o = e / (S * N), s = (e / N) % S, j = e % N;
+            size_t a = ((size_t)z * S + C.partner[s]) * N + j;
+            double v;
+            if (o == 0) v = C.w[j] * (1.0 - L.J[a]) * shv[j];  // production: w (1 - J) e^{-(eps_j - eps_0)/T} 2^sv
+            else if (o == 2) v = C.w[j] * L.H[a] * shv[j];
+            else v = C.w[j] * (o == 1 ? L.J[a] : L.H[a]);
+            vec[e] = (float)v;
         }
 
         // ---- quadrature ------------------------------------------------------------------------
@@ -400,7 +403,7 @@ __global__ void __launch_bounds__(VX_TPB_MAX, 1) k_pair_mixed(const __grid_const
             const float bI = C.bI[s], bII = C.bII[s];
             const float *v = vec + (size_t)(o * S + s) * N;
             const double cl = l ? c1 : c0;
-            const double scal = prod ? sc[i] : 1.0;
+            const double scal = prod ? sc[i] * ldexp(1.0, -zs.sv) : 1.0;
             double res[3];  // contraction of: the kernel, its T tangent, its eta tangent
             const int nres = ADJ ? 3 : 1;
 #pragma unroll

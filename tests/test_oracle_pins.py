@@ -350,5 +350,6 @@ def test_magnitude_companions_bound_and_limit():
         mba = oracle.phi_zone(eps, n_mu, 4, 5.0, 0.0, boltzmann=True, mag=True)
         np.testing.assert_allclose(mba[1, 0, 1] / mb[1, 0, 0], 9 / 16, rtol=tol)
     st, J, H = vx_inputs.random_zones(3, 2, n_bins=7)
-    out = oracle.evaluate(eps, 8, 8, [0, 1, 2], st, J, H, mag=True)
+    out = oracle.evaluate(eps, 8, 8, [0, 1, 2], st, J, H, mag=True, jac=True)
     assert np.all(out["j1_abs"] >= np.abs(out["j1"])) and np.all(out["chi1_abs"] >= np.abs(out["chi1"]))
+    assert np.all(out["jac_abs"] >= np.abs(out["jac"]) * (1 - 1e-14))
