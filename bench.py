@@ -158,7 +158,7 @@ def run_ours(args):
     Z, N, S = b["state"].shape[0], len(b["eps"]), len(b["species"])
     host = {k: torch.from_numpy(np.ascontiguousarray(b[k])).pin_memory() for k in ("state", "J", "H")}
     d = {k: v.to(dev) for k, v in host.items()}
-    rates = PairRates(b["eps"], b["n_mu"], b["n_e"], species=b["species"], graph=True)
+    rates = PairRates(b["eps"], b["n_mu"], b["n_e"], species=b["species"], graph=True, autotune=True)
     stream = torch.cuda.current_stream()
     out = {k: torch.empty((Z, S, N), dtype=torch.float64, device=dev) for k in ("j0", "chi0", "j1", "chi1")}
     jac = torch.empty((Z, S, N, 4, 3), dtype=torch.float64, device=dev)
@@ -253,7 +253,7 @@ def run_ours(args):
                        "zones": Z, "rays": int(len(b["ray_offsets"]) - 1), "bins": N,
                        "quadrature": f"{b['n_mu']}x{b['n_e']}", "species": S,
                        "l2": "inputs larger than L2 (J, H: %.2f GB)" % (2 * b["J"].nbytes / 1e9),
-                       "graph": True},
+                       "graph": True, "autotune": True},
             "e2e": {"value": entries(Z, N) * world / (ms_e2e / 1000), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": args.steps,

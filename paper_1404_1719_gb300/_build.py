@@ -10,8 +10,9 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libvx_rates.so")
-SOURCES = ["vx_rates.cu", "vx_mixed_fwd.cu", "vx_mixed_adj.cu", "vx_fp64.cu"]
-HEADERS = ["vx_internal.h", "vx_kernel_mixed.cuh"]
+SOURCES = ["vx_rates.cu", "vx_mixed_fwd_b2.cu", "vx_mixed_fwd_b3.cu", "vx_mixed_adj_b2.cu", "vx_mixed_adj_b3.cu",
+           "vx_fp64.cu"]
+HEADERS = ["vx_internal.h", "vx_kernel_mixed.cuh", "vx_mixed_inst.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 

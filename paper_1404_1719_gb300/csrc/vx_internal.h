@@ -13,7 +13,8 @@
 #define VX_MAX_BINS 32
 #define VX_MAX_PAIRS (VX_MAX_BINS * (VX_MAX_BINS + 1) / 2)
 #define VX_MAX_SPECIES 3
-#define VX_TPB_MAX 512
+#define VX_TPB_MAX 512    // FP64 kernel: threads per CTA (bin pairs)
+#define VX_TPB_MIXED 256  // mixed kernels: threads per CTA, two CTAs per SM; more pairs loop
 #define VX_ETA_MAX 80.0
 
 // device numeric flag bits
@@ -80,16 +81,33 @@ struct Launch64 {
     int *flag;
 };
 
-// Shared-memory bytes a launch needs (matrices + vectors + scales).
-size_t smem_mixed(const Common &c, bool adj);
+// Dynamic shared memory of the mixed kernel (floats unless noted), N2 = N*N:
+//   mats[q][3][N2]: per quantity q (kernel; and with tangents: T of annihilation, T of production,
+//                   eta), l = 0, l = 1 hi, l = 1 lo of Phi_I(i,j) (term II is the transpose)
+//   vec[4][S][N]  : contraction vectors per output (j0, chi0, j1, chi1) and species
+//   sc, em, shv [N] (double): per-bin FP64 factors;  red[64] (double): block reduction
+__host__ __device__ inline size_t smem_mixed_bytes(int N, int S, bool adj) {
+    size_t nq = adj ? 4 : 1;
+    size_t f = nq * 3 * (size_t)N * N + 4 * (size_t)S * N;
+    f = (f + 1) & ~(size_t)1;
+    return f * 4 + 3 * (size_t)N * 8 + 64 * 8;
+}
 size_t smem_fp64(const Common &c);
 
-// Kernel launchers (return the launch error). n_e selects the unrolled instantiation.
-cudaError_t launch_mixed_fwd(const Launch &L, int grid, int block, size_t smem, cudaStream_t s);
-cudaError_t launch_mixed_adj(const Launch &L, int grid, int block, size_t smem, cudaStream_t s);
+// Kernel launchers (return the launch error). n_e selects the unrolled instantiation; the mixed
+// kernels exist with register budgets for 2 and 3 CTAs per SM (minb).
+const void *kernel_mixed(bool adj, int minb, int n_e);
+cudaError_t launch_mixed(bool adj, int minb, const Launch &L, int grid, int block, size_t smem, cudaStream_t s);
 cudaError_t launch_fp64_fwd(const Launch64 &L, int grid, int block, size_t smem, cudaStream_t s);
-const void *kernel_mixed_fwd(int n_e);
-const void *kernel_mixed_adj(int n_e);
 const void *kernel_fp64_fwd(int n_e);
+
+#define VX_DECL_MIXED(sfx)                                                                            \
+    const void *kernel_mixed_##sfx(int n_e);                                                          \
+    cudaError_t launch_mixed_##sfx(const Launch &L, int grid, int block, size_t smem, cudaStream_t s);
+VX_DECL_MIXED(fwd_b2)
+VX_DECL_MIXED(fwd_b3)
+VX_DECL_MIXED(adj_b2)
+VX_DECL_MIXED(adj_b3)
+#undef VX_DECL_MIXED
 
 }  // namespace vx

@@ -3,9 +3,10 @@
 //
 // Work decomposition. One CTA owns one zone at a time and pulls the next zone from a global
 // atomic counter (zones of all rays are concatenated; every zone costs the same node count, so
-// ragged rays need no special handling). Thread slot = (unordered bin pair (i <= j), chunk of
-// cos(omega) nodes). A thread loops over its omega nodes and, inside, over the n_e electron-
-// energy nodes with compile-time indices, so the node constants are constant-bank operands.
+// ragged rays need no special handling); two CTAs share an SM, so one's per-zone set-up and
+// contraction overlap the other's quadrature. Thread = unordered bin pair (i <= j): it loops
+// over the omega nodes and, inside, over the n_e electron-energy nodes, whose constants are
+// broadcast from shared memory.
 //
 // Kernel algebra (exact rewrites of the definition; see the oracle for the definition itself).
 // With d = eps - eps', g = eps eps' (1 + cos w), |q|^2 = d^2 + 2 g, h = |q|/2, the electron energy
@@ -96,66 +97,87 @@ struct Mom {
     __device__ __forceinline__ void zero() { p = m = z = 0.f; }
 };
 
+// Electron-energy node constants, staged once per CTA in shared memory (uniform address within
+// a warp, so every read is a broadcast): a = {1+tau, 1-tau, w(1+tau)^2, w(1-tau)^2},
+// b = {w(1-tau^2), 1+tau on the 2^-11 grid, remainder, 0}.
+struct NodeSm {
+    float4 a, b;
+};
+
 // One (pair, omega) node loop. Fills the moments of the blocking factor O and, with ADJ, of
 // GTa = O (f_e E + f_ebar Ebar), GTp = O ((1-f_e) E + (1-f_ebar) Ebar), GEt = O (f_ebar - f_e).
 // With the zone scale (degenerate path) e1 and the "1" of 1 + e1 carry the factor 2^-sc, so
 // r = 2^sc O; c1 = 2^-sc recovers 1 - f_e, while f_e, f_ebar and 1 - f_ebar need no correction.
+// The loop is unrolled 16 nodes deep (the instruction footprint stays cache resident); the
+// forward fast path, which is MUFU-bound, turns two reciprocals into one.
 template <int NE, bool ADJ, bool DEG>
-__device__ __forceinline__ void node_loop(const Nodes32 &nd, int ne, float B, float Pe, float Pp,
-                                          float Bq, float Bl, float Pq, float Pl, float h, float Em,
-                                          float c1, Mom &mo, Mom &ta, Mom &tp, Mom &et) {
-    const int n = NE > 0 ? NE : ne;
-    auto accum = [&](int k, float e1, float e2, float t, float r) {
-        mo.p = fmaf(nd.cp[k], r, mo.p);
-        mo.m = fmaf(nd.cm[k], r, mo.m);
-        mo.z = fmaf(nd.c0[k], r, mo.z);
+__device__ __forceinline__ void node_loop(const NodeSm *__restrict__ nd, int ne, float B, float Pe,
+                                          float Pp, float Bq, float Bl, float Pq, float Pl, float h,
+                                          float Em, float c1, Mom &mo, Mom &ta, Mom &tp, Mom &et) {
+    constexpr bool PAIR = !ADJ && !DEG;
+    constexpr int U = 16;
+    auto accum = [&](const NodeSm &q, float e1, float e2, float t, float r) {
+        mo.p = fmaf(q.a.z, r, mo.p);
+        mo.m = fmaf(q.a.w, r, mo.m);
+        mo.z = fmaf(q.b.x, r, mo.z);
         if (ADJ) {
             float qv = (1.f + e2) * r;
             float se = DEG ? c1 * qv : qv;  // 1 - f_e
             float sp = t * r;               // 1 - f_ebar
             float fe = e1 * qv, fp = e2 * sp;
-            float E = fmaf(h, nd.u[k], Em), Eb = fmaf(h, nd.v[k], Em);
+            float E = fmaf(h, q.a.x, Em), Eb = fmaf(h, q.a.y, Em);
             float ga = fmaf(fe, E, fp * Eb) * r;
             float gp = fmaf(se, E, sp * Eb) * r;
             float ge = (fp - fe) * r;
-            ta.p = fmaf(nd.cp[k], ga, ta.p); ta.m = fmaf(nd.cm[k], ga, ta.m); ta.z = fmaf(nd.c0[k], ga, ta.z);
-            tp.p = fmaf(nd.cp[k], gp, tp.p); tp.m = fmaf(nd.cm[k], gp, tp.m); tp.z = fmaf(nd.c0[k], gp, tp.z);
-            et.p = fmaf(nd.cp[k], ge, et.p); et.m = fmaf(nd.cm[k], ge, et.m); et.z = fmaf(nd.c0[k], ge, et.z);
+            ta.p = fmaf(q.a.z, ga, ta.p); ta.m = fmaf(q.a.w, ga, ta.m); ta.z = fmaf(q.b.x, ga, ta.z);
+            tp.p = fmaf(q.a.z, gp, tp.p); tp.m = fmaf(q.a.w, gp, tp.m); tp.z = fmaf(q.b.x, gp, tp.z);
+            et.p = fmaf(q.a.z, ge, et.p); et.m = fmaf(q.a.w, ge, et.m); et.z = fmaf(q.b.x, ge, et.z);
         }
     };
-    if (!DEG) {
-        // |eta| <= eta_sw: d = (1+e1)(1+e2) <= 2 (1 + e^{eta_sw}), so a product of two stays finite.
-        int k = 0;
-#pragma unroll
-        for (; k + 1 < (NE > 0 ? NE : VX_MAX_NE); k += 2) {
-            if (NE == 0 && k + 1 >= n) break;
-            float xa = fmaf(B, nd.u[k], Pe), ya = fmaf(B, nd.v[k], Pp);
-            float xb = fmaf(B, nd.u[k + 1], Pe), yb = fmaf(B, nd.v[k + 1], Pp);
-            float e1a = ex2a(-xa), e2a = ex2a(-ya), e1b = ex2a(-xb), e2b = ex2a(-yb);
-            float ta_ = 1.f + e1a, tb_ = 1.f + e1b;
-            float da = fmaf(ta_, e2a, ta_), db = fmaf(tb_, e2b, tb_);
-            float R = rcpa(da * db);
-            accum(k, e1a, e2a, ta_, R * db);
-            accum(k + 1, e1b, e2b, tb_, R * da);
+    auto factors = [&](const NodeSm &q, float &e1, float &e2, float &t) {
+        if (!DEG) {
+            e1 = ex2a(-fmaf(B, q.a.x, Pe));
+            e2 = ex2a(-fmaf(B, q.a.y, Pp));
+            t = 1.f + e1;
+        } else {
+            float s = fmaf(Bq, q.b.y, Pq);                      // exact by the grid choice
+            float lo = fmaf(Bq, q.b.z, fmaf(Bl, q.a.x, Pl));    // small remainder
+            e1 = ex2a(-s) * ex2a(-lo);
+            e2 = ex2a(-fmaf(B, q.a.y, Pp));
+            t = c1 + e1;
         }
-        if (NE == 0 || (NE & 1)) {
-            for (; k < n; ++k) {
-                float x = fmaf(B, nd.u[k], Pe), y = fmaf(B, nd.v[k], Pp);
-                float e1 = ex2a(-x), e2 = ex2a(-y);
-                float t = 1.f + e1;
-                accum(k, e1, e2, t, rcpa(fmaf(t, e2, t)));
+    };
+    if (NE > 0) {
+        static_assert(NE % U == 0 || NE == 0, "unrolled instantiations need a multiple of the unroll depth");
+#pragma unroll 1
+        for (int k0 = 0; k0 < NE; k0 += U) {
+#pragma unroll
+            for (int kk = 0; kk < U; kk += PAIR ? 2 : 1) {
+                const NodeSm qa = nd[k0 + kk];
+                float e1a, e2a, ta_;
+                factors(qa, e1a, e2a, ta_);
+                float da = fmaf(ta_, e2a, ta_);
+                if (PAIR) {
+                    // |eta| <= eta_sw: d <= 2 (1 + e^{eta_sw}), so a product of two stays finite
+                    const NodeSm qb = nd[k0 + kk + 1];
+                    float e1b, e2b, tb_;
+                    factors(qb, e1b, e2b, tb_);
+                    float db = fmaf(tb_, e2b, tb_);
+                    float R = rcpa(da * db);
+                    accum(qa, e1a, e2a, ta_, R * db);
+                    accum(qb, e1b, e2b, tb_, R * da);
+                } else {
+                    accum(qa, e1a, e2a, ta_, rcpa(da));
+                }
             }
         }
     } else {
-#pragma unroll
-        for (int k = 0; k < (NE > 0 ? NE : VX_MAX_NE); ++k) {
-            if (NE == 0 && k >= n) break;
-            float s = fmaf(Bq, nd.uh[k], Pq);                      // exact by the grid choice
-            float lo = fmaf(Bq, nd.ul[k], fmaf(Bl, nd.u[k], Pl));  // small remainder
-            float e1 = ex2a(-s) * ex2a(-lo);
-            float e2 = ex2a(-fmaf(B, nd.v[k], Pp));
-            float t = c1 + e1;
-            accum(k, e1, e2, t, rcpa(fmaf(t, e2, t)));
+#pragma unroll 2
+        for (int k = 0; k < ne; ++k) {
+            const NodeSm q = nd[k];
+            float e1, e2, t;
+            factors(q, e1, e2, t);
+            accum(q, e1, e2, t, rcpa(fmaf(t, e2, t)));
         }
     }
 }
@@ -186,39 +208,25 @@ __device__ __forceinline__ void project(Proj &P, const Mom &M, float kp, float k
     }
 }
 
-// Writes (chunk 0) or adds (later chunks) one thread's projections into the zone matrices:
-// term I of pair (i,j) is Phi_I(i,j), term II is Phi_I(j,i).
-__device__ __forceinline__ void store_proj(float *q3, int N2, int N, int pi, int pj, int c, const Proj &P) {
+// Writes one pair's projections into the zone matrices: term I of pair (i,j) is Phi_I(i,j),
+// term II is Phi_I(j,i).
+__device__ __forceinline__ void store_proj(float *q3, int N2, int N, int pi, int pj, const Proj &P) {
     float *M0 = q3, *M1h = q3 + N2, *M1l = q3 + 2 * N2;
     const int a = pi * N + pj, b = pj * N + pi;
-    if (c == 0) {
-        M0[a] = P.o0I; M1h[a] = P.o1Ih; M1l[a] = P.o1Il;
-        if (pi != pj) { M0[b] = P.o0II; M1h[b] = P.o1IIh; M1l[b] = P.o1IIl; }
-    } else {
-        M0[a] += P.o0I;
-        df_add(M1h[a], M1l[a], P.o1Ih, P.o1Il);
-        if (pi != pj) { M0[b] += P.o0II; df_add(M1h[b], M1l[b], P.o1IIh, P.o1IIl); }
-    }
+    M0[a] = P.o0I; M1h[a] = P.o1Ih; M1l[a] = P.o1Il;
+    if (pi != pj) { M0[b] = P.o0II; M1h[b] = P.o1IIh; M1l[b] = P.o1IIl; }
 }
 
-// Shared-memory layout (floats unless noted), N2 = N*N:
-//   mats[q][3][N2]: for each quantity q, l0, l1 hi, l1 lo of Phi_I(i,j) (term II = transpose)
-//   vec[4][S][N]  : contraction vectors per output (j0, chi0, j1, chi1) and species
-//   sc[N] (double): exp(-(eps_i + eps_0)/T);  em[N]: exp(-eps_i/T);  shv[N]: exp(-(eps_i-eps_0)/T) 2^sv
-__host__ __device__ inline size_t smem_mixed_bytes(int N, int S, bool adj) {
-    size_t nq = adj ? 4 : 1;
-    size_t f = nq * 3 * (size_t)N * N + 4 * (size_t)S * N;
-    f = (f + 1) & ~(size_t)1;
-    return f * 4 + 3 * (size_t)N * 8 + 64 * 8;
-}
-
-template <int NE, bool ADJ>
-__global__ void __launch_bounds__(VX_TPB_MAX, 1) k_pair_mixed(const __grid_constant__ Launch L) {
+// MINB = CTAs per SM the register allocation must allow (2: up to 128 registers, 3: up to 80);
+// both are compiled and the autotuner picks per kernel kind and quadrature.
+template <int NE, bool ADJ, int MINB>
+__global__ void __launch_bounds__(VX_TPB_MIXED, MINB) k_pair_mixed(const __grid_constant__ Launch L) {
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ ZoneSh zs;
     __shared__ long long s_zone;
+    __shared__ NodeSm s_nodes[VX_MAX_NE];
     const Common &C = L.c;
-    const int N = C.N, S = C.S, N2 = N * N, npair = C.npair, ms = C.ms;
+    const int N = C.N, S = C.S, N2 = N * N, npair = C.npair;
     const int nq = ADJ ? 4 : 1;
     float *mats = reinterpret_cast<float *>(smraw);
     float *vec = mats + (size_t)nq * 3 * N2;
@@ -228,12 +236,10 @@ __global__ void __launch_bounds__(VX_TPB_MAX, 1) k_pair_mixed(const __grid_const
     double *shv = em + N;  // exp(-(eps_j - eps_0)/T) 2^sv
     double *red = shv + N;  // 64 doubles for block reductions
     const int tid = threadIdx.x;
-    const int nslot = npair * ms;
-    const bool active = tid < nslot;
-    const int chunk = active ? tid / npair : 0;
-    const int p = active ? tid % npair : 0;
-    const int pi = C.pij[p] >> 8, pj = C.pij[p] & 0xff;
-    const int m0 = chunk * C.n_mu / ms, m1 = (chunk + 1) * C.n_mu / ms;
+    for (int k = tid; k < C.n_e; k += blockDim.x) {
+        s_nodes[k].a = make_float4(L.n32.u[k], L.n32.v[k], L.n32.cp[k], L.n32.cm[k]);
+        s_nodes[k].b = make_float4(L.n32.c0[k], L.n32.uh[k], L.n32.ul[k], 0.f);
+    }
 
     for (;;) {
         if (tid == 0) s_zone = (long long)atomicAdd(L.counter, 1ull);
@@ -318,14 +324,16 @@ __global__ void __launch_bounds__(VX_TPB_MAX, 1) k_pair_mixed(const __grid_const
             vec[e] = (float)v;
         }
 
-        // ---- quadrature ------------------------------------------------------------------------
-        Proj PO, PTa, PTp, PEt;
-        PO.zero();
-        if (ADJ) { PTa.zero(); PTp.zero(); PEt.zero(); }
-        if (active) {
+        // ---- quadrature: one thread per unordered bin pair, all omega nodes -------------------
+        for (int p = tid; p < npair; p += blockDim.x) {
+            const int pi = C.pij[p] >> 8, pj = C.pij[p] & 0xff;
+            Proj PO, PTa, PTp, PEt;
+            PO.zero();
+            if (ADJ) { PTa.zero(); PTp.zero(); PEt.zero(); }
             const float il_h = zs.il_h, el_h = zs.el_h;
             const bool deg = zs.deg, neg = zs.neg;
-            for (int m = m0; m < m1; ++m) {
+#pragma unroll 1
+            for (int m = 0; m < C.n_mu; ++m) {
                 const float4 *rec = L.tab32 + ((size_t)m * npair + p) * 3;
                 float4 R0 = __ldg(rec), R1 = __ldg(rec + 1), R2 = __ldg(rec + 2);
                 const float h = R0.x, h_lo = R0.y, Em = R0.z, Em_lo = R0.w;
@@ -341,7 +349,7 @@ __global__ void __launch_bounds__(VX_TPB_MAX, 1) k_pair_mixed(const __grid_const
                 const float Pp = fmaf(Em, il_h, el_h);
                 if (!deg) {
                     const float Pe = fmaf(Em, il_h, -el_h);
-                    node_loop<NE, ADJ, false>(L.n32, C.n_e, B, Pe, Pp, 0.f, 0.f, 0.f, 0.f, h, Em, 1.f, mo, ta, tp, et);
+                    node_loop<NE, ADJ, false>(s_nodes, C.n_e, B, Pe, Pp, 0.f, 0.f, 0.f, 0.f, h, Em, 1.f, mo, ta, tp, et);
                     project<false>(PO, mo, kp, km, k0, kpl, kml, k0l, C.t_hi[m], C.t_lo[m]);
                     if (ADJ) {
                         project<false>(PTa, ta, kp, km, k0, kpl, kml, k0l, C.t_hi[m], C.t_lo[m]);
@@ -365,7 +373,7 @@ __global__ void __launch_bounds__(VX_TPB_MAX, 1) k_pair_mixed(const __grid_const
                     float Pq = __fmul_rn(rintf(__fmul_rn(s, zs.sP)), zs.iP);
                     float Pl = __fadd_rn(__fsub_rn(s, Pq), slo);
                     Pq = __fadd_rn(Pq, zs.sc);  // exact: an integer on the same grid
-                    node_loop<NE, ADJ, true>(L.n32, C.n_e, B, 0.f, Pp, Bq, Bl, Pq, Pl, h, Em, zs.c1, mo, ta, tp, et);
+                    node_loop<NE, ADJ, true>(s_nodes, C.n_e, B, 0.f, Pp, Bq, Bl, Pq, Pl, h, Em, zs.c1, mo, ta, tp, et);
                     project<true>(PO, mo, kp, km, k0, kpl, kml, k0l, C.t_hi[m], C.t_lo[m]);
                     if (ADJ) {
                         project<true>(PTa, ta, kp, km, k0, kpl, kml, k0l, C.t_hi[m], C.t_lo[m]);
@@ -374,19 +382,14 @@ __global__ void __launch_bounds__(VX_TPB_MAX, 1) k_pair_mixed(const __grid_const
                     }
                 }
             }
-        }
-        // ---- combine the omega chunks into Phi_I(i,j) matrices, in chunk order (deterministic)
-        for (int c = 0; c < ms; ++c) {
-            if (active && chunk == c) {
-                store_proj(mats + 0 * 3 * (size_t)N2, N2, N, pi, pj, c, PO);
-                if (ADJ) {
-                    store_proj(mats + 1 * 3 * (size_t)N2, N2, N, pi, pj, c, PTa);
-                    store_proj(mats + 2 * 3 * (size_t)N2, N2, N, pi, pj, c, PTp);
-                    store_proj(mats + 3 * 3 * (size_t)N2, N2, N, pi, pj, c, PEt);
-                }
+            store_proj(mats + 0 * 3 * (size_t)N2, N2, N, pi, pj, PO);
+            if (ADJ) {
+                store_proj(mats + 1 * 3 * (size_t)N2, N2, N, pi, pj, PTa);
+                store_proj(mats + 2 * 3 * (size_t)N2, N2, N, pi, pj, PTp);
+                store_proj(mats + 3 * 3 * (size_t)N2, N2, N, pi, pj, PEt);
             }
-            __syncthreads();
         }
+        __syncthreads();
 
         // ---- contraction (and tangents) --------------------------------------------------------
         const double two_pi = 6.283185307179586;

@@ -1,0 +1,5 @@
+// vx_mixed_fwd_b2.cu -- mixed-precision forward kernel, register budget for 2 CTAs per SM.
+#define VX_ADJ false
+#define VX_MINB 2
+#define VX_SUFFIX fwd_b2
+#include "vx_mixed_inst.cuh"

@@ -1,0 +1,5 @@
+// vx_mixed_fwd_b3.cu -- mixed-precision forward kernel, register budget for 3 CTAs per SM.
+#define VX_ADJ false
+#define VX_MINB 3
+#define VX_SUFFIX fwd_b3
+#include "vx_mixed_inst.cuh"

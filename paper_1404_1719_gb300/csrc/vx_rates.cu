@@ -98,13 +98,29 @@ struct vx_rates {
     double *d_tab64 = nullptr;
     unsigned long long *d_counter = nullptr;
     int *d_flag = nullptr;
-    // launch shapes (ms = omega chunks per pair)
-    int ms = 1, block = 32;
-    int grid_fwd = 0, grid_adj = 0, grid_64 = 0;
+    // launch shapes: one thread per bin pair; mixed kernels in two register budgets
+    int ms = 1, block = 32, block_mixed = 32;
+    int grid_mixed[2][2] = {{0, 0}, {0, 0}};  // [forward, tangents][2 or 3 CTAs per SM]
+    int minb[2] = {2, 3};                      // chosen budget per kind (autotuned with VX_AUTOTUNE)
+    bool tuned[2] = {false, false};
+    float tune_ms[2][2] = {{0, 0}, {0, 0}};
+    int grid_64 = 0;
     size_t smem_fwd = 0, smem_adj = 0, smem_64 = 0;
-    // graph of the last eval launch
-    cudaGraphExec_t gexec = nullptr;
+    int cc_major = 0, cc_minor = 0;
+    // one cached executable graph per kernel kind: mixed forward, mixed tangents, FP64
+    cudaGraphExec_t gexec[3] = {nullptr, nullptr, nullptr};
 };
+
+namespace vx {
+const void *kernel_mixed(bool adj, int minb, int n_e) {
+    if (adj) return minb == 3 ? kernel_mixed_adj_b3(n_e) : kernel_mixed_adj_b2(n_e);
+    return minb == 3 ? kernel_mixed_fwd_b3(n_e) : kernel_mixed_fwd_b2(n_e);
+}
+cudaError_t launch_mixed(bool adj, int minb, const Launch &L, int grid, int block, size_t smem, cudaStream_t s) {
+    if (adj) return minb == 3 ? launch_mixed_adj_b3(L, grid, block, smem, s) : launch_mixed_adj_b2(L, grid, block, smem, s);
+    return minb == 3 ? launch_mixed_fwd_b3(L, grid, block, smem, s) : launch_mixed_fwd_b2(L, grid, block, smem, s);
+}
+}  // namespace vx
 
 extern "C" {
 
@@ -259,18 +275,11 @@ vx_status vx_rates_create(const vx_config *cfg, vx_rates **out) {
     C.h_max = hmax;
     C.q0h_max = q0hmax;
 
-    // launch shape: omega chunks per pair so that pairs x chunks fills <= VX_TPB_MAX threads
-    int ms = 1;
-    for (int cand : {4, 2}) {
-        if (np * cand <= VX_TPB_MAX && nmu / cand >= 4) { ms = cand; break; }
-    }
-    if (np * ms > VX_TPB_MAX) {
-        delete h;
-        return fail(VX_ERR_UNSUPPORTED, "%d bin pairs exceed one CTA of %d threads", np, VX_TPB_MAX);
-    }
-    C.ms = ms;
-    h->ms = ms;
-    h->block = round_up(np * ms, 32);
+    // launch shape: one thread per unordered bin pair
+    C.ms = 1;
+    h->ms = 1;
+    h->block = round_up(np, 32);                           // FP64 kernel (<= 496 pairs)
+    h->block_mixed = std::min(round_up(np, 32), VX_TPB_MIXED);
 
     auto cleanup = [&](vx_status s) { vx_rates_destroy(h); return s; };
     cudaError_t ce = cudaGetDevice(&h->device);
@@ -297,19 +306,23 @@ vx_status vx_rates_create(const vx_config *cfg, vx_rates **out) {
     VX_CUC(cudaMemcpy(h->d_tab64, t64.data(), t64.size() * sizeof(double), cudaMemcpyHostToDevice));
     VX_CUC(cudaMemset(h->d_flag, 0, sizeof(int)));
 
-    h->smem_fwd = vx::smem_mixed(C, false);
-    h->smem_adj = vx::smem_mixed(C, true);
+    h->smem_fwd = vx::smem_mixed_bytes(N, S, false);
+    h->smem_adj = vx::smem_mixed_bytes(N, S, true);
     h->smem_64 = vx::smem_fp64(C);
-    struct K { const void *fn; size_t smem; int *grid; };
-    K ks[3] = {{vx::kernel_mixed_fwd(ne), h->smem_fwd, &h->grid_fwd},
-               {vx::kernel_mixed_adj(ne), h->smem_adj, &h->grid_adj},
-               {vx::kernel_fp64_fwd(ne), h->smem_64, &h->grid_64}};
+    h->cc_major = prop.major;
+    h->cc_minor = prop.minor;
+    struct K { const void *fn; size_t smem; int *grid; int block; };
+    K ks[5] = {{vx::kernel_mixed(false, 2, ne), h->smem_fwd, &h->grid_mixed[0][0], h->block_mixed},
+               {vx::kernel_mixed(false, 3, ne), h->smem_fwd, &h->grid_mixed[0][1], h->block_mixed},
+               {vx::kernel_mixed(true, 2, ne), h->smem_adj, &h->grid_mixed[1][0], h->block_mixed},
+               {vx::kernel_mixed(true, 3, ne), h->smem_adj, &h->grid_mixed[1][1], h->block_mixed},
+               {vx::kernel_fp64_fwd(ne), h->smem_64, &h->grid_64, h->block}};
     for (K &k : ks) {
         if (k.smem > 48 * 1024)
             VX_CUC(cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem));
         int occ = 0;
-        VX_CUC(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k.fn, h->block, k.smem));
-        if (occ < 1) return cleanup(fail(VX_ERR_UNSUPPORTED, "kernel does not fit on an SM (block %d, smem %zu)", h->block, k.smem));
+        VX_CUC(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k.fn, k.block, k.smem));
+        if (occ < 1) return cleanup(fail(VX_ERR_UNSUPPORTED, "kernel does not fit on an SM (block %d, smem %zu)", k.block, k.smem));
         *k.grid = occ * h->nsm;
     }
 #undef VX_CUC
@@ -380,7 +393,9 @@ struct DeviceGuard {
 
 // Launch through a graph (memset node + kernel node), re-using the executable graph when the
 // topology is unchanged and only the parameters differ.
-static vx_status launch_graph(vx_rates *h, const void *fn, void *param, int grid, size_t smem, cudaStream_t s) {
+static vx_status launch_graph(vx_rates *h, int slot, const void *fn, void *param, int grid, int block,
+                              size_t smem, cudaStream_t s) {
+    cudaGraphExec_t &gexec = h->gexec[slot];
     cudaGraph_t g = nullptr;
     cudaGraphNode_t nm = nullptr, nk = nullptr;
     VX_CU(cudaGraphCreate(&g, 0));
@@ -395,24 +410,24 @@ static vx_status launch_graph(vx_rates *h, const void *fn, void *param, int grid
     cudaKernelNodeParams kp{};
     kp.func = (void *)fn;
     kp.gridDim = dim3(grid);
-    kp.blockDim = dim3(h->block);
+    kp.blockDim = dim3(block);
     kp.sharedMemBytes = (unsigned)smem;
     void *args[1] = {param};
     kp.kernelParams = args;
     if (e == cudaSuccess) e = cudaGraphAddKernelNode(&nk, g, &nm, 1, &kp);
     if (e == cudaSuccess) {
         bool fresh = true;
-        if (h->gexec) {
+        if (gexec) {
             cudaGraphExecUpdateResultInfo info;
-            if (cudaGraphExecUpdate(h->gexec, g, &info) == cudaSuccess) fresh = false;
+            if (cudaGraphExecUpdate(gexec, g, &info) == cudaSuccess) fresh = false;
             else {
                 cudaGetLastError();
-                cudaGraphExecDestroy(h->gexec);
-                h->gexec = nullptr;
+                cudaGraphExecDestroy(gexec);
+                gexec = nullptr;
             }
         }
-        if (fresh) e = cudaGraphInstantiate(&h->gexec, g, 0);
-        if (e == cudaSuccess) e = cudaGraphLaunch(h->gexec, s);
+        if (fresh) e = cudaGraphInstantiate(&gexec, g, 0);
+        if (e == cudaSuccess) e = cudaGraphLaunch(gexec, s);
     }
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail(VX_ERR_CUDA, "graph launch: %s", cudaGetErrorString(e));
@@ -433,6 +448,108 @@ static void fill_launch(const vx_rates *h, const vx_batch *b, vx::Launch &L) {
     L.flag = h->d_flag;
 }
 
+// ---- autotuner ------------------------------------------------------------------------------
+// Picks, per kernel kind, the register budget (2 or 3 CTAs per SM) that runs a sample of the
+// first batch fastest: the first zones of the batch, a few per CTA, each variant once to warm up
+// and once timed with CUDA events. The choice is kept in the handle and, when the environment
+// variable VX_AUTOTUNE_CACHE names a file, in that JSON file under a key of the quadrature, the
+// kernel kind and the device (SM count, compute capability). Tuning synchronises the stream, so
+// the first tuned call must not be inside a stream capture; its sample outputs are overwritten
+// by the real launch that follows.
+static std::string tune_key(const vx_rates *h, bool adj) {
+    char k[160];
+    snprintf(k, sizeof k, "N=%d,n_mu=%d,n_e=%d,S=%d,kind=%s,sm=%d,cc=%d.%d", h->common.N, h->common.n_mu,
+             h->common.n_e, h->common.S, adj ? "tangents" : "forward", h->nsm, h->cc_major, h->cc_minor);
+    return k;
+}
+
+static std::vector<std::pair<std::string, std::string>> cache_read(const char *path) {
+    std::vector<std::pair<std::string, std::string>> m;
+    FILE *f = fopen(path, "r");
+    if (!f) return m;
+    char line[512];
+    while (fgets(line, sizeof line, f)) {
+        char *q0 = strchr(line, '"');
+        if (!q0) continue;
+        char *q1 = strchr(q0 + 1, '"');
+        char *br = q1 ? strchr(q1, '{') : nullptr;
+        char *be = br ? strchr(br, '}') : nullptr;
+        if (!q1 || !br || !be) continue;
+        m.emplace_back(std::string(q0 + 1, q1), std::string(br, be + 1));
+    }
+    fclose(f);
+    return m;
+}
+
+static void cache_write(const char *path, const std::string &key, const std::string &val) {
+    auto m = cache_read(path);
+    bool found = false;
+    for (auto &kv : m)
+        if (kv.first == key) { kv.second = val; found = true; }
+    if (!found) m.emplace_back(key, val);
+    std::string tmp = std::string(path) + ".tmp";
+    FILE *f = fopen(tmp.c_str(), "w");
+    if (!f) return;  // the cache is an optimisation: an unwritable path is not an error
+    fprintf(f, "{\n");
+    for (size_t i = 0; i < m.size(); ++i)
+        fprintf(f, "  \"%s\": %s%s\n", m[i].first.c_str(), m[i].second.c_str(), i + 1 < m.size() ? "," : "");
+    fprintf(f, "}\n");
+    fclose(f);
+    rename(tmp.c_str(), path);
+}
+
+static vx_status autotune(vx_rates *h, bool adj, const vx::Launch &L, cudaStream_t s) {
+    const int kind = adj ? 1 : 0;
+    if (!(h->cfg.flags & VX_AUTOTUNE) || h->tuned[kind]) return VX_OK;
+    const char *path = getenv("VX_AUTOTUNE_CACHE");
+    const std::string key = tune_key(h, adj);
+    if (path && *path) {
+        for (auto &kv : cache_read(path)) {
+            int mb = 0;
+            if (kv.first == key && sscanf(kv.second.c_str(), "{\"minb\": %d", &mb) == 1 && (mb == 2 || mb == 3)) {
+                h->minb[kind] = mb;
+                h->tuned[kind] = true;
+                return VX_OK;
+            }
+        }
+    }
+    const long long sample = std::min<long long>(L.Z, 8LL * h->grid_mixed[kind][1]);
+    if (sample < 2LL * h->grid_mixed[kind][1]) return VX_OK;  // too small to tell apart: keep the default
+    vx::Launch Ls = L;
+    Ls.Z = sample;
+    const size_t smem = adj ? h->smem_adj : h->smem_fwd;
+    cudaEvent_t e0, e1;
+    VX_CU(cudaEventCreate(&e0));
+    VX_CU(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int bestb = h->minb[kind];
+    for (int mb = 2; mb <= 3; ++mb) {
+        const int grid = (int)std::min<long long>(h->grid_mixed[kind][mb - 2], sample);
+        float ms = 0.f;
+        for (int rep = 0; rep < 2; ++rep) {
+            VX_CU(cudaMemsetAsync(h->d_counter, 0, sizeof(unsigned long long), s));
+            if (rep) VX_CU(cudaEventRecord(e0, s));
+            VX_CU(vx::launch_mixed(adj, mb, Ls, grid, h->block_mixed, smem, s));
+            if (rep) VX_CU(cudaEventRecord(e1, s));
+        }
+        VX_CU(cudaEventSynchronize(e1));
+        VX_CU(cudaEventElapsedTime(&ms, e0, e1));
+        h->tune_ms[kind][mb - 2] = ms;
+        if (ms < best) { best = ms; bestb = mb; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->minb[kind] = bestb;
+    h->tuned[kind] = true;
+    if (path && *path) {
+        char v[128];
+        snprintf(v, sizeof v, "{\"minb\": %d, \"ms_b2\": %.4f, \"ms_b3\": %.4f, \"zones\": %lld}", bestb,
+                 h->tune_ms[kind][0], h->tune_ms[kind][1], sample);
+        cache_write(path, key, v);
+    }
+    return VX_OK;
+}
+
 vx_status vx_rates_eval(vx_rates *h, const vx_batch *b, const vx_out *out, vx_stream stream) {
     vx_status st = validate_batch(h, b);
     if (st != VX_OK) return st;
@@ -445,10 +562,12 @@ vx_status vx_rates_eval(vx_rates *h, const vx_batch *b, const vx_out *out, vx_st
         vx::Launch L;
         fill_launch(h, b, L);
         L.j0 = out->j0; L.chi0 = out->chi0; L.j1 = out->j1; L.chi1 = out->chi1; L.phi = out->phi;
-        int grid = (int)std::min<long long>(h->grid_fwd, b->n_zones);
-        if (graph) return launch_graph(h, vx::kernel_mixed_fwd(h->common.n_e), &L, grid, h->smem_fwd, s);
+        if ((st = autotune(h, false, L, s)) != VX_OK) return st;
+        const int mb = h->minb[0];
+        int grid = (int)std::min<long long>(h->grid_mixed[0][mb - 2], b->n_zones);
+        if (graph) return launch_graph(h, 0, vx::kernel_mixed(false, mb, h->common.n_e), &L, grid, h->block_mixed, h->smem_fwd, s);
         VX_CU(cudaMemsetAsync(h->d_counter, 0, sizeof(unsigned long long), s));
-        VX_CU(vx::launch_mixed_fwd(L, grid, h->block, h->smem_fwd, s));
+        VX_CU(vx::launch_mixed(false, mb, L, grid, h->block_mixed, h->smem_fwd, s));
     } else {
         vx::Launch64 L;
         L.c = h->common;
@@ -460,7 +579,7 @@ vx_status vx_rates_eval(vx_rates *h, const vx_batch *b, const vx_out *out, vx_st
         L.counter = h->d_counter;
         L.flag = h->d_flag;
         int grid = (int)std::min<long long>(h->grid_64, b->n_zones);
-        if (graph) return launch_graph(h, vx::kernel_fp64_fwd(h->common.n_e), &L, grid, h->smem_64, s);
+        if (graph) return launch_graph(h, 2, vx::kernel_fp64_fwd(h->common.n_e), &L, grid, h->block, h->smem_64, s);
         VX_CU(cudaMemsetAsync(h->d_counter, 0, sizeof(unsigned long long), s));
         VX_CU(vx::launch_fp64_fwd(L, grid, h->block, h->smem_64, s));
     }
@@ -492,10 +611,13 @@ vx_status vx_rates_adjoint(vx_rates *h, const vx_batch *b, const vx_out *grad_ou
     L.jac = jac;
     L.grad_state = grad_state;
     if (grad_state) { L.g_j0 = grad_out->j0; L.g_chi0 = grad_out->chi0; L.g_j1 = grad_out->j1; L.g_chi1 = grad_out->chi1; }
-    int grid = (int)std::min<long long>(h->grid_adj, b->n_zones);
-    if (h->cfg.flags & VX_USE_GRAPH) return launch_graph(h, vx::kernel_mixed_adj(h->common.n_e), &L, grid, h->smem_adj, s);
+    if ((st = autotune(h, true, L, s)) != VX_OK) return st;
+    const int mb = h->minb[1];
+    int grid = (int)std::min<long long>(h->grid_mixed[1][mb - 2], b->n_zones);
+    if (h->cfg.flags & VX_USE_GRAPH)
+        return launch_graph(h, 1, vx::kernel_mixed(true, mb, h->common.n_e), &L, grid, h->block_mixed, h->smem_adj, s);
     VX_CU(cudaMemsetAsync(h->d_counter, 0, sizeof(unsigned long long), s));
-    VX_CU(vx::launch_mixed_adj(L, grid, h->block, h->smem_adj, s));
+    VX_CU(vx::launch_mixed(true, mb, L, grid, h->block_mixed, h->smem_adj, s));
     return VX_OK;
 }
 
@@ -518,7 +640,8 @@ void vx_rates_destroy(vx_rates *h) {
     if (!h) return;
     DeviceGuard dg(h->device);
     cudaDeviceSynchronize();
-    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    for (cudaGraphExec_t &g : h->gexec)
+        if (g) cudaGraphExecDestroy(g);
     cudaFree(h->d_tab32);
     cudaFree(h->d_tab64);
     cudaFree(h->d_counter);

@@ -187,3 +187,30 @@ def test_ragged_rays_full_size_sampled():
     for k in KEYS:
         assert err(got, ref, k) <= 1e-5, k
     rates.close()
+
+
+def test_autotune_picks_a_variant_and_caches_it(tmp_path, monkeypatch):
+    """VX_AUTOTUNE times both register budgets on the first batch, writes the choice to the JSON
+    file named by VX_AUTOTUNE_CACHE, and a second handle reads it back; results stay within the
+    mixed tolerance of an untuned handle."""
+    import json
+    cache = tmp_path / "tune.json"
+    monkeypatch.setenv("VX_AUTOTUNE_CACHE", str(cache))
+    b = vx_inputs.make_batch(3, rays=range(24))
+    st, J, H = dev(b["state"]), dev(b["J"]), dev(b["H"])
+    r1 = make(b, "mixed", autotune=True)
+    o1 = r1.adjoint(st, J, H, jacobian=True, forward=True)
+    assert r1.check()
+    data = json.loads(cache.read_text())
+    (key, val), = data.items()
+    assert "kind=tangents" in key and val["minb"] in (2, 3) and val["ms_b2"] > 0 and val["ms_b3"] > 0
+    r2 = make(b, "mixed", autotune=True)
+    o2 = r2.adjoint(st, J, H, jacobian=True, forward=True)
+    r0 = make(b, "mixed")
+    o0 = r0.adjoint(st, J, H, jacobian=True, forward=True)
+    torch.cuda.synchronize()
+    for k in KEYS:
+        assert torch.equal(o1[k], o2[k])
+        assert worst(o1[k].cpu().numpy(), o0[k].cpu().numpy()) <= 2e-6
+    for r in (r0, r1, r2):
+        r.close()
