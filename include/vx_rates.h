@@ -139,6 +139,28 @@ long long vx_rates_entries_per_zone(const vx_rates *h);
 /* Releases the handle's tables, graphs and scratch; NULL is a no-op. Synchronises the device. */
 void vx_rates_destroy(vx_rates *h);
 
+/* Allocation-free forward evaluation (mixed form). The paper has no counterpart: this entry point
+ * exists for callers that must not have the library allocate device memory -- for example a
+ * transport code that hands all device memory to its own pool allocator before time stepping,
+ * or one whose implicit time step cannot afford the device-wide synchronisation that cudaMalloc
+ * and cudaFree imply. It takes the config directly (no handle) and computes the same rates as
+ * vx_rates_eval on a mixed-precision handle; the caller passes inputs and outputs as there.
+ *   - Scratch: one file-scope device array of 461,056 bytes (work counter, numeric flag and the
+ *     bin-pair table), present on every device that loads the library until the process exits.
+ *     The call performs no cudaMalloc, cudaFree or other allocation.
+ *   - Limits: at most 24 energy bins and 32 cos(omega) nodes; larger configs are rejected with
+ *     VX_ERR_UNSUPPORTED and a message naming the limit. prec must be VX_PREC_MIXED; flags are
+ *     ignored.
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ *     that device current; make that first call before any stream capture.
+ *   - Every call on a device shares that device's copy of the array and leaves its contents behind:
+ *     each call zeroes the counter and flag and rebuilds the table on `stream`, so calls whose work
+ *     overlaps on the same GPU (for example on two streams) race and must be serialised by the
+ *     caller. Not thread-safe.
+ *   - Device-side numeric problems show up as NaN outputs of the affected zones; there is no
+ *     check call for this entry point. */
+vx_status vx_rates_eval_noalloc(const vx_config *cfg, const vx_batch *batch, const vx_out *out, vx_stream stream);
+
 const char *vx_status_string(vx_status s);
 /* Last error message of the calling thread (static storage, never NULL). */
 const char *vx_last_error(void);

@@ -43,7 +43,8 @@ class VxError(RuntimeError):
 
 
 SYMBOLS = ("vx_rates_create", "vx_rates_eval", "vx_rates_adjoint", "vx_rates_check",
-           "vx_rates_entries_per_zone", "vx_rates_destroy", "vx_status_string", "vx_last_error")
+           "vx_rates_entries_per_zone", "vx_rates_destroy", "vx_status_string", "vx_last_error",
+           "vx_rates_eval_noalloc")
 
 _lib = None
 
@@ -73,6 +74,9 @@ def lib(path: str | None = None):
     L.vx_rates_destroy.restype = None
     L.vx_status_string.argtypes = [ctypes.c_int]
     L.vx_status_string.restype = ctypes.c_char_p
+    L.vx_rates_eval_noalloc.argtypes = [ctypes.POINTER(vx_config), ctypes.POINTER(vx_batch), ctypes.POINTER(vx_out),
+                                        ctypes.c_void_p]
+    L.vx_rates_eval_noalloc.restype = ctypes.c_int
     L.vx_last_error.argtypes = []
     L.vx_last_error.restype = ctypes.c_char_p
     _lib = L
@@ -100,6 +104,13 @@ def vx_rates_create(cfg: vx_config) -> ctypes.c_void_p:
 
 def vx_rates_eval(h, batch: vx_batch, out: vx_out, stream: int = 0) -> None:
     _check(lib().vx_rates_eval(h, ctypes.byref(batch), ctypes.byref(out), ctypes.c_void_p(stream)), "vx_rates_eval")
+
+
+def vx_rates_eval_noalloc(cfg: vx_config, batch: vx_batch, out: vx_out, stream: int = 0) -> None:
+    """Forward rates without a handle and without any allocation by the library (see the header
+    for its limits and the shared scratch it uses)."""
+    _check(lib().vx_rates_eval_noalloc(ctypes.byref(cfg), ctypes.byref(batch), ctypes.byref(out),
+                                       ctypes.c_void_p(stream)), "vx_rates_eval_noalloc")
 
 
 def vx_rates_adjoint(h, batch: vx_batch, grad_out: vx_out | None, jac: int | None, grad_state: int | None,

@@ -650,3 +650,233 @@ void vx_rates_destroy(vx_rates *h) {
 }
 
 }  // extern "C"
+
+// =============================================================================================
+// Allocation-free evaluation (vx_rates_eval_noalloc). Everything the forward mixed kernel needs
+// besides the caller's inputs and outputs -- the work counter, the numeric flag and the
+// (bin pair, omega node) table -- lives in one file-scope device array, so the call allocates
+// nothing. Limits: at most VX_NOALLOC_MAX_BINS bins and VX_NOALLOC_MAX_MU cos(omega) nodes.
+// =============================================================================================
+#define VX_NOALLOC_MAX_BINS 24
+#define VX_NOALLOC_MAX_MU 32
+#define VX_NOALLOC_MAX_PAIRS (VX_NOALLOC_MAX_BINS * (VX_NOALLOC_MAX_BINS + 1) / 2)
+#define VX_NOALLOC_TABLE_OFFSET 256
+#define VX_NOALLOC_SCRATCH_BYTES \
+    (VX_NOALLOC_TABLE_OFFSET + (size_t)VX_NOALLOC_MAX_PAIRS * VX_NOALLOC_MAX_MU * 3 * sizeof(float4))
+#define VX_NOALLOC_MAX_DEVICES 64
+
+// 461,056 bytes on every device that loads the library, held until the process exits.
+// Layout: [0, 8) work counter, [8, 12) numeric flag, [256, ...) the pair table.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[VX_NOALLOC_SCRATCH_BYTES];
+
+// Device address of g_noalloc_scratch per device; the name itself is only a host-side stand-in.
+static unsigned char *g_noalloc_ptr[VX_NOALLOC_MAX_DEVICES] = {nullptr};
+
+namespace {
+
+struct NoallocTab {
+    double eps[VX_NOALLOC_MAX_BINS];
+    double tm[VX_NOALLOC_MAX_MU], wm[VX_NOALLOC_MAX_MU];
+    uint16_t pij[VX_NOALLOC_MAX_PAIRS];
+    int N, n_mu, npair;
+};
+
+// Fills the (omega node, unordered pair) table in scratch with the records vx_rates_create builds
+// on the host: half-width |q|/2, lower electron energy E-, and the three moment coefficients, each
+// as an FP32 value plus FP32 remainder.
+__global__ void k_noalloc_table(const __grid_constant__ NoallocTab P, float4 *tab) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= P.n_mu * P.npair) return;
+    const int m = e / P.npair, p = e % P.npair;
+    const int i = P.pij[p] >> 8, j = P.pij[p] & 0xff;
+    const double pi = 3.14159265358979323846;
+    const double t = P.tm[m], y = 1.0 - t;
+    const double ee = P.eps[i], ep = P.eps[j];
+    const double d = ee - ep, g = ee * ep * (1.0 + t);
+    const double q2 = d * d + 2.0 * g, q = sqrt(q2), hh = 0.5 * q;
+    const double q0 = ee + ep, s = 2.0 * ee * ep * y;
+    const double Em = s / (2.0 * (q0 + q));
+    const double pref = P.wm[m] * pi * ee * ep * y * y / (16.0 * q2);
+    const double kp = pref * 0.25 * (q + d) * (q + d), km = pref * 0.25 * (q - d) * (q - d), k0 = pref * 2.0 * g;
+    float4 *r = tab + ((size_t)m * P.npair + p) * 3;
+    float fh = (float)hh, fEm = (float)Em, fkp = (float)kp, fkm = (float)km, fk0 = (float)k0;
+    r[0] = make_float4(fh, (float)(hh - fh), fEm, (float)(Em - fEm));
+    r[1] = make_float4(fkp, fkm, fk0, 0.f);
+    r[2] = make_float4((float)(kp - fkp), (float)(km - fkm), (float)(k0 - fk0), 0.f);
+}
+
+// Gauss-Legendre nodes and weights into caller arrays (the same Newton iteration as
+// gauss_legendre, without heap storage).
+void gl_fixed(int n, double *x, double *w) {
+    const double pi = 3.14159265358979323846;
+    for (int k = 1; k <= n / 2 + (n & 1); ++k) {
+        double r = std::cos(pi * (k - 0.25) / (n + 0.5)), dP = 1.0;
+        for (int it = 0; it < 60; ++it) {
+            double Pm = 1.0, P = r;
+            for (int m = 2; m <= n; ++m) {
+                double Pn = ((2 * m - 1) * r * P - (m - 1) * Pm) / m;
+                Pm = P;
+                P = Pn;
+            }
+            if (n == 1) { P = r; Pm = 1.0; }
+            dP = n * (Pm - r * P) / (1.0 - r * r);
+            double step = P / dP;
+            r -= step;
+            if (std::fabs(step) <= 1e-17) {
+                Pm = 1.0; P = r;
+                for (int m = 2; m <= n; ++m) {
+                    double Pn = ((2 * m - 1) * r * P - (m - 1) * Pm) / m;
+                    Pm = P;
+                    P = Pn;
+                }
+                if (n == 1) { P = r; Pm = 1.0; }
+                dP = n * (Pm - r * P) / (1.0 - r * r);
+                break;
+            }
+        }
+        double wk = 2.0 / ((1.0 - r * r) * dP * dP);
+        x[n - k] = r; x[k - 1] = -r;
+        w[n - k] = wk; w[k - 1] = wk;
+    }
+    if (n & 1) x[n / 2] = 0.0;
+}
+
+}  // namespace
+
+// Kernel parameters of a config, built as vx_rates_create builds them, on the stack.
+static void noalloc_params(const vx_config *cfg, vx::Launch &L, NoallocTab &T) {
+    const int N = cfg->n_bins, S = cfg->n_species, nmu = cfg->n_mu, ne = cfg->n_e;
+    vx::Common &C = L.c;
+    memset(&L, 0, sizeof L);
+    memset(&T, 0, sizeof T);
+    C.N = N; C.n_mu = nmu; C.n_e = ne; C.S = S;
+    C.npair = N * (N + 1) / 2;
+    C.ms = 1;
+    C.g2 = cfg->g2; C.norm = cfg->norm; C.eta_sw = cfg->eta_fp64 == 0.0 ? 10.0 : cfg->eta_fp64;
+    const double *eps = cfg->eps;
+    for (int i = 0; i < N; ++i) {
+        double w;
+        if (cfg->weights) w = cfg->weights[i];
+        else {
+            double lo = i ? std::sqrt(eps[i - 1] * eps[i]) : eps[0] * std::sqrt(eps[0] / eps[1]);
+            double hi = i < N - 1 ? std::sqrt(eps[i] * eps[i + 1]) : eps[N - 1] * std::sqrt(eps[N - 1] / eps[N - 2]);
+            w = eps[i] * eps[i] * (hi - lo);
+        }
+        C.eps[i] = eps[i];
+        C.w[i] = w;
+        T.eps[i] = eps[i];
+    }
+    for (int s = 0; s < S; ++s) {
+        int sp = cfg->species[s];
+        int want = sp == VX_NU_E ? VX_NU_EBAR : sp == VX_NU_EBAR ? VX_NU_E : VX_NU_X;
+        for (int t = 0; t < S; ++t) if (cfg->species[t] == want) C.partner[s] = t;
+        C.species[s] = sp;
+        double cv = (sp == VX_NU_X ? -0.5 : 0.5) + 2.0 * cfg->sin2w, ca = sp == VX_NU_X ? -0.5 : 0.5;
+        double b1 = (cv + ca) * (cv + ca), b2 = (cv - ca) * (cv - ca);
+        if (sp == VX_NU_EBAR) std::swap(b1, b2);
+        C.bI64[s] = b1; C.bII64[s] = b2;
+        C.bI[s] = (float)b1; C.bII[s] = (float)b2;
+    }
+    int p = 0;
+    for (int i = 0; i < N; ++i)
+        for (int j = i; j < N; ++j) { C.pij[p] = (uint16_t)((i << 8) | j); T.pij[p] = C.pij[p]; ++p; }
+    double tm[VX_MAX_MU], wm[VX_MAX_MU], tk[VX_MAX_NE], wk[VX_MAX_NE];
+    gl_fixed(nmu, tm, wm);
+    gl_fixed(ne, tk, wk);
+    for (int m = 0; m < nmu; ++m) {
+        C.t64[m] = tm[m];
+        C.t_hi[m] = (float)tm[m];
+        C.t_lo[m] = (float)(tm[m] - (double)C.t_hi[m]);
+        T.tm[m] = tm[m];
+        T.wm[m] = wm[m];
+    }
+    for (int k = 0; k < ne; ++k) {
+        double u = 1.0 + tk[k], v = 1.0 - tk[k];
+        L.n32.u[k] = (float)u; L.n32.v[k] = (float)v;
+        L.n32.cp[k] = (float)(wk[k] * u * u); L.n32.cm[k] = (float)(wk[k] * v * v); L.n32.c0[k] = (float)(wk[k] * u * v);
+        double uh = std::nearbyint(u * 2048.0) / 2048.0;
+        L.n32.uh[k] = (float)uh;
+        L.n32.ul[k] = (float)(u - uh);
+    }
+    double hmax = 0.0, q0hmax = 0.0;
+    for (int m = 0; m < nmu; ++m)
+        for (int q = 0; q < C.npair; ++q) {
+            const int i = C.pij[q] >> 8, j = C.pij[q] & 0xff;
+            const double d = eps[i] - eps[j], g = eps[i] * eps[j] * (1.0 + tm[m]);
+            hmax = std::fmax(hmax, 0.5 * std::sqrt(d * d + 2.0 * g));
+            q0hmax = std::fmax(q0hmax, 0.5 * (eps[i] + eps[j]));
+        }
+    C.h_max = hmax;
+    C.q0h_max = q0hmax;
+    T.N = N; T.n_mu = nmu; T.npair = C.npair;
+}
+
+extern "C" {
+
+vx_status vx_rates_eval_noalloc(const vx_config *cfg, const vx_batch *b, const vx_out *out, vx_stream stream) {
+    vx_status st = validate_config(cfg);
+    if (st != VX_OK) return st;
+    if (cfg->prec != VX_PREC_MIXED) return fail(VX_ERR_UNSUPPORTED, "vx_rates_eval_noalloc evaluates the mixed form only");
+    if (cfg->n_bins > VX_NOALLOC_MAX_BINS || cfg->n_mu > VX_NOALLOC_MAX_MU)
+        return fail(VX_ERR_UNSUPPORTED,
+                    "vx_rates_eval_noalloc: %d bins x %d cos(omega) nodes exceed its fixed scratch of %zu bytes "
+                    "(at most %d bins and %d nodes); use a handle from vx_rates_create",
+                    cfg->n_bins, cfg->n_mu, (size_t)VX_NOALLOC_SCRATCH_BYTES, VX_NOALLOC_MAX_BINS, VX_NOALLOC_MAX_MU);
+    if (!b) return fail(VX_ERR_INVALID_ARG, "batch is NULL");
+    if (b->n_zones < 0 || b->n_rays < 0) return fail(VX_ERR_INVALID_ARG, "negative batch size");
+    if (b->ray_offsets) {
+        if (b->ray_offsets[0] != 0) return fail(VX_ERR_INVALID_ARG, "ray_offsets[0] must be 0");
+        for (int r = 0; r < b->n_rays; ++r)
+            if (b->ray_offsets[r + 1] < b->ray_offsets[r])
+                return fail(VX_ERR_INVALID_ARG, "ray_offsets must be non-decreasing (ray %d)", r);
+        if ((long long)b->ray_offsets[b->n_rays] != b->n_zones)
+            return fail(VX_ERR_INVALID_ARG, "ray_offsets[n_rays] does not equal n_zones");
+    }
+    if (b->n_zones == 0) return VX_OK;
+    if ((st = check_device_ptr(b->state, "state")) != VX_OK) return st;
+    if ((st = check_device_ptr(b->J, "J")) != VX_OK) return st;
+    if ((st = check_device_ptr(b->H, "H")) != VX_OK) return st;
+    if ((st = validate_out(out, true)) != VX_OK) return st;
+
+    int dev = 0;
+    VX_CU(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= VX_NOALLOC_MAX_DEVICES) return fail(VX_ERR_UNSUPPORTED, "device ordinal %d too large", dev);
+    if (!g_noalloc_ptr[dev]) {  // once per device, with that device current
+        void *ptr = nullptr;
+        VX_CU(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+        g_noalloc_ptr[dev] = (unsigned char *)ptr;
+    }
+    unsigned char *scratch = g_noalloc_ptr[dev];
+
+    vx::Launch L;
+    NoallocTab T;
+    noalloc_params(cfg, L, T);
+    L.tab32 = reinterpret_cast<const float4 *>(scratch + VX_NOALLOC_TABLE_OFFSET);
+    L.tab64 = nullptr;
+    L.Z = b->n_zones;
+    L.state = b->state; L.J = b->J; L.H = b->H;
+    L.j0 = out->j0; L.chi0 = out->chi0; L.j1 = out->j1; L.chi1 = out->chi1; L.phi = out->phi;
+    L.counter = reinterpret_cast<unsigned long long *>(scratch);
+    L.flag = reinterpret_cast<int *>(scratch + 8);
+
+    const int ne = cfg->n_e, minb = 2;
+    const int block = std::min(round_up(L.c.npair, 32), VX_TPB_MIXED);
+    const size_t smem = vx::smem_mixed_bytes(cfg->n_bins, cfg->n_species, false);
+    const void *fn = vx::kernel_mixed(false, minb, ne);
+    if (smem > 48 * 1024) VX_CU(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int nsm = 0, occ = 0;
+    VX_CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    VX_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, block, smem));
+    if (occ < 1) return fail(VX_ERR_UNSUPPORTED, "kernel does not fit on an SM");
+    const int grid = (int)std::min<long long>((long long)occ * nsm, b->n_zones);
+
+    cudaStream_t s = (cudaStream_t)stream;
+    VX_CU(cudaMemsetAsync(scratch, 0, 16, s));  // work counter and numeric flag start at zero
+    const int nrec = T.n_mu * T.npair;
+    k_noalloc_table<<<(nrec + 255) / 256, 256, 0, s>>>(T, reinterpret_cast<float4 *>(scratch + VX_NOALLOC_TABLE_OFFSET));
+    VX_CU(cudaGetLastError());
+    VX_CU(vx::launch_mixed(false, minb, L, grid, block, smem, s));
+    return VX_OK;
+}
+
+}  // extern "C"

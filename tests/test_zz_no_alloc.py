@@ -1,0 +1,83 @@
+"""The allocation-free entry point vx_rates_eval_noalloc, called through the C ABI.
+
+It serves callers that must not have the library allocate device memory (their memory belongs
+to their own pool, or their time step cannot afford the synchronisation of cudaMalloc/cudaFree).
+Its rates must match those of vx_rates_eval on a mixed-precision handle within the mixed
+tolerance, call after call, although every call reuses the same fixed device scratch.
+This file is collected last so that a run stopping at the first failure has run everything else.
+"""
+import numpy as np
+import pytest
+
+import vx_inputs
+from _metrics import worst
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+KEYS = ("j0", "chi0", "j1", "chi1")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1404_1719_gb300 import _build
+    _build.build()
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).cuda()
+
+
+def config(capi, b, keep):
+    eps = np.ascontiguousarray(b["eps"], dtype=np.float64)
+    sp = np.ascontiguousarray(b["species"], dtype=np.int32)
+    keep += [eps, sp]
+    return capi.vx_config(n_bins=len(eps), eps=eps.ctypes.data_as(capi._dp), weights=None, n_mu=b["n_mu"],
+                          n_e=b["n_e"], n_species=len(sp), species=sp.ctypes.data_as(capi._ip), sin2w=0.23,
+                          g2=1.0, norm=1.0, eta_fp64=0.0, prec=capi.VX_PREC_MIXED, flags=0)
+
+
+def noalloc(capi, b, keep):
+    st, J, H = dev(b["state"]), dev(b["J"]), dev(b["H"])
+    keep += [st, J, H]
+    Z, S, N = J.shape
+    out = {k: torch.full((Z, S, N), float("nan"), dtype=torch.float64, device="cuda") for k in KEYS}
+    batch = capi.vx_batch(n_rays=1, n_zones=Z, ray_offsets=None, state=st.data_ptr(), J=J.data_ptr(), H=H.data_ptr())
+    o = capi.vx_out(*(out[k].data_ptr() for k in KEYS), None)
+    capi.vx_rates_eval_noalloc(config(capi, b, keep), batch, o, torch.cuda.current_stream().cuda_stream)
+    return out
+
+
+def with_handle(b):
+    from paper_1404_1719_gb300 import PairRates
+    r = PairRates(b["eps"], b["n_mu"], b["n_e"], species=b["species"])
+    res = r.evaluate(dev(b["state"]), dev(b["J"]), dev(b["H"]))
+    assert r.check()
+    out = {k: v.cpu().numpy() for k, v in res.items()}
+    r.close()
+    return out
+
+
+def test_noalloc_matches_handle_on_consecutive_calls():
+    from paper_1404_1719_gb300 import capi
+    keep = []
+    # two calls in a row with different grids and quadratures: the second rebuilds the shared table
+    for b in (vx_inputs.make_batch(2), vx_inputs.make_batch(1), vx_inputs.make_batch(5, rays=[7])):
+        got = noalloc(capi, b, keep)
+        torch.cuda.synchronize()
+        ref = with_handle(b)
+        for k in KEYS:
+            g = got[k].cpu().numpy()
+            assert np.all(np.isfinite(g)), k
+            assert worst(g, ref[k]) <= 1e-5, k
+
+
+def test_noalloc_rejects_sizes_beyond_its_scratch():
+    from paper_1404_1719_gb300 import capi
+    keep = []
+    b = vx_inputs.make_batch(1, rays=[0])
+    b = dict(b, eps=vx_inputs.energy_centres(25, 1.0, 300.0), J=np.zeros((64, 3, 25)), H=np.zeros((64, 3, 25)))
+    with pytest.raises(capi.VxError) as e:
+        noalloc(capi, b, keep)
+    assert e.value.status == capi.VX_ERR_UNSUPPORTED and "at most 24 bins" in str(e.value)
