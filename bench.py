@@ -155,6 +155,10 @@ def run_ours(args):
     _build.build()
 
     b = vx_inputs.make_batch(WORKLOAD, seed=rank, rays=None if args.rays is None else range(args.rays))
+    # the autotuner's choice is reported from its cache file
+    tune_file = os.environ.get("VX_AUTOTUNE_CACHE") or os.path.join(
+        os.environ.get("TMPDIR", "/tmp"), f"vx_bench_tune_{os.getpid()}.json")
+    os.environ["VX_AUTOTUNE_CACHE"] = tune_file
     Z, N, S = b["state"].shape[0], len(b["eps"]), len(b["species"])
     host = {k: torch.from_numpy(np.ascontiguousarray(b[k])).pin_memory() for k in ("state", "J", "H")}
     d = {k: v.to(dev) for k, v in host.items()}
@@ -244,6 +248,14 @@ def run_ours(args):
         torch.cuda.synchronize()
         v64 = entries(sub, N) / (f0.elapsed_time(f1) / 1000)
         r64.close()
+        tune = {}
+        try:
+            with open(tune_file) as f:
+                tune = {k.split("kind=")[1].split(",")[0]: v for k, v in json.load(f).items()
+                        if f"N={N},n_mu={b['n_mu']},n_e={b['n_e']}," in k}
+        except (OSError, ValueError, IndexError):
+            pass
+        minb = tune.get("tangents", {}).get("minb", 3)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -260,7 +272,8 @@ def run_ours(args):
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None,
                          "peak_note": f"FP32 {nsm} SMs x 128 FMA x 2 x {mhz:.0f} MHz (median SM clock in the run)",
-                         "kernel": "k_pair_mixed<64,true>"},
+                         "kernel": f"k_pair_mixed<{b['n_e']}, tangents, {minb} CTAs/SM>"},
+            "autotune": tune,
             "fp64_fwd": {"value": v64, "unit": UNIT, "sample": f"first {sub} zones, plain FP64 forward only",
                          "ratio_mixed_fwd_adj_over_fp64_fwd": value / world / v64},
             "clocks": c,

@@ -15,10 +15,15 @@ SOURCES = ["vx_rates.cu", "vx_mixed_fwd_b2.cu", "vx_mixed_fwd_b3.cu", "vx_mixed_
 HEADERS = ["vx_internal.h", "vx_kernel_mixed.cuh", "vx_mixed_inst.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
+# Extra nvcc flags (e.g. -DVX_ADJ_PAIR=1) for tuning experiments; part of the staleness check.
+EXTRA = os.environ.get("VX_NVCC_FLAGS", "").split()
 
 
 def _stale() -> bool:
     if not os.path.exists(LIB):
+        return True
+    stamp = LIB + ".flags"
+    if not os.path.exists(stamp) or open(stamp).read() != " ".join(EXTRA):
         return True
     t = os.path.getmtime(LIB)
     deps = [os.path.join(CSRC, f) for f in SOURCES + HEADERS] + [os.path.join(INCLUDE, "vx_rates.h")]
@@ -35,7 +40,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(src):
         obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-        cmd = [nvcc] + ARCH + FLAGS + ["-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [nvcc] + ARCH + FLAGS + EXTRA + ["-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr}")
@@ -51,6 +56,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
     os.replace(tmp, LIB)
+    with open(LIB + ".flags", "w") as f:
+        f.write(" ".join(EXTRA))
     return LIB
 
 

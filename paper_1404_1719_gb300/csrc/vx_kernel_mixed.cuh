@@ -33,6 +33,11 @@
 #pragma once
 #include "vx_internal.h"
 
+// Pair reciprocals (one rcp for two nodes) also in the tangent kernel's fast path.
+#ifndef VX_ADJ_PAIR
+#define VX_ADJ_PAIR 0
+#endif
+
 namespace vx {
 
 __device__ __forceinline__ float ex2a(float x) {
@@ -44,6 +49,17 @@ __device__ __forceinline__ float rcpa(float x) {
     float y;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
+}
+
+// 2^-y (y > -1023) as an FP64 value: the integer part of y becomes an exact power of two, the
+// fraction goes through MUFU ex2 (relative error ~2^-22, ample for factors that scale FP32 sums).
+// Results below the FP64 range flush to 0, as the definition's own values do.
+__device__ __forceinline__ double exp2neg(double y) {
+    const double n = floor(y);
+    if (n > 1022.0) return 0.0;
+    const float f = (float)(y - n);  // in [0, 1)
+    const double p2 = __longlong_as_double((long long)(1023 - (int)n) << 52);
+    return (double)ex2a(-f) * p2;
 }
 
 // (h, l) += (ah + al) * M : error-free product and two-sum in FP32 (no contraction).
@@ -114,14 +130,14 @@ template <int NE, bool ADJ, bool DEG>
 __device__ __forceinline__ void node_loop(const NodeSm *__restrict__ nd, int ne, float B, float Pe,
                                           float Pp, float Bq, float Bl, float Pq, float Pl, float h,
                                           float Em, float c1, Mom &mo, Mom &ta, Mom &tp, Mom &et) {
-    constexpr bool PAIR = !ADJ && !DEG;
+    constexpr bool PAIR = !DEG && (!ADJ || VX_ADJ_PAIR);
     constexpr int U = 16;
     auto accum = [&](const NodeSm &q, float e1, float e2, float t, float r) {
         mo.p = fmaf(q.a.z, r, mo.p);
         mo.m = fmaf(q.a.w, r, mo.m);
         mo.z = fmaf(q.b.x, r, mo.z);
         if (ADJ) {
-            float qv = (1.f + e2) * r;
+            float qv = fmaf(e2, r, r);  // (1 + e2) r
             float se = DEG ? c1 * qv : qv;  // 1 - f_e
             float sp = t * r;               // 1 - f_ebar
             float fe = e1 * qv, fp = e2 * sp;
@@ -182,29 +198,47 @@ __device__ __forceinline__ void node_loop(const NodeSm *__restrict__ nd, int ne,
     }
 }
 
-// Projection of one quantity's moments onto l = 0, 1 for terms I and II. (kp, km) are already
-// exchanged for eta < 0.
+// Coefficients that turn one (pair, omega) node's moments into its contributions: l = 0 in FP32
+// (kp, km, k0), l = 1 as t * k in FP32 (fast path) or as FP32 pairs (degenerate path). (kp, km)
+// are already exchanged for eta < 0.
+struct Coef {
+    float kp, km, k0;        // l = 0
+    float lph, lmh, l0h;     // l = 1, high parts
+    float lpl, lml, l0l;     // l = 1, low parts (degenerate path)
+};
+
 template <bool DEG>
-__device__ __forceinline__ void project(Proj &P, const Mom &M, float kp, float km, float k0, float kpl,
-                                        float kml, float k0l, float th, float tl) {
-    float KI = fmaf(kp, M.p, fmaf(km, M.m, k0 * M.z));
-    float KII = fmaf(km, M.p, fmaf(kp, M.m, k0 * M.z));
-    P.o0I += KI;
-    P.o0II += KII;
+__device__ __forceinline__ Coef make_coef(float kp, float km, float k0, float kpl, float kml, float k0l, float th,
+                                          float tl) {
+    Coef c;
+    c.kp = kp; c.km = km; c.k0 = k0;
     if (!DEG) {
-        P.o1Ih = fmaf(th, KI, P.o1Ih);
-        P.o1IIh = fmaf(th, KII, P.o1IIh);
+        c.lph = th * kp; c.lmh = th * km; c.l0h = th * k0;
+        c.lpl = c.lml = c.l0l = 0.f;
     } else {
-        float lph, lpl, lmh, lml, l0h, l0l;
-        df_mul(th, tl, kp, kpl, lph, lpl);
-        df_mul(th, tl, km, kml, lmh, lml);
-        df_mul(th, tl, k0, k0l, l0h, l0l);
-        df_fma(P.o1Ih, P.o1Il, lph, lpl, M.p);
-        df_fma(P.o1Ih, P.o1Il, lmh, lml, M.m);
-        df_fma(P.o1Ih, P.o1Il, l0h, l0l, M.z);
-        df_fma(P.o1IIh, P.o1IIl, lmh, lml, M.p);
-        df_fma(P.o1IIh, P.o1IIl, lph, lpl, M.m);
-        df_fma(P.o1IIh, P.o1IIl, l0h, l0l, M.z);
+        df_mul(th, tl, kp, kpl, c.lph, c.lpl);
+        df_mul(th, tl, km, kml, c.lmh, c.lml);
+        df_mul(th, tl, k0, k0l, c.l0h, c.l0l);
+    }
+    return c;
+}
+
+// Projection of one quantity's moments onto l = 0, 1 for terms I and II (term II of a pair uses
+// the coefficients with kp and km exchanged).
+template <bool DEG>
+__device__ __forceinline__ void project(Proj &P, const Mom &M, const Coef &c) {
+    P.o0I += fmaf(c.kp, M.p, fmaf(c.km, M.m, c.k0 * M.z));
+    P.o0II += fmaf(c.km, M.p, fmaf(c.kp, M.m, c.k0 * M.z));
+    if (!DEG) {
+        P.o1Ih += fmaf(c.lph, M.p, fmaf(c.lmh, M.m, c.l0h * M.z));
+        P.o1IIh += fmaf(c.lmh, M.p, fmaf(c.lph, M.m, c.l0h * M.z));
+    } else {
+        df_fma(P.o1Ih, P.o1Il, c.lph, c.lpl, M.p);
+        df_fma(P.o1Ih, P.o1Il, c.lmh, c.lml, M.m);
+        df_fma(P.o1Ih, P.o1Il, c.l0h, c.l0l, M.z);
+        df_fma(P.o1IIh, P.o1IIl, c.lmh, c.lml, M.p);
+        df_fma(P.o1IIh, P.o1IIl, c.lph, c.lpl, M.m);
+        df_fma(P.o1IIh, P.o1IIl, c.l0h, c.l0l, M.z);
     }
 }
 
@@ -273,9 +307,10 @@ __global__ void __launch_bounds__(VX_TPB_MIXED, MINB) k_pair_mixed(const __grid_
                 zs.unsc = ldexp(1.0, -sc);
                 // grid of the exact split: B_hi on 2^-kb with < 2^11 steps, P_hi and the sum on
                 // 2^-(kb+11) with |sum| < 2^24 steps
-                double Bmax = C.h_max * il * 1.0001 + 1e-30;
-                double Pmax = C.q0h_max * il + el + sc + 1.0;
-                int kb = (int)floor(fmin(11.0 - log2(Bmax), 13.0 - log2(Pmax + 2.0 * Bmax))) - 1;
+                // (log2f is accurate to far better than the factor-2 margin left by the "- 1")
+                float Bmax = (float)(C.h_max * il * 1.0001 + 1e-30);
+                float Pmax = (float)(C.q0h_max * il + el + sc + 1.0);
+                int kb = (int)floorf(fminf(11.f - log2f(Bmax), 13.f - log2f(Pmax + 2.f * Bmax))) - 1;
                 kb = kb < -60 ? -60 : (kb > 60 ? 60 : kb);
                 if (kb + 11 < 0) {  // grid coarser than 1: the integer shift would not be exact
                     zs.sc = 0.f;
@@ -308,10 +343,14 @@ __global__ void __launch_bounds__(VX_TPB_MIXED, MINB) k_pair_mixed(const __grid_
         }
 
         // ---- per-zone FP64 scales and contraction vectors -------------------------------------
-        for (int i = tid; i < N; i += blockDim.x) {
-            sc[i] = exp(-(C.eps[i] + C.eps[0]) / T);
-            em[i] = exp(-C.eps[i] / T);
-            shv[i] = exp(-(C.eps[i] - C.eps[0]) / T + zs.sv * 0.6931471805599453);
+        {
+            const double il = 1.4426950408889634 / T;  // log2(e)/T
+            for (int e = tid; e < 3 * N; e += blockDim.x) {
+                const int i = e % N, which = e / N;
+                if (which == 0) sc[i] = exp2neg((C.eps[i] + C.eps[0]) * il);           // e^{-(eps_i+eps_0)/T}
+                else if (which == 1) em[i] = exp2neg(C.eps[i] * il);                     // e^{-eps_i/T}
+                else shv[i] = exp2neg((C.eps[i] - C.eps[0]) * il - (double)zs.sv);       // e^{-(eps_i-eps_0)/T} 2^sv
+            }
         }
         __syncthreads();
         for (int e = tid; e < 4 * S * N; e += blockDim.x) {
@@ -350,11 +389,12 @@ __global__ void __launch_bounds__(VX_TPB_MIXED, MINB) k_pair_mixed(const __grid_
                 if (!deg) {
                     const float Pe = fmaf(Em, il_h, -el_h);
                     node_loop<NE, ADJ, false>(s_nodes, C.n_e, B, Pe, Pp, 0.f, 0.f, 0.f, 0.f, h, Em, 1.f, mo, ta, tp, et);
-                    project<false>(PO, mo, kp, km, k0, kpl, kml, k0l, C.t_hi[m], C.t_lo[m]);
+                    const Coef cf = make_coef<false>(kp, km, k0, kpl, kml, k0l, C.t_hi[m], C.t_lo[m]);
+                    project<false>(PO, mo, cf);
                     if (ADJ) {
-                        project<false>(PTa, ta, kp, km, k0, kpl, kml, k0l, C.t_hi[m], C.t_lo[m]);
-                        project<false>(PTp, tp, kp, km, k0, kpl, kml, k0l, C.t_hi[m], C.t_lo[m]);
-                        project<false>(PEt, et, kp, km, k0, kpl, kml, k0l, C.t_hi[m], C.t_lo[m]);
+                        project<false>(PTa, ta, cf);
+                        project<false>(PTp, tp, cf);
+                        project<false>(PEt, et, cf);
                     }
                 } else {
                     const float il_l = zs.il_l, el_l = zs.el_l;
@@ -374,11 +414,12 @@ __global__ void __launch_bounds__(VX_TPB_MIXED, MINB) k_pair_mixed(const __grid_
                     float Pl = __fadd_rn(__fsub_rn(s, Pq), slo);
                     Pq = __fadd_rn(Pq, zs.sc);  // exact: an integer on the same grid
                     node_loop<NE, ADJ, true>(s_nodes, C.n_e, B, 0.f, Pp, Bq, Bl, Pq, Pl, h, Em, zs.c1, mo, ta, tp, et);
-                    project<true>(PO, mo, kp, km, k0, kpl, kml, k0l, C.t_hi[m], C.t_lo[m]);
+                    const Coef cf = make_coef<true>(kp, km, k0, kpl, kml, k0l, C.t_hi[m], C.t_lo[m]);
+                    project<true>(PO, mo, cf);
                     if (ADJ) {
-                        project<true>(PTa, ta, kp, km, k0, kpl, kml, k0l, C.t_hi[m], C.t_lo[m]);
-                        project<true>(PTp, tp, kp, km, k0, kpl, kml, k0l, C.t_hi[m], C.t_lo[m]);
-                        project<true>(PEt, et, kp, km, k0, kpl, kml, k0l, C.t_hi[m], C.t_lo[m]);
+                        project<true>(PTa, ta, cf);
+                        project<true>(PTp, tp, cf);
+                        project<true>(PEt, et, cf);
                     }
                 }
             }

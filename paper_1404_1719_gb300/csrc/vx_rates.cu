@@ -450,8 +450,8 @@ static void fill_launch(const vx_rates *h, const vx_batch *b, vx::Launch &L) {
 
 // ---- autotuner ------------------------------------------------------------------------------
 // Picks, per kernel kind, the register budget (2 or 3 CTAs per SM) that runs a sample of the
-// first batch fastest: the first zones of the batch, a few per CTA, each variant once to warm up
-// and once timed with CUDA events. The choice is kept in the handle and, when the environment
+// first batch fastest: the first zones of the batch, about 48 per CTA, each variant once to warm
+// up and once timed with CUDA events (four launches in all). The choice is kept in the handle and, when the environment
 // variable VX_AUTOTUNE_CACHE names a file, in that JSON file under a key of the quadrature, the
 // kernel kind and the device (SM count, compute capability). Tuning synchronises the stream, so
 // the first tuned call must not be inside a stream capture; its sample outputs are overwritten
@@ -513,8 +513,10 @@ static vx_status autotune(vx_rates *h, bool adj, const vx::Launch &L, cudaStream
             }
         }
     }
-    const long long sample = std::min<long long>(L.Z, 8LL * h->grid_mixed[kind][1]);
-    if (sample < 2LL * h->grid_mixed[kind][1]) return VX_OK;  // too small to tell apart: keep the default
+    // ~48 zones per CTA of the larger grid: long enough that start-up and tail effects of the
+    // persistent grid do not decide the comparison
+    const long long sample = std::min<long long>(L.Z, 48LL * h->grid_mixed[kind][1]);
+    if (sample < 8LL * h->grid_mixed[kind][1]) return VX_OK;  // too small to tell apart: keep the default
     vx::Launch Ls = L;
     Ls.Z = sample;
     const size_t smem = adj ? h->smem_adj : h->smem_fwd;
