@@ -86,11 +86,12 @@ struct Launch64 {
 //                   eta), l = 0, l = 1 hi, l = 1 lo of Phi_I(i,j) (term II is the transpose)
 //   vec[4][S][N]  : contraction vectors per output (j0, chi0, j1, chi1) and species
 //   sc, em, shv [N] (double): per-bin FP64 factors;  red[64] (double): block reduction
-__host__ __device__ inline size_t smem_mixed_bytes(int N, int S, bool adj) {
+//   part[block][2][q][6]: partial projections of bin pairs split between two threads
+__host__ __device__ inline size_t smem_mixed_bytes(int N, int S, bool adj, int block) {
     size_t nq = adj ? 4 : 1;
     size_t f = nq * 3 * (size_t)N * N + 4 * (size_t)S * N;
     f = (f + 1) & ~(size_t)1;
-    return f * 4 + 3 * (size_t)N * 8 + 64 * 8;
+    return f * 4 + 3 * (size_t)N * 8 + 64 * 8 + (size_t)block * 2 * nq * 6 * 4;
 }
 size_t smem_fp64(const Common &c);
 

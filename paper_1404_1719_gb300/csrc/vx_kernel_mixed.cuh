@@ -269,6 +269,7 @@ __global__ void __launch_bounds__(VX_TPB_MIXED, MINB) k_pair_mixed(const __grid_
     double *em = sc + N;
     double *shv = em + N;  // exp(-(eps_j - eps_0)/T) 2^sv
     double *red = shv + N;  // 64 doubles for block reductions
+    Proj *part = reinterpret_cast<Proj *>(red + 64);  // [blockDim][2 slots][nq] partial projections
     const int tid = threadIdx.x;
     for (int k = tid; k < C.n_e; k += blockDim.x) {
         s_nodes[k].a = make_float4(L.n32.u[k], L.n32.v[k], L.n32.cp[k], L.n32.cm[k]);
@@ -363,16 +364,23 @@ __global__ void __launch_bounds__(VX_TPB_MIXED, MINB) k_pair_mixed(const __grid_
             vec[e] = (float)v;
         }
 
-        // ---- quadrature: one thread per unordered bin pair, all omega nodes -------------------
-        for (int p = tid; p < npair; p += blockDim.x) {
-            const int pi = C.pij[p] >> 8, pj = C.pij[p] & 0xff;
-            Proj PO, PTa, PTp, PEt;
-            PO.zero();
-            if (ADJ) { PTa.zero(); PTp.zero(); PEt.zero(); }
-            const float il_h = zs.il_h, el_h = zs.el_h;
-            const bool deg = zs.deg, neg = zs.neg;
+        // ---- quadrature: the npair * n_mu (pair, omega) units in equal contiguous ranges --------
+        // A thread's range covers whole pairs and at most one partial pair at each end; partial
+        // projections go to two slots per thread and are combined in thread order below.
+        const int nmu = C.n_mu, U = npair * nmu, TB = blockDim.x;
+        const int u0 = tid * U / TB, u1 = (tid + 1) * U / TB;
+        const float il_h = zs.il_h, el_h = zs.el_h;
+        const bool deg = zs.deg, neg = zs.neg;
+        // One iteration per unit (28 or 29 per thread at N = 21, n_mu = 32): every lane runs the
+        // node loop in step; only the flush at a pair boundary diverges.
+        int p = u0 / nmu, m = u0 - (u0 / nmu) * nmu, mb = m;
+        bool first = true;
+        Proj PO, PTa, PTp, PEt;
+        PO.zero();
+        if (ADJ) { PTa.zero(); PTp.zero(); PEt.zero(); }
 #pragma unroll 1
-            for (int m = 0; m < C.n_mu; ++m) {
+        for (int u = u0; u < u1; ++u) {
+            {
                 const float4 *rec = L.tab32 + ((size_t)m * npair + p) * 3;
                 float4 R0 = __ldg(rec), R1 = __ldg(rec + 1), R2 = __ldg(rec + 2);
                 const float h = R0.x, h_lo = R0.y, Em = R0.z, Em_lo = R0.w;
@@ -423,11 +431,49 @@ __global__ void __launch_bounds__(VX_TPB_MIXED, MINB) k_pair_mixed(const __grid_
                     }
                 }
             }
-            store_proj(mats + 0 * 3 * (size_t)N2, N2, N, pi, pj, PO);
-            if (ADJ) {
-                store_proj(mats + 1 * 3 * (size_t)N2, N2, N, pi, pj, PTa);
-                store_proj(mats + 2 * 3 * (size_t)N2, N2, N, pi, pj, PTp);
-                store_proj(mats + 3 * 3 * (size_t)N2, N2, N, pi, pj, PEt);
+            ++m;
+            if (m == nmu || u + 1 == u1) {  // end of a pair or of this thread's range: flush
+                if (mb == 0 && m == nmu) {  // the whole pair in this thread
+                    const int pi = C.pij[p] >> 8, pj = C.pij[p] & 0xff;
+                    store_proj(mats + 0 * 3 * (size_t)N2, N2, N, pi, pj, PO);
+                    if (ADJ) {
+                        store_proj(mats + 1 * 3 * (size_t)N2, N2, N, pi, pj, PTa);
+                        store_proj(mats + 2 * 3 * (size_t)N2, N2, N, pi, pj, PTp);
+                        store_proj(mats + 3 * 3 * (size_t)N2, N2, N, pi, pj, PEt);
+                    }
+                } else {
+                    Proj *slot = part + ((size_t)tid * 2 + (first ? 0 : 1)) * nq;
+                    slot[0] = PO;
+                    if (ADJ) { slot[1] = PTa; slot[2] = PTp; slot[3] = PEt; }
+                }
+                PO.zero();
+                if (ADJ) { PTa.zero(); PTp.zero(); PEt.zero(); }
+                first = false;
+                ++p;
+                m = 0;
+                mb = 0;
+            }
+        }
+        __syncthreads();
+        // pairs split between threads: sum their partial projections over the owning threads in
+        // order (owner of unit v: ceil((v+1) TB / U) - 1), then store
+        for (int p = tid; p < npair; p += TB) {
+            const int ua = p * nmu, ub = ua + nmu - 1;
+            const int ta = ((ua + 1) * TB + U - 1) / U - 1, tb = ((ub + 1) * TB + U - 1) / U - 1;
+            if (ta == tb) continue;
+            const int pi = C.pij[p] >> 8, pj = C.pij[p] & 0xff;
+            for (int q = 0; q < nq; ++q) {
+                Proj acc;
+                acc.zero();
+                for (int t = ta; t <= tb; ++t) {
+                    const int sl = (t == ta && ua > t * U / TB) ? 1 : 0;
+                    const Proj &x = part[((size_t)t * 2 + sl) * nq + q];
+                    acc.o0I += x.o0I;
+                    acc.o0II += x.o0II;
+                    df_add(acc.o1Ih, acc.o1Il, x.o1Ih, x.o1Il);
+                    df_add(acc.o1IIh, acc.o1IIl, x.o1IIh, x.o1IIl);
+                }
+                store_proj(mats + (size_t)q * 3 * N2, N2, N, pi, pj, acc);
             }
         }
         __syncthreads();

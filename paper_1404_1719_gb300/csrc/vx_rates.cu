@@ -279,7 +279,7 @@ vx_status vx_rates_create(const vx_config *cfg, vx_rates **out) {
     C.ms = 1;
     h->ms = 1;
     h->block = round_up(np, 32);                           // FP64 kernel (<= 496 pairs)
-    h->block_mixed = std::min(round_up(np, 32), VX_TPB_MIXED);
+    h->block_mixed = std::min(round_up(np * nmu, 32), VX_TPB_MIXED);  // (pair, omega) units
 
     auto cleanup = [&](vx_status s) { vx_rates_destroy(h); return s; };
     cudaError_t ce = cudaGetDevice(&h->device);
@@ -306,8 +306,8 @@ vx_status vx_rates_create(const vx_config *cfg, vx_rates **out) {
     VX_CUC(cudaMemcpy(h->d_tab64, t64.data(), t64.size() * sizeof(double), cudaMemcpyHostToDevice));
     VX_CUC(cudaMemset(h->d_flag, 0, sizeof(int)));
 
-    h->smem_fwd = vx::smem_mixed_bytes(N, S, false);
-    h->smem_adj = vx::smem_mixed_bytes(N, S, true);
+    h->smem_fwd = vx::smem_mixed_bytes(N, S, false, h->block_mixed);
+    h->smem_adj = vx::smem_mixed_bytes(N, S, true, h->block_mixed);
     h->smem_64 = vx::smem_fp64(C);
     h->cc_major = prop.major;
     h->cc_minor = prop.minor;
@@ -862,8 +862,8 @@ vx_status vx_rates_eval_noalloc(const vx_config *cfg, const vx_batch *b, const v
     L.flag = reinterpret_cast<int *>(scratch + 8);
 
     const int ne = cfg->n_e, minb = 2;
-    const int block = std::min(round_up(L.c.npair, 32), VX_TPB_MIXED);
-    const size_t smem = vx::smem_mixed_bytes(cfg->n_bins, cfg->n_species, false);
+    const int block = std::min(round_up(L.c.npair * cfg->n_mu, 32), VX_TPB_MIXED);
+    const size_t smem = vx::smem_mixed_bytes(cfg->n_bins, cfg->n_species, false, block);
     const void *fn = vx::kernel_mixed(false, minb, ne);
     if (smem > 48 * 1024) VX_CU(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int nsm = 0, occ = 0;
