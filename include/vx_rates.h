@@ -84,7 +84,7 @@ typedef struct {
     double g2;              /* global kernel scale (G^2 in the kernel's units), e.g. 1.0      */
     double norm;            /* phase-space constant C of the contraction, e.g. 1.0            */
     double eta_fp64;        /* |eta_e| above which the mixed form uses its extended-precision
-                               argument and l = 1 accumulation path (0 -> default 10)         */
+                               argument and l = 1 accumulation path (0 -> default 20)         */
     vx_precision prec;
     unsigned flags;
 } vx_config;

@@ -28,8 +28,9 @@
 //  * degenerate path (|eta| > eta_sw): the electron argument B (1 + tau) + P is formed exactly:
 //    B, P and 1 + tau are split into a high part on a power-of-two grid (chosen per zone so that
 //    fma(B_hi, u_hi, P_hi) is exact in FP32) and a remainder, and exp2 of the exact high part and
-//    of the small remainder are multiplied. The l = 1 projections, whose omega sum cancels by up
-//    to ~300x at high degeneracy, are accumulated in FP32-pair (double-float) arithmetic.
+//    of the small remainder are multiplied. The l = 1 projection of the kernel, whose omega sum
+//    cancels by up to ~760x at high degeneracy, is accumulated in FP32-pair (double-float)
+//    arithmetic; the tangents' l = 1 sums in FP32.
 #pragma once
 #include "vx_internal.h"
 
@@ -424,10 +425,10 @@ __global__ void __launch_bounds__(VX_TPB_MIXED, MINB) k_pair_mixed(const __grid_
                     node_loop<NE, ADJ, true>(s_nodes, C.n_e, B, 0.f, Pp, Bq, Bl, Pq, Pl, h, Em, zs.c1, mo, ta, tp, et);
                     const Coef cf = make_coef<true>(kp, km, k0, kpl, kml, k0l, C.t_hi[m], C.t_lo[m]);
                     project<true>(PO, mo, cf);
-                    if (ADJ) {
-                        project<true>(PTa, ta, cf);
-                        project<true>(PTp, tp, cf);
-                        project<true>(PEt, et, cf);
+                    if (ADJ) {  // tangent l = 1 sums: FP32 (checked against their absolute-value bound)
+                        project<false>(PTa, ta, cf);
+                        project<false>(PTp, tp, cf);
+                        project<false>(PEt, et, cf);
                     }
                 }
             }

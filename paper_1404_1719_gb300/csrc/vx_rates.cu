@@ -200,7 +200,7 @@ vx_status vx_rates_create(const vx_config *cfg, vx_rates **out) {
         h->w[i] = h->eps[i] * h->eps[i] * (hi - lo);
     }
     h->cfg.weights = h->w.data();
-    if (h->cfg.eta_fp64 == 0.0) h->cfg.eta_fp64 = 10.0;
+    if (h->cfg.eta_fp64 == 0.0) h->cfg.eta_fp64 = 20.0;
 
     vx::Common &C = h->common;
     C.N = N; C.n_mu = nmu; C.n_e = ne; C.S = S;
@@ -754,7 +754,7 @@ static void noalloc_params(const vx_config *cfg, vx::Launch &L, NoallocTab &T) {
     C.N = N; C.n_mu = nmu; C.n_e = ne; C.S = S;
     C.npair = N * (N + 1) / 2;
     C.ms = 1;
-    C.g2 = cfg->g2; C.norm = cfg->norm; C.eta_sw = cfg->eta_fp64 == 0.0 ? 10.0 : cfg->eta_fp64;
+    C.g2 = cfg->g2; C.norm = cfg->norm; C.eta_sw = cfg->eta_fp64 == 0.0 ? 20.0 : cfg->eta_fp64;
     const double *eps = cfg->eps;
     for (int i = 0; i < N; ++i) {
         double w;

@@ -62,7 +62,7 @@ def test_jacobian_against_oracle(workload, rays):
 
 def test_jacobian_edge_states():
     eps = vx_inputs.energy_centres(11, 1.0, 300.0)
-    rows = [(T, eta) for T in (0.5, 4.0, 35.0) for eta in (-30.0, -5.0, 0.0, 6.0, 10.5, 40.0, 75.0)]
+    rows = [(T, eta) for T in (0.5, 4.0, 35.0) for eta in (-30.0, -5.0, 0.0, 6.0, 19.9, 20.1, 40.0, 75.0)]
     st, J, H = vx_inputs.random_zones(len(rows), 8, n_bins=11)
     st[:, 0] = [a for a, _ in rows]
     st[:, 1] = [c for _, c in rows]

@@ -83,7 +83,7 @@ def _edge_batch():
     eps = vx_inputs.energy_centres(13, 1.0, 300.0)
     rows = []
     for T in (0.3, 1.0, 7.0, 40.0):
-        for eta in (-45.0, -12.0, -3.0, 0.0, 2.5, 9.999, 10.001, 25.0, 60.0, 79.5):
+        for eta in (-45.0, -12.0, -3.0, 0.0, 2.5, 9.999, 19.999, 20.001, 25.0, 60.0, 79.5):
             rows.append((T, eta))
     st, J, H = vx_inputs.random_zones(len(rows), 21, n_bins=13)
     st[:, 0] = [r[0] for r in rows]
