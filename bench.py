@@ -39,6 +39,12 @@ def entries(Z, N):
     return Z * N * N * 2
 
 
+# DRAM bytes (read + write) per zone of the forward + tangent kernel, from one ncu capture of the
+# 200-ray case of this workload (dram__bytes_read.sum + dram__bytes_write.sum = 676.6 MB for
+# 80,000 zones); scaled to a launch by the zone count. Must be re-measured when the kernel changes.
+TRAFFIC_BYTES_PER_ZONE = 8458
+
+
 def algorithmic_flops_per_node(adj: bool) -> int:
     """FP32 operations the method needs per (zone, unordered bin pair, omega, E) node, counting an
     FMA as 2 and an exp or reciprocal as 1: forward 16, tangents 36 more."""
@@ -270,7 +276,8 @@ def run_ours(args):
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": args.steps,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": TRAFFIC_BYTES_PER_ZONE * Z,
+                         "traffic_note": "ncu DRAM read+write of an 80,000-zone capture, scaled by zone count",
                          "peak_note": f"FP32 {nsm} SMs x 128 FMA x 2 x {mhz:.0f} MHz (median SM clock in the run)",
                          "kernel": f"k_pair_mixed<{b['n_e']}, tangents, {minb} CTAs/SM>"},
             "autotune": tune,
