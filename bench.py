@@ -51,6 +51,26 @@ def algorithmic_flops_per_node(adj: bool) -> int:
     return 52 if adj else 16
 
 
+def rank_batch(rank: int, rays=None) -> dict:
+    """Each rank evaluates its own independent copy of the workload (seed = rank): weak scaling,
+    no data exchanged between ranks."""
+    return vx_inputs.make_batch(WORKLOAD, seed=rank, rays=rays)
+
+
+def max_over_ranks(ms_local: float, world: int, dist=None, device="cpu") -> float:
+    """Step time of the whole job: the slowest rank's (all_reduce MAX; identity on one rank)."""
+    import torch
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(entries_per_rank: int, world: int, ms: float) -> float:
+    """Whole-job throughput: all ranks' entries over the slowest rank's step time."""
+    return entries_per_rank * world / (ms / 1000.0)
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms while active."""
 
@@ -160,7 +180,7 @@ def run_ours(args):
     from paper_1404_1719_gb300 import PairRates, _build
     _build.build()
 
-    b = vx_inputs.make_batch(WORKLOAD, seed=rank, rays=None if args.rays is None else range(args.rays))
+    b = rank_batch(rank, rays=None if args.rays is None else range(args.rays))
     # the autotuner's choice is reported from its cache file
     tune_file = os.environ.get("VX_AUTOTUNE_CACHE") or os.path.join(
         os.environ.get("TMPDIR", "/tmp"), f"vx_bench_tune_{os.getpid()}.json")
@@ -196,10 +216,7 @@ def run_ours(args):
     ms_local = e0.elapsed_time(e1) / args.steps
     if world > 1:
         dist.barrier()
-    t = torch.tensor([ms_local], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms = float(t.item())
+    ms = max_over_ranks(ms_local, world, dist, dev)
     ok = rates.check()
 
     # ---- end-to-end: pinned host inputs -> device -> fused pass -> host rates + Jacobian
@@ -221,17 +238,13 @@ def run_ours(args):
     a1.record(stream)
     torch.cuda.synchronize()
     ms_e2e = a0.elapsed_time(a1) / e2e_steps
-    te = torch.tensor([ms_e2e], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    ms_e2e = float(te.item())
+    ms_e2e = max_over_ranks(ms_e2e, world, dist, dev)
     h2d = sum(v.numel() * v.element_size() for v in host.values())
     d2h = sum(v.numel() * v.element_size() for v in out.values()) + jac.numel() * jac.element_size()
 
     line = None
     if rank == 0:
-        ent = entries(Z, N) * world
-        value = ent / (ms / 1000)
+        value = job_rate(entries(Z, N), world, ms)
         # roofline of the one kernel of the step (FP32 pipe peak from the unit counts and clock)
         c = clk.summary()
         nsm = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -272,7 +285,7 @@ def run_ours(args):
                        "quadrature": f"{b['n_mu']}x{b['n_e']}", "species": S,
                        "l2": "inputs larger than L2 (J, H: %.2f GB)" % (2 * b["J"].nbytes / 1e9),
                        "graph": True, "autotune": True},
-            "e2e": {"value": entries(Z, N) * world / (ms_e2e / 1000), "unit": UNIT,
+            "e2e": {"value": job_rate(entries(Z, N), world, ms_e2e), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": args.steps,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",

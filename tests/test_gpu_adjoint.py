@@ -117,3 +117,41 @@ def test_full_size_forward_adjoint_sampled():
     for k in KEYS:
         assert worst(res[k][torch.as_tensor(pick, device="cuda")].cpu().numpy(), ref[k], mag=mg[k]) <= 1e-5
     r.close()
+
+
+def test_maximum_sizes_forward_and_tangents():
+    """31 bins (496 bin pairs) with 64 x 64 quadrature: the largest grid and node counts."""
+    eps = vx_inputs.energy_centres(31, 0.5, 400.0)
+    st, J, H = vx_inputs.random_zones(9, 31, n_bins=31, T_range=(0.8, 35.0), eta_range=(-5.0, 45.0))
+    b = dict(eps=eps, n_mu=64, n_e=64, species=np.array([0, 1, 2], np.int32), state=st, J=J, H=H)
+    r = rates_for(b)
+    res = r.adjoint(dev(st), dev(J), dev(H), jacobian=True, forward=True)
+    assert r.check()
+    ref = oracle.evaluate(eps, 64, 64, b["species"], st, J, H, jac=True, mag=True)
+    check_jac(res["jac"].cpu().numpy(), ref)
+    mg = magnitudes(ref)
+    for k in KEYS:
+        assert worst(res[k].cpu().numpy(), ref[k], mag=mg[k]) <= 1e-5, k
+    r.close()
+
+
+def test_3d_scale_workload_full_size_sampled():
+    """16200 rays x 400 zones (6.48 M zones), 16 x 48 quadrature, eta_e up to ~63: forward and
+    Jacobian of every zone in one pass; sampled zones against the oracle."""
+    b = vx_inputs.make_batch(5)
+    Z = b["state"].shape[0]
+    r = rates_for(b, graph=True)
+    st, J, H = dev(b["state"]), dev(b["J"]), dev(b["H"])
+    res = r.adjoint(st, J, H, jacobian=True, forward=True, ray_offsets=b["ray_offsets"])
+    assert r.check()
+    rng = np.random.default_rng(5)
+    pick = np.unique(np.concatenate([rng.integers(0, Z, 14), [0, 1, 399, Z - 1]]))
+    ref = oracle.evaluate(b["eps"], b["n_mu"], b["n_e"], b["species"], b["state"][pick], b["J"][pick],
+                          b["H"][pick], jac=True, mag=True)
+    ix = torch.as_tensor(pick, device="cuda")
+    check_jac(res["jac"][ix].cpu().numpy(), ref)
+    mg = magnitudes(ref)
+    for k in KEYS:
+        assert worst(res[k][ix].cpu().numpy(), ref[k], mag=mg[k]) <= 1e-5, k
+    assert torch.isfinite(res["jac"]).all() and torch.isfinite(res["j0"]).all()
+    r.close()
