@@ -51,10 +51,10 @@ def algorithmic_flops_per_node(adj: bool) -> int:
     return 52 if adj else 16
 
 
-def rank_batch(rank: int, rays=None) -> dict:
+def rank_batch(rank: int, rays=None, workload: int = WORKLOAD) -> dict:
     """Each rank evaluates its own independent copy of the workload (seed = rank): weak scaling,
     no data exchanged between ranks."""
-    return vx_inputs.make_batch(WORKLOAD, seed=rank, rays=rays)
+    return vx_inputs.make_batch(workload, seed=rank, rays=rays)
 
 
 def max_over_ranks(ms_local: float, world: int, dist=None, device="cpu") -> float:
@@ -127,13 +127,14 @@ def oracle_sample_rate(b, n_zones: int, jac: bool):
     return entries(n_zones, len(b["eps"])) / dt, out["threads"], dt
 
 
-def cpu_baseline(target_s: float = 15.0):
-    b = vx_inputs.make_batch(WORKLOAD, rays=[0, 1, 2, 3])
-    rate, thr, dt = oracle_sample_rate(b, 16, True)
+def cpu_baseline(target_s: float = 15.0, workload: int = WORKLOAD, jac: bool = True):
+    b = vx_inputs.make_batch(workload, rays=[0, 1, 2, 3])
+    rate, thr, dt = oracle_sample_rate(b, 16, jac)
     n = int(min(len(b["state"]), max(16, 16 * target_s / max(dt, 1e-3))))
-    rate, thr, dt = oracle_sample_rate(b, n, True)
+    rate, thr, dt = oracle_sample_rate(b, n, jac)
+    what = "forward + Jacobian" if jac else "forward"
     return {"value": rate, "unit": UNIT, "cores": thr, "kind": "oracle",
-            "sample": f"first {n} zones of workload {WORKLOAD} (rays 0-3), forward + Jacobian, FP64, {dt:.1f} s"}
+            "sample": f"first {n} zones of workload {workload} (rays 0-3), {what}, FP64, {dt:.1f} s"}
 
 
 def run_reference(args):
@@ -180,7 +181,8 @@ def run_ours(args):
     from paper_1404_1719_gb300 import PairRates, _build
     _build.build()
 
-    b = rank_batch(rank, rays=None if args.rays is None else range(args.rays))
+    b = rank_batch(rank, rays=None if args.rays is None else range(args.rays), workload=args.workload)
+    fwd_only = args.mode == "fwd"
     # the autotuner's choice is reported from its cache file
     tune_file = os.environ.get("VX_AUTOTUNE_CACHE") or os.path.join(
         os.environ.get("TMPDIR", "/tmp"), f"vx_bench_tune_{os.getpid()}.json")
@@ -191,13 +193,16 @@ def run_ours(args):
     rates = PairRates(b["eps"], b["n_mu"], b["n_e"], species=b["species"], graph=True, autotune=True)
     stream = torch.cuda.current_stream()
     out = {k: torch.empty((Z, S, N), dtype=torch.float64, device=dev) for k in ("j0", "chi0", "j1", "chi1")}
-    jac = torch.empty((Z, S, N, 4, 3), dtype=torch.float64, device=dev)
+    jac = torch.empty((Z, S, N, 4, 3) if args.mode != "fwd" else (1,), dtype=torch.float64, device=dev)
     from paper_1404_1719_gb300 import capi
     bt = rates._batch(d["state"], d["J"], d["H"], b["ray_offsets"])
     fwd = capi.vx_out(*(out[k].data_ptr() for k in ("j0", "chi0", "j1", "chi1")), None)
 
     def step():
-        capi.vx_rates_adjoint(rates.handle, bt, None, jac.data_ptr(), None, fwd, stream.cuda_stream)
+        if fwd_only:
+            capi.vx_rates_eval(rates.handle, bt, fwd, stream.cuda_stream)
+        else:
+            capi.vx_rates_adjoint(rates.handle, bt, None, jac.data_ptr(), None, fwd, stream.cuda_stream)
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -234,13 +239,14 @@ def run_ours(args):
         step()
         for k in out:
             h_out[k].copy_(out[k], non_blocking=True)
-        h_jac.copy_(jac, non_blocking=True)
+        if not fwd_only:
+            h_jac.copy_(jac, non_blocking=True)
     a1.record(stream)
     torch.cuda.synchronize()
     ms_e2e = a0.elapsed_time(a1) / e2e_steps
     ms_e2e = max_over_ranks(ms_e2e, world, dist, dev)
     h2d = sum(v.numel() * v.element_size() for v in host.values())
-    d2h = sum(v.numel() * v.element_size() for v in out.values()) + jac.numel() * jac.element_size()
+    d2h = sum(v.numel() * v.element_size() for v in out.values()) + (0 if fwd_only else jac.numel() * jac.element_size())
 
     line = None
     if rank == 0:
@@ -252,7 +258,7 @@ def run_ours(args):
         peak = nsm * 128 * 2 * mhz * 1e6 / 1e12
         npair = N * (N + 1) // 2
         nodes = Z * npair * b["n_mu"] * b["n_e"]
-        achieved = nodes * algorithmic_flops_per_node(True) / (ms_local / 1000) / 1e12
+        achieved = nodes * algorithmic_flops_per_node(not fwd_only) / (ms_local / 1000) / 1e12
         # FP64 forward-only comparison on a sample of the same workload
         sub = min(48 * 400, Z)
         r64 = PairRates(b["eps"], b["n_mu"], b["n_e"], species=b["species"], precision="fp64")
@@ -274,12 +280,14 @@ def run_ours(args):
                         if f"N={N},n_mu={b['n_mu']},n_e={b['n_e']}," in k}
         except (OSError, ValueError, IndexError):
             pass
-        minb = tune.get("tangents", {}).get("minb", 3)
+        kind = "forward" if fwd_only else "tangents"
+        minb = tune.get(kind, {}).get("minb", 2)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": vx_inputs.WORKLOADS[WORKLOAD]["name"] + " forward+jacobian (mixed)"
+            "config": {"workload": vx_inputs.WORKLOADS[args.workload]["name"]
+                       + (" forward (mixed)" if fwd_only else " forward+jacobian (mixed)")
                        + ("" if args.rays is None else f" [first {args.rays} rays]"),
                        "zones": Z, "rays": int(len(b["ray_offsets"]) - 1), "bins": N,
                        "quadrature": f"{b['n_mu']}x{b['n_e']}", "species": S,
@@ -289,10 +297,11 @@ def run_ours(args):
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": args.steps,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": TRAFFIC_BYTES_PER_ZONE * Z,
+                         "frac": achieved / peak,
+                         "traffic": TRAFFIC_BYTES_PER_ZONE * Z if (args.workload == WORKLOAD and not fwd_only) else None,
                          "traffic_note": "ncu DRAM read+write of an 80,000-zone capture, scaled by zone count",
                          "peak_note": f"FP32 {nsm} SMs x 128 FMA x 2 x {mhz:.0f} MHz (median SM clock in the run)",
-                         "kernel": f"k_pair_mixed<{b['n_e']}, tangents, {minb} CTAs/SM>"},
+                         "kernel": f"k_pair_mixed<{b['n_e']}, {kind}, {minb} CTAs/SM>"},
             "autotune": tune,
             "fp64_fwd": {"value": v64, "unit": UNIT, "sample": f"first {sub} zones, plain FP64 forward only",
                          "ratio_mixed_fwd_adj_over_fp64_fwd": value / world / v64},
@@ -300,7 +309,7 @@ def run_ours(args):
             "numeric_ok": bool(ok),
         }
         if not args.no_cpu:
-            line["cpu_baseline"] = cpu_baseline()
+            line["cpu_baseline"] = cpu_baseline(workload=args.workload, jac=not fwd_only)
         print(json.dumps(line))
     if world > 1:
         dist.barrier()
@@ -316,6 +325,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU-baseline leg")
+    ap.add_argument("--workload", type=int, default=WORKLOAD, choices=sorted(vx_inputs.WORKLOADS),
+                    help="synthetic workload (default 4: 4096 rays x 400 zones)")
+    ap.add_argument("--mode", choices=["fwd+jac", "fwd"], default="fwd+jac",
+                    help="step = forward + Jacobian pass (default) or forward rates only")
     ap.add_argument("--rays", type=int, default=None,
                     help="use only the first R rays of the workload (small cases for profiling)")
     args = ap.parse_args()
