@@ -24,7 +24,8 @@
 // Blocking factor (1 - f_e)(1 - f_ebar) = 1 / ((1 + e1)(1 + e2)), e1 = exp(-x_e), e2 = exp(-x_p),
 // x_e = (E - mu)/T, x_p = (Ebar + mu)/T, evaluated with MUFU ex2 / rcp. The zone is mapped to
 // eta >= 0 (eta -> -eta exchanges e- and e+, i.e. tau -> -tau, i.e. M+ <-> M-).
-//  * fast path (|eta| <= eta_sw): x arguments anchored at E- in FP32, two reciprocals per rcp.
+//  * fast path (|eta| <= eta_sw): x arguments anchored at E- in FP32; nodes taken in mirror
+//    pairs tau, -tau, which share one ex2 per node and (forward) one reciprocal per pair.
 //  * degenerate path (|eta| > eta_sw): the electron argument B (1 + tau) + P is formed exactly:
 //    B, P and 1 + tau are split into a high part on a power-of-two grid (chosen per zone so that
 //    fma(B_hi, u_hi, P_hi) is exact in FP32) and a remainder, and exp2 of the exact high part and
@@ -102,6 +103,7 @@ struct ZoneSh {
     float iB, iP;      // their inverses
     float sc;          // degenerate path: blocking factor carried as O 2^sc (keeps the deepest-
     float c1;          //   blocked nodes of the zone far from the FP32 underflow); c1 = 2^-sc
+    float K;           // e^{-2|eta|} (fast path: e2 on a node from e1 on its mirror node)
     double unsc;       // 2^-sc, applied in FP64 to every result of the zone
     int sv;            // production vectors carried as v 2^sv (degenerate zones); the two scales
                        //   share the FP32 exponent headroom so no product can overflow
@@ -125,31 +127,39 @@ struct NodeSm {
 // GTa = O (f_e E + f_ebar Ebar), GTp = O ((1-f_e) E + (1-f_ebar) Ebar), GEt = O (f_ebar - f_e).
 // With the zone scale (degenerate path) e1 and the "1" of 1 + e1 carry the factor 2^-sc, so
 // r = 2^sc O; c1 = 2^-sc recovers 1 - f_e, while f_e, f_ebar and 1 - f_ebar need no correction.
-// The loop is unrolled 16 nodes deep (the instruction footprint stays cache resident); the
-// forward fast path, which is MUFU-bound, turns two reciprocals into one.
+// The loop is unrolled 16 nodes deep (the instruction footprint stays cache resident).
+//
+// Fast path, unrolled instantiations (even n_e): the Gauss-Legendre nodes come in exact mirror
+// pairs tau, -tau (records k and n_e-1-k hold the same values with u <-> v and
+// w(1+tau)^2 <-> w(1-tau)^2). On the mirror node the electron argument is the positron argument
+// of tau less 2|eta|, so e2(tau) = e1(-tau) K and e2(-tau) = e1(tau) K with K = e^{-2|eta|}: one
+// ex2 and half a record read per node, and (MPAIR) one reciprocal per node pair.
 template <int NE, bool ADJ, bool DEG>
 __device__ __forceinline__ void node_loop(const NodeSm *__restrict__ nd, int ne, float B, float Pe,
                                           float Pp, float Bq, float Bl, float Pq, float Pl, float h,
-                                          float Em, float c1, Mom &mo, Mom &ta, Mom &tp, Mom &et) {
-    constexpr bool PAIR = !DEG && (!ADJ || VX_ADJ_PAIR);
+                                          float Em, float c1, float K, Mom &mo, Mom &ta, Mom &tp,
+                                          Mom &et) {
+    constexpr bool MIRROR = !DEG && NE > 0;
+    constexpr bool MPAIR = !ADJ || VX_ADJ_PAIR;
     constexpr int U = 16;
+    // tangent integrands of one node, accumulated with its basis weights (cp, cm, c0)
+    auto tang = [&](float cp, float cm, float c0, float e1, float e2, float t, float r, float E, float Eb) {
+        float qv = fmaf(e2, r, r);      // (1 + e2) r
+        float se = DEG ? c1 * qv : qv;  // 1 - f_e
+        float sp = t * r;               // 1 - f_ebar
+        float fe = e1 * qv, fp = e2 * sp;
+        float ga = fmaf(fe, E, fp * Eb) * r;
+        float gp = fmaf(se, E, sp * Eb) * r;
+        float ge = (fp - fe) * r;
+        ta.p = fmaf(cp, ga, ta.p); ta.m = fmaf(cm, ga, ta.m); ta.z = fmaf(c0, ga, ta.z);
+        tp.p = fmaf(cp, gp, tp.p); tp.m = fmaf(cm, gp, tp.m); tp.z = fmaf(c0, gp, tp.z);
+        et.p = fmaf(cp, ge, et.p); et.m = fmaf(cm, ge, et.m); et.z = fmaf(c0, ge, et.z);
+    };
     auto accum = [&](const NodeSm &q, float e1, float e2, float t, float r) {
         mo.p = fmaf(q.a.z, r, mo.p);
         mo.m = fmaf(q.a.w, r, mo.m);
         mo.z = fmaf(q.b.x, r, mo.z);
-        if (ADJ) {
-            float qv = fmaf(e2, r, r);  // (1 + e2) r
-            float se = DEG ? c1 * qv : qv;  // 1 - f_e
-            float sp = t * r;               // 1 - f_ebar
-            float fe = e1 * qv, fp = e2 * sp;
-            float E = fmaf(h, q.a.x, Em), Eb = fmaf(h, q.a.y, Em);
-            float ga = fmaf(fe, E, fp * Eb) * r;
-            float gp = fmaf(se, E, sp * Eb) * r;
-            float ge = (fp - fe) * r;
-            ta.p = fmaf(q.a.z, ga, ta.p); ta.m = fmaf(q.a.w, ga, ta.m); ta.z = fmaf(q.b.x, ga, ta.z);
-            tp.p = fmaf(q.a.z, gp, tp.p); tp.m = fmaf(q.a.w, gp, tp.m); tp.z = fmaf(q.b.x, gp, tp.z);
-            et.p = fmaf(q.a.z, ge, et.p); et.m = fmaf(q.a.w, ge, et.m); et.z = fmaf(q.b.x, ge, et.z);
-        }
+        if (ADJ) tang(q.a.z, q.a.w, q.b.x, e1, e2, t, r, fmaf(h, q.a.x, Em), fmaf(h, q.a.y, Em));
     };
     auto factors = [&](const NodeSm &q, float &e1, float &e2, float &t) {
         if (!DEG) {
@@ -164,28 +174,46 @@ __device__ __forceinline__ void node_loop(const NodeSm *__restrict__ nd, int ne,
             t = c1 + e1;
         }
     };
-    if (NE > 0) {
+    if (MIRROR) {
         static_assert(NE % U == 0 || NE == 0, "unrolled instantiations need a multiple of the unroll depth");
+#pragma unroll 1
+        for (int k0 = 0; k0 < NE / 2; k0 += U / 2) {
+#pragma unroll
+            for (int kk = 0; kk < U / 2; ++kk) {
+                const NodeSm q = nd[k0 + kk];
+                const float ea = ex2a(-fmaf(B, q.a.x, Pe));  // e1(tau)
+                const float eb = ex2a(-fmaf(B, q.a.y, Pe));  // e1(-tau)
+                const float fa = eb * K, fb = ea * K;        // e2(tau), e2(-tau)
+                const float ta_ = 1.f + ea, tb_ = 1.f + eb;
+                const float da = fmaf(ta_, fa, ta_), db = fmaf(tb_, fb, tb_);
+                float ra, rb;
+                if (MPAIR) {
+                    // |eta| <= eta_sw <= 40: d <= 2 (1 + e^40), so the product stays finite
+                    const float R = rcpa(da * db);
+                    ra = R * db;
+                    rb = R * da;
+                } else {
+                    ra = rcpa(da);
+                    rb = rcpa(db);
+                }
+                mo.p = fmaf(q.a.z, ra, mo.p); mo.m = fmaf(q.a.w, ra, mo.m); mo.z = fmaf(q.b.x, ra, mo.z);
+                mo.p = fmaf(q.a.w, rb, mo.p); mo.m = fmaf(q.a.z, rb, mo.m); mo.z = fmaf(q.b.x, rb, mo.z);
+                if (ADJ) {
+                    const float Ea = fmaf(h, q.a.x, Em), Eba = fmaf(h, q.a.y, Em);  // E(tau) = Ebar(-tau)
+                    tang(q.a.z, q.a.w, q.b.x, ea, fa, ta_, ra, Ea, Eba);
+                    tang(q.a.w, q.a.z, q.b.x, eb, fb, tb_, rb, Eba, Ea);
+                }
+            }
+        }
+    } else if (NE > 0) {
 #pragma unroll 1
         for (int k0 = 0; k0 < NE; k0 += U) {
 #pragma unroll
-            for (int kk = 0; kk < U; kk += PAIR ? 2 : 1) {
-                const NodeSm qa = nd[k0 + kk];
-                float e1a, e2a, ta_;
-                factors(qa, e1a, e2a, ta_);
-                float da = fmaf(ta_, e2a, ta_);
-                if (PAIR) {
-                    // |eta| <= eta_sw: d <= 2 (1 + e^{eta_sw}), so a product of two stays finite
-                    const NodeSm qb = nd[k0 + kk + 1];
-                    float e1b, e2b, tb_;
-                    factors(qb, e1b, e2b, tb_);
-                    float db = fmaf(tb_, e2b, tb_);
-                    float R = rcpa(da * db);
-                    accum(qa, e1a, e2a, ta_, R * db);
-                    accum(qb, e1b, e2b, tb_, R * da);
-                } else {
-                    accum(qa, e1a, e2a, ta_, rcpa(da));
-                }
+            for (int kk = 0; kk < U; ++kk) {
+                const NodeSm q = nd[k0 + kk];
+                float e1, e2, t;
+                factors(q, e1, e2, t);
+                accum(q, e1, e2, t, rcpa(fmaf(t, e2, t)));
             }
         }
     } else {
@@ -300,6 +328,7 @@ __global__ void __launch_bounds__(VX_TPB_MIXED, MINB) k_pair_mixed(const __grid_
                 zs.el_l = (float)(el - (double)zs.el_h);
                 zs.neg = eta < 0.0;
                 zs.deg = ae > C.eta_sw;
+                zs.K = (float)exp(-2.0 * ae);
                 // zone scales: with O in [e^-|eta|, 1] and production vectors whose relevant
                 // entries reach e^-|eta| times their row's largest, lift both off the FP32 floor
                 int sc = zs.deg ? (int)floor(0.3 * el) : 0;
@@ -397,7 +426,7 @@ __global__ void __launch_bounds__(VX_TPB_MIXED, MINB) k_pair_mixed(const __grid_
                 const float Pp = fmaf(Em, il_h, el_h);
                 if (!deg) {
                     const float Pe = fmaf(Em, il_h, -el_h);
-                    node_loop<NE, ADJ, false>(s_nodes, C.n_e, B, Pe, Pp, 0.f, 0.f, 0.f, 0.f, h, Em, 1.f, mo, ta, tp, et);
+                    node_loop<NE, ADJ, false>(s_nodes, C.n_e, B, Pe, Pp, 0.f, 0.f, 0.f, 0.f, h, Em, 1.f, zs.K, mo, ta, tp, et);
                     const Coef cf = make_coef<false>(kp, km, k0, kpl, kml, k0l, C.t_hi[m], C.t_lo[m]);
                     project<false>(PO, mo, cf);
                     if (ADJ) {
@@ -422,7 +451,7 @@ __global__ void __launch_bounds__(VX_TPB_MIXED, MINB) k_pair_mixed(const __grid_
                     float Pq = __fmul_rn(rintf(__fmul_rn(s, zs.sP)), zs.iP);
                     float Pl = __fadd_rn(__fsub_rn(s, Pq), slo);
                     Pq = __fadd_rn(Pq, zs.sc);  // exact: an integer on the same grid
-                    node_loop<NE, ADJ, true>(s_nodes, C.n_e, B, 0.f, Pp, Bq, Bl, Pq, Pl, h, Em, zs.c1, mo, ta, tp, et);
+                    node_loop<NE, ADJ, true>(s_nodes, C.n_e, B, 0.f, Pp, Bq, Bl, Pq, Pl, h, Em, zs.c1, 0.f, mo, ta, tp, et);
                     const Coef cf = make_coef<true>(kp, km, k0, kpl, kml, k0l, C.t_hi[m], C.t_lo[m]);
                     project<true>(PO, mo, cf);
                     if (ADJ) {  // tangent l = 1 sums: FP32 (checked against their absolute-value bound)

@@ -56,7 +56,8 @@ def test_jacobian_against_oracle(workload, rays):
     mg = magnitudes(ref)
     for k in KEYS:
         assert worst(res[k].cpu().numpy(), ref[k], mag=mg[k]) <= 1e-5
-        assert worst(res[k].cpu().numpy(), fw[k].cpu().numpy()) <= 2e-6  # two FP32 instantiations
+        # two FP32 instantiations: l = 1 sums that cancel differ at rounding times their absolute sum
+        assert worst(res[k].cpu().numpy(), fw[k].cpu().numpy(), mag=mg[k]) <= 2e-6
     r.close()
 
 
