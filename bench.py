@@ -40,9 +40,9 @@ def entries(Z, N):
 
 
 # DRAM bytes (read + write) per zone of the forward + tangent kernel, from one ncu capture of the
-# 200-ray case of this workload (dram__bytes_read.sum + dram__bytes_write.sum = 676.6 MB for
-# 80,000 zones); scaled to a launch by the zone count. Must be re-measured when the kernel changes.
-TRAFFIC_BYTES_PER_ZONE = 8458
+# 200-ray case of this workload; scaled to a launch by the zone count. None until the current
+# kernel has been captured (a figure taken on an earlier version of the kernel is not reported).
+TRAFFIC_BYTES_PER_ZONE = None
 
 
 def algorithmic_flops_per_node(adj: bool) -> int:
@@ -298,7 +298,8 @@ def run_ours(args):
             "gpu_launches": args.steps,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak,
-                         "traffic": TRAFFIC_BYTES_PER_ZONE * Z if (args.workload == WORKLOAD and not fwd_only) else None,
+                         "traffic": (TRAFFIC_BYTES_PER_ZONE * Z if (TRAFFIC_BYTES_PER_ZONE and args.workload == WORKLOAD
+                                                                    and not fwd_only) else None),
                          "traffic_note": "ncu DRAM read+write of an 80,000-zone capture, scaled by zone count",
                          "peak_note": f"FP32 {nsm} SMs x 128 FMA x 2 x {mhz:.0f} MHz (median SM clock in the run)",
                          "kernel": f"k_pair_mixed<{b['n_e']}, {kind}, {minb} CTAs/SM>"},

@@ -39,6 +39,10 @@
 #ifndef VX_ADJ_PAIR
 #define VX_ADJ_PAIR 0
 #endif
+// Degenerate path: e2 from the mirror node's e1 (saves one ex2 per node, costs registers).
+#ifndef VX_DEG_MIRROR
+#define VX_DEG_MIRROR 0
+#endif
 
 namespace vx {
 
@@ -103,7 +107,8 @@ struct ZoneSh {
     float iB, iP;      // their inverses
     float sc;          // degenerate path: blocking factor carried as O 2^sc (keeps the deepest-
     float c1;          //   blocked nodes of the zone far from the FP32 underflow); c1 = 2^-sc
-    float K;           // e^{-2|eta|} (fast path: e2 on a node from e1 on its mirror node)
+    float K, K2;       // e2 on a node from e1 on its mirror node: fast path K = e^{-2|eta|};
+                       //   degenerate path K = 2^sc e^{-|eta|}, K2 = e^{-|eta|}
     double unsc;       // 2^-sc, applied in FP64 to every result of the zone
     int sv;            // production vectors carried as v 2^sv (degenerate zones); the two scales
                        //   share the FP32 exponent headroom so no product can overflow
@@ -137,20 +142,33 @@ struct NodeSm {
 template <int NE, bool ADJ, bool DEG>
 __device__ __forceinline__ void node_loop(const NodeSm *__restrict__ nd, int ne, float B, float Pe,
                                           float Pp, float Bq, float Bl, float Pq, float Pl, float h,
-                                          float Em, float c1, float K, Mom &mo, Mom &ta, Mom &tp,
-                                          Mom &et) {
+                                          float Em, float c1, float K, float K2, Mom &mo, Mom &ta,
+                                          Mom &tp, Mom &et) {
     constexpr bool MIRROR = !DEG && NE > 0;
     constexpr bool MPAIR = !ADJ || VX_ADJ_PAIR;
     constexpr int U = 16;
     // tangent integrands of one node, accumulated with its basis weights (cp, cm, c0)
     auto tang = [&](float cp, float cm, float c0, float e1, float e2, float t, float r, float E, float Eb) {
-        float qv = fmaf(e2, r, r);      // (1 + e2) r
-        float se = DEG ? c1 * qv : qv;  // 1 - f_e
-        float sp = t * r;               // 1 - f_ebar
-        float fe = e1 * qv, fp = e2 * sp;
-        float ga = fmaf(fe, E, fp * Eb) * r;
-        float gp = fmaf(se, E, sp * Eb) * r;
-        float ge = (fp - fe) * r;
+        float ga, gp, ge;
+        if (!DEG) {
+            // r >= 1 / (2 (1 + e^40)) here, so r2 = r^2 stays normal: (1 - f_e) r = (1 + e2) r2,
+            // (1 - f_ebar) r = t r2, f_e r = e1 (1 + e2) r2, f_ebar r = e2 t r2
+            const float r2 = r * r;
+            const float s0 = fmaf(e2, r2, r2), p = t * r2;
+            const float a1 = e1 * s0, a2 = e2 * p;
+            ga = fmaf(a1, E, a2 * Eb);
+            gp = fmaf(s0, E, p * Eb);
+            ge = a2 - a1;
+        } else {
+            // r = 2^sc O can lie near the FP32 floor: keep products with r to first order
+            const float qv = fmaf(e2, r, r);  // (1 + e2) r
+            const float se = c1 * qv;         // 1 - f_e
+            const float sp = t * r;           // 1 - f_ebar
+            const float fe = e1 * qv, fp = e2 * sp;
+            ga = fmaf(fe, E, fp * Eb) * r;
+            gp = fmaf(se, E, sp * Eb) * r;
+            ge = (fp - fe) * r;
+        }
         ta.p = fmaf(cp, ga, ta.p); ta.m = fmaf(cm, ga, ta.m); ta.z = fmaf(c0, ga, ta.z);
         tp.p = fmaf(cp, gp, tp.p); tp.m = fmaf(cm, gp, tp.m); tp.z = fmaf(c0, gp, tp.z);
         et.p = fmaf(cp, ge, et.p); et.m = fmaf(cm, ge, et.m); et.z = fmaf(c0, ge, et.z);
@@ -203,6 +221,24 @@ __device__ __forceinline__ void node_loop(const NodeSm *__restrict__ nd, int ne,
                     tang(q.a.z, q.a.w, q.b.x, ea, fa, ta_, ra, Ea, Eba);
                     tang(q.a.w, q.a.z, q.b.x, eb, fb, tb_, rb, Eba, Ea);
                 }
+            }
+        }
+    } else if (NE > 0 && VX_DEG_MIRROR) {
+        // degenerate path: e1 from the exact split on both nodes of a mirror pair, and
+        // e2(tau) = e1(-tau) 2^sc e^{-2|eta|} as (e1(-tau) K) K2, K = 2^sc e^{-|eta|}, K2 = e^{-|eta|}
+        // (the intermediate is e^{-Ebar(tau)/T} <= 1 and both factors are normal for |eta| <= 80)
+        static_assert(NE % U == 0 || NE == 0, "unrolled instantiations need a multiple of the unroll depth");
+#pragma unroll 1
+        for (int k0 = 0; k0 < NE / 2; k0 += U / 2) {
+#pragma unroll
+            for (int kk = 0; kk < U / 2; ++kk) {
+                const NodeSm qa = nd[k0 + kk], qb = nd[NE - 1 - k0 - kk];
+                const float ea = ex2a(-fmaf(Bq, qa.b.y, Pq)) * ex2a(-fmaf(Bq, qa.b.z, fmaf(Bl, qa.a.x, Pl)));
+                const float eb = ex2a(-fmaf(Bq, qb.b.y, Pq)) * ex2a(-fmaf(Bq, qb.b.z, fmaf(Bl, qb.a.x, Pl)));
+                const float fa = (eb * K) * K2, fb = (ea * K) * K2;
+                const float ta_ = c1 + ea, tb_ = c1 + eb;
+                accum(qa, ea, fa, ta_, rcpa(fmaf(ta_, fa, ta_)));
+                accum(qb, eb, fb, tb_, rcpa(fmaf(tb_, fb, tb_)));
             }
         }
     } else if (NE > 0) {
@@ -348,6 +384,10 @@ __global__ void __launch_bounds__(VX_TPB_MIXED, MINB) k_pair_mixed(const __grid_
                     zs.c1 = 1.f;
                     zs.unsc = 1.0;
                 }
+                if (zs.deg) {
+                    zs.K = (float)ldexp(exp(-ae), (int)zs.sc);
+                    zs.K2 = (float)exp(-ae);
+                }
                 zs.sB = ldexpf(1.f, kb);
                 zs.iB = ldexpf(1.f, -kb);
                 zs.sP = ldexpf(1.f, kb + 11);
@@ -426,7 +466,7 @@ __global__ void __launch_bounds__(VX_TPB_MIXED, MINB) k_pair_mixed(const __grid_
                 const float Pp = fmaf(Em, il_h, el_h);
                 if (!deg) {
                     const float Pe = fmaf(Em, il_h, -el_h);
-                    node_loop<NE, ADJ, false>(s_nodes, C.n_e, B, Pe, Pp, 0.f, 0.f, 0.f, 0.f, h, Em, 1.f, zs.K, mo, ta, tp, et);
+                    node_loop<NE, ADJ, false>(s_nodes, C.n_e, B, Pe, Pp, 0.f, 0.f, 0.f, 0.f, h, Em, 1.f, zs.K, 0.f, mo, ta, tp, et);
                     const Coef cf = make_coef<false>(kp, km, k0, kpl, kml, k0l, C.t_hi[m], C.t_lo[m]);
                     project<false>(PO, mo, cf);
                     if (ADJ) {
@@ -451,7 +491,7 @@ __global__ void __launch_bounds__(VX_TPB_MIXED, MINB) k_pair_mixed(const __grid_
                     float Pq = __fmul_rn(rintf(__fmul_rn(s, zs.sP)), zs.iP);
                     float Pl = __fadd_rn(__fsub_rn(s, Pq), slo);
                     Pq = __fadd_rn(Pq, zs.sc);  // exact: an integer on the same grid
-                    node_loop<NE, ADJ, true>(s_nodes, C.n_e, B, 0.f, Pp, Bq, Bl, Pq, Pl, h, Em, zs.c1, 0.f, mo, ta, tp, et);
+                    node_loop<NE, ADJ, true>(s_nodes, C.n_e, B, 0.f, Pp, Bq, Bl, Pq, Pl, h, Em, zs.c1, zs.K, zs.K2, mo, ta, tp, et);
                     const Coef cf = make_coef<true>(kp, km, k0, kpl, kml, k0l, C.t_hi[m], C.t_lo[m]);
                     project<true>(PO, mo, cf);
                     if (ADJ) {  // tangent l = 1 sums: FP32 (checked against their absolute-value bound)
