@@ -145,7 +145,7 @@ void vx_rates_destroy(vx_rates *h);
  * or one whose implicit time step cannot afford the device-wide synchronisation that cudaMalloc
  * and cudaFree imply. It takes the config directly (no handle) and computes the same rates as
  * vx_rates_eval on a mixed-precision handle; the caller passes inputs and outputs as there.
- *   - Scratch: one file-scope device array of 461,056 bytes (work counter, numeric flag and the
+ *   - Scratch: one file-scope device array of 307,456 bytes (work counter, numeric flag and the
  *     bin-pair table), present on every device that loads the library until the process exits.
  *     The call performs no cudaMalloc, cudaFree or other allocation.
  *   - Limits: at most 24 energy bins and 32 cos(omega) nodes; larger configs are rejected with

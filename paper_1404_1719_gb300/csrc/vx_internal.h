@@ -59,7 +59,8 @@ struct Common {
 struct Launch {
     Common c;
     Nodes32 n32;
-    const float4 *tab32;           // [n_mu][npair][3] float4 (mixed form)
+    const float4 *tab32;           // [npair][n_mu][2] float4 (mixed form): {|q|/2, E-} as FP32
+                                   //   value + remainder; {kp, km, k0, cos(omega_m)}
     const double *tab64;           // [n_mu][npair][5] (FP64 form)
     long long Z;
     const double *state, *J, *H;
@@ -82,16 +83,16 @@ struct Launch64 {
 };
 
 // Dynamic shared memory of the mixed kernel (floats unless noted), N2 = N*N:
-//   mats[q][3][N2]: per quantity q (kernel; and with tangents: T of annihilation, T of production,
-//                   eta), l = 0, l = 1 hi, l = 1 lo of Phi_I(i,j) (term II is the transpose)
+//   mats[q][2][N2]: per quantity q (kernel; and with tangents: T of annihilation, T of production,
+//                   eta), l = 0, 1 of Phi_I(i,j) (term II is the transpose)
 //   vec[4][S][N]  : contraction vectors per output (j0, chi0, j1, chi1) and species
 //   sc, em, shv [N] (double): per-bin FP64 factors;  red[64] (double): block reduction
-//   part[block][2][q][6]: partial projections of bin pairs split between two threads
+//   part[2][q][4][block]: partial projections of bin pairs split between two threads
 __host__ __device__ inline size_t smem_mixed_bytes(int N, int S, bool adj, int block) {
     size_t nq = adj ? 4 : 1;
-    size_t f = nq * 3 * (size_t)N * N + 4 * (size_t)S * N;
+    size_t f = nq * 2 * (size_t)N * N + 4 * (size_t)S * N;
     f = (f + 1) & ~(size_t)1;
-    return f * 4 + 3 * (size_t)N * 8 + 64 * 8 + (size_t)block * 2 * nq * 6 * 4;
+    return f * 4 + 3 * (size_t)N * 8 + 64 * 8 + (size_t)block * 2 * nq * 4 * 4;
 }
 size_t smem_fp64(const Common &c);
 

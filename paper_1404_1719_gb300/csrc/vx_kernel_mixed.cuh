@@ -29,15 +29,20 @@
 //  * degenerate path (|eta| > eta_sw): the electron argument B (1 + tau) + P is formed exactly:
 //    B, P and 1 + tau are split into a high part on a power-of-two grid (chosen per zone so that
 //    fma(B_hi, u_hi, P_hi) is exact in FP32) and a remainder, and exp2 of the exact high part and
-//    of the small remainder are multiplied. The l = 1 projection of the kernel, whose omega sum
-//    cancels by up to ~760x at high degeneracy, is accumulated in FP32-pair (double-float)
-//    arithmetic; the tangents' l = 1 sums in FP32.
+//    of the small remainder are multiplied.
+// The l = 1 omega projections and the spectral contraction are FP32 sums; their rounding is
+// bounded by the same sums taken over absolute values, the scale that the parity metric uses
+// for every l = 1 quantity (their omega sum cancels by up to ~760x at high degeneracy).
 #pragma once
 #include "vx_internal.h"
 
 // Pair reciprocals (one rcp for two nodes) also in the tangent kernel's fast path.
 #ifndef VX_ADJ_PAIR
 #define VX_ADJ_PAIR 0
+#endif
+// Nodes per unrolled chunk of the forward kernel's fast-path loop (a divisor of 16).
+#ifndef VX_UNROLL_FWD
+#define VX_UNROLL_FWD 16
 #endif
 // Degenerate path: e2 from the mirror node's e1 (saves one ex2 per node, costs registers).
 #ifndef VX_DEG_MIRROR
@@ -50,6 +55,9 @@ __device__ __forceinline__ float ex2a(float x) {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
+}
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 __device__ __forceinline__ float rcpa(float x) {
     float y;
@@ -68,35 +76,11 @@ __device__ __forceinline__ double exp2neg(double y) {
     return (double)ex2a(-f) * p2;
 }
 
-// (h, l) += (ah + al) * M : error-free product and two-sum in FP32 (no contraction).
-__device__ __forceinline__ void df_fma(float &h, float &l, float ah, float al, float M) {
-    float p = __fmul_rn(ah, M);
-    float pe = fmaf(ah, M, -p);
-    float s = __fadd_rn(h, p);
-    float bb = __fsub_rn(s, h);
-    float err = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(p, bb));
-    h = s;
-    l = __fadd_rn(l, __fadd_rn(err, fmaf(al, M, pe)));
-}
-// (h, l) += (bh, bl)
-__device__ __forceinline__ void df_add(float &h, float &l, float bh, float bl) {
-    float s = __fadd_rn(h, bh);
-    float bb = __fsub_rn(s, h);
-    float err = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(bh, bb));
-    h = s;
-    l = __fadd_rn(l, __fadd_rn(err, bl));
-}
-// (ph, pl) = (ah, al) * (bh, bl) to ~2^-44
-__device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, float &ph, float &pl) {
-    ph = __fmul_rn(ah, bh);
-    pl = __fadd_rn(fmaf(ah, bh, -ph), __fadd_rn(__fmul_rn(ah, bl), __fmul_rn(al, bh)));
-}
-
 // Projections of one quantity (blocking factor or one of its tangents) onto l = 0, 1 for
 // coupling terms I and II.
 struct Proj {
-    float o0I, o0II, o1Ih, o1Il, o1IIh, o1IIl;
-    __device__ __forceinline__ void zero() { o0I = o0II = o1Ih = o1Il = o1IIh = o1IIl = 0.f; }
+    float o0I, o0II, o1I, o1II;
+    __device__ __forceinline__ void zero() { o0I = o0II = o1I = o1II = 0.f; }
 };
 
 struct ZoneSh {
@@ -107,9 +91,10 @@ struct ZoneSh {
     float iB, iP;      // their inverses
     float sc;          // degenerate path: blocking factor carried as O 2^sc (keeps the deepest-
     float c1;          //   blocked nodes of the zone far from the FP32 underflow); c1 = 2^-sc
-    float K, K2;       // e2 on a node from e1 on its mirror node: fast path K = e^{-2|eta|};
-                       //   degenerate path K = 2^sc e^{-|eta|}, K2 = e^{-|eta|}
+    float K, K2;       // e2 on a node from e1 on its mirror node: K = e^{-2|eta|}, K2 = e^{-|eta|}
+    float p2sc;        // 2^sc
     double unsc;       // 2^-sc, applied in FP64 to every result of the zone
+    double iT2;        // 1/T^2
     int sv;            // production vectors carried as v 2^sv (degenerate zones); the two scales
                        //   share the FP32 exponent headroom so no product can overflow
     int deg, neg, bad;
@@ -147,6 +132,7 @@ __device__ __forceinline__ void node_loop(const NodeSm *__restrict__ nd, int ne,
     constexpr bool MIRROR = !DEG && NE > 0;
     constexpr bool MPAIR = !ADJ || VX_ADJ_PAIR;
     constexpr int U = 16;
+    constexpr int UM = ADJ ? U : VX_UNROLL_FWD;  // nodes per unrolled chunk of the mirror loop
     // tangent integrands of one node, accumulated with its basis weights (cp, cm, c0)
     auto tang = [&](float cp, float cm, float c0, float e1, float e2, float t, float r, float E, float Eb) {
         float ga, gp, ge;
@@ -195,9 +181,9 @@ __device__ __forceinline__ void node_loop(const NodeSm *__restrict__ nd, int ne,
     if (MIRROR) {
         static_assert(NE % U == 0 || NE == 0, "unrolled instantiations need a multiple of the unroll depth");
 #pragma unroll 1
-        for (int k0 = 0; k0 < NE / 2; k0 += U / 2) {
+        for (int k0 = 0; k0 < NE / 2; k0 += UM / 2) {
 #pragma unroll
-            for (int kk = 0; kk < U / 2; ++kk) {
+            for (int kk = 0; kk < UM / 2; ++kk) {
                 const NodeSm q = nd[k0 + kk];
                 const float ea = ex2a(-fmaf(B, q.a.x, Pe));  // e1(tau)
                 const float eb = ex2a(-fmaf(B, q.a.y, Pe));  // e1(-tau)
@@ -263,57 +249,49 @@ __device__ __forceinline__ void node_loop(const NodeSm *__restrict__ nd, int ne,
     }
 }
 
-// Coefficients that turn one (pair, omega) node's moments into its contributions: l = 0 in FP32
-// (kp, km, k0), l = 1 as t * k in FP32 (fast path) or as FP32 pairs (degenerate path). (kp, km)
-// are already exchanged for eta < 0.
+// Coefficients that turn one (pair, omega) node's moments into its contributions: l = 0
+// (kp, km, k0) and l = 1 (t kp, t km, t k0). (kp, km) are already exchanged for eta < 0.
 struct Coef {
-    float kp, km, k0;        // l = 0
-    float lph, lmh, l0h;     // l = 1, high parts
-    float lpl, lml, l0l;     // l = 1, low parts (degenerate path)
+    float kp, km, k0;  // l = 0
+    float lp, lm, l0;  // l = 1
 };
 
-template <bool DEG>
-__device__ __forceinline__ Coef make_coef(float kp, float km, float k0, float kpl, float kml, float k0l, float th,
-                                          float tl) {
+__device__ __forceinline__ Coef make_coef(float kp, float km, float k0, float t) {
     Coef c;
     c.kp = kp; c.km = km; c.k0 = k0;
-    if (!DEG) {
-        c.lph = th * kp; c.lmh = th * km; c.l0h = th * k0;
-        c.lpl = c.lml = c.l0l = 0.f;
-    } else {
-        df_mul(th, tl, kp, kpl, c.lph, c.lpl);
-        df_mul(th, tl, km, kml, c.lmh, c.lml);
-        df_mul(th, tl, k0, k0l, c.l0h, c.l0l);
-    }
+    c.lp = t * kp; c.lm = t * km; c.l0 = t * k0;
     return c;
 }
 
 // Projection of one quantity's moments onto l = 0, 1 for terms I and II (term II of a pair uses
 // the coefficients with kp and km exchanged).
-template <bool DEG>
 __device__ __forceinline__ void project(Proj &P, const Mom &M, const Coef &c) {
     P.o0I += fmaf(c.kp, M.p, fmaf(c.km, M.m, c.k0 * M.z));
     P.o0II += fmaf(c.km, M.p, fmaf(c.kp, M.m, c.k0 * M.z));
-    if (!DEG) {
-        P.o1Ih += fmaf(c.lph, M.p, fmaf(c.lmh, M.m, c.l0h * M.z));
-        P.o1IIh += fmaf(c.lmh, M.p, fmaf(c.lph, M.m, c.l0h * M.z));
-    } else {
-        df_fma(P.o1Ih, P.o1Il, c.lph, c.lpl, M.p);
-        df_fma(P.o1Ih, P.o1Il, c.lmh, c.lml, M.m);
-        df_fma(P.o1Ih, P.o1Il, c.l0h, c.l0l, M.z);
-        df_fma(P.o1IIh, P.o1IIl, c.lmh, c.lml, M.p);
-        df_fma(P.o1IIh, P.o1IIl, c.lph, c.lpl, M.m);
-        df_fma(P.o1IIh, P.o1IIl, c.l0h, c.l0l, M.z);
-    }
+    P.o1I += fmaf(c.lp, M.p, fmaf(c.lm, M.m, c.l0 * M.z));
+    P.o1II += fmaf(c.lm, M.p, fmaf(c.lp, M.m, c.l0 * M.z));
 }
 
-// Writes one pair's projections into the zone matrices: term I of pair (i,j) is Phi_I(i,j),
-// term II is Phi_I(j,i).
-__device__ __forceinline__ void store_proj(float *q3, int N2, int N, int pi, int pj, const Proj &P) {
-    float *M0 = q3, *M1h = q3 + N2, *M1l = q3 + 2 * N2;
+// Writes one pair's projections into the zone matrices [l][N][N]: term I of pair (i,j) is
+// Phi_I(i,j), term II is Phi_I(j,i).
+__device__ __forceinline__ void store_proj(float *q2, int N2, int N, int pi, int pj, const Proj &P) {
+    float *M0 = q2, *M1 = q2 + N2;
     const int a = pi * N + pj, b = pj * N + pi;
-    M0[a] = P.o0I; M1h[a] = P.o1Ih; M1l[a] = P.o1Il;
-    if (pi != pj) { M0[b] = P.o0II; M1h[b] = P.o1IIh; M1l[b] = P.o1IIl; }
+    M0[a] = P.o0I; M1[a] = P.o1I;
+    if (pi != pj) { M0[b] = P.o0II; M1[b] = P.o1II; }
+}
+
+// Partial projections of bin pairs split between threads: part[slot q][4][TB] floats, thread
+// index fastest, so a warp's stores and loads fall in distinct banks.
+__device__ __forceinline__ void part_put(float *part, int TB, int t, int sq, const Proj &P) {
+    float *b = part + (size_t)sq * 4 * TB + t;
+    b[0] = P.o0I; b[TB] = P.o0II; b[2 * TB] = P.o1I; b[3 * TB] = P.o1II;
+}
+__device__ __forceinline__ Proj part_get(const float *part, int TB, int t, int sq) {
+    const float *b = part + (size_t)sq * 4 * TB + t;
+    Proj P;
+    P.o0I = b[0]; P.o0II = b[TB]; P.o1I = b[2 * TB]; P.o1II = b[3 * TB];
+    return P;
 }
 
 // MINB = CTAs per SM the register allocation must allow (2: up to 128 registers, 3: up to 80);
@@ -324,30 +302,48 @@ __global__ void __launch_bounds__(VX_TPB_MIXED, MINB) k_pair_mixed(const __grid_
     __shared__ ZoneSh zs;
     __shared__ long long s_zone;
     __shared__ NodeSm s_nodes[VX_MAX_NE];
+    __shared__ uint16_t s_pij[VX_MAX_PAIRS];
     const Common &C = L.c;
     const int N = C.N, S = C.S, N2 = N * N, npair = C.npair;
     const int nq = ADJ ? 4 : 1;
     float *mats = reinterpret_cast<float *>(smraw);
-    float *vec = mats + (size_t)nq * 3 * N2;
-    size_t foff = ((size_t)nq * 3 * N2 + 4 * (size_t)S * N + 1) & ~(size_t)1;
+    float *vec = mats + (size_t)nq * 2 * N2;
+    size_t foff = ((size_t)nq * 2 * N2 + 4 * (size_t)S * N + 1) & ~(size_t)1;
     double *sc = reinterpret_cast<double *>(smraw + foff * 4);
     double *em = sc + N;
     double *shv = em + N;  // exp(-(eps_j - eps_0)/T) 2^sv
     double *red = shv + N;  // 64 doubles for block reductions
-    Proj *part = reinterpret_cast<Proj *>(red + 64);  // [blockDim][2 slots][nq] partial projections
+    float *part = reinterpret_cast<float *>(red + 64);  // [2 slots][nq][4][blockDim] partial projections
     const int tid = threadIdx.x;
     for (int k = tid; k < C.n_e; k += blockDim.x) {
         s_nodes[k].a = make_float4(L.n32.u[k], L.n32.v[k], L.n32.cp[k], L.n32.cm[k]);
         s_nodes[k].b = make_float4(L.n32.c0[k], L.n32.uh[k], L.n32.ul[k], 0.f);
     }
+    for (int p = tid; p < npair; p += blockDim.x) s_pij[p] = C.pij[p];
+
+    // Thread 0 reserves the next zone one iteration ahead and prefetches its inputs into L2 while
+    // the current zone's quadrature runs, so a zone starts without an atomic or DRAM round trip.
+    long long next_z = 0;
+    if (tid == 0) next_z = (long long)atomicAdd(L.counter, 1ull);
+    const int t_aux = blockDim.x > 32 ? 32 : 1;  // a thread of another warp for the set-up
 
     for (;;) {
-        if (tid == 0) s_zone = (long long)atomicAdd(L.counter, 1ull);
+        if (tid == 0) s_zone = next_z;
         __syncthreads();
         const long long z = s_zone;
         if (z >= L.Z) break;
+        if (tid == 0) next_z = (long long)atomicAdd(L.counter, 1ull);
 
-        // ---- zone set-up (FP64, one thread) --------------------------------------------------
+        // ---- zone set-up (FP64): the main scalars on thread 0, exponentials and 1/T^2 in parallel
+        if (tid == t_aux) {
+            const double T = L.state[4 * z + 0], ae = fabs(L.state[4 * z + 1]);
+            zs.iT2 = 1.0 / (T * T);
+            if (ae <= VX_ETA_MAX) {
+                const double LOG2E = 1.4426950408889634;
+                zs.K = (float)exp2neg(2.0 * ae * LOG2E);  // e^{-2|eta|}
+                zs.K2 = (float)exp2neg(ae * LOG2E);       // e^{-|eta|}
+            }
+        }
         if (tid == 0) {
             double T = L.state[4 * z + 0], eta = L.state[4 * z + 1];
             int bad = !(T > 0.0) || !isfinite(T) || !isfinite(eta) || fabs(eta) > VX_ETA_MAX;
@@ -364,7 +360,6 @@ __global__ void __launch_bounds__(VX_TPB_MIXED, MINB) k_pair_mixed(const __grid_
                 zs.el_l = (float)(el - (double)zs.el_h);
                 zs.neg = eta < 0.0;
                 zs.deg = ae > C.eta_sw;
-                zs.K = (float)exp(-2.0 * ae);
                 // zone scales: with O in [e^-|eta|, 1] and production vectors whose relevant
                 // entries reach e^-|eta| times their row's largest, lift both off the FP32 floor
                 int sc = zs.deg ? (int)floor(0.3 * el) : 0;
@@ -384,10 +379,7 @@ __global__ void __launch_bounds__(VX_TPB_MIXED, MINB) k_pair_mixed(const __grid_
                     zs.c1 = 1.f;
                     zs.unsc = 1.0;
                 }
-                if (zs.deg) {
-                    zs.K = (float)ldexp(exp(-ae), (int)zs.sc);
-                    zs.K2 = (float)exp(-ae);
-                }
+                zs.p2sc = ldexpf(1.f, (int)zs.sc);
                 zs.sB = ldexpf(1.f, kb);
                 zs.iB = ldexpf(1.f, -kb);
                 zs.sP = ldexpf(1.f, kb + 11);
@@ -418,7 +410,7 @@ __global__ void __launch_bounds__(VX_TPB_MIXED, MINB) k_pair_mixed(const __grid_
             const double il = 1.4426950408889634 / T;  // log2(e)/T
             for (int e = tid; e < 3 * N; e += blockDim.x) {
                 const int i = e % N, which = e / N;
-                if (which == 0) sc[i] = exp2neg((C.eps[i] + C.eps[0]) * il);           // e^{-(eps_i+eps_0)/T}
+                if (which == 0) sc[i] = exp2neg((C.eps[i] + C.eps[0]) * il + (double)zs.sv);  // e^{-(eps_i+eps_0)/T} 2^-sv
                 else if (which == 1) em[i] = exp2neg(C.eps[i] * il);                     // e^{-eps_i/T}
                 else shv[i] = exp2neg((C.eps[i] - C.eps[0]) * il - (double)zs.sv);       // e^{-(eps_i-eps_0)/T} 2^sv
             }
@@ -432,6 +424,15 @@ __global__ void __launch_bounds__(VX_TPB_MIXED, MINB) k_pair_mixed(const __grid_
             else if (o == 2) v = C.w[j] * L.H[a] * shv[j];
             else v = C.w[j] * (o == 1 ? L.J[a] : L.H[a]);
             vec[e] = (float)v;
+        }
+
+        if (tid == 0 && next_z < L.Z) {
+            prefetch_l2(L.state + 4 * next_z);
+            const size_t off = (size_t)next_z * S * N;
+            for (int b = 0; b < S * N; b += 16) {
+                prefetch_l2(L.J + off + b);
+                prefetch_l2(L.H + off + b);
+            }
         }
 
         // ---- quadrature: the npair * n_mu (pair, omega) units in equal contiguous ranges --------
@@ -451,13 +452,13 @@ __global__ void __launch_bounds__(VX_TPB_MIXED, MINB) k_pair_mixed(const __grid_
 #pragma unroll 1
         for (int u = u0; u < u1; ++u) {
             {
-                const float4 *rec = L.tab32 + ((size_t)m * npair + p) * 3;
-                float4 R0 = __ldg(rec), R1 = __ldg(rec + 1), R2 = __ldg(rec + 2);
+                const float4 *rec = L.tab32 + ((size_t)p * nmu + m) * 2;  // a thread's units are consecutive records
+                const float4 R0 = __ldg(rec), R1 = __ldg(rec + 1);
                 const float h = R0.x, h_lo = R0.y, Em = R0.z, Em_lo = R0.w;
-                float kp = R1.x, km = R1.y, k0 = R1.z, kpl = R2.x, kml = R2.y, k0l = R2.z;
+                float kp = R1.x, km = R1.y;
+                const float k0 = R1.z;
                 if (neg) {  // eta < 0: electron and positron exchange roles, M+ <-> M-
                     float t = kp; kp = km; km = t;
-                    t = kpl; kpl = kml; kml = t;
                 }
                 Mom mo, ta, tp, et;
                 mo.zero();
@@ -467,12 +468,12 @@ __global__ void __launch_bounds__(VX_TPB_MIXED, MINB) k_pair_mixed(const __grid_
                 if (!deg) {
                     const float Pe = fmaf(Em, il_h, -el_h);
                     node_loop<NE, ADJ, false>(s_nodes, C.n_e, B, Pe, Pp, 0.f, 0.f, 0.f, 0.f, h, Em, 1.f, zs.K, 0.f, mo, ta, tp, et);
-                    const Coef cf = make_coef<false>(kp, km, k0, kpl, kml, k0l, C.t_hi[m], C.t_lo[m]);
-                    project<false>(PO, mo, cf);
+                    const Coef cf = make_coef(kp, km, k0, R1.w);
+                    project(PO, mo, cf);
                     if (ADJ) {
-                        project<false>(PTa, ta, cf);
-                        project<false>(PTp, tp, cf);
-                        project<false>(PEt, et, cf);
+                        project(PTa, ta, cf);
+                        project(PTp, tp, cf);
+                        project(PEt, et, cf);
                     }
                 } else {
                     const float il_l = zs.il_l, el_l = zs.el_l;
@@ -491,30 +492,34 @@ __global__ void __launch_bounds__(VX_TPB_MIXED, MINB) k_pair_mixed(const __grid_
                     float Pq = __fmul_rn(rintf(__fmul_rn(s, zs.sP)), zs.iP);
                     float Pl = __fadd_rn(__fsub_rn(s, Pq), slo);
                     Pq = __fadd_rn(Pq, zs.sc);  // exact: an integer on the same grid
-                    node_loop<NE, ADJ, true>(s_nodes, C.n_e, B, 0.f, Pp, Bq, Bl, Pq, Pl, h, Em, zs.c1, zs.K, zs.K2, mo, ta, tp, et);
-                    const Coef cf = make_coef<true>(kp, km, k0, kpl, kml, k0l, C.t_hi[m], C.t_lo[m]);
-                    project<true>(PO, mo, cf);
-                    if (ADJ) {  // tangent l = 1 sums: FP32 (checked against their absolute-value bound)
-                        project<false>(PTa, ta, cf);
-                        project<false>(PTp, tp, cf);
-                        project<false>(PEt, et, cf);
+                    node_loop<NE, ADJ, true>(s_nodes, C.n_e, B, 0.f, Pp, Bq, Bl, Pq, Pl, h, Em, zs.c1, zs.K2 * zs.p2sc, zs.K2, mo, ta, tp, et);
+                    const Coef cf = make_coef(kp, km, k0, R1.w);
+                    project(PO, mo, cf);
+                    if (ADJ) {
+                        project(PTa, ta, cf);
+                        project(PTp, tp, cf);
+                        project(PEt, et, cf);
                     }
                 }
             }
             ++m;
             if (m == nmu || u + 1 == u1) {  // end of a pair or of this thread's range: flush
                 if (mb == 0 && m == nmu) {  // the whole pair in this thread
-                    const int pi = C.pij[p] >> 8, pj = C.pij[p] & 0xff;
-                    store_proj(mats + 0 * 3 * (size_t)N2, N2, N, pi, pj, PO);
+                    const int pi = s_pij[p] >> 8, pj = s_pij[p] & 0xff;
+                    store_proj(mats + 0 * 2 * (size_t)N2, N2, N, pi, pj, PO);
                     if (ADJ) {
-                        store_proj(mats + 1 * 3 * (size_t)N2, N2, N, pi, pj, PTa);
-                        store_proj(mats + 2 * 3 * (size_t)N2, N2, N, pi, pj, PTp);
-                        store_proj(mats + 3 * 3 * (size_t)N2, N2, N, pi, pj, PEt);
+                        store_proj(mats + 1 * 2 * (size_t)N2, N2, N, pi, pj, PTa);
+                        store_proj(mats + 2 * 2 * (size_t)N2, N2, N, pi, pj, PTp);
+                        store_proj(mats + 3 * 2 * (size_t)N2, N2, N, pi, pj, PEt);
                     }
                 } else {
-                    Proj *slot = part + ((size_t)tid * 2 + (first ? 0 : 1)) * nq;
-                    slot[0] = PO;
-                    if (ADJ) { slot[1] = PTa; slot[2] = PTp; slot[3] = PEt; }
+                    const int sq = (first ? 0 : 1) * nq;
+                    part_put(part, TB, tid, sq, PO);
+                    if (ADJ) {
+                        part_put(part, TB, tid, sq + 1, PTa);
+                        part_put(part, TB, tid, sq + 2, PTp);
+                        part_put(part, TB, tid, sq + 3, PEt);
+                    }
                 }
                 PO.zero();
                 if (ADJ) { PTa.zero(); PTp.zero(); PEt.zero(); }
@@ -531,19 +536,19 @@ __global__ void __launch_bounds__(VX_TPB_MIXED, MINB) k_pair_mixed(const __grid_
             const int ua = p * nmu, ub = ua + nmu - 1;
             const int ta = ((ua + 1) * TB + U - 1) / U - 1, tb = ((ub + 1) * TB + U - 1) / U - 1;
             if (ta == tb) continue;
-            const int pi = C.pij[p] >> 8, pj = C.pij[p] & 0xff;
+            const int pi = s_pij[p] >> 8, pj = s_pij[p] & 0xff;
             for (int q = 0; q < nq; ++q) {
                 Proj acc;
                 acc.zero();
                 for (int t = ta; t <= tb; ++t) {
                     const int sl = (t == ta && ua > t * U / TB) ? 1 : 0;
-                    const Proj &x = part[((size_t)t * 2 + sl) * nq + q];
+                    const Proj x = part_get(part, TB, t, sl * nq + q);
                     acc.o0I += x.o0I;
                     acc.o0II += x.o0II;
-                    df_add(acc.o1Ih, acc.o1Il, x.o1Ih, x.o1Il);
-                    df_add(acc.o1IIh, acc.o1IIl, x.o1IIh, x.o1IIl);
+                    acc.o1I += x.o1I;
+                    acc.o1II += x.o1II;
                 }
-                store_proj(mats + (size_t)q * 3 * N2, N2, N, pi, pj, acc);
+                store_proj(mats + (size_t)q * 2 * N2, N2, N, pi, pj, acc);
             }
         }
         __syncthreads();
@@ -551,7 +556,7 @@ __global__ void __launch_bounds__(VX_TPB_MIXED, MINB) k_pair_mixed(const __grid_
         // ---- contraction (and tangents) --------------------------------------------------------
         const double two_pi = 6.283185307179586;
         const double c0 = two_pi * C.norm * C.g2 * zs.unsc, c1 = 3.0 * c0;
-        const double iT2 = 1.0 / (T * T);
+        const double iT2 = zs.iT2;
         const double sgn = zs.neg ? -1.0 : 1.0;  // d/deta of the eta >= 0 mapping
         const int nout = 4 * S * N;
         double gT = 0.0, gE = 0.0;
@@ -563,31 +568,16 @@ __global__ void __launch_bounds__(VX_TPB_MIXED, MINB) k_pair_mixed(const __grid_
             const float bI = C.bI[s], bII = C.bII[s];
             const float *v = vec + (size_t)(o * S + s) * N;
             const double cl = l ? c1 : c0;
-            const double scal = prod ? sc[i] * ldexp(1.0, -zs.sv) : 1.0;
+            const double scal = prod ? sc[i] : 1.0;
             double res[3];  // contraction of: the kernel, its T tangent, its eta tangent
             const int nres = ADJ ? 3 : 1;
 #pragma unroll
             for (int r = 0; r < nres; ++r) {
                 const int q = r == 0 ? 0 : r == 2 ? 3 : (prod ? 2 : 1);
-                const float *M0 = mats + (size_t)(q * 3 + 0) * N2;
-                const float *M1h = mats + (size_t)(q * 3 + 1) * N2;
-                const float *M1l = mats + (size_t)(q * 3 + 2) * N2;
-                if (l == 0) {
-                    float acc = 0.f;
-                    for (int j = 0; j < N; ++j)
-                        acc = fmaf(fmaf(bI, M0[i * N + j], bII * M0[j * N + i]), v[j], acc);
-                    res[r] = (double)acc;
-                } else {
-                    float ah = 0.f, al = 0.f;
-                    for (int j = 0; j < N; ++j) {
-                        float kh, kl, th, tl;
-                        df_mul(bI, 0.f, M1h[i * N + j], M1l[i * N + j], kh, kl);
-                        df_mul(bII, 0.f, M1h[j * N + i], M1l[j * N + i], th, tl);
-                        df_add(kh, kl, th, tl);
-                        df_fma(ah, al, kh, kl, v[j]);
-                    }
-                    res[r] = (double)ah + (double)al;
-                }
+                const float *M = mats + (size_t)(q * 2 + l) * N2;
+                float acc = 0.f;
+                for (int j = 0; j < N; ++j) acc = fmaf(fmaf(bI, M[i * N + j], bII * M[j * N + i]), v[j], acc);
+                res[r] = (double)acc;
             }
             const size_t oi = ((size_t)z * S + s) * N + i;
             const double fwd = cl * scal * res[0];
@@ -635,7 +625,7 @@ __global__ void __launch_bounds__(VX_TPB_MIXED, MINB) k_pair_mixed(const __grid_
         if (L.phi) {  // raw kernel of term I, G2 applied: [dir][l][i][j]
             for (int e = tid; e < 4 * N2; e += blockDim.x) {
                 const int d = e / (2 * N2), l = (e / N2) & 1, ij = e % N2, i = ij / N, j = ij % N;
-                double a = l ? (double)mats[N2 + ij] + (double)mats[2 * N2 + ij] : (double)mats[ij];
+                double a = (double)mats[l * N2 + ij];
                 double v = C.g2 * zs.unsc * (d == 0 ? em[i] * em[j] * a : a);
                 L.phi[(size_t)z * 4 * N2 + e] = v;
             }

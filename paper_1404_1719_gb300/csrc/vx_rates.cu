@@ -243,9 +243,10 @@ vx_status vx_rates_create(const vx_config *cfg, vx_rates **out) {
         h->n32.uh[k] = (float)uh;
         h->n32.ul[k] = (float)(u - uh);
     }
-    // per (omega node m, unordered pair p) tables
+    // per (unordered pair p, omega node m) tables: FP32 records pair-major (a thread's consecutive
+    // units are adjacent), FP64 records omega-major
     const int np = C.npair;
-    std::vector<float4> t32((size_t)nmu * np * 3);
+    std::vector<float4> t32((size_t)nmu * np * 2);
     std::vector<double> t64((size_t)nmu * np * 5);
     const double pi = 3.14159265358979323846;
     double hmax = 0.0, q0hmax = 0.0;
@@ -263,11 +264,10 @@ vx_status vx_rates_create(const vx_config *cfg, vx_rates **out) {
             const double kp = pref * 0.25 * (q + d) * (q + d), km = pref * 0.25 * (q - d) * (q - d), k0 = pref * 2.0 * g;
             hmax = std::fmax(hmax, hh);
             q0hmax = std::fmax(q0hmax, 0.5 * q0);
-            float4 *r = &t32[((size_t)m * np + p) * 3];
-            float fh = (float)hh, fEm = (float)Em, fkp = (float)kp, fkm = (float)km, fk0 = (float)k0;
+            float4 *r = &t32[((size_t)p * nmu + m) * 2];
+            const float fh = (float)hh, fEm = (float)Em;
             r[0] = make_float4(fh, (float)(hh - fh), fEm, (float)(Em - fEm));
-            r[1] = make_float4(fkp, fkm, fk0, 0.f);
-            r[2] = make_float4((float)(kp - fkp), (float)(km - fkm), (float)(k0 - fk0), 0.f);
+            r[1] = make_float4((float)kp, (float)km, (float)k0, C.t_hi[m]);
             double *r64 = &t64[((size_t)m * np + p) * 5];
             r64[0] = hh; r64[1] = Em; r64[2] = kp; r64[3] = km; r64[4] = k0;
         }
@@ -318,8 +318,8 @@ vx_status vx_rates_create(const vx_config *cfg, vx_rates **out) {
                {vx::kernel_mixed(true, 3, ne), h->smem_adj, &h->grid_mixed[1][1], h->block_mixed},
                {vx::kernel_fp64_fwd(ne), h->smem_64, &h->grid_64, h->block}};
     for (K &k : ks) {
-        if (k.smem > 48 * 1024)
-            VX_CUC(cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem));
+        // opt in to the dynamic size always: the 48 KB default bounds static + dynamic together
+        VX_CUC(cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem));
         int occ = 0;
         VX_CUC(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k.fn, k.block, k.smem));
         if (occ < 1) return cleanup(fail(VX_ERR_UNSUPPORTED, "kernel does not fit on an SM (block %d, smem %zu)", k.block, k.smem));
@@ -664,7 +664,7 @@ void vx_rates_destroy(vx_rates *h) {
 #define VX_NOALLOC_MAX_PAIRS (VX_NOALLOC_MAX_BINS * (VX_NOALLOC_MAX_BINS + 1) / 2)
 #define VX_NOALLOC_TABLE_OFFSET 256
 #define VX_NOALLOC_SCRATCH_BYTES \
-    (VX_NOALLOC_TABLE_OFFSET + (size_t)VX_NOALLOC_MAX_PAIRS * VX_NOALLOC_MAX_MU * 3 * sizeof(float4))
+    (VX_NOALLOC_TABLE_OFFSET + (size_t)VX_NOALLOC_MAX_PAIRS * VX_NOALLOC_MAX_MU * 2 * sizeof(float4))
 #define VX_NOALLOC_MAX_DEVICES 64
 
 // 461,056 bytes on every device that loads the library, held until the process exits.
@@ -683,9 +683,9 @@ struct NoallocTab {
     int N, n_mu, npair;
 };
 
-// Fills the (omega node, unordered pair) table in scratch with the records vx_rates_create builds
-// on the host: half-width |q|/2, lower electron energy E-, and the three moment coefficients, each
-// as an FP32 value plus FP32 remainder.
+// Fills the (unordered pair, omega node) table in scratch with the records vx_rates_create builds
+// on the host: half-width |q|/2 and lower electron energy E- (FP32 value plus remainder), the
+// three moment coefficients and cos(omega).
 __global__ void k_noalloc_table(const __grid_constant__ NoallocTab P, float4 *tab) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= P.n_mu * P.npair) return;
@@ -700,11 +700,10 @@ __global__ void k_noalloc_table(const __grid_constant__ NoallocTab P, float4 *ta
     const double Em = s / (2.0 * (q0 + q));
     const double pref = P.wm[m] * pi * ee * ep * y * y / (16.0 * q2);
     const double kp = pref * 0.25 * (q + d) * (q + d), km = pref * 0.25 * (q - d) * (q - d), k0 = pref * 2.0 * g;
-    float4 *r = tab + ((size_t)m * P.npair + p) * 3;
-    float fh = (float)hh, fEm = (float)Em, fkp = (float)kp, fkm = (float)km, fk0 = (float)k0;
+    float4 *r = tab + ((size_t)p * P.n_mu + m) * 2;
+    const float fh = (float)hh, fEm = (float)Em;
     r[0] = make_float4(fh, (float)(hh - fh), fEm, (float)(Em - fEm));
-    r[1] = make_float4(fkp, fkm, fk0, 0.f);
-    r[2] = make_float4((float)(kp - fkp), (float)(km - fkm), (float)(k0 - fk0), 0.f);
+    r[1] = make_float4((float)kp, (float)km, (float)k0, (float)t);
 }
 
 // Gauss-Legendre nodes and weights into caller arrays (the same Newton iteration as
@@ -865,7 +864,7 @@ vx_status vx_rates_eval_noalloc(const vx_config *cfg, const vx_batch *b, const v
     const int block = std::min(round_up(L.c.npair * cfg->n_mu, 32), VX_TPB_MIXED);
     const size_t smem = vx::smem_mixed_bytes(cfg->n_bins, cfg->n_species, false, block);
     const void *fn = vx::kernel_mixed(false, minb, ne);
-    if (smem > 48 * 1024) VX_CU(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    VX_CU(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int nsm = 0, occ = 0;
     VX_CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     VX_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, block, smem));
