@@ -40,15 +40,18 @@ def entries(Z, N):
 
 
 # DRAM bytes (read + write) per zone of the forward + tangent kernel, from one ncu capture of the
-# 200-ray case of this workload; scaled to a launch by the zone count. None until the current
-# kernel has been captured (a figure taken on an earlier version of the kernel is not reported).
-TRAFFIC_BYTES_PER_ZONE = None
+# 200-ray case of this workload (dram__bytes_read.sum + dram__bytes_write.sum = 89.4 + 586.5 MB
+# for 80,000 zones); scaled to a launch by the zone count. Set to None whenever the kernel
+# changes, until it has been captured again.
+TRAFFIC_BYTES_PER_ZONE = 8449
 
 
 def algorithmic_flops_per_node(adj: bool) -> int:
-    """FP32 operations the method needs per (zone, unordered bin pair, omega, E) node, counting an
-    FMA as 2 and an exp or reciprocal as 1: forward 16, tangents 36 more."""
-    return 52 if adj else 16
+    """FP32 operations the method needs per (zone, unordered bin pair, omega, E) node in the
+    formulation the kernel evaluates (nodes in mirror pairs tau, -tau; tangents from r^2),
+    counting an FMA as 2 and an exp, reciprocal, add or multiply as 1: forward 14, tangents 33
+    more."""
+    return 47 if adj else 14
 
 
 def rank_batch(rank: int, rays=None, workload: int = WORKLOAD) -> dict:
