@@ -43,7 +43,7 @@ def entries(Z, N):
 # 200-ray case of this workload (dram__bytes_read.sum + dram__bytes_write.sum = 89.4 + 586.5 MB
 # for 80,000 zones); scaled to a launch by the zone count. Set to None whenever the kernel
 # changes, until it has been captured again.
-TRAFFIC_BYTES_PER_ZONE = 8449
+TRAFFIC_BYTES_PER_ZONE = None
 
 
 def algorithmic_flops_per_node(adj: bool) -> int:

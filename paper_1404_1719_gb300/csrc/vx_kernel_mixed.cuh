@@ -40,6 +40,11 @@
 #ifndef VX_ADJ_PAIR
 #define VX_ADJ_PAIR 0
 #endif
+// Fast path in packed FP32x2 arithmetic (one instruction for the same operation on a node and its
+// mirror node) or in scalar FP32.
+#ifndef VX_F32X2
+#define VX_F32X2 1
+#endif
 // Nodes per unrolled chunk of the forward kernel's fast-path loop (a divisor of 16).
 #ifndef VX_UNROLL_FWD
 #define VX_UNROLL_FWD 16
@@ -113,6 +118,12 @@ struct NodeSm {
     float4 a, b;
 };
 
+// The first n_e/2 nodes again, laid out for packed FP32x2 arithmetic on a mirror pair (tau, -tau):
+// a = {1+tau, 1-tau, w(1+tau)^2, w(1-tau)^2}, b = the same pairs swapped, c = {w(1-tau^2) twice}.
+struct NodeMir {
+    float4 a, b, c;
+};
+
 // One (pair, omega) node loop. Fills the moments of the blocking factor O and, with ADJ, of
 // GTa = O (f_e E + f_ebar Ebar), GTp = O ((1-f_e) E + (1-f_ebar) Ebar), GEt = O (f_ebar - f_e).
 // With the zone scale (degenerate path) e1 and the "1" of 1 + e1 carry the factor 2^-sc, so
@@ -125,7 +136,8 @@ struct NodeSm {
 // of tau less 2|eta|, so e2(tau) = e1(-tau) K and e2(-tau) = e1(tau) K with K = e^{-2|eta|}: one
 // ex2 and half a record read per node, and (MPAIR) one reciprocal per node pair.
 template <int NE, bool ADJ, bool DEG>
-__device__ __forceinline__ void node_loop(const NodeSm *__restrict__ nd, int ne, float B, float Pe,
+__device__ __forceinline__ void node_loop(const NodeSm *__restrict__ nd, const NodeMir *__restrict__ nm, int ne,
+                                          float B, float Pe,
                                           float Pp, float Bq, float Bl, float Pq, float Pl, float h,
                                           float Em, float c1, float K, float K2, Mom &mo, Mom &ta,
                                           Mom &tp, Mom &et) {
@@ -178,7 +190,58 @@ __device__ __forceinline__ void node_loop(const NodeSm *__restrict__ nd, int ne,
             t = c1 + e1;
         }
     };
-    if (MIRROR) {
+    if (MIRROR && VX_F32X2) {
+        // packed form: lane x of every float2 is node tau, lane y its mirror -tau
+        const float2 B2 = make_float2(B, B), Pe2 = make_float2(Pe, Pe), one2 = make_float2(1.f, 1.f);
+        const float2 h2 = make_float2(h, h), Em2 = make_float2(Em, Em), mone2 = make_float2(-1.f, -1.f);
+        const float2 z2 = make_float2(0.f, 0.f);
+        float2 P2 = z2, M2 = z2, Z2 = z2;
+        float2 TAp = z2, TAm = z2, TAz = z2, TPp = z2, TPm = z2, TPz = z2, ETp = z2, ETm = z2, ETz = z2;
+#pragma unroll 1
+        for (int k0 = 0; k0 < NE / 2; k0 += UM / 2) {
+#pragma unroll
+            for (int kk = 0; kk < UM / 2; ++kk) {
+                const NodeMir q = nm[k0 + kk];
+                const float2 uv = make_float2(q.a.x, q.a.y), cpm = make_float2(q.a.z, q.a.w);
+                const float2 cmp = make_float2(q.b.z, q.b.w), c00 = make_float2(q.c.x, q.c.y);
+                const float2 x = __ffma2_rn(B2, uv, Pe2);
+                const float ea = ex2a(-x.x), eb = ex2a(-x.y);  // e1(tau), e1(-tau)
+                const float2 e = make_float2(ea, eb);
+                const float2 f = make_float2(eb * K, ea * K);  // e2(tau), e2(-tau)
+                const float2 t = __fadd2_rn(e, one2);
+                const float2 d = __ffma2_rn(t, f, t);
+                float2 r;
+                if (MPAIR) {
+                    const float R = rcpa(d.x * d.y);  // finite: see the scalar form
+                    r = make_float2(R * d.y, R * d.x);
+                } else {
+                    r = make_float2(rcpa(d.x), rcpa(d.y));
+                }
+                P2 = __ffma2_rn(cpm, r, P2);
+                M2 = __ffma2_rn(cmp, r, M2);
+                Z2 = __ffma2_rn(c00, r, Z2);
+                if (ADJ) {
+                    const float2 vu = make_float2(q.b.x, q.b.y);
+                    const float2 E2 = __ffma2_rn(h2, uv, Em2), Eb2 = __ffma2_rn(h2, vu, Em2);
+                    const float2 r2 = __fmul2_rn(r, r);
+                    const float2 s0 = __ffma2_rn(f, r2, r2), p = __fmul2_rn(t, r2);
+                    const float2 a1 = __fmul2_rn(e, s0), a2 = __fmul2_rn(f, p);
+                    const float2 ga = __ffma2_rn(a1, E2, __fmul2_rn(a2, Eb2));
+                    const float2 gp = __ffma2_rn(s0, E2, __fmul2_rn(p, Eb2));
+                    const float2 ge = __ffma2_rn(a1, mone2, a2);  // a2 - a1
+                    TAp = __ffma2_rn(cpm, ga, TAp); TAm = __ffma2_rn(cmp, ga, TAm); TAz = __ffma2_rn(c00, ga, TAz);
+                    TPp = __ffma2_rn(cpm, gp, TPp); TPm = __ffma2_rn(cmp, gp, TPm); TPz = __ffma2_rn(c00, gp, TPz);
+                    ETp = __ffma2_rn(cpm, ge, ETp); ETm = __ffma2_rn(cmp, ge, ETm); ETz = __ffma2_rn(c00, ge, ETz);
+                }
+            }
+        }
+        mo.p = P2.x + P2.y; mo.m = M2.x + M2.y; mo.z = Z2.x + Z2.y;
+        if (ADJ) {
+            ta.p = TAp.x + TAp.y; ta.m = TAm.x + TAm.y; ta.z = TAz.x + TAz.y;
+            tp.p = TPp.x + TPp.y; tp.m = TPm.x + TPm.y; tp.z = TPz.x + TPz.y;
+            et.p = ETp.x + ETp.y; et.m = ETm.x + ETm.y; et.z = ETz.x + ETz.y;
+        }
+    } else if (MIRROR) {
         static_assert(NE % U == 0 || NE == 0, "unrolled instantiations need a multiple of the unroll depth");
 #pragma unroll 1
         for (int k0 = 0; k0 < NE / 2; k0 += UM / 2) {
@@ -302,6 +365,7 @@ __global__ void __launch_bounds__(VX_TPB_MIXED, MINB) k_pair_mixed(const __grid_
     __shared__ ZoneSh zs;
     __shared__ long long s_zone;
     __shared__ NodeSm s_nodes[VX_MAX_NE];
+    __shared__ NodeMir s_mir[VX_MAX_NE / 2];
     __shared__ uint16_t s_pij[VX_MAX_PAIRS];
     const Common &C = L.c;
     const int N = C.N, S = C.S, N2 = N * N, npair = C.npair;
@@ -318,6 +382,11 @@ __global__ void __launch_bounds__(VX_TPB_MIXED, MINB) k_pair_mixed(const __grid_
     for (int k = tid; k < C.n_e; k += blockDim.x) {
         s_nodes[k].a = make_float4(L.n32.u[k], L.n32.v[k], L.n32.cp[k], L.n32.cm[k]);
         s_nodes[k].b = make_float4(L.n32.c0[k], L.n32.uh[k], L.n32.ul[k], 0.f);
+        if (k < C.n_e / 2) {
+            s_mir[k].a = make_float4(L.n32.u[k], L.n32.v[k], L.n32.cp[k], L.n32.cm[k]);
+            s_mir[k].b = make_float4(L.n32.v[k], L.n32.u[k], L.n32.cm[k], L.n32.cp[k]);
+            s_mir[k].c = make_float4(L.n32.c0[k], L.n32.c0[k], 0.f, 0.f);
+        }
     }
     for (int p = tid; p < npair; p += blockDim.x) s_pij[p] = C.pij[p];
 
@@ -467,7 +536,7 @@ __global__ void __launch_bounds__(VX_TPB_MIXED, MINB) k_pair_mixed(const __grid_
                 const float Pp = fmaf(Em, il_h, el_h);
                 if (!deg) {
                     const float Pe = fmaf(Em, il_h, -el_h);
-                    node_loop<NE, ADJ, false>(s_nodes, C.n_e, B, Pe, Pp, 0.f, 0.f, 0.f, 0.f, h, Em, 1.f, zs.K, 0.f, mo, ta, tp, et);
+                    node_loop<NE, ADJ, false>(s_nodes, s_mir, C.n_e, B, Pe, Pp, 0.f, 0.f, 0.f, 0.f, h, Em, 1.f, zs.K, 0.f, mo, ta, tp, et);
                     const Coef cf = make_coef(kp, km, k0, R1.w);
                     project(PO, mo, cf);
                     if (ADJ) {
@@ -492,7 +561,7 @@ __global__ void __launch_bounds__(VX_TPB_MIXED, MINB) k_pair_mixed(const __grid_
                     float Pq = __fmul_rn(rintf(__fmul_rn(s, zs.sP)), zs.iP);
                     float Pl = __fadd_rn(__fsub_rn(s, Pq), slo);
                     Pq = __fadd_rn(Pq, zs.sc);  // exact: an integer on the same grid
-                    node_loop<NE, ADJ, true>(s_nodes, C.n_e, B, 0.f, Pp, Bq, Bl, Pq, Pl, h, Em, zs.c1, zs.K2 * zs.p2sc, zs.K2, mo, ta, tp, et);
+                    node_loop<NE, ADJ, true>(s_nodes, s_mir, C.n_e, B, 0.f, Pp, Bq, Bl, Pq, Pl, h, Em, zs.c1, zs.K2 * zs.p2sc, zs.K2, mo, ta, tp, et);
                     const Coef cf = make_coef(kp, km, k0, R1.w);
                     project(PO, mo, cf);
                     if (ADJ) {
