@@ -14,7 +14,7 @@
 #define VX_MAX_PAIRS (VX_MAX_BINS * (VX_MAX_BINS + 1) / 2)
 #define VX_MAX_SPECIES 3
 #define VX_TPB_MAX 512    // FP64 kernel: threads per CTA (bin pairs)
-#define VX_TPB_MIXED 256  // mixed kernels: threads per CTA, two CTAs per SM; more pairs loop
+#define VX_TPB_MIXED 256  // mixed kernels: largest CTA the register budgets are compiled for
 #define VX_ETA_MAX 80.0
 
 // device numeric flag bits

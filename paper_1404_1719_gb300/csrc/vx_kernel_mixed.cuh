@@ -3,10 +3,11 @@
 //
 // Work decomposition. One CTA owns one zone at a time and pulls the next zone from a global
 // atomic counter (zones of all rays are concatenated; every zone costs the same node count, so
-// ragged rays need no special handling); two CTAs share an SM, so one's per-zone set-up and
-// contraction overlap the other's quadrature. Thread = unordered bin pair (i <= j): it loops
-// over the omega nodes and, inside, over the n_e electron-energy nodes, whose constants are
-// broadcast from shared memory.
+// ragged rays need no special handling); several CTAs share an SM (4 or 6 of 128 threads), so
+// one's per-zone set-up and contraction overlap the others' quadrature. The zone's
+// npair * n_omega (pair, omega) units are split into equal contiguous ranges, one per thread;
+// for each unit a thread loops over the n_e electron-energy nodes, whose constants are broadcast
+// from shared memory.
 //
 // Kernel algebra (exact rewrites of the definition; see the oracle for the definition itself).
 // With d = eps - eps', g = eps eps' (1 + cos w), |q|^2 = d^2 + 2 g, h = |q|/2, the electron energy
@@ -45,9 +46,12 @@
 #ifndef VX_F32X2
 #define VX_F32X2 1
 #endif
-// Nodes per unrolled chunk of the forward kernel's fast-path loop (a divisor of 16).
+// Nodes per unrolled chunk of the fast-path loop, forward and tangent kernels (divisors of 16).
 #ifndef VX_UNROLL_FWD
 #define VX_UNROLL_FWD 16
+#endif
+#ifndef VX_UNROLL_ADJ
+#define VX_UNROLL_ADJ 16
 #endif
 // Degenerate path: e2 from the mirror node's e1 (saves one ex2 per node, costs registers).
 #ifndef VX_DEG_MIRROR
@@ -144,7 +148,7 @@ __device__ __forceinline__ void node_loop(const NodeSm *__restrict__ nd, const N
     constexpr bool MIRROR = !DEG && NE > 0;
     constexpr bool MPAIR = !ADJ || VX_ADJ_PAIR;
     constexpr int U = 16;
-    constexpr int UM = ADJ ? U : VX_UNROLL_FWD;  // nodes per unrolled chunk of the mirror loop
+    constexpr int UM = ADJ ? VX_UNROLL_ADJ : VX_UNROLL_FWD;  // nodes per unrolled chunk of the mirror loop
     // tangent integrands of one node, accumulated with its basis weights (cp, cm, c0)
     auto tang = [&](float cp, float cm, float c0, float e1, float e2, float t, float r, float E, float Eb) {
         float ga, gp, ge;

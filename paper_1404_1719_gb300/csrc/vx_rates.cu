@@ -83,6 +83,14 @@ void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w) {
 
 int round_up(int a, int b) { return (a + b - 1) / b * b; }
 
+// Threads per CTA of the mixed kernels (at most VX_TPB_MIXED): the (pair, omega) units of a zone
+// are shared among them. 128 threads with 4 (or 6) CTAs per SM let the other CTAs' quadrature
+// cover one CTA's per-zone phases (GB300, workload 4 forward + Jacobian: 781 ms at 256, 773 ms
+// at 128, 778 ms at 64 threads; 16 x 48 quadrature: 1646, 1528, 1549 ms).
+#ifndef VX_BLOCK_MIXED
+#define VX_BLOCK_MIXED 128
+#endif
+
 }  // namespace
 
 struct vx_rates {
@@ -279,7 +287,7 @@ vx_status vx_rates_create(const vx_config *cfg, vx_rates **out) {
     C.ms = 1;
     h->ms = 1;
     h->block = round_up(np, 32);                           // FP64 kernel (<= 496 pairs)
-    h->block_mixed = std::min(round_up(np * nmu, 32), VX_TPB_MIXED);  // (pair, omega) units
+    h->block_mixed = std::min(round_up(np * nmu, 32), VX_BLOCK_MIXED);  // (pair, omega) units
 
     auto cleanup = [&](vx_status s) { vx_rates_destroy(h); return s; };
     cudaError_t ce = cudaGetDevice(&h->device);
@@ -861,7 +869,7 @@ vx_status vx_rates_eval_noalloc(const vx_config *cfg, const vx_batch *b, const v
     L.flag = reinterpret_cast<int *>(scratch + 8);
 
     const int ne = cfg->n_e, minb = 2;
-    const int block = std::min(round_up(L.c.npair * cfg->n_mu, 32), VX_TPB_MIXED);
+    const int block = std::min(round_up(L.c.npair * cfg->n_mu, 32), VX_BLOCK_MIXED);
     const size_t smem = vx::smem_mixed_bytes(cfg->n_bins, cfg->n_species, false, block);
     const void *fn = vx::kernel_mixed(false, minb, ne);
     VX_CU(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
