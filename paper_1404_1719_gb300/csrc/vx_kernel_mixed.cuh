@@ -46,6 +46,16 @@
 #ifndef VX_F32X2
 #define VX_F32X2 1
 #endif
+// Degenerate path: scalar (0), packed FP32x2 inline (1) or packed out of line (2), per kernel kind.
+// Out of line, the packed loop gets its own register allocation and leaves the fast path's alone
+// (GB300, tangent kernel: workload 4 773 / 781 / 772 ms, 16 x 48 eta <= 63 workload 1526 / 1410 /
+// 1388 ms for 0 / 1 / 2).
+#ifndef VX_DEG_PACK_ADJ
+#define VX_DEG_PACK_ADJ 2
+#endif
+#ifndef VX_DEG_PACK_FWD
+#define VX_DEG_PACK_FWD 1
+#endif
 // Nodes per unrolled chunk of the fast-path loop, forward and tangent kernels (divisors of 16).
 #ifndef VX_UNROLL_FWD
 #define VX_UNROLL_FWD 16
@@ -122,10 +132,84 @@ struct NodeSm {
     float4 a, b;
 };
 
-// The first n_e/2 nodes again, laid out for packed FP32x2 arithmetic on a mirror pair (tau, -tau):
-// a = {1+tau, 1-tau, w(1+tau)^2, w(1-tau)^2}, b = the same pairs swapped, c = {w(1-tau^2) twice}.
+// The first n_e/2 nodes again, laid out for packed FP32x2 arithmetic on a mirror pair (tau, -tau)
+// (lane x: node k, lane y: node n_e-1-k): a = {1+tau, 1-tau, w(1+tau)^2, w(1-tau)^2}, b = the same
+// pairs swapped, c = {w(1-tau^2) twice, uh of both nodes}, d = {ul of both nodes, 0, 0}, with uh
+// and ul the split of 1 + tau used by the degenerate path.
 struct NodeMir {
-    float4 a, b, c;
+    float4 a, b, c, d;
+};
+
+// Degenerate path, packed on mirror pairs: exact-split electron argument, direct positron argument,
+// first-order products with r (see node_loop), inline or as an out-of-line call (OUTLINE).
+template <int NE, bool ADJ, bool OUTLINE>
+struct DegPacked {
+    static __device__ __forceinline__ void body(const NodeMir *__restrict__ nm, float B, float Pp, float Bq, float Bl,
+                                                float Pq, float Pl, float h, float Em, float c1, Mom &mo, Mom &ta,
+                                                Mom &tp, Mom &et) {
+        constexpr int U = 16;
+        const float2 Bq2 = make_float2(Bq, Bq), Bl2 = make_float2(Bl, Bl), Pq2 = make_float2(Pq, Pq);
+        const float2 Pl2 = make_float2(Pl, Pl), B2 = make_float2(B, B), Pp2 = make_float2(Pp, Pp);
+        const float2 c12 = make_float2(c1, c1), h2 = make_float2(h, h), Em2 = make_float2(Em, Em);
+        const float2 mone2 = make_float2(-1.f, -1.f), z2 = make_float2(0.f, 0.f);
+        float2 P2 = z2, M2 = z2, Z2 = z2;
+        float2 TAp = z2, TAm = z2, TAz = z2, TPp = z2, TPm = z2, TPz = z2, ETp = z2, ETm = z2, ETz = z2;
+#pragma unroll 1
+        for (int k0 = 0; k0 < NE / 2; k0 += U / 2) {
+#pragma unroll
+            for (int kk = 0; kk < U / 2; ++kk) {
+                const NodeMir q = nm[k0 + kk];
+                const float2 u2 = make_float2(q.a.x, q.a.y), v2 = make_float2(q.b.x, q.b.y);
+                const float2 cpm = make_float2(q.a.z, q.a.w), cmp = make_float2(q.b.z, q.b.w);
+                const float2 c00 = make_float2(q.c.x, q.c.y);
+                const float2 sx = __ffma2_rn(Bq2, make_float2(q.c.z, q.c.w), Pq2);  // exact by the grid choice
+                const float2 lo = __ffma2_rn(Bq2, make_float2(q.d.x, q.d.y), __ffma2_rn(Bl2, u2, Pl2));
+                const float2 e1 = __fmul2_rn(make_float2(ex2a(-sx.x), ex2a(-sx.y)), make_float2(ex2a(-lo.x), ex2a(-lo.y)));
+                const float2 xp = __ffma2_rn(B2, v2, Pp2);
+                const float2 e2 = make_float2(ex2a(-xp.x), ex2a(-xp.y));
+                const float2 t = __fadd2_rn(c12, e1);
+                const float2 d = __ffma2_rn(t, e2, t);
+                const float2 r = make_float2(rcpa(d.x), rcpa(d.y));
+                P2 = __ffma2_rn(cpm, r, P2);
+                M2 = __ffma2_rn(cmp, r, M2);
+                Z2 = __ffma2_rn(c00, r, Z2);
+                if (ADJ) {
+                    const float2 qv = __ffma2_rn(e2, r, r);  // (1 + e2) r
+                    const float2 se = __fmul2_rn(c12, qv);   // 1 - f_e
+                    const float2 sp = __fmul2_rn(t, r);      // 1 - f_ebar
+                    const float2 fe = __fmul2_rn(e1, qv), fp = __fmul2_rn(e2, sp);
+                    const float2 E2 = __ffma2_rn(h2, u2, Em2), Eb2 = __ffma2_rn(h2, v2, Em2);
+                    const float2 ga = __fmul2_rn(__ffma2_rn(fe, E2, __fmul2_rn(fp, Eb2)), r);
+                    const float2 gp = __fmul2_rn(__ffma2_rn(se, E2, __fmul2_rn(sp, Eb2)), r);
+                    const float2 ge = __fmul2_rn(__ffma2_rn(fe, mone2, fp), r);
+                    TAp = __ffma2_rn(cpm, ga, TAp); TAm = __ffma2_rn(cmp, ga, TAm); TAz = __ffma2_rn(c00, ga, TAz);
+                    TPp = __ffma2_rn(cpm, gp, TPp); TPm = __ffma2_rn(cmp, gp, TPm); TPz = __ffma2_rn(c00, gp, TPz);
+                    ETp = __ffma2_rn(cpm, ge, ETp); ETm = __ffma2_rn(cmp, ge, ETm); ETz = __ffma2_rn(c00, ge, ETz);
+                }
+            }
+        }
+        mo.p = P2.x + P2.y; mo.m = M2.x + M2.y; mo.z = Z2.x + Z2.y;
+        if (ADJ) {
+            ta.p = TAp.x + TAp.y; ta.m = TAm.x + TAm.y; ta.z = TAz.x + TAz.y;
+            tp.p = TPp.x + TPp.y; tp.m = TPm.x + TPm.y; tp.z = TPz.x + TPz.y;
+            et.p = ETp.x + ETp.y; et.m = ETm.x + ETm.y; et.z = ETz.x + ETz.y;
+        }
+    }
+    static __device__ __noinline__ void outline(const NodeMir *__restrict__ nm, float B, float Pp, float Bq,
+                                                float Bl, float Pq, float Pl, float h, float Em, float c1, Mom *m4) {
+        body(nm, B, Pp, Bq, Bl, Pq, Pl, h, Em, c1, m4[0], m4[1], m4[2], m4[3]);
+    }
+    static __device__ __forceinline__ void run(const NodeMir *__restrict__ nm, float B, float Pp, float Bq, float Bl,
+                                               float Pq, float Pl, float h, float Em, float c1, Mom &mo, Mom &ta,
+                                               Mom &tp, Mom &et) {
+        if (OUTLINE) {
+            Mom m4[4];
+            outline(nm, B, Pp, Bq, Bl, Pq, Pl, h, Em, c1, m4);
+            mo = m4[0]; ta = m4[1]; tp = m4[2]; et = m4[3];
+        } else {
+            body(nm, B, Pp, Bq, Bl, Pq, Pl, h, Em, c1, mo, ta, tp, et);
+        }
+    }
 };
 
 // One (pair, omega) node loop. Fills the moments of the blocking factor O and, with ADJ, of
@@ -276,6 +360,9 @@ __device__ __forceinline__ void node_loop(const NodeSm *__restrict__ nd, const N
                 }
             }
         }
+    } else if (DEG && NE > 0 && VX_F32X2 && (ADJ ? VX_DEG_PACK_ADJ : VX_DEG_PACK_FWD)) {
+        DegPacked<NE, ADJ, (ADJ ? VX_DEG_PACK_ADJ : VX_DEG_PACK_FWD) == 2>::run(nm, B, Pp, Bq, Bl, Pq, Pl, h, Em, c1, mo,
+                                                                              ta, tp, et);
     } else if (NE > 0 && VX_DEG_MIRROR) {
         // degenerate path: e1 from the exact split on both nodes of a mirror pair, and
         // e2(tau) = e1(-tau) 2^sc e^{-2|eta|} as (e1(-tau) K) K2, K = 2^sc e^{-|eta|}, K2 = e^{-|eta|}
@@ -389,7 +476,9 @@ __global__ void __launch_bounds__(VX_TPB_MIXED, MINB) k_pair_mixed(const __grid_
         if (k < C.n_e / 2) {
             s_mir[k].a = make_float4(L.n32.u[k], L.n32.v[k], L.n32.cp[k], L.n32.cm[k]);
             s_mir[k].b = make_float4(L.n32.v[k], L.n32.u[k], L.n32.cm[k], L.n32.cp[k]);
-            s_mir[k].c = make_float4(L.n32.c0[k], L.n32.c0[k], 0.f, 0.f);
+            const int km = C.n_e - 1 - k;
+            s_mir[k].c = make_float4(L.n32.c0[k], L.n32.c0[k], L.n32.uh[k], L.n32.uh[km]);
+            s_mir[k].d = make_float4(L.n32.ul[k], L.n32.ul[km], 0.f, 0.f);
         }
     }
     for (int p = tid; p < npair; p += blockDim.x) s_pij[p] = C.pij[p];
