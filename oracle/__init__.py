@@ -54,7 +54,8 @@ def _load():
         lib.vxo_phi_zone.restype = None
         lib.vxo_eval.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _ip,
                                  ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_long,
-                                 _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, ctypes.c_int]
+                                 _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp,
+                                 ctypes.c_int]
         lib.vxo_eval.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -115,12 +116,14 @@ def phi_zone(eps, n_mu, n_e, T, eta, g2=1.0, boltzmann=False, grad=False, mag=Fa
 
 
 def evaluate(eps, n_mu, n_e, species, state, J, H, weights=None, sin2w=0.23, g2=1.0, norm=1.0,
-             phi=False, jac=False, mag=False, threads=0) -> dict:
+             phi=False, jac=False, spectral=False, mag=False, threads=0) -> dict:
     """Rates j0, chi0, j1, chi1 [Z][S][N] for every zone; optionally the K^I dump
-    phi [Z][dir][l][N][N], the Jacobian jac [Z][S][N][4 outputs][3 inputs T, eta, Y_e], and with
-    mag=True the magnitudes j1_abs, chi1_abs (phi_abs with phi=True, jac_abs with jac=True): the
-    same sums with every term replaced by its absolute value, which bound the rounding of results
-    whose terms change sign (the l = 1 projections and the derivatives)."""
+    phi [Z][dir][l][N][N], the Jacobian jac [Z][S][N][4 outputs][3 inputs T, eta, Y_e], the
+    spectral blocks dsrc [Z][S][4][N][N] (d j0/dJ, d chi0/dJ, d j1/dH, d chi1/dH of the partner
+    spectrum; see vxo_eval), and with mag=True the magnitudes j1_abs, chi1_abs (phi_abs, jac_abs,
+    dsrc_abs with the corresponding option): the same sums with every term replaced by its
+    absolute value, which bound the rounding of results whose terms change sign (the l = 1
+    projections and the derivatives)."""
     eps = _f64(eps)
     state = _f64(state)
     J, H = _f64(J), _f64(H)
@@ -135,12 +138,38 @@ def evaluate(eps, n_mu, n_e, species, state, J, H, weights=None, sin2w=0.23, g2=
         out[k] = np.empty((Z, S, n)) if mag else None
     out["phi_abs"] = np.empty((Z, 2, 2, n, n)) if (mag and phi) else None
     out["jac_abs"] = np.empty((Z, S, n, 4, 3)) if (mag and jac) else None
+    out["dsrc"] = np.empty((Z, S, 4, n, n)) if spectral else None
+    out["dsrc_abs"] = np.empty((Z, S, 4, n, n)) if (mag and spectral) else None
     w = None if weights is None else _f64(weights)
     used = _load().vxo_eval(n, _p(eps), _p(w), n_mu, n_e, S, species.ctypes.data_as(_ip), sin2w, g2, norm,
                             Z, _p(state), _p(J), _p(H), _p(out["j0"]), _p(out["chi0"]), _p(out["j1"]),
                             _p(out["chi1"]), _p(out["phi"]), _p(out["jac"]), _p(out["j1_abs"]),
-                            _p(out["chi1_abs"]), _p(out["phi_abs"]), _p(out["jac_abs"]), int(threads))
+                            _p(out["chi1_abs"]), _p(out["phi_abs"]), _p(out["jac_abs"]), _p(out["dsrc"]),
+                            _p(out["dsrc_abs"]), int(threads))
     if used < 0:
         raise ValueError("oracle rejected the arguments")
     out["threads"] = used
     return out
+
+
+def partner_indices(species) -> np.ndarray:
+    """Index, in the species list, of each species' partner spectrum: nu_e <-> anti-nu_e, nu_x with
+    itself (the pairing vx_oracle.c uses; -1 where the partner is absent)."""
+    sp = [int(x) for x in species]
+    want = {0: 1, 1: 0, 2: 2}
+    return np.array([sp.index(want[x]) if want[x] in sp else -1 for x in sp], dtype=np.int64)
+
+
+def spectral_vjp(dsrc, species, g_j0, g_chi0, g_j1, g_chi1):
+    """Vector-Jacobian product of seeds g_* [Z][S][N] with the spectral blocks dsrc [Z][S][4][N][N]:
+    grad_J, grad_H [Z][S][N], indexed by the spectrum (each species' rates read its partner's)."""
+    Z, S, _, N, _ = dsrc.shape
+    pk = partner_indices(species)
+    gJ = np.zeros((Z, S, N))
+    gH = np.zeros((Z, S, N))
+    for s in range(S):
+        gJ[:, pk[s], :] += np.einsum("zij,zi->zj", dsrc[:, s, 0], g_j0[:, s]) + \
+            np.einsum("zij,zi->zj", dsrc[:, s, 1], g_chi0[:, s])
+        gH[:, pk[s], :] += np.einsum("zij,zi->zj", dsrc[:, s, 2], g_j1[:, s]) + \
+            np.einsum("zij,zi->zj", dsrc[:, s, 3], g_chi1[:, s])
+    return gJ, gH

@@ -276,12 +276,18 @@ static int partner_index(int S, const int *species, int si)
 /* term replaced by its absolute value (|P_l|, |H|), which bound the rounding of a sum whose      */
 /* terms cancel; for the l = 0 outputs the terms never change sign. jacabs, like jac: the same    */
 /* for the derivatives, whose node terms can change sign as well.                                 */
+/* dsrc: NULL or [Z][S][4][N][N], the derivatives of the rates with respect to the partner       */
+/* spectrum they are contracted with (the rates are affine in J and linear in H):                */
+/*   [z][s][0][i][j] = d j0[z][s][i] / d J[z][p(s)][j],   [1] = d chi0 / d J,                    */
+/*   [2] = d j1 / d H[z][p(s)][j],   [3] = d chi1 / d H,   p(s) = the partner species' index.    */
+/* dsrcabs (like dsrc): the same with |P_l| in the omega sum (equal to |dsrc| for l = 0).        */
 /* Returns the number of threads used (>= 1), or -1 on a bad argument.                         */
 int vxo_eval(int n, const double *eps, const double *weights, int n_mu, int n_e,
              int n_species, const int *species, double sin2w, double g2, double norm,
              long Z, const double *state, const double *J, const double *H,
              double *j0, double *chi0, double *j1, double *chi1, double *phi_out, double *jac,
-             double *j1abs, double *chi1abs, double *phiabs_out, double *jacabs, int n_threads)
+             double *j1abs, double *chi1abs, double *phiabs_out, double *jacabs, double *dsrc,
+             double *dsrcabs, int n_threads)
 {
     if (n < 2 || n_mu < 1 || n_e < 1 || n_species < 1 || Z < 0 || !eps || !species) return -1;
     for (int k = 0; k < n_species; k++)
@@ -307,7 +313,7 @@ int vxo_eval(int n, const double *eps, const double *weights, int n_mu, int n_e,
 #endif
         double *phi = (double *)malloc(8 * NN * sizeof(double));
         double *dphi = jac ? (double *)malloc(16 * NN * sizeof(double)) : NULL;
-        int want_abs = j1abs || chi1abs || phiabs_out;
+        int want_abs = j1abs || chi1abs || phiabs_out || dsrcabs;
         double *pabs = want_abs ? (double *)malloc(8 * NN * sizeof(double)) : NULL;
         double *dpabs = (jac && jacabs) ? (double *)malloc(16 * NN * sizeof(double)) : NULL;
 #pragma omp for schedule(dynamic, 1)
@@ -331,6 +337,9 @@ int vxo_eval(int n, const double *eps, const double *weights, int n_mu, int n_e,
                 species_betas(sp, sin2w, &bI, &bII);
                 const double *Jp = J + ((size_t)z * S + pk) * N;
                 const double *Hp = H + ((size_t)z * S + pk) * N;
+                const double c0 = 2.0 * VXO_PI * norm, c1 = 6.0 * VXO_PI * norm;
+                double *D = dsrc ? dsrc + ((size_t)z * S + si) * 4 * NN : NULL;
+                double *Da = dsrcabs ? dsrcabs + ((size_t)z * S + si) * 4 * NN : NULL;
                 for (int i = 0; i < N; i++) {
                     double a_j0 = 0, a_c0 = 0, a_j1 = 0, a_c1 = 0, m_j1 = 0, m_c1 = 0;
                     double g[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
@@ -346,6 +355,18 @@ int vxo_eval(int n, const double *eps, const double *weights, int n_mu, int n_e,
                         a_c0 += w[j] * pa0 * Jp[j];
                         a_j1 += w[j] * pp1 * Hp[j];
                         a_c1 += w[j] * pa1 * Hp[j];
+                        if (D) { /* coefficients of (1 - J), J, H, H in the four sums above */
+                            D[0 * NN + ij] = -c0 * w[j] * pp0;
+                            D[1 * NN + ij] = c0 * w[j] * pa0;
+                            D[2 * NN + ij] = c1 * w[j] * pp1;
+                            D[3 * NN + ij] = c1 * w[j] * pa1;
+                        }
+                        if (Da) {
+                            Da[0 * NN + ij] = c0 * w[j] * fabs(pp0);
+                            Da[1 * NN + ij] = c0 * w[j] * fabs(pa0);
+                            Da[2 * NN + ij] = c1 * w[j] * (bI * PHI(pabs, 0, 0, 1, ij) + bII * PHI(pabs, 0, 1, 1, ij));
+                            Da[3 * NN + ij] = c1 * w[j] * (bI * PHI(pabs, 1, 0, 1, ij) + bII * PHI(pabs, 1, 1, 1, ij));
+                        }
                         if (pabs) {
                             m_j1 += w[j] * (bI * PHI(pabs, 0, 0, 1, ij) + bII * PHI(pabs, 0, 1, 1, ij)) * fabs(Hp[j]);
                             m_c1 += w[j] * (bI * PHI(pabs, 1, 0, 1, ij) + bII * PHI(pabs, 1, 1, 1, ij)) * fabs(Hp[j]);
@@ -369,7 +390,6 @@ int vxo_eval(int n, const double *eps, const double *weights, int n_mu, int n_e,
                             }
                     }
                     size_t o = ((size_t)z * S + si) * N + i;
-                    double c0 = 2.0 * VXO_PI * norm, c1 = 6.0 * VXO_PI * norm;
                     j0[o] = c0 * a_j0;
                     chi0[o] = c0 * a_c0;
                     j1[o] = c1 * a_j1;

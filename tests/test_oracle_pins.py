@@ -353,3 +353,83 @@ def test_magnitude_companions_bound_and_limit():
     out = oracle.evaluate(eps, 8, 8, [0, 1, 2], st, J, H, mag=True, jac=True)
     assert np.all(out["j1_abs"] >= np.abs(out["j1"])) and np.all(out["chi1_abs"] >= np.abs(out["chi1"]))
     assert np.all(out["jac_abs"] >= np.abs(out["jac"]) * (1 - 1e-14))
+
+
+# -------------------------------------------------------------- derivatives w.r.t. the spectra
+def _spectral_case(species=(0, 1, 2), zones=3, seed=5):
+    b = vx_inputs.make_batch(1, seed=seed)
+    st, J, H = b["state"][:zones], b["J"][:zones], b["H"][:zones]
+    sp = np.array(species, np.int32)
+    if len(sp) != J.shape[1]:
+        J, H = J[:, : len(sp)].copy(), H[:, : len(sp)].copy()
+    return b, st, J, H, sp
+
+
+def _ev(b, sp, st, J, H, **kw):
+    return oracle.evaluate(b["eps"], b["n_mu"], b["n_e"], sp, st, J, H, **kw)
+
+
+@pytest.mark.parametrize("species", [(0, 1, 2), (1, 0), (2,)])
+def test_spectral_blocks_are_the_affine_coefficients(species):
+    """The rates are affine in J (j0 through 1 - J, chi0 through J) and linear in H, so a
+    perturbation of the partner spectra changes them by exactly the blocks times the perturbation,
+    and j1 = D2 H, chi1 = D3 H, chi0 = D1 J, j0(J = 0) = -sum_j D0. These identities tie the blocks
+    to the forward rates (pinned above) and catch a wrong sign, factor, partner or transposition."""
+    b, st, J, H, sp = _spectral_case(species)
+    ref = _ev(b, sp, st, J, H, spectral=True)
+    D = ref["dsrc"]
+    pk = oracle.partner_indices(sp)
+    rng = np.random.default_rng(11)
+    dJ = rng.uniform(-0.2, 0.2, J.shape)
+    dH = rng.uniform(-0.2, 0.2, H.shape)
+    moved = _ev(b, sp, st, J + dJ, H + dH)
+    scale = lambda k: np.abs(ref[k]).max() + np.abs(moved[k]).max()
+    for s in range(len(sp)):
+        p = pk[s]
+        for k, o, dX in (("j0", 0, dJ), ("chi0", 1, dJ), ("j1", 2, dH), ("chi1", 3, dH)):
+            pred = np.einsum("zij,zj->zi", D[:, s, o], dX[:, p])
+            assert np.abs(moved[k][:, s] - ref[k][:, s] - pred).max() <= 1e-12 * scale(k), (k, s)
+        assert np.allclose(ref["chi0"][:, s], np.einsum("zij,zj->zi", D[:, s, 1], J[:, p]), rtol=1e-12, atol=0)
+        assert np.allclose(ref["j1"][:, s], np.einsum("zij,zj->zi", D[:, s, 2], H[:, p]), rtol=1e-11,
+                           atol=1e-13 * np.abs(ref["j1"]).max())
+        assert np.allclose(ref["chi1"][:, s], np.einsum("zij,zj->zi", D[:, s, 3], H[:, p]), rtol=1e-11,
+                           atol=1e-13 * np.abs(ref["chi1"]).max())
+    zero = _ev(b, sp, st, np.zeros_like(J), H)
+    assert np.allclose(zero["j0"], -D[:, :, 0].sum(axis=-1), rtol=1e-12, atol=0)
+    assert np.all(D[:, :, 0] <= 0) and np.all(D[:, :, 1] >= 0)
+
+
+def test_spectral_vjp_is_the_adjoint_of_the_perturbation():
+    """<g, f(J + dJ, H + dH) - f(J, H)> = <grad_J, dJ> + <grad_H, dH> for random seeds g: pins the
+    partner bookkeeping of the vector-Jacobian product against the forward oracle."""
+    b, st, J, H, sp = _spectral_case((1, 2, 0), zones=2, seed=9)
+    ref = _ev(b, sp, st, J, H, spectral=True)
+    rng = np.random.default_rng(3)
+    g = {k: rng.normal(size=J.shape) for k in ("j0", "chi0", "j1", "chi1")}
+    gJ, gH = oracle.spectral_vjp(ref["dsrc"], sp, g["j0"], g["chi0"], g["j1"], g["chi1"])
+    dJ = rng.uniform(-0.1, 0.1, J.shape)
+    dH = rng.uniform(-0.1, 0.1, H.shape)
+    moved = _ev(b, sp, st, J + dJ, H + dH)
+    lhs = sum(np.sum(g[k] * (moved[k] - ref[k])) for k in g)
+    rhs = np.sum(gJ * dJ) + np.sum(gH * dH)
+    mag = sum(np.sum(np.abs(g[k]) * (np.abs(moved[k]) + np.abs(ref[k]))) for k in g)
+    assert abs(lhs - rhs) <= 1e-12 * mag
+
+
+def test_spectral_blocks_exchange_symmetry_between_nu_e_and_anti_nu_e():
+    """The anti-neutrino's couplings are the neutrino's with (C_V + C_A)^2 and (C_V - C_A)^2
+    exchanged, and term II(i, j) is term I(j, i). So both species' chi0 blocks follow from the raw
+    term-I dump (pinned above through the zone kernel): nu_e uses beta_I Phi_I + beta_II Phi_I^T,
+    anti-nu_e beta_II Phi_I + beta_I Phi_I^T, each times 2 pi w_j."""
+    b, st, J, H, sp = _spectral_case((0, 1), zones=2, seed=4)
+    ref = _ev(b, sp, st, J, H, spectral=True, phi=True)
+    D, phi, w = ref["dsrc"], ref["phi"], oracle.energy_weights(b["eps"])
+    cv, ca = 0.5 + 2 * SIN2W, 0.5
+    bI, bII = (cv + ca) ** 2, (cv - ca) ** 2
+    c0 = 2.0 * math.pi
+    for z in range(st.shape[0]):
+        KI = phi[z, 1, 0]  # annihilation, l = 0, term I
+        k_nu = bI * KI + bII * KI.T
+        k_nubar = bII * KI + bI * KI.T
+        assert np.allclose(D[z, 0, 1], c0 * k_nu * w[None, :], rtol=1e-12, atol=0)
+        assert np.allclose(D[z, 1, 1], c0 * k_nubar * w[None, :], rtol=1e-12, atol=0)
