@@ -129,6 +129,25 @@ vx_status vx_rates_eval(vx_rates *h, const vx_batch *batch, const vx_out *out, v
 vx_status vx_rates_adjoint(vx_rates *h, const vx_batch *batch, const vx_out *grad_out,
                            double *jac, double *grad_state, const vx_out *fwd, vx_stream stream);
 
+/* Derivatives with respect to the partner spectra, which the rates are contracted with
+ * (sec. 2.1: emissivities and opacities from the kernel and the neutrino spectra). The rates are
+ * affine in J (j0 through 1 - J, chi0 through J) and linear in H (j1, chi1), so these are exact
+ * and independent of J and H; with the T / eta Jacobian of vx_rates_adjoint they are the
+ * zone's blocks of the Newton matrix of an implicit transport step (sec. 2.2). One pass of the
+ * forward kernel; any of the outputs may be NULL, not all:
+ *   blocks  device [Z][S][4][N][N]: [z][s][0][i][j] = d j0[z][s][i] / d J[z][p(s)][j],
+ *           [1] = d chi0 / d J, [2] = d j1 / d H[z][p(s)][j], [3] = d chi1 / d H, where p(s) is
+ *           the index (in config order) of the partner species whose spectrum species s reads
+ *           (nu_e <-> anti-nu_e, nu_x with itself)
+ *   grad_J, grad_H  device [Z][S][N], both or neither: vector-Jacobian product of grad_out with
+ *           the blocks, indexed by spectrum, i.e. d(sum_o <grad_out_o, o>)/d J and d/d H; needs
+ *           grad_out (NULL members count as 0)
+ *   fwd     forward rates of the same pass (its phi member must be NULL)
+ * Invalid zone states give NaN in every output of the zone and raise the device flag. Mixed
+ * precision only (VX_ERR_UNSUPPORTED for an FP64 handle). */
+vx_status vx_rates_spectral(vx_rates *h, const vx_batch *batch, const vx_out *grad_out, double *grad_J,
+                            double *grad_H, double *blocks, const vx_out *fwd, vx_stream stream);
+
 /* Synchronises `stream`, reads and clears the device numeric flag: VX_OK or VX_ERR_NUMERIC. */
 vx_status vx_rates_check(vx_rates *h, vx_stream stream);
 

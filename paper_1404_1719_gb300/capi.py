@@ -44,7 +44,7 @@ class VxError(RuntimeError):
 
 SYMBOLS = ("vx_rates_create", "vx_rates_eval", "vx_rates_adjoint", "vx_rates_check",
            "vx_rates_entries_per_zone", "vx_rates_destroy", "vx_status_string", "vx_last_error",
-           "vx_rates_eval_noalloc")
+           "vx_rates_eval_noalloc", "vx_rates_spectral")
 
 _lib = None
 
@@ -66,6 +66,9 @@ def lib(path: str | None = None):
     L.vx_rates_adjoint.argtypes = [ctypes.c_void_p, ctypes.POINTER(vx_batch), ctypes.POINTER(vx_out), ctypes.c_void_p,
                                    ctypes.c_void_p, ctypes.POINTER(vx_out), ctypes.c_void_p]
     L.vx_rates_adjoint.restype = ctypes.c_int
+    L.vx_rates_spectral.argtypes = [ctypes.c_void_p, ctypes.POINTER(vx_batch), ctypes.POINTER(vx_out), ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(vx_out), ctypes.c_void_p]
+    L.vx_rates_spectral.restype = ctypes.c_int
     L.vx_rates_check.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
     L.vx_rates_check.restype = ctypes.c_int
     L.vx_rates_entries_per_zone.argtypes = [ctypes.c_void_p]
@@ -119,6 +122,15 @@ def vx_rates_adjoint(h, batch: vx_batch, grad_out: vx_out | None, jac: int | Non
                                 ctypes.c_void_p(jac or 0), ctypes.c_void_p(grad_state or 0),
                                 ctypes.byref(fwd) if fwd is not None else None, ctypes.c_void_p(stream))
     _check(st, "vx_rates_adjoint")
+
+
+def vx_rates_spectral(h, batch: vx_batch, grad_out: vx_out | None, grad_J: int | None, grad_H: int | None,
+                      blocks: int | None, fwd: vx_out | None, stream: int = 0) -> None:
+    st = lib().vx_rates_spectral(h, ctypes.byref(batch), ctypes.byref(grad_out) if grad_out is not None else None,
+                                 ctypes.c_void_p(grad_J or 0), ctypes.c_void_p(grad_H or 0),
+                                 ctypes.c_void_p(blocks or 0), ctypes.byref(fwd) if fwd is not None else None,
+                                 ctypes.c_void_p(stream))
+    _check(st, "vx_rates_spectral")
 
 
 def vx_rates_check(h, stream: int = 0) -> int:

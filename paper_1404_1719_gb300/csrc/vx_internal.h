@@ -67,6 +67,7 @@ struct Launch {
     double *j0, *chi0, *j1, *chi1, *phi;
     double *jac, *grad_state;                   // adjoint outputs (may be NULL)
     const double *g_j0, *g_chi0, *g_j1, *g_chi1; // VJP seeds (may be NULL)
+    double *blocks, *grad_J, *grad_H;           // spectral derivatives (forward kernel; may be NULL)
     unsigned long long *counter;   // work counter, zeroed before every launch
     int *flag;                     // numeric flag (bits above)
 };

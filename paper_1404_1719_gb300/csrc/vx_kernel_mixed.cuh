@@ -562,6 +562,13 @@ __global__ void __launch_bounds__(VX_TPB_MIXED, MINB) k_pair_mixed(const __grid_
             if (L.phi)
                 for (int e = tid; e < 4 * N2; e += blockDim.x) L.phi[(size_t)z * 4 * N2 + e] = nan;
             if (ADJ && L.grad_state && tid < 4) L.grad_state[4 * z + tid] = nan;
+            if (!ADJ && L.blocks)
+                for (int e = tid; e < S * 4 * N2; e += blockDim.x) L.blocks[(size_t)z * S * 4 * N2 + e] = nan;
+            if (!ADJ && L.grad_J)
+                for (int e = tid; e < S * N; e += blockDim.x) {
+                    L.grad_J[(size_t)z * S * N + e] = nan;
+                    L.grad_H[(size_t)z * S * N + e] = nan;
+                }
             if (tid == 0) atomicOr(L.flag, VX_FLAG_BAD_STATE);
             __syncthreads();
             continue;
@@ -782,6 +789,39 @@ __global__ void __launch_bounds__(VX_TPB_MIXED, MINB) k_pair_mixed(const __grid_
                 L.grad_state[4 * z + 1] = b;
                 L.grad_state[4 * z + 2] = 0.0;
                 L.grad_state[4 * z + 3] = 0.0;
+            }
+        }
+        if (!ADJ && L.blocks) {
+            // d(rates)/d(partner spectrum): the coefficients of (1 - J), J, H, H in the contraction
+            // above, scaled in FP64 (production carries e^{-(eps_i + eps_j)/T} = sc[i] shv[j])
+            const int nb = 4 * N2;
+            for (int e = tid; e < S * nb; e += blockDim.x) {
+                const int s = e / nb, o = (e / N2) & 3, i = (e / N) % N, j = e % N;
+                const float *M = mats + (size_t)(o >> 1) * N2;
+                const float k = fmaf(C.bI[s], M[i * N + j], C.bII[s] * M[j * N + i]);
+                double f = ((o >> 1) ? c1 : c0) * C.w[j];
+                if ((o & 1) == 0) f *= (o == 0 ? -sc[i] : sc[i]) * shv[j];
+                L.blocks[(size_t)z * S * nb + e] = f * (double)k;
+            }
+        }
+        if (!ADJ && L.grad_J) {
+            // vector-Jacobian product with those coefficients, per spectrum q and bin j; spectrum q
+            // is read by species partner[q] (the pairing is an involution)
+            for (int e = tid; e < 2 * S * N; e += blockDim.x) {
+                const int hq = e / (S * N), q = (e / N) % S, j = e % N;
+                const int s = C.partner[q];
+                const float bI = C.bI[s], bII = C.bII[s];
+                const float *M = mats + (size_t)hq * N2;
+                const double *gp = hq ? L.g_j1 : L.g_j0, *ga = hq ? L.g_chi1 : L.g_chi0;
+                const size_t row = ((size_t)z * S + s) * N;
+                double sa = 0.0, sp = 0.0;  // annihilation and production sums over the species' bins i
+                for (int i = 0; i < N; ++i) {
+                    const double k = (double)fmaf(bI, M[i * N + j], bII * M[j * N + i]);
+                    if (ga) sa = fma(k, ga[row + i], sa);
+                    if (gp) sp = fma(k, gp[row + i] * sc[i], sp);
+                }
+                const double v = (hq ? c1 : c0) * C.w[j] * (hq ? sa + shv[j] * sp : sa - shv[j] * sp);
+                (hq ? L.grad_H : L.grad_J)[((size_t)z * S + q) * N + j] = v;
             }
         }
         if (L.phi) {  // raw kernel of term I, G2 applied: [dir][l][i][j]

@@ -452,6 +452,7 @@ static void fill_launch(const vx_rates *h, const vx_batch *b, vx::Launch &L) {
     L.j0 = L.chi0 = L.j1 = L.chi1 = L.phi = nullptr;
     L.jac = L.grad_state = nullptr;
     L.g_j0 = L.g_chi0 = L.g_j1 = L.g_chi1 = nullptr;
+    L.blocks = L.grad_J = L.grad_H = nullptr;
     L.counter = h->d_counter;
     L.flag = h->d_flag;
 }
@@ -569,7 +570,7 @@ vx_status vx_rates_eval(vx_rates *h, const vx_batch *b, const vx_out *out, vx_st
     cudaStream_t s = (cudaStream_t)stream;
     const bool graph = (h->cfg.flags & VX_USE_GRAPH) != 0;
     if (h->cfg.prec == VX_PREC_MIXED) {
-        vx::Launch L;
+        vx::Launch L{};
         fill_launch(h, b, L);
         L.j0 = out->j0; L.chi0 = out->chi0; L.j1 = out->j1; L.chi1 = out->chi1; L.phi = out->phi;
         if ((st = autotune(h, false, L, s)) != VX_OK) return st;
@@ -615,7 +616,7 @@ vx_status vx_rates_adjoint(vx_rates *h, const vx_batch *b, const vx_out *grad_ou
     }
     DeviceGuard dg(h->device);
     cudaStream_t s = (cudaStream_t)stream;
-    vx::Launch L;
+    vx::Launch L{};
     fill_launch(h, b, L);
     if (fwd) { L.j0 = fwd->j0; L.chi0 = fwd->chi0; L.j1 = fwd->j1; L.chi1 = fwd->chi1; }
     L.jac = jac;
@@ -628,6 +629,44 @@ vx_status vx_rates_adjoint(vx_rates *h, const vx_batch *b, const vx_out *grad_ou
         return launch_graph(h, 1, vx::kernel_mixed(true, mb, h->common.n_e), &L, grid, h->block_mixed, h->smem_adj, s);
     VX_CU(cudaMemsetAsync(h->d_counter, 0, sizeof(unsigned long long), s));
     VX_CU(vx::launch_mixed(true, mb, L, grid, h->block_mixed, h->smem_adj, s));
+    return VX_OK;
+}
+
+vx_status vx_rates_spectral(vx_rates *h, const vx_batch *b, const vx_out *grad_out, double *grad_J,
+                            double *grad_H, double *blocks, const vx_out *fwd, vx_stream stream) {
+    vx_status st = validate_batch(h, b);
+    if (st != VX_OK) return st;
+    if (h->cfg.prec != VX_PREC_MIXED) return fail(VX_ERR_UNSUPPORTED, "the spectral derivatives are provided for the mixed form");
+    if (!blocks && !grad_J && !grad_H && !fwd) return fail(VX_ERR_INVALID_ARG, "no output requested");
+    if (!grad_J != !grad_H) return fail(VX_ERR_INVALID_ARG, "grad_J and grad_H go together");
+    if (grad_J && !grad_out) return fail(VX_ERR_INVALID_ARG, "grad_J and grad_H need grad_out");
+    if (b->n_zones == 0) return VX_OK;
+    if (blocks && (st = check_device_ptr(blocks, "blocks")) != VX_OK) return st;
+    if (grad_J && (st = check_device_ptr(grad_J, "grad_J")) != VX_OK) return st;
+    if (grad_H && (st = check_device_ptr(grad_H, "grad_H")) != VX_OK) return st;
+    if (fwd && (st = validate_out(fwd, false)) != VX_OK) return st;
+    if (grad_J) {
+        const double *g[4] = {grad_out->j0, grad_out->chi0, grad_out->j1, grad_out->chi1};
+        const char *nm[4] = {"grad_out.j0", "grad_out.chi0", "grad_out.j1", "grad_out.chi1"};
+        for (int k = 0; k < 4; ++k)
+            if (g[k] && (st = check_device_ptr(g[k], nm[k])) != VX_OK) return st;
+    }
+    DeviceGuard dg(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    vx::Launch L{};
+    fill_launch(h, b, L);
+    if (fwd) { L.j0 = fwd->j0; L.chi0 = fwd->chi0; L.j1 = fwd->j1; L.chi1 = fwd->chi1; }
+    L.blocks = blocks;
+    L.grad_J = grad_J;
+    L.grad_H = grad_H;
+    if (grad_J) { L.g_j0 = grad_out->j0; L.g_chi0 = grad_out->chi0; L.g_j1 = grad_out->j1; L.g_chi1 = grad_out->chi1; }
+    if ((st = autotune(h, false, L, s)) != VX_OK) return st;
+    const int mb = h->minb[0];
+    int grid = (int)std::min<long long>(h->grid_mixed[0][mb - 2], b->n_zones);
+    if (h->cfg.flags & VX_USE_GRAPH)
+        return launch_graph(h, 0, vx::kernel_mixed(false, mb, h->common.n_e), &L, grid, h->block_mixed, h->smem_fwd, s);
+    VX_CU(cudaMemsetAsync(h->d_counter, 0, sizeof(unsigned long long), s));
+    VX_CU(vx::launch_mixed(false, mb, L, grid, h->block_mixed, h->smem_fwd, s));
     return VX_OK;
 }
 
@@ -857,7 +896,7 @@ vx_status vx_rates_eval_noalloc(const vx_config *cfg, const vx_batch *b, const v
     }
     unsigned char *scratch = g_noalloc_ptr[dev];
 
-    vx::Launch L;
+    vx::Launch L{};
     NoallocTab T;
     noalloc_params(cfg, L, T);
     L.tab32 = reinterpret_cast<const float4 *>(scratch + VX_NOALLOC_TABLE_OFFSET);

@@ -4,7 +4,8 @@ the computation runs in libvx_rates.
     rates = PairRates(eps, n_mu=32, n_e=64)                    # one handle per device/stream
     out = rates.evaluate(state, J, H)                           # dict of [Z][S][N] float64 tensors
     jac = rates.jacobian(state, J, H)                           # [Z][S][N][4][3]
-    j0, chi0, j1, chi1 = VxRatesFn.apply(rates, state, J, H)    # differentiable in `state`
+    blk = rates.spectral(state, J, H)["blocks"]                 # [Z][S][4][N][N], d rates / d(J, H)
+    j0, chi0, j1, chi1 = VxRatesFn.apply(rates, state, J, H)    # differentiable in state, J and H
 """
 from __future__ import annotations
 
@@ -122,6 +123,30 @@ class PairRates:
                               self._stream(stream))
         return res
 
+    def spectral(self, state, J, H, grad_out=None, blocks: bool = True, forward: bool = False,
+                 ray_offsets=None, stream=None) -> dict:
+        """Derivatives with respect to the partner spectra from one forward pass: blocks
+        [Z][S][4][N][N] (d j0/dJ, d chi0/dJ, d j1/dH, d chi1/dH of the spectrum each species reads)
+        and/or, for grad_out (dict of [Z][S][N] tensors), grad_J and grad_H [Z][S][N] indexed by
+        spectrum; forward=True adds the rates."""
+        Z = state.shape[0]
+        b = self._batch(state, J, H, ray_offsets)
+        res = {}
+        if blocks:
+            res["blocks"] = torch.empty((Z, self.S, 4, self.N, self.N), dtype=torch.float64, device=self.device)
+        g = None
+        if grad_out is not None:
+            g = capi.vx_out(*(_ptr(grad_out.get(k)) for k in _OUT_KEYS), None)
+            res["grad_J"] = torch.empty((Z, self.S, self.N), dtype=torch.float64, device=self.device)
+            res["grad_H"] = torch.empty((Z, self.S, self.N), dtype=torch.float64, device=self.device)
+        fwd = None
+        if forward:
+            res.update(self._alloc(Z))
+            fwd = capi.vx_out(*(_ptr(res[k]) for k in _OUT_KEYS), None)
+        capi.vx_rates_spectral(self._h, b, g, _ptr(res.get("grad_J")), _ptr(res.get("grad_H")), _ptr(res.get("blocks")),
+                               fwd, self._stream(stream))
+        return res
+
     def jacobian(self, state, J, H, **kw):
         return self.adjoint(state, J, H, jacobian=True, **kw)["jac"]
 
@@ -145,9 +170,9 @@ class PairRates:
 
 
 class VxRatesFn(torch.autograd.Function):
-    """(j0, chi0, j1, chi1) = f(state; J, H): forward through vx_rates_eval, backward through the
-    adjoint kernel in vector-Jacobian mode. Gradients flow to `state` (T, eta_e; the Y_e and rho
-    entries are zero for this process); J and H are treated as constants."""
+    """(j0, chi0, j1, chi1) = f(state, J, H): forward through vx_rates_eval; backward through the
+    adjoint kernel (state: T, eta_e; the Y_e and rho entries are zero for this process) and the
+    spectral kernel (J, H), each in vector-Jacobian mode and only for the inputs that need it."""
 
     @staticmethod
     def forward(ctx, rates: PairRates, state, J, H):
@@ -160,5 +185,11 @@ class VxRatesFn(torch.autograd.Function):
     def backward(ctx, *grads):
         state, J, H = ctx.saved_tensors
         g = {k: (gr.contiguous() if gr is not None else None) for k, gr in zip(_OUT_KEYS, grads)}
-        res = ctx.rates.adjoint(state, J, H, grad_out=g, jacobian=False)
-        return None, res["grad_state"], None, None
+        gs = gJ = gH = None
+        if ctx.needs_input_grad[1]:
+            gs = ctx.rates.adjoint(state, J, H, grad_out=g, jacobian=False)["grad_state"]
+        if ctx.needs_input_grad[2] or ctx.needs_input_grad[3]:
+            res = ctx.rates.spectral(state, J, H, grad_out=g, blocks=False)
+            gJ = res["grad_J"] if ctx.needs_input_grad[2] else None
+            gH = res["grad_H"] if ctx.needs_input_grad[3] else None
+        return None, gs, gJ, gH
