@@ -40,10 +40,12 @@ def entries(Z, N):
 
 
 # DRAM bytes (read + write) per zone of the forward + tangent kernel, from one ncu capture of the
-# 200-ray case of this workload (dram__bytes_read.sum + dram__bytes_write.sum = 89.4 + 586.5 MB
+# 200-ray case of this workload (dram__bytes_read.sum + dram__bytes_write.sum = 92.0 + 592.7 MB
 # for 80,000 zones); scaled to a launch by the zone count. Set to None whenever the kernel
 # changes, until it has been captured again.
-TRAFFIC_BYTES_PER_ZONE = None
+TRAFFIC_BYTES_PER_ZONE = 8559
+# rays of the default workload in --mode spectral (410k zones: 17 GB of blocks)
+SPECTRAL_RAYS = 1024
 
 
 def algorithmic_flops_per_node(adj: bool) -> int:
@@ -118,24 +120,24 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(sm)}
 
 
-def oracle_sample_rate(b, n_zones: int, jac: bool):
+def oracle_sample_rate(b, n_zones: int, jac: bool, spectral: bool = False):
     """Entries/s of the FP64 oracle on the first n_zones zones of a batch (all host threads)."""
     import oracle
     oracle.build()
     sl = slice(0, n_zones)
     t0 = time.perf_counter()
     out = oracle.evaluate(b["eps"], b["n_mu"], b["n_e"], b["species"], b["state"][sl], b["J"][sl], b["H"][sl],
-                          jac=jac)
+                          jac=jac, spectral=spectral)
     dt = time.perf_counter() - t0
     return entries(n_zones, len(b["eps"])) / dt, out["threads"], dt
 
 
-def cpu_baseline(target_s: float = 15.0, workload: int = WORKLOAD, jac: bool = True):
+def cpu_baseline(target_s: float = 15.0, workload: int = WORKLOAD, jac: bool = True, spectral: bool = False):
     b = vx_inputs.make_batch(workload, rays=[0, 1, 2, 3])
-    rate, thr, dt = oracle_sample_rate(b, 16, jac)
+    rate, thr, dt = oracle_sample_rate(b, 16, jac, spectral)
     n = int(min(len(b["state"]), max(16, 16 * target_s / max(dt, 1e-3))))
-    rate, thr, dt = oracle_sample_rate(b, n, jac)
-    what = "forward + Jacobian" if jac else "forward"
+    rate, thr, dt = oracle_sample_rate(b, n, jac, spectral)
+    what = "forward + Jacobian" if jac else ("forward + spectral blocks" if spectral else "forward")
     return {"value": rate, "unit": UNIT, "cores": thr, "kind": "oracle",
             "sample": f"first {n} zones of workload {workload} (rays 0-3), {what}, FP64, {dt:.1f} s"}
 
@@ -184,8 +186,11 @@ def run_ours(args):
     from paper_1404_1719_gb300 import PairRates, _build
     _build.build()
 
+    spec = args.mode == "spectral"
+    if spec and args.rays is None:
+        args.rays = SPECTRAL_RAYS  # the blocks are 42 KB per zone at 21 bins: bound the buffers
     b = rank_batch(rank, rays=None if args.rays is None else range(args.rays), workload=args.workload)
-    fwd_only = args.mode == "fwd"
+    fwd_only = args.mode != "fwd+jac"  # the forward kernel (with the spectral epilogue in "spectral")
     # the autotuner's choice is reported from its cache file
     tune_file = os.environ.get("VX_AUTOTUNE_CACHE") or os.path.join(
         os.environ.get("TMPDIR", "/tmp"), f"vx_bench_tune_{os.getpid()}.json")
@@ -196,13 +201,24 @@ def run_ours(args):
     rates = PairRates(b["eps"], b["n_mu"], b["n_e"], species=b["species"], graph=True, autotune=True)
     stream = torch.cuda.current_stream()
     out = {k: torch.empty((Z, S, N), dtype=torch.float64, device=dev) for k in ("j0", "chi0", "j1", "chi1")}
-    jac = torch.empty((Z, S, N, 4, 3) if args.mode != "fwd" else (1,), dtype=torch.float64, device=dev)
+    jac = torch.empty((Z, S, N, 4, 3) if not fwd_only else (1,), dtype=torch.float64, device=dev)
+    spec_out = {}
+    if spec:
+        spec_out = {"blocks": torch.empty((Z, S, 4, N, N), dtype=torch.float64, device=dev),
+                    "grad_J": torch.empty((Z, S, N), dtype=torch.float64, device=dev),
+                    "grad_H": torch.empty((Z, S, N), dtype=torch.float64, device=dev)}
+        seeds = torch.ones((Z, S, N), dtype=torch.float64, device=dev)
     from paper_1404_1719_gb300 import capi
     bt = rates._batch(d["state"], d["J"], d["H"], b["ray_offsets"])
     fwd = capi.vx_out(*(out[k].data_ptr() for k in ("j0", "chi0", "j1", "chi1")), None)
 
+    gout = capi.vx_out(*([seeds.data_ptr()] * 4), None) if spec else None
+
     def step():
-        if fwd_only:
+        if spec:
+            capi.vx_rates_spectral(rates.handle, bt, gout, spec_out["grad_J"].data_ptr(), spec_out["grad_H"].data_ptr(),
+                                   spec_out["blocks"].data_ptr(), fwd, stream.cuda_stream)
+        elif fwd_only:
             capi.vx_rates_eval(rates.handle, bt, fwd, stream.cuda_stream)
         else:
             capi.vx_rates_adjoint(rates.handle, bt, None, jac.data_ptr(), None, fwd, stream.cuda_stream)
@@ -231,6 +247,7 @@ def run_ours(args):
     e2e_steps = max(1, min(3, args.steps))
     h_out = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in out.items()}
     h_jac = torch.empty(jac.shape, dtype=jac.dtype, pin_memory=True)
+    h_spec = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in spec_out.items()}
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -244,12 +261,15 @@ def run_ours(args):
             h_out[k].copy_(out[k], non_blocking=True)
         if not fwd_only:
             h_jac.copy_(jac, non_blocking=True)
+        for k in spec_out:
+            h_spec[k].copy_(spec_out[k], non_blocking=True)
     a1.record(stream)
     torch.cuda.synchronize()
     ms_e2e = a0.elapsed_time(a1) / e2e_steps
     ms_e2e = max_over_ranks(ms_e2e, world, dist, dev)
     h2d = sum(v.numel() * v.element_size() for v in host.values())
     d2h = sum(v.numel() * v.element_size() for v in out.values()) + (0 if fwd_only else jac.numel() * jac.element_size())
+    d2h += sum(v.numel() * v.element_size() for v in spec_out.values())
 
     line = None
     if rank == 0:
@@ -290,7 +310,8 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": vx_inputs.WORKLOADS[args.workload]["name"]
-                       + (" forward (mixed)" if fwd_only else " forward+jacobian (mixed)")
+                       + (" forward+spectral derivatives (mixed; blocks, J/H VJP, rates)" if spec else
+                          " forward (mixed)" if fwd_only else " forward+jacobian (mixed)")
                        + ("" if args.rays is None else f" [first {args.rays} rays]"),
                        "zones": Z, "rays": int(len(b["ray_offsets"]) - 1), "bins": N,
                        "quadrature": f"{b['n_mu']}x{b['n_e']}", "species": S,
@@ -307,13 +328,16 @@ def run_ours(args):
                          "peak_note": f"FP32 {nsm} SMs x 128 FMA x 2 x {mhz:.0f} MHz (median SM clock in the run)",
                          "kernel": f"k_pair_mixed<{b['n_e']}, {kind}, {minb} CTAs/SM>"},
             "autotune": tune,
+            **({"hbm": {"algorithmic_bytes_per_step": h2d + d2h,
+                        "achieved_gbs": (h2d + d2h) / (ms_local / 1000) / 1e9,
+                        "note": "inputs read + rates, blocks and J/H gradients written, per step"}} if spec else {}),
             "fp64_fwd": {"value": v64, "unit": UNIT, "sample": f"first {sub} zones, plain FP64 forward only",
                          "ratio_mixed_fwd_adj_over_fp64_fwd": value / world / v64},
             "clocks": c,
             "numeric_ok": bool(ok),
         }
         if not args.no_cpu:
-            line["cpu_baseline"] = cpu_baseline(workload=args.workload, jac=not fwd_only)
+            line["cpu_baseline"] = cpu_baseline(workload=args.workload, jac=not fwd_only, spectral=spec)
         print(json.dumps(line))
     if world > 1:
         dist.barrier()
@@ -331,8 +355,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU-baseline leg")
     ap.add_argument("--workload", type=int, default=WORKLOAD, choices=sorted(vx_inputs.WORKLOADS),
                     help="synthetic workload (default 4: 4096 rays x 400 zones)")
-    ap.add_argument("--mode", choices=["fwd+jac", "fwd"], default="fwd+jac",
-                    help="step = forward + Jacobian pass (default) or forward rates only")
+    ap.add_argument("--mode", choices=["fwd+jac", "fwd", "spectral"], default="fwd+jac",
+                    help="step = forward + Jacobian pass (default), forward rates only, or forward + the "
+                         "derivatives with respect to the spectra (blocks and J/H VJP)")
     ap.add_argument("--rays", type=int, default=None,
                     help="use only the first R rays of the workload (small cases for profiling)")
     args = ap.parse_args()
