@@ -15,6 +15,13 @@
 #define VX_MAX_SPECIES 3
 #define VX_TPB_MAX 512    // FP64 kernel: threads per CTA (bin pairs)
 #define VX_TPB_MIXED 256  // mixed kernels: largest CTA the register budgets are compiled for
+// Threads per CTA of the mixed kernels (at most VX_TPB_MIXED): the (pair, omega) units of a zone
+// are shared among them. 128 threads with 4 to 6 CTAs per SM let the other CTAs' quadrature
+// cover one CTA's per-zone phases (GB300, workload 4 forward + Jacobian: 781 ms at 256, 773 ms
+// at 128, 778 ms at 64 threads; 16 x 48 quadrature: 1646, 1528, 1549 ms).
+#ifndef VX_BLOCK_MIXED
+#define VX_BLOCK_MIXED 128
+#endif
 #define VX_ETA_MAX 80.0
 
 // device numeric flag bits
@@ -98,7 +105,7 @@ __host__ __device__ inline size_t smem_mixed_bytes(int N, int S, bool adj, int b
 size_t smem_fp64(const Common &c);
 
 // Kernel launchers (return the launch error). n_e selects the unrolled instantiation; the mixed
-// kernels exist with register budgets for 2 and 3 CTAs per SM (minb).
+// kernels exist with two register budgets (minb 2: 128 registers; 3: 80 forward, 96 tangents).
 const void *kernel_mixed(bool adj, int minb, int n_e);
 cudaError_t launch_mixed(bool adj, int minb, const Launch &L, int grid, int block, size_t smem, cudaStream_t s);
 cudaError_t launch_fp64_fwd(const Launch64 &L, int grid, int block, size_t smem, cudaStream_t s);

@@ -46,6 +46,12 @@
 #ifndef VX_F32X2
 #define VX_F32X2 1
 #endif
+// The second register budget ("minb 3"): 3 CTAs of 256 threads (80 registers) for the forward
+// kernel; for the tangent kernel 640 threads per SM in CTAs of VX_BLOCK_MIXED (5 x 128: 96
+// registers). GB300, tangent kernel at 96 vs 80 registers: workload 4 764 vs 772 ms, 16 x 48
+// eta <= 63 workload 1377 vs 1388 ms; the forward kernel is faster at 80 (293 vs 296 ms).
+#define VX_LB3_THREADS_ADJ VX_BLOCK_MIXED
+#define VX_LB3_CTAS_ADJ (640 / VX_BLOCK_MIXED > 1 ? 640 / VX_BLOCK_MIXED : 1)
 // Degenerate path: scalar (0), packed FP32x2 inline (1) or packed out of line (2), per kernel kind.
 // Out of line, the packed loop gets its own register allocation and leaves the fast path's alone
 // (GB300, tangent kernel: workload 4 773 / 781 / 772 ms, 16 x 48 eta <= 63 workload 1526 / 1410 /
@@ -448,10 +454,13 @@ __device__ __forceinline__ Proj part_get(const float *part, int TB, int t, int s
     return P;
 }
 
-// MINB = CTAs per SM the register allocation must allow (2: up to 128 registers, 3: up to 80);
-// both are compiled and the autotuner picks per kernel kind and quadrature.
+// MINB selects one of two register budgets (2: up to 128 registers; 3: up to 80 for the forward
+// kernel, 96 for the tangent kernel); both are compiled and the autotuner picks per kernel kind
+// and quadrature.
 template <int NE, bool ADJ, int MINB>
-__global__ void __launch_bounds__(VX_TPB_MIXED, MINB) k_pair_mixed(const __grid_constant__ Launch L) {
+__global__ void __launch_bounds__(MINB == 3 ? (ADJ ? VX_LB3_THREADS_ADJ : VX_TPB_MIXED) : VX_TPB_MIXED,
+                                  MINB == 3 ? (ADJ ? VX_LB3_CTAS_ADJ : 3) : MINB)
+    k_pair_mixed(const __grid_constant__ Launch L) {
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ ZoneSh zs;
     __shared__ long long s_zone;

@@ -83,13 +83,6 @@ void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w) {
 
 int round_up(int a, int b) { return (a + b - 1) / b * b; }
 
-// Threads per CTA of the mixed kernels (at most VX_TPB_MIXED): the (pair, omega) units of a zone
-// are shared among them. 128 threads with 4 (or 6) CTAs per SM let the other CTAs' quadrature
-// cover one CTA's per-zone phases (GB300, workload 4 forward + Jacobian: 781 ms at 256, 773 ms
-// at 128, 778 ms at 64 threads; 16 x 48 quadrature: 1646, 1528, 1549 ms).
-#ifndef VX_BLOCK_MIXED
-#define VX_BLOCK_MIXED 128
-#endif
 
 }  // namespace
 
@@ -108,7 +101,7 @@ struct vx_rates {
     int *d_flag = nullptr;
     // launch shapes: one thread per bin pair; mixed kernels in two register budgets
     int ms = 1, block = 32, block_mixed = 32;
-    int grid_mixed[2][2] = {{0, 0}, {0, 0}};  // [forward, tangents][2 or 3 CTAs per SM]
+    int grid_mixed[2][2] = {{0, 0}, {0, 0}};  // [forward, tangents][larger, smaller register budget]
     int minb[2] = {2, 3};                      // chosen budget per kind (autotuned with VX_AUTOTUNE)
     bool tuned[2] = {false, false};
     float tune_ms[2][2] = {{0, 0}, {0, 0}};
@@ -458,7 +451,7 @@ static void fill_launch(const vx_rates *h, const vx_batch *b, vx::Launch &L) {
 }
 
 // ---- autotuner ------------------------------------------------------------------------------
-// Picks, per kernel kind, the register budget (2 or 3 CTAs per SM) that runs a sample of the
+// Picks, per kernel kind, the register budget (minb 2 or 3: see k_pair_mixed) that runs a sample of the
 // first batch fastest: the first zones of the batch, about 48 per CTA, each variant once to warm
 // up and once timed with CUDA events (four launches in all). The choice is kept in the handle and, when the environment
 // variable VX_AUTOTUNE_CACHE names a file, in that JSON file under a key of the quadrature, the
