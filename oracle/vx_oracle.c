@@ -38,6 +38,10 @@
  *   "Gauss-Laguerre in electron energy", but for fixed (eps, eps', omega) the electron energy
  *   lives on a finite interval where a Laguerre rule does not apply.
  *   O_p and O_a are evaluated independently, each from its own formula.
+ *   Split rule (the E-panel variant, an alternative discrete rule): where the Fermi edge of the
+ *   degenerate lepton lies inside (E-, E+), two Gauss-Legendre panels of n_e/2 nodes meet at it
+ *   (vxo_kernel_point_split). READING: the edge is the electron's, E = mu_e, for eta >= 0 and
+ *   the positron's, Ebar = -mu_e, for eta < 0 (the two cases are mirror images).
  *
  * Species (READING): nu_e uses couplings beta_I = (CV + CA)^2, beta_II = (CV - CA)^2 with
  * CV = 1/2 + 2 sin^2(theta_W), CA = 1/2 and partner spectrum anti-nu_e; anti-nu_e uses the
@@ -64,6 +68,8 @@
 #endif
 
 #define VXO_PI 3.14159265358979323846
+
+#define VXO_MAX_HALF 512 /* largest panel rule of the split form */
 
 /* ---------------------------------------------------------------------------------------- */
 /* Gauss-Legendre nodes (ascending) and weights on [-1, 1]: Newton iteration on P_n, using the */
@@ -139,77 +145,130 @@ static void species_betas(int species, double sin2w, double *bI, double *bII)
 /* X 0 = I, 1 = II; dK[dir][X][0] = d/dT, dK[dir][X][1] = d/deta.  G2 = 1 here.               */
 /* occ selects the statistics: 0 = Fermi-Dirac (the kernel); 1 = Boltzmann limit (O_p =        */
 /* exp(-q0/T), O_a = 1), used only to check the kinematics against the closed form.           */
+/* Kinematics of one point (eps, eps', y) and the electron-energy sums of one kernel point. */
+typedef struct {
+    double eps, epsp, q0, s, q, Ep, Em, kq, kpq, perp, Qk;
+} kin_t;
+
+typedef struct {
+    double sum[2][2], dsum[2][2][2], dabs[2][2][2];
+} acc_t;
+
+static void kin_init(double eps, double epsp, double y, kin_t *k)
+{
+    k->eps = eps;
+    k->epsp = epsp;
+    k->q0 = eps + epsp;
+    k->s = 2.0 * eps * epsp * y;
+    k->q = sqrt(k->q0 * k->q0 - k->s);
+    k->Ep = 0.5 * (k->q0 + k->q);
+    k->Em = k->s / (2.0 * (k->q0 + k->q));
+    k->kq = eps * (k->q0 - epsp * y);    /* k . q  */
+    k->kpq = epsp * (k->q0 - eps * y);   /* k' . q */
+    k->perp = eps * eps * epsp * epsp * y * (2.0 - y) / (k->q * k->q); /* |k_perp|^2 */
+    k->Qk = 0.5 * k->s;                  /* Q.k = Q.k' */
+}
+
+/* Adds one electron-energy node E with quadrature weight W (dE measure) to the sums. */
+static void node_add(const kin_t *k, double E, double W, double T, double eta, int occ, int want_d,
+                     int want_abs, acc_t *a)
+{
+    double Eb = k->q0 - E;
+    double xe = E / T - eta;
+    double xp = Eb / T + eta;
+    double Op = 1.0 / ((exp(xe) + 1.0) * (exp(xp) + 1.0));
+    double Oa = 1.0 / ((1.0 + exp(-xe)) * (1.0 + exp(-xp)));
+    if (occ == 1) { Op = exp(-k->q0 / T); Oa = 1.0; }
+    double Ec = (2.0 * k->q0 * E - k->s) / (2.0 * k->q);
+    double pk = E * k->eps - Ec * k->kq / k->q;     /* <p.k>  */
+    double pkp = E * k->epsp - Ec * k->kpq / k->q;  /* <p.k'> */
+    double half_sin2 = 0.5 * (E * E - Ec * Ec);
+    /* (a,b) = (k',k): <p.k'>(Q.k) - [<p.k'><p.k> + (E^2 - Ec^2)/2 (k'_perp.k_perp)] */
+    double MI = pkp * k->Qk - (pkp * pk - half_sin2 * k->perp);
+    /* (a,b) = (k,k'): <p.k>(Q.k') - [<p.k><p.k'> + (E^2 - Ec^2)/2 (k_perp.k'_perp)] */
+    double MII = pk * k->Qk - (pk * pkp - half_sin2 * k->perp);
+    a->sum[0][0] += W * Op * MI;
+    a->sum[0][1] += W * Op * MII;
+    a->sum[1][0] += W * Oa * MI;
+    a->sum[1][1] += W * Oa * MII;
+    if (want_d) {
+        double fe = 1.0 / (exp(xe) + 1.0);   /* electron occupation   */
+        double fp = 1.0 / (exp(xp) + 1.0);   /* positron occupation   */
+        /* dO_p/dT = O_p [(1-f_e) E + (1-f_ebar) Ebar]/T^2,  dO_p/deta = O_p (f_ebar - f_e) */
+        double dOpT = Op * ((1.0 - fe) * E + (1.0 - fp) * Eb) / (T * T);
+        double dOpe = Op * (fp - fe);
+        /* dO_a/dT = -O_a [f_e E + f_ebar Ebar]/T^2,      dO_a/deta = O_a (f_ebar - f_e) */
+        double dOaT = -Oa * (fe * E + fp * Eb) / (T * T);
+        double dOae = Oa * (fp - fe);
+        a->dsum[0][0][0] += W * dOpT * MI;  a->dsum[0][0][1] += W * dOpe * MI;
+        a->dsum[0][1][0] += W * dOpT * MII; a->dsum[0][1][1] += W * dOpe * MII;
+        a->dsum[1][0][0] += W * dOaT * MI;  a->dsum[1][0][1] += W * dOae * MI;
+        a->dsum[1][1][0] += W * dOaT * MII; a->dsum[1][1][1] += W * dOae * MII;
+        if (want_abs) { /* the same sums of absolute values: the rounding bound of each derivative */
+            a->dabs[0][0][0] += W * fabs(dOpT * MI);  a->dabs[0][0][1] += W * fabs(dOpe * MI);
+            a->dabs[0][1][0] += W * fabs(dOpT * MII); a->dabs[0][1][1] += W * fabs(dOpe * MII);
+            a->dabs[1][0][0] += W * fabs(dOaT * MI);  a->dabs[1][0][1] += W * fabs(dOae * MI);
+            a->dabs[1][1][0] += W * fabs(dOaT * MII); a->dabs[1][1][1] += W * fabs(dOae * MII);
+        }
+    }
+}
+
+static void kernel_finish(const kin_t *k, const acc_t *a, double *K, double *dK, double *dKabs)
+{
+    double pref = 2.0 * VXO_PI / (4.0 * k->q * k->eps * k->epsp);
+    for (int d = 0; d < 2; d++)
+        for (int X = 0; X < 2; X++) {
+            K[2 * d + X] = pref * a->sum[d][X];
+            if (dK) {
+                dK[(2 * d + X) * 2 + 0] = pref * a->dsum[d][X][0];
+                dK[(2 * d + X) * 2 + 1] = pref * a->dsum[d][X][1];
+            }
+            if (dKabs) {
+                dKabs[(2 * d + X) * 2 + 0] = pref * a->dabs[d][X][0];
+                dKabs[(2 * d + X) * 2 + 1] = pref * a->dabs[d][X][1];
+            }
+        }
+}
+
 void vxo_kernel_point(double eps, double epsp, double y, double T, double eta, int occ,
                       int n_e, const double *tE, const double *wE, double *K, double *dK,
                       double *dKabs)
 {
-    double q0 = eps + epsp;
-    double s = 2.0 * eps * epsp * y;
-    double q = sqrt(q0 * q0 - s);
-    double Ep = 0.5 * (q0 + q);
-    double Em = s / (2.0 * (q0 + q));
-    double kq = eps * (q0 - epsp * y);    /* k . q  */
-    double kpq = epsp * (q0 - eps * y);   /* k' . q */
-    double perp = eps * eps * epsp * epsp * y * (2.0 - y) / (q * q); /* |k_perp|^2 */
-    double Qk = 0.5 * s;                  /* Q.k = Q.k' */
-    double sum[2][2] = {{0, 0}, {0, 0}};
-    double dsum[2][2][2] = {{{0, 0}, {0, 0}}, {{0, 0}, {0, 0}}};
-    double dabs[2][2][2] = {{{0, 0}, {0, 0}}, {{0, 0}, {0, 0}}};
-    for (int k = 0; k < n_e; k++) {
-        double E = 0.5 * (Ep + Em) + 0.5 * (Ep - Em) * tE[k];
-        double W = 0.5 * (Ep - Em) * wE[k];
-        double Eb = q0 - E;
-        double xe = E / T - eta;
-        double xp = Eb / T + eta;
-        double Op = 1.0 / ((exp(xe) + 1.0) * (exp(xp) + 1.0));
-        double Oa = 1.0 / ((1.0 + exp(-xe)) * (1.0 + exp(-xp)));
-        if (occ == 1) { Op = exp(-q0 / T); Oa = 1.0; }
-        double Ec = (2.0 * q0 * E - s) / (2.0 * q);
-        double pk = E * eps - Ec * kq / q;     /* <p.k>  */
-        double pkp = E * epsp - Ec * kpq / q;  /* <p.k'> */
-        double half_sin2 = 0.5 * (E * E - Ec * Ec);
-        /* (a,b) = (k',k): <p.k'>(Q.k) - [<p.k'><p.k> + (E^2 - Ec^2)/2 (k'_perp.k_perp)] */
-        double MI = pkp * Qk - (pkp * pk - half_sin2 * perp);
-        /* (a,b) = (k,k'): <p.k>(Q.k') - [<p.k><p.k'> + (E^2 - Ec^2)/2 (k_perp.k'_perp)] */
-        double MII = pk * Qk - (pk * pkp - half_sin2 * perp);
-        sum[0][0] += W * Op * MI;
-        sum[0][1] += W * Op * MII;
-        sum[1][0] += W * Oa * MI;
-        sum[1][1] += W * Oa * MII;
-        if (dK) {
-            double fe = 1.0 / (exp(xe) + 1.0);   /* electron occupation   */
-            double fp = 1.0 / (exp(xp) + 1.0);   /* positron occupation   */
-            /* dO_p/dT = O_p [(1-f_e) E + (1-f_ebar) Ebar]/T^2,  dO_p/deta = O_p (f_ebar - f_e) */
-            double dOpT = Op * ((1.0 - fe) * E + (1.0 - fp) * Eb) / (T * T);
-            double dOpe = Op * (fp - fe);
-            /* dO_a/dT = -O_a [f_e E + f_ebar Ebar]/T^2,      dO_a/deta = O_a (f_ebar - f_e) */
-            double dOaT = -Oa * (fe * E + fp * Eb) / (T * T);
-            double dOae = Oa * (fp - fe);
-            dsum[0][0][0] += W * dOpT * MI;  dsum[0][0][1] += W * dOpe * MI;
-            dsum[0][1][0] += W * dOpT * MII; dsum[0][1][1] += W * dOpe * MII;
-            dsum[1][0][0] += W * dOaT * MI;  dsum[1][0][1] += W * dOae * MI;
-            dsum[1][1][0] += W * dOaT * MII; dsum[1][1][1] += W * dOae * MII;
-            if (dKabs) { /* the same sums of absolute values: the rounding bound of each derivative */
-                dabs[0][0][0] += W * fabs(dOpT * MI);  dabs[0][0][1] += W * fabs(dOpe * MI);
-                dabs[0][1][0] += W * fabs(dOpT * MII); dabs[0][1][1] += W * fabs(dOpe * MII);
-                dabs[1][0][0] += W * fabs(dOaT * MI);  dabs[1][0][1] += W * fabs(dOae * MI);
-                dabs[1][1][0] += W * fabs(dOaT * MII); dabs[1][1][1] += W * fabs(dOae * MII);
-            }
-        }
+    kin_t k;
+    acc_t a;
+    memset(&a, 0, sizeof a);
+    kin_init(eps, epsp, y, &k);
+    for (int i = 0; i < n_e; i++) {
+        double E = 0.5 * (k.Ep + k.Em) + 0.5 * (k.Ep - k.Em) * tE[i];
+        double W = 0.5 * (k.Ep - k.Em) * wE[i];
+        node_add(&k, E, W, T, eta, occ, dK != NULL, dKabs != NULL, &a);
     }
-    double pref = 2.0 * VXO_PI / (4.0 * q * eps * epsp);
-    for (int d = 0; d < 2; d++)
-        for (int X = 0; X < 2; X++) {
-            K[2 * d + X] = pref * sum[d][X];
-            if (dK) {
-                dK[(2 * d + X) * 2 + 0] = pref * dsum[d][X][0];
-                dK[(2 * d + X) * 2 + 1] = pref * dsum[d][X][1];
-            }
-            if (dKabs) {
-                dKabs[(2 * d + X) * 2 + 0] = pref * dabs[d][X][0];
-                dKabs[(2 * d + X) * 2 + 1] = pref * dabs[d][X][1];
-            }
-        }
+    kernel_finish(&k, &a, K, dK, dKabs);
+}
+
+/* The split rule (E-panel variant): if the Fermi edge of the degenerate lepton, E_s = mu_e for  */
+/* eta >= 0 (electron) and E_s = q0 + mu_e for eta < 0 (the positron's edge Ebar = -mu_e), lies */
+/* strictly inside (E-, E+), the interval is split there into two Gauss-Legendre panels, each    */
+/* with the n_h-node rule (tH, wH); otherwise the standard n_e-node rule (tE, wE) is used.       */
+void vxo_kernel_point_split(double eps, double epsp, double y, double T, double eta, int occ,
+                            int n_e, const double *tE, const double *wE, int n_h, const double *tH,
+                            const double *wH, double *K, double *dK, double *dKabs)
+{
+    kin_t k;
+    kin_init(eps, epsp, y, &k);
+    double Es = eta >= 0.0 ? eta * T : k.q0 + eta * T;
+    if (!(k.Em < Es && Es < k.Ep)) {
+        vxo_kernel_point(eps, epsp, y, T, eta, occ, n_e, tE, wE, K, dK, dKabs);
+        return;
+    }
+    acc_t a;
+    memset(&a, 0, sizeof a);
+    double hA = 0.5 * (Es - k.Em), hB = 0.5 * (k.Ep - Es);
+    for (int i = 0; i < n_h; i++) {
+        node_add(&k, Es - hA * (1.0 - tH[i]), hA * wH[i], T, eta, occ, dK != NULL, dKabs != NULL, &a);
+        node_add(&k, Es + hB * (1.0 + tH[i]), hB * wH[i], T, eta, occ, dK != NULL, dKabs != NULL, &a);
+    }
+    kernel_finish(&k, &a, K, dK, dKabs);
 }
 
 /* ---------------------------------------------------------------------------------------- */
@@ -219,9 +278,12 @@ void vxo_kernel_point(double eps, double epsp, double y, double T, double eta, i
 /* the l = 1 projection (whose terms change sign with cos(omega)); equal to phi for l = 0.       */
 void vxo_phi_zone(int n, const double *eps, int n_mu, const double *tmu, const double *wmu,
                   int n_e, const double *tE, const double *wE, double g2, double T, double eta,
-                  int occ, double *phi, double *dphi, double *phiabs, double *dphiabs)
+                  int occ, int split, double *phi, double *dphi, double *phiabs, double *dphiabs)
 {
     size_t NN = (size_t)n * n;
+    int n_h = n_e / 2;
+    double tH[VXO_MAX_HALF], wH[VXO_MAX_HALF];
+    if (split) vxo_gauss_legendre(n_h, tH, wH);
     memset(phi, 0, 8 * NN * sizeof(double));
     if (phiabs) memset(phiabs, 0, 8 * NN * sizeof(double));
     if (dphiabs) memset(dphiabs, 0, 16 * NN * sizeof(double));
@@ -231,8 +293,12 @@ void vxo_phi_zone(int n, const double *eps, int n_mu, const double *tmu, const d
             for (int m = 0; m < n_mu; m++) {
                 double y = 1.0 - tmu[m];
                 double K[4], dK[8], dKa[8];
-                vxo_kernel_point(eps[i], eps[j], y, T, eta, occ, n_e, tE, wE, K, dphi ? dK : NULL,
-                                 dphiabs ? dKa : NULL);
+                if (split)
+                    vxo_kernel_point_split(eps[i], eps[j], y, T, eta, occ, n_e, tE, wE, n_h, tH, wH, K,
+                                           dphi ? dK : NULL, dphiabs ? dKa : NULL);
+                else
+                    vxo_kernel_point(eps[i], eps[j], y, T, eta, occ, n_e, tE, wE, K, dphi ? dK : NULL,
+                                     dphiabs ? dKa : NULL);
                 for (int d = 0; d < 2; d++)
                     for (int X = 0; X < 2; X++)
                         for (int l = 0; l < 2; l++) {
@@ -281,15 +347,17 @@ static int partner_index(int S, const int *species, int si)
 /*   [z][s][0][i][j] = d j0[z][s][i] / d J[z][p(s)][j],   [1] = d chi0 / d J,                    */
 /*   [2] = d j1 / d H[z][p(s)][j],   [3] = d chi1 / d H,   p(s) = the partner species' index.    */
 /* dsrcabs (like dsrc): the same with |P_l| in the omega sum (equal to |dsrc| for l = 0).        */
+/* split: 0 = the standard discrete rule, 1 = the split rule (vxo_kernel_point_split; n_e even). */
 /* Returns the number of threads used (>= 1), or -1 on a bad argument.                         */
 int vxo_eval(int n, const double *eps, const double *weights, int n_mu, int n_e,
              int n_species, const int *species, double sin2w, double g2, double norm,
              long Z, const double *state, const double *J, const double *H,
              double *j0, double *chi0, double *j1, double *chi1, double *phi_out, double *jac,
              double *j1abs, double *chi1abs, double *phiabs_out, double *jacabs, double *dsrc,
-             double *dsrcabs, int n_threads)
+             double *dsrcabs, int split, int n_threads)
 {
     if (n < 2 || n_mu < 1 || n_e < 1 || n_species < 1 || Z < 0 || !eps || !species) return -1;
+    if (split && (n_e % 2 != 0 || n_e / 2 > VXO_MAX_HALF)) return -1;
     for (int k = 0; k < n_species; k++)
         if (species[k] < 0 || species[k] > 2 || partner_index(n_species, species, k) < 0) return -1;
     double *w = (double *)malloc(n * sizeof(double));
@@ -319,7 +387,7 @@ int vxo_eval(int n, const double *eps, const double *weights, int n_mu, int n_e,
 #pragma omp for schedule(dynamic, 1)
         for (long z = 0; z < Z; z++) {
             double T = state[4 * z + 0], eta = state[4 * z + 1];
-            vxo_phi_zone(N, eps, n_mu, tmu, wmu, n_e, tE, wE, g2, T, eta, 0, phi, dphi, pabs, dpabs);
+            vxo_phi_zone(N, eps, n_mu, tmu, wmu, n_e, tE, wE, g2, T, eta, 0, split, phi, dphi, pabs, dpabs);
             if (phiabs_out)
                 for (int d = 0; d < 2; d++)
                     for (int l = 0; l < 2; l++)
