@@ -198,7 +198,8 @@ def run_ours(args):
     Z, N, S = b["state"].shape[0], len(b["eps"]), len(b["species"])
     host = {k: torch.from_numpy(np.ascontiguousarray(b[k])).pin_memory() for k in ("state", "J", "H")}
     d = {k: v.to(dev) for k, v in host.items()}
-    rates = PairRates(b["eps"], b["n_mu"], b["n_e"], species=b["species"], graph=True, autotune=True)
+    split = args.quad == "split"
+    rates = PairRates(b["eps"], b["n_mu"], b["n_e"], species=b["species"], graph=True, autotune=True, split=split)
     stream = torch.cuda.current_stream()
     out = {k: torch.empty((Z, S, N), dtype=torch.float64, device=dev) for k in ("j0", "chi0", "j1", "chi1")}
     jac = torch.empty((Z, S, N, 4, 3) if not fwd_only else (1,), dtype=torch.float64, device=dev)
@@ -299,8 +300,8 @@ def run_ours(args):
         tune = {}
         try:
             with open(tune_file) as f:
-                tune = {k.split("kind=")[1].split(",")[0]: v for k, v in json.load(f).items()
-                        if f"N={N},n_mu={b['n_mu']},n_e={b['n_e']}," in k}
+                tune = {k.split("kind=")[1].split(",")[0].split("+")[0]: v for k, v in json.load(f).items()
+                        if f"N={N},n_mu={b['n_mu']},n_e={b['n_e']}," in k and ("+split" in k) == split}
         except (OSError, ValueError, IndexError):
             pass
         kind = "forward" if fwd_only else "tangents"
@@ -312,6 +313,7 @@ def run_ours(args):
             "config": {"workload": vx_inputs.WORKLOADS[args.workload]["name"]
                        + (" forward+spectral derivatives (mixed; blocks, J/H VJP, rates)" if spec else
                           " forward (mixed)" if fwd_only else " forward+jacobian (mixed)")
+                       + (", split rule" if split else "")
                        + ("" if args.rays is None else f" [first {args.rays} rays]"),
                        "zones": Z, "rays": int(len(b["ray_offsets"]) - 1), "bins": N,
                        "quadrature": f"{b['n_mu']}x{b['n_e']}", "species": S,
@@ -323,7 +325,7 @@ def run_ours(args):
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak,
                          "traffic": (TRAFFIC_BYTES_PER_ZONE * Z if (TRAFFIC_BYTES_PER_ZONE and args.workload == WORKLOAD
-                                                                    and not fwd_only) else None),
+                                                                    and not fwd_only and not split) else None),
                          "traffic_note": "ncu DRAM read+write of an 80,000-zone capture, scaled by zone count",
                          "peak_note": f"FP32 {nsm} SMs x 128 FMA x 2 x {mhz:.0f} MHz (median SM clock in the run)",
                          "kernel": f"k_pair_mixed<{b['n_e']}, {kind}, {minb} CTAs/SM>"},
@@ -358,6 +360,8 @@ def main():
     ap.add_argument("--mode", choices=["fwd+jac", "fwd", "spectral"], default="fwd+jac",
                     help="step = forward + Jacobian pass (default), forward rates only, or forward + the "
                          "derivatives with respect to the spectra (blocks and J/H VJP)")
+    ap.add_argument("--quad", choices=["standard", "split"], default="standard",
+                    help="discrete rule in electron energy: standard, or split at the Fermi edge (VX_QUAD_SPLIT)")
     ap.add_argument("--rays", type=int, default=None,
                     help="use only the first R rays of the workload (small cases for profiling)")
     args = ap.parse_args()

@@ -69,6 +69,13 @@ typedef enum { VX_NU_E = 0, VX_NU_EBAR = 1, VX_NU_X = 2 } vx_species;
 #define VX_AUTOTUNE 2u  /* pick launch shapes by timing them on the first batch; cached on disk
                            in the JSON file named by the environment variable VX_AUTOTUNE_CACHE
                            (default: no file)                                                   */
+#define VX_QUAD_SPLIT 4u /* split discrete rule in electron energy: in zones with |eta_e| >
+                            eta_fp64, where the Fermi edge of the degenerate lepton (E = mu_e
+                            for eta >= 0, Ebar = -mu_e for eta < 0) lies inside (E-, E+), two
+                            Gauss-Legendre panels of n_e/2 nodes meet at it; elsewhere the
+                            standard n_e-node rule. It converges much faster at high
+                            degeneracy. n_e must be even; mixed precision only
+                            (VX_ERR_UNSUPPORTED with VX_PREC_FP64)                           */
 
 typedef struct {
     int n_bins;             /* N, 2..31 energy bins                                           */

@@ -53,12 +53,12 @@ def _load():
         lib.vxo_kernel_point_split.restype = None
         lib.vxo_phi_zone.argtypes = [ctypes.c_int, _dp, ctypes.c_int, _dp, _dp, ctypes.c_int, _dp, _dp,
                                      ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
-                                     ctypes.c_int, _dp, _dp, _dp, _dp]
+                                     ctypes.c_int, ctypes.c_double, _dp, _dp, _dp, _dp]
         lib.vxo_phi_zone.restype = None
         lib.vxo_eval.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _ip,
                                  ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_long,
                                  _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp,
-                                 ctypes.c_int, ctypes.c_int]
+                                 ctypes.c_int, ctypes.c_double, ctypes.c_int]
         lib.vxo_eval.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -108,7 +108,8 @@ def kernel_point(eps, epsp, y, T, eta, n_e, boltzmann=False, grad=False, split=F
     return (K.reshape(2, 2), dK.reshape(2, 2, 2)) if grad else K.reshape(2, 2)
 
 
-def phi_zone(eps, n_mu, n_e, T, eta, g2=1.0, boltzmann=False, grad=False, mag=False, split=False):
+def phi_zone(eps, n_mu, n_e, T, eta, g2=1.0, boltzmann=False, grad=False, mag=False, split=False,
+             eta_split=20.0):
     """Phi^dir_{l,X}(i,j) of one zone: array [dir][X][l][i][j] (and [.., 2] gradients); mag=True
     returns instead the same sums with |P_l| (the magnitude bounding the l = 1 rounding)."""
     eps = _f64(eps)
@@ -119,7 +120,8 @@ def phi_zone(eps, n_mu, n_e, T, eta, g2=1.0, boltzmann=False, grad=False, mag=Fa
     dphi = np.empty(16 * n * n) if grad else None
     pabs = np.empty(8 * n * n) if mag else None
     _load().vxo_phi_zone(n, _p(eps), n_mu, _p(tmu), _p(wmu), n_e, _p(tE), _p(wE), float(g2), float(T),
-                         float(eta), int(boltzmann), int(split), _p(phi), _p(dphi), _p(pabs), None)
+                         float(eta), int(boltzmann), int(split), float(eta_split), _p(phi), _p(dphi), _p(pabs),
+                         None)
     if mag:
         return pabs.reshape(2, 2, 2, n, n)
     phi = phi.reshape(2, 2, 2, n, n)
@@ -127,14 +129,15 @@ def phi_zone(eps, n_mu, n_e, T, eta, g2=1.0, boltzmann=False, grad=False, mag=Fa
 
 
 def evaluate(eps, n_mu, n_e, species, state, J, H, weights=None, sin2w=0.23, g2=1.0, norm=1.0,
-             phi=False, jac=False, spectral=False, mag=False, split=False, threads=0) -> dict:
+             phi=False, jac=False, spectral=False, mag=False, split=False, eta_split=20.0, threads=0) -> dict:
     """Rates j0, chi0, j1, chi1 [Z][S][N] for every zone; optionally the K^I dump
     phi [Z][dir][l][N][N], the Jacobian jac [Z][S][N][4 outputs][3 inputs T, eta, Y_e], the
     spectral blocks dsrc [Z][S][4][N][N] (d j0/dJ, d chi0/dJ, d j1/dH, d chi1/dH of the partner
     spectrum; see vxo_eval), and with mag=True the magnitudes j1_abs, chi1_abs (phi_abs, jac_abs,
     dsrc_abs with the corresponding option): the same sums with every term replaced by its
     absolute value, which bound the rounding of results whose terms change sign (the l = 1
-    projections and the derivatives). split=True selects the split discrete rule (n_e even)."""
+    projections and the derivatives). split=True selects the split discrete rule (n_e even) in
+    zones with |eta| > eta_split (20, the GPU's default precision switch)."""
     eps = _f64(eps)
     state = _f64(state)
     J, H = _f64(J), _f64(H)
@@ -156,7 +159,7 @@ def evaluate(eps, n_mu, n_e, species, state, J, H, weights=None, sin2w=0.23, g2=
                             Z, _p(state), _p(J), _p(H), _p(out["j0"]), _p(out["chi0"]), _p(out["j1"]),
                             _p(out["chi1"]), _p(out["phi"]), _p(out["jac"]), _p(out["j1_abs"]),
                             _p(out["chi1_abs"]), _p(out["phi_abs"]), _p(out["jac_abs"]), _p(out["dsrc"]),
-                            _p(out["dsrc_abs"]), int(bool(split)), int(threads))
+                            _p(out["dsrc_abs"]), int(bool(split)), float(eta_split), int(threads))
     if used < 0:
         raise ValueError("oracle rejected the arguments")
     out["threads"] = used

@@ -38,10 +38,13 @@
  *   "Gauss-Laguerre in electron energy", but for fixed (eps, eps', omega) the electron energy
  *   lives on a finite interval where a Laguerre rule does not apply.
  *   O_p and O_a are evaluated independently, each from its own formula.
- *   Split rule (the E-panel variant, an alternative discrete rule): where the Fermi edge of the
- *   degenerate lepton lies inside (E-, E+), two Gauss-Legendre panels of n_e/2 nodes meet at it
- *   (vxo_kernel_point_split). READING: the edge is the electron's, E = mu_e, for eta >= 0 and
- *   the positron's, Ebar = -mu_e, for eta < 0 (the two cases are mirror images).
+ *   Split rule (the E-panel variant, an alternative discrete rule): in zones with |eta| above a
+ *   threshold eta_split, where the Fermi edge of the degenerate lepton lies inside (E-, E+), two
+ *   Gauss-Legendre panels of n_e/2 nodes meet at it (vxo_kernel_point_split); elsewhere the
+ *   standard rule. READING: the edge is the electron's, E = mu_e, for eta >= 0 and the
+ *   positron's, Ebar = -mu_e, for eta < 0 (the two cases are mirror images). The threshold
+ *   (default 20, the GPU's precision switch) keeps the standard rule in cold, mildly degenerate
+ *   zones, where half the nodes on a panel that spans ~100 T of Boltzmann tail do worse.
  *
  * Species (READING): nu_e uses couplings beta_I = (CV + CA)^2, beta_II = (CV - CA)^2 with
  * CV = 1/2 + 2 sin^2(theta_W), CA = 1/2 and partner spectrum anti-nu_e; anti-nu_e uses the
@@ -278,11 +281,13 @@ void vxo_kernel_point_split(double eps, double epsp, double y, double T, double 
 /* the l = 1 projection (whose terms change sign with cos(omega)); equal to phi for l = 0.       */
 void vxo_phi_zone(int n, const double *eps, int n_mu, const double *tmu, const double *wmu,
                   int n_e, const double *tE, const double *wE, double g2, double T, double eta,
-                  int occ, int split, double *phi, double *dphi, double *phiabs, double *dphiabs)
+                  int occ, int split, double eta_split, double *phi, double *dphi, double *phiabs,
+                  double *dphiabs)
 {
     size_t NN = (size_t)n * n;
     int n_h = n_e / 2;
     double tH[VXO_MAX_HALF], wH[VXO_MAX_HALF];
+    split = split && fabs(eta) > eta_split;
     if (split) vxo_gauss_legendre(n_h, tH, wH);
     memset(phi, 0, 8 * NN * sizeof(double));
     if (phiabs) memset(phiabs, 0, 8 * NN * sizeof(double));
@@ -347,14 +352,15 @@ static int partner_index(int S, const int *species, int si)
 /*   [z][s][0][i][j] = d j0[z][s][i] / d J[z][p(s)][j],   [1] = d chi0 / d J,                    */
 /*   [2] = d j1 / d H[z][p(s)][j],   [3] = d chi1 / d H,   p(s) = the partner species' index.    */
 /* dsrcabs (like dsrc): the same with |P_l| in the omega sum (equal to |dsrc| for l = 0).        */
-/* split: 0 = the standard discrete rule, 1 = the split rule (vxo_kernel_point_split; n_e even). */
+/* split: 0 = the standard discrete rule, 1 = the split rule (vxo_kernel_point_split; n_e even) */
+/* in zones with |eta| > eta_split.                                                              */
 /* Returns the number of threads used (>= 1), or -1 on a bad argument.                         */
 int vxo_eval(int n, const double *eps, const double *weights, int n_mu, int n_e,
              int n_species, const int *species, double sin2w, double g2, double norm,
              long Z, const double *state, const double *J, const double *H,
              double *j0, double *chi0, double *j1, double *chi1, double *phi_out, double *jac,
              double *j1abs, double *chi1abs, double *phiabs_out, double *jacabs, double *dsrc,
-             double *dsrcabs, int split, int n_threads)
+             double *dsrcabs, int split, double eta_split, int n_threads)
 {
     if (n < 2 || n_mu < 1 || n_e < 1 || n_species < 1 || Z < 0 || !eps || !species) return -1;
     if (split && (n_e % 2 != 0 || n_e / 2 > VXO_MAX_HALF)) return -1;
@@ -387,7 +393,8 @@ int vxo_eval(int n, const double *eps, const double *weights, int n_mu, int n_e,
 #pragma omp for schedule(dynamic, 1)
         for (long z = 0; z < Z; z++) {
             double T = state[4 * z + 0], eta = state[4 * z + 1];
-            vxo_phi_zone(N, eps, n_mu, tmu, wmu, n_e, tE, wE, g2, T, eta, 0, split, phi, dphi, pabs, dpabs);
+            vxo_phi_zone(N, eps, n_mu, tmu, wmu, n_e, tE, wE, g2, T, eta, 0, split, eta_split, phi, dphi, pabs,
+                         dpabs);
             if (phiabs_out)
                 for (int d = 0; d < 2; d++)
                     for (int l = 0; l < 2; l++)

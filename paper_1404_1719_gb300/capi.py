@@ -13,7 +13,7 @@ from . import _build
 VX_OK, VX_ERR_INVALID_ARG, VX_ERR_CUDA, VX_ERR_OOM, VX_ERR_NUMERIC, VX_ERR_UNSUPPORTED, VX_ERR_TIMEOUT = range(7)
 VX_PREC_FP64, VX_PREC_MIXED = 0, 1
 VX_NU_E, VX_NU_EBAR, VX_NU_X = 0, 1, 2
-VX_USE_GRAPH, VX_AUTOTUNE = 1, 2
+VX_USE_GRAPH, VX_AUTOTUNE, VX_QUAD_SPLIT = 1, 2, 4
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int)

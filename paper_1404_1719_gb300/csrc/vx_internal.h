@@ -39,6 +39,8 @@ struct Nodes32 {
     float c0[VX_MAX_NE];  // w_k (1 - tau_k^2)
     float uh[VX_MAX_NE];  // 1 + tau_k rounded to a multiple of 2^-11
     float ul[VX_MAX_NE];  // (1 + tau_k) - uh
+    // the n_e/2-node rule of the split form's panels: 1 + x_k, 1 - x_k, w_k
+    float hp[VX_MAX_NE / 2], hm[VX_MAX_NE / 2], hw[VX_MAX_NE / 2];
 };
 
 struct Nodes64 {
@@ -60,6 +62,7 @@ struct Common {
     double t64[VX_MAX_MU];
     double g2, norm, eta_sw;
     double h_max, q0h_max;         // max half-width |q|/2 and max q0/2 over the pair table
+    int split;                     // split discrete rule (VX_QUAD_SPLIT)
 };
 
 // One launch: the handle constants plus the batch.
@@ -104,15 +107,16 @@ __host__ __device__ inline size_t smem_mixed_bytes(int N, int S, bool adj, int b
 }
 size_t smem_fp64(const Common &c);
 
-// Kernel launchers (return the launch error). n_e selects the unrolled instantiation; the mixed
+// Kernel launchers (return the launch error). n_e selects the unrolled instantiation and split the
+// instantiations with the split rule (launch_mixed reads it from L.c.split); the mixed
 // kernels exist with two register budgets (minb 2: 128 registers; 3: 80 forward, 96 tangents).
-const void *kernel_mixed(bool adj, int minb, int n_e);
+const void *kernel_mixed(bool adj, int minb, int n_e, bool split);
 cudaError_t launch_mixed(bool adj, int minb, const Launch &L, int grid, int block, size_t smem, cudaStream_t s);
 cudaError_t launch_fp64_fwd(const Launch64 &L, int grid, int block, size_t smem, cudaStream_t s);
 const void *kernel_fp64_fwd(int n_e);
 
 #define VX_DECL_MIXED(sfx)                                                                            \
-    const void *kernel_mixed_##sfx(int n_e);                                                          \
+    const void *kernel_mixed_##sfx(int n_e, bool split);                                              \
     cudaError_t launch_mixed_##sfx(const Launch &L, int grid, int block, size_t smem, cudaStream_t s);
 VX_DECL_MIXED(fwd_b2)
 VX_DECL_MIXED(fwd_b3)

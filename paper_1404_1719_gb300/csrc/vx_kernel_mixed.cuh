@@ -118,6 +118,7 @@ struct ZoneSh {
     float c1;          //   blocked nodes of the zone far from the FP32 underflow); c1 = 2^-sc
     float K, K2;       // e2 on a node from e1 on its mirror node: K = e^{-2|eta|}, K2 = e^{-|eta|}
     float p2sc;        // 2^sc
+    float mu_hi, mu_lo;  // |eta| T, the Fermi edge of the split rule, as an FP32 pair
     double unsc;       // 2^-sc, applied in FP64 to every result of the zone
     double iT2;        // 1/T^2
     int sv;            // production vectors carried as v 2^sv (degenerate zones); the two scales
@@ -217,6 +218,93 @@ struct DegPacked {
         }
     }
 };
+
+// Split rule, one (pair, omega) unit whose Fermi edge E_s lies inside (E-, E+): panels
+// A = [E-, E_s] and B = [E_s, E+] share the n_e/2-node rule; lane x of every float2 is panel A's
+// node, lane y panel B's. With rA = (E_s - E-)/(2h) and rB = 1 - rA, a node x of the rule sits at
+// 1 + tau = rA (1 + x) (A) or 2 rA + rB (1 + x) (B) of the full interval, with weight r_P w, so the
+// moment basis and the (pair, omega) coefficients are those of the standard rule. The electron
+// argument X = (E - mu) log2(e)/T is formed relative to the edge: -rA B (1 - x) or rB B (1 + x)
+// plus the rounding of the boundary and the zone scale (dls), accurate where the blocking factor
+// changes; the positron argument is Qs - X with Qs = q0 log2(e)/T + sc. Tangents use the
+// first-order products with r (r may be far below the FP32 normal range squared).
+template <bool ADJ, bool OUTLINE>
+struct SplitUnit {
+    static __device__ __forceinline__ void body(const float4 *__restrict__ hs, int nh, float rA, float B, float dls,
+                                                float Qs, float h, float Em, float c1, Mom &mo, Mom &ta, Mom &tp,
+                                                Mom &et) {
+        const float rB = 1.f - rA;
+        const float2 rho = make_float2(rA, rB), au = make_float2(0.f, 2.f * rA), av = make_float2(2.f * rB, 0.f);
+        const float2 nb = make_float2(-rA * B, rB * B), off = make_float2(dls, dls), mQ = make_float2(-Qs, -Qs);
+        const float2 c12 = make_float2(c1, c1), h2 = make_float2(h, h), Em2 = make_float2(Em, Em);
+        const float2 mone2 = make_float2(-1.f, -1.f), z2 = make_float2(0.f, 0.f);
+        float2 P2 = z2, M2 = z2, Z2 = z2;
+        float2 TAp = z2, TAm = z2, TAz = z2, TPp = z2, TPm = z2, TPz = z2, ETp = z2, ETm = z2, ETz = z2;
+#pragma unroll 4
+        for (int k = 0; k < nh; ++k) {
+            const float4 q = hs[k];  // 1 + x, 1 - x, w
+            const float2 u2 = __ffma2_rn(rho, make_float2(q.x, q.x), au);
+            const float2 v2 = __ffma2_rn(rho, make_float2(q.y, q.y), av);
+            const float2 W2 = __fmul2_rn(rho, make_float2(q.z, q.z));
+            const float2 xs = __ffma2_rn(nb, make_float2(q.y, q.x), off);  // X + sc
+            const float2 e1 = make_float2(ex2a(-xs.x), ex2a(-xs.y));        // e^{-x_e} 2^-sc
+            const float2 xp = __fadd2_rn(xs, mQ);                           // -(x_p log2 e)
+            const float2 e2 = make_float2(ex2a(xp.x), ex2a(xp.y));
+            const float2 t = __fadd2_rn(c12, e1);
+            const float2 d = __ffma2_rn(t, e2, t);
+            const float2 r = make_float2(rcpa(d.x), rcpa(d.y));
+            const float2 Wu = __fmul2_rn(W2, u2);
+            const float2 cp = __fmul2_rn(Wu, u2), c0 = __fmul2_rn(Wu, v2), cm = __fmul2_rn(__fmul2_rn(W2, v2), v2);
+            P2 = __ffma2_rn(cp, r, P2);
+            M2 = __ffma2_rn(cm, r, M2);
+            Z2 = __ffma2_rn(c0, r, Z2);
+            if (ADJ) {
+                const float2 qv = __ffma2_rn(e2, r, r);  // (1 + e2) r
+                const float2 se = __fmul2_rn(c12, qv);   // 1 - f_e
+                const float2 sp = __fmul2_rn(t, r);      // 1 - f_ebar
+                const float2 fe = __fmul2_rn(e1, qv), fp = __fmul2_rn(e2, sp);
+                const float2 E2 = __ffma2_rn(h2, u2, Em2), Eb2 = __ffma2_rn(h2, v2, Em2);
+                const float2 ga = __fmul2_rn(__ffma2_rn(fe, E2, __fmul2_rn(fp, Eb2)), r);
+                const float2 gp = __fmul2_rn(__ffma2_rn(se, E2, __fmul2_rn(sp, Eb2)), r);
+                const float2 ge = __fmul2_rn(__ffma2_rn(fe, mone2, fp), r);
+                TAp = __ffma2_rn(cp, ga, TAp); TAm = __ffma2_rn(cm, ga, TAm); TAz = __ffma2_rn(c0, ga, TAz);
+                TPp = __ffma2_rn(cp, gp, TPp); TPm = __ffma2_rn(cm, gp, TPm); TPz = __ffma2_rn(c0, gp, TPz);
+                ETp = __ffma2_rn(cp, ge, ETp); ETm = __ffma2_rn(cm, ge, ETm); ETz = __ffma2_rn(c0, ge, ETz);
+            }
+        }
+        mo.p = P2.x + P2.y; mo.m = M2.x + M2.y; mo.z = Z2.x + Z2.y;
+        if (ADJ) {
+            ta.p = TAp.x + TAp.y; ta.m = TAm.x + TAm.y; ta.z = TAz.x + TAz.y;
+            tp.p = TPp.x + TPp.y; tp.m = TPm.x + TPm.y; tp.z = TPz.x + TPz.y;
+            et.p = ETp.x + ETp.y; et.m = ETm.x + ETm.y; et.z = ETz.x + ETz.y;
+        }
+    }
+    static __device__ __noinline__ void outline(const float4 *__restrict__ hs, int nh, float rA, float B, float dls,
+                                                float Qs, float h, float Em, float c1, Mom *m4) {
+        body(hs, nh, rA, B, dls, Qs, h, Em, c1, m4[0], m4[1], m4[2], m4[3]);
+    }
+    static __device__ __forceinline__ void run(const float4 *__restrict__ hs, int nh, float rA, float B, float dls,
+                                               float Qs, float h, float Em, float c1, Mom &mo, Mom &ta, Mom &tp,
+                                               Mom &et) {
+        if (OUTLINE) {
+            Mom m4[4];
+            outline(hs, nh, rA, B, dls, Qs, h, Em, c1, m4);
+            mo = m4[0]; ta = m4[1]; tp = m4[2]; et = m4[3];
+        } else {
+            body(hs, nh, rA, B, dls, Qs, h, Em, c1, mo, ta, tp, et);
+        }
+    }
+};
+
+// (ah + al) - (bh + bl) as a normalised FP32 pair (two-sum of the high parts; no contraction).
+__device__ __forceinline__ void df_diff(float ah, float al, float bh, float bl, float &dh, float &dl) {
+    const float s = __fsub_rn(ah, bh);
+    const float v = __fsub_rn(s, ah);
+    const float e = __fadd_rn(__fsub_rn(ah, __fsub_rn(s, v)), __fsub_rn(-bh, v));
+    const float t = __fadd_rn(e, __fsub_rn(al, bl));
+    dh = __fadd_rn(s, t);
+    dl = __fsub_rn(t, __fsub_rn(dh, s));
+}
 
 // One (pair, omega) node loop. Fills the moments of the blocking factor O and, with ADJ, of
 // GTa = O (f_e E + f_ebar Ebar), GTp = O ((1-f_e) E + (1-f_ebar) Ebar), GEt = O (f_ebar - f_e).
@@ -456,8 +544,9 @@ __device__ __forceinline__ Proj part_get(const float *part, int TB, int t, int s
 
 // MINB selects one of two register budgets (2: up to 128 registers; 3: up to 80 for the forward
 // kernel, 96 for the tangent kernel); both are compiled and the autotuner picks per kernel kind
-// and quadrature.
-template <int NE, bool ADJ, int MINB>
+// and quadrature. SPLIT compiles the split rule in (separate instantiations, so that the standard
+// form's register allocation is not shaped by it).
+template <int NE, bool ADJ, int MINB, bool SPLIT>
 __global__ void __launch_bounds__(MINB == 3 ? (ADJ ? VX_LB3_THREADS_ADJ : VX_TPB_MIXED) : VX_TPB_MIXED,
                                   MINB == 3 ? (ADJ ? VX_LB3_CTAS_ADJ : 3) : MINB)
     k_pair_mixed(const __grid_constant__ Launch L) {
@@ -466,6 +555,7 @@ __global__ void __launch_bounds__(MINB == 3 ? (ADJ ? VX_LB3_THREADS_ADJ : VX_TPB
     __shared__ long long s_zone;
     __shared__ NodeSm s_nodes[VX_MAX_NE];
     __shared__ NodeMir s_mir[VX_MAX_NE / 2];
+    __shared__ float4 s_half[VX_MAX_NE / 2];  // split rule: 1 + x, 1 - x, w of the n_e/2-node rule
     __shared__ uint16_t s_pij[VX_MAX_PAIRS];
     const Common &C = L.c;
     const int N = C.N, S = C.S, N2 = N * N, npair = C.npair;
@@ -491,6 +581,9 @@ __global__ void __launch_bounds__(MINB == 3 ? (ADJ ? VX_LB3_THREADS_ADJ : VX_TPB
         }
     }
     for (int p = tid; p < npair; p += blockDim.x) s_pij[p] = C.pij[p];
+    if (SPLIT)
+        for (int k = tid; k < C.n_e / 2; k += blockDim.x)
+            s_half[k] = make_float4(L.n32.hp[k], L.n32.hm[k], L.n32.hw[k], 0.f);
 
     // Thread 0 reserves the next zone one iteration ahead and prefetches its inputs into L2 while
     // the current zone's quadrature runs, so a zone starts without an atomic or DRAM round trip.
@@ -530,6 +623,9 @@ __global__ void __launch_bounds__(MINB == 3 ? (ADJ ? VX_LB3_THREADS_ADJ : VX_TPB
                 zs.el_h = (float)el;
                 zs.el_l = (float)(el - (double)zs.el_h);
                 zs.neg = eta < 0.0;
+                const double mu = ae * T;
+                zs.mu_hi = (float)mu;
+                zs.mu_lo = (float)(mu - (double)zs.mu_hi);
                 zs.deg = ae > C.eta_sw;
                 // zone scales: with O in [e^-|eta|, 1] and production vectors whose relevant
                 // entries reach e^-|eta| times their row's largest, lift both off the FP32 floor
@@ -643,7 +739,34 @@ __global__ void __launch_bounds__(MINB == 3 ? (ADJ ? VX_LB3_THREADS_ADJ : VX_TPB
                 if (ADJ) { ta.zero(); tp.zero(); et.zero(); }
                 const float B = h * il_h;
                 const float Pp = fmaf(Em, il_h, el_h);
-                if (!deg) {
+                // split rule (degenerate zones only): is the Fermi edge (|eta| T in the eta >= 0
+                // frame) inside (E-, E+)? Decided on FP32 pairs (~2^-48 relative), like the
+                // definition's FP64 comparison
+                bool in_split = false;
+                float rA = 0.f, dls = 0.f;
+                if (SPLIT && deg) {
+                    float dh, dl, gh, gl;
+                    df_diff(zs.mu_hi, zs.mu_lo, Em, Em_lo, dh, dl);   // mu - E-
+                    df_diff(2.f * h, 2.f * h_lo, dh, dl, gh, gl);     // E+ - mu
+                    in_split = (dh > 0.f || (dh == 0.f && dl > 0.f)) && (gh > 0.f || (gh == 0.f && gl > 0.f));
+                    if (in_split) {
+                        rA = fminf(fmaxf(__fdividef(dh, 2.f * h), 0.f), 1.f);
+                        // (E- + 2 h rA) - mu: the boundary's offset from the edge, then in log2 units
+                        const float delta = fmaf(2.f * h, rA, -dh) + fmaf(2.f * h_lo, rA, -dl);
+                        dls = fmaf(delta, il_h, zs.sc);
+                    }
+                }
+                if (in_split) {
+                    const float Qs = fmaf(2.f * (Em + h), il_h, zs.sc);
+                    SplitUnit<ADJ, ADJ>::run(s_half, C.n_e / 2, rA, B, dls, Qs, h, Em, zs.c1, mo, ta, tp, et);
+                    const Coef cf = make_coef(kp, km, k0, R1.w);
+                    project(PO, mo, cf);
+                    if (ADJ) {
+                        project(PTa, ta, cf);
+                        project(PTp, tp, cf);
+                        project(PEt, et, cf);
+                    }
+                } else if (!deg) {
                     const float Pe = fmaf(Em, il_h, -el_h);
                     node_loop<NE, ADJ, false>(s_nodes, s_mir, C.n_e, B, Pe, Pp, 0.f, 0.f, 0.f, 0.f, h, Em, 1.f, zs.K, 0.f, mo, ta, tp, et);
                     const Coef cf = make_coef(kp, km, k0, R1.w);

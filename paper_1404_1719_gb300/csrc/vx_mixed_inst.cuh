@@ -8,30 +8,41 @@
 
 namespace vx {
 
-template <int NE>
+template <int NE, bool SPLIT>
 static cudaError_t VX_CAT(go_, VX_SUFFIX)(const Launch &L, int grid, int block, size_t smem, cudaStream_t s) {
-    k_pair_mixed<NE, VX_ADJ, VX_MINB><<<grid, block, smem, s>>>(L);
+    k_pair_mixed<NE, VX_ADJ, VX_MINB, SPLIT><<<grid, block, smem, s>>>(L);
     return cudaGetLastError();
 }
 
-const void *VX_CAT(kernel_mixed_, VX_SUFFIX)(int n_e) {
+template <bool SPLIT>
+static const void *VX_CAT(kernel_, VX_SUFFIX)(int n_e) {
     switch (n_e) {
-        case 16: return (const void *)k_pair_mixed<16, VX_ADJ, VX_MINB>;
-        case 32: return (const void *)k_pair_mixed<32, VX_ADJ, VX_MINB>;
-        case 48: return (const void *)k_pair_mixed<48, VX_ADJ, VX_MINB>;
-        case 64: return (const void *)k_pair_mixed<64, VX_ADJ, VX_MINB>;
-        default: return (const void *)k_pair_mixed<0, VX_ADJ, VX_MINB>;
+        case 16: return (const void *)k_pair_mixed<16, VX_ADJ, VX_MINB, SPLIT>;
+        case 32: return (const void *)k_pair_mixed<32, VX_ADJ, VX_MINB, SPLIT>;
+        case 48: return (const void *)k_pair_mixed<48, VX_ADJ, VX_MINB, SPLIT>;
+        case 64: return (const void *)k_pair_mixed<64, VX_ADJ, VX_MINB, SPLIT>;
+        default: return (const void *)k_pair_mixed<0, VX_ADJ, VX_MINB, SPLIT>;
+    }
+}
+
+const void *VX_CAT(kernel_mixed_, VX_SUFFIX)(int n_e, bool split) {
+    return split ? VX_CAT(kernel_, VX_SUFFIX)<true>(n_e) : VX_CAT(kernel_, VX_SUFFIX)<false>(n_e);
+}
+
+template <bool SPLIT>
+static cudaError_t VX_CAT(launch_, VX_SUFFIX)(const Launch &L, int grid, int block, size_t smem, cudaStream_t s) {
+    switch (L.c.n_e) {
+        case 16: return VX_CAT(go_, VX_SUFFIX)<16, SPLIT>(L, grid, block, smem, s);
+        case 32: return VX_CAT(go_, VX_SUFFIX)<32, SPLIT>(L, grid, block, smem, s);
+        case 48: return VX_CAT(go_, VX_SUFFIX)<48, SPLIT>(L, grid, block, smem, s);
+        case 64: return VX_CAT(go_, VX_SUFFIX)<64, SPLIT>(L, grid, block, smem, s);
+        default: return VX_CAT(go_, VX_SUFFIX)<0, SPLIT>(L, grid, block, smem, s);
     }
 }
 
 cudaError_t VX_CAT(launch_mixed_, VX_SUFFIX)(const Launch &L, int grid, int block, size_t smem, cudaStream_t s) {
-    switch (L.c.n_e) {
-        case 16: return VX_CAT(go_, VX_SUFFIX)<16>(L, grid, block, smem, s);
-        case 32: return VX_CAT(go_, VX_SUFFIX)<32>(L, grid, block, smem, s);
-        case 48: return VX_CAT(go_, VX_SUFFIX)<48>(L, grid, block, smem, s);
-        case 64: return VX_CAT(go_, VX_SUFFIX)<64>(L, grid, block, smem, s);
-        default: return VX_CAT(go_, VX_SUFFIX)<0>(L, grid, block, smem, s);
-    }
+    return L.c.split ? VX_CAT(launch_, VX_SUFFIX)<true>(L, grid, block, smem, s)
+                     : VX_CAT(launch_, VX_SUFFIX)<false>(L, grid, block, smem, s);
 }
 
 }  // namespace vx

@@ -113,9 +113,9 @@ struct vx_rates {
 };
 
 namespace vx {
-const void *kernel_mixed(bool adj, int minb, int n_e) {
-    if (adj) return minb == 3 ? kernel_mixed_adj_b3(n_e) : kernel_mixed_adj_b2(n_e);
-    return minb == 3 ? kernel_mixed_fwd_b3(n_e) : kernel_mixed_fwd_b2(n_e);
+const void *kernel_mixed(bool adj, int minb, int n_e, bool split) {
+    if (adj) return minb == 3 ? kernel_mixed_adj_b3(n_e, split) : kernel_mixed_adj_b2(n_e, split);
+    return minb == 3 ? kernel_mixed_fwd_b3(n_e, split) : kernel_mixed_fwd_b2(n_e, split);
 }
 cudaError_t launch_mixed(bool adj, int minb, const Launch &L, int grid, int block, size_t smem, cudaStream_t s) {
     if (adj) return minb == 3 ? launch_mixed_adj_b3(L, grid, block, smem, s) : launch_mixed_adj_b2(L, grid, block, smem, s);
@@ -176,7 +176,11 @@ static vx_status validate_config(const vx_config *c) {
     if (c->eta_fp64 > 40.0)  // keeps two paired denominators below the FP32 range
         return fail(VX_ERR_INVALID_ARG, "eta_fp64 must be <= 40");
     if (c->prec != VX_PREC_FP64 && c->prec != VX_PREC_MIXED) return fail(VX_ERR_INVALID_ARG, "unknown precision");
-    if (c->flags & ~(VX_USE_GRAPH | VX_AUTOTUNE)) return fail(VX_ERR_INVALID_ARG, "unknown flag bits");
+    if (c->flags & ~(VX_USE_GRAPH | VX_AUTOTUNE | VX_QUAD_SPLIT)) return fail(VX_ERR_INVALID_ARG, "unknown flag bits");
+    if ((c->flags & VX_QUAD_SPLIT) && (c->n_e % 2 != 0))
+        return fail(VX_ERR_INVALID_ARG, "VX_QUAD_SPLIT needs an even n_e (got %d)", c->n_e);
+    if ((c->flags & VX_QUAD_SPLIT) && c->prec != VX_PREC_MIXED)
+        return fail(VX_ERR_UNSUPPORTED, "VX_QUAD_SPLIT is provided for the mixed form");
     return VX_OK;
 }
 
@@ -243,6 +247,16 @@ vx_status vx_rates_create(const vx_config *cfg, vx_rates **out) {
         double uh = std::nearbyint(u * 2048.0) / 2048.0;
         h->n32.uh[k] = (float)uh;
         h->n32.ul[k] = (float)(u - uh);
+    }
+    C.split = (cfg->flags & VX_QUAD_SPLIT) ? 1 : 0;
+    if (C.split) {
+        std::vector<double> th, wh;
+        gauss_legendre(ne / 2, th, wh);
+        for (int k = 0; k < ne / 2; ++k) {
+            h->n32.hp[k] = (float)(1.0 + th[k]);
+            h->n32.hm[k] = (float)(1.0 - th[k]);
+            h->n32.hw[k] = (float)wh[k];
+        }
     }
     // per (unordered pair p, omega node m) tables: FP32 records pair-major (a thread's consecutive
     // units are adjacent), FP64 records omega-major
@@ -313,10 +327,11 @@ vx_status vx_rates_create(const vx_config *cfg, vx_rates **out) {
     h->cc_major = prop.major;
     h->cc_minor = prop.minor;
     struct K { const void *fn; size_t smem; int *grid; int block; };
-    K ks[5] = {{vx::kernel_mixed(false, 2, ne), h->smem_fwd, &h->grid_mixed[0][0], h->block_mixed},
-               {vx::kernel_mixed(false, 3, ne), h->smem_fwd, &h->grid_mixed[0][1], h->block_mixed},
-               {vx::kernel_mixed(true, 2, ne), h->smem_adj, &h->grid_mixed[1][0], h->block_mixed},
-               {vx::kernel_mixed(true, 3, ne), h->smem_adj, &h->grid_mixed[1][1], h->block_mixed},
+    const bool sp = C.split != 0;
+    K ks[5] = {{vx::kernel_mixed(false, 2, ne, sp), h->smem_fwd, &h->grid_mixed[0][0], h->block_mixed},
+               {vx::kernel_mixed(false, 3, ne, sp), h->smem_fwd, &h->grid_mixed[0][1], h->block_mixed},
+               {vx::kernel_mixed(true, 2, ne, sp), h->smem_adj, &h->grid_mixed[1][0], h->block_mixed},
+               {vx::kernel_mixed(true, 3, ne, sp), h->smem_adj, &h->grid_mixed[1][1], h->block_mixed},
                {vx::kernel_fp64_fwd(ne), h->smem_64, &h->grid_64, h->block}};
     for (K &k : ks) {
         // opt in to the dynamic size always: the 48 KB default bounds static + dynamic together
@@ -460,8 +475,9 @@ static void fill_launch(const vx_rates *h, const vx_batch *b, vx::Launch &L) {
 // by the real launch that follows.
 static std::string tune_key(const vx_rates *h, bool adj) {
     char k[160];
-    snprintf(k, sizeof k, "N=%d,n_mu=%d,n_e=%d,S=%d,kind=%s,sm=%d,cc=%d.%d", h->common.N, h->common.n_mu,
-             h->common.n_e, h->common.S, adj ? "tangents" : "forward", h->nsm, h->cc_major, h->cc_minor);
+    snprintf(k, sizeof k, "N=%d,n_mu=%d,n_e=%d,S=%d,kind=%s%s,sm=%d,cc=%d.%d", h->common.N, h->common.n_mu,
+             h->common.n_e, h->common.S, adj ? "tangents" : "forward", h->common.split ? "+split" : "", h->nsm,
+             h->cc_major, h->cc_minor);
     return k;
 }
 
@@ -569,7 +585,7 @@ vx_status vx_rates_eval(vx_rates *h, const vx_batch *b, const vx_out *out, vx_st
         if ((st = autotune(h, false, L, s)) != VX_OK) return st;
         const int mb = h->minb[0];
         int grid = (int)std::min<long long>(h->grid_mixed[0][mb - 2], b->n_zones);
-        if (graph) return launch_graph(h, 0, vx::kernel_mixed(false, mb, h->common.n_e), &L, grid, h->block_mixed, h->smem_fwd, s);
+        if (graph) return launch_graph(h, 0, vx::kernel_mixed(false, mb, h->common.n_e, h->common.split != 0), &L, grid, h->block_mixed, h->smem_fwd, s);
         VX_CU(cudaMemsetAsync(h->d_counter, 0, sizeof(unsigned long long), s));
         VX_CU(vx::launch_mixed(false, mb, L, grid, h->block_mixed, h->smem_fwd, s));
     } else {
@@ -619,7 +635,7 @@ vx_status vx_rates_adjoint(vx_rates *h, const vx_batch *b, const vx_out *grad_ou
     const int mb = h->minb[1];
     int grid = (int)std::min<long long>(h->grid_mixed[1][mb - 2], b->n_zones);
     if (h->cfg.flags & VX_USE_GRAPH)
-        return launch_graph(h, 1, vx::kernel_mixed(true, mb, h->common.n_e), &L, grid, h->block_mixed, h->smem_adj, s);
+        return launch_graph(h, 1, vx::kernel_mixed(true, mb, h->common.n_e, h->common.split != 0), &L, grid, h->block_mixed, h->smem_adj, s);
     VX_CU(cudaMemsetAsync(h->d_counter, 0, sizeof(unsigned long long), s));
     VX_CU(vx::launch_mixed(true, mb, L, grid, h->block_mixed, h->smem_adj, s));
     return VX_OK;
@@ -657,7 +673,7 @@ vx_status vx_rates_spectral(vx_rates *h, const vx_batch *b, const vx_out *grad_o
     const int mb = h->minb[0];
     int grid = (int)std::min<long long>(h->grid_mixed[0][mb - 2], b->n_zones);
     if (h->cfg.flags & VX_USE_GRAPH)
-        return launch_graph(h, 0, vx::kernel_mixed(false, mb, h->common.n_e), &L, grid, h->block_mixed, h->smem_fwd, s);
+        return launch_graph(h, 0, vx::kernel_mixed(false, mb, h->common.n_e, h->common.split != 0), &L, grid, h->block_mixed, h->smem_fwd, s);
     VX_CU(cudaMemsetAsync(h->d_counter, 0, sizeof(unsigned long long), s));
     VX_CU(vx::launch_mixed(false, mb, L, grid, h->block_mixed, h->smem_fwd, s));
     return VX_OK;
@@ -903,7 +919,7 @@ vx_status vx_rates_eval_noalloc(const vx_config *cfg, const vx_batch *b, const v
     const int ne = cfg->n_e, minb = 2;
     const int block = std::min(round_up(L.c.npair * cfg->n_mu, 32), VX_BLOCK_MIXED);
     const size_t smem = vx::smem_mixed_bytes(cfg->n_bins, cfg->n_species, false, block);
-    const void *fn = vx::kernel_mixed(false, minb, ne);
+    const void *fn = vx::kernel_mixed(false, minb, ne, false);
     VX_CU(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int nsm = 0, occ = 0;
     VX_CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));

@@ -444,8 +444,12 @@ def test_split_rule_without_an_edge_is_the_standard_rule():
     the standard rule, bit for bit."""
     eps = vx_inputs.energy_centres(9, 1.0, 300.0)
     a = oracle.phi_zone(eps, 6, 16, 4.0, 0.0, grad=True)
-    b = oracle.phi_zone(eps, 6, 16, 4.0, 0.0, grad=True, split=True)
+    b = oracle.phi_zone(eps, 6, 16, 4.0, 0.0, grad=True, split=True, eta_split=0.0)
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    # below the degeneracy threshold the split form keeps the standard rule
+    a = oracle.phi_zone(eps, 6, 16, 2.0, 15.0)
+    b = oracle.phi_zone(eps, 6, 16, 2.0, 15.0, split=True)
+    assert np.array_equal(a, b)
 
 
 @pytest.mark.parametrize("T,eta", SPLIT_STATES)
@@ -454,7 +458,7 @@ def test_split_and_standard_rules_share_their_limit(T, eta):
     panel map, weight or edge would leave a finite gap."""
     eps = vx_inputs.energy_centres(9, 1.0, 300.0)
     a = oracle.phi_zone(eps, 6, 1024, T, eta)
-    b = oracle.phi_zone(eps, 6, 1024, T, eta, split=True)
+    b = oracle.phi_zone(eps, 6, 1024, T, eta, split=True, eta_split=0.0)
     assert np.max(np.abs(a - b)) <= 1e-13 * np.max(np.abs(a))
 
 
@@ -463,10 +467,10 @@ def test_split_rule_converges_faster_at_high_degeneracy(T, eta):
     """Where the Fermi edge cuts the electron-energy interval, panels meeting at the edge converge
     much faster: at 64 nodes the split rule is at least 100x closer to the converged value."""
     eps = vx_inputs.energy_centres(13, 1.0, 300.0)
-    ref = oracle.phi_zone(eps, 8, 1024, T, eta, split=True)
+    ref = oracle.phi_zone(eps, 8, 1024, T, eta, split=True, eta_split=0.0)
     scale = np.abs(ref).max(axis=-1, keepdims=True) + 1e-300
     err_std = np.max(np.abs(oracle.phi_zone(eps, 8, 64, T, eta) - ref) / scale)
-    err_split = np.max(np.abs(oracle.phi_zone(eps, 8, 64, T, eta, split=True) - ref) / scale)
+    err_split = np.max(np.abs(oracle.phi_zone(eps, 8, 64, T, eta, split=True, eta_split=0.0) - ref) / scale)
     assert err_split * 100 <= err_std, (err_split, err_std)
 
 
@@ -490,15 +494,15 @@ def test_split_rule_gradient_central_differences():
     eps = vx_inputs.energy_centres(7, 1.0, 300.0)
     st, J, H = vx_inputs.random_zones(3, 12, n_bins=7, eta_range=(8.0, 40.0))
     args = (eps, 6, 256, [0, 1, 2])
-    base = oracle.evaluate(*args, st, J, H, jac=True, split=True)
+    base = oracle.evaluate(*args, st, J, H, jac=True, split=True, eta_split=0.0)
     keys = ("j0", "chi0", "j1", "chi1")
     for v, rel in ((0, lambda s: 1e-4 * s[:, 0]), (1, lambda s: 1e-4 * np.maximum(np.abs(s[:, 1]), 1.0))):
         h = rel(st)
         sp, sm = st.copy(), st.copy()
         sp[:, v] += h
         sm[:, v] -= h
-        fp = oracle.evaluate(*args, sp, J, H, split=True)
-        fm = oracle.evaluate(*args, sm, J, H, split=True)
+        fp = oracle.evaluate(*args, sp, J, H, split=True, eta_split=0.0)
+        fm = oracle.evaluate(*args, sm, J, H, split=True, eta_split=0.0)
         for o, k in enumerate(keys):
             fd = (fp[k] - fm[k]) / (2 * h[:, None, None])
             an = base["jac"][..., o, v]
