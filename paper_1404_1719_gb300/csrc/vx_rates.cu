@@ -110,6 +110,14 @@ struct vx_rates {
     int cc_major = 0, cc_minor = 0;
     // one cached executable graph per kernel kind: mixed forward, mixed tangents, FP64
     cudaGraphExec_t gexec[3] = {nullptr, nullptr, nullptr};
+    // host-buffer calls: two staging slots of `chunk` zones, each with its stream and counter
+    struct {
+        long long chunk = 0;
+        bool jac = false;                     // slots sized for the Jacobian too
+        double *buf[2] = {nullptr, nullptr};
+        unsigned long long *cnt = nullptr;    // [2]
+        cudaStream_t st[2] = {nullptr, nullptr};
+    } hs;
 };
 
 namespace vx {
@@ -547,7 +555,7 @@ static vx_status autotune(vx_rates *h, bool adj, const vx::Launch &L, cudaStream
         const int grid = (int)std::min<long long>(h->grid_mixed[kind][mb - 2], sample);
         float ms = 0.f;
         for (int rep = 0; rep < 2; ++rep) {
-            VX_CU(cudaMemsetAsync(h->d_counter, 0, sizeof(unsigned long long), s));
+            VX_CU(cudaMemsetAsync(Ls.counter, 0, sizeof(unsigned long long), s));
             if (rep) VX_CU(cudaEventRecord(e0, s));
             VX_CU(vx::launch_mixed(adj, mb, Ls, grid, h->block_mixed, smem, s));
             if (rep) VX_CU(cudaEventRecord(e1, s));
@@ -679,6 +687,109 @@ vx_status vx_rates_spectral(vx_rates *h, const vx_batch *b, const vx_out *grad_o
     return VX_OK;
 }
 
+// ---- host-buffer calls ----------------------------------------------------------------------
+// The batch is processed in chunks of VX_HOST_CHUNK zones through two staging slots of device
+// memory owned by the handle (allocated on first use, about 0.6 GB each with the Jacobian at
+// 21 bins and 3 species). Each slot has its own stream and work counter, so the copies of one
+// chunk overlap the kernel of the next. Host arrays should be pinned for the copies to be
+// asynchronous; the call returns when every output is in host memory.
+#ifndef VX_HOST_CHUNK
+#define VX_HOST_CHUNK 65536
+#endif
+
+static vx_status host_prepare(vx_rates *h, bool adj) {
+    auto &hs = h->hs;
+    if (hs.buf[0] && (hs.jac || !adj)) return VX_OK;
+    const size_t SN = (size_t)h->common.S * h->common.N;
+    const long long chunk = VX_HOST_CHUNK;
+    const size_t per_zone = 4 + 2 * SN + 4 * SN + (adj ? 12 * SN : 0);
+    for (int k = 0; k < 2; ++k) {
+        if (hs.st[k]) VX_CU(cudaStreamSynchronize(hs.st[k]));
+        cudaFree(hs.buf[k]);
+        hs.buf[k] = nullptr;
+    }
+    for (int k = 0; k < 2; ++k) {
+        cudaError_t e = cudaMalloc(&hs.buf[k], per_zone * chunk * sizeof(double));
+        if (e != cudaSuccess)
+            return fail(e == cudaErrorMemoryAllocation ? VX_ERR_OOM : VX_ERR_CUDA, "staging slot: %s", cudaGetErrorString(e));
+        if (!hs.st[k]) VX_CU(cudaStreamCreateWithFlags(&hs.st[k], cudaStreamNonBlocking));
+    }
+    if (!hs.cnt) VX_CU(cudaMalloc(&hs.cnt, 2 * sizeof(unsigned long long)));
+    hs.chunk = chunk;
+    hs.jac = adj;
+    return VX_OK;
+}
+
+static vx_status host_run(vx_rates *h, const vx_batch *b, const vx_out *out, double *jac, bool adj) {
+    if (!h) return fail(VX_ERR_INVALID_ARG, "handle is NULL");
+    if (!b) return fail(VX_ERR_INVALID_ARG, "batch is NULL");
+    if (h->cfg.prec != VX_PREC_MIXED) return fail(VX_ERR_UNSUPPORTED, "the host-buffer calls are provided for the mixed form");
+    if (b->n_zones < 0 || b->n_rays < 0) return fail(VX_ERR_INVALID_ARG, "negative size");
+    if (b->ray_offsets) {
+        if (b->ray_offsets[0] != 0) return fail(VX_ERR_INVALID_ARG, "ray_offsets[0] must be 0");
+        for (int r = 0; r < b->n_rays; ++r)
+            if (b->ray_offsets[r + 1] < b->ray_offsets[r])
+                return fail(VX_ERR_INVALID_ARG, "ray_offsets must be non-decreasing (ray %d)", r);
+        if ((long long)b->ray_offsets[b->n_rays] != b->n_zones)
+            return fail(VX_ERR_INVALID_ARG, "ray_offsets[n_rays] = %d but n_zones = %lld", b->ray_offsets[b->n_rays], b->n_zones);
+    }
+    if (adj && !jac && !out) return fail(VX_ERR_INVALID_ARG, "no output requested");
+    if (!adj && !out) return fail(VX_ERR_INVALID_ARG, "out is NULL");
+    if (out && (!out->j0 || !out->chi0 || !out->j1 || !out->chi1)) return fail(VX_ERR_INVALID_ARG, "an output array is NULL");
+    if (out && out->phi) return fail(VX_ERR_INVALID_ARG, "phi output is not produced by the host-buffer calls");
+    if (b->n_zones == 0) return VX_OK;
+    if (!b->state || !b->J || !b->H) return fail(VX_ERR_INVALID_ARG, "state, J and H must be host arrays");
+    DeviceGuard dg(h->device);
+    vx_status st;
+    if ((st = host_prepare(h, adj)) != VX_OK) return st;
+    auto &hs = h->hs;
+    const size_t SN = (size_t)h->common.S * h->common.N;
+    const long long Z = b->n_zones, chunk = hs.chunk;
+    const int kind = adj ? 1 : 0;
+    const size_t smem = adj ? h->smem_adj : h->smem_fwd;
+    for (long long c = 0, z0 = 0; z0 < Z; ++c, z0 += chunk) {
+        const long long n = std::min(chunk, Z - z0);
+        const int sl = (int)(c & 1);
+        cudaStream_t s = hs.st[sl];
+        double *p = hs.buf[sl];
+        double *d_state = p, *d_J = d_state + 4 * chunk, *d_H = d_J + SN * chunk;
+        double *d_out = d_H + SN * chunk, *d_jac = d_out + 4 * SN * chunk;
+        VX_CU(cudaMemcpyAsync(d_state, b->state + 4 * z0, 4 * n * sizeof(double), cudaMemcpyHostToDevice, s));
+        VX_CU(cudaMemcpyAsync(d_J, b->J + SN * z0, SN * n * sizeof(double), cudaMemcpyHostToDevice, s));
+        VX_CU(cudaMemcpyAsync(d_H, b->H + SN * z0, SN * n * sizeof(double), cudaMemcpyHostToDevice, s));
+        vx_batch db{0, n, nullptr, d_state, d_J, d_H};
+        vx::Launch L{};
+        fill_launch(h, &db, L);
+        L.counter = hs.cnt + sl;
+        if (out) { L.j0 = d_out; L.chi0 = d_out + SN * n; L.j1 = d_out + 2 * SN * n; L.chi1 = d_out + 3 * SN * n; }
+        if (adj && jac) L.jac = d_jac;
+        if ((st = autotune(h, adj, L, s)) != VX_OK) return st;
+        const int mb = h->minb[kind];
+        const int grid = (int)std::min<long long>(h->grid_mixed[kind][mb - 2], n);
+        VX_CU(cudaMemsetAsync(L.counter, 0, sizeof(unsigned long long), s));
+        VX_CU(vx::launch_mixed(adj, mb, L, grid, h->block_mixed, smem, s));
+        if (out) {
+            double *dst[4] = {out->j0, out->chi0, out->j1, out->chi1};
+            for (int k = 0; k < 4; ++k)
+                VX_CU(cudaMemcpyAsync(dst[k] + SN * z0, d_out + k * SN * n, SN * n * sizeof(double),
+                                      cudaMemcpyDeviceToHost, s));
+        }
+        if (adj && jac)
+            VX_CU(cudaMemcpyAsync(jac + 12 * SN * z0, d_jac, 12 * SN * n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    }
+    VX_CU(cudaStreamSynchronize(hs.st[0]));
+    VX_CU(cudaStreamSynchronize(hs.st[1]));
+    return VX_OK;
+}
+
+vx_status vx_rates_eval_host(vx_rates *h, const vx_batch *host_batch, const vx_out *host_out) {
+    return host_run(h, host_batch, host_out, nullptr, false);
+}
+
+vx_status vx_rates_adjoint_host(vx_rates *h, const vx_batch *host_batch, double *host_jac, const vx_out *host_fwd) {
+    return host_run(h, host_batch, host_fwd, host_jac, true);
+}
+
 vx_status vx_rates_check(vx_rates *h, vx_stream stream) {
     if (!h) return fail(VX_ERR_INVALID_ARG, "handle is NULL");
     DeviceGuard dg(h->device);
@@ -704,6 +815,11 @@ void vx_rates_destroy(vx_rates *h) {
     cudaFree(h->d_tab64);
     cudaFree(h->d_counter);
     cudaFree(h->d_flag);
+    for (int k = 0; k < 2; ++k) {
+        cudaFree(h->hs.buf[k]);
+        if (h->hs.st[k]) cudaStreamDestroy(h->hs.st[k]);
+    }
+    cudaFree(h->hs.cnt);
     delete h;
 }
 

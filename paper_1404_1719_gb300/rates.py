@@ -157,18 +157,44 @@ class PairRates:
         return capi.vx_rates_check(self._h, self._stream(stream)) == capi.VX_OK
 
     # ------------------------------------------------------------------------------------------
-    def evaluate_host(self, state, J, H, ray_offsets=None, stream=None) -> dict:
-        """End-to-end call with host (numpy or pinned torch) inputs: host->device copies, the rate
-        evaluation and device->host copies of the four rate arrays, all on one stream."""
-        s = stream if stream is not None else torch.cuda.current_stream()
-        with torch.cuda.stream(s):
-            dev = [torch.as_tensor(x).to(self.device, non_blocking=True) for x in (state, J, H)]
-            res = self.evaluate(*dev, ray_offsets=ray_offsets, stream=s)
-            host = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in res.items()}
-            for k in res:
-                host[k].copy_(res[k], non_blocking=True)
-        s.synchronize()
-        return host
+    def _host_batch(self, state, J, H, ray_offsets):
+        arrs = [np.ascontiguousarray(torch.as_tensor(x).numpy() if torch.is_tensor(x) else x, dtype=np.float64)
+                for x in (state, J, H)]
+        Z = arrs[0].shape[0]
+        for name, a, shape in zip(("state", "J", "H"), arrs, ((Z, 4), (Z, self.S, self.N), (Z, self.S, self.N))):
+            if a.shape != shape:
+                raise ValueError(f"{name} must have shape {shape}")
+        offs = None if ray_offsets is None else np.ascontiguousarray(ray_offsets, dtype=np.int32)
+        b = capi.vx_batch(n_rays=1 if offs is None else len(offs) - 1, n_zones=Z,
+                          ray_offsets=None if offs is None else offs.ctypes.data_as(capi._ip),
+                          state=arrs[0].ctypes.data, J=arrs[1].ctypes.data, H=arrs[2].ctypes.data)
+        b._keep = (arrs, offs)
+        return b, Z
+
+    def _host_out(self, Z, out):
+        res = out if out is not None else {k: torch.empty((Z, self.S, self.N), dtype=torch.float64, pin_memory=True)
+                                           for k in _OUT_KEYS}
+        return res, capi.vx_out(*(res[k].data_ptr() for k in _OUT_KEYS), None)
+
+    def evaluate_host(self, state, J, H, ray_offsets=None, out=None) -> dict:
+        """End-to-end call on host arrays (numpy or pinned torch CPU tensors): vx_rates_eval_host
+        copies chunks of zones in, evaluates and copies the rates back, overlapping the copies of
+        one chunk with the kernel of the next. Returns host tensors (pinned unless `out` given)."""
+        b, Z = self._host_batch(state, J, H, ray_offsets)
+        res, o = self._host_out(Z, out)
+        with torch.cuda.device(self.device):
+            capi.vx_rates_eval_host(self._h, b, o)
+        return res
+
+    def adjoint_host(self, state, J, H, forward: bool = True, ray_offsets=None, out=None, jac=None) -> dict:
+        """End-to-end forward rates and Jacobian on host arrays (vx_rates_adjoint_host)."""
+        b, Z = self._host_batch(state, J, H, ray_offsets)
+        res, o = self._host_out(Z, out) if forward else ({}, None)
+        res["jac"] = jac if jac is not None else torch.empty((Z, self.S, self.N, 4, 3), dtype=torch.float64,
+                                                             pin_memory=True)
+        with torch.cuda.device(self.device):
+            capi.vx_rates_adjoint_host(self._h, b, res["jac"].data_ptr(), o)
+        return res
 
 
 class VxRatesFn(torch.autograd.Function):
