@@ -245,9 +245,8 @@ def run_ours(args):
     ok = rates.check()
 
     # ---- end-to-end: pinned host inputs -> device -> fused pass -> host rates (+ Jacobian).
-    # The forward and forward + Jacobian steps go through the library's host-buffer calls, which
-    # stage chunks of zones through device memory and overlap their copies with the kernels; the
-    # spectral step copies explicitly around vx_rates_spectral.
+    # Every mode goes through the library's host-buffer call, which stages chunks of zones through
+    # device memory and overlaps their copies with the kernels.
     e2e_steps = max(1, min(3, args.steps))
     h_out = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in out.items()}
     h_jac = torch.empty(jac.shape, dtype=jac.dtype, pin_memory=True)
@@ -255,17 +254,13 @@ def run_ours(args):
     hb = capi.vx_batch(n_rays=bt.n_rays, n_zones=Z, ray_offsets=bt.ray_offsets, state=host["state"].data_ptr(),
                        J=host["J"].data_ptr(), H=host["H"].data_ptr())
     hfwd = capi.vx_out(*(h_out[k].data_ptr() for k in ("j0", "chi0", "j1", "chi1")), None)
+    h_seeds = torch.ones((Z, S, N), dtype=torch.float64, pin_memory=True) if spec else None
+    hseeds = capi.vx_out(*([h_seeds.data_ptr()] * 4), None) if spec else None
 
     def step_e2e():
         if spec:
-            for k in ("state", "J", "H"):
-                d[k].copy_(host[k], non_blocking=True)
-            step()
-            for k in out:
-                h_out[k].copy_(out[k], non_blocking=True)
-            for k in spec_out:
-                h_spec[k].copy_(spec_out[k], non_blocking=True)
-            torch.cuda.synchronize()
+            capi.vx_rates_spectral_host(rates.handle, hb, hseeds, h_spec["grad_J"].data_ptr(),
+                                        h_spec["grad_H"].data_ptr(), h_spec["blocks"].data_ptr(), hfwd)
         elif fwd_only:
             capi.vx_rates_eval_host(rates.handle, hb, hfwd)
         else:
@@ -284,6 +279,7 @@ def run_ours(args):
     h2d = sum(v.numel() * v.element_size() for v in host.values())
     d2h = sum(v.numel() * v.element_size() for v in out.values()) + (0 if fwd_only else jac.numel() * jac.element_size())
     d2h += sum(v.numel() * v.element_size() for v in spec_out.values())
+    h2d += h_seeds.numel() * h_seeds.element_size() * 4 if spec else 0
 
     line = None
     if rank == 0:
@@ -334,7 +330,7 @@ def run_ours(args):
                        "graph": True, "autotune": True},
             "e2e": {"value": job_rate(entries(Z, N), world, ms_e2e), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "call": ("torch copies around vx_rates_spectral" if spec else
+                    "call": ("vx_rates_spectral_host" if spec else
                              "vx_rates_eval_host" if fwd_only else "vx_rates_adjoint_host") + " (host buffers, pinned)",
                     "ms_per_step": ms_e2e},
             "gpu_launches": args.steps,

@@ -155,16 +155,20 @@ vx_status vx_rates_adjoint(vx_rates *h, const vx_batch *batch, const vx_out *gra
 vx_status vx_rates_spectral(vx_rates *h, const vx_batch *batch, const vx_out *grad_out, double *grad_J,
                             double *grad_H, double *blocks, const vx_out *fwd, vx_stream stream);
 
-/* Host-buffer forms of vx_rates_eval and vx_rates_adjoint (forward rates and Jacobian): the
- * batch's state, J and H and every output are HOST arrays in the layouts above (pinned memory
- * lets the copies run asynchronously). The library copies the batch in chunks of zones through
- * two staging slots of device memory it owns (allocated on the first such call and kept until
- * vx_rates_destroy: about 0.6 GB per slot at 21 bins and 3 species with the Jacobian), on two
- * streams of its own, so one chunk's copies overlap the next chunk's kernel. Synchronous: returns
- * when the outputs are in host memory. out->phi must be NULL; host_fwd or host_jac may be NULL,
- * not both. Mixed precision only. */
+/* Host-buffer forms of vx_rates_eval, vx_rates_adjoint (forward rates and Jacobian) and
+ * vx_rates_spectral: the batch's state, J and H, the seeds and every output are HOST arrays in
+ * the layouts above (pinned memory lets the copies run asynchronously). The library copies the
+ * batch in chunks of zones through two staging slots of device memory it owns (640 MiB each, or
+ * the MiB given by the environment variable VX_HOST_SLOT_MB; allocated on the handle's first such
+ * call and kept until vx_rates_destroy), on two streams of its own,
+ * so one chunk's copies overlap the next chunk's kernel. Synchronous: returns when the outputs
+ * are in host memory. Output rules as for the device calls; out->phi must be NULL. Mixed
+ * precision only. */
 vx_status vx_rates_eval_host(vx_rates *h, const vx_batch *host_batch, const vx_out *host_out);
 vx_status vx_rates_adjoint_host(vx_rates *h, const vx_batch *host_batch, double *host_jac, const vx_out *host_fwd);
+vx_status vx_rates_spectral_host(vx_rates *h, const vx_batch *host_batch, const vx_out *host_grad_out,
+                                 double *host_grad_J, double *host_grad_H, double *host_blocks,
+                                 const vx_out *host_fwd);
 
 /* Synchronises `stream`, reads and clears the device numeric flag: VX_OK or VX_ERR_NUMERIC. */
 vx_status vx_rates_check(vx_rates *h, vx_stream stream);

@@ -44,7 +44,8 @@ class VxError(RuntimeError):
 
 SYMBOLS = ("vx_rates_create", "vx_rates_eval", "vx_rates_adjoint", "vx_rates_check",
            "vx_rates_entries_per_zone", "vx_rates_destroy", "vx_status_string", "vx_last_error",
-           "vx_rates_eval_noalloc", "vx_rates_spectral", "vx_rates_eval_host", "vx_rates_adjoint_host")
+           "vx_rates_eval_noalloc", "vx_rates_spectral", "vx_rates_eval_host", "vx_rates_adjoint_host",
+           "vx_rates_spectral_host")
 
 _lib = None
 
@@ -74,6 +75,9 @@ def lib(path: str | None = None):
     L.vx_rates_adjoint_host.argtypes = [ctypes.c_void_p, ctypes.POINTER(vx_batch), ctypes.c_void_p,
                                         ctypes.POINTER(vx_out)]
     L.vx_rates_adjoint_host.restype = ctypes.c_int
+    L.vx_rates_spectral_host.argtypes = [ctypes.c_void_p, ctypes.POINTER(vx_batch), ctypes.POINTER(vx_out),
+                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(vx_out)]
+    L.vx_rates_spectral_host.restype = ctypes.c_int
     L.vx_rates_check.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
     L.vx_rates_check.restype = ctypes.c_int
     L.vx_rates_entries_per_zone.argtypes = [ctypes.c_void_p]
@@ -147,6 +151,15 @@ def vx_rates_adjoint_host(h, batch: vx_batch, jac: int | None, fwd: vx_out | Non
     """Host arrays in and out (see the header); synchronous."""
     _check(lib().vx_rates_adjoint_host(h, ctypes.byref(batch), ctypes.c_void_p(jac or 0),
                                        ctypes.byref(fwd) if fwd is not None else None), "vx_rates_adjoint_host")
+
+
+def vx_rates_spectral_host(h, batch: vx_batch, grad_out: vx_out | None, grad_J: int | None, grad_H: int | None,
+                           blocks: int | None, fwd: vx_out | None) -> None:
+    """Host arrays in and out (see the header); synchronous."""
+    st = lib().vx_rates_spectral_host(h, ctypes.byref(batch), ctypes.byref(grad_out) if grad_out is not None else None,
+                                      ctypes.c_void_p(grad_J or 0), ctypes.c_void_p(grad_H or 0),
+                                      ctypes.c_void_p(blocks or 0), ctypes.byref(fwd) if fwd is not None else None)
+    _check(st, "vx_rates_spectral_host")
 
 
 def vx_rates_check(h, stream: int = 0) -> int:

@@ -110,10 +110,9 @@ struct vx_rates {
     int cc_major = 0, cc_minor = 0;
     // one cached executable graph per kernel kind: mixed forward, mixed tangents, FP64
     cudaGraphExec_t gexec[3] = {nullptr, nullptr, nullptr};
-    // host-buffer calls: two staging slots of `chunk` zones, each with its stream and counter
+    // host-buffer calls: two staging slots, each with its stream and work counter
     struct {
-        long long chunk = 0;
-        bool jac = false;                     // slots sized for the Jacobian too
+        size_t bytes = 0;                     // per slot
         double *buf[2] = {nullptr, nullptr};
         unsigned long long *cnt = nullptr;    // [2]
         cudaStream_t st[2] = {nullptr, nullptr};
@@ -688,39 +687,46 @@ vx_status vx_rates_spectral(vx_rates *h, const vx_batch *b, const vx_out *grad_o
 }
 
 // ---- host-buffer calls ----------------------------------------------------------------------
-// The batch is processed in chunks of VX_HOST_CHUNK zones through two staging slots of device
-// memory owned by the handle (allocated on first use, about 0.6 GB each with the Jacobian at
-// 21 bins and 3 species). Each slot has its own stream and work counter, so the copies of one
-// chunk overlap the kernel of the next. Host arrays should be pinned for the copies to be
-// asynchronous; the call returns when every output is in host memory.
-#ifndef VX_HOST_CHUNK
-#define VX_HOST_CHUNK 65536
+// The batch is processed in chunks of zones through two staging slots of device memory owned by
+// the handle (VX_HOST_SLOT_BYTES each, or VX_HOST_SLOT_MB MiB from the environment, allocated on
+// first use). Each call sizes its chunk to what
+// one zone of its inputs and outputs occupies (~70k zones with the Jacobian, ~13k with spectral
+// blocks at 21 bins and 3 species). Each slot has its own stream and work counter, so the copies
+// of one chunk overlap the kernel of the next. Host arrays should be pinned for the copies to be
+// asynchronous; the calls return when every output is in host memory.
+#ifndef VX_HOST_SLOT_BYTES
+#define VX_HOST_SLOT_BYTES (640ull << 20)
 #endif
 
-static vx_status host_prepare(vx_rates *h, bool adj) {
+static vx_status host_prepare(vx_rates *h) {
     auto &hs = h->hs;
-    if (hs.buf[0] && (hs.jac || !adj)) return VX_OK;
-    const size_t SN = (size_t)h->common.S * h->common.N;
-    const long long chunk = VX_HOST_CHUNK;
-    const size_t per_zone = 4 + 2 * SN + 4 * SN + (adj ? 12 * SN : 0);
-    for (int k = 0; k < 2; ++k) {
-        if (hs.st[k]) VX_CU(cudaStreamSynchronize(hs.st[k]));
-        cudaFree(hs.buf[k]);
-        hs.buf[k] = nullptr;
+    if (hs.buf[0]) return VX_OK;
+    hs.bytes = VX_HOST_SLOT_BYTES;
+    if (const char *mb = getenv("VX_HOST_SLOT_MB")) {
+        const long long v = atoll(mb);
+        if (v >= 1 && v <= (1ll << 20)) hs.bytes = (size_t)v << 20;
     }
     for (int k = 0; k < 2; ++k) {
-        cudaError_t e = cudaMalloc(&hs.buf[k], per_zone * chunk * sizeof(double));
+        cudaError_t e = cudaMalloc(&hs.buf[k], hs.bytes);
         if (e != cudaSuccess)
             return fail(e == cudaErrorMemoryAllocation ? VX_ERR_OOM : VX_ERR_CUDA, "staging slot: %s", cudaGetErrorString(e));
         if (!hs.st[k]) VX_CU(cudaStreamCreateWithFlags(&hs.st[k], cudaStreamNonBlocking));
     }
     if (!hs.cnt) VX_CU(cudaMalloc(&hs.cnt, 2 * sizeof(unsigned long long)));
-    hs.chunk = chunk;
-    hs.jac = adj;
     return VX_OK;
 }
 
-static vx_status host_run(vx_rates *h, const vx_batch *b, const vx_out *out, double *jac, bool adj) {
+// What one host-buffer call reads and writes (host pointers; NULL = absent).
+struct HostIO {
+    int kind;                 // 0 forward, 1 forward + tangents, 2 spectral derivatives
+    const vx_out *fwd;        // rates
+    double *jac;              // [Z][S][N][4][3]
+    const vx_out *seeds;      // VJP seeds (spectral)
+    double *grad_J, *grad_H;  // [Z][S][N]
+    double *blocks;           // [Z][S][4][N][N]
+};
+
+static vx_status host_validate_batch(const vx_rates *h, const vx_batch *b) {
     if (!h) return fail(VX_ERR_INVALID_ARG, "handle is NULL");
     if (!b) return fail(VX_ERR_INVALID_ARG, "batch is NULL");
     if (h->cfg.prec != VX_PREC_MIXED) return fail(VX_ERR_UNSUPPORTED, "the host-buffer calls are provided for the mixed form");
@@ -733,18 +739,32 @@ static vx_status host_run(vx_rates *h, const vx_batch *b, const vx_out *out, dou
         if ((long long)b->ray_offsets[b->n_rays] != b->n_zones)
             return fail(VX_ERR_INVALID_ARG, "ray_offsets[n_rays] = %d but n_zones = %lld", b->ray_offsets[b->n_rays], b->n_zones);
     }
-    if (adj && !jac && !out) return fail(VX_ERR_INVALID_ARG, "no output requested");
-    if (!adj && !out) return fail(VX_ERR_INVALID_ARG, "out is NULL");
-    if (out && (!out->j0 || !out->chi0 || !out->j1 || !out->chi1)) return fail(VX_ERR_INVALID_ARG, "an output array is NULL");
-    if (out && out->phi) return fail(VX_ERR_INVALID_ARG, "phi output is not produced by the host-buffer calls");
+    if (b->n_zones > 0 && (!b->state || !b->J || !b->H)) return fail(VX_ERR_INVALID_ARG, "state, J and H must be host arrays");
+    return VX_OK;
+}
+
+static vx_status host_run(vx_rates *h, const vx_batch *b, const HostIO &io) {
+    vx_status st = host_validate_batch(h, b);
+    if (st != VX_OK) return st;
+    if (io.fwd && (!io.fwd->j0 || !io.fwd->chi0 || !io.fwd->j1 || !io.fwd->chi1))
+        return fail(VX_ERR_INVALID_ARG, "an output array is NULL");
+    if (io.fwd && io.fwd->phi) return fail(VX_ERR_INVALID_ARG, "phi output is not produced by the host-buffer calls");
     if (b->n_zones == 0) return VX_OK;
-    if (!b->state || !b->J || !b->H) return fail(VX_ERR_INVALID_ARG, "state, J and H must be host arrays");
     DeviceGuard dg(h->device);
-    vx_status st;
-    if ((st = host_prepare(h, adj)) != VX_OK) return st;
+    if ((st = host_prepare(h)) != VX_OK) return st;
     auto &hs = h->hs;
-    const size_t SN = (size_t)h->common.S * h->common.N;
-    const long long Z = b->n_zones, chunk = hs.chunk;
+    const size_t S = h->common.S, N = h->common.N, SN = S * N;
+    const double *seed[4] = {nullptr, nullptr, nullptr, nullptr};
+    if (io.seeds) { seed[0] = io.seeds->j0; seed[1] = io.seeds->chi0; seed[2] = io.seeds->j1; seed[3] = io.seeds->chi1; }
+    int nseed = 0;
+    for (int k = 0; k < 4; ++k) nseed += seed[k] != nullptr;
+    // doubles per zone in a slot
+    const size_t per = 4 + 2 * SN + (io.fwd ? 4 * SN : 0) + (io.jac ? 12 * SN : 0) + nseed * SN +
+                       (io.grad_J ? 2 * SN : 0) + (io.blocks ? 4 * N * N * S : 0);
+    const long long chunk = (long long)(hs.bytes / (per * sizeof(double)));
+    if (chunk < 1) return fail(VX_ERR_UNSUPPORTED, "one zone does not fit a staging slot");
+    const long long Z = b->n_zones;
+    const bool adj = io.kind == 1;
     const int kind = adj ? 1 : 0;
     const size_t smem = adj ? h->smem_adj : h->smem_fwd;
     for (long long c = 0, z0 = 0; z0 < Z; ++c, z0 += chunk) {
@@ -752,8 +772,8 @@ static vx_status host_run(vx_rates *h, const vx_batch *b, const vx_out *out, dou
         const int sl = (int)(c & 1);
         cudaStream_t s = hs.st[sl];
         double *p = hs.buf[sl];
-        double *d_state = p, *d_J = d_state + 4 * chunk, *d_H = d_J + SN * chunk;
-        double *d_out = d_H + SN * chunk, *d_jac = d_out + 4 * SN * chunk;
+        auto take = [&](size_t count) { double *q = p; p += count; return q; };
+        double *d_state = take(4 * n), *d_J = take(SN * n), *d_H = take(SN * n);
         VX_CU(cudaMemcpyAsync(d_state, b->state + 4 * z0, 4 * n * sizeof(double), cudaMemcpyHostToDevice, s));
         VX_CU(cudaMemcpyAsync(d_J, b->J + SN * z0, SN * n * sizeof(double), cudaMemcpyHostToDevice, s));
         VX_CU(cudaMemcpyAsync(d_H, b->H + SN * z0, SN * n * sizeof(double), cudaMemcpyHostToDevice, s));
@@ -761,21 +781,43 @@ static vx_status host_run(vx_rates *h, const vx_batch *b, const vx_out *out, dou
         vx::Launch L{};
         fill_launch(h, &db, L);
         L.counter = hs.cnt + sl;
-        if (out) { L.j0 = d_out; L.chi0 = d_out + SN * n; L.j1 = d_out + 2 * SN * n; L.chi1 = d_out + 3 * SN * n; }
-        if (adj && jac) L.jac = d_jac;
+        double *d_out = nullptr, *d_jac = nullptr, *d_blk = nullptr, *d_gJ = nullptr, *d_gH = nullptr;
+        if (io.fwd) {
+            d_out = take(4 * SN * n);
+            L.j0 = d_out; L.chi0 = d_out + SN * n; L.j1 = d_out + 2 * SN * n; L.chi1 = d_out + 3 * SN * n;
+        }
+        if (io.jac) L.jac = d_jac = take(12 * SN * n);
+        if (nseed) {
+            const double **gs[4] = {&L.g_j0, &L.g_chi0, &L.g_j1, &L.g_chi1};
+            for (int k = 0; k < 4; ++k)
+                if (seed[k]) {
+                    double *q = take(SN * n);
+                    VX_CU(cudaMemcpyAsync(q, seed[k] + SN * z0, SN * n * sizeof(double), cudaMemcpyHostToDevice, s));
+                    *gs[k] = q;
+                }
+        }
+        if (io.grad_J) { L.grad_J = d_gJ = take(SN * n); L.grad_H = d_gH = take(SN * n); }
+        if (io.blocks) L.blocks = d_blk = take(4 * N * N * S * n);
         if ((st = autotune(h, adj, L, s)) != VX_OK) return st;
         const int mb = h->minb[kind];
         const int grid = (int)std::min<long long>(h->grid_mixed[kind][mb - 2], n);
         VX_CU(cudaMemsetAsync(L.counter, 0, sizeof(unsigned long long), s));
         VX_CU(vx::launch_mixed(adj, mb, L, grid, h->block_mixed, smem, s));
-        if (out) {
-            double *dst[4] = {out->j0, out->chi0, out->j1, out->chi1};
+        if (io.fwd) {
+            double *dst[4] = {io.fwd->j0, io.fwd->chi0, io.fwd->j1, io.fwd->chi1};
             for (int k = 0; k < 4; ++k)
                 VX_CU(cudaMemcpyAsync(dst[k] + SN * z0, d_out + k * SN * n, SN * n * sizeof(double),
                                       cudaMemcpyDeviceToHost, s));
         }
-        if (adj && jac)
-            VX_CU(cudaMemcpyAsync(jac + 12 * SN * z0, d_jac, 12 * SN * n * sizeof(double), cudaMemcpyDeviceToHost, s));
+        if (d_jac)
+            VX_CU(cudaMemcpyAsync(io.jac + 12 * SN * z0, d_jac, 12 * SN * n * sizeof(double), cudaMemcpyDeviceToHost, s));
+        if (d_gJ) {
+            VX_CU(cudaMemcpyAsync(io.grad_J + SN * z0, d_gJ, SN * n * sizeof(double), cudaMemcpyDeviceToHost, s));
+            VX_CU(cudaMemcpyAsync(io.grad_H + SN * z0, d_gH, SN * n * sizeof(double), cudaMemcpyDeviceToHost, s));
+        }
+        if (d_blk)
+            VX_CU(cudaMemcpyAsync(io.blocks + 4 * N * N * S * z0, d_blk, 4 * N * N * S * n * sizeof(double),
+                                  cudaMemcpyDeviceToHost, s));
     }
     VX_CU(cudaStreamSynchronize(hs.st[0]));
     VX_CU(cudaStreamSynchronize(hs.st[1]));
@@ -783,11 +825,23 @@ static vx_status host_run(vx_rates *h, const vx_batch *b, const vx_out *out, dou
 }
 
 vx_status vx_rates_eval_host(vx_rates *h, const vx_batch *host_batch, const vx_out *host_out) {
-    return host_run(h, host_batch, host_out, nullptr, false);
+    if (!host_out) return fail(VX_ERR_INVALID_ARG, "out is NULL");
+    return host_run(h, host_batch, HostIO{0, host_out, nullptr, nullptr, nullptr, nullptr, nullptr});
 }
 
 vx_status vx_rates_adjoint_host(vx_rates *h, const vx_batch *host_batch, double *host_jac, const vx_out *host_fwd) {
-    return host_run(h, host_batch, host_fwd, host_jac, true);
+    if (!host_jac && !host_fwd) return fail(VX_ERR_INVALID_ARG, "no output requested");
+    return host_run(h, host_batch, HostIO{1, host_fwd, host_jac, nullptr, nullptr, nullptr, nullptr});
+}
+
+vx_status vx_rates_spectral_host(vx_rates *h, const vx_batch *host_batch, const vx_out *host_grad_out,
+                                 double *host_grad_J, double *host_grad_H, double *host_blocks,
+                                 const vx_out *host_fwd) {
+    if (!host_blocks && !host_grad_J && !host_grad_H && !host_fwd) return fail(VX_ERR_INVALID_ARG, "no output requested");
+    if (!host_grad_J != !host_grad_H) return fail(VX_ERR_INVALID_ARG, "grad_J and grad_H go together");
+    if (host_grad_J && !host_grad_out) return fail(VX_ERR_INVALID_ARG, "grad_J and grad_H need grad_out");
+    return host_run(h, host_batch,
+                    HostIO{2, host_fwd, nullptr, host_grad_J ? host_grad_out : nullptr, host_grad_J, host_grad_H, host_blocks});
 }
 
 vx_status vx_rates_check(vx_rates *h, vx_stream stream) {

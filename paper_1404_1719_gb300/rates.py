@@ -197,6 +197,33 @@ class PairRates:
         return res
 
 
+    def spectral_host(self, state, J, H, grad_out=None, blocks: bool = True, forward: bool = False,
+                      ray_offsets=None) -> dict:
+        """Spectral derivatives on host arrays (vx_rates_spectral_host): blocks and/or, for host
+        seeds grad_out, grad_J and grad_H; forward=True adds the rates."""
+        b, Z = self._host_batch(state, J, H, ray_offsets)
+        res = {}
+        pin = dict(dtype=torch.float64, pin_memory=True)
+        if blocks:
+            res["blocks"] = torch.empty((Z, self.S, 4, self.N, self.N), **pin)
+        g = None
+        if grad_out is not None:
+            seeds = {k: np.ascontiguousarray(torch.as_tensor(v).numpy() if torch.is_tensor(v) else v, dtype=np.float64)
+                     for k, v in grad_out.items() if v is not None}
+            g = capi.vx_out(*((seeds[k].ctypes.data if k in seeds else None) for k in _OUT_KEYS), None)
+            g._keep = seeds
+            res["grad_J"] = torch.empty((Z, self.S, self.N), **pin)
+            res["grad_H"] = torch.empty((Z, self.S, self.N), **pin)
+        fwd = None
+        if forward:
+            fw, fwd = self._host_out(Z, None)
+            res.update(fw)
+        with torch.cuda.device(self.device):
+            capi.vx_rates_spectral_host(self._h, b, g, _ptr(res.get("grad_J")), _ptr(res.get("grad_H")),
+                                        _ptr(res.get("blocks")), fwd)
+        return res
+
+
 class VxRatesFn(torch.autograd.Function):
     """(j0, chi0, j1, chi1) = f(state, J, H): forward through vx_rates_eval; backward through the
     adjoint kernel (state: T, eta_e; the Y_e and rho entries are zero for this process) and the
