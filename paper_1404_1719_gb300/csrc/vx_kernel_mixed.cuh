@@ -71,6 +71,12 @@
 #ifndef VX_UNROLL_ADJ
 #define VX_UNROLL_ADJ 32
 #endif
+// Degenerate path of the forward kernel: nodes per unrolled chunk where it divides n_e (16
+// otherwise; the tangent kernel keeps 16). GB300, 16 x 48 eta <= 63 workload: forward 617 / 600 ms
+// at 16 / 48; the tangent kernel is slower at 48 (1440 vs 1399 ms).
+#ifndef VX_UNROLL_DEG_FWD
+#define VX_UNROLL_DEG_FWD 48
+#endif
 // Degenerate path: e2 from the mirror node's e1 (saves one ex2 per node, costs registers).
 #ifndef VX_DEG_MIRROR
 #define VX_DEG_MIRROR 0
@@ -156,7 +162,8 @@ struct DegPacked {
     static __device__ __forceinline__ void body(const NodeMir *__restrict__ nm, float B, float Pp, float Bq, float Bl,
                                                 float Pq, float Pl, float h, float Em, float c1, Mom &mo, Mom &ta,
                                                 Mom &tp, Mom &et) {
-        constexpr int U = 16;
+        constexpr int UD = ADJ ? 16 : VX_UNROLL_DEG_FWD;
+        constexpr int U = (NE > 0 && NE % UD == 0) ? UD : 16;
         const float2 Bq2 = make_float2(Bq, Bq), Bl2 = make_float2(Bl, Bl), Pq2 = make_float2(Pq, Pq);
         const float2 Pl2 = make_float2(Pl, Pl), B2 = make_float2(B, B), Pp2 = make_float2(Pp, Pp);
         const float2 c12 = make_float2(c1, c1), h2 = make_float2(h, h), Em2 = make_float2(Em, Em);
