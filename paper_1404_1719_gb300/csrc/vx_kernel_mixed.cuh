@@ -77,10 +77,6 @@
 #ifndef VX_UNROLL_DEG_FWD
 #define VX_UNROLL_DEG_FWD 48
 #endif
-// Degenerate path: e2 from the mirror node's e1 (saves one ex2 per node, costs registers).
-#ifndef VX_DEG_MIRROR
-#define VX_DEG_MIRROR 0
-#endif
 
 namespace vx {
 
@@ -124,8 +120,7 @@ struct ZoneSh {
     float iB, iP;      // their inverses
     float sc;          // degenerate path: blocking factor carried as O 2^sc (keeps the deepest-
     float c1;          //   blocked nodes of the zone far from the FP32 underflow); c1 = 2^-sc
-    float K, K2;       // e2 on a node from e1 on its mirror node: K = e^{-2|eta|}, K2 = e^{-|eta|}
-    float p2sc;        // 2^sc
+    float K;           // e^{-2|eta|}: e2 on a node from e1 on its mirror node (fast path)
     float mu_hi, mu_lo;  // |eta| T, the Fermi edge of the split rule, as an FP32 pair
     double unsc;       // 2^-sc, applied in FP64 to every result of the zone
     double iT2;        // 1/T^2
@@ -330,7 +325,7 @@ template <int NE, bool ADJ, bool DEG>
 __device__ __forceinline__ void node_loop(const NodeSm *__restrict__ nd, const NodeMir *__restrict__ nm, int ne,
                                           float B, float Pe,
                                           float Pp, float Bq, float Bl, float Pq, float Pl, float h,
-                                          float Em, float c1, float K, float K2, Mom &mo, Mom &ta,
+                                          float Em, float c1, float K, Mom &mo, Mom &ta,
                                           Mom &tp, Mom &et) {
     constexpr bool MIRROR = !DEG && NE > 0;
     constexpr bool MPAIR = !ADJ || VX_ADJ_PAIR;
@@ -468,24 +463,6 @@ __device__ __forceinline__ void node_loop(const NodeSm *__restrict__ nd, const N
     } else if (DEG && NE > 0 && VX_F32X2 && (ADJ ? VX_DEG_PACK_ADJ : VX_DEG_PACK_FWD)) {
         DegPacked<NE, ADJ, (ADJ ? VX_DEG_PACK_ADJ : VX_DEG_PACK_FWD) == 2>::run(nm, B, Pp, Bq, Bl, Pq, Pl, h, Em, c1, mo,
                                                                               ta, tp, et);
-    } else if (NE > 0 && VX_DEG_MIRROR) {
-        // degenerate path: e1 from the exact split on both nodes of a mirror pair, and
-        // e2(tau) = e1(-tau) 2^sc e^{-2|eta|} as (e1(-tau) K) K2, K = 2^sc e^{-|eta|}, K2 = e^{-|eta|}
-        // (the intermediate is e^{-Ebar(tau)/T} <= 1 and both factors are normal for |eta| <= 80)
-        static_assert(NE % U == 0 || NE == 0, "unrolled instantiations need a multiple of the unroll depth");
-#pragma unroll 1
-        for (int k0 = 0; k0 < NE / 2; k0 += U / 2) {
-#pragma unroll
-            for (int kk = 0; kk < U / 2; ++kk) {
-                const NodeSm qa = nd[k0 + kk], qb = nd[NE - 1 - k0 - kk];
-                const float ea = ex2a(-fmaf(Bq, qa.b.y, Pq)) * ex2a(-fmaf(Bq, qa.b.z, fmaf(Bl, qa.a.x, Pl)));
-                const float eb = ex2a(-fmaf(Bq, qb.b.y, Pq)) * ex2a(-fmaf(Bq, qb.b.z, fmaf(Bl, qb.a.x, Pl)));
-                const float fa = (eb * K) * K2, fb = (ea * K) * K2;
-                const float ta_ = c1 + ea, tb_ = c1 + eb;
-                accum(qa, ea, fa, ta_, rcpa(fmaf(ta_, fa, ta_)));
-                accum(qb, eb, fb, tb_, rcpa(fmaf(tb_, fb, tb_)));
-            }
-        }
     } else if (NE > 0) {
 #pragma unroll 1
         for (int k0 = 0; k0 < NE; k0 += U) {
@@ -616,7 +593,6 @@ __global__ void __launch_bounds__(MINB == 3 ? (ADJ ? VX_LB3_THREADS_ADJ : VX_TPB
             if (ae <= VX_ETA_MAX) {
                 const double LOG2E = 1.4426950408889634;
                 zs.K = (float)exp2neg(2.0 * ae * LOG2E);  // e^{-2|eta|}
-                zs.K2 = (float)exp2neg(ae * LOG2E);       // e^{-|eta|}
             }
         }
         if (tid == 0) {
@@ -657,7 +633,6 @@ __global__ void __launch_bounds__(MINB == 3 ? (ADJ ? VX_LB3_THREADS_ADJ : VX_TPB
                     zs.c1 = 1.f;
                     zs.unsc = 1.0;
                 }
-                zs.p2sc = ldexpf(1.f, (int)zs.sc);
                 zs.sB = ldexpf(1.f, kb);
                 zs.iB = ldexpf(1.f, -kb);
                 zs.sP = ldexpf(1.f, kb + 11);
@@ -779,7 +754,7 @@ __global__ void __launch_bounds__(MINB == 3 ? (ADJ ? VX_LB3_THREADS_ADJ : VX_TPB
                     }
                 } else if (!deg) {
                     const float Pe = fmaf(Em, il_h, -el_h);
-                    node_loop<NE, ADJ, false>(s_nodes, s_mir, C.n_e, B, Pe, Pp, 0.f, 0.f, 0.f, 0.f, h, Em, 1.f, zs.K, 0.f, mo, ta, tp, et);
+                    node_loop<NE, ADJ, false>(s_nodes, s_mir, C.n_e, B, Pe, Pp, 0.f, 0.f, 0.f, 0.f, h, Em, 1.f, zs.K, mo, ta, tp, et);
                     const Coef cf = make_coef(kp, km, k0, R1.w);
                     project(PO, mo, cf);
                     if (ADJ) {
@@ -804,7 +779,7 @@ __global__ void __launch_bounds__(MINB == 3 ? (ADJ ? VX_LB3_THREADS_ADJ : VX_TPB
                     float Pq = __fmul_rn(rintf(__fmul_rn(s, zs.sP)), zs.iP);
                     float Pl = __fadd_rn(__fsub_rn(s, Pq), slo);
                     Pq = __fadd_rn(Pq, zs.sc);  // exact: an integer on the same grid
-                    node_loop<NE, ADJ, true>(s_nodes, s_mir, C.n_e, B, 0.f, Pp, Bq, Bl, Pq, Pl, h, Em, zs.c1, zs.K2 * zs.p2sc, zs.K2, mo, ta, tp, et);
+                    node_loop<NE, ADJ, true>(s_nodes, s_mir, C.n_e, B, 0.f, Pp, Bq, Bl, Pq, Pl, h, Em, zs.c1, 0.f, mo, ta, tp, et);
                     const Coef cf = make_coef(kp, km, k0, R1.w);
                     project(PO, mo, cf);
                     if (ADJ) {
