@@ -127,6 +127,7 @@ struct ZoneSh {
     int sv;            // production vectors carried as v 2^sv (degenerate zones); the two scales
                        //   share the FP32 exponent headroom so no product can overflow
     int deg, neg, bad;
+    bool r2ok;         // degenerate path: r^2 stays in the FP32 range (tangents in the r^2 form)
 };
 
 // Moments of one quantity against the three non-negative basis weights.
@@ -152,7 +153,7 @@ struct NodeMir {
 
 // Degenerate path, packed on mirror pairs: exact-split electron argument, direct positron argument,
 // first-order products with r (see node_loop), inline or as an out-of-line call (OUTLINE).
-template <int NE, bool ADJ, bool OUTLINE>
+template <int NE, bool ADJ, bool OUTLINE, bool R2>
 struct DegPacked {
     static __device__ __forceinline__ void body(const NodeMir *__restrict__ nm, float B, float Pp, float Bq, float Bl,
                                                 float Pq, float Pl, float h, float Em, float c1, Mom &mo, Mom &ta,
@@ -185,14 +186,27 @@ struct DegPacked {
                 M2 = __ffma2_rn(cmp, r, M2);
                 Z2 = __ffma2_rn(c00, r, Z2);
                 if (ADJ) {
-                    const float2 qv = __ffma2_rn(e2, r, r);  // (1 + e2) r
-                    const float2 se = __fmul2_rn(c12, qv);   // 1 - f_e
-                    const float2 sp = __fmul2_rn(t, r);      // 1 - f_ebar
-                    const float2 fe = __fmul2_rn(e1, qv), fp = __fmul2_rn(e2, sp);
                     const float2 E2 = __ffma2_rn(h2, u2, Em2), Eb2 = __ffma2_rn(h2, v2, Em2);
-                    const float2 ga = __fmul2_rn(__ffma2_rn(fe, E2, __fmul2_rn(fp, Eb2)), r);
-                    const float2 gp = __fmul2_rn(__ffma2_rn(se, E2, __fmul2_rn(sp, Eb2)), r);
-                    const float2 ge = __fmul2_rn(__ffma2_rn(fe, mone2, fp), r);
+                    float2 ga, gp, ge;
+                    if (R2) {
+                        // r = 2^sc O with r^2 in the FP32 range (zone scale chosen for it):
+                        // (1 - f_e) r = c1 (1 + e2) r^2, (1 - f_ebar) r = t r^2, f_e r = e1 (1 + e2) r^2,
+                        // f_ebar r = e2 t r^2
+                        const float2 r2 = __fmul2_rn(r, r);
+                        const float2 s0 = __ffma2_rn(e2, r2, r2), p = __fmul2_rn(t, r2);
+                        const float2 a1 = __fmul2_rn(e1, s0), a2 = __fmul2_rn(e2, p);
+                        ga = __ffma2_rn(a1, E2, __fmul2_rn(a2, Eb2));
+                        gp = __ffma2_rn(__fmul2_rn(c12, s0), E2, __fmul2_rn(p, Eb2));
+                        ge = __ffma2_rn(a1, mone2, a2);
+                    } else {
+                        const float2 qv = __ffma2_rn(e2, r, r);  // (1 + e2) r
+                        const float2 se = __fmul2_rn(c12, qv);   // 1 - f_e
+                        const float2 sp = __fmul2_rn(t, r);      // 1 - f_ebar
+                        const float2 fe = __fmul2_rn(e1, qv), fp = __fmul2_rn(e2, sp);
+                        ga = __fmul2_rn(__ffma2_rn(fe, E2, __fmul2_rn(fp, Eb2)), r);
+                        gp = __fmul2_rn(__ffma2_rn(se, E2, __fmul2_rn(sp, Eb2)), r);
+                        ge = __fmul2_rn(__ffma2_rn(fe, mone2, fp), r);
+                    }
                     TAp = __ffma2_rn(cpm, ga, TAp); TAm = __ffma2_rn(cmp, ga, TAm); TAz = __ffma2_rn(c00, ga, TAz);
                     TPp = __ffma2_rn(cpm, gp, TPp); TPm = __ffma2_rn(cmp, gp, TPm); TPz = __ffma2_rn(c00, gp, TPz);
                     ETp = __ffma2_rn(cpm, ge, ETp); ETm = __ffma2_rn(cmp, ge, ETm); ETz = __ffma2_rn(c00, ge, ETz);
@@ -325,7 +339,7 @@ template <int NE, bool ADJ, bool DEG>
 __device__ __forceinline__ void node_loop(const NodeSm *__restrict__ nd, const NodeMir *__restrict__ nm, int ne,
                                           float B, float Pe,
                                           float Pp, float Bq, float Bl, float Pq, float Pl, float h,
-                                          float Em, float c1, float K, Mom &mo, Mom &ta,
+                                          float Em, float c1, float K, bool r2ok, Mom &mo, Mom &ta,
                                           Mom &tp, Mom &et) {
     constexpr bool MIRROR = !DEG && NE > 0;
     constexpr bool MPAIR = !ADJ || VX_ADJ_PAIR;
@@ -461,8 +475,11 @@ __device__ __forceinline__ void node_loop(const NodeSm *__restrict__ nd, const N
             }
         }
     } else if (DEG && NE > 0 && VX_F32X2 && (ADJ ? VX_DEG_PACK_ADJ : VX_DEG_PACK_FWD)) {
-        DegPacked<NE, ADJ, (ADJ ? VX_DEG_PACK_ADJ : VX_DEG_PACK_FWD) == 2>::run(nm, B, Pp, Bq, Bl, Pq, Pl, h, Em, c1, mo,
-                                                                              ta, tp, et);
+        constexpr bool OL = (ADJ ? VX_DEG_PACK_ADJ : VX_DEG_PACK_FWD) == 2;
+        if (!ADJ || r2ok)
+            DegPacked<NE, ADJ, OL, ADJ>::run(nm, B, Pp, Bq, Bl, Pq, Pl, h, Em, c1, mo, ta, tp, et);
+        else
+            DegPacked<NE, ADJ, OL, false>::run(nm, B, Pp, Bq, Bl, Pq, Pl, h, Em, c1, mo, ta, tp, et);
     } else if (NE > 0) {
 #pragma unroll 1
         for (int k0 = 0; k0 < NE; k0 += U) {
@@ -615,9 +632,11 @@ __global__ void __launch_bounds__(MINB == 3 ? (ADJ ? VX_LB3_THREADS_ADJ : VX_TPB
                 zs.mu_lo = (float)(mu - (double)zs.mu_hi);
                 zs.deg = ae > C.eta_sw;
                 // zone scales: with O in [e^-|eta|, 1] and production vectors whose relevant
-                // entries reach e^-|eta| times their row's largest, lift both off the FP32 floor
-                int sc = zs.deg ? (int)floor(0.3 * el) : 0;
-                zs.sv = zs.deg ? (int)floor(0.4 * el) : 0;
+                // entries reach e^-|eta| times their row's largest, lift both off the FP32 floor.
+                // sc also keeps r^2 = (2^sc O)^2 above 2^-126 (sc >= el - 62); sc + sv stays
+                // floor(0.7 el), the headroom the contraction's products share
+                int sc = zs.deg ? max((int)floor(0.3 * el), (int)ceil(el - 62.0)) : 0;
+                zs.sv = zs.deg ? (int)floor(0.7 * el) - sc : 0;
                 zs.sc = (float)sc;
                 zs.c1 = ldexpf(1.f, -sc);
                 zs.unsc = ldexp(1.0, -sc);
@@ -633,6 +652,7 @@ __global__ void __launch_bounds__(MINB == 3 ? (ADJ ? VX_LB3_THREADS_ADJ : VX_TPB
                     zs.c1 = 1.f;
                     zs.unsc = 1.0;
                 }
+                zs.r2ok = zs.sc >= (float)(el - 62.0);  // the tangents' r^2 form is in range
                 zs.sB = ldexpf(1.f, kb);
                 zs.iB = ldexpf(1.f, -kb);
                 zs.sP = ldexpf(1.f, kb + 11);
@@ -754,7 +774,7 @@ __global__ void __launch_bounds__(MINB == 3 ? (ADJ ? VX_LB3_THREADS_ADJ : VX_TPB
                     }
                 } else if (!deg) {
                     const float Pe = fmaf(Em, il_h, -el_h);
-                    node_loop<NE, ADJ, false>(s_nodes, s_mir, C.n_e, B, Pe, Pp, 0.f, 0.f, 0.f, 0.f, h, Em, 1.f, zs.K, mo, ta, tp, et);
+                    node_loop<NE, ADJ, false>(s_nodes, s_mir, C.n_e, B, Pe, Pp, 0.f, 0.f, 0.f, 0.f, h, Em, 1.f, zs.K, false, mo, ta, tp, et);
                     const Coef cf = make_coef(kp, km, k0, R1.w);
                     project(PO, mo, cf);
                     if (ADJ) {
@@ -779,7 +799,7 @@ __global__ void __launch_bounds__(MINB == 3 ? (ADJ ? VX_LB3_THREADS_ADJ : VX_TPB
                     float Pq = __fmul_rn(rintf(__fmul_rn(s, zs.sP)), zs.iP);
                     float Pl = __fadd_rn(__fsub_rn(s, Pq), slo);
                     Pq = __fadd_rn(Pq, zs.sc);  // exact: an integer on the same grid
-                    node_loop<NE, ADJ, true>(s_nodes, s_mir, C.n_e, B, 0.f, Pp, Bq, Bl, Pq, Pl, h, Em, zs.c1, 0.f, mo, ta, tp, et);
+                    node_loop<NE, ADJ, true>(s_nodes, s_mir, C.n_e, B, 0.f, Pp, Bq, Bl, Pq, Pl, h, Em, zs.c1, 0.f, zs.r2ok, mo, ta, tp, et);
                     const Coef cf = make_coef(kp, km, k0, R1.w);
                     project(PO, mo, cf);
                     if (ADJ) {
