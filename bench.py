@@ -40,10 +40,10 @@ def entries(Z, N):
 
 
 # DRAM bytes (read + write) per zone of the forward + tangent kernel, from one ncu capture of the
-# 200-ray case of this workload (dram__bytes_read.sum + dram__bytes_write.sum = 90.9 + 592.9 MB
+# 200-ray case of this workload (dram__bytes_read.sum + dram__bytes_write.sum = 89.0 + 592.0 MB
 # for 80,000 zones); scaled to a launch by the zone count. Set to None whenever the kernel
 # changes, until it has been captured again.
-TRAFFIC_BYTES_PER_ZONE = None
+TRAFFIC_BYTES_PER_ZONE = 8512
 # rays of the default workload in --mode spectral (410k zones: 17 GB of blocks)
 SPECTRAL_RAYS = 1024
 
@@ -51,9 +51,10 @@ SPECTRAL_RAYS = 1024
 def algorithmic_flops_per_node(adj: bool) -> int:
     """FP32 operations the method needs per (zone, unordered bin pair, omega, E) node in the
     formulation the kernel evaluates (nodes in mirror pairs tau, -tau; tangents from r^2),
-    counting an FMA as 2 and an exp, reciprocal, add or multiply as 1: forward 14, tangents 33
-    more."""
-    return 47 if adj else 14
+    counting an FMA as 2 and an exp, reciprocal, add or multiply as 1: forward 14; with tangents
+    41, since the blocking factor's three moments then follow per (pair, omega) from the energy
+    tangents' (forward 8 per node + tangents 33)."""
+    return 41 if adj else 14
 
 
 def rank_batch(rank: int, rays=None, workload: int = WORKLOAD) -> dict:

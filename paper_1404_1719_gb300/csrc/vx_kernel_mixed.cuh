@@ -41,6 +41,17 @@
 #ifndef VX_ADJ_PAIR
 #define VX_ADJ_PAIR 0
 #endif
+// Tangent kernel, packed loops: the blocking factor's own moments from the two energy tangents
+// (1) instead of a separate accumulation (0). Per node GTa + GTp = O (E + Ebar) = O q0 with both
+// terms non-negative, so M(O) = (M(GTa) + M(GTp)) / q0 loses nothing to cancellation.
+#ifndef VX_MO_TANG
+#define VX_MO_TANG 1
+#endif
+// Packed loops: the positron energies of a mirror pair as the electron energies with the lanes
+// exchanged (1; Ebar(tau) = E(-tau) bit for bit) or from their own fused multiply-add (0).
+#ifndef VX_ESWAP
+#define VX_ESWAP 1
+#endif
 // Fast path in packed FP32x2 arithmetic (one instruction for the same operation on a node and its
 // mirror node) or in scalar FP32.
 #ifndef VX_F32X2
@@ -151,6 +162,15 @@ struct NodeMir {
     float4 a, b, c, d;
 };
 
+// Moments of the blocking factor from those of GTa and GTp: E + Ebar = 2 (h + E-) = q0 on every
+// node, and both tangents are non-negative.
+__device__ __forceinline__ void mo_from_tangents(Mom &mo, const Mom &ta, const Mom &tp, float h, float Em) {
+    const float iq = 0.5f * rcpa(h + Em);
+    mo.p = (ta.p + tp.p) * iq;
+    mo.m = (ta.m + tp.m) * iq;
+    mo.z = (ta.z + tp.z) * iq;
+}
+
 // Degenerate path, packed on mirror pairs: exact-split electron argument, direct positron argument,
 // first-order products with r (see node_loop), inline or as an out-of-line call (OUTLINE).
 template <int NE, bool ADJ, bool OUTLINE, bool R2>
@@ -182,11 +202,14 @@ struct DegPacked {
                 const float2 t = __fadd2_rn(c12, e1);
                 const float2 d = __ffma2_rn(t, e2, t);
                 const float2 r = make_float2(rcpa(d.x), rcpa(d.y));
-                P2 = __ffma2_rn(cpm, r, P2);
-                M2 = __ffma2_rn(cmp, r, M2);
-                Z2 = __ffma2_rn(c00, r, Z2);
+                if (!(ADJ && VX_MO_TANG)) {
+                    P2 = __ffma2_rn(cpm, r, P2);
+                    M2 = __ffma2_rn(cmp, r, M2);
+                    Z2 = __ffma2_rn(c00, r, Z2);
+                }
                 if (ADJ) {
-                    const float2 E2 = __ffma2_rn(h2, u2, Em2), Eb2 = __ffma2_rn(h2, v2, Em2);
+                    const float2 E2 = __ffma2_rn(h2, u2, Em2);
+                    const float2 Eb2 = VX_ESWAP ? make_float2(E2.y, E2.x) : __ffma2_rn(h2, v2, Em2);
                     float2 ga, gp, ge;
                     if (R2) {
                         // r = 2^sc O with r^2 in the FP32 range (zone scale chosen for it):
@@ -213,11 +236,15 @@ struct DegPacked {
                 }
             }
         }
-        mo.p = P2.x + P2.y; mo.m = M2.x + M2.y; mo.z = Z2.x + Z2.y;
         if (ADJ) {
             ta.p = TAp.x + TAp.y; ta.m = TAm.x + TAm.y; ta.z = TAz.x + TAz.y;
             tp.p = TPp.x + TPp.y; tp.m = TPm.x + TPm.y; tp.z = TPz.x + TPz.y;
             et.p = ETp.x + ETp.y; et.m = ETm.x + ETm.y; et.z = ETz.x + ETz.y;
+        }
+        if (ADJ && VX_MO_TANG) {
+            mo_from_tangents(mo, ta, tp, h, Em);
+        } else {
+            mo.p = P2.x + P2.y; mo.m = M2.x + M2.y; mo.z = Z2.x + Z2.y;
         }
     }
     static __device__ __noinline__ void outline(const NodeMir *__restrict__ nm, float B, float Pp, float Bq,
@@ -273,9 +300,11 @@ struct SplitUnit {
             const float2 r = make_float2(rcpa(d.x), rcpa(d.y));
             const float2 Wu = __fmul2_rn(W2, u2);
             const float2 cp = __fmul2_rn(Wu, u2), c0 = __fmul2_rn(Wu, v2), cm = __fmul2_rn(__fmul2_rn(W2, v2), v2);
-            P2 = __ffma2_rn(cp, r, P2);
-            M2 = __ffma2_rn(cm, r, M2);
-            Z2 = __ffma2_rn(c0, r, Z2);
+            if (!(ADJ && VX_MO_TANG)) {
+                P2 = __ffma2_rn(cp, r, P2);
+                M2 = __ffma2_rn(cm, r, M2);
+                Z2 = __ffma2_rn(c0, r, Z2);
+            }
             if (ADJ) {
                 const float2 qv = __ffma2_rn(e2, r, r);  // (1 + e2) r
                 const float2 se = __fmul2_rn(c12, qv);   // 1 - f_e
@@ -290,11 +319,15 @@ struct SplitUnit {
                 ETp = __ffma2_rn(cp, ge, ETp); ETm = __ffma2_rn(cm, ge, ETm); ETz = __ffma2_rn(c0, ge, ETz);
             }
         }
-        mo.p = P2.x + P2.y; mo.m = M2.x + M2.y; mo.z = Z2.x + Z2.y;
         if (ADJ) {
             ta.p = TAp.x + TAp.y; ta.m = TAm.x + TAm.y; ta.z = TAz.x + TAz.y;
             tp.p = TPp.x + TPp.y; tp.m = TPm.x + TPm.y; tp.z = TPz.x + TPz.y;
             et.p = ETp.x + ETp.y; et.m = ETm.x + ETm.y; et.z = ETz.x + ETz.y;
+        }
+        if (ADJ && VX_MO_TANG) {
+            mo_from_tangents(mo, ta, tp, h, Em);
+        } else {
+            mo.p = P2.x + P2.y; mo.m = M2.x + M2.y; mo.z = Z2.x + Z2.y;
         }
     }
     static __device__ __noinline__ void outline(const float4 *__restrict__ hs, int nh, float rA, float B, float dls,
@@ -419,12 +452,15 @@ __device__ __forceinline__ void node_loop(const NodeSm *__restrict__ nd, const N
                 } else {
                     r = make_float2(rcpa(d.x), rcpa(d.y));
                 }
-                P2 = __ffma2_rn(cpm, r, P2);
-                M2 = __ffma2_rn(cmp, r, M2);
-                Z2 = __ffma2_rn(c00, r, Z2);
+                if (!(ADJ && VX_MO_TANG)) {
+                    P2 = __ffma2_rn(cpm, r, P2);
+                    M2 = __ffma2_rn(cmp, r, M2);
+                    Z2 = __ffma2_rn(c00, r, Z2);
+                }
                 if (ADJ) {
                     const float2 vu = make_float2(q.b.x, q.b.y);
-                    const float2 E2 = __ffma2_rn(h2, uv, Em2), Eb2 = __ffma2_rn(h2, vu, Em2);
+                    const float2 E2 = __ffma2_rn(h2, uv, Em2);
+                    const float2 Eb2 = VX_ESWAP ? make_float2(E2.y, E2.x) : __ffma2_rn(h2, vu, Em2);
                     const float2 r2 = __fmul2_rn(r, r);
                     const float2 s0 = __ffma2_rn(f, r2, r2), p = __fmul2_rn(t, r2);
                     const float2 a1 = __fmul2_rn(e, s0), a2 = __fmul2_rn(f, p);
@@ -437,11 +473,15 @@ __device__ __forceinline__ void node_loop(const NodeSm *__restrict__ nd, const N
                 }
             }
         }
-        mo.p = P2.x + P2.y; mo.m = M2.x + M2.y; mo.z = Z2.x + Z2.y;
         if (ADJ) {
             ta.p = TAp.x + TAp.y; ta.m = TAm.x + TAm.y; ta.z = TAz.x + TAz.y;
             tp.p = TPp.x + TPp.y; tp.m = TPm.x + TPm.y; tp.z = TPz.x + TPz.y;
             et.p = ETp.x + ETp.y; et.m = ETm.x + ETm.y; et.z = ETz.x + ETz.y;
+        }
+        if (ADJ && VX_MO_TANG) {
+            mo_from_tangents(mo, ta, tp, h, Em);
+        } else {
+            mo.p = P2.x + P2.y; mo.m = M2.x + M2.y; mo.z = Z2.x + Z2.y;
         }
     } else if (MIRROR) {
         static_assert(NE % U == 0 || NE == 0, "unrolled instantiations need a multiple of the unroll depth");
