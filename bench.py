@@ -40,10 +40,10 @@ def entries(Z, N):
 
 
 # DRAM bytes (read + write) per zone of the forward + tangent kernel, from one ncu capture of the
-# 200-ray case of this workload (dram__bytes_read.sum + dram__bytes_write.sum = 89.0 + 592.0 MB
+# 200-ray case of this workload (dram__bytes_read.sum + dram__bytes_write.sum = 89.3 + 591.8 MB
 # for 80,000 zones); scaled to a launch by the zone count. Set to None whenever the kernel
 # changes, until it has been captured again.
-TRAFFIC_BYTES_PER_ZONE = 8512
+TRAFFIC_BYTES_PER_ZONE = 8514
 # rays of the default workload in --mode spectral (410k zones: 17 GB of blocks)
 SPECTRAL_RAYS = 1024
 
@@ -341,7 +341,8 @@ def run_ours(args):
                                                                     and not fwd_only and not split) else None),
                          "traffic_note": "ncu DRAM read+write of an 80,000-zone capture, scaled by zone count",
                          "peak_note": f"FP32 {nsm} SMs x 128 FMA x 2 x {mhz:.0f} MHz (median SM clock in the run)",
-                         "kernel": f"k_pair_mixed<{b['n_e']}, {kind}, {minb} CTAs/SM>"},
+                         "kernel": f"k_pair_mixed<{b['n_e']}, {kind}, "
+                                   f"{128 if minb == 2 else (80 if fwd_only else 96)}-register budget>"},
             "autotune": tune,
             **({"hbm": {"algorithmic_bytes_per_step": h2d + d2h,
                         "achieved_gbs": (h2d + d2h) / (ms_local / 1000) / 1e9,

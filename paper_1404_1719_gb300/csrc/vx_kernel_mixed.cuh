@@ -73,23 +73,34 @@
 #ifndef VX_DEG_PACK_FWD
 #define VX_DEG_PACK_FWD 1
 #endif
-// Nodes per unrolled chunk of the fast-path loop of the forward and tangent kernels (16 where
-// they do not divide n_e). GB300, workload 4: forward 290 / 278 ms at 16 / 64 nodes; tangents
-// 765 / 755 / 753 ms at 16 / 32 / 64.
+// Unrolling of the node loops (unroll_depth): chunks of the cap where it divides n_e; else, where
+// the loop may be unrolled whole, the whole rule if n_e is below the cap; else chunks of 16.
+// GB300, tangent kernel: workload 4 674 / 668 / 646 ms at caps 16 / 32 / 64 (fast loop); 16 x 48
+// eta <= 63 workload 1228 / 1211 ms with the degenerate loop in chunks of 16 / whole, but 1283 ms
+// with the fast loop whole as well. Forward kernel: workload 4 290 / 278 ms at 16 / 64; 16 x 48
+// workload 611 / 600 ms with the fast loop in chunks of 16 / whole, 617 / 600 ms with the
+// degenerate loop in chunks of 16 / 48 (whole at n_e = 64 it spills in the smaller register budget).
 #ifndef VX_UNROLL_FWD
 #define VX_UNROLL_FWD 64
 #endif
 #ifndef VX_UNROLL_ADJ
-#define VX_UNROLL_ADJ 32
+#define VX_UNROLL_ADJ 64
 #endif
-// Degenerate path of the forward kernel: nodes per unrolled chunk where it divides n_e (16
-// otherwise; the tangent kernel keeps 16). GB300, 16 x 48 eta <= 63 workload: forward 617 / 600 ms
-// at 16 / 48; the tangent kernel is slower at 48 (1440 vs 1399 ms).
 #ifndef VX_UNROLL_DEG_FWD
 #define VX_UNROLL_DEG_FWD 48
 #endif
+#ifndef VX_UNROLL_DEG_ADJ
+#define VX_UNROLL_DEG_ADJ 64
+#endif
 
 namespace vx {
+
+// Nodes per unrolled chunk of a node loop over NE nodes with unroll cap CAP (NE = 0: run-time n_e);
+// WHOLE allows the whole loop below the cap.
+template <int NE, int CAP, bool WHOLE>
+__host__ __device__ constexpr int unroll_depth() {
+    return NE > 0 && NE % CAP == 0 ? CAP : (WHOLE && NE > 0 && NE < CAP ? NE : 16);
+}
 
 __device__ __forceinline__ float ex2a(float x) {
     float y;
@@ -173,13 +184,13 @@ __device__ __forceinline__ void mo_from_tangents(Mom &mo, const Mom &ta, const M
 
 // Degenerate path, packed on mirror pairs: exact-split electron argument, direct positron argument,
 // first-order products with r (see node_loop), inline or as an out-of-line call (OUTLINE).
-template <int NE, bool ADJ, bool OUTLINE, bool R2>
+// (UD: unroll cap; the tangent kernel's loop may be unrolled whole.)
+template <int NE, bool ADJ, bool OUTLINE, bool R2, int UD>
 struct DegPacked {
     static __device__ __forceinline__ void body(const NodeMir *__restrict__ nm, float B, float Pp, float Bq, float Bl,
                                                 float Pq, float Pl, float h, float Em, float c1, Mom &mo, Mom &ta,
                                                 Mom &tp, Mom &et) {
-        constexpr int UD = ADJ ? 16 : VX_UNROLL_DEG_FWD;
-        constexpr int U = (NE > 0 && NE % UD == 0) ? UD : 16;
+        constexpr int U = unroll_depth<NE, UD, ADJ>();
         const float2 Bq2 = make_float2(Bq, Bq), Bl2 = make_float2(Bl, Bl), Pq2 = make_float2(Pq, Pq);
         const float2 Pl2 = make_float2(Pl, Pl), B2 = make_float2(B, B), Pp2 = make_float2(Pp, Pp);
         const float2 c12 = make_float2(c1, c1), h2 = make_float2(h, h), Em2 = make_float2(Em, Em);
@@ -368,7 +379,10 @@ __device__ __forceinline__ void df_diff(float ah, float al, float bh, float bl, 
 // w(1+tau)^2 <-> w(1-tau)^2). On the mirror node the electron argument is the positron argument
 // of tau less 2|eta|, so e2(tau) = e1(-tau) K and e2(-tau) = e1(tau) K with K = e^{-2|eta|}: one
 // ex2 and half a record read per node, and (MPAIR) one reciprocal per node pair.
-template <int NE, bool ADJ, bool DEG>
+// SPLIT: the kernel carries the split rule too; its degenerate loop then stays in chunks of 16
+// (unrolled whole beside the split loop it was slower: 16 x 48 eta <= 63 workload, 1758 vs
+// 1805 ms).
+template <int NE, bool ADJ, bool DEG, bool SPLIT>
 __device__ __forceinline__ void node_loop(const NodeSm *__restrict__ nd, const NodeMir *__restrict__ nm, int ne,
                                           float B, float Pe,
                                           float Pp, float Bq, float Bl, float Pq, float Pl, float h,
@@ -379,7 +393,7 @@ __device__ __forceinline__ void node_loop(const NodeSm *__restrict__ nd, const N
     constexpr int U = 16;
     // nodes per unrolled chunk of the mirror loop (a chunk must divide n_e)
     constexpr int UM0 = ADJ ? VX_UNROLL_ADJ : VX_UNROLL_FWD;
-    constexpr int UM = (NE > 0 && NE % UM0 == 0) ? UM0 : U;
+    constexpr int UM = unroll_depth<NE, UM0, !ADJ>();
     // tangent integrands of one node, accumulated with its basis weights (cp, cm, c0)
     auto tang = [&](float cp, float cm, float c0, float e1, float e2, float t, float r, float E, float Eb) {
         float ga, gp, ge;
@@ -516,10 +530,11 @@ __device__ __forceinline__ void node_loop(const NodeSm *__restrict__ nd, const N
         }
     } else if (DEG && NE > 0 && VX_F32X2 && (ADJ ? VX_DEG_PACK_ADJ : VX_DEG_PACK_FWD)) {
         constexpr bool OL = (ADJ ? VX_DEG_PACK_ADJ : VX_DEG_PACK_FWD) == 2;
+        constexpr int UDG = !ADJ ? VX_UNROLL_DEG_FWD : (SPLIT ? 16 : VX_UNROLL_DEG_ADJ);
         if (!ADJ || r2ok)
-            DegPacked<NE, ADJ, OL, ADJ>::run(nm, B, Pp, Bq, Bl, Pq, Pl, h, Em, c1, mo, ta, tp, et);
+            DegPacked<NE, ADJ, OL, ADJ, UDG>::run(nm, B, Pp, Bq, Bl, Pq, Pl, h, Em, c1, mo, ta, tp, et);
         else
-            DegPacked<NE, ADJ, OL, false>::run(nm, B, Pp, Bq, Bl, Pq, Pl, h, Em, c1, mo, ta, tp, et);
+            DegPacked<NE, ADJ, OL, false, UDG>::run(nm, B, Pp, Bq, Bl, Pq, Pl, h, Em, c1, mo, ta, tp, et);
     } else if (NE > 0) {
 #pragma unroll 1
         for (int k0 = 0; k0 < NE; k0 += U) {
@@ -814,7 +829,7 @@ __global__ void __launch_bounds__(MINB == 3 ? (ADJ ? VX_LB3_THREADS_ADJ : VX_TPB
                     }
                 } else if (!deg) {
                     const float Pe = fmaf(Em, il_h, -el_h);
-                    node_loop<NE, ADJ, false>(s_nodes, s_mir, C.n_e, B, Pe, Pp, 0.f, 0.f, 0.f, 0.f, h, Em, 1.f, zs.K, false, mo, ta, tp, et);
+                    node_loop<NE, ADJ, false, SPLIT>(s_nodes, s_mir, C.n_e, B, Pe, Pp, 0.f, 0.f, 0.f, 0.f, h, Em, 1.f, zs.K, false, mo, ta, tp, et);
                     const Coef cf = make_coef(kp, km, k0, R1.w);
                     project(PO, mo, cf);
                     if (ADJ) {
@@ -839,7 +854,7 @@ __global__ void __launch_bounds__(MINB == 3 ? (ADJ ? VX_LB3_THREADS_ADJ : VX_TPB
                     float Pq = __fmul_rn(rintf(__fmul_rn(s, zs.sP)), zs.iP);
                     float Pl = __fadd_rn(__fsub_rn(s, Pq), slo);
                     Pq = __fadd_rn(Pq, zs.sc);  // exact: an integer on the same grid
-                    node_loop<NE, ADJ, true>(s_nodes, s_mir, C.n_e, B, 0.f, Pp, Bq, Bl, Pq, Pl, h, Em, zs.c1, 0.f, zs.r2ok, mo, ta, tp, et);
+                    node_loop<NE, ADJ, true, SPLIT>(s_nodes, s_mir, C.n_e, B, 0.f, Pp, Bq, Bl, Pq, Pl, h, Em, zs.c1, 0.f, zs.r2ok, mo, ta, tp, et);
                     const Coef cf = make_coef(kp, km, k0, R1.w);
                     project(PO, mo, cf);
                     if (ADJ) {
