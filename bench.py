@@ -43,7 +43,7 @@ def entries(Z, N):
 # 200-ray case of this workload (dram__bytes_read.sum + dram__bytes_write.sum = 89.3 + 591.8 MB
 # for 80,000 zones); scaled to a launch by the zone count. Set to None whenever the kernel
 # changes, until it has been captured again.
-TRAFFIC_BYTES_PER_ZONE = 8514
+TRAFFIC_BYTES_PER_ZONE = None
 # rays of the default workload in --mode spectral (410k zones: 17 GB of blocks)
 SPECTRAL_RAYS = 1024
 

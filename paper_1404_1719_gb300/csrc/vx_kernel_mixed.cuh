@@ -166,11 +166,13 @@ struct NodeSm {
 };
 
 // The first n_e/2 nodes again, laid out for packed FP32x2 arithmetic on a mirror pair (tau, -tau)
-// (lane x: node k, lane y: node n_e-1-k): a = {1+tau, 1-tau, w(1+tau)^2, w(1-tau)^2}, b = the same
-// pairs swapped, c = {w(1-tau^2) twice, uh of both nodes}, d = {ul of both nodes, 0, 0}, with uh
-// and ul the split of 1 + tau used by the degenerate path.
+// (lane x: node k, lane y: node n_e-1-k): a = {1+tau, 1-tau, w(1+tau)^2, w(1-tau)^2} (1+tau of
+// both nodes, then their first weights), b = {w(1-tau)^2, w(1+tau)^2, w(1-tau^2) twice} (their
+// second and third weights), c = {uh of both nodes, ul of both nodes}, with uh and ul the split of
+// 1 + tau used by the degenerate path. The fast path reads a and b, the degenerate path all three;
+// 1 - tau of both nodes is a's first pair exchanged.
 struct NodeMir {
-    float4 a, b, c, d;
+    float4 a, b, c;
 };
 
 // Moments of the blocking factor from those of GTa and GTp: E + Ebar = 2 (h + E-) = q0 on every
@@ -202,11 +204,11 @@ struct DegPacked {
 #pragma unroll
             for (int kk = 0; kk < U / 2; ++kk) {
                 const NodeMir q = nm[k0 + kk];
-                const float2 u2 = make_float2(q.a.x, q.a.y), v2 = make_float2(q.b.x, q.b.y);
-                const float2 cpm = make_float2(q.a.z, q.a.w), cmp = make_float2(q.b.z, q.b.w);
-                const float2 c00 = make_float2(q.c.x, q.c.y);
-                const float2 sx = __ffma2_rn(Bq2, make_float2(q.c.z, q.c.w), Pq2);  // exact by the grid choice
-                const float2 lo = __ffma2_rn(Bq2, make_float2(q.d.x, q.d.y), __ffma2_rn(Bl2, u2, Pl2));
+                const float2 u2 = make_float2(q.a.x, q.a.y), v2 = make_float2(q.a.y, q.a.x);
+                const float2 cpm = make_float2(q.a.z, q.a.w), cmp = make_float2(q.b.x, q.b.y);
+                const float2 c00 = make_float2(q.b.z, q.b.w);
+                const float2 sx = __ffma2_rn(Bq2, make_float2(q.c.x, q.c.y), Pq2);  // exact by the grid choice
+                const float2 lo = __ffma2_rn(Bq2, make_float2(q.c.z, q.c.w), __ffma2_rn(Bl2, u2, Pl2));
                 const float2 e1 = __fmul2_rn(make_float2(ex2a(-sx.x), ex2a(-sx.y)), make_float2(ex2a(-lo.x), ex2a(-lo.y)));
                 const float2 xp = __ffma2_rn(B2, v2, Pp2);
                 const float2 e2 = make_float2(ex2a(-xp.x), ex2a(-xp.y));
@@ -452,7 +454,7 @@ __device__ __forceinline__ void node_loop(const NodeSm *__restrict__ nd, const N
             for (int kk = 0; kk < UM / 2; ++kk) {
                 const NodeMir q = nm[k0 + kk];
                 const float2 uv = make_float2(q.a.x, q.a.y), cpm = make_float2(q.a.z, q.a.w);
-                const float2 cmp = make_float2(q.b.z, q.b.w), c00 = make_float2(q.c.x, q.c.y);
+                const float2 cmp = make_float2(q.b.x, q.b.y), c00 = make_float2(q.b.z, q.b.w);
                 const float2 x = __ffma2_rn(B2, uv, Pe2);
                 const float ea = ex2a(-x.x), eb = ex2a(-x.y);  // e1(tau), e1(-tau)
                 const float2 e = make_float2(ea, eb);
@@ -472,7 +474,7 @@ __device__ __forceinline__ void node_loop(const NodeSm *__restrict__ nd, const N
                     Z2 = __ffma2_rn(c00, r, Z2);
                 }
                 if (ADJ) {
-                    const float2 vu = make_float2(q.b.x, q.b.y);
+                    const float2 vu = make_float2(q.a.y, q.a.x);
                     const float2 E2 = __ffma2_rn(h2, uv, Em2);
                     const float2 Eb2 = VX_ESWAP ? make_float2(E2.y, E2.x) : __ffma2_rn(h2, vu, Em2);
                     const float2 r2 = __fmul2_rn(r, r);
@@ -633,11 +635,10 @@ __global__ void __launch_bounds__(MINB == 3 ? (ADJ ? VX_LB3_THREADS_ADJ : VX_TPB
         s_nodes[k].a = make_float4(L.n32.u[k], L.n32.v[k], L.n32.cp[k], L.n32.cm[k]);
         s_nodes[k].b = make_float4(L.n32.c0[k], L.n32.uh[k], L.n32.ul[k], 0.f);
         if (k < C.n_e / 2) {
-            s_mir[k].a = make_float4(L.n32.u[k], L.n32.v[k], L.n32.cp[k], L.n32.cm[k]);
-            s_mir[k].b = make_float4(L.n32.v[k], L.n32.u[k], L.n32.cm[k], L.n32.cp[k]);
             const int km = C.n_e - 1 - k;
-            s_mir[k].c = make_float4(L.n32.c0[k], L.n32.c0[k], L.n32.uh[k], L.n32.uh[km]);
-            s_mir[k].d = make_float4(L.n32.ul[k], L.n32.ul[km], 0.f, 0.f);
+            s_mir[k].a = make_float4(L.n32.u[k], L.n32.v[k], L.n32.cp[k], L.n32.cm[k]);
+            s_mir[k].b = make_float4(L.n32.cm[k], L.n32.cp[k], L.n32.c0[k], L.n32.c0[k]);
+            s_mir[k].c = make_float4(L.n32.uh[k], L.n32.uh[km], L.n32.ul[k], L.n32.ul[km]);
         }
     }
     for (int p = tid; p < npair; p += blockDim.x) s_pij[p] = C.pij[p];
