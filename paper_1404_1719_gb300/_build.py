@@ -11,7 +11,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libvx_rates.so")
 SOURCES = ["vx_rates.cu", "vx_mixed_fwd_b2.cu", "vx_mixed_fwd_b3.cu", "vx_mixed_adj_b2.cu", "vx_mixed_adj_b3.cu",
-           "vx_fp64.cu"]
+           "vx_fp64.cu", "vx_btd.cu"]
 HEADERS = ["vx_internal.h", "vx_kernel_mixed.cuh", "vx_mixed_inst.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
@@ -26,7 +26,8 @@ def _stale() -> bool:
     if not os.path.exists(stamp) or open(stamp).read() != " ".join(EXTRA):
         return True
     t = os.path.getmtime(LIB)
-    deps = [os.path.join(CSRC, f) for f in SOURCES + HEADERS] + [os.path.join(INCLUDE, "vx_rates.h")]
+    deps = [os.path.join(CSRC, f) for f in SOURCES + HEADERS] + [os.path.join(INCLUDE, h)
+                                                                  for h in ("vx_rates.h", "vx_btd.h")]
     return any(os.path.getmtime(d) > t for d in deps)
 
 

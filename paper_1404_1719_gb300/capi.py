@@ -1,4 +1,5 @@
-"""ctypes binding of the C ABI in include/vx_rates.h: same names, argument marshalling only.
+"""ctypes binding of the C ABI in include/vx_rates.h and include/vx_btd.h: same names, argument
+marshalling only.
 
 The shared library is built in-tree by ``paper_1404_1719_gb300._build.build()``. There is no
 fallback: if it is missing or cannot be loaded, :func:`lib` raises.
@@ -45,7 +46,7 @@ class VxError(RuntimeError):
 SYMBOLS = ("vx_rates_create", "vx_rates_eval", "vx_rates_adjoint", "vx_rates_check",
            "vx_rates_entries_per_zone", "vx_rates_destroy", "vx_status_string", "vx_last_error",
            "vx_rates_eval_noalloc", "vx_rates_spectral", "vx_rates_eval_host", "vx_rates_adjoint_host",
-           "vx_rates_spectral_host")
+           "vx_rates_spectral_host", "vx_btd_create", "vx_btd_solve", "vx_btd_check", "vx_btd_destroy")
 
 _lib = None
 
@@ -91,6 +92,14 @@ def lib(path: str | None = None):
     L.vx_rates_eval_noalloc.restype = ctypes.c_int
     L.vx_last_error.argtypes = []
     L.vx_last_error.restype = ctypes.c_char_p
+    L.vx_btd_create.argtypes = [ctypes.c_int, ctypes.c_longlong, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]
+    L.vx_btd_create.restype = ctypes.c_int
+    L.vx_btd_solve.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong] + [ctypes.c_void_p] * 7
+    L.vx_btd_solve.restype = ctypes.c_int
+    L.vx_btd_check.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    L.vx_btd_check.restype = ctypes.c_int
+    L.vx_btd_destroy.argtypes = [ctypes.c_void_p]
+    L.vx_btd_destroy.restype = None
     _lib = L
     return L
 
@@ -176,3 +185,31 @@ def vx_rates_entries_per_zone(h) -> int:
 
 def vx_rates_destroy(h) -> None:
     lib().vx_rates_destroy(h)
+
+
+VX_BTD_MAX_M, VX_BTD_MAX_REFINE = 128, 8
+
+
+def vx_btd_create(m: int, max_zones: int, n_refine: int) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(lib().vx_btd_create(int(m), int(max_zones), int(n_refine), ctypes.byref(h)), "vx_btd_create")
+    return h
+
+
+def vx_btd_solve(h, n_rays: int, n_zones: int, ray_offsets: int, A: int, B: int, C: int, d: int, x: int,
+                 stream: int = 0) -> None:
+    st = lib().vx_btd_solve(h, int(n_rays), int(n_zones), *(ctypes.c_void_p(p or 0) for p in (ray_offsets, A, B, C, d, x)),
+                            ctypes.c_void_p(stream))
+    _check(st, "vx_btd_solve")
+
+
+def vx_btd_check(h, stream: int = 0) -> int:
+    """VX_OK or VX_ERR_NUMERIC (other failures raise)."""
+    st = lib().vx_btd_check(h, ctypes.c_void_p(stream))
+    if st not in (VX_OK, VX_ERR_NUMERIC):
+        raise VxError(st, "vx_btd_check")
+    return st
+
+
+def vx_btd_destroy(h) -> None:
+    lib().vx_btd_destroy(h)

@@ -1,0 +1,558 @@
+// vx_btd.cu -- batched block-tridiagonal solve of the per-ray Newton systems (include/vx_btd.h).
+//
+// Three kernels, all one ray per CTA (or per warp), since a ray's zones are a sequential chain:
+//  * k_btd_factor: block LU along the ray in FP32. Per zone: load B_k (and A_k) as FP32 into shared
+//    memory, form the Schur complement D_k = B_k - A_k G_{k-1} (G_{k-1} is still in shared memory
+//    from the previous zone; 4 x 4 register tiles), factor D_k with partial pivoting (warp 0 picks
+//    the pivot, swaps and scales; the CTA updates the trailing block), then G_k = D_k^{-1} C_k by
+//    forward and back substitution over the m right-hand sides. The factors, G_k and an FP32 copy
+//    of A_k are written column-major, the row permutation as an index vector.
+//  * k_btd_sweep: one warp per ray solves M delta = rhs with those factors: forward
+//    y_k = D_k^{-1} (rhs_k - A_k y_{k-1}), backward delta_k = y_k - G_k delta_{k+1}; a lane holds
+//    rows lane + 32 t of a zone's vector and the column being eliminated is broadcast by shuffle.
+//    The first sweep writes x = delta, later ones add delta to x in FP64.
+//  * k_btd_resid: the FP64 residual r = d - M x from the caller's FP64 blocks, one warp per zone
+//    row block, lanes across a row (coalesced), a fixed butterfly reduction per row.
+// The host runs factor, sweep, then n_refine times (resid, sweep), all on the caller's stream.
+#include "../../include/vx_btd.h"
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+namespace vx {
+vx_status set_error(vx_status s, const char *msg);  // the library's last-error text (vx_rates.cu)
+}
+
+namespace {
+
+constexpr int kFactorThreads = 256;
+constexpr int kSweepWarps = 4;
+constexpr int kResidThreads = 256;
+
+vx_status bfail(vx_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    return vx::set_error(s, buf);
+}
+
+#define BTD_CU(call)                                                                          \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return bfail(e_ == cudaErrorMemoryAllocation ? VX_ERR_OOM : VX_ERR_CUDA, "%s: %s (%s:%d)", \
+                         #call, cudaGetErrorString(e_), __FILE__, __LINE__);                  \
+    } while (0)
+
+struct BtdArgs {
+    int m, ld, n_rays;
+    long long n_zones;
+    const int *off;
+    const double *A, *B, *C, *d, *rhs;
+    double *x, *r;
+    float *LUt, *Gt, *At, *y;
+    int *perm, *zbad, *flag;
+    const int *inval;  // set by k_btd_validate when the offsets are not a partition of the zones
+};
+
+// The zone range of a ray; false (nothing to do) when the offsets failed validation.
+__device__ __forceinline__ bool ray_range(const BtdArgs &a, int ray, long long &z0, long long &z1) {
+    if (*a.inval) return false;
+    z0 = a.off[ray];
+    z1 = a.off[ray + 1];
+    return true;
+}
+
+// offsets[0] = 0, offsets[n_rays] = n_zones and non-decreasing; any violation marks the whole call
+// invalid (so no two rays can share zones) and raises the numeric flag.
+__global__ void k_btd_validate(const int *off, int n_rays, long long n_zones, int *inval, int *flag) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > n_rays) return;
+    const long long v = off[i];
+    bool bad = v < 0 || v > n_zones || (i == 0 && v != 0) || (i == n_rays && v != n_zones);
+    if (i < n_rays && off[i + 1] < v) bad = true;
+    if (bad) {
+        atomicOr(inval, 1);
+        atomicOr(flag, 1);
+    }
+}
+
+// sD -= sA sW over m x m blocks (row stride ld). Thread tiles of 4 x 4 with rows ti + r T and
+// columns tj + q T (T = ceil(m / 4)), so a warp's reads of sW fall in distinct banks.
+__device__ void schur_update(float *sD, const float *sA, const float *sW, int m, int ld) {
+    const int T = (m + 3) / 4;
+    for (int t = threadIdx.x; t < T * T; t += blockDim.x) {
+        const int ti = t / T, tj = t - ti * T;
+        float acc[4][4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[r][q] = 0.f;
+        for (int c = 0; c < m; ++c) {
+            float av[4], gv[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int i = ti + r * T;
+                av[r] = i < m ? sA[i * ld + c] : 0.f;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int j = tj + q * T;
+                gv[q] = j < m ? sW[c * ld + j] : 0.f;
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[r][q] = fmaf(av[r], gv[q], acc[r][q]);
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int i = ti + r * T, j = tj + q * T;
+                if (i < m && j < m) sD[i * ld + j] -= acc[r][q];
+            }
+    }
+    __syncthreads();
+}
+
+// In-place LU with partial pivoting of sD (P D = L U, unit L below the diagonal, U on and above).
+// Column j: warp 0 finds the pivot (largest magnitude, lowest row on ties), swaps the rows and
+// scales the multipliers; then the CTA updates the trailing block. A zero or non-finite pivot sets
+// *bad; the arithmetic then runs on (NaN/inf), which only this ray sees.
+__device__ void lu_factor(float *sD, int m, int ld, int *piv, int *bad) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int j = 0; j < m; ++j) {
+        if (warp == 0) {
+            float best = -1.f;
+            int bi = j;
+            for (int i = j + lane; i < m; i += 32) {
+                const float v = fabsf(sD[i * ld + j]);
+                if (v > best) {
+                    best = v;
+                    bi = i;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ob > best || (ob == best && oi < bi)) {
+                    best = ob;
+                    bi = oi;
+                }
+            }
+            if (lane == 0) {
+                piv[j] = bi;
+                if (!(best > 0.f) || !(best < INFINITY)) *bad = 1;
+            }
+            if (bi != j)
+                for (int c = lane; c < m; c += 32) {
+                    const float t = sD[j * ld + c];
+                    sD[j * ld + c] = sD[bi * ld + c];
+                    sD[bi * ld + c] = t;
+                }
+            __syncwarp();
+            const float inv = 1.f / sD[j * ld + j];
+            for (int i = j + 1 + lane; i < m; i += 32) sD[i * ld + j] *= inv;
+        }
+        __syncthreads();
+        for (int i = j + 1 + warp; i < m; i += nw) {
+            const float l = sD[i * ld + j];
+            for (int c = j + 1 + lane; c < m; c += 32) sD[i * ld + c] = fmaf(-l, sD[j * ld + c], sD[i * ld + c]);
+        }
+        __syncthreads();
+    }
+}
+
+// sW <- U^{-1} L^{-1} sW for the m right-hand sides in the columns of sW (already row-permuted).
+__device__ void lu_solve_block(const float *sD, float *sW, int m, int ld) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int j = 0; j + 1 < m; ++j) {
+        for (int i = j + 1 + warp; i < m; i += nw) {
+            const float l = sD[i * ld + j];
+            for (int c = lane; c < m; c += 32) sW[i * ld + c] = fmaf(-l, sW[j * ld + c], sW[i * ld + c]);
+        }
+        __syncthreads();
+    }
+    // back substitution on unscaled rows: row j is final once the rows below are eliminated, and
+    // it enters the rows above as (U_ij / U_jj) row_j; every row is divided by its pivot at the end
+    for (int j = m - 1; j > 0; --j) {
+        const float inv = 1.f / sD[j * ld + j];
+        for (int i = warp; i < j; i += nw) {
+            const float u = sD[i * ld + j] * inv;
+            for (int c = lane; c < m; c += 32) sW[i * ld + c] = fmaf(-u, sW[j * ld + c], sW[i * ld + c]);
+        }
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+        const int i = e / m, c = e - i * m;
+        sW[i * ld + c] /= sD[i * ld + i];
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kFactorThreads) k_btd_factor(const BtdArgs a) {
+    extern __shared__ __align__(16) float sm[];
+    __shared__ int s_bad;
+    const int m = a.m, ld = a.ld, tid = threadIdx.x, nt = blockDim.x;
+    float *sD = sm, *sW = sD + m * ld, *sA = sW + m * ld;
+    int *sPiv = reinterpret_cast<int *>(sA + m * ld);
+    int *sPerm = sPiv + m;
+    long long z0, z1;
+    if (!ray_range(a, blockIdx.x, z0, z1) || z1 == z0) return;
+    if (tid == 0) s_bad = 0;
+    const size_t mm = (size_t)m * m;
+    for (long long k = z0; k < z1; ++k) {
+        const bool prev = k > z0;
+        const double *Bk = a.B + k * mm, *Ak = a.A + k * mm;
+        for (int e = tid; e < m * m; e += nt) {
+            const int i = e / m, j = e - i * m;
+            sD[i * ld + j] = (float)Bk[e];
+            if (prev) sA[i * ld + j] = (float)Ak[e];
+        }
+        __syncthreads();
+        if (prev) {
+            schur_update(sD, sA, sW, m, ld);
+            float *At = a.At + k * mm;
+            for (int e = tid; e < m * m; e += nt) {
+                const int c = e / m, i = e - c * m;
+                At[e] = sA[i * ld + c];
+            }
+        }
+        lu_factor(sD, m, ld, sPiv, &s_bad);
+        if (tid == 0) {
+            for (int i = 0; i < m; ++i) sPerm[i] = i;
+            for (int j = 0; j < m; ++j) {
+                const int p = sPiv[j], t = sPerm[j];
+                sPerm[j] = sPerm[p];
+                sPerm[p] = t;
+            }
+        }
+        __syncthreads();
+        float *LUt = a.LUt + k * mm;
+        for (int e = tid; e < m * m; e += nt) {
+            const int c = e / m, i = e - c * m;
+            LUt[e] = sD[i * ld + c];
+        }
+        for (int i = tid; i < m; i += nt) a.perm[k * m + i] = sPerm[i];
+        if (k + 1 < z1) {
+            const double *Ck = a.C + k * mm;
+            for (int e = tid; e < m * m; e += nt) {
+                const int i = e / m, c = e - i * m;
+                sW[i * ld + c] = (float)Ck[(size_t)sPerm[i] * m + c];
+            }
+            __syncthreads();
+            lu_solve_block(sD, sW, m, ld);
+            float *Gt = a.Gt + k * mm;
+            for (int e = tid; e < m * m; e += nt) {
+                const int c = e / m, i = e - c * m;
+                Gt[e] = sW[i * ld + c];
+            }
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        a.zbad[z0] = s_bad;
+        if (s_bad) atomicOr(a.flag, 2);
+    }
+}
+
+template <bool FIRST, bool LAST>
+__global__ void __launch_bounds__(32 * kSweepWarps) k_btd_sweep(const BtdArgs a) {
+    __shared__ float s_buf[kSweepWarps][VX_BTD_MAX_M];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int ray = blockIdx.x * kSweepWarps + w;
+    if (ray >= a.n_rays) return;
+    long long z0, z1;
+    if (!ray_range(a, ray, z0, z1) || z1 == z0) return;
+    const int m = a.m;
+    const size_t mm = (size_t)m * m;
+    if (a.zbad[z0]) {
+        if (LAST)
+            for (long long e = z0 * m + lane; e < z1 * m; e += 32) a.x[e] = __longlong_as_double(0x7ff8000000000000ll);
+        return;
+    }
+    float v[4], yp[4] = {0.f, 0.f, 0.f, 0.f};
+    for (long long k = z0; k < z1; ++k) {
+        const double *rhs = a.rhs + k * m;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int i = lane + 32 * t;
+            v[t] = i < m ? (float)rhs[i] : 0.f;
+        }
+        if (k > z0) {  // rhs_k - A_k y_{k-1}
+            const float *At = a.At + k * mm;
+#pragma unroll
+            for (int tc = 0; tc < 4; ++tc) {
+                if (32 * tc >= m) break;
+                const int lim = m - 32 * tc < 32 ? m - 32 * tc : 32;
+                for (int l = 0; l < lim; ++l) {
+                    const int c = 32 * tc + l;
+                    const float yc = __shfl_sync(0xffffffffu, yp[tc], l);
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const int i = lane + 32 * t;
+                        if (i < m) v[t] = fmaf(-At[(size_t)c * m + i], yc, v[t]);
+                    }
+                }
+            }
+        }
+        // row permutation of the factorisation
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int i = lane + 32 * t;
+            if (i < m) s_buf[w][i] = v[t];
+        }
+        __syncwarp();
+        const int *perm = a.perm + k * m;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int i = lane + 32 * t;
+            if (i < m) v[t] = s_buf[w][perm[i]];
+        }
+        __syncwarp();
+        const float *LUt = a.LUt + k * mm;
+        // unit lower triangle
+#pragma unroll
+        for (int tj = 0; tj < 4; ++tj) {
+            if (32 * tj >= m - 1) break;
+            const int lim = m - 1 - 32 * tj < 32 ? m - 1 - 32 * tj : 32;
+            for (int l = 0; l < lim; ++l) {
+                const int j = 32 * tj + l;
+                const float vj = __shfl_sync(0xffffffffu, v[tj], l);
+#pragma unroll
+                for (int t = tj; t < 4; ++t) {
+                    const int i = lane + 32 * t;
+                    if (i > j && i < m) v[t] = fmaf(-LUt[(size_t)j * m + i], vj, v[t]);
+                }
+            }
+        }
+        // upper triangle, last row first
+#pragma unroll
+        for (int tj = 3; tj >= 0; --tj) {
+            if (32 * tj >= m) continue;
+            const int top = m - 32 * tj < 32 ? m - 32 * tj : 32;
+            for (int l = top - 1; l >= 0; --l) {
+                const int j = 32 * tj + l;
+                const float vj = __shfl_sync(0xffffffffu, v[tj], l) / LUt[(size_t)j * m + j];
+                if (lane == l) v[tj] = vj;
+#pragma unroll
+                for (int t = 0; t <= tj; ++t) {
+                    const int i = lane + 32 * t;
+                    if (i < j) v[t] = fmaf(-LUt[(size_t)j * m + i], vj, v[t]);
+                }
+            }
+        }
+        float *yk = a.y + k * m;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int i = lane + 32 * t;
+            if (i < m) yk[i] = v[t];
+            yp[t] = v[t];
+        }
+    }
+    // backward: delta_k = y_k - G_k delta_{k+1}; x += delta (FP64)
+    float dn[4] = {0.f, 0.f, 0.f, 0.f};
+    for (long long k = z1 - 1; k >= z0; --k) {
+        const float *yk = a.y + k * m;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int i = lane + 32 * t;
+            v[t] = i < m ? yk[i] : 0.f;
+        }
+        if (k + 1 < z1) {
+            const float *Gt = a.Gt + k * mm;
+#pragma unroll
+            for (int tc = 0; tc < 4; ++tc) {
+                if (32 * tc >= m) break;
+                const int lim = m - 32 * tc < 32 ? m - 32 * tc : 32;
+                for (int l = 0; l < lim; ++l) {
+                    const int c = 32 * tc + l;
+                    const float dc = __shfl_sync(0xffffffffu, dn[tc], l);
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const int i = lane + 32 * t;
+                        if (i < m) v[t] = fmaf(-Gt[(size_t)c * m + i], dc, v[t]);
+                    }
+                }
+            }
+        }
+        double *xk = a.x + k * m;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int i = lane + 32 * t;
+            if (i < m) xk[i] = FIRST ? (double)v[t] : xk[i] + (double)v[t];
+            dn[t] = v[t];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kResidThreads) k_btd_resid(const BtdArgs a) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    long long z0, z1;
+    if (!ray_range(a, blockIdx.x, z0, z1) || z1 == z0 || a.zbad[z0]) return;
+    const int m = a.m;
+    const size_t mm = (size_t)m * m;
+    for (long long k = z0 + warp; k < z1; k += nw) {
+        const double *Ak = a.A + k * mm, *Bk = a.B + k * mm, *Ck = a.C + k * mm;
+        const double *xm = a.x + (k - 1) * m, *x0 = a.x + k * m, *xp = a.x + (k + 1) * m;
+        const bool lo = k > z0, hi = k + 1 < z1;
+        for (int i = 0; i < m; ++i) {
+            double s = 0.0;
+            for (int j = lane; j < m; j += 32) {
+                s = fma(Bk[(size_t)i * m + j], x0[j], s);
+                if (lo) s = fma(Ak[(size_t)i * m + j], xm[j], s);
+                if (hi) s = fma(Ck[(size_t)i * m + j], xp[j], s);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) a.r[k * m + i] = a.d[k * m + i] - s;
+        }
+    }
+}
+
+}  // namespace
+
+struct vx_btd {
+    int m = 0, ld = 0, n_refine = 0;
+    long long max_zones = 0;
+    size_t smem = 0;
+    float *LUt = nullptr, *Gt = nullptr, *At = nullptr, *y = nullptr;
+    int *perm = nullptr, *zbad = nullptr, *flag = nullptr;  // flag[0]: numeric flag, flag[1]: offsets invalid
+    double *r = nullptr;
+};
+
+static void btd_free(vx_btd *h) {
+    if (!h) return;
+    cudaFree(h->LUt);
+    cudaFree(h->Gt);
+    cudaFree(h->At);
+    cudaFree(h->y);
+    cudaFree(h->perm);
+    cudaFree(h->zbad);
+    cudaFree(h->flag);
+    cudaFree(h->r);
+    delete h;
+}
+
+extern "C" vx_status vx_btd_create(int m, long long max_zones, int n_refine, vx_btd **out) {
+    if (!out) return bfail(VX_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (m < 1 || m > VX_BTD_MAX_M) return bfail(VX_ERR_INVALID_ARG, "m = %d outside 1..%d", m, VX_BTD_MAX_M);
+    if (max_zones < 0) return bfail(VX_ERR_INVALID_ARG, "max_zones = %lld < 0", max_zones);
+    if (n_refine < 0 || n_refine > VX_BTD_MAX_REFINE)
+        return bfail(VX_ERR_INVALID_ARG, "n_refine = %d outside 0..%d", n_refine, VX_BTD_MAX_REFINE);
+    vx_btd *h = new (std::nothrow) vx_btd;
+    if (!h) return bfail(VX_ERR_OOM, "host allocation failed");
+    h->m = m;
+    h->ld = m | 1;  // odd row stride: column walks through shared memory hit distinct banks
+    h->n_refine = n_refine;
+    h->max_zones = max_zones;
+    h->smem = (size_t)3 * m * h->ld * sizeof(float) + (size_t)2 * m * sizeof(int);
+    const size_t zc = (size_t)(max_zones > 0 ? max_zones : 1), mm = (size_t)m * m;
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMalloc(&h->LUt, zc * mm * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&h->Gt, zc * mm * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&h->At, zc * mm * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&h->y, zc * m * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&h->perm, zc * m * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&h->zbad, zc * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&h->r, zc * m * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&h->flag, 2 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(h->flag, 0, 2 * sizeof(int));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_btd_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem);
+    if (e != cudaSuccess) {
+        btd_free(h);
+        return bfail(e == cudaErrorMemoryAllocation ? VX_ERR_OOM : VX_ERR_CUDA, "vx_btd_create: %s",
+                     cudaGetErrorString(e));
+    }
+    *out = h;
+    return VX_OK;
+}
+
+extern "C" vx_status vx_btd_solve(vx_btd *h, int n_rays, long long n_zones, const int *ray_offsets, const double *A,
+                                  const double *B, const double *C, const double *d, double *x, vx_stream stream) {
+    if (!h) return bfail(VX_ERR_INVALID_ARG, "handle is NULL");
+    if (n_rays < 0) return bfail(VX_ERR_INVALID_ARG, "n_rays = %d < 0", n_rays);
+    if (n_zones < 0 || n_zones > h->max_zones)
+        return bfail(VX_ERR_INVALID_ARG, "n_zones = %lld outside 0..%lld", n_zones, h->max_zones);
+    if (n_zones > 0 && n_rays == 0) return bfail(VX_ERR_INVALID_ARG, "n_zones > 0 with no rays");
+    if (n_zones == 0) return VX_OK;
+    if (!ray_offsets || !A || !B || !C || !d || !x) return bfail(VX_ERR_INVALID_ARG, "NULL array");
+    const size_t vec = (size_t)n_zones * h->m * sizeof(double), blk = vec * h->m;
+    auto overlap = [](const void *p, size_t np, const void *q, size_t nq) {
+        const char *a = (const char *)p, *b = (const char *)q;
+        return a < b + nq && b < a + np;
+    };
+    if (overlap(x, vec, d, vec) || overlap(x, vec, A, blk) || overlap(x, vec, B, blk) || overlap(x, vec, C, blk))
+        return bfail(VX_ERR_INVALID_ARG, "x overlaps an input");
+    cudaStream_t s = (cudaStream_t)stream;
+    BtdArgs a;
+    a.m = h->m;
+    a.ld = h->ld;
+    a.n_rays = n_rays;
+    a.n_zones = n_zones;
+    a.off = ray_offsets;
+    a.A = A;
+    a.B = B;
+    a.C = C;
+    a.d = d;
+    a.rhs = d;
+    a.x = x;
+    a.r = h->r;
+    a.LUt = h->LUt;
+    a.Gt = h->Gt;
+    a.At = h->At;
+    a.y = h->y;
+    a.perm = h->perm;
+    a.zbad = h->zbad;
+    a.flag = h->flag;
+    a.inval = h->flag + 1;
+    const int sweep_grid = (n_rays + kSweepWarps - 1) / kSweepWarps;
+    BTD_CU(cudaMemsetAsync(h->flag + 1, 0, sizeof(int), s));
+    k_btd_validate<<<(unsigned)((n_rays + 256) / 256), 256, 0, s>>>(ray_offsets, n_rays, n_zones, h->flag + 1, h->flag);
+    BTD_CU(cudaGetLastError());
+    k_btd_factor<<<n_rays, kFactorThreads, h->smem, s>>>(a);
+    BTD_CU(cudaGetLastError());
+    if (h->n_refine == 0)
+        k_btd_sweep<true, true><<<sweep_grid, 32 * kSweepWarps, 0, s>>>(a);
+    else
+        k_btd_sweep<true, false><<<sweep_grid, 32 * kSweepWarps, 0, s>>>(a);
+    BTD_CU(cudaGetLastError());
+    for (int it = 1; it <= h->n_refine; ++it) {
+        a.rhs = d;
+        k_btd_resid<<<n_rays, kResidThreads, 0, s>>>(a);
+        BTD_CU(cudaGetLastError());
+        a.rhs = h->r;
+        if (it == h->n_refine)
+            k_btd_sweep<false, true><<<sweep_grid, 32 * kSweepWarps, 0, s>>>(a);
+        else
+            k_btd_sweep<false, false><<<sweep_grid, 32 * kSweepWarps, 0, s>>>(a);
+        BTD_CU(cudaGetLastError());
+    }
+    return VX_OK;
+}
+
+extern "C" vx_status vx_btd_check(vx_btd *h, vx_stream stream) {
+    if (!h) return bfail(VX_ERR_INVALID_ARG, "handle is NULL");
+    BTD_CU(cudaStreamSynchronize((cudaStream_t)stream));
+    int f = 0;
+    BTD_CU(cudaMemcpy(&f, h->flag, sizeof(int), cudaMemcpyDeviceToHost));
+    if (f) {
+        BTD_CU(cudaMemset(h->flag, 0, sizeof(int)));
+        return bfail(VX_ERR_NUMERIC, "block-tridiagonal solve: %s%s", (f & 2) ? "zero or non-finite pivot" : "",
+                     (f & 1) ? ((f & 2) ? "; invalid ray offsets" : "invalid ray offsets") : "");
+    }
+    return VX_OK;
+}
+
+extern "C" void vx_btd_destroy(vx_btd *h) { btd_free(h); }

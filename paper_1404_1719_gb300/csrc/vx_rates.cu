@@ -86,6 +86,11 @@ int round_up(int a, int b) { return (a + b - 1) / b * b; }
 
 }  // namespace
 
+namespace vx {
+// The last-error text for the library's other translation units (the block-tridiagonal solver).
+vx_status set_error(vx_status s, const char *msg) { return fail(s, "%s", msg); }
+}  // namespace vx
+
 struct vx_rates {
     int device = 0;
     int nsm = 0;

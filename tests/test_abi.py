@@ -1,5 +1,5 @@
 """C ABI checks that need no GPU: the library builds for sm_103a, loads, exports every entry point
-include/vx_rates.h declares, and rejects invalid configurations on the host before any CUDA call.
+include/*.h declares, and rejects invalid configurations on the host before any CUDA call.
 Also checks that the product package is independent of the oracle."""
 import ctypes
 import os
@@ -19,9 +19,13 @@ def capi():
 
 
 def header_functions():
-    src = open(os.path.join(ROOT, "include", "vx_rates.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(vx_[a-z_]+)\s*\(", src)))
+    names = set()
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", h)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(vx_[a-z_]+)\s*\(", src))
+    return sorted(names)
 
 
 def test_exports_every_declared_symbol(capi):
