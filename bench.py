@@ -8,6 +8,11 @@ launch). Workload: 4096 rays x 400 zones, 21 bins, 32 x 64 quadrature, 3 species
 synthetic rays). One entry = one Phi_l(eps_i, eps_j) of one zone and one l: Z N^2 2 per step.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--mode fwd+jac|fwd|spectral|solve]
+
+`--mode solve` times the consumer of those Jacobians instead: the batched block-tridiagonal solve
+of the per-ray Newton systems (sec. 2.2), 304 rays x 400 zones with m = 84 unknowns per zone (J and
+H of nu_e and nu_ebar in 21 bins), FP32 block LU + two FP64 refinement sweeps per step.
 
 Under torchrun every rank runs its own independent copy of the workload (weak scaling, no
 collective on the data path); the time is the max over ranks. `--impl reference` times the FP64
@@ -170,6 +175,145 @@ def run_reference(args):
                              "sample": f"first {n} zones of workload {WORKLOAD} per step, forward + Jacobian"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+    return 0
+
+
+SOLVE_RAYS, SOLVE_ZONES, SOLVE_BINS, SOLVE_REFINE = 304, 400, 21, 2
+SOLVE_METRIC = "Newton block rows solved/s (per-ray block-tridiagonal, FP32 LU + FP64 refinement)"
+
+
+def solve_oracle_rate(s, rays):
+    from oracle import btd as obtd
+    o = s["offsets"]
+    t0 = time.perf_counter()
+    obtd.solve(s["A"], s["B"], s["C"], s["d"], o, rays=rays)
+    dt = time.perf_counter() - t0
+    return sum(int(o[r + 1] - o[r]) for r in rays) / dt, dt
+
+
+def run_solve(args):
+    import torch
+    import torch.distributed as dist
+    from vx_inputs import btd as gen
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    n_rays = args.rays or SOLVE_RAYS
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        s = gen.newton_system([SOLVE_ZONES] * 2, n_bins=SOLVE_BINS, seed=0)
+        for _ in range(args.warmup):
+            solve_oracle_rate(s, [0])
+        t = [solve_oracle_rate(s, [0, 1])[1] for _ in range(args.steps)]
+        ms = 1000 * float(np.mean(t))
+        value = 2 * SOLVE_ZONES / (ms / 1000)
+        print(json.dumps({"impl": "reference", "metric": SOLVE_METRIC, "value": value, "unit": "zones/s",
+                          "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                          "data": "synthetic", "config": {"workload": f"2 rays x {SOLVE_ZONES} zones, m = 84"},
+                          "cpu_baseline": {"value": value, "unit": "zones/s", "cores": 1, "kind": "oracle",
+                                           "sample": "2 rays per step, banded LU (scipy solve_banded)"},
+                          "e2e": {"value": value, "unit": "zones/s", "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0}}))
+        return 0
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    from paper_1404_1719_gb300 import BlockTridiagSolver, _build
+    _build.build()
+    s = gen.newton_system([SOLVE_ZONES] * n_rays, n_bins=SOLVE_BINS, seed=rank)
+    m, Z = s["m"], s["d"].shape[0]
+    host = {k: torch.from_numpy(np.ascontiguousarray(s[k])).pin_memory() for k in ("offsets", "A", "B", "C", "d")}
+    dv = {k: v.to(dev) for k, v in host.items()}
+    sv = BlockTridiagSolver(m, Z, SOLVE_REFINE)
+    stream = torch.cuda.current_stream()
+    x = torch.empty_like(dv["d"])
+
+    def step():
+        sv.solve(dv["offsets"], dv["A"], dv["B"], dv["C"], dv["d"], out=x)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    assert sv.check(), "numeric flag raised during warm-up"
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms_local = e0.elapsed_time(e1) / args.steps
+    ms = max_over_ranks(ms_local, world, dist, dev)
+    ok = sv.check()
+    # residual of the last solve, on the device in FP64 (a property that holds at any size)
+    Ad, Bd, Cd, dd = dv["A"], dv["B"], dv["C"], dv["d"]
+    r = dd - torch.einsum("zij,zj->zi", Bd, x)
+    first = torch.zeros(Z, dtype=torch.bool, device=dev)
+    first[dv["offsets"][:-1].long()] = True
+    last = torch.roll(first, -1)
+    r[1:] -= torch.where(first[1:, None], 0.0, torch.einsum("zij,zj->zi", Ad[1:], x[:-1]))
+    r[:-1] -= torch.where(last[:-1, None], 0.0, torch.einsum("zij,zj->zi", Cd[:-1], x[1:]))
+    rel_res = float(r.abs().max() / dd.abs().max())
+    # end to end: pinned host blocks -> device -> solve -> host solution
+    e2e_steps = max(1, min(3, args.steps))
+    sv.solve_host(host["offsets"], host["A"], host["B"], host["C"], host["d"], device=dev)
+    t_e2e = time.perf_counter()
+    for _ in range(e2e_steps):
+        sv.solve_host(host["offsets"], host["A"], host["B"], host["C"], host["d"], device=dev)
+    ms_e2e = 1000.0 * (time.perf_counter() - t_e2e) / e2e_steps
+    ms_e2e = max_over_ranks(ms_e2e, world, dist, dev)
+    h2d = sum(v.numel() * v.element_size() for v in host.values())
+    d2h = x.numel() * x.element_size()
+    if rank == 0:
+        c = clk.summary()
+        nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+        mhz = c["sm_mhz"] or 2070.0
+        peak = nsm * 128 * 2 * mhz * 1e6 / 1e12
+        # FP32 flops of the block factorisation: Schur update A_k G_{k-1} (2 m^3) on every zone but a
+        # ray's first, LU of D_k (2 m^3 / 3) on every zone, G_k = D_k^{-1} C_k by two triangular solves
+        # over m right-hand sides (2 m^3) on every zone but a ray's last; the O(m^2) sweeps and FP64
+        # residuals are not counted
+        flops = (Z - n_rays) * 2.0 * m ** 3 + Z * 2.0 * m ** 3 / 3.0 + (Z - n_rays) * 2.0 * m ** 3
+        achieved = flops / (ms_local / 1000) / 1e12
+        line = {
+            "metric": SOLVE_METRIC, "value": job_rate(Z, world, ms), "unit": "zones/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{n_rays} rays x {SOLVE_ZONES} zones, block-tridiagonal Newton systems, "
+                                   f"m = {m} (J, H of nu_e, nu_ebar x {SOLVE_BINS} bins)",
+                       "zones": Z, "m": m, "n_refine": SOLVE_REFINE,
+                       "l2": "inputs larger than L2 (A, B, C: %.1f GB)" % (3 * s["A"].nbytes / 1e9)},
+            "e2e": {"value": job_rate(Z, world, ms_e2e), "unit": "zones/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "call": "BlockTridiagSolver.solve_host (pinned host tensors)",
+                    "ms_per_step": ms_e2e},
+            "gpu_launches": args.steps * (3 + 2 * SOLVE_REFINE),  # validate, factor, sweep; resid + sweep each
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                         "traffic": None,
+                         "note": "FP32 flops of the block factorisation over the whole step (factor kernel, "
+                                 "sweeps and FP64 residuals); the factor kernel's pivot steps are sequential",
+                         "peak_note": f"FP32 {nsm} SMs x 128 FMA x 2 x {mhz:.0f} MHz (median SM clock in the run)",
+                         "kernel": "k_btd_factor + k_btd_sweep + k_btd_resid"},
+            "residual_max_rel": rel_res,
+            "clocks": c,
+            "numeric_ok": bool(ok),
+        }
+        if not args.no_cpu:
+            sub = gen.newton_system([SOLVE_ZONES] * n_rays, n_bins=SOLVE_BINS, seed=rank, rays=range(12))
+            rate, dt = solve_oracle_rate(sub, list(range(12)))
+            line["cpu_baseline"] = {"value": rate, "unit": "zones/s", "cores": 1, "kind": "oracle",
+                                    "sample": f"rays 0-11 of the workload, banded LU (scipy solve_banded), {dt:.1f} s"}
+        print(json.dumps(line))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    sv.close()
     return 0
 
 
@@ -371,14 +515,17 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU-baseline leg")
     ap.add_argument("--workload", type=int, default=WORKLOAD, choices=sorted(vx_inputs.WORKLOADS),
                     help="synthetic workload (default 4: 4096 rays x 400 zones)")
-    ap.add_argument("--mode", choices=["fwd+jac", "fwd", "spectral"], default="fwd+jac",
-                    help="step = forward + Jacobian pass (default), forward rates only, or forward + the "
-                         "derivatives with respect to the spectra (blocks and J/H VJP)")
+    ap.add_argument("--mode", choices=["fwd+jac", "fwd", "spectral", "solve"], default="fwd+jac",
+                    help="step = forward + Jacobian pass (default), forward rates only, forward + the "
+                         "derivatives with respect to the spectra (blocks and J/H VJP), or the per-ray "
+                         "block-tridiagonal Newton solve")
     ap.add_argument("--quad", choices=["standard", "split"], default="standard",
                     help="discrete rule in electron energy: standard, or split at the Fermi edge (VX_QUAD_SPLIT)")
     ap.add_argument("--rays", type=int, default=None,
                     help="use only the first R rays of the workload (small cases for profiling)")
     args = ap.parse_args()
+    if args.mode == "solve":
+        return run_solve(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

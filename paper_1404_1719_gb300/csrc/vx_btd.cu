@@ -22,6 +22,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <cstdint>
 #include <new>
 
 namespace vx {
@@ -31,7 +32,6 @@ vx_status set_error(vx_status s, const char *msg);  // the library's last-error 
 namespace {
 
 constexpr int kFactorThreads = 256;
-constexpr int kSweepWarps = 4;
 constexpr int kResidThreads = 256;
 
 vx_status bfail(vx_status s, const char *fmt, ...) {
@@ -203,6 +203,7 @@ __global__ void __launch_bounds__(kFactorThreads) k_btd_factor(const BtdArgs a) 
     extern __shared__ __align__(16) float sm[];
     __shared__ int s_bad;
     const int m = a.m, ld = a.ld, tid = threadIdx.x, nt = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     float *sD = sm, *sW = sD + m * ld, *sA = sW + m * ld;
     int *sPiv = reinterpret_cast<int *>(sA + m * ld);
     int *sPerm = sPiv + m;
@@ -213,19 +214,17 @@ __global__ void __launch_bounds__(kFactorThreads) k_btd_factor(const BtdArgs a) 
     for (long long k = z0; k < z1; ++k) {
         const bool prev = k > z0;
         const double *Bk = a.B + k * mm, *Ak = a.A + k * mm;
-        for (int e = tid; e < m * m; e += nt) {
-            const int i = e / m, j = e - i * m;
-            sD[i * ld + j] = (float)Bk[e];
-            if (prev) sA[i * ld + j] = (float)Ak[e];
-        }
+        for (int i = warp; i < m; i += nw)  // rows by warp, columns by lane: coalesced
+            for (int j = lane; j < m; j += 32) {
+                sD[i * ld + j] = (float)Bk[(size_t)i * m + j];
+                if (prev) sA[i * ld + j] = (float)Ak[(size_t)i * m + j];
+            }
         __syncthreads();
         if (prev) {
             schur_update(sD, sA, sW, m, ld);
             float *At = a.At + k * mm;
-            for (int e = tid; e < m * m; e += nt) {
-                const int c = e / m, i = e - c * m;
-                At[e] = sA[i * ld + c];
-            }
+            for (int c = warp; c < m; c += nw)  // column-major copy: lanes along a column
+                for (int i = lane; i < m; i += 32) At[(size_t)c * m + i] = sA[i * ld + c];
         }
         lu_factor(sD, m, ld, sPiv, &s_bad);
         if (tid == 0) {
@@ -238,24 +237,20 @@ __global__ void __launch_bounds__(kFactorThreads) k_btd_factor(const BtdArgs a) 
         }
         __syncthreads();
         float *LUt = a.LUt + k * mm;
-        for (int e = tid; e < m * m; e += nt) {
-            const int c = e / m, i = e - c * m;
-            LUt[e] = sD[i * ld + c];
-        }
+        for (int c = warp; c < m; c += nw)
+            for (int i = lane; i < m; i += 32) LUt[(size_t)c * m + i] = sD[i * ld + c];
         for (int i = tid; i < m; i += nt) a.perm[k * m + i] = sPerm[i];
         if (k + 1 < z1) {
             const double *Ck = a.C + k * mm;
-            for (int e = tid; e < m * m; e += nt) {
-                const int i = e / m, c = e - i * m;
-                sW[i * ld + c] = (float)Ck[(size_t)sPerm[i] * m + c];
+            for (int i = warp; i < m; i += nw) {
+                const double *row = Ck + (size_t)sPerm[i] * m;
+                for (int c = lane; c < m; c += 32) sW[i * ld + c] = (float)row[c];
             }
             __syncthreads();
             lu_solve_block(sD, sW, m, ld);
             float *Gt = a.Gt + k * mm;
-            for (int e = tid; e < m * m; e += nt) {
-                const int c = e / m, i = e - c * m;
-                Gt[e] = sW[i * ld + c];
-            }
+            for (int c = warp; c < m; c += nw)
+                for (int i = lane; i < m; i += 32) Gt[(size_t)c * m + i] = sW[i * ld + c];
         }
         __syncthreads();
     }
@@ -265,22 +260,50 @@ __global__ void __launch_bounds__(kFactorThreads) k_btd_factor(const BtdArgs a) 
     }
 }
 
+// Asynchronous copy of n floats from global to shared memory by one warp (16-byte cp.async where
+// both ends are 16-byte aligned and n is a multiple of 4, else plain loads), as one commit group.
+__device__ __forceinline__ void warp_stage(float *dst, const float *src, int n, int lane) {
+    const bool vec = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15) == 0 && (n & 3) == 0;
+    if (vec) {
+        const unsigned base = (unsigned)__cvta_generic_to_shared(dst);
+        for (int e = 4 * lane; e < n; e += 128)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(base + 4u * (unsigned)e), "l"(src + e)
+                         : "memory");
+    } else {
+        for (int e = lane; e < n; e += 32) dst[e] = src[e];
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void stage_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+    __syncwarp();
+}
+
+// One warp per ray (one warp per CTA). Each zone's FP32 matrices are staged in shared memory
+// (two buffers: the next matrix is in flight while the current one is used) and the vector being
+// eliminated is broadcast by shuffle: rows lane + 32 t of a zone's vector live in lane `lane`.
 template <bool FIRST, bool LAST>
-__global__ void __launch_bounds__(32 * kSweepWarps) k_btd_sweep(const BtdArgs a) {
-    __shared__ float s_buf[kSweepWarps][VX_BTD_MAX_M];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int ray = blockIdx.x * kSweepWarps + w;
-    if (ray >= a.n_rays) return;
+__global__ void __launch_bounds__(32) k_btd_sweep(const BtdArgs a) {
+    extern __shared__ __align__(16) float sbuf[];
+    const int lane = threadIdx.x;
+    const int ray = blockIdx.x;
     long long z0, z1;
     if (!ray_range(a, ray, z0, z1) || z1 == z0) return;
-    const int m = a.m;
-    const size_t mm = (size_t)m * m;
+    const int m = a.m, mm = m * m;
+    float *S0 = sbuf, *S1 = sbuf + ((mm + 3) & ~3), *sv = S1 + ((mm + 3) & ~3);
     if (a.zbad[z0]) {
         if (LAST)
             for (long long e = z0 * m + lane; e < z1 * m; e += 32) a.x[e] = __longlong_as_double(0x7ff8000000000000ll);
         return;
     }
     float v[4], yp[4] = {0.f, 0.f, 0.f, 0.f};
+    // forward: S0 holds A_k (zones after the first), S1 the LU factors of D_k. Every zone commits
+    // two groups in the order they are needed (an empty one where nothing is copied), so
+    // wait_group 1 always completes the older of the two in flight.
+    warp_stage(S1, a.LUt + (size_t)z0 * mm, mm, lane);
+    if (z0 + 1 < z1) warp_stage(S0, a.At + (size_t)(z0 + 1) * mm, mm, lane);
+    else asm volatile("cp.async.commit_group;" ::: "memory");
     for (long long k = z0; k < z1; ++k) {
         const double *rhs = a.rhs + k * m;
 #pragma unroll
@@ -289,7 +312,7 @@ __global__ void __launch_bounds__(32 * kSweepWarps) k_btd_sweep(const BtdArgs a)
             v[t] = i < m ? (float)rhs[i] : 0.f;
         }
         if (k > z0) {  // rhs_k - A_k y_{k-1}
-            const float *At = a.At + k * mm;
+            stage_wait<1>();  // A_k (the LU factors of D_k are the newer group)
 #pragma unroll
             for (int tc = 0; tc < 4; ++tc) {
                 if (32 * tc >= m) break;
@@ -300,26 +323,29 @@ __global__ void __launch_bounds__(32 * kSweepWarps) k_btd_sweep(const BtdArgs a)
 #pragma unroll
                     for (int t = 0; t < 4; ++t) {
                         const int i = lane + 32 * t;
-                        if (i < m) v[t] = fmaf(-At[(size_t)c * m + i], yc, v[t]);
+                        if (i < m) v[t] = fmaf(-S0[c * m + i], yc, v[t]);
                     }
                 }
             }
+            __syncwarp();
+            if (k + 1 < z1) warp_stage(S0, a.At + (size_t)(k + 1) * mm, mm, lane);
+            else asm volatile("cp.async.commit_group;" ::: "memory");
         }
+        stage_wait<1>();  // the LU factors of D_k
         // row permutation of the factorisation
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
             const int i = lane + 32 * t;
-            if (i < m) s_buf[w][i] = v[t];
+            if (i < m) sv[i] = v[t];
         }
         __syncwarp();
         const int *perm = a.perm + k * m;
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
             const int i = lane + 32 * t;
-            if (i < m) v[t] = s_buf[w][perm[i]];
+            if (i < m) v[t] = sv[perm[i]];
         }
         __syncwarp();
-        const float *LUt = a.LUt + k * mm;
         // unit lower triangle
 #pragma unroll
         for (int tj = 0; tj < 4; ++tj) {
@@ -331,7 +357,7 @@ __global__ void __launch_bounds__(32 * kSweepWarps) k_btd_sweep(const BtdArgs a)
 #pragma unroll
                 for (int t = tj; t < 4; ++t) {
                     const int i = lane + 32 * t;
-                    if (i > j && i < m) v[t] = fmaf(-LUt[(size_t)j * m + i], vj, v[t]);
+                    if (i > j && i < m) v[t] = fmaf(-S1[j * m + i], vj, v[t]);
                 }
             }
         }
@@ -342,15 +368,18 @@ __global__ void __launch_bounds__(32 * kSweepWarps) k_btd_sweep(const BtdArgs a)
             const int top = m - 32 * tj < 32 ? m - 32 * tj : 32;
             for (int l = top - 1; l >= 0; --l) {
                 const int j = 32 * tj + l;
-                const float vj = __shfl_sync(0xffffffffu, v[tj], l) / LUt[(size_t)j * m + j];
+                const float vj = __shfl_sync(0xffffffffu, v[tj], l) / S1[j * m + j];
                 if (lane == l) v[tj] = vj;
 #pragma unroll
                 for (int t = 0; t <= tj; ++t) {
                     const int i = lane + 32 * t;
-                    if (i < j) v[t] = fmaf(-LUt[(size_t)j * m + i], vj, v[t]);
+                    if (i < j) v[t] = fmaf(-S1[j * m + i], vj, v[t]);
                 }
             }
         }
+        __syncwarp();
+        if (k + 1 < z1) warp_stage(S1, a.LUt + (size_t)(k + 1) * mm, mm, lane);
+        else asm volatile("cp.async.commit_group;" ::: "memory");
         float *yk = a.y + k * m;
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
@@ -359,8 +388,10 @@ __global__ void __launch_bounds__(32 * kSweepWarps) k_btd_sweep(const BtdArgs a)
             yp[t] = v[t];
         }
     }
-    // backward: delta_k = y_k - G_k delta_{k+1}; x += delta (FP64)
+    stage_wait<0>();
+    // backward: delta_k = y_k - G_k delta_{k+1}; x += delta (FP64). G of zone k in buffer k & 1.
     float dn[4] = {0.f, 0.f, 0.f, 0.f};
+    if (z1 - 2 >= z0) warp_stage(((z1 - 2) & 1) ? S1 : S0, a.Gt + (size_t)(z1 - 2) * mm, mm, lane);
     for (long long k = z1 - 1; k >= z0; --k) {
         const float *yk = a.y + k * m;
 #pragma unroll
@@ -369,7 +400,10 @@ __global__ void __launch_bounds__(32 * kSweepWarps) k_btd_sweep(const BtdArgs a)
             v[t] = i < m ? yk[i] : 0.f;
         }
         if (k + 1 < z1) {
-            const float *Gt = a.Gt + k * mm;
+            const float *G = (k & 1) ? S1 : S0;
+            if (k - 1 >= z0) warp_stage(((k - 1) & 1) ? S1 : S0, a.Gt + (size_t)(k - 1) * mm, mm, lane);
+            else asm volatile("cp.async.commit_group;" ::: "memory");
+            stage_wait<1>();  // G_k (G_{k-1} is the newer group)
 #pragma unroll
             for (int tc = 0; tc < 4; ++tc) {
                 if (32 * tc >= m) break;
@@ -380,10 +414,11 @@ __global__ void __launch_bounds__(32 * kSweepWarps) k_btd_sweep(const BtdArgs a)
 #pragma unroll
                     for (int t = 0; t < 4; ++t) {
                         const int i = lane + 32 * t;
-                        if (i < m) v[t] = fmaf(-Gt[(size_t)c * m + i], dc, v[t]);
+                        if (i < m) v[t] = fmaf(-G[c * m + i], dc, v[t]);
                     }
                 }
             }
+            __syncwarp();
         }
         double *xk = a.x + k * m;
 #pragma unroll
@@ -393,6 +428,7 @@ __global__ void __launch_bounds__(32 * kSweepWarps) k_btd_sweep(const BtdArgs a)
             dn[t] = v[t];
         }
     }
+    stage_wait<0>();
 }
 
 __global__ void __launch_bounds__(kResidThreads) k_btd_resid(const BtdArgs a) {
@@ -424,7 +460,7 @@ __global__ void __launch_bounds__(kResidThreads) k_btd_resid(const BtdArgs a) {
 struct vx_btd {
     int m = 0, ld = 0, n_refine = 0;
     long long max_zones = 0;
-    size_t smem = 0;
+    size_t smem = 0, smem_sweep = 0;
     float *LUt = nullptr, *Gt = nullptr, *At = nullptr, *y = nullptr;
     int *perm = nullptr, *zbad = nullptr, *flag = nullptr;  // flag[0]: numeric flag, flag[1]: offsets invalid
     double *r = nullptr;
@@ -457,6 +493,7 @@ extern "C" vx_status vx_btd_create(int m, long long max_zones, int n_refine, vx_
     h->n_refine = n_refine;
     h->max_zones = max_zones;
     h->smem = (size_t)3 * m * h->ld * sizeof(float) + (size_t)2 * m * sizeof(int);
+    h->smem_sweep = ((size_t)2 * ((m * m + 3) & ~3) + m) * sizeof(float);
     const size_t zc = (size_t)(max_zones > 0 ? max_zones : 1), mm = (size_t)m * m;
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = cudaMalloc(&h->LUt, zc * mm * sizeof(float));
@@ -470,6 +507,10 @@ extern "C" vx_status vx_btd_create(int m, long long max_zones, int n_refine, vx_
     if (e == cudaSuccess) e = cudaMemset(h->flag, 0, 2 * sizeof(int));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_btd_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem);
+    const void *sweeps[4] = {(const void *)k_btd_sweep<true, true>, (const void *)k_btd_sweep<true, false>,
+                             (const void *)k_btd_sweep<false, true>, (const void *)k_btd_sweep<false, false>};
+    for (int i = 0; i < 4 && e == cudaSuccess; ++i)
+        e = cudaFuncSetAttribute(sweeps[i], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem_sweep);
     if (e != cudaSuccess) {
         btd_free(h);
         return bfail(e == cudaErrorMemoryAllocation ? VX_ERR_OOM : VX_ERR_CUDA, "vx_btd_create: %s",
@@ -517,16 +558,15 @@ extern "C" vx_status vx_btd_solve(vx_btd *h, int n_rays, long long n_zones, cons
     a.zbad = h->zbad;
     a.flag = h->flag;
     a.inval = h->flag + 1;
-    const int sweep_grid = (n_rays + kSweepWarps - 1) / kSweepWarps;
     BTD_CU(cudaMemsetAsync(h->flag + 1, 0, sizeof(int), s));
     k_btd_validate<<<(unsigned)((n_rays + 256) / 256), 256, 0, s>>>(ray_offsets, n_rays, n_zones, h->flag + 1, h->flag);
     BTD_CU(cudaGetLastError());
     k_btd_factor<<<n_rays, kFactorThreads, h->smem, s>>>(a);
     BTD_CU(cudaGetLastError());
     if (h->n_refine == 0)
-        k_btd_sweep<true, true><<<sweep_grid, 32 * kSweepWarps, 0, s>>>(a);
+        k_btd_sweep<true, true><<<n_rays, 32, h->smem_sweep, s>>>(a);
     else
-        k_btd_sweep<true, false><<<sweep_grid, 32 * kSweepWarps, 0, s>>>(a);
+        k_btd_sweep<true, false><<<n_rays, 32, h->smem_sweep, s>>>(a);
     BTD_CU(cudaGetLastError());
     for (int it = 1; it <= h->n_refine; ++it) {
         a.rhs = d;
@@ -534,9 +574,9 @@ extern "C" vx_status vx_btd_solve(vx_btd *h, int n_rays, long long n_zones, cons
         BTD_CU(cudaGetLastError());
         a.rhs = h->r;
         if (it == h->n_refine)
-            k_btd_sweep<false, true><<<sweep_grid, 32 * kSweepWarps, 0, s>>>(a);
+            k_btd_sweep<false, true><<<n_rays, 32, h->smem_sweep, s>>>(a);
         else
-            k_btd_sweep<false, false><<<sweep_grid, 32 * kSweepWarps, 0, s>>>(a);
+            k_btd_sweep<false, false><<<n_rays, 32, h->smem_sweep, s>>>(a);
         BTD_CU(cudaGetLastError());
     }
     return VX_OK;

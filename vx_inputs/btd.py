@@ -30,37 +30,30 @@ def _ray_newton(seed: int, ray: int, n: int, N: int, pair: bool):
     m = 2 * S * N
     x = np.arange(n) / max(n - 1, 1)
     # opacity x time step per (zone, species, moment, bin): centre of the ray optically thick
-    logk = 3.0 - 6.0 * x[:, None, None, None] + rng.uniform(-0.5, 0.5, (n, S, 2, N))
-    kap = 10.0 ** logk
+    kap = 10.0 ** (3.0 - 6.0 * x[:, None, None, None] + rng.uniform(-0.5, 0.5, (n, S, 2, N)))
     rho = rng.uniform(0.1, 0.9, n)
     c = 10.0 ** rng.uniform(-2.0, np.log10(3.0), n)
     fedd = rng.uniform(1.0 / 3.0, 1.0, (n, S, N))
+    w = rng.uniform(0.0, 1.0, (n, S, 2, N, N))  # pair coupling of (species, moment) rows to the partner
+    w *= (rho[:, None, None, None] * kap)[..., None] / w.sum(axis=-1, keepdims=True)
+    d = rng.standard_normal((n, m))
     A = np.zeros((n, m, m))
     B = np.zeros((n, m, m))
     C = np.zeros((n, m, m))
-
-    def idx(s, q, i):
-        return (s * 2 + q) * N + i
-
+    diag = np.arange(m)
+    B[:, diag, diag] = 1.0 + kap.reshape(n, m)
     ii = np.arange(N)
-    for k in range(n):
-        B[k][np.arange(m), np.arange(m)] = 1.0 + kap[k].reshape(-1)
-        for s in range(S):
-            sp = (1 - s) if pair else s  # partner species
-            for q in range(2):
-                w = rng.uniform(0.0, 1.0, (N, N))
-                w *= (rho[k] * kap[k, s, q])[:, None] / w.sum(axis=1, keepdims=True)
-                r0, c0 = idx(s, q, 0), idx(sp, q, 0)
-                B[k, r0:r0 + N, c0:c0 + N] -= w
-            # flux coupling: J_s(i) <- H_s(i) of the neighbours, H_s(i) <- J_s(i)
-            rJ, rH = idx(s, 0, ii), idx(s, 1, ii)
-            if k > 0:
-                A[k, rJ, rH] = -c[k]
-                A[k, rH, rJ] = -c[k] * fedd[k, s]
-            if k + 1 < n:
-                C[k, rJ, rH] = c[k]
-                C[k, rH, rJ] = c[k] * fedd[k, s]
-    d = rng.standard_normal((n, m))
+    for s in range(S):
+        sp = (1 - s) if pair else s  # partner species
+        for q in range(2):
+            r0, c0 = (2 * s + q) * N, (2 * sp + q) * N
+            B[:, r0:r0 + N, c0:c0 + N] -= w[:, s, q]
+        # flux coupling: J_s(i) <- H_s(i) of the neighbours, H_s(i) <- J_s(i)
+        rJ, rH = 2 * s * N + ii, (2 * s + 1) * N + ii
+        A[1:, rJ, rH] = -c[1:, None]
+        A[1:, rH, rJ] = -(c[:, None] * fedd[:, s])[1:]
+        C[:-1, rJ, rH] = c[:-1, None]
+        C[:-1, rH, rJ] = (c[:, None] * fedd[:, s])[:-1]
     return A, B, C, d
 
 
