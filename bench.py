@@ -11,7 +11,7 @@ synthetic rays). One entry = one Phi_l(eps_i, eps_j) of one zone and one l: Z N^
                     [--mode fwd+jac|fwd|spectral|solve]
 
 `--mode solve` times the consumer of those Jacobians instead: the batched block-tridiagonal solve
-of the per-ray Newton systems (sec. 2.2), 304 rays x 400 zones with m = 84 unknowns per zone (J and
+of the per-ray Newton systems (sec. 2.1), 304 rays x 400 zones with m = 84 unknowns per zone (J and
 H of nu_e and nu_ebar in 21 bins), FP32 block LU + two FP64 refinement sweeps per step.
 
 Under torchrun every rank runs its own independent copy of the workload (weak scaling, no

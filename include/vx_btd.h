@@ -4,7 +4,7 @@
  * Where it sits in the method. The radial transport sweeps of Marek et al. (arXiv:1404.1719) are
  * implicit in time and run ray by ray; each ray's step is a non-linear system in the zone unknowns,
  * solved by Newton-Raphson iterations with an explicitly built Jacobian and a direct solve of the
- * linearised system (sec. 2.2). A radial difference scheme couples a zone only to its neighbours,
+ * linearised system (sec. 2.1). A radial difference scheme couples a zone only to its neighbours,
  * so for the zones k = 0 .. n-1 of one ray, with m unknowns per zone, that linear system reads
  *
  *     A_k x_{k-1} + B_k x_k + C_k x_{k+1} = d_k        (A_0 and C_{n-1} are not read).

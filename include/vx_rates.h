@@ -7,8 +7,8 @@
  *
  * Where it sits in the method. Marek et al. (arXiv:1404.1719) solve the neutrino moment equations
  * ray by ray (sec. 2.1): each ray's radial sweep is an implicit Newton-Raphson solve with an
- * explicit Jacobian, and "the emission, absorption, and scattering rates of neutrinos" are one of
- * the components that solve needs (sec. 2.1). Rays are independent (sec. 2.2), and parallelism
+ * explicit Jacobian, and the neutrinos' emission, absorption and scattering rates are among the
+ * components that solve needs (sec. 2.1). Rays are independent (sec. 2.2), and parallelism
  * inside a ray's phase space is the paper's stated next step (sec. 4). The paper does not write
  * the rate kernels down; the kernel evaluated here is the standard electroweak pair kernel with
  * massless leptons and Fermi-Dirac blocking, under these readings:

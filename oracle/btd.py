@@ -3,7 +3,7 @@
 Only the tests, ``__graft_entry__.smoke()`` and the CPU legs of ``bench.py`` may import this
 module; the product library never calls it and shares no code with it.
 
-What is solved (paper sec. 2.2): the radial transport sweeps are implicit in time and run ray by
+What is solved (paper sec. 2.1): the radial transport sweeps are implicit in time and run ray by
 ray; each ray's time step is a non-linear system in the zone unknowns, solved by Newton-Raphson
 iterations with an explicitly built Jacobian and a direct solve of the linearised system. A radial
 difference scheme couples a zone only to its two neighbours, so that linear system is block

@@ -6,8 +6,8 @@
  * header, table or constant with the GPU path.
  *
  * What it computes. The paper (Marek et al., "Towards Petaflops Capability of the VERTEX
- * Supernova Code", sec. 2.1) lists "the emission, absorption, and scattering rates of
- * neutrinos" as a component of the PDE system and uses the neutrino occupation f, the intensity
+ * Supernova Code", sec. 2.1) counts the neutrinos' emission, absorption and scattering rates
+ * among the components of the PDE system and uses the neutrino occupation f, the intensity
  * I = c/(2 pi hbar c)^3 eps^3 f, and the angular moments J, H of I (the one numbered equation of
  * sec. 2.1). It does not define the rate kernels. The definition below is the standard
  * electroweak e- e+ <-> nu nubar kernel with massless leptons and Fermi-Dirac blocking; each
