@@ -3,10 +3,10 @@
 // Three kernels, all one ray per CTA (or per warp), since a ray's zones are a sequential chain:
 //  * k_btd_factor: block LU along the ray in FP32. Per zone: load B_k (and A_k) as FP32 into shared
 //    memory, form the Schur complement D_k = B_k - A_k G_{k-1} (G_{k-1} is still in shared memory
-//    from the previous zone; 4 x 4 register tiles), factor D_k with partial pivoting (warp 0 picks
-//    the pivot, swaps and scales; the CTA updates the trailing block), then G_k = D_k^{-1} C_k by
-//    forward and back substitution over the m right-hand sides. The factors, G_k and an FP32 copy
-//    of A_k are written column-major, the row permutation as an index vector.
+//    from the previous zone; 4 x 4 register tiles), factor D_k with partial pivoting by row
+//    indirection (one CTA barrier per column), then G_k = D_k^{-1} C_k by forward and back
+//    substitution over the m right-hand sides in blocks of 8 rows. The factors, G_k and an FP32
+//    copy of A_k are written column-major, the row permutation as an index vector.
 //  * k_btd_sweep: one warp per ray solves M delta = rhs with those factors: forward
 //    y_k = D_k^{-1} (rhs_k - A_k y_{k-1}), backward delta_k = y_k - G_k delta_{k+1}; a lane holds
 //    rows lane + 32 t of a zone's vector and the column being eliminated is broadcast by shuffle.
@@ -123,80 +123,132 @@ __device__ void schur_update(float *sD, const float *sA, const float *sW, int m,
     __syncthreads();
 }
 
-// In-place LU with partial pivoting of sD (P D = L U, unit L below the diagonal, U on and above).
-// Column j: warp 0 finds the pivot (largest magnitude, lowest row on ties), swaps the rows and
-// scales the multipliers; then the CTA updates the trailing block. A zero or non-finite pivot sets
-// *bad; the arithmetic then runs on (NaN/inf), which only this ray sees.
-__device__ void lu_factor(float *sD, int m, int ld, int *piv, int *bad) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+// LU with partial pivoting of sD by row indirection: cur[q] is the physical row at pivot position
+// q. Every warp searches the pivot column itself (largest magnitude, lowest position on ties: the
+// same answer in every warp), so a column costs one CTA barrier and no single-warp phase. During
+// column j nothing in column j of sD is written: the multipliers go to sM (by physical row) and
+// the row order to the other of the two permutation buffers. On return sOut holds the factors in
+// pivot order (unit L below the diagonal, U on and above) and the returned vector the final row
+// order, so that P D = L U with (P D)[q] = D[perm[q]]. A zero or non-finite pivot sets *bad; the
+// arithmetic then runs on (NaN/inf), which only this ray sees.
+__device__ const int *lu_factor(float *sD, float *sM, float *sOut, int m, int ld, int *p0, int *p1, int *bad) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5, nt = blockDim.x;
+    for (int q = tid; q < m; q += nt) p0[q] = q;
+    __syncthreads();
+    int *cur = p0, *nxt = p1;
     for (int j = 0; j < m; ++j) {
-        if (warp == 0) {
-            float best = -1.f;
-            int bi = j;
-            for (int i = j + lane; i < m; i += 32) {
-                const float v = fabsf(sD[i * ld + j]);
-                if (v > best) {
-                    best = v;
-                    bi = i;
+        float best = -1.f;
+        int bq = j;
+        for (int q = j + lane; q < m; q += 32) {
+            const float v = fabsf(sD[cur[q] * ld + j]);
+            if (v > best) {
+                best = v;
+                bq = q;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oq = __shfl_xor_sync(0xffffffffu, bq, o);
+            if (ob > best || (ob == best && oq < bq)) {
+                best = ob;
+                bq = oq;
+            }
+        }
+        const int pj = cur[bq], pq = cur[j];  // the pivot row; the row that moves to position bq
+        if (tid == 0 && !(best > 0.f && best < INFINITY)) *bad = 1;
+        for (int q = tid; q < m; q += nt) nxt[q] = q == j ? pj : (q == bq ? pq : cur[q]);
+        const float piv = sD[pj * ld + j];
+        for (int q = j + 1 + warp; q < m; q += nw) {
+            const int r = q == bq ? pq : cur[q];
+            const float l = sD[r * ld + j] / piv;
+            for (int c = j + 1 + lane; c < m; c += 32) sD[r * ld + c] = fmaf(-l, sD[pj * ld + c], sD[r * ld + c]);
+            if (lane == 0) sM[r * ld + j] = l;
+        }
+        __syncthreads();
+        int *t = cur;
+        cur = nxt;
+        nxt = t;
+    }
+    for (int q = warp; q < m; q += nw) {
+        const int r = cur[q];
+        for (int c = lane; c < m; c += 32) sOut[q * ld + c] = c < q ? sM[r * ld + c] : sD[r * ld + c];
+    }
+    __syncthreads();
+    return cur;
+}
+
+// sW <- U^{-1} L^{-1} sW for the m right-hand sides in the columns of sW (rows in pivot order), with
+// the factors of sL in pivot order. Blocks of kSub rows: the block's own triangle first (one thread
+// per column), then the block's update of the rows still to come (rank kSub, a warp per row, lanes
+// along the columns); two CTA barriers per block.
+constexpr int kSub = 8;
+__device__ void lu_solve_block(const float *sL, float *sW, int m, int ld) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5, nt = blockDim.x;
+    for (int j0 = 0; j0 < m; j0 += kSub) {  // forward: unit lower triangle
+        const int jb = m - j0 < kSub ? m - j0 : kSub;
+        for (int c = tid; c < m; c += nt) {
+            float w[kSub];
+#pragma unroll
+            for (int r = 0; r < kSub; ++r) w[r] = r < jb ? sW[(j0 + r) * ld + c] : 0.f;
+#pragma unroll
+            for (int r = 1; r < kSub; ++r)
+#pragma unroll
+                for (int q = 0; q < r; ++q)
+                    if (r < jb) w[r] = fmaf(-sL[(j0 + r) * ld + j0 + q], w[q], w[r]);
+#pragma unroll
+            for (int r = 1; r < kSub; ++r)
+                if (r < jb) sW[(j0 + r) * ld + c] = w[r];
+        }
+        __syncthreads();
+        for (int i = j0 + jb + warp; i < m; i += nw) {
+            float l[kSub];
+#pragma unroll
+            for (int q = 0; q < kSub; ++q) l[q] = q < jb ? sL[i * ld + j0 + q] : 0.f;
+            for (int c = lane; c < m; c += 32) {
+                float acc = sW[i * ld + c];
+#pragma unroll
+                for (int q = 0; q < kSub; ++q)
+                    if (q < jb) acc = fmaf(-l[q], sW[(j0 + q) * ld + c], acc);
+                sW[i * ld + c] = acc;
+            }
+        }
+        __syncthreads();
+    }
+    for (int j1 = m; j1 > 0; j1 -= kSub) {  // backward: upper triangle, rows j0 .. j1-1
+        const int j0 = j1 > kSub ? j1 - kSub : 0, jb = j1 - j0;
+        for (int c = tid; c < m; c += nt) {
+            float w[kSub];
+#pragma unroll
+            for (int r = 0; r < kSub; ++r) w[r] = r < jb ? sW[(j0 + r) * ld + c] : 0.f;
+#pragma unroll
+            for (int r = kSub - 1; r >= 0; --r) {
+                if (r < jb) {
+#pragma unroll
+                    for (int q = r + 1; q < kSub; ++q)
+                        if (q < jb) w[r] = fmaf(-sL[(j0 + r) * ld + j0 + q], w[q], w[r]);
+                    w[r] /= sL[(j0 + r) * ld + j0 + r];
                 }
             }
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                if (ob > best || (ob == best && oi < bi)) {
-                    best = ob;
-                    bi = oi;
-                }
+            for (int r = 0; r < kSub; ++r)
+                if (r < jb) sW[(j0 + r) * ld + c] = w[r];
+        }
+        __syncthreads();
+        for (int i = warp; i < j0; i += nw) {
+            float u[kSub];
+#pragma unroll
+            for (int q = 0; q < kSub; ++q) u[q] = q < jb ? sL[i * ld + j0 + q] : 0.f;
+            for (int c = lane; c < m; c += 32) {
+                float acc = sW[i * ld + c];
+#pragma unroll
+                for (int q = 0; q < kSub; ++q)
+                    if (q < jb) acc = fmaf(-u[q], sW[(j0 + q) * ld + c], acc);
+                sW[i * ld + c] = acc;
             }
-            if (lane == 0) {
-                piv[j] = bi;
-                if (!(best > 0.f) || !(best < INFINITY)) *bad = 1;
-            }
-            if (bi != j)
-                for (int c = lane; c < m; c += 32) {
-                    const float t = sD[j * ld + c];
-                    sD[j * ld + c] = sD[bi * ld + c];
-                    sD[bi * ld + c] = t;
-                }
-            __syncwarp();
-            const float inv = 1.f / sD[j * ld + j];
-            for (int i = j + 1 + lane; i < m; i += 32) sD[i * ld + j] *= inv;
-        }
-        __syncthreads();
-        for (int i = j + 1 + warp; i < m; i += nw) {
-            const float l = sD[i * ld + j];
-            for (int c = j + 1 + lane; c < m; c += 32) sD[i * ld + c] = fmaf(-l, sD[j * ld + c], sD[i * ld + c]);
         }
         __syncthreads();
     }
-}
-
-// sW <- U^{-1} L^{-1} sW for the m right-hand sides in the columns of sW (already row-permuted).
-__device__ void lu_solve_block(const float *sD, float *sW, int m, int ld) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int j = 0; j + 1 < m; ++j) {
-        for (int i = j + 1 + warp; i < m; i += nw) {
-            const float l = sD[i * ld + j];
-            for (int c = lane; c < m; c += 32) sW[i * ld + c] = fmaf(-l, sW[j * ld + c], sW[i * ld + c]);
-        }
-        __syncthreads();
-    }
-    // back substitution on unscaled rows: row j is final once the rows below are eliminated, and
-    // it enters the rows above as (U_ij / U_jj) row_j; every row is divided by its pivot at the end
-    for (int j = m - 1; j > 0; --j) {
-        const float inv = 1.f / sD[j * ld + j];
-        for (int i = warp; i < j; i += nw) {
-            const float u = sD[i * ld + j] * inv;
-            for (int c = lane; c < m; c += 32) sW[i * ld + c] = fmaf(-u, sW[j * ld + c], sW[i * ld + c]);
-        }
-        __syncthreads();
-    }
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-        const int i = e / m, c = e - i * m;
-        sW[i * ld + c] /= sD[i * ld + i];
-    }
-    __syncthreads();
 }
 
 __global__ void __launch_bounds__(kFactorThreads) k_btd_factor(const BtdArgs a) {
@@ -205,8 +257,8 @@ __global__ void __launch_bounds__(kFactorThreads) k_btd_factor(const BtdArgs a) 
     const int m = a.m, ld = a.ld, tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     float *sD = sm, *sW = sD + m * ld, *sA = sW + m * ld;
-    int *sPiv = reinterpret_cast<int *>(sA + m * ld);
-    int *sPerm = sPiv + m;
+    int *sP0 = reinterpret_cast<int *>(sA + m * ld);
+    int *sP1 = sP0 + m;
     long long z0, z1;
     if (!ray_range(a, blockIdx.x, z0, z1) || z1 == z0) return;
     if (tid == 0) s_bad = 0;
@@ -226,28 +278,20 @@ __global__ void __launch_bounds__(kFactorThreads) k_btd_factor(const BtdArgs a) 
             for (int c = warp; c < m; c += nw)  // column-major copy: lanes along a column
                 for (int i = lane; i < m; i += 32) At[(size_t)c * m + i] = sA[i * ld + c];
         }
-        lu_factor(sD, m, ld, sPiv, &s_bad);
-        if (tid == 0) {
-            for (int i = 0; i < m; ++i) sPerm[i] = i;
-            for (int j = 0; j < m; ++j) {
-                const int p = sPiv[j], t = sPerm[j];
-                sPerm[j] = sPerm[p];
-                sPerm[p] = t;
-            }
-        }
-        __syncthreads();
+        // G_{k-1} in sW and A_k in sA are consumed: sW takes the multipliers, sA the factors
+        const int *perm = lu_factor(sD, sW, sA, m, ld, sP0, sP1, &s_bad);
         float *LUt = a.LUt + k * mm;
         for (int c = warp; c < m; c += nw)
-            for (int i = lane; i < m; i += 32) LUt[(size_t)c * m + i] = sD[i * ld + c];
-        for (int i = tid; i < m; i += nt) a.perm[k * m + i] = sPerm[i];
+            for (int i = lane; i < m; i += 32) LUt[(size_t)c * m + i] = sA[i * ld + c];
+        for (int i = tid; i < m; i += nt) a.perm[k * m + i] = perm[i];
         if (k + 1 < z1) {
             const double *Ck = a.C + k * mm;
             for (int i = warp; i < m; i += nw) {
-                const double *row = Ck + (size_t)sPerm[i] * m;
+                const double *row = Ck + (size_t)perm[i] * m;
                 for (int c = lane; c < m; c += 32) sW[i * ld + c] = (float)row[c];
             }
             __syncthreads();
-            lu_solve_block(sD, sW, m, ld);
+            lu_solve_block(sA, sW, m, ld);
             float *Gt = a.Gt + k * mm;
             for (int c = warp; c < m; c += nw)
                 for (int i = lane; i < m; i += 32) Gt[(size_t)c * m + i] = sW[i * ld + c];
