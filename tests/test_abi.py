@@ -84,6 +84,19 @@ def test_null_arguments_are_rejected(capi):
     assert lib.vx_rates_entries_per_zone(None) == 0
 
 
+def test_btd_create_rejects_invalid_arguments(capi):
+    """Checked on the host before any CUDA call."""
+    lib = capi.lib()
+    h = ctypes.c_void_p()
+    for m, z, n in ((0, 4, 2), (129, 4, 2), (-3, 4, 2), (4, -1, 2), (4, 4, -1), (4, 4, 9)):
+        assert lib.vx_btd_create(m, z, n, ctypes.byref(h)) == capi.VX_ERR_INVALID_ARG
+        assert not h.value
+    assert lib.vx_btd_create(4, 4, 2, None) == capi.VX_ERR_INVALID_ARG
+    assert lib.vx_btd_solve(None, 1, 1, *([None] * 7)) == capi.VX_ERR_INVALID_ARG
+    assert lib.vx_btd_check(None, None) == capi.VX_ERR_INVALID_ARG
+    lib.vx_btd_destroy(None)
+
+
 def test_product_package_does_not_use_the_oracle():
     pkg = os.path.join(ROOT, "paper_1404_1719_gb300")
     for dp, _, files in os.walk(pkg):
