@@ -45,10 +45,10 @@ def entries(Z, N):
 
 
 # DRAM bytes (read + write) per zone of the forward + tangent kernel, from one ncu capture of the
-# 200-ray case of this workload (dram__bytes_read.sum + dram__bytes_write.sum = 89.3 + 591.8 MB
+# 200-ray case of this workload (dram__bytes_read.sum + dram__bytes_write.sum = 90.2 + 591.4 MB
 # for 80,000 zones); scaled to a launch by the zone count. Set to None whenever the kernel
 # changes, until it has been captured again.
-TRAFFIC_BYTES_PER_ZONE = None
+TRAFFIC_BYTES_PER_ZONE = 8520
 # rays of the default workload in --mode spectral (410k zones: 17 GB of blocks)
 SPECTRAL_RAYS = 1024
 
