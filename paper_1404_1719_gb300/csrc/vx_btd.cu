@@ -1,12 +1,12 @@
 // vx_btd.cu -- batched block-tridiagonal solve of the per-ray Newton systems (include/vx_btd.h).
 //
 // Three kernels, all one ray per CTA (or per warp), since a ray's zones are a sequential chain:
-//  * k_btd_factor: block LU along the ray in FP32. Per zone: load B_k (and A_k) as FP32 into shared
-//    memory, form the Schur complement D_k = B_k - A_k G_{k-1} (G_{k-1} is still in shared memory
-//    from the previous zone; 4 x 4 register tiles), factor D_k with partial pivoting by row
-//    indirection (one CTA barrier per column), then G_k = D_k^{-1} C_k by forward and back
-//    substitution over the m right-hand sides in blocks of 8 rows. The factors, G_k and an FP32
-//    copy of A_k are written column-major, the row permutation as an index vector.
+//  * k_btd_factor: block LU along the ray in FP32, the zone's block held in registers across the
+//    CTA. Per zone: load B_k, subtract the Schur term A_k G_{k-1} (G_{k-1} is still in shared memory
+//    from the previous zone), factor D_k with partial pivoting by row indirection, then
+//    G_k = D_k^{-1} C_k by forward and back substitution over the m right-hand sides in blocks of 8
+//    rows. The factors, G_k and an FP32 copy of A_k are written column-major, the row permutation
+//    as an index vector.
 //  * k_btd_sweep: one warp per ray solves M delta = rhs with those factors: forward
 //    y_k = D_k^{-1} (rhs_k - A_k y_{k-1}), backward delta_k = y_k - G_k delta_{k+1}; a lane holds
 //    rows lane + 32 t of a zone's vector and the column being eliminated is broadcast by shuffle.
@@ -84,100 +84,6 @@ __global__ void k_btd_validate(const int *off, int n_rays, long long n_zones, in
     }
 }
 
-// sD -= sA sW over m x m blocks (row stride ld). Thread tiles of 4 x 4 with rows ti + r T and
-// columns tj + q T (T = ceil(m / 4)), so a warp's reads of sW fall in distinct banks.
-__device__ void schur_update(float *sD, const float *sA, const float *sW, int m, int ld) {
-    const int T = (m + 3) / 4;
-    for (int t = threadIdx.x; t < T * T; t += blockDim.x) {
-        const int ti = t / T, tj = t - ti * T;
-        float acc[4][4];
-#pragma unroll
-        for (int r = 0; r < 4; ++r)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc[r][q] = 0.f;
-        for (int c = 0; c < m; ++c) {
-            float av[4], gv[4];
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const int i = ti + r * T;
-                av[r] = i < m ? sA[i * ld + c] : 0.f;
-            }
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int j = tj + q * T;
-                gv[q] = j < m ? sW[c * ld + j] : 0.f;
-            }
-#pragma unroll
-            for (int r = 0; r < 4; ++r)
-#pragma unroll
-                for (int q = 0; q < 4; ++q) acc[r][q] = fmaf(av[r], gv[q], acc[r][q]);
-        }
-#pragma unroll
-        for (int r = 0; r < 4; ++r)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int i = ti + r * T, j = tj + q * T;
-                if (i < m && j < m) sD[i * ld + j] -= acc[r][q];
-            }
-    }
-    __syncthreads();
-}
-
-// LU with partial pivoting of sD by row indirection: cur[q] is the physical row at pivot position
-// q. Every warp searches the pivot column itself (largest magnitude, lowest position on ties: the
-// same answer in every warp), so a column costs one CTA barrier and no single-warp phase. During
-// column j nothing in column j of sD is written: the multipliers go to sM (by physical row) and
-// the row order to the other of the two permutation buffers. On return sOut holds the factors in
-// pivot order (unit L below the diagonal, U on and above) and the returned vector the final row
-// order, so that P D = L U with (P D)[q] = D[perm[q]]. A zero or non-finite pivot sets *bad; the
-// arithmetic then runs on (NaN/inf), which only this ray sees.
-__device__ const int *lu_factor(float *sD, float *sM, float *sOut, int m, int ld, int *p0, int *p1, int *bad) {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5, nt = blockDim.x;
-    for (int q = tid; q < m; q += nt) p0[q] = q;
-    __syncthreads();
-    int *cur = p0, *nxt = p1;
-    for (int j = 0; j < m; ++j) {
-        float best = -1.f;
-        int bq = j;
-        for (int q = j + lane; q < m; q += 32) {
-            const float v = fabsf(sD[cur[q] * ld + j]);
-            if (v > best) {
-                best = v;
-                bq = q;
-            }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-            const int oq = __shfl_xor_sync(0xffffffffu, bq, o);
-            if (ob > best || (ob == best && oq < bq)) {
-                best = ob;
-                bq = oq;
-            }
-        }
-        const int pj = cur[bq], pq = cur[j];  // the pivot row; the row that moves to position bq
-        if (tid == 0 && !(best > 0.f && best < INFINITY)) *bad = 1;
-        for (int q = tid; q < m; q += nt) nxt[q] = q == j ? pj : (q == bq ? pq : cur[q]);
-        const float piv = sD[pj * ld + j];
-        for (int q = j + 1 + warp; q < m; q += nw) {
-            const int r = q == bq ? pq : cur[q];
-            const float l = sD[r * ld + j] / piv;
-            for (int c = j + 1 + lane; c < m; c += 32) sD[r * ld + c] = fmaf(-l, sD[pj * ld + c], sD[r * ld + c]);
-            if (lane == 0) sM[r * ld + j] = l;
-        }
-        __syncthreads();
-        int *t = cur;
-        cur = nxt;
-        nxt = t;
-    }
-    for (int q = warp; q < m; q += nw) {
-        const int r = cur[q];
-        for (int c = lane; c < m; c += 32) sOut[q * ld + c] = c < q ? sM[r * ld + c] : sD[r * ld + c];
-    }
-    __syncthreads();
-    return cur;
-}
-
 // sW <- U^{-1} L^{-1} sW for the m right-hand sides in the columns of sW (rows in pivot order), with
 // the factors of sL in pivot order. Blocks of kSub rows: the block's own triangle first (one thread
 // per column), then the block's update of the rows still to come (rank kSub, a warp per row, lanes
@@ -251,49 +157,167 @@ __device__ void lu_solve_block(const float *sL, float *sW, int m, int ld) {
     }
 }
 
-__global__ void __launch_bounds__(kFactorThreads) k_btd_factor(const BtdArgs a) {
+// The factor kernel. Thread (warp w, lane x) of the 8 x 32 CTA holds in registers the elements of
+// D_k in rows w + 8 s (s < RS) and columns x + 32 t (t < CS), RS = ceil(m / 8), CS = ceil(m / 32):
+// B_k is loaded there, the Schur update A_k G_{k-1} is subtracted there (A_k and G_{k-1} from shared
+// memory, RS + CS loads per RS x CS FMAs), and the LU runs there. Column j of the LU: the lanes
+// holding column j publish it; every warp finds the pivot itself (largest magnitude among the rows
+// not yet pivots, lowest position on ties: the same in every warp) and the warp holding the pivot row
+// publishes that row; then every thread eliminates column j from its rows that are not yet pivots,
+// leaving the multiplier in column j. Rows are never moved: the pivot order is an index vector
+// (double-buffered, so it is never read and written in the same phase), and the column and row
+// buffers alternate between columns. Two CTA barriers per column. At the end the factors are
+// written to shared memory in pivot order for the substitutions and the column-major copy.
+template <int RS, int CS>
+__global__ void __launch_bounds__(kFactorThreads, 2) k_btd_factor(const BtdArgs a) {
     extern __shared__ __align__(16) float sm[];
     __shared__ int s_bad;
-    const int m = a.m, ld = a.ld, tid = threadIdx.x, nt = blockDim.x;
-    const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-    float *sD = sm, *sW = sD + m * ld, *sA = sW + m * ld;
-    int *sP0 = reinterpret_cast<int *>(sA + m * ld);
-    int *sP1 = sP0 + m;
+    const int m = a.m, ld = a.ld, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float *sA = sm;              // A_k, then the factors of D_k in pivot order
+    float *sW = sA + m * ld;     // G_{k-1}, then P C_k -> G_k
+    float *colb = sW + m * ld;   // [2][m] the pivot column
+    float *rowb = colb + 2 * m;  // [2][m] the pivot row
+    int *p0 = reinterpret_cast<int *>(rowb + 2 * m), *p1 = p0 + m, *pos = p1 + m;
     long long z0, z1;
     if (!ray_range(a, blockIdx.x, z0, z1) || z1 == z0) return;
     if (tid == 0) s_bad = 0;
     const size_t mm = (size_t)m * m;
     for (long long k = z0; k < z1; ++k) {
         const bool prev = k > z0;
-        const double *Bk = a.B + k * mm, *Ak = a.A + k * mm;
-        for (int i = warp; i < m; i += nw)  // rows by warp, columns by lane: coalesced
-            for (int j = lane; j < m; j += 32) {
-                sD[i * ld + j] = (float)Bk[(size_t)i * m + j];
-                if (prev) sA[i * ld + j] = (float)Ak[(size_t)i * m + j];
-            }
-        __syncthreads();
+        float v[RS][CS];
+        {
+            const double *Bk = a.B + k * mm;
+#pragma unroll
+            for (int s = 0; s < RS; ++s)
+#pragma unroll
+                for (int t = 0; t < CS; ++t) {
+                    const int i = warp + 8 * s, c = lane + 32 * t;
+                    v[s][t] = (i < m && c < m) ? (float)Bk[(size_t)i * m + c] : 0.f;
+                }
+        }
         if (prev) {
-            schur_update(sD, sA, sW, m, ld);
-            float *At = a.At + k * mm;
-            for (int c = warp; c < m; c += nw)  // column-major copy: lanes along a column
+            const double *Ak = a.A + k * mm;
+            for (int i = warp; i < m; i += 8)
+                for (int c = lane; c < m; c += 32) sA[i * ld + c] = (float)Ak[(size_t)i * m + c];
+            __syncthreads();
+            for (int c = 0; c < m; ++c) {  // v -= A_k G_{k-1}
+                float ar[RS], gc[CS];
+#pragma unroll
+                for (int s = 0; s < RS; ++s) {
+                    const int i = warp + 8 * s;
+                    ar[s] = i < m ? sA[i * ld + c] : 0.f;
+                }
+#pragma unroll
+                for (int t = 0; t < CS; ++t) {
+                    const int col = lane + 32 * t;
+                    gc[t] = col < m ? sW[c * ld + col] : 0.f;
+                }
+#pragma unroll
+                for (int s = 0; s < RS; ++s)
+#pragma unroll
+                    for (int t = 0; t < CS; ++t) v[s][t] = fmaf(-ar[s], gc[t], v[s][t]);
+            }
+            float *At = a.At + k * mm;  // FP32 column-major copy for the solve sweeps
+            for (int c = warp; c < m; c += 8)
                 for (int i = lane; i < m; i += 32) At[(size_t)c * m + i] = sA[i * ld + c];
         }
-        // G_{k-1} in sW and A_k in sA are consumed: sW takes the multipliers, sA the factors
-        const int *perm = lu_factor(sD, sW, sA, m, ld, sP0, sP1, &s_bad);
+        for (int q = tid; q < m; q += kFactorThreads) p0[q] = q;
+        __syncthreads();
+        // LU in registers
+        int *cur = p0, *nxt = p1;
+        unsigned done = 0u;  // bit s: my row warp + 8 s has been a pivot
+        for (int j = 0; j < m; ++j) {
+            float *cb = colb + (j & 1) * m, *rb = rowb + (j & 1) * m;
+            if (lane == (j & 31)) {
+                const int tj = j >> 5;
+#pragma unroll
+                for (int t = 0; t < CS; ++t)
+                    if (t == tj)
+#pragma unroll
+                        for (int s = 0; s < RS; ++s) {
+                            const int i = warp + 8 * s;
+                            if (i < m) cb[i] = v[s][t];
+                        }
+            }
+            __syncthreads();
+            float best = -1.f;
+            int bq = j;
+            for (int q = j + lane; q < m; q += 32) {
+                const float x = fabsf(cb[cur[q]]);
+                if (x > best) {
+                    best = x;
+                    bq = q;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const int oq = __shfl_xor_sync(0xffffffffu, bq, o);
+                if (ob > best || (ob == best && oq < bq)) {
+                    best = ob;
+                    bq = oq;
+                }
+            }
+            const int pj = cur[bq], pq = cur[j];  // the pivot row; the row that moves to position bq
+            if (tid == 0 && !(best > 0.f && best < INFINITY)) s_bad = 1;
+            for (int q = tid; q < m; q += kFactorThreads) nxt[q] = q == j ? pj : (q == bq ? pq : cur[q]);
+            if (warp == (pj & 7)) {
+                const int sp = pj >> 3;
+#pragma unroll
+                for (int s = 0; s < RS; ++s)
+                    if (s == sp) {
+#pragma unroll
+                        for (int t = 0; t < CS; ++t) {
+                            const int c = lane + 32 * t;
+                            if (c < m) rb[c] = v[s][t];
+                        }
+                        done |= 1u << s;
+                    }
+            }
+            __syncthreads();
+            const float ipiv = 1.f / rb[j];
+#pragma unroll
+            for (int s = 0; s < RS; ++s) {
+                const int i = warp + 8 * s;
+                if (i < m && !((done >> s) & 1u)) {
+                    const float l = cb[i] * ipiv;
+#pragma unroll
+                    for (int t = 0; t < CS; ++t) {
+                        const int c = lane + 32 * t;
+                        if (c > j && c < m) v[s][t] = fmaf(-l, rb[c], v[s][t]);
+                        else if (c == j) v[s][t] = l;
+                    }
+                }
+            }
+            int *tmp = cur;
+            cur = nxt;
+            nxt = tmp;
+        }
+        // factors in pivot order (A_k is no longer needed: the barriers above ordered its last reads)
+        for (int q = tid; q < m; q += kFactorThreads) pos[cur[q]] = q;
+        __syncthreads();
+#pragma unroll
+        for (int s = 0; s < RS; ++s)
+#pragma unroll
+            for (int t = 0; t < CS; ++t) {
+                const int i = warp + 8 * s, c = lane + 32 * t;
+                if (i < m && c < m) sA[pos[i] * ld + c] = v[s][t];
+            }
+        __syncthreads();
         float *LUt = a.LUt + k * mm;
-        for (int c = warp; c < m; c += nw)
+        for (int c = warp; c < m; c += 8)
             for (int i = lane; i < m; i += 32) LUt[(size_t)c * m + i] = sA[i * ld + c];
-        for (int i = tid; i < m; i += nt) a.perm[k * m + i] = perm[i];
+        for (int i = tid; i < m; i += kFactorThreads) a.perm[k * m + i] = cur[i];
         if (k + 1 < z1) {
             const double *Ck = a.C + k * mm;
-            for (int i = warp; i < m; i += nw) {
-                const double *row = Ck + (size_t)perm[i] * m;
+            for (int i = warp; i < m; i += 8) {
+                const double *row = Ck + (size_t)cur[i] * m;
                 for (int c = lane; c < m; c += 32) sW[i * ld + c] = (float)row[c];
             }
             __syncthreads();
             lu_solve_block(sA, sW, m, ld);
             float *Gt = a.Gt + k * mm;
-            for (int c = warp; c < m; c += nw)
+            for (int c = warp; c < m; c += 8)
                 for (int i = lane; i < m; i += 32) Gt[(size_t)c * m + i] = sW[i * ld + c];
         }
         __syncthreads();
@@ -501,6 +525,20 @@ __global__ void __launch_bounds__(kResidThreads) k_btd_resid(const BtdArgs a) {
 
 }  // namespace
 
+// The factor kernel's register tile for m unknowns per zone: rows per warp x columns per lane.
+static const void *factor_kernel(int m) {
+    if (m <= 32) return (const void *)k_btd_factor<4, 1>;
+    if (m <= 64) return (const void *)k_btd_factor<8, 2>;
+    if (m <= 96) return (const void *)k_btd_factor<12, 3>;
+    return (const void *)k_btd_factor<16, 4>;
+}
+static void launch_factor(int m, int grid, size_t smem, cudaStream_t s, const BtdArgs &a) {
+    if (m <= 32) k_btd_factor<4, 1><<<grid, kFactorThreads, smem, s>>>(a);
+    else if (m <= 64) k_btd_factor<8, 2><<<grid, kFactorThreads, smem, s>>>(a);
+    else if (m <= 96) k_btd_factor<12, 3><<<grid, kFactorThreads, smem, s>>>(a);
+    else k_btd_factor<16, 4><<<grid, kFactorThreads, smem, s>>>(a);
+}
+
 struct vx_btd {
     int m = 0, ld = 0, n_refine = 0;
     long long max_zones = 0;
@@ -536,7 +574,7 @@ extern "C" vx_status vx_btd_create(int m, long long max_zones, int n_refine, vx_
     h->ld = m | 1;  // odd row stride: column walks through shared memory hit distinct banks
     h->n_refine = n_refine;
     h->max_zones = max_zones;
-    h->smem = (size_t)3 * m * h->ld * sizeof(float) + (size_t)2 * m * sizeof(int);
+    h->smem = ((size_t)2 * m * h->ld + 4 * (size_t)m) * sizeof(float) + (size_t)3 * m * sizeof(int);
     h->smem_sweep = ((size_t)2 * ((m * m + 3) & ~3) + m) * sizeof(float);
     const size_t zc = (size_t)(max_zones > 0 ? max_zones : 1), mm = (size_t)m * m;
     cudaError_t e = cudaSuccess;
@@ -550,7 +588,7 @@ extern "C" vx_status vx_btd_create(int m, long long max_zones, int n_refine, vx_
     if (e == cudaSuccess) e = cudaMalloc(&h->flag, 2 * sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(h->flag, 0, 2 * sizeof(int));
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_btd_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem);
+        e = cudaFuncSetAttribute(factor_kernel(m), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem);
     const void *sweeps[4] = {(const void *)k_btd_sweep<true, true>, (const void *)k_btd_sweep<true, false>,
                              (const void *)k_btd_sweep<false, true>, (const void *)k_btd_sweep<false, false>};
     for (int i = 0; i < 4 && e == cudaSuccess; ++i)
@@ -605,7 +643,7 @@ extern "C" vx_status vx_btd_solve(vx_btd *h, int n_rays, long long n_zones, cons
     BTD_CU(cudaMemsetAsync(h->flag + 1, 0, sizeof(int), s));
     k_btd_validate<<<(unsigned)((n_rays + 256) / 256), 256, 0, s>>>(ray_offsets, n_rays, n_zones, h->flag + 1, h->flag);
     BTD_CU(cudaGetLastError());
-    k_btd_factor<<<n_rays, kFactorThreads, h->smem, s>>>(a);
+    launch_factor(h->m, n_rays, h->smem, s, a);
     BTD_CU(cudaGetLastError());
     if (h->n_refine == 0)
         k_btd_sweep<true, true><<<n_rays, 32, h->smem_sweep, s>>>(a);
