@@ -1,6 +1,7 @@
 // vx_btd.cu -- batched block-tridiagonal solve of the per-ray Newton systems (include/vx_btd.h).
 //
-// Three kernels, all one ray per CTA (or per warp), since a ray's zones are a sequential chain:
+// One ray per CTA (or per warp), since a ray's zones are a sequential chain; k_btd_validate first
+// checks that the ray offsets partition the zones (else every kernel returns at once):
 //  * k_btd_factor: block LU along the ray in FP32, the zone's block held in registers across the
 //    CTA. Per zone: load B_k, subtract the Schur term A_k G_{k-1} (G_{k-1} is still in shared memory
 //    from the previous zone), factor D_k with partial pivoting by row indirection, then
@@ -13,7 +14,8 @@
 //    The first sweep writes x = delta, later ones add delta to x in FP64.
 //  * k_btd_resid: the FP64 residual r = d - M x from the caller's FP64 blocks, one warp per zone
 //    row block, lanes across a row (coalesced), a fixed butterfly reduction per row.
-// The host runs factor, sweep, then n_refine times (resid, sweep), all on the caller's stream.
+// The host runs validate, factor, sweep, then n_refine times (resid, sweep), all on the caller's
+// stream.
 #include "../../include/vx_btd.h"
 
 #include <cuda_runtime.h>
