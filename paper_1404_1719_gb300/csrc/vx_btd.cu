@@ -91,6 +91,7 @@ __global__ void k_btd_validate(const int *off, int n_rays, long long n_zones, in
 // per column), then the block's update of the rows still to come (rank kSub, a warp per row, lanes
 // along the columns); two CTA barriers per block.
 constexpr int kSub = 8;
+constexpr int kPan = 8;  // columns per LU panel
 __device__ void lu_solve_block(const float *sL, float *sW, int m, int ld) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5, nt = blockDim.x;
     for (int j0 = 0; j0 < m; j0 += kSub) {  // forward: unit lower triangle
@@ -162,13 +163,13 @@ __device__ void lu_solve_block(const float *sL, float *sW, int m, int ld) {
 // The factor kernel. Thread (warp w, lane x) of the 8 x 32 CTA holds in registers the elements of
 // D_k in rows w + 8 s (s < RS) and columns x + 32 t (t < CS), RS = ceil(m / 8), CS = ceil(m / 32):
 // B_k is loaded there, the Schur update A_k G_{k-1} is subtracted there (A_k and G_{k-1} from shared
-// memory, RS + CS loads per RS x CS FMAs), and the LU runs there. Column j of the LU: the lanes
-// holding column j publish it; every warp finds the pivot itself (largest magnitude among the rows
-// not yet pivots, lowest position on ties: the same in every warp) and the warp holding the pivot row
-// publishes that row; then every thread eliminates column j from its rows that are not yet pivots,
-// leaving the multiplier in column j. Rows are never moved: the pivot order is an index vector
-// (double-buffered, so it is never read and written in the same phase), and the column and row
-// buffers alternate between columns. Two CTA barriers per column. At the end the factors are
+// memory, RS + CS loads per RS x CS FMAs), and the LU runs there, in panels of kPan columns:
+// (1) the panel columns of the rows not yet pivots go to shared memory; (2) warp 0 factors the
+// panel alone (partial pivoting: largest magnitude, lowest position on ties; no CTA barrier inside
+// the panel); (3) the panel's pivot rows publish their trailing columns and every thread takes the
+// factored panel columns back; (4) U12 = L11^{-1} U by one thread per trailing column; (5) the pivot
+// rows take U12 and every other row gets the rank-kPan update in registers. Rows are never moved:
+// the pivot order is an index vector. Five CTA barriers per panel. At the end the factors are
 // written to shared memory in pivot order for the substitutions and the column-major copy.
 template <int RS, int CS>
 __global__ void __launch_bounds__(kFactorThreads, 2) k_btd_factor(const BtdArgs a) {
@@ -177,9 +178,9 @@ __global__ void __launch_bounds__(kFactorThreads, 2) k_btd_factor(const BtdArgs 
     const int m = a.m, ld = a.ld, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     float *sA = sm;              // A_k, then the factors of D_k in pivot order
     float *sW = sA + m * ld;     // G_{k-1}, then P C_k -> G_k
-    float *colb = sW + m * ld;   // [2][m] the pivot column
-    float *rowb = colb + 2 * m;  // [2][m] the pivot row
-    int *p0 = reinterpret_cast<int *>(rowb + 2 * m), *p1 = p0 + m, *pos = p1 + m;
+    float *P = sW + m * ld;      // [m][kPan] the panel columns (by physical row), then L21 and L11
+    float *U = P + kPan * m;     // [kPan][m] the panel's pivot rows, trailing columns, then U12
+    int *p0 = reinterpret_cast<int *>(U + kPan * m), *pos = p0 + m;
     long long z0, z1;
     if (!ray_range(a, blockIdx.x, z0, z1) || z1 == z0) return;
     if (tid == 0) s_bad = 0;
@@ -225,75 +226,149 @@ __global__ void __launch_bounds__(kFactorThreads, 2) k_btd_factor(const BtdArgs 
         }
         for (int q = tid; q < m; q += kFactorThreads) p0[q] = q;
         __syncthreads();
-        // LU in registers
-        int *cur = p0, *nxt = p1;
+        // LU in registers, in panels of kPan columns
+        int *cur = p0;      // position -> physical row; written only by warp 0 inside a panel
         unsigned done = 0u;  // bit s: my row warp + 8 s has been a pivot
-        for (int j = 0; j < m; ++j) {
-            float *cb = colb + (j & 1) * m, *rb = rowb + (j & 1) * m;
-            if (lane == (j & 31)) {
-                const int tj = j >> 5;
+        for (int j0 = 0; j0 < m; j0 += kPan) {
+            const int jb = m - j0 < kPan ? m - j0 : kPan;
+            // (1) the panel columns of the rows not yet pivots go to P[row][0 .. jb)
 #pragma unroll
-                for (int t = 0; t < CS; ++t)
-                    if (t == tj)
+            for (int t = 0; t < CS; ++t) {
+                const int c = lane + 32 * t;
+                if (c >= j0 && c < j0 + jb)
 #pragma unroll
-                        for (int s = 0; s < RS; ++s) {
-                            const int i = warp + 8 * s;
-                            if (i < m) cb[i] = v[s][t];
-                        }
-            }
-            __syncthreads();
-            float best = -1.f;
-            int bq = j;
-            for (int q = j + lane; q < m; q += 32) {
-                const float x = fabsf(cb[cur[q]]);
-                if (x > best) {
-                    best = x;
-                    bq = q;
-                }
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-                const int oq = __shfl_xor_sync(0xffffffffu, bq, o);
-                if (ob > best || (ob == best && oq < bq)) {
-                    best = ob;
-                    bq = oq;
-                }
-            }
-            const int pj = cur[bq], pq = cur[j];  // the pivot row; the row that moves to position bq
-            if (tid == 0 && !(best > 0.f && best < INFINITY)) s_bad = 1;
-            for (int q = tid; q < m; q += kFactorThreads) nxt[q] = q == j ? pj : (q == bq ? pq : cur[q]);
-            if (warp == (pj & 7)) {
-                const int sp = pj >> 3;
-#pragma unroll
-                for (int s = 0; s < RS; ++s)
-                    if (s == sp) {
-#pragma unroll
-                        for (int t = 0; t < CS; ++t) {
-                            const int c = lane + 32 * t;
-                            if (c < m) rb[c] = v[s][t];
-                        }
-                        done |= 1u << s;
+                    for (int s = 0; s < RS; ++s) {
+                        const int i = warp + 8 * s;
+                        if (i < m && !((done >> s) & 1u)) P[i * kPan + (c - j0)] = v[s][t];
                     }
             }
             __syncthreads();
-            const float ipiv = 1.f / rb[j];
+            // (2) warp 0 factors the panel: partial pivoting over the positions not yet pivots
+            if (warp == 0) {
+                for (int jj = 0; jj < jb; ++jj) {
+                    const int j = j0 + jj;
+                    float best = -1.f;
+                    int bq = j;
+                    for (int q = j + lane; q < m; q += 32) {
+                        const float x = fabsf(P[cur[q] * kPan + jj]);
+                        if (x > best) {
+                            best = x;
+                            bq = q;
+                        }
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+                        const int oq = __shfl_xor_sync(0xffffffffu, bq, o);
+                        if (ob > best || (ob == best && oq < bq)) {
+                            best = ob;
+                            bq = oq;
+                        }
+                    }
+                    const int pj = cur[bq];
+                    __syncwarp();
+                    if (lane == 0) {
+                        cur[bq] = cur[j];
+                        cur[j] = pj;
+                        if (!(best > 0.f && best < INFINITY)) s_bad = 1;
+                    }
+                    __syncwarp();
+                    const float ipiv = 1.f / P[pj * kPan + jj];
+                    for (int q = j + 1 + lane; q < m; q += 32) {
+                        const int r = cur[q];
+                        const float l = P[r * kPan + jj] * ipiv;
+                        P[r * kPan + jj] = l;
+                        for (int kk = jj + 1; kk < jb; ++kk)
+                            P[r * kPan + kk] = fmaf(-l, P[pj * kPan + kk], P[r * kPan + kk]);
+                    }
+                    __syncwarp();
+                }
+            }
+            __syncthreads();
+            // (3) the panel's pivot rows publish their trailing columns to U[a][c]; the panel
+            //     columns come back from P; the panel's pivot rows are now done
+            for (int a = 0; a < jb; ++a) {
+                const int pr = cur[j0 + a];
+                if (warp == (pr & 7)) {
+                    const int sp = pr >> 3;
+#pragma unroll
+                    for (int s = 0; s < RS; ++s)
+                        if (s == sp)
+#pragma unroll
+                            for (int t = 0; t < CS; ++t) {
+                                const int c = lane + 32 * t;
+                                if (c >= j0 + jb && c < m) U[a * m + c] = v[s][t];
+                            }
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < CS; ++t) {
+                const int c = lane + 32 * t;
+                if (c >= j0 && c < j0 + jb)
+#pragma unroll
+                    for (int s = 0; s < RS; ++s) {
+                        const int i = warp + 8 * s;
+                        if (i < m && !((done >> s) & 1u)) v[s][t] = P[i * kPan + (c - j0)];
+                    }
+            }
+            for (int a = 0; a < jb; ++a) {
+                const int pr = cur[j0 + a];
+                if (warp == (pr & 7)) done |= 1u << (pr >> 3);
+            }
+            __syncthreads();
+            // (4) U12 = L11^{-1} U, one thread per trailing column
+            for (int c = j0 + jb + tid; c < m; c += kFactorThreads) {
+                float u[kPan];
+#pragma unroll
+                for (int a = 0; a < kPan; ++a) u[a] = a < jb ? U[a * m + c] : 0.f;
+#pragma unroll
+                for (int a = 1; a < kPan; ++a)
+                    if (a < jb) {
+                        const float *la = P + cur[j0 + a] * kPan;
+#pragma unroll
+                        for (int b = 0; b < a; ++b) u[a] = fmaf(-la[b], u[b], u[a]);
+                    }
+#pragma unroll
+                for (int a = 0; a < kPan; ++a)
+                    if (a < jb) U[a * m + c] = u[a];
+            }
+            __syncthreads();
+            // (5) the pivot rows take U12; the other rows get the rank-jb update
+            for (int a = 0; a < jb; ++a) {
+                const int pr = cur[j0 + a];
+                if (warp == (pr & 7)) {
+                    const int sp = pr >> 3;
+#pragma unroll
+                    for (int s = 0; s < RS; ++s)
+                        if (s == sp)
+#pragma unroll
+                            for (int t = 0; t < CS; ++t) {
+                                const int c = lane + 32 * t;
+                                if (c >= j0 + jb && c < m) v[s][t] = U[a * m + c];
+                            }
+                }
+            }
 #pragma unroll
             for (int s = 0; s < RS; ++s) {
                 const int i = warp + 8 * s;
                 if (i < m && !((done >> s) & 1u)) {
-                    const float l = cb[i] * ipiv;
+                    float l[kPan];
+#pragma unroll
+                    for (int a = 0; a < kPan; ++a) l[a] = a < jb ? P[i * kPan + a] : 0.f;
 #pragma unroll
                     for (int t = 0; t < CS; ++t) {
                         const int c = lane + 32 * t;
-                        if (c > j && c < m) v[s][t] = fmaf(-l, rb[c], v[s][t]);
-                        else if (c == j) v[s][t] = l;
+                        if (c >= j0 + jb && c < m) {
+                            float acc = v[s][t];
+#pragma unroll
+                            for (int a = 0; a < kPan; ++a)
+                                if (a < jb) acc = fmaf(-l[a], U[a * m + c], acc);
+                            v[s][t] = acc;
+                        }
                     }
                 }
             }
-            int *tmp = cur;
-            cur = nxt;
-            nxt = tmp;
+            __syncthreads();
         }
         // factors in pivot order (A_k is no longer needed: the barriers above ordered its last reads)
         for (int q = tid; q < m; q += kFactorThreads) pos[cur[q]] = q;
@@ -576,7 +651,7 @@ extern "C" vx_status vx_btd_create(int m, long long max_zones, int n_refine, vx_
     h->ld = m | 1;  // odd row stride: column walks through shared memory hit distinct banks
     h->n_refine = n_refine;
     h->max_zones = max_zones;
-    h->smem = ((size_t)2 * m * h->ld + 4 * (size_t)m) * sizeof(float) + (size_t)3 * m * sizeof(int);
+    h->smem = ((size_t)2 * m * h->ld + 2 * (size_t)kPan * m) * sizeof(float) + (size_t)2 * m * sizeof(int);
     h->smem_sweep = ((size_t)2 * ((m * m + 3) & ~3) + m) * sizeof(float);
     const size_t zc = (size_t)(max_zones > 0 ? max_zones : 1), mm = (size_t)m * m;
     cudaError_t e = cudaSuccess;
