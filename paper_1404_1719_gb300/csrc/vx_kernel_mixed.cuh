@@ -185,7 +185,8 @@ __device__ __forceinline__ void mo_from_tangents(Mom &mo, const Mom &ta, const M
 }
 
 // Degenerate path, packed on mirror pairs: exact-split electron argument, direct positron argument,
-// first-order products with r (see node_loop), inline or as an out-of-line call (OUTLINE).
+// tangents from r^2 where the zone scale keeps r^2 in the FP32 range (R2), else first-order products
+// with r (see node_loop), inline or as an out-of-line call (OUTLINE).
 // (UD: unroll cap; the tangent kernel's loop may be unrolled whole.)
 template <int NE, bool ADJ, bool OUTLINE, bool R2, int UD>
 struct DegPacked {
@@ -374,7 +375,7 @@ __device__ __forceinline__ void df_diff(float ah, float al, float bh, float bl, 
 // GTa = O (f_e E + f_ebar Ebar), GTp = O ((1-f_e) E + (1-f_ebar) Ebar), GEt = O (f_ebar - f_e).
 // With the zone scale (degenerate path) e1 and the "1" of 1 + e1 carry the factor 2^-sc, so
 // r = 2^sc O; c1 = 2^-sc recovers 1 - f_e, while f_e, f_ebar and 1 - f_ebar need no correction.
-// The loop is unrolled 16 nodes deep (the instruction footprint stays cache resident).
+// The unroll depth of each loop is set by unroll_depth (the whole rule or chunks that divide n_e).
 //
 // Fast path, unrolled instantiations (even n_e): the Gauss-Legendre nodes come in exact mirror
 // pairs tau, -tau (records k and n_e-1-k hold the same values with u <-> v and
