@@ -396,8 +396,9 @@ def run_ours(args):
     h_out = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in out.items()}
     h_jac = torch.empty(jac.shape, dtype=jac.dtype, pin_memory=True)
     h_spec = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in spec_out.items()}
-    hb = capi.vx_batch(n_rays=bt.n_rays, n_zones=Z, ray_offsets=bt.ray_offsets, state=host["state"].data_ptr(),
-                       J=host["J"].data_ptr(), H=host["H"].data_ptr())
+    offs_host = np.ascontiguousarray(b["ray_offsets"], dtype=np.int32)  # the host calls take host offsets
+    hb = capi.vx_batch(n_rays=bt.n_rays, n_zones=Z, ray_offsets=offs_host.ctypes.data_as(capi._ip),
+                       state=host["state"].data_ptr(), J=host["J"].data_ptr(), H=host["H"].data_ptr())
     hfwd = capi.vx_out(*(h_out[k].data_ptr() for k in ("j0", "chi0", "j1", "chi1")), None)
     h_seeds = torch.ones((Z, S, N), dtype=torch.float64, pin_memory=True) if spec else None
     hseeds = capi.vx_out(*([h_seeds.data_ptr()] * 4), None) if spec else None

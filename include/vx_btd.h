@@ -58,8 +58,9 @@ vx_status vx_btd_create(int m, long long max_zones, int n_refine, vx_btd **out);
  *   d:           device FP64 [n_zones][m], right-hand sides.
  *   x:           device FP64 [n_zones][m], the solution (written; must not overlap d or the blocks).
  * A ray with a zero or non-finite pivot gets NaN in x and raises the numeric flag (vx_btd_check).
- * Errors: VX_ERR_INVALID_ARG (NULL handle or pointers with n_zones > 0, n_rays < 0, n_zones out of
- * range, x == d), VX_ERR_CUDA. */
+ * Errors: VX_ERR_INVALID_ARG (NULL handle or pointers with n_zones > 0, a pointer that is not device
+ * (or managed) memory, offsets not 4-byte or FP64 arrays not 8-byte aligned, n_rays < 0, n_zones
+ * out of range, x overlapping an input), VX_ERR_CUDA. Nothing is launched then. */
 vx_status vx_btd_solve(vx_btd *h, int n_rays, long long n_zones, const int *ray_offsets, const double *A,
                        const double *B, const double *C, const double *d, double *x, vx_stream stream);
 

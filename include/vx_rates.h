@@ -106,9 +106,16 @@ vx_status vx_rates_create(const vx_config *cfg, vx_rates **out);
 typedef struct {
     int n_rays;               /* R >= 0                                                        */
     long long n_zones;        /* Z >= 0 (zones of all rays, concatenated ray by ray)           */
-    const int *ray_offsets;   /* host [R+1] or NULL (one ray): offsets[0] = 0, non-decreasing,
-                                 offsets[R] = Z. Rays may be ragged; the rate of a zone does not
-                                 depend on its ray, so the layout is only validated.            */
+    const int *ray_offsets;   /* device int32 [R+1] or NULL (one ray), as in vx_btd_solve:
+                                 offsets[0] = 0, non-decreasing, offsets[R] = Z. Rays may be
+                                 ragged; the rate of a zone does not depend on its ray, so the
+                                 layout is only validated, on the device by the launch: offsets
+                                 that are not such a partition raise the device flag
+                                 (vx_rates_check: VX_ERR_NUMERIC, "invalid ray offsets") and every
+                                 zone is still evaluated. A pointer that is not device memory, or
+                                 R = 0 with Z > 0, is rejected on the host (VX_ERR_INVALID_ARG).
+                                 The host-buffer calls below take a HOST array instead, validated
+                                 on the host like the rest of their arguments.                   */
     const double *state;      /* device [Z][4]: T (MeV, > 0), eta_e = mu_e/T, Y_e, rho (g/cm^3) */
     const double *J;          /* device [Z][S][N]: 0th occupation moment of each species' own
                                  spectrum (species in config order)                             */
@@ -156,8 +163,9 @@ vx_status vx_rates_spectral(vx_rates *h, const vx_batch *batch, const vx_out *gr
                             double *grad_H, double *blocks, const vx_out *fwd, vx_stream stream);
 
 /* Host-buffer forms of vx_rates_eval, vx_rates_adjoint (forward rates and Jacobian) and
- * vx_rates_spectral: the batch's state, J and H, the seeds and every output are HOST arrays in
- * the layouts above (pinned memory lets the copies run asynchronously). The library copies the
+ * vx_rates_spectral: the batch's ray_offsets, state, J and H, the seeds and every output are HOST
+ * arrays in the layouts above (pinned memory lets the copies run asynchronously); ray offsets
+ * that are not a partition of the zones are rejected with VX_ERR_INVALID_ARG. The library copies the
  * batch in chunks of zones through two staging slots of device memory it owns (640 MiB each, or
  * the MiB given by the environment variable VX_HOST_SLOT_MB; allocated on the handle's first such
  * call and kept until vx_rates_destroy), on two streams of its own,
@@ -199,7 +207,8 @@ void vx_rates_destroy(vx_rates *h);
  *     overlaps on the same GPU (for example on two streams) race and must be serialised by the
  *     caller. Not thread-safe.
  *   - Device-side numeric problems show up as NaN outputs of the affected zones; there is no
- *     check call for this entry point. */
+ *     check call for this entry point. batch->ray_offsets, if given, must be device memory but is
+ *     not read (the rates do not depend on the ray layout, and there is no flag to report it). */
 vx_status vx_rates_eval_noalloc(const vx_config *cfg, const vx_batch *batch, const vx_out *out, vx_stream stream);
 
 const char *vx_status_string(vx_status s);

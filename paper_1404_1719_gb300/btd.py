@@ -35,6 +35,11 @@ class BlockTridiagSolver:
         for t in (offsets, A, B, C, d):
             if not t.is_cuda:
                 raise ValueError("solve() takes CUDA tensors; use solve_host() for host data")
+        if len({t.device for t in (offsets, A, B, C, d)}) != 1:
+            raise ValueError("offsets, A, B, C and d must be on one device")
+        if out is not None and (not torch.is_tensor(out) or out.dtype != torch.float64 or not out.is_contiguous()
+                                or tuple(out.shape) != tuple(d.shape) or out.device != d.device):
+            raise ValueError(f"out must be a contiguous float64 tensor of shape {tuple(d.shape)} on {d.device}")
         x = torch.empty_like(d) if out is None else out
         s = (stream or torch.cuda.current_stream(d.device)).cuda_stream
         capi.vx_btd_solve(self.handle, n_rays, Z, offsets.data_ptr(), A.data_ptr(), B.data_ptr(), C.data_ptr(),

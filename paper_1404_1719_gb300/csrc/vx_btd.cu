@@ -45,6 +45,20 @@ vx_status bfail(vx_status s, const char *fmt, ...) {
     return vx::set_error(s, buf);
 }
 
+// Device memory of the current device (or managed memory) with the given alignment; a host or
+// unregistered pointer is rejected before anything is launched.
+vx_status device_array(const void *p, size_t align, const char *name) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return bfail(VX_ERR_INVALID_ARG, "%s: not a CUDA pointer", name);
+    }
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+        return bfail(VX_ERR_INVALID_ARG, "%s must be device memory", name);
+    if ((uintptr_t)p % align) return bfail(VX_ERR_INVALID_ARG, "%s must be %zu-byte aligned", name, align);
+    return VX_OK;
+}
+
 #define BTD_CU(call)                                                                          \
     do {                                                                                      \
         cudaError_t e_ = (call);                                                              \
@@ -688,6 +702,13 @@ extern "C" vx_status vx_btd_solve(vx_btd *h, int n_rays, long long n_zones, cons
     if (n_zones > 0 && n_rays == 0) return bfail(VX_ERR_INVALID_ARG, "n_zones > 0 with no rays");
     if (n_zones == 0) return VX_OK;
     if (!ray_offsets || !A || !B || !C || !d || !x) return bfail(VX_ERR_INVALID_ARG, "NULL array");
+    {
+        vx_status st;
+        const void *arr[6] = {ray_offsets, A, B, C, d, x};
+        const char *nm[6] = {"ray_offsets", "A", "B", "C", "d", "x"};
+        for (int k = 0; k < 6; ++k)
+            if ((st = device_array(arr[k], k ? 8 : 4, nm[k])) != VX_OK) return st;
+    }
     const size_t vec = (size_t)n_zones * h->m * sizeof(double), blk = vec * h->m;
     auto overlap = [](const void *p, size_t np, const void *q, size_t nq) {
         const char *a = (const char *)p, *b = (const char *)q;

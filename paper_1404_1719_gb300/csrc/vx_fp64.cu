@@ -37,6 +37,7 @@ __global__ void __launch_bounds__(VX_TPB_MAX, 1) k_pair_fp64(const __grid_consta
     const int pi = C.pij[p] >> 8, pj = C.pij[p] & 0xff;
     const int m0 = chunk * C.n_mu / ms, m1 = (chunk + 1) * C.n_mu / ms;
     const int n = NE > 0 ? NE : C.n_e;
+    validate_offsets(L.off, L.n_rays, L.Z, L.flag);
 
     for (;;) {
         if (tid == 0) s_zone = (long long)atomicAdd(L.counter, 1ull);

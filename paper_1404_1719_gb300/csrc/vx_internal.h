@@ -27,6 +27,7 @@
 // device numeric flag bits
 #define VX_FLAG_BAD_STATE 1   // T <= 0, non-finite T or eta, or |eta| > VX_ETA_MAX
 #define VX_FLAG_NONFINITE 2   // a non-finite result was produced
+#define VX_FLAG_BAD_OFFSETS 4 // the ray offsets are not a partition of the zones
 
 namespace vx {
 
@@ -73,6 +74,8 @@ struct Launch {
                                    //   value + remainder; {kp, km, k0, cos(omega_m)}
     const double *tab64;           // [n_mu][npair][5] (FP64 form)
     long long Z;
+    const int *off;                // device ray offsets [n_rays + 1] or NULL (checked, not used)
+    int n_rays;
     const double *state, *J, *H;
     double *j0, *chi0, *j1, *chi1, *phi;
     double *jac, *grad_state;                   // adjoint outputs (may be NULL)
@@ -87,11 +90,26 @@ struct Launch64 {
     Nodes64 n64;
     const double *tab64;
     long long Z;
+    const int *off;
+    int n_rays;
     const double *state, *J, *H;
     double *j0, *chi0, *j1, *chi1, *phi;
     unsigned long long *counter;
     int *flag;
 };
+
+#ifdef __CUDACC__
+// Block 0 of a launch checks that the ray offsets partition the Z zones (off[0] = 0, no decrease,
+// off[n_rays] = Z) and raises VX_FLAG_BAD_OFFSETS if not. The rate of a zone does not depend on
+// its ray, so nothing else reads the offsets.
+__device__ inline void validate_offsets(const int *off, int n_rays, long long Z, int *flag) {
+    if (!off || blockIdx.x != 0) return;
+    bool bad = false;
+    for (int r = threadIdx.x; r < n_rays; r += blockDim.x) bad |= off[r + 1] < off[r];
+    if (threadIdx.x == 0) bad |= off[0] != 0 || (long long)off[n_rays] != Z;
+    if (bad) atomicOr(flag, VX_FLAG_BAD_OFFSETS);
+}
+#endif
 
 // Dynamic shared memory of the mixed kernel (floats unless noted), N2 = N*N:
 //   mats[q][2][N2]: per quantity q (kernel; and with tangents: T of annihilation, T of production,

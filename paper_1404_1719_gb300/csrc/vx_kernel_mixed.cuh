@@ -647,6 +647,8 @@ __global__ void __launch_bounds__(MINB == 3 ? (ADJ ? VX_LB3_THREADS_ADJ : VX_TPB
         for (int k = tid; k < C.n_e / 2; k += blockDim.x)
             s_half[k] = make_float4(L.n32.hp[k], L.n32.hm[k], L.n32.hw[k], 0.f);
 
+    validate_offsets(L.off, L.n_rays, L.Z, L.flag);
+
     // Thread 0 reserves the next zone one iteration ahead and prefetches its inputs into L2 while
     // the current zone's quadrature runs, so a zone starts without an atomic or DRAM round trip.
     long long next_z = 0;

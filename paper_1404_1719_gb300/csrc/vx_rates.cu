@@ -39,11 +39,10 @@ vx_status fail(vx_status s, const char *fmt, ...) {
                         "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
     } while (0)
 
-// Gauss-Legendre nodes (ascending, exactly antisymmetric) and weights on [-1, 1]: Newton's method
-// on P_n from the asymptotic first guess cos(pi (k - 1/4) / (n + 1/2)).
-void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w) {
-    x.assign(n, 0.0);
-    w.assign(n, 0.0);
+// Gauss-Legendre nodes (ascending, exactly antisymmetric) and weights on [-1, 1] into caller arrays
+// of n entries: Newton's method on P_n from the asymptotic first guess cos(pi (k - 1/4) / (n + 1/2)).
+// Used by vx_rates_create and, without heap storage, by vx_rates_eval_noalloc.
+void gauss_legendre(int n, double *x, double *w) {
     const double pi = 3.14159265358979323846;
     for (int k = 1; k <= n / 2 + (n & 1); ++k) {
         double r = std::cos(pi * (k - 0.25) / (n + 0.5));
@@ -79,6 +78,12 @@ void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w) {
         w[k - 1] = wk;
     }
     if (n & 1) x[n / 2] = 0.0;
+}
+
+void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w) {
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    gauss_legendre(n, x.data(), w.data());
 }
 
 int round_up(int a, int b) { return (a + b - 1) / b * b; }
@@ -362,7 +367,7 @@ long long vx_rates_entries_per_zone(const vx_rates *h) {
     return h ? (long long)h->common.N * h->common.N : 0;
 }
 
-static vx_status check_device_ptr(const void *p, const char *name) {
+static vx_status check_device_ptr(const void *p, const char *name, size_t align = 8) {
     cudaPointerAttributes a;
     cudaError_t e = cudaPointerGetAttributes(&a, p);
     if (e != cudaSuccess) {
@@ -371,7 +376,7 @@ static vx_status check_device_ptr(const void *p, const char *name) {
     }
     if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
         return fail(VX_ERR_INVALID_ARG, "%s must be device memory", name);
-    if (((uintptr_t)p) % 8) return fail(VX_ERR_INVALID_ARG, "%s must be 8-byte aligned", name);
+    if (((uintptr_t)p) % align) return fail(VX_ERR_INVALID_ARG, "%s must be %zu-byte aligned", name, align);
     return VX_OK;
 }
 
@@ -380,13 +385,10 @@ static vx_status validate_batch(const vx_rates *h, const vx_batch *b) {
     if (!b) return fail(VX_ERR_INVALID_ARG, "batch is NULL");
     if (b->n_zones < 0) return fail(VX_ERR_INVALID_ARG, "n_zones < 0");
     if (b->n_rays < 0) return fail(VX_ERR_INVALID_ARG, "n_rays < 0");
-    if (b->ray_offsets) {
-        if (b->ray_offsets[0] != 0) return fail(VX_ERR_INVALID_ARG, "ray_offsets[0] must be 0");
-        for (int r = 0; r < b->n_rays; ++r)
-            if (b->ray_offsets[r + 1] < b->ray_offsets[r])
-                return fail(VX_ERR_INVALID_ARG, "ray_offsets must be non-decreasing (ray %d)", r);
-        if ((long long)b->ray_offsets[b->n_rays] != b->n_zones)
-            return fail(VX_ERR_INVALID_ARG, "ray_offsets[n_rays] = %d but n_zones = %lld", b->ray_offsets[b->n_rays], b->n_zones);
+    if (b->ray_offsets) {  // device memory: the partition itself is checked by the launch
+        if (b->n_rays == 0 && b->n_zones > 0) return fail(VX_ERR_INVALID_ARG, "n_zones > 0 with no rays");
+        vx_status s0 = check_device_ptr(b->ray_offsets, "ray_offsets", 4);
+        if (s0 != VX_OK) return s0;
     }
     if (b->n_zones == 0) return VX_OK;
     vx_status s;
@@ -468,6 +470,8 @@ static void fill_launch(const vx_rates *h, const vx_batch *b, vx::Launch &L) {
     L.tab32 = h->d_tab32;
     L.tab64 = h->d_tab64;
     L.Z = b->n_zones;
+    L.off = b->ray_offsets;
+    L.n_rays = b->n_rays;
     L.state = b->state; L.J = b->J; L.H = b->H;
     L.j0 = L.chi0 = L.j1 = L.chi1 = L.phi = nullptr;
     L.jac = L.grad_state = nullptr;
@@ -606,6 +610,8 @@ vx_status vx_rates_eval(vx_rates *h, const vx_batch *b, const vx_out *out, vx_st
         L.n64 = h->n64;
         L.tab64 = h->d_tab64;
         L.Z = b->n_zones;
+        L.off = b->ray_offsets;
+        L.n_rays = b->n_rays;
         L.state = b->state; L.J = b->J; L.H = b->H;
         L.j0 = out->j0; L.chi0 = out->chi0; L.j1 = out->j1; L.chi1 = out->chi1; L.phi = out->phi;
         L.counter = h->d_counter;
@@ -857,9 +863,10 @@ vx_status vx_rates_check(vx_rates *h, vx_stream stream) {
     VX_CU(cudaMemcpy(&flag, h->d_flag, sizeof(int), cudaMemcpyDeviceToHost));
     if (flag) {
         VX_CU(cudaMemset(h->d_flag, 0, sizeof(int)));
-        return fail(VX_ERR_NUMERIC, "device numeric flag 0x%x (%s%s)", flag,
+        return fail(VX_ERR_NUMERIC, "device numeric flag 0x%x (%s%s%s)", flag,
                     (flag & VX_FLAG_BAD_STATE) ? "invalid zone state; " : "",
-                    (flag & VX_FLAG_NONFINITE) ? "non-finite result" : "");
+                    (flag & VX_FLAG_NONFINITE) ? "non-finite result; " : "",
+                    (flag & VX_FLAG_BAD_OFFSETS) ? "invalid ray offsets" : "");
     }
     return VX_OK;
 }
@@ -898,8 +905,10 @@ void vx_rates_destroy(vx_rates *h) {
     (VX_NOALLOC_TABLE_OFFSET + (size_t)VX_NOALLOC_MAX_PAIRS * VX_NOALLOC_MAX_MU * 2 * sizeof(float4))
 #define VX_NOALLOC_MAX_DEVICES 64
 
-// 461,056 bytes on every device that loads the library, held until the process exits.
-// Layout: [0, 8) work counter, [8, 12) numeric flag, [256, ...) the pair table.
+// 307,456 bytes (256 + 300 pairs x 32 nodes x 2 float4) on every device that loads the library,
+// held until the process exits. Layout: [0, 8) work counter, [8, 12) numeric flag, [256, ...) the
+// pair table.
+static_assert(VX_NOALLOC_SCRATCH_BYTES == 307456, "the header states the scratch size");
 static __device__ __align__(256) unsigned char g_noalloc_scratch[VX_NOALLOC_SCRATCH_BYTES];
 
 // Device address of g_noalloc_scratch per device; the name itself is only a host-side stand-in.
@@ -935,42 +944,6 @@ __global__ void k_noalloc_table(const __grid_constant__ NoallocTab P, float4 *ta
     const float fh = (float)hh, fEm = (float)Em;
     r[0] = make_float4(fh, (float)(hh - fh), fEm, (float)(Em - fEm));
     r[1] = make_float4((float)kp, (float)km, (float)k0, (float)t);
-}
-
-// Gauss-Legendre nodes and weights into caller arrays (the same Newton iteration as
-// gauss_legendre, without heap storage).
-void gl_fixed(int n, double *x, double *w) {
-    const double pi = 3.14159265358979323846;
-    for (int k = 1; k <= n / 2 + (n & 1); ++k) {
-        double r = std::cos(pi * (k - 0.25) / (n + 0.5)), dP = 1.0;
-        for (int it = 0; it < 60; ++it) {
-            double Pm = 1.0, P = r;
-            for (int m = 2; m <= n; ++m) {
-                double Pn = ((2 * m - 1) * r * P - (m - 1) * Pm) / m;
-                Pm = P;
-                P = Pn;
-            }
-            if (n == 1) { P = r; Pm = 1.0; }
-            dP = n * (Pm - r * P) / (1.0 - r * r);
-            double step = P / dP;
-            r -= step;
-            if (std::fabs(step) <= 1e-17) {
-                Pm = 1.0; P = r;
-                for (int m = 2; m <= n; ++m) {
-                    double Pn = ((2 * m - 1) * r * P - (m - 1) * Pm) / m;
-                    Pm = P;
-                    P = Pn;
-                }
-                if (n == 1) { P = r; Pm = 1.0; }
-                dP = n * (Pm - r * P) / (1.0 - r * r);
-                break;
-            }
-        }
-        double wk = 2.0 / ((1.0 - r * r) * dP * dP);
-        x[n - k] = r; x[k - 1] = -r;
-        w[n - k] = wk; w[k - 1] = wk;
-    }
-    if (n & 1) x[n / 2] = 0.0;
 }
 
 }  // namespace
@@ -1013,8 +986,8 @@ static void noalloc_params(const vx_config *cfg, vx::Launch &L, NoallocTab &T) {
     for (int i = 0; i < N; ++i)
         for (int j = i; j < N; ++j) { C.pij[p] = (uint16_t)((i << 8) | j); T.pij[p] = C.pij[p]; ++p; }
     double tm[VX_MAX_MU], wm[VX_MAX_MU], tk[VX_MAX_NE], wk[VX_MAX_NE];
-    gl_fixed(nmu, tm, wm);
-    gl_fixed(ne, tk, wk);
+    gauss_legendre(nmu, tm, wm);
+    gauss_legendre(ne, tk, wk);
     for (int m = 0; m < nmu; ++m) {
         C.t64[m] = tm[m];
         C.t_hi[m] = (float)tm[m];
@@ -1056,15 +1029,8 @@ vx_status vx_rates_eval_noalloc(const vx_config *cfg, const vx_batch *b, const v
                     cfg->n_bins, cfg->n_mu, (size_t)VX_NOALLOC_SCRATCH_BYTES, VX_NOALLOC_MAX_BINS, VX_NOALLOC_MAX_MU);
     if (!b) return fail(VX_ERR_INVALID_ARG, "batch is NULL");
     if (b->n_zones < 0 || b->n_rays < 0) return fail(VX_ERR_INVALID_ARG, "negative batch size");
-    if (b->ray_offsets) {
-        if (b->ray_offsets[0] != 0) return fail(VX_ERR_INVALID_ARG, "ray_offsets[0] must be 0");
-        for (int r = 0; r < b->n_rays; ++r)
-            if (b->ray_offsets[r + 1] < b->ray_offsets[r])
-                return fail(VX_ERR_INVALID_ARG, "ray_offsets must be non-decreasing (ray %d)", r);
-        if ((long long)b->ray_offsets[b->n_rays] != b->n_zones)
-            return fail(VX_ERR_INVALID_ARG, "ray_offsets[n_rays] does not equal n_zones");
-    }
     if (b->n_zones == 0) return VX_OK;
+    if (b->ray_offsets && (st = check_device_ptr(b->ray_offsets, "ray_offsets", 4)) != VX_OK) return st;
     if ((st = check_device_ptr(b->state, "state")) != VX_OK) return st;
     if ((st = check_device_ptr(b->J, "J")) != VX_OK) return st;
     if ((st = check_device_ptr(b->H, "H")) != VX_OK) return st;

@@ -68,20 +68,43 @@ class PairRates:
         """Kernel entries per zone and l: N^2."""
         return capi.vx_rates_entries_per_zone(self._h)
 
-    def _batch(self, state, J, H, ray_offsets):
+    def _batch(self, state, J, H, ray_offsets, stream=None):
         Z = state.shape[0]
         for name, t, shape in (("state", state, (Z, 4)), ("J", J, (Z, self.S, self.N)), ("H", H, (Z, self.S, self.N))):
             if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous() or tuple(t.shape) != shape:
                 raise ValueError(f"{name} must be a contiguous CUDA float64 tensor of shape {shape}")
+            if t.device != self.device:
+                raise ValueError(f"{name} is on {t.device}, the handle on {self.device}")
         offs = None
         nr = 1
         if ray_offsets is not None:
-            offs = np.ascontiguousarray(ray_offsets, dtype=np.int32)
-            nr = len(offs) - 1
-        b = capi.vx_batch(n_rays=nr, n_zones=Z, ray_offsets=None if offs is None else offs.ctypes.data_as(capi._ip),
+            if torch.is_tensor(ray_offsets) and ray_offsets.is_cuda:
+                # device offsets: the library checks the partition on the device (vx_rates_check)
+                if ray_offsets.dtype != torch.int32 or not ray_offsets.is_contiguous() or ray_offsets.dim() != 1:
+                    raise ValueError("ray_offsets must be a contiguous 1-D int32 tensor")
+                offs = ray_offsets
+            else:
+                h = np.ascontiguousarray(ray_offsets.cpu().numpy() if torch.is_tensor(ray_offsets) else ray_offsets,
+                                         dtype=np.int64)
+                if h.ndim != 1 or len(h) < 2 or h[0] != 0 or np.any(np.diff(h) < 0) or h[-1] != Z:
+                    raise ValueError(f"ray_offsets must start at 0, not decrease and end at {Z}")
+                offs = torch.from_numpy(h.astype(np.int32)).to(self.device, non_blocking=False)
+                if stream is not None:
+                    offs.record_stream(stream)
+            nr = offs.shape[0] - 1
+        b = capi.vx_batch(n_rays=nr, n_zones=Z, ray_offsets=None if offs is None else ctypes.cast(offs.data_ptr(), capi._ip),
                           state=state.data_ptr(), J=J.data_ptr(), H=H.data_ptr())
         b._keep = offs
         return b
+
+    def _check_out(self, name, t, shape, host=False):
+        """Caller-supplied output (or seed) tensor: float64, contiguous, the given shape, on the
+        handle's device (host=True: in host memory)."""
+        ok = (torch.is_tensor(t) and t.dtype == torch.float64 and t.is_contiguous() and tuple(t.shape) == tuple(shape)
+              and ((not t.is_cuda) if host else (t.is_cuda and t.device == self.device)))
+        if not ok:
+            where = "host" if host else f"{self.device}"
+            raise ValueError(f"{name} must be a contiguous float64 tensor of shape {tuple(shape)} on {where}")
 
     def _alloc(self, Z):
         return {k: torch.empty((Z, self.S, self.N), dtype=torch.float64, device=self.device) for k in _OUT_KEYS}
@@ -95,7 +118,12 @@ class PairRates:
         """Rates j0, chi0, j1, chi1 of every zone ([Z][S][N] float64); phi=True adds the raw kernel
         of term I, [Z][2 dir][2 l][N][N]."""
         Z = state.shape[0]
-        b = self._batch(state, J, H, ray_offsets)
+        b = self._batch(state, J, H, ray_offsets, stream)
+        if out is not None:
+            for k in _OUT_KEYS:
+                self._check_out(f"out[{k!r}]", out.get(k), (Z, self.S, self.N))
+            if phi and "phi" in out:
+                self._check_out("out['phi']", out["phi"], (Z, 2, 2, self.N, self.N))
         res = out if out is not None else self._alloc(Z)
         if phi and "phi" not in res:
             res["phi"] = torch.empty((Z, 2, 2, self.N, self.N), dtype=torch.float64, device=self.device)
@@ -109,7 +137,8 @@ class PairRates:
         vector-Jacobian product grad_state [Z][4] for grad_out (dict of [Z][S][N] tensors) and/or
         the forward rates."""
         Z = state.shape[0]
-        b = self._batch(state, J, H, ray_offsets)
+        b = self._batch(state, J, H, ray_offsets, stream)
+        self._check_seeds(grad_out, Z)
         res = {}
         if jacobian:
             res["jac"] = torch.empty((Z, self.S, self.N, 4, 3), dtype=torch.float64, device=self.device)
@@ -132,7 +161,8 @@ class PairRates:
         and/or, for grad_out (dict of [Z][S][N] tensors), grad_J and grad_H [Z][S][N] indexed by
         spectrum; forward=True adds the rates."""
         Z = state.shape[0]
-        b = self._batch(state, J, H, ray_offsets)
+        b = self._batch(state, J, H, ray_offsets, stream)
+        self._check_seeds(grad_out, Z)
         res = {}
         if blocks:
             res["blocks"] = torch.empty((Z, self.S, 4, self.N, self.N), dtype=torch.float64, device=self.device)
@@ -148,6 +178,15 @@ class PairRates:
         capi.vx_rates_spectral(self._h, b, g, _ptr(res.get("grad_J")), _ptr(res.get("grad_H")), _ptr(res.get("blocks")),
                                fwd, self._stream(stream))
         return res
+
+    def _check_seeds(self, grad_out, Z, host=False):
+        if grad_out is None:
+            return
+        for k, v in grad_out.items():
+            if k not in _OUT_KEYS:
+                raise ValueError(f"grad_out has an unknown key {k!r}")
+            if v is not None:
+                self._check_out(f"grad_out[{k!r}]", v, (Z, self.S, self.N), host=host)
 
     def jacobian(self, state, J, H, **kw):
         return self.adjoint(state, J, H, jacobian=True, **kw)["jac"]
@@ -172,6 +211,9 @@ class PairRates:
         return b, Z
 
     def _host_out(self, Z, out):
+        if out is not None:
+            for k in _OUT_KEYS:
+                self._check_out(f"out[{k!r}]", out.get(k), (Z, self.S, self.N), host=True)
         res = out if out is not None else {k: torch.empty((Z, self.S, self.N), dtype=torch.float64, pin_memory=True)
                                            for k in _OUT_KEYS}
         return res, capi.vx_out(*(res[k].data_ptr() for k in _OUT_KEYS), None)
@@ -190,6 +232,8 @@ class PairRates:
         """End-to-end forward rates and Jacobian on host arrays (vx_rates_adjoint_host)."""
         b, Z = self._host_batch(state, J, H, ray_offsets)
         res, o = self._host_out(Z, out) if forward else ({}, None)
+        if jac is not None:
+            self._check_out("jac", jac, (Z, self.S, self.N, 4, 3), host=True)
         res["jac"] = jac if jac is not None else torch.empty((Z, self.S, self.N, 4, 3), dtype=torch.float64,
                                                              pin_memory=True)
         with torch.cuda.device(self.device):

@@ -147,6 +147,24 @@ def test_argument_checks():
         capi.vx_btd_solve(sv.handle, 2, 5, off.data_ptr(), A.data_ptr(), None, C.data_ptr(), d.data_ptr(),
                           torch.empty_like(d).data_ptr())
     assert e.value.status == capi.VX_ERR_INVALID_ARG
+    # offsets in host memory (the rate calls' host-buffer convention): rejected before any launch
+    host_off = s["offsets"].astype(np.int32)
+    with pytest.raises(capi.VxError) as e:
+        capi.vx_btd_solve(sv.handle, 2, 5, host_off.ctypes.data, A.data_ptr(), B.data_ptr(), C.data_ptr(),
+                          d.data_ptr(), torch.empty_like(d).data_ptr())
+    assert e.value.status == capi.VX_ERR_INVALID_ARG and "ray_offsets must be device memory" in str(e.value)
+    host_x = np.zeros(d.shape)
+    with pytest.raises(capi.VxError) as e:  # a host output
+        capi.vx_btd_solve(sv.handle, 2, 5, off.data_ptr(), A.data_ptr(), B.data_ptr(), C.data_ptr(),
+                          d.data_ptr(), host_x.ctypes.data)
+    assert e.value.status == capi.VX_ERR_INVALID_ARG
+    # a caller-supplied solution tensor of the wrong shape, type or place: caught in Python
+    for bad in (torch.empty(4, 4, dtype=torch.float64, device="cuda"), torch.empty_like(d, dtype=torch.float32),
+                torch.empty(d.shape, dtype=torch.float64)):
+        with pytest.raises(ValueError):
+            sv.solve(off, A, B, C, d, out=bad)
+    torch.cuda.synchronize()
+    assert sv.check()
     sv.close()
 
 

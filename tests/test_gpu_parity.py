@@ -138,9 +138,20 @@ def test_host_argument_checks():
     b = vx_inputs.make_batch(1, rays=[0])
     rates = make(b, "mixed")
     st, J, H = dev(b["state"]), dev(b["J"]), dev(b["H"])
-    with pytest.raises(capi.VxError) as e:  # ray offsets that do not cover the zones
+    Z = st.shape[0]
+    with pytest.raises(ValueError):  # host offsets that do not cover the zones: caught before the C call
         rates.evaluate(st, J, H, ray_offsets=[0, 10, 20])
-    assert e.value.status == capi.VX_ERR_INVALID_ARG
+    import ctypes
+    host_offs = np.array([0, Z], np.int32)
+    bt = capi.vx_batch(n_rays=1, n_zones=Z, ray_offsets=host_offs.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                       state=st.data_ptr(), J=J.data_ptr(), H=H.data_ptr())
+    good = rates._alloc(Z)
+    o = capi.vx_out(*(good[k].data_ptr() for k in KEYS), None)
+    with pytest.raises(capi.VxError) as e:  # offsets in host memory: the device calls take device offsets
+        capi.vx_rates_eval(rates.handle, bt, o, 0)
+    assert e.value.status == capi.VX_ERR_INVALID_ARG and "ray_offsets" in str(e.value)
+    with pytest.raises(ValueError):  # a caller-supplied output of the wrong shape
+        rates.evaluate(st, J, H, out={k: torch.empty(3, dtype=torch.float64, device="cuda") for k in KEYS})
     bt = capi.vx_batch(n_rays=1, n_zones=st.shape[0], ray_offsets=None, state=st.data_ptr(), J=J.data_ptr(),
                        H=H.data_ptr())
     host = np.zeros(st.shape[0] * 3 * 17)
@@ -153,6 +164,32 @@ def test_host_argument_checks():
                    torch.empty((0, 3, 17), dtype=torch.float64, device="cuda"))
     assert rates.check()
     rates.close()
+
+
+def test_device_ray_offsets_validated_on_the_device():
+    """ray_offsets are device memory: a valid partition passes, an invalid one raises the device
+    flag (VX_ERR_NUMERIC) while every zone is still evaluated (the rates do not depend on rays)."""
+    from paper_1404_1719_gb300 import capi
+    b = vx_inputs.make_batch(1, rays=[0])
+    st, J, H = dev(b["state"]), dev(b["J"]), dev(b["H"])
+    Z = st.shape[0]
+    for graph in (False, True):
+        rates = make(b, "mixed", graph=graph)
+        ref = rates.evaluate(st, J, H)
+        ref = {k: v.clone() for k, v in ref.items()}
+        good = torch.tensor([0, 20, 20, Z], dtype=torch.int32, device="cuda")
+        out = rates.evaluate(st, J, H, ray_offsets=good)
+        assert rates.check()
+        for k in KEYS:
+            assert torch.equal(out[k], ref[k])
+        for bad in ([0, 30, 20, Z], [1, 20, 30, Z], [0, 20, 30, Z - 1]):
+            out = rates.evaluate(st, J, H, ray_offsets=torch.tensor(bad, dtype=torch.int32, device="cuda"))
+            status = capi.vx_rates_check(rates.handle, torch.cuda.current_stream().cuda_stream)
+            assert status == capi.VX_ERR_NUMERIC and "invalid ray offsets" in capi.vx_last_error()
+            for k in KEYS:
+                assert torch.equal(out[k], ref[k])
+        assert rates.check()
+        rates.close()
 
 
 def test_graph_replay_is_bitwise_deterministic():

@@ -38,14 +38,22 @@ def config(capi, b, keep):
                           g2=1.0, norm=1.0, eta_fp64=0.0, prec=capi.VX_PREC_MIXED, flags=0)
 
 
-def noalloc(capi, b, keep):
+def noalloc(capi, b, keep, free_bytes=None):
+    """One call; with free_bytes (a list) it also records the device's free memory just before and
+    just after the call (inputs and outputs are allocated beforehand)."""
     st, J, H = dev(b["state"]), dev(b["J"]), dev(b["H"])
     keep += [st, J, H]
     Z, S, N = J.shape
     out = {k: torch.full((Z, S, N), float("nan"), dtype=torch.float64, device="cuda") for k in KEYS}
     batch = capi.vx_batch(n_rays=1, n_zones=Z, ray_offsets=None, state=st.data_ptr(), J=J.data_ptr(), H=H.data_ptr())
     o = capi.vx_out(*(out[k].data_ptr() for k in KEYS), None)
-    capi.vx_rates_eval_noalloc(config(capi, b, keep), batch, o, torch.cuda.current_stream().cuda_stream)
+    cfg = config(capi, b, keep)
+    torch.cuda.synchronize()
+    before = torch.cuda.mem_get_info()[0]
+    capi.vx_rates_eval_noalloc(cfg, batch, o, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    if free_bytes is not None:
+        free_bytes.append((before, torch.cuda.mem_get_info()[0]))
     return out
 
 
@@ -62,15 +70,17 @@ def with_handle(b):
 def test_noalloc_matches_handle_on_consecutive_calls():
     from paper_1404_1719_gb300 import capi
     keep = []
-    # two calls in a row with different grids and quadratures: the second rebuilds the shared table
-    for b in (vx_inputs.make_batch(2), vx_inputs.make_batch(1), vx_inputs.make_batch(5, rays=[7])):
-        got = noalloc(capi, b, keep)
-        torch.cuda.synchronize()
+    # calls in a row with different grids and quadratures: each rebuilds the shared table. After
+    # the first (which also loads the kernels), a call leaves the device's free memory unchanged.
+    free = []
+    for n, b in enumerate((vx_inputs.make_batch(2), vx_inputs.make_batch(1), vx_inputs.make_batch(5, rays=[7]))):
+        got = noalloc(capi, b, keep, free if n else None)
         ref = with_handle(b)
         for k in KEYS:
             g = got[k].cpu().numpy()
             assert np.all(np.isfinite(g)), k
             assert worst(g, ref[k]) <= 1e-5, k
+    assert free and all(a == b for a, b in free), free
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
