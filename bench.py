@@ -54,12 +54,33 @@ SPECTRAL_RAYS = 1024
 
 
 def algorithmic_flops_per_node(adj: bool) -> int:
-    """FP32 operations the method needs per (zone, unordered bin pair, omega, E) node in the
-    formulation the kernel evaluates (nodes in mirror pairs tau, -tau; tangents from r^2),
-    counting an FMA as 2 and an exp, reciprocal, add or multiply as 1: forward 14; with tangents
-    41, since the blocking factor's three moments then follow per (pair, omega) from the energy
-    tangents' (forward 8 per node + tangents 33)."""
+    """Algorithmic FP32 operations per (zone, unordered bin pair, omega, E) node of the quadrature,
+    counting an FMA as 2 and an exp, reciprocal, add or multiply as 1 (the count of the method,
+    independent of how the kernel formulates it): the node's energy (1 FMA), the two Fermi-Dirac
+    arguments (2 FMA), two exponentials and one reciprocal, the blocking product (2 FMA), the two
+    quadratic kinematic factors (4 FMA) and the accumulation (2 FMA): 22 forward; the tangents
+    add about 6 FMA per node (12), 34 in all. Only unordered bin pairs are integrated, since the
+    exchange symmetry K_II(i, j) = K_I(j, i) is exact."""
+    return 34 if adj else 22
+
+
+def formulation_flops_per_node(adj: bool) -> int:
+    """FP32 operations per node in the formulation the kernel evaluates (nodes in mirror pairs
+    tau, -tau; tangents from r^2), same counting: forward 14; with tangents 41, since the blocking
+    factor's three moments then follow per (pair, omega) from the energy tangents' (forward 8 per
+    node + tangents 33)."""
     return 41 if adj else 14
+
+
+# Pipe utilisation of the benchmark's kernels from one ncu capture each (see profiles/; set to
+# None whenever the kernel changes, until it has been captured again): the MUFU (XU) issue
+# fraction of the forward + tangent kernel and the FP64-pipe fraction of the plain FP64 kernel.
+MUFU_FRAC_TANGENT = None
+FP64_FRAC_FP64FWD = None
+# fraction of the workload's zones the plain FP64 comparison leg evaluates, and its timed launches
+FP64_SAMPLE_FRAC, FP64_REPEATS = 0.05, 3
+# timed launches of the precise-mode leg (after two untimed ones)
+PRECISE_REPEATS = 3
 
 
 def rank_batch(rank: int, rays=None, workload: int = WORKLOAD) -> dict:
@@ -438,8 +459,12 @@ def run_ours(args):
         npair = N * (N + 1) // 2
         nodes = Z * npair * b["n_mu"] * b["n_e"]
         achieved = nodes * algorithmic_flops_per_node(not fwd_only) / (ms_local / 1000) / 1e12
-        # FP64 forward-only comparison on a sample of the same workload
-        sub = min(48 * 400, Z)
+        achieved_form = nodes * formulation_flops_per_node(not fwd_only) / (ms_local / 1000) / 1e12
+        # measured pipe rates of this GPU (per SM per clock), for the probe-based peaks
+        pipes = capi.vx_probe_pipes(stream.cuda_stream)
+        peak_probe = pipes["ffma2"] * 2 * nsm * mhz * 1e6 / 1e12
+        # FP64 forward-only comparison on a sample of the same workload, timed over repeated launches
+        sub = min(max(1, int(round(FP64_SAMPLE_FRAC * Z))), Z)
         r64 = PairRates(b["eps"], b["n_mu"], b["n_e"], species=b["species"], precision="fp64")
         o64 = {k: torch.empty((sub, S, N), dtype=torch.float64, device=dev) for k in out}
         args64 = (d["state"][:sub], d["J"][:sub], d["H"][:sub])
@@ -447,11 +472,45 @@ def run_ours(args):
         torch.cuda.synchronize()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         f0.record(stream)
-        r64.evaluate(*args64, out=o64)
+        for _ in range(FP64_REPEATS):
+            r64.evaluate(*args64, out=o64)
         f1.record(stream)
         torch.cuda.synchronize()
-        v64 = entries(sub, N) / (f0.elapsed_time(f1) / 1000)
+        ms64 = f0.elapsed_time(f1) / FP64_REPEATS
+        v64 = entries(sub, N) / (ms64 / 1000)
+        nodes64 = sub * npair * b["n_mu"] * b["n_e"]
+        peak64 = pipes["dfma"] * 2 * nsm * mhz * 1e6 / 1e12
+        ach64 = nodes64 * algorithmic_flops_per_node(False) / (ms64 / 1000) / 1e12
         r64.close()
+        # the same step in the precise mode (VX_PRECISE), a few timed launches: its cost
+        precise = None
+        if not spec and not split:
+            rp = PairRates(b["eps"], b["n_mu"], b["n_e"], species=b["species"], graph=True, autotune=True,
+                           precise=True)
+            btp = rp._batch(d["state"], d["J"], d["H"], b["ray_offsets"])
+
+            def step_p():
+                if fwd_only:
+                    capi.vx_rates_eval(rp.handle, btp, fwd, stream.cuda_stream)
+                else:
+                    capi.vx_rates_adjoint(rp.handle, btp, None, jac.data_ptr(), None, fwd, stream.cuda_stream)
+
+            for _ in range(2):
+                step_p()
+            torch.cuda.synchronize()
+            p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            p0.record(stream)
+            for _ in range(PRECISE_REPEATS):
+                step_p()
+            p1.record(stream)
+            torch.cuda.synchronize()
+            msp = p0.elapsed_time(p1) / PRECISE_REPEATS
+            precise = {"value": entries(Z, N) / (msp / 1000), "unit": UNIT, "ms_per_step": msp,
+                       "time_vs_default": msp / ms_local, "numeric_ok": bool(rp.check()),
+                       "what": "VX_PRECISE: exact electron arguments in every zone, double-float l = 1 and "
+                               "eta-tangent sums; |g - o|/|o| <= 1e-5 wherever the sum cancels < 100x "
+                               "(tests/test_gpu_precision.py)"}
+            rp.close()
         tune = {}
         try:
             with open(tune_file) as f:
@@ -482,18 +541,39 @@ def run_ours(args):
             "gpu_launches": args.steps,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak,
+                         "frac_survey": achieved / peak,
+                         "frac_formulation": achieved_form / peak,
+                         "frac_of_probe_peak": achieved / peak_probe,
+                         "flop_per_node": {"algorithmic": algorithmic_flops_per_node(not fwd_only),
+                                           "formulation": formulation_flops_per_node(not fwd_only)},
+                         "nodes_per_step": nodes,
+                         "mufu_frac": MUFU_FRAC_TANGENT if (not fwd_only and not split) else None,
+                         "mufu_note": "ncu sm__inst_executed_pipe_xu.avg.pct_of_peak_sustained_active of the "
+                                      "forward + tangent kernel (profiles/)",
                          "traffic": (TRAFFIC_BYTES_PER_ZONE * Z if (TRAFFIC_BYTES_PER_ZONE and args.workload == WORKLOAD
                                                                     and not fwd_only and not split) else None),
                          "traffic_note": "ncu DRAM read+write of an 80,000-zone capture, scaled by zone count",
-                         "peak_note": f"FP32 {nsm} SMs x 128 FMA x 2 x {mhz:.0f} MHz (median SM clock in the run)",
+                         "peak_note": f"FP32 {nsm} SMs x 128 FMA x 2 x {mhz:.0f} MHz (median SM clock in the run); "
+                                      f"probe: {pipes['ffma2']:.1f} FP32 lanes/clk/SM with packed FMAs = "
+                                      f"{peak_probe:.1f} TFLOP/s at the same clock",
                          "kernel": f"k_pair_mixed<{b['n_e']}, {kind}, "
                                    f"{128 if minb == 2 else (80 if fwd_only else 96)}-register budget>"},
             "autotune": tune,
             **({"hbm": {"algorithmic_bytes_per_step": h2d + d2h,
                         "achieved_gbs": (h2d + d2h) / (ms_local / 1000) / 1e9,
                         "note": "inputs read + rates, blocks and J/H gradients written, per step"}} if spec else {}),
-            "fp64_fwd": {"value": v64, "unit": UNIT, "sample": f"first {sub} zones, plain FP64 forward only",
-                         "ratio_mixed_fwd_adj_over_fp64_fwd": value / world / v64},
+            "fp64_fwd": {"value": v64, "unit": UNIT, "ms_per_launch": ms64, "launches_timed": FP64_REPEATS,
+                         "sample": f"first {sub} zones ({100 * sub / Z:.1f} % of the workload), plain FP64 forward only",
+                         "ratio_mixed_fwd_adj_over_fp64_fwd": value / world / v64,
+                         "roofline": {"bound": "alu", "achieved": ach64, "peak": peak64, "unit": "TFLOP/s",
+                                      "frac": ach64 / peak64,
+                                      "peak_note": f"FP64 {nsm} SMs x {pipes['dfma']:.2f} DFMA/clk (probe) x 2 x "
+                                                   f"{mhz:.0f} MHz",
+                                      "fp64_frac": FP64_FRAC_FP64FWD,
+                                      "fp64_note": "ncu sm__pipe_fp64_cycles_active.avg.pct_of_peak_sustained_active "
+                                                   "of k_pair_fp64 (profiles/)"}},
+            "pipes": pipes,
+            "precise_mode": precise,
             "clocks": c,
             "numeric_ok": bool(ok),
         }

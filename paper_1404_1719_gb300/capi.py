@@ -14,7 +14,7 @@ from . import _build
 VX_OK, VX_ERR_INVALID_ARG, VX_ERR_CUDA, VX_ERR_OOM, VX_ERR_NUMERIC, VX_ERR_UNSUPPORTED, VX_ERR_TIMEOUT = range(7)
 VX_PREC_FP64, VX_PREC_MIXED = 0, 1
 VX_NU_E, VX_NU_EBAR, VX_NU_X = 0, 1, 2
-VX_USE_GRAPH, VX_AUTOTUNE, VX_QUAD_SPLIT = 1, 2, 4
+VX_USE_GRAPH, VX_AUTOTUNE, VX_QUAD_SPLIT, VX_PRECISE = 1, 2, 4, 8
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int)
@@ -37,6 +37,12 @@ class vx_out(ctypes.Structure):
                 ("chi1", ctypes.c_void_p), ("phi", ctypes.c_void_p)]
 
 
+class vx_pipe_rates(ctypes.Structure):
+    _fields_ = [("ffma", ctypes.c_double), ("ffma2", ctypes.c_double), ("dfma", ctypes.c_double),
+                ("ex2", ctypes.c_double), ("rcp", ctypes.c_double), ("sm_mhz", ctypes.c_double),
+                ("n_sm", ctypes.c_int)]
+
+
 class VxError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
@@ -46,7 +52,8 @@ class VxError(RuntimeError):
 SYMBOLS = ("vx_rates_create", "vx_rates_eval", "vx_rates_adjoint", "vx_rates_check",
            "vx_rates_entries_per_zone", "vx_rates_destroy", "vx_status_string", "vx_last_error",
            "vx_rates_eval_noalloc", "vx_rates_spectral", "vx_rates_eval_host", "vx_rates_adjoint_host",
-           "vx_rates_spectral_host", "vx_btd_create", "vx_btd_solve", "vx_btd_check", "vx_btd_destroy")
+           "vx_rates_spectral_host", "vx_btd_create", "vx_btd_solve", "vx_btd_check", "vx_btd_destroy",
+           "vx_probe_pipes")
 
 _lib = None
 
@@ -100,6 +107,8 @@ def lib(path: str | None = None):
     L.vx_btd_check.restype = ctypes.c_int
     L.vx_btd_destroy.argtypes = [ctypes.c_void_p]
     L.vx_btd_destroy.restype = None
+    L.vx_probe_pipes.argtypes = [ctypes.POINTER(vx_pipe_rates), ctypes.c_void_p]
+    L.vx_probe_pipes.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -213,3 +222,10 @@ def vx_btd_check(h, stream: int = 0) -> int:
 
 def vx_btd_destroy(h) -> None:
     lib().vx_btd_destroy(h)
+
+
+def vx_probe_pipes(stream: int = 0) -> dict:
+    """Measured pipe rates of the current device (per SM per clock; include/vx_probe.h)."""
+    r = vx_pipe_rates()
+    _check(lib().vx_probe_pipes(ctypes.byref(r), ctypes.c_void_p(stream)), "vx_probe_pipes")
+    return {k: getattr(r, k) for k, _ in vx_pipe_rates._fields_}

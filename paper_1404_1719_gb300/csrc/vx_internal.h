@@ -64,6 +64,7 @@ struct Common {
     double g2, norm, eta_sw;
     double h_max, q0h_max;         // max half-width |q|/2 and max q0/2 over the pair table
     int split;                     // split discrete rule (VX_QUAD_SPLIT)
+    int precise;                   // precise mode (VX_PRECISE)
 };
 
 // One launch: the handle constants plus the batch.
@@ -116,19 +117,21 @@ __device__ inline void validate_offsets(const int *off, int n_rays, long long Z,
 //                   eta), l = 0, 1 of Phi_I(i,j) (term II is the transpose)
 //   vec[4][S][N]  : contraction vectors per output (j0, chi0, j1, chi1) and species
 //   sc, em, shv [N] (double): per-bin FP64 factors;  red[64] (double): block reduction
-//   part[2][q][4][block]: partial projections of bin pairs split between two threads
-__host__ __device__ inline size_t smem_mixed_bytes(int N, int S, bool adj, int block) {
+//   part[2][q][4 or 8][block]: partial projections of bin pairs split between two threads (the
+//                   precise mode keeps the low parts of its double-float sums as well)
+__host__ __device__ inline size_t smem_mixed_bytes(int N, int S, bool adj, int block, bool prec = false) {
     size_t nq = adj ? 4 : 1;
     size_t f = nq * 2 * (size_t)N * N + 4 * (size_t)S * N;
     f = (f + 1) & ~(size_t)1;
-    return f * 4 + 3 * (size_t)N * 8 + 64 * 8 + (size_t)block * 2 * nq * 4 * 4;
+    return f * 4 + 3 * (size_t)N * 8 + 64 * 8 + (size_t)block * 2 * nq * (prec ? 8 : 4) * 4;
 }
 size_t smem_fp64(const Common &c);
 
-// Kernel launchers (return the launch error). n_e selects the unrolled instantiation and split the
-// instantiations with the split rule (launch_mixed reads it from L.c.split); the mixed
-// kernels exist with two register budgets (minb 2: 128 registers; 3: 80 forward, 96 tangents).
-const void *kernel_mixed(bool adj, int minb, int n_e, bool split);
+// Kernel launchers (return the launch error). n_e selects the unrolled instantiation, split the
+// instantiations with the split rule and prec those of the precise mode (launch_mixed reads both
+// from L.c); the mixed kernels exist with two register budgets (minb 2: 128 registers; 3: 80
+// forward, 96 tangents).
+const void *kernel_mixed(bool adj, int minb, int n_e, bool split, bool prec);
 cudaError_t launch_mixed(bool adj, int minb, const Launch &L, int grid, int block, size_t smem, cudaStream_t s);
 cudaError_t launch_fp64_fwd(const Launch64 &L, int grid, int block, size_t smem, cudaStream_t s);
 const void *kernel_fp64_fwd(int n_e);
@@ -140,6 +143,10 @@ VX_DECL_MIXED(fwd_b2)
 VX_DECL_MIXED(fwd_b3)
 VX_DECL_MIXED(adj_b2)
 VX_DECL_MIXED(adj_b3)
+VX_DECL_MIXED(fwd_b2p)
+VX_DECL_MIXED(fwd_b3p)
+VX_DECL_MIXED(adj_b2p)
+VX_DECL_MIXED(adj_b3p)
 #undef VX_DECL_MIXED
 
 }  // namespace vx

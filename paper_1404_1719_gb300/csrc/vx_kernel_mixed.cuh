@@ -129,10 +129,27 @@ __device__ __forceinline__ double exp2neg(double y) {
 
 // Projections of one quantity (blocking factor or one of its tangents) onto l = 0, 1 for
 // coupling terms I and II.
+// In the precise mode (PREC) every projection is carried as an unevaluated FP32 pair hi + lo
+// (double-float): the l = 1 sums over cos(omega) cancel, and so do the eta-tangent sums.
 struct Proj {
     float o0I, o0II, o1I, o1II;
-    __device__ __forceinline__ void zero() { o0I = o0II = o1I = o1II = 0.f; }
+    float l0I, l0II, l1I, l1II;  // low parts (precise mode only)
+    __device__ __forceinline__ void zero() { o0I = o0II = o1I = o1II = 0.f; l0I = l0II = l1I = l1II = 0.f; }
 };
+
+// s + e = a + b exactly, s the rounded sum (Knuth's two-sum; no contraction, no reordering).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// hi + lo += t, with the rounding error of the high sum kept exactly.
+__device__ __forceinline__ void acc2(float &hi, float &lo, float t) {
+    float e;
+    two_sum(hi, t, hi, e);
+    lo = __fadd_rn(lo, e);
+}
 
 struct ZoneSh {
     double T, eta;
@@ -385,7 +402,10 @@ __device__ __forceinline__ void df_diff(float ah, float al, float bh, float bl, 
 // SPLIT: the kernel carries the split rule too; its degenerate loop then stays in chunks of 16
 // (unrolled whole beside the split loop it was slower: 16 x 48 eta <= 63 workload, 1758 vs
 // 1805 ms).
-template <int NE, bool ADJ, bool DEG, bool SPLIT>
+// PREC (precise mode): the packed mirror loop forms the electron argument exactly as the
+// degenerate path does (high part on the zone's grid, exact in FP32, remainder through a second
+// ex2), so the blocking factor's relative error no longer grows like |x| 2^-24 with the argument.
+template <int NE, bool ADJ, bool DEG, bool SPLIT, bool PREC>
 __device__ __forceinline__ void node_loop(const NodeSm *__restrict__ nd, const NodeMir *__restrict__ nm, int ne,
                                           float B, float Pe,
                                           float Pp, float Bq, float Bl, float Pq, float Pl, float h,
@@ -430,7 +450,7 @@ __device__ __forceinline__ void node_loop(const NodeSm *__restrict__ nd, const N
         if (ADJ) tang(q.a.z, q.a.w, q.b.x, e1, e2, t, r, fmaf(h, q.a.x, Em), fmaf(h, q.a.y, Em));
     };
     auto factors = [&](const NodeSm &q, float &e1, float &e2, float &t) {
-        if (!DEG) {
+        if (!DEG && !PREC) {
             e1 = ex2a(-fmaf(B, q.a.x, Pe));
             e2 = ex2a(-fmaf(B, q.a.y, Pp));
             t = 1.f + e1;
@@ -445,6 +465,8 @@ __device__ __forceinline__ void node_loop(const NodeSm *__restrict__ nd, const N
     if (MIRROR && VX_F32X2) {
         // packed form: lane x of every float2 is node tau, lane y its mirror -tau
         const float2 B2 = make_float2(B, B), Pe2 = make_float2(Pe, Pe), one2 = make_float2(1.f, 1.f);
+        const float2 Bq2 = make_float2(Bq, Bq), Bl2 = make_float2(Bl, Bl);
+        const float2 Pq2 = make_float2(Pq, Pq), Pl2 = make_float2(Pl, Pl);
         const float2 h2 = make_float2(h, h), Em2 = make_float2(Em, Em), mone2 = make_float2(-1.f, -1.f);
         const float2 z2 = make_float2(0.f, 0.f);
         float2 P2 = z2, M2 = z2, Z2 = z2;
@@ -456,10 +478,16 @@ __device__ __forceinline__ void node_loop(const NodeSm *__restrict__ nd, const N
                 const NodeMir q = nm[k0 + kk];
                 const float2 uv = make_float2(q.a.x, q.a.y), cpm = make_float2(q.a.z, q.a.w);
                 const float2 cmp = make_float2(q.b.x, q.b.y), c00 = make_float2(q.b.z, q.b.w);
-                const float2 x = __ffma2_rn(B2, uv, Pe2);
-                const float ea = ex2a(-x.x), eb = ex2a(-x.y);  // e1(tau), e1(-tau)
-                const float2 e = make_float2(ea, eb);
-                const float2 f = make_float2(eb * K, ea * K);  // e2(tau), e2(-tau)
+                float2 e;  // e1(tau), e1(-tau)
+                if (PREC) {
+                    const float2 sx = __ffma2_rn(Bq2, make_float2(q.c.x, q.c.y), Pq2);  // exact by the grid choice
+                    const float2 lo = __ffma2_rn(Bq2, make_float2(q.c.z, q.c.w), __ffma2_rn(Bl2, uv, Pl2));
+                    e = __fmul2_rn(make_float2(ex2a(-sx.x), ex2a(-sx.y)), make_float2(ex2a(-lo.x), ex2a(-lo.y)));
+                } else {
+                    const float2 x = __ffma2_rn(B2, uv, Pe2);
+                    e = make_float2(ex2a(-x.x), ex2a(-x.y));
+                }
+                const float2 f = make_float2(e.y * K, e.x * K);  // e2(tau), e2(-tau)
                 const float2 t = __fadd2_rn(e, one2);
                 const float2 d = __ffma2_rn(t, f, t);
                 float2 r;
@@ -576,40 +604,85 @@ __device__ __forceinline__ Coef make_coef(float kp, float km, float k0, float t)
 
 // Projection of one quantity's moments onto l = 0, 1 for terms I and II (term II of a pair uses
 // the coefficients with kp and km exchanged).
+// PREC: the l = 1 sums (and, for a quantity whose moments change sign -- SIGNED, the eta
+// tangent -- the l = 0 sums too) go into double-float accumulators; sums of non-negative terms
+// stay FP32, whose rounding is relative to the sum itself.
+template <bool PREC, bool SIGNED = false>
 __device__ __forceinline__ void project(Proj &P, const Mom &M, const Coef &c) {
-    P.o0I += fmaf(c.kp, M.p, fmaf(c.km, M.m, c.k0 * M.z));
-    P.o0II += fmaf(c.km, M.p, fmaf(c.kp, M.m, c.k0 * M.z));
-    P.o1I += fmaf(c.lp, M.p, fmaf(c.lm, M.m, c.l0 * M.z));
-    P.o1II += fmaf(c.lm, M.p, fmaf(c.lp, M.m, c.l0 * M.z));
+    const float a = fmaf(c.kp, M.p, fmaf(c.km, M.m, c.k0 * M.z));
+    const float b = fmaf(c.km, M.p, fmaf(c.kp, M.m, c.k0 * M.z));
+    const float d = fmaf(c.lp, M.p, fmaf(c.lm, M.m, c.l0 * M.z));
+    const float e = fmaf(c.lm, M.p, fmaf(c.lp, M.m, c.l0 * M.z));
+    if (PREC) {
+        if (SIGNED) { acc2(P.o0I, P.l0I, a); acc2(P.o0II, P.l0II, b); }
+        else { P.o0I += a; P.o0II += b; }
+        acc2(P.o1I, P.l1I, d); acc2(P.o1II, P.l1II, e);
+    } else {
+        P.o0I += a; P.o0II += b; P.o1I += d; P.o1II += e;
+    }
 }
 
 // Writes one pair's projections into the zone matrices [l][N][N]: term I of pair (i,j) is
 // Phi_I(i,j), term II is Phi_I(j,i).
+// (Precise mode: each double-float sum is rounded once, to nearest, on the way to FP32.)
+template <bool PREC>
 __device__ __forceinline__ void store_proj(float *q2, int N2, int N, int pi, int pj, const Proj &P) {
     float *M0 = q2, *M1 = q2 + N2;
     const int a = pi * N + pj, b = pj * N + pi;
-    M0[a] = P.o0I; M1[a] = P.o1I;
-    if (pi != pj) { M0[b] = P.o0II; M1[b] = P.o1II; }
+    M0[a] = PREC ? __fadd_rn(P.o0I, P.l0I) : P.o0I;
+    M1[a] = PREC ? __fadd_rn(P.o1I, P.l1I) : P.o1I;
+    if (pi != pj) {
+        M0[b] = PREC ? __fadd_rn(P.o0II, P.l0II) : P.o0II;
+        M1[b] = PREC ? __fadd_rn(P.o1II, P.l1II) : P.o1II;
+    }
 }
 
-// Partial projections of bin pairs split between threads: part[slot q][4][TB] floats, thread
-// index fastest, so a warp's stores and loads fall in distinct banks.
+// Partial projections of bin pairs split between threads: part[slot q][4 or 8][TB] floats (the
+// precise mode adds the four low parts), thread index fastest, so a warp's stores and loads fall
+// in distinct banks.
+template <bool PREC>
 __device__ __forceinline__ void part_put(float *part, int TB, int t, int sq, const Proj &P) {
-    float *b = part + (size_t)sq * 4 * TB + t;
+    float *b = part + (size_t)sq * (PREC ? 8 : 4) * TB + t;
     b[0] = P.o0I; b[TB] = P.o0II; b[2 * TB] = P.o1I; b[3 * TB] = P.o1II;
+    if (PREC) { b[4 * TB] = P.l0I; b[5 * TB] = P.l0II; b[6 * TB] = P.l1I; b[7 * TB] = P.l1II; }
 }
+template <bool PREC>
 __device__ __forceinline__ Proj part_get(const float *part, int TB, int t, int sq) {
-    const float *b = part + (size_t)sq * 4 * TB + t;
+    const float *b = part + (size_t)sq * (PREC ? 8 : 4) * TB + t;
     Proj P;
     P.o0I = b[0]; P.o0II = b[TB]; P.o1I = b[2 * TB]; P.o1II = b[3 * TB];
+    if (PREC) { P.l0I = b[4 * TB]; P.l0II = b[5 * TB]; P.l1I = b[6 * TB]; P.l1II = b[7 * TB]; }
+    else { P.l0I = P.l0II = P.l1I = P.l1II = 0.f; }
     return P;
+}
+
+// One contraction term pair of the precise mode: (bI a + bII b) v added to hi + lo, with both
+// products and the sum carried exactly to FP32-pair precision (two-product by FMA, two-sum).
+__device__ __forceinline__ void contract2(float &hi, float &lo, float bI, float a, float bII, float b, float v) {
+    const float p1 = __fmul_rn(bI, a), e1 = fmaf(bI, a, -p1);
+    const float p2 = __fmul_rn(bII, b), e2 = fmaf(bII, b, -p2);
+    float kh, kl;
+    two_sum(p1, p2, kh, kl);
+    kl = __fadd_rn(kl, __fadd_rn(e1, e2));
+    const float th = __fmul_rn(kh, v), tl = fmaf(kh, v, -th);
+    acc2(hi, lo, th);
+    lo = fmaf(kl, v, __fadd_rn(lo, tl));
+}
+
+// bI a + bII b of the precise mode as an FP64 value (exact products, two-sum of the FP32 pair).
+__device__ __forceinline__ double kern2(float bI, float a, float bII, float b) {
+    const float p1 = __fmul_rn(bI, a), e1 = fmaf(bI, a, -p1);
+    const float p2 = __fmul_rn(bII, b), e2 = fmaf(bII, b, -p2);
+    float kh, kl;
+    two_sum(p1, p2, kh, kl);
+    return (double)kh + ((double)kl + ((double)e1 + (double)e2));
 }
 
 // MINB selects one of two register budgets (2: up to 128 registers; 3: up to 80 for the forward
 // kernel, 96 for the tangent kernel); both are compiled and the autotuner picks per kernel kind
 // and quadrature. SPLIT compiles the split rule in (separate instantiations, so that the standard
 // form's register allocation is not shaped by it).
-template <int NE, bool ADJ, int MINB, bool SPLIT>
+template <int NE, bool ADJ, int MINB, bool SPLIT, bool PREC>
 __global__ void __launch_bounds__(MINB == 3 ? (ADJ ? VX_LB3_THREADS_ADJ : VX_TPB_MIXED) : VX_TPB_MIXED,
                                   MINB == 3 ? (ADJ ? VX_LB3_CTAS_ADJ : 3) : MINB)
     k_pair_mixed(const __grid_constant__ Launch L) {
@@ -630,7 +703,7 @@ __global__ void __launch_bounds__(MINB == 3 ? (ADJ ? VX_LB3_THREADS_ADJ : VX_TPB
     double *em = sc + N;
     double *shv = em + N;  // exp(-(eps_j - eps_0)/T) 2^sv
     double *red = shv + N;  // 64 doubles for block reductions
-    float *part = reinterpret_cast<float *>(red + 64);  // [2 slots][nq][4][blockDim] partial projections
+    float *part = reinterpret_cast<float *>(red + 64);  // [2 slots][nq][4 or 8][blockDim] partial projections
     const int tid = threadIdx.x;
     for (int k = tid; k < C.n_e; k += blockDim.x) {
         s_nodes[k].a = make_float4(L.n32.u[k], L.n32.v[k], L.n32.cp[k], L.n32.cm[k]);
@@ -825,46 +898,45 @@ __global__ void __launch_bounds__(MINB == 3 ? (ADJ ? VX_LB3_THREADS_ADJ : VX_TPB
                     const float Qs = fmaf(2.f * (Em + h), il_h, zs.sc);
                     SplitUnit<ADJ, ADJ>::run(s_half, C.n_e / 2, rA, B, dls, Qs, h, Em, zs.c1, mo, ta, tp, et);
                     const Coef cf = make_coef(kp, km, k0, R1.w);
-                    project(PO, mo, cf);
+                    project<PREC>(PO, mo, cf);
                     if (ADJ) {
-                        project(PTa, ta, cf);
-                        project(PTp, tp, cf);
-                        project(PEt, et, cf);
-                    }
-                } else if (!deg) {
-                    const float Pe = fmaf(Em, il_h, -el_h);
-                    node_loop<NE, ADJ, false, SPLIT>(s_nodes, s_mir, C.n_e, B, Pe, Pp, 0.f, 0.f, 0.f, 0.f, h, Em, 1.f, zs.K, false, mo, ta, tp, et);
-                    const Coef cf = make_coef(kp, km, k0, R1.w);
-                    project(PO, mo, cf);
-                    if (ADJ) {
-                        project(PTa, ta, cf);
-                        project(PTp, tp, cf);
-                        project(PEt, et, cf);
+                        project<PREC>(PTa, ta, cf);
+                        project<PREC>(PTp, tp, cf);
+                        project<PREC, true>(PEt, et, cf);
                     }
                 } else {
-                    const float il_l = zs.il_l, el_l = zs.el_l;
-                    // B = h * log2e/T as a double-float, split onto the 2^-kb grid
-                    float bh = __fmul_rn(h, il_h);
-                    float bl = __fadd_rn(fmaf(h, il_h, -bh), __fadd_rn(__fmul_rn(h, il_l), __fmul_rn(h_lo, il_h)));
-                    float Bq = __fmul_rn(rintf(__fmul_rn(bh, zs.sB)), zs.iB);
-                    float Bl = __fadd_rn(__fsub_rn(bh, Bq), bl);
-                    // P = (E- log2e/T - |eta| log2e) as a double-float, split onto 2^-(kb+11)
-                    float ph = __fmul_rn(Em, il_h);
-                    float pl = __fadd_rn(fmaf(Em, il_h, -ph), __fadd_rn(__fmul_rn(Em, il_l), __fmul_rn(Em_lo, il_h)));
-                    float s = __fsub_rn(ph, el_h);
-                    float bb = __fsub_rn(s, ph);
-                    float err = __fadd_rn(__fsub_rn(ph, __fsub_rn(s, bb)), __fsub_rn(-el_h, bb));
-                    float slo = __fsub_rn(__fadd_rn(err, pl), el_l);
-                    float Pq = __fmul_rn(rintf(__fmul_rn(s, zs.sP)), zs.iP);
-                    float Pl = __fadd_rn(__fsub_rn(s, Pq), slo);
-                    Pq = __fadd_rn(Pq, zs.sc);  // exact: an integer on the same grid
-                    node_loop<NE, ADJ, true, SPLIT>(s_nodes, s_mir, C.n_e, B, 0.f, Pp, Bq, Bl, Pq, Pl, h, Em, zs.c1, 0.f, zs.r2ok, mo, ta, tp, et);
+                    // exact split of the electron argument (degenerate path; every zone in the
+                    // precise mode): B = h log2e/T and P = E- log2e/T - |eta| log2e as
+                    // double-floats, their high parts on the zone's 2^-kb and 2^-(kb+11) grids
+                    float Bq = 0.f, Bl = 0.f, Pq = 0.f, Pl = 0.f;
+                    if (deg || PREC) {
+                        const float il_l = zs.il_l, el_l = zs.el_l;
+                        float bh = __fmul_rn(h, il_h);
+                        float bl = __fadd_rn(fmaf(h, il_h, -bh), __fadd_rn(__fmul_rn(h, il_l), __fmul_rn(h_lo, il_h)));
+                        Bq = __fmul_rn(rintf(__fmul_rn(bh, zs.sB)), zs.iB);
+                        Bl = __fadd_rn(__fsub_rn(bh, Bq), bl);
+                        float ph = __fmul_rn(Em, il_h);
+                        float pl = __fadd_rn(fmaf(Em, il_h, -ph), __fadd_rn(__fmul_rn(Em, il_l), __fmul_rn(Em_lo, il_h)));
+                        float s = __fsub_rn(ph, el_h);
+                        float bb = __fsub_rn(s, ph);
+                        float err = __fadd_rn(__fsub_rn(ph, __fsub_rn(s, bb)), __fsub_rn(-el_h, bb));
+                        float slo = __fsub_rn(__fadd_rn(err, pl), el_l);
+                        Pq = __fmul_rn(rintf(__fmul_rn(s, zs.sP)), zs.iP);
+                        Pl = __fadd_rn(__fsub_rn(s, Pq), slo);
+                        Pq = __fadd_rn(Pq, zs.sc);  // exact: an integer on the same grid
+                    }
+                    if (!deg) {
+                        const float Pe = fmaf(Em, il_h, -el_h);
+                        node_loop<NE, ADJ, false, SPLIT, PREC>(s_nodes, s_mir, C.n_e, B, Pe, Pp, Bq, Bl, Pq, Pl, h, Em, 1.f, zs.K, false, mo, ta, tp, et);
+                    } else {
+                        node_loop<NE, ADJ, true, SPLIT, false>(s_nodes, s_mir, C.n_e, B, 0.f, Pp, Bq, Bl, Pq, Pl, h, Em, zs.c1, 0.f, zs.r2ok, mo, ta, tp, et);
+                    }
                     const Coef cf = make_coef(kp, km, k0, R1.w);
-                    project(PO, mo, cf);
+                    project<PREC>(PO, mo, cf);
                     if (ADJ) {
-                        project(PTa, ta, cf);
-                        project(PTp, tp, cf);
-                        project(PEt, et, cf);
+                        project<PREC>(PTa, ta, cf);
+                        project<PREC>(PTp, tp, cf);
+                        project<PREC, true>(PEt, et, cf);
                     }
                 }
             }
@@ -872,19 +944,19 @@ __global__ void __launch_bounds__(MINB == 3 ? (ADJ ? VX_LB3_THREADS_ADJ : VX_TPB
             if (m == nmu || u + 1 == u1) {  // end of a pair or of this thread's range: flush
                 if (mb == 0 && m == nmu) {  // the whole pair in this thread
                     const int pi = s_pij[p] >> 8, pj = s_pij[p] & 0xff;
-                    store_proj(mats + 0 * 2 * (size_t)N2, N2, N, pi, pj, PO);
+                    store_proj<PREC>(mats + 0 * 2 * (size_t)N2, N2, N, pi, pj, PO);
                     if (ADJ) {
-                        store_proj(mats + 1 * 2 * (size_t)N2, N2, N, pi, pj, PTa);
-                        store_proj(mats + 2 * 2 * (size_t)N2, N2, N, pi, pj, PTp);
-                        store_proj(mats + 3 * 2 * (size_t)N2, N2, N, pi, pj, PEt);
+                        store_proj<PREC>(mats + 1 * 2 * (size_t)N2, N2, N, pi, pj, PTa);
+                        store_proj<PREC>(mats + 2 * 2 * (size_t)N2, N2, N, pi, pj, PTp);
+                        store_proj<PREC>(mats + 3 * 2 * (size_t)N2, N2, N, pi, pj, PEt);
                     }
                 } else {
                     const int sq = (first ? 0 : 1) * nq;
-                    part_put(part, TB, tid, sq, PO);
+                    part_put<PREC>(part, TB, tid, sq, PO);
                     if (ADJ) {
-                        part_put(part, TB, tid, sq + 1, PTa);
-                        part_put(part, TB, tid, sq + 2, PTp);
-                        part_put(part, TB, tid, sq + 3, PEt);
+                        part_put<PREC>(part, TB, tid, sq + 1, PTa);
+                        part_put<PREC>(part, TB, tid, sq + 2, PTp);
+                        part_put<PREC>(part, TB, tid, sq + 3, PEt);
                     }
                 }
                 PO.zero();
@@ -908,13 +980,20 @@ __global__ void __launch_bounds__(MINB == 3 ? (ADJ ? VX_LB3_THREADS_ADJ : VX_TPB
                 acc.zero();
                 for (int t = ta; t <= tb; ++t) {
                     const int sl = (t == ta && ua > t * U / TB) ? 1 : 0;
-                    const Proj x = part_get(part, TB, t, sl * nq + q);
-                    acc.o0I += x.o0I;
-                    acc.o0II += x.o0II;
-                    acc.o1I += x.o1I;
-                    acc.o1II += x.o1II;
+                    const Proj x = part_get<PREC>(part, TB, t, sl * nq + q);
+                    if (PREC) {
+                        acc2(acc.o0I, acc.l0I, x.o0I); acc.l0I = __fadd_rn(acc.l0I, x.l0I);
+                        acc2(acc.o0II, acc.l0II, x.o0II); acc.l0II = __fadd_rn(acc.l0II, x.l0II);
+                        acc2(acc.o1I, acc.l1I, x.o1I); acc.l1I = __fadd_rn(acc.l1I, x.l1I);
+                        acc2(acc.o1II, acc.l1II, x.o1II); acc.l1II = __fadd_rn(acc.l1II, x.l1II);
+                    } else {
+                        acc.o0I += x.o0I;
+                        acc.o0II += x.o0II;
+                        acc.o1I += x.o1I;
+                        acc.o1II += x.o1II;
+                    }
                 }
-                store_proj(mats + (size_t)q * 2 * N2, N2, N, pi, pj, acc);
+                store_proj<PREC>(mats + (size_t)q * 2 * N2, N2, N, pi, pj, acc);
             }
         }
         __syncthreads();
@@ -941,9 +1020,15 @@ __global__ void __launch_bounds__(MINB == 3 ? (ADJ ? VX_LB3_THREADS_ADJ : VX_TPB
             for (int r = 0; r < nres; ++r) {
                 const int q = r == 0 ? 0 : r == 2 ? 3 : (prod ? 2 : 1);
                 const float *M = mats + (size_t)(q * 2 + l) * N2;
-                float acc = 0.f;
-                for (int j = 0; j < N; ++j) acc = fmaf(fmaf(bI, M[i * N + j], bII * M[j * N + i]), v[j], acc);
-                res[r] = (double)acc;
+                if (PREC && (l == 1 || q == 3)) {  // sums whose terms change sign
+                    float ah = 0.f, al = 0.f;
+                    for (int j = 0; j < N; ++j) contract2(ah, al, bI, M[i * N + j], bII, M[j * N + i], v[j]);
+                    res[r] = (double)ah + (double)al;
+                } else {
+                    float acc = 0.f;
+                    for (int j = 0; j < N; ++j) acc = fmaf(fmaf(bI, M[i * N + j], bII * M[j * N + i]), v[j], acc);
+                    res[r] = (double)acc;
+                }
             }
             const size_t oi = ((size_t)z * S + s) * N + i;
             const double fwd = cl * scal * res[0];
@@ -995,10 +1080,11 @@ __global__ void __launch_bounds__(MINB == 3 ? (ADJ ? VX_LB3_THREADS_ADJ : VX_TPB
             for (int e = tid; e < S * nb; e += blockDim.x) {
                 const int s = e / nb, o = (e / N2) & 3, i = (e / N) % N, j = e % N;
                 const float *M = mats + (size_t)(o >> 1) * N2;
-                const float k = fmaf(C.bI[s], M[i * N + j], C.bII[s] * M[j * N + i]);
+                const double k = PREC ? kern2(C.bI[s], M[i * N + j], C.bII[s], M[j * N + i])
+                                      : (double)fmaf(C.bI[s], M[i * N + j], C.bII[s] * M[j * N + i]);
                 double f = ((o >> 1) ? c1 : c0) * C.w[j];
                 if ((o & 1) == 0) f *= (o == 0 ? -sc[i] : sc[i]) * shv[j];
-                L.blocks[(size_t)z * S * nb + e] = f * (double)k;
+                L.blocks[(size_t)z * S * nb + e] = f * k;
             }
         }
         if (!ADJ && L.grad_J) {
@@ -1013,7 +1099,8 @@ __global__ void __launch_bounds__(MINB == 3 ? (ADJ ? VX_LB3_THREADS_ADJ : VX_TPB
                 const size_t row = ((size_t)z * S + s) * N;
                 double sa = 0.0, sp = 0.0;  // annihilation and production sums over the species' bins i
                 for (int i = 0; i < N; ++i) {
-                    const double k = (double)fmaf(bI, M[i * N + j], bII * M[j * N + i]);
+                    const double k = PREC ? kern2(bI, M[i * N + j], bII, M[j * N + i])
+                                          : (double)fmaf(bI, M[i * N + j], bII * M[j * N + i]);
                     if (ga) sa = fma(k, ga[row + i], sa);
                     if (gp) sp = fma(k, gp[row + i] * sc[i], sp);
                 }

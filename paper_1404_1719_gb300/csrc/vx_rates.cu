@@ -130,11 +130,19 @@ struct vx_rates {
 };
 
 namespace vx {
-const void *kernel_mixed(bool adj, int minb, int n_e, bool split) {
+const void *kernel_mixed(bool adj, int minb, int n_e, bool split, bool prec) {
+    if (prec) {
+        if (adj) return minb == 3 ? kernel_mixed_adj_b3p(n_e, split) : kernel_mixed_adj_b2p(n_e, split);
+        return minb == 3 ? kernel_mixed_fwd_b3p(n_e, split) : kernel_mixed_fwd_b2p(n_e, split);
+    }
     if (adj) return minb == 3 ? kernel_mixed_adj_b3(n_e, split) : kernel_mixed_adj_b2(n_e, split);
     return minb == 3 ? kernel_mixed_fwd_b3(n_e, split) : kernel_mixed_fwd_b2(n_e, split);
 }
 cudaError_t launch_mixed(bool adj, int minb, const Launch &L, int grid, int block, size_t smem, cudaStream_t s) {
+    if (L.c.precise) {
+        if (adj) return minb == 3 ? launch_mixed_adj_b3p(L, grid, block, smem, s) : launch_mixed_adj_b2p(L, grid, block, smem, s);
+        return minb == 3 ? launch_mixed_fwd_b3p(L, grid, block, smem, s) : launch_mixed_fwd_b2p(L, grid, block, smem, s);
+    }
     if (adj) return minb == 3 ? launch_mixed_adj_b3(L, grid, block, smem, s) : launch_mixed_adj_b2(L, grid, block, smem, s);
     return minb == 3 ? launch_mixed_fwd_b3(L, grid, block, smem, s) : launch_mixed_fwd_b2(L, grid, block, smem, s);
 }
@@ -193,7 +201,9 @@ static vx_status validate_config(const vx_config *c) {
     if (c->eta_fp64 > 40.0)  // keeps two paired denominators below the FP32 range
         return fail(VX_ERR_INVALID_ARG, "eta_fp64 must be <= 40");
     if (c->prec != VX_PREC_FP64 && c->prec != VX_PREC_MIXED) return fail(VX_ERR_INVALID_ARG, "unknown precision");
-    if (c->flags & ~(VX_USE_GRAPH | VX_AUTOTUNE | VX_QUAD_SPLIT)) return fail(VX_ERR_INVALID_ARG, "unknown flag bits");
+    if (c->flags & ~(VX_USE_GRAPH | VX_AUTOTUNE | VX_QUAD_SPLIT | VX_PRECISE)) return fail(VX_ERR_INVALID_ARG, "unknown flag bits");
+    if ((c->flags & VX_PRECISE) && c->prec != VX_PREC_MIXED)
+        return fail(VX_ERR_UNSUPPORTED, "VX_PRECISE is a mode of the mixed form");
     if ((c->flags & VX_QUAD_SPLIT) && (c->n_e % 2 != 0))
         return fail(VX_ERR_INVALID_ARG, "VX_QUAD_SPLIT needs an even n_e (got %d)", c->n_e);
     if ((c->flags & VX_QUAD_SPLIT) && c->prec != VX_PREC_MIXED)
@@ -266,6 +276,7 @@ vx_status vx_rates_create(const vx_config *cfg, vx_rates **out) {
         h->n32.ul[k] = (float)(u - uh);
     }
     C.split = (cfg->flags & VX_QUAD_SPLIT) ? 1 : 0;
+    C.precise = (cfg->flags & VX_PRECISE) ? 1 : 0;
     if (C.split) {
         std::vector<double> th, wh;
         gauss_legendre(ne / 2, th, wh);
@@ -338,17 +349,17 @@ vx_status vx_rates_create(const vx_config *cfg, vx_rates **out) {
     VX_CUC(cudaMemcpy(h->d_tab64, t64.data(), t64.size() * sizeof(double), cudaMemcpyHostToDevice));
     VX_CUC(cudaMemset(h->d_flag, 0, sizeof(int)));
 
-    h->smem_fwd = vx::smem_mixed_bytes(N, S, false, h->block_mixed);
-    h->smem_adj = vx::smem_mixed_bytes(N, S, true, h->block_mixed);
+    h->smem_fwd = vx::smem_mixed_bytes(N, S, false, h->block_mixed, C.precise != 0);
+    h->smem_adj = vx::smem_mixed_bytes(N, S, true, h->block_mixed, C.precise != 0);
     h->smem_64 = vx::smem_fp64(C);
     h->cc_major = prop.major;
     h->cc_minor = prop.minor;
     struct K { const void *fn; size_t smem; int *grid; int block; };
-    const bool sp = C.split != 0;
-    K ks[5] = {{vx::kernel_mixed(false, 2, ne, sp), h->smem_fwd, &h->grid_mixed[0][0], h->block_mixed},
-               {vx::kernel_mixed(false, 3, ne, sp), h->smem_fwd, &h->grid_mixed[0][1], h->block_mixed},
-               {vx::kernel_mixed(true, 2, ne, sp), h->smem_adj, &h->grid_mixed[1][0], h->block_mixed},
-               {vx::kernel_mixed(true, 3, ne, sp), h->smem_adj, &h->grid_mixed[1][1], h->block_mixed},
+    const bool sp = C.split != 0, pr = C.precise != 0;
+    K ks[5] = {{vx::kernel_mixed(false, 2, ne, sp, pr), h->smem_fwd, &h->grid_mixed[0][0], h->block_mixed},
+               {vx::kernel_mixed(false, 3, ne, sp, pr), h->smem_fwd, &h->grid_mixed[0][1], h->block_mixed},
+               {vx::kernel_mixed(true, 2, ne, sp, pr), h->smem_adj, &h->grid_mixed[1][0], h->block_mixed},
+               {vx::kernel_mixed(true, 3, ne, sp, pr), h->smem_adj, &h->grid_mixed[1][1], h->block_mixed},
                {vx::kernel_fp64_fwd(ne), h->smem_64, &h->grid_64, h->block}};
     for (K &k : ks) {
         // opt in to the dynamic size always: the 48 KB default bounds static + dynamic together
@@ -491,9 +502,9 @@ static void fill_launch(const vx_rates *h, const vx_batch *b, vx::Launch &L) {
 // by the real launch that follows.
 static std::string tune_key(const vx_rates *h, bool adj) {
     char k[160];
-    snprintf(k, sizeof k, "N=%d,n_mu=%d,n_e=%d,S=%d,kind=%s%s,sm=%d,cc=%d.%d", h->common.N, h->common.n_mu,
-             h->common.n_e, h->common.S, adj ? "tangents" : "forward", h->common.split ? "+split" : "", h->nsm,
-             h->cc_major, h->cc_minor);
+    snprintf(k, sizeof k, "N=%d,n_mu=%d,n_e=%d,S=%d,kind=%s%s%s,sm=%d,cc=%d.%d", h->common.N, h->common.n_mu,
+             h->common.n_e, h->common.S, adj ? "tangents" : "forward", h->common.split ? "+split" : "",
+             h->common.precise ? "+precise" : "", h->nsm, h->cc_major, h->cc_minor);
     return k;
 }
 
@@ -553,6 +564,7 @@ static vx_status autotune(vx_rates *h, bool adj, const vx::Launch &L, cudaStream
     if (sample < 8LL * h->grid_mixed[kind][1]) return VX_OK;  // too small to tell apart: keep the default
     vx::Launch Ls = L;
     Ls.Z = sample;
+    Ls.off = nullptr;  // the sample is a prefix of the zones, not a partition by rays
     const size_t smem = adj ? h->smem_adj : h->smem_fwd;
     cudaEvent_t e0, e1;
     VX_CU(cudaEventCreate(&e0));
@@ -601,7 +613,7 @@ vx_status vx_rates_eval(vx_rates *h, const vx_batch *b, const vx_out *out, vx_st
         if ((st = autotune(h, false, L, s)) != VX_OK) return st;
         const int mb = h->minb[0];
         int grid = (int)std::min<long long>(h->grid_mixed[0][mb - 2], b->n_zones);
-        if (graph) return launch_graph(h, 0, vx::kernel_mixed(false, mb, h->common.n_e, h->common.split != 0), &L, grid, h->block_mixed, h->smem_fwd, s);
+        if (graph) return launch_graph(h, 0, vx::kernel_mixed(false, mb, h->common.n_e, h->common.split != 0, h->common.precise != 0), &L, grid, h->block_mixed, h->smem_fwd, s);
         VX_CU(cudaMemsetAsync(h->d_counter, 0, sizeof(unsigned long long), s));
         VX_CU(vx::launch_mixed(false, mb, L, grid, h->block_mixed, h->smem_fwd, s));
     } else {
@@ -653,7 +665,7 @@ vx_status vx_rates_adjoint(vx_rates *h, const vx_batch *b, const vx_out *grad_ou
     const int mb = h->minb[1];
     int grid = (int)std::min<long long>(h->grid_mixed[1][mb - 2], b->n_zones);
     if (h->cfg.flags & VX_USE_GRAPH)
-        return launch_graph(h, 1, vx::kernel_mixed(true, mb, h->common.n_e, h->common.split != 0), &L, grid, h->block_mixed, h->smem_adj, s);
+        return launch_graph(h, 1, vx::kernel_mixed(true, mb, h->common.n_e, h->common.split != 0, h->common.precise != 0), &L, grid, h->block_mixed, h->smem_adj, s);
     VX_CU(cudaMemsetAsync(h->d_counter, 0, sizeof(unsigned long long), s));
     VX_CU(vx::launch_mixed(true, mb, L, grid, h->block_mixed, h->smem_adj, s));
     return VX_OK;
@@ -691,7 +703,7 @@ vx_status vx_rates_spectral(vx_rates *h, const vx_batch *b, const vx_out *grad_o
     const int mb = h->minb[0];
     int grid = (int)std::min<long long>(h->grid_mixed[0][mb - 2], b->n_zones);
     if (h->cfg.flags & VX_USE_GRAPH)
-        return launch_graph(h, 0, vx::kernel_mixed(false, mb, h->common.n_e, h->common.split != 0), &L, grid, h->block_mixed, h->smem_fwd, s);
+        return launch_graph(h, 0, vx::kernel_mixed(false, mb, h->common.n_e, h->common.split != 0, h->common.precise != 0), &L, grid, h->block_mixed, h->smem_fwd, s);
     VX_CU(cudaMemsetAsync(h->d_counter, 0, sizeof(unsigned long long), s));
     VX_CU(vx::launch_mixed(false, mb, L, grid, h->block_mixed, h->smem_fwd, s));
     return VX_OK;
@@ -1060,7 +1072,7 @@ vx_status vx_rates_eval_noalloc(const vx_config *cfg, const vx_batch *b, const v
     const int ne = cfg->n_e, minb = 2;
     const int block = std::min(round_up(L.c.npair * cfg->n_mu, 32), VX_BLOCK_MIXED);
     const size_t smem = vx::smem_mixed_bytes(cfg->n_bins, cfg->n_species, false, block);
-    const void *fn = vx::kernel_mixed(false, minb, ne, false);
+    const void *fn = vx::kernel_mixed(false, minb, ne, false, false);
     VX_CU(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int nsm = 0, occ = 0;
     VX_CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));

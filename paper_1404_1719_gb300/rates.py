@@ -25,11 +25,13 @@ def _ptr(t):
 
 class PairRates:
     """Handle of the pair-process rate library for one energy grid and quadrature (split=True:
-    the split discrete rule in electron energy, panels meeting at the Fermi edge)."""
+    the split discrete rule in electron energy, panels meeting at the Fermi edge; precise=True:
+    the precise mode, VX_PRECISE, for results whose sums cancel)."""
 
     def __init__(self, eps, n_mu: int, n_e: int, species=(0, 1, 2), weights=None, sin2w: float = 0.23,
                  g2: float = 1.0, norm: float = 1.0, eta_fp64: float = 0.0, precision: str = "mixed",
-                 graph: bool = False, autotune: bool = False, split: bool = False, device=None):
+                 graph: bool = False, autotune: bool = False, split: bool = False, precise: bool = False,
+                 device=None):
         self.eps = np.ascontiguousarray(eps, dtype=np.float64)
         self.weights = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64)
         self.species = np.ascontiguousarray(species, dtype=np.int32)
@@ -44,7 +46,7 @@ class PairRates:
             n_mu=self.n_mu, n_e=self.n_e, n_species=self.S, species=self.species.ctypes.data_as(capi._ip),
             sin2w=sin2w, g2=g2, norm=norm, eta_fp64=eta_fp64, prec=prec,
             flags=(capi.VX_USE_GRAPH if graph else 0) | (capi.VX_AUTOTUNE if autotune else 0)
-            | (capi.VX_QUAD_SPLIT if split else 0))
+            | (capi.VX_QUAD_SPLIT if split else 0) | (capi.VX_PRECISE if precise else 0))
         with torch.cuda.device(self.device):
             self._h = capi.vx_rates_create(cfg)
 

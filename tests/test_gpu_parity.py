@@ -233,10 +233,12 @@ def test_autotune_picks_a_variant_and_caches_it(tmp_path, monkeypatch):
     import json
     cache = tmp_path / "tune.json"
     monkeypatch.setenv("VX_AUTOTUNE_CACHE", str(cache))
-    b = vx_inputs.make_batch(3, rays=range(24))
+    b = vx_inputs.make_batch(3, rays=range(96))  # ~41k zones: more than the tuning sample
     st, J, H = dev(b["state"]), dev(b["J"]), dev(b["H"])
     r1 = make(b, "mixed", autotune=True)
-    o1 = r1.adjoint(st, J, H, jacobian=True, forward=True)
+    # with the batch's ray offsets: the tuning sample (a prefix of the zones) must not trip the
+    # device-side check of the offsets
+    o1 = r1.adjoint(st, J, H, jacobian=True, forward=True, ray_offsets=b["ray_offsets"])
     assert r1.check()
     data = json.loads(cache.read_text())
     (key, val), = data.items()
