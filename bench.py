@@ -75,8 +75,8 @@ def formulation_flops_per_node(adj: bool) -> int:
 # Pipe utilisation of the benchmark's kernels from one ncu capture each (see profiles/; set to
 # None whenever the kernel changes, until it has been captured again): the MUFU (XU) issue
 # fraction of the forward + tangent kernel and the FP64-pipe fraction of the plain FP64 kernel.
-MUFU_FRAC_TANGENT = None
-FP64_FRAC_FP64FWD = None
+MUFU_FRAC_TANGENT = 0.2418   # profiles/k_pair_mixed_tangents_and_k_pair_fp64_pipes_20rays.md
+FP64_FRAC_FP64FWD = 0.9154
 # fraction of the workload's zones the plain FP64 comparison leg evaluates, and its timed launches
 FP64_SAMPLE_FRAC, FP64_REPEATS = 0.05, 3
 # timed launches of the precise-mode leg (after two untimed ones)
