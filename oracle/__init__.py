@@ -11,6 +11,7 @@ stated in the header comment of ``vx_oracle.c``.
 from __future__ import annotations
 
 import ctypes
+import functools
 import os
 import subprocess
 
@@ -18,6 +19,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "vx_oracle.c")
+_SRC_NES = os.path.join(_HERE, "vx_nes_oracle.c")
 _SO = os.path.join(_HERE, "libvx_oracle.so")
 _lib = None
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -25,11 +27,13 @@ _ip = ctypes.POINTER(ctypes.c_int)
 
 
 def build(force: bool = False) -> str:
-    """Compile vx_oracle.c into libvx_oracle.so (gcc, -O2, OpenMP when available)."""
-    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(_SRC):
+    """Compile vx_oracle.c and vx_nes_oracle.c into libvx_oracle.so (gcc, -O2, OpenMP when
+    available)."""
+    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= max(os.path.getmtime(_SRC),
+                                                                            os.path.getmtime(_SRC_NES)):
         return _SO
     base = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-std=c11",
-            "-o", _SO + ".tmp", _SRC, "-lm"]
+            "-o", _SO + ".tmp", _SRC, _SRC_NES, "-lm"]
     try:
         subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
     except subprocess.CalledProcessError:
@@ -60,6 +64,19 @@ def _load():
                                  _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp,
                                  ctypes.c_int, ctypes.c_double, ctypes.c_int]
         lib.vxo_eval.restype = ctypes.c_int
+        lib.vxo_gauss_laguerre.argtypes = [ctypes.c_int, _dp, _dp]
+        lib.vxo_nes_nodes.argtypes = [ctypes.c_double] * 5 + [ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp]
+        lib.vxo_nes_nodes.restype = None
+        lib.vxo_nes_point.argtypes = [ctypes.c_double] * 5 + [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp,
+                                                              _dp, _dp, _dp]
+        lib.vxo_nes_point.restype = None
+        lib.vxo_nes_eval.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _ip,
+                                     ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_long,
+                                     _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp,
+                                     ctypes.c_int]
+        lib.vxo_nes_eval.restype = ctypes.c_int
+        lib.vxo_eos_eta.argtypes = [ctypes.c_long, _dp, _dp, _dp]
+        lib.vxo_eos_eta.restype = None
         _lib = lib
     return _lib
 
@@ -187,3 +204,89 @@ def spectral_vjp(dsrc, species, g_j0, g_chi0, g_j1, g_chi1):
         gH[:, pk[s], :] += np.einsum("zij,zi->zj", dsrc[:, s, 2], g_j1[:, s]) + \
             np.einsum("zij,zi->zj", dsrc[:, s, 3], g_chi1[:, s])
     return gJ, gH
+
+
+# ---- inelastic neutrino-electron scattering (vx_nes_oracle.c) --------------------------------
+
+def gauss_laguerre(n: int):
+    """Gauss-Laguerre nodes (ascending) and weights for the weight e^{-x} on [0, inf)."""
+    x, w = np.empty(n), np.empty(n)
+    if _load().vxo_gauss_laguerre(n, _p(x), _p(w)) != 0:
+        raise ValueError("bad node count")
+    return x, w
+
+
+@functools.lru_cache(maxsize=None)
+def _nes_rules(n_e):
+    if n_e % 3:
+        raise ValueError("n_e must be a multiple of 3 (three panels)")
+    n_p = n_e // 3
+    tg, wg = gauss_legendre(n_p)
+    xl, wl = gauss_laguerre(n_p)
+    return n_p, tg, wg, xl, wl
+
+
+def nes_nodes(eps, epsp, y, T, eta, n_e):
+    """Electron energies E and weights W (dE included) of the three-panel rule at one point."""
+    n_p, tg, wg, xl, wl = _nes_rules(n_e)
+    E, W = np.empty(3 * n_p), np.empty(3 * n_p)
+    _load().vxo_nes_nodes(float(eps), float(epsp), float(y), float(T), float(eta), n_p, _p(tg), _p(wg), _p(xl),
+                          _p(wl), _p(E), _p(W))
+    return E, W
+
+
+def nes_point(eps, epsp, y, T, eta, n_e, boltzmann=False, grad=False, mag=False):
+    """NES kernel R^dir_X(eps, eps', y) with G2 = 1: array [dir][X] (dir 0 = in, 1 = out; X 0 = I,
+    1 = II); grad=True adds dK [dir][X][(d/dT, d/deta)], mag=True the sums of |terms|."""
+    n_p, tg, wg, xl, wl = _nes_rules(n_e)
+    K, dK, Ka = np.empty(4), np.empty(8), np.empty(4)
+    _load().vxo_nes_point(float(eps), float(epsp), float(y), float(T), float(eta), int(boltzmann), n_p, _p(tg),
+                          _p(wg), _p(xl), _p(wl), _p(K), _p(dK) if grad else None, _p(Ka))
+    out = [K.reshape(2, 2)]
+    if grad:
+        out.append(dK.reshape(2, 2, 2))
+    if mag:
+        out.append(Ka.reshape(2, 2))
+    return out[0] if len(out) == 1 else tuple(out)
+
+
+def nes_evaluate(eps, n_mu, n_e, species, state, J, H, weights=None, sin2w=0.23, g2=1.0, norm=1.0, phi=False,
+                 jac=False, mag=False, threads=0) -> dict:
+    """NES rates j0 (in-scattering, J), chi0 (out-scattering, 1 - J), j1, chi1 (H) [Z][S][N] of every
+    zone, with the source df/dt = (1 - f)(j0 - mu j1) - f (chi0 + mu chi1); optionally the kernel dump
+    phi [Z][2 X][2 dir][2 l][N][N] (dir 0 = in, 1 = out), the Jacobian jac [Z][S][N][4][3]
+    (d/dT, d/deta, d/dY_e = 0) and, with mag=True, the sums of |terms| (j1_abs, chi1_abs, phi_abs,
+    jac_abs)."""
+    eps = _f64(eps)
+    state = _f64(state)
+    J, H = _f64(J), _f64(H)
+    species = np.ascontiguousarray(species, dtype=np.int32)
+    n, S, Z = len(eps), len(species), state.shape[0]
+    if J.shape != (Z, S, n) or H.shape != (Z, S, n) or state.shape != (Z, 4):
+        raise ValueError("shape mismatch")
+    out = {k: np.empty((Z, S, n)) for k in ("j0", "chi0", "j1", "chi1")}
+    out["phi"] = np.empty((Z, 2, 2, 2, n, n)) if phi else None
+    out["jac"] = np.empty((Z, S, n, 4, 3)) if jac else None
+    for k in ("j1_abs", "chi1_abs"):
+        out[k] = np.empty((Z, S, n)) if mag else None
+    out["phi_abs"] = np.empty((Z, 2, 2, 2, n, n)) if (mag and phi) else None
+    out["jac_abs"] = np.empty((Z, S, n, 4, 3)) if (mag and jac) else None
+    w = None if weights is None else _f64(weights)
+    used = _load().vxo_nes_eval(n, _p(eps), _p(w), n_mu, n_e, S, species.ctypes.data_as(_ip), sin2w, g2, norm, Z,
+                                _p(state), _p(J), _p(H), _p(out["j0"]), _p(out["chi0"]), _p(out["j1"]),
+                                _p(out["chi1"]), _p(out["phi"]), _p(out["jac"]), _p(out["j1_abs"]),
+                                _p(out["chi1_abs"]), _p(out["phi_abs"]), _p(out["jac_abs"]), int(threads))
+    if used < 0:
+        raise ValueError("oracle rejected the arguments")
+    out["threads"] = used
+    return out
+
+
+def eos_eta(state):
+    """eta_e of every zone from T, Y_e, rho (state [Z][4]) by the massless electron-gas closure, and
+    d eta / d(T, Y_e, rho) [Z][3]."""
+    state = _f64(state)
+    Z = state.shape[0]
+    eta, deta = np.empty(Z), np.empty((Z, 3))
+    _load().vxo_eos_eta(Z, _p(state), _p(eta), _p(deta))
+    return eta, deta
