@@ -222,6 +222,21 @@ def test_contraction_is_the_collision_integral():
                 assert abs(direct - moments) <= 1e-12 * (abs(gain) + abs(loss)), (species, i, mu, direct, moments)
 
 
+def test_discrete_kernel_obeys_detailed_balance_and_time_reversal_exactly():
+    """The zone's discrete kernel (down-scattering order integrated, the rest by symmetry):
+    Phi^in(i,j) = e^{-(eps_i - eps_j)/T} Phi^out(i,j) for every ordered pair (the oracle computes
+    the two blocking factors independently), and Phi^out(i,j) = Phi^in(j,i)."""
+    eps = np.array([2.0, 9.0, 30.0, 90.0, 200.0])
+    T, eta = 7.0, 4.0
+    st = np.array([[T, eta, 0.3, 1e12]])
+    J = np.full((1, 1, len(eps)), 0.3)
+    r = oracle.nes_evaluate(eps, 12, 48, np.array([0], np.int32), st, J, 0.5 * J, phi=True)
+    phi = r["phi"][0]  # [X][dir][l][i][j], dir 0 = in, 1 = out
+    X = np.exp(-(eps[:, None] - eps[None, :]) / T)
+    np.testing.assert_allclose(phi[:, 0], X[None, None] * phi[:, 1], rtol=1e-12, atol=0)
+    np.testing.assert_allclose(phi[:, 1], np.swapaxes(phi[:, 0], -1, -2), rtol=1e-12, atol=0)
+
+
 def test_eos_closure_against_fermi_integrals():
     """The net electron density of the massless gas at the returned eta, from a numerical Fermi
     integral, equals rho Y_e / m_u; the derivatives match central differences."""
