@@ -338,6 +338,150 @@ def run_solve(args):
     return 0
 
 
+NES_METRIC = "NES kernel entries/s (zone*eps*eps'*l), FP32 forward+Jacobian, % FP peak"
+NES_N_MU, NES_N_E = 16, 48
+
+
+def nes_oracle_rate(b, n_zones):
+    import oracle
+    oracle.build()
+    sl = slice(0, n_zones)
+    t0 = time.perf_counter()
+    out = oracle.nes_evaluate(b["eps"], NES_N_MU, NES_N_E, b["species"], b["state"][sl], b["J"][sl], b["H"][sl],
+                              jac=True)
+    dt = time.perf_counter() - t0
+    return entries(n_zones, len(b["eps"])) / dt, out["threads"], dt
+
+
+def run_nes(args):
+    """Inelastic neutrino-electron scattering: forward rates + Jacobian of every zone of workload 4's
+    4096 rays x 400 zones (21 bins), 16 cos(omega) nodes x 48 electron-energy nodes (three panels)."""
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        b = vx_inputs.make_batch(WORKLOAD, rays=[0])
+        _, thr, dt = nes_oracle_rate(b, 4)
+        n = int(min(len(b["state"]), max(4, 4 * 4.0 / max(dt, 1e-3))))
+        t = [nes_oracle_rate(b, n)[2] for _ in range(args.steps)]
+        ms = 1000 * float(np.mean(t))
+        value = entries(n, len(b["eps"])) / (ms / 1000)
+        print(json.dumps({"impl": "reference", "metric": NES_METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                          "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                          "config": {"workload": vx_inputs.WORKLOADS[WORKLOAD]["name"] + " NES forward+jacobian",
+                                     "zones_per_step": n, "quadrature": f"{NES_N_MU}x{NES_N_E}"},
+                          "cpu_baseline": {"value": value, "unit": UNIT, "cores": thr, "kind": "oracle",
+                                           "sample": f"first {n} zones of workload {WORKLOAD} per step"},
+                          "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+        return 0
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    from paper_1404_1719_gb300 import NesRates, _build, capi
+    _build.build()
+    b = rank_batch(rank, rays=None if args.rays is None else range(args.rays))
+    Z, N, S = b["state"].shape[0], len(b["eps"]), len(b["species"])
+    host = {k: torch.from_numpy(np.ascontiguousarray(b[k])).pin_memory() for k in ("state", "J", "H")}
+    d = {k: v.to(dev) for k, v in host.items()}
+    nes = NesRates(b["eps"], NES_N_MU, NES_N_E, species=b["species"])
+    stream = torch.cuda.current_stream()
+    out = {k: torch.empty((Z, S, N), dtype=torch.float64, device=dev) for k in ("j0", "chi0", "j1", "chi1")}
+    jac = torch.empty((Z, S, N, 4, 3), dtype=torch.float64, device=dev)
+    bt = nes._batch(d["state"], d["J"], d["H"], b["ray_offsets"])
+    fwd = capi.vx_out(*(out[k].data_ptr() for k in ("j0", "chi0", "j1", "chi1")), None)
+
+    def step():
+        capi.vx_nes_adjoint(nes.handle, bt, jac.data_ptr(), fwd, stream.cuda_stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    assert nes.check(), "numeric flag raised during warm-up"
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms_local = e0.elapsed_time(e1) / args.steps
+    ms = max_over_ranks(ms_local, world, dist, dev)
+    ok = nes.check()
+    # end to end through the public API: pinned host inputs in, rates and Jacobian back to pinned host
+    h_out = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in out.items()}
+    h_jac = torch.empty(jac.shape, dtype=jac.dtype, pin_memory=True)
+
+    def step_e2e():
+        for k in ("state", "J", "H"):
+            d[k].copy_(host[k], non_blocking=True)
+        res = nes.adjoint(d["state"], d["J"], d["H"], forward=True, ray_offsets=b["ray_offsets"])
+        for k in ("j0", "chi0", "j1", "chi1"):
+            h_out[k].copy_(res[k], non_blocking=True)
+        h_jac.copy_(res["jac"], non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+
+    step_e2e()
+    e2e_steps = max(1, min(3, args.steps))
+    t_e2e = time.perf_counter()
+    for _ in range(e2e_steps):
+        step_e2e()
+    ms_e2e = max_over_ranks(1000.0 * (time.perf_counter() - t_e2e) / e2e_steps, world, dist, dev)
+    h2d = sum(v.numel() * v.element_size() for v in host.values())
+    d2h = sum(v.numel() * v.element_size() for v in h_out.values()) + h_jac.numel() * h_jac.element_size()
+    if rank == 0:
+        c = clk.summary()
+        nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+        mhz = c["sm_mhz"] or 2070.0
+        peak = nsm * 128 * 2 * mhz * 1e6 / 1e12
+        nodes = Z * (N * (N + 1) // 2) * NES_N_MU * NES_N_E
+        achieved = nodes * algorithmic_flops_per_node(True) / (ms_local / 1000) / 1e12
+        value = job_rate(entries(Z, N), world, ms)
+        line = {
+            "metric": NES_METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": vx_inputs.WORKLOADS[WORKLOAD]["name"] + " NES forward+jacobian (mixed)"
+                                   + ("" if args.rays is None else f" [first {args.rays} rays]"),
+                       "zones": Z, "bins": N, "quadrature": f"{NES_N_MU}x{NES_N_E} (3 electron-energy panels)",
+                       "species": S, "l2": "inputs larger than L2 (J, H: %.2f GB)" % (2 * b["J"].nbytes / 1e9)},
+            "e2e": {"value": job_rate(entries(Z, N), world, ms_e2e), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e,
+                    "call": "NesRates.adjoint with the inputs copied in from and the outputs back to pinned host "
+                            "tensors every step"},
+            "gpu_launches": args.steps,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                         "flop_per_node": algorithmic_flops_per_node(True), "nodes_per_step": nodes,
+                         "traffic": None,
+                         "peak_note": f"FP32 {nsm} SMs x 128 FMA x 2 x {mhz:.0f} MHz (median SM clock in the run)",
+                         "kernel": f"k_nes<float, tangents, {NES_N_E // 3} nodes per panel>"},
+            "clocks": c, "numeric_ok": bool(ok),
+        }
+        if not args.no_cpu:
+            bb = vx_inputs.make_batch(WORKLOAD, rays=[0, 1])
+            _, thr, dt = nes_oracle_rate(bb, 8)
+            n = int(min(len(bb["state"]), max(8, 8 * 15.0 / max(dt, 1e-3))))
+            rate, thr, dt = nes_oracle_rate(bb, n)
+            line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": thr, "kind": "oracle",
+                                    "sample": f"first {n} zones of workload {WORKLOAD}, NES forward + Jacobian, "
+                                              f"FP64, {dt:.1f} s"}
+        print(json.dumps(line))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    nes.close()
+    return 0
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -596,10 +740,11 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU-baseline leg")
     ap.add_argument("--workload", type=int, default=WORKLOAD, choices=sorted(vx_inputs.WORKLOADS),
                     help="synthetic workload (default 4: 4096 rays x 400 zones)")
-    ap.add_argument("--mode", choices=["fwd+jac", "fwd", "spectral", "solve"], default="fwd+jac",
+    ap.add_argument("--mode", choices=["fwd+jac", "fwd", "spectral", "solve", "nes"], default="fwd+jac",
                     help="step = forward + Jacobian pass (default), forward rates only, forward + the "
-                         "derivatives with respect to the spectra (blocks and J/H VJP), or the per-ray "
-                         "block-tridiagonal Newton solve")
+                         "derivatives with respect to the spectra (blocks and J/H VJP), the per-ray "
+                         "block-tridiagonal Newton solve, or the inelastic neutrino-electron scattering "
+                         "kernel (forward + Jacobian)")
     ap.add_argument("--quad", choices=["standard", "split"], default="standard",
                     help="discrete rule in electron energy: standard, or split at the Fermi edge (VX_QUAD_SPLIT)")
     ap.add_argument("--rays", type=int, default=None,
@@ -607,6 +752,8 @@ def main():
     args = ap.parse_args()
     if args.mode == "solve":
         return run_solve(args)
+    if args.mode == "nes":
+        return run_nes(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

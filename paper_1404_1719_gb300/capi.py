@@ -53,7 +53,8 @@ SYMBOLS = ("vx_rates_create", "vx_rates_eval", "vx_rates_adjoint", "vx_rates_che
            "vx_rates_entries_per_zone", "vx_rates_destroy", "vx_status_string", "vx_last_error",
            "vx_rates_eval_noalloc", "vx_rates_spectral", "vx_rates_eval_host", "vx_rates_adjoint_host",
            "vx_rates_spectral_host", "vx_btd_create", "vx_btd_solve", "vx_btd_check", "vx_btd_destroy",
-           "vx_probe_pipes")
+           "vx_probe_pipes", "vx_nes_create", "vx_nes_eval", "vx_nes_adjoint", "vx_nes_check", "vx_nes_destroy",
+           "vx_eos_eta", "vx_eos_chain")
 
 _lib = None
 
@@ -109,6 +110,22 @@ def lib(path: str | None = None):
     L.vx_btd_destroy.restype = None
     L.vx_probe_pipes.argtypes = [ctypes.POINTER(vx_pipe_rates), ctypes.c_void_p]
     L.vx_probe_pipes.restype = ctypes.c_int
+    L.vx_nes_create.argtypes = [ctypes.POINTER(vx_config), ctypes.POINTER(ctypes.c_void_p)]
+    L.vx_nes_create.restype = ctypes.c_int
+    L.vx_nes_eval.argtypes = [ctypes.c_void_p, ctypes.POINTER(vx_batch), ctypes.POINTER(vx_out), ctypes.c_void_p]
+    L.vx_nes_eval.restype = ctypes.c_int
+    L.vx_nes_adjoint.argtypes = [ctypes.c_void_p, ctypes.POINTER(vx_batch), ctypes.c_void_p, ctypes.POINTER(vx_out),
+                                 ctypes.c_void_p]
+    L.vx_nes_adjoint.restype = ctypes.c_int
+    L.vx_nes_check.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    L.vx_nes_check.restype = ctypes.c_int
+    L.vx_nes_destroy.argtypes = [ctypes.c_void_p]
+    L.vx_nes_destroy.restype = None
+    L.vx_eos_eta.argtypes = [ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    L.vx_eos_eta.restype = ctypes.c_int
+    L.vx_eos_chain.argtypes = [ctypes.c_longlong, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                               ctypes.c_void_p]
+    L.vx_eos_chain.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -229,3 +246,41 @@ def vx_probe_pipes(stream: int = 0) -> dict:
     r = vx_pipe_rates()
     _check(lib().vx_probe_pipes(ctypes.byref(r), ctypes.c_void_p(stream)), "vx_probe_pipes")
     return {k: getattr(r, k) for k, _ in vx_pipe_rates._fields_}
+
+
+def vx_nes_create(cfg: vx_config) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(lib().vx_nes_create(ctypes.byref(cfg), ctypes.byref(h)), "vx_nes_create")
+    return h
+
+
+def vx_nes_eval(h, batch: vx_batch, out: vx_out, stream: int = 0) -> None:
+    _check(lib().vx_nes_eval(h, ctypes.byref(batch), ctypes.byref(out), ctypes.c_void_p(stream)), "vx_nes_eval")
+
+
+def vx_nes_adjoint(h, batch: vx_batch, jac: int, fwd: vx_out | None, stream: int = 0) -> None:
+    _check(lib().vx_nes_adjoint(h, ctypes.byref(batch), ctypes.c_void_p(jac or 0),
+                                ctypes.byref(fwd) if fwd is not None else None, ctypes.c_void_p(stream)),
+           "vx_nes_adjoint")
+
+
+def vx_nes_check(h, stream: int = 0) -> int:
+    """VX_OK or VX_ERR_NUMERIC (other failures raise)."""
+    st = lib().vx_nes_check(h, ctypes.c_void_p(stream))
+    if st not in (VX_OK, VX_ERR_NUMERIC):
+        raise VxError(st, "vx_nes_check")
+    return st
+
+
+def vx_nes_destroy(h) -> None:
+    lib().vx_nes_destroy(h)
+
+
+def vx_eos_eta(n_zones: int, state: int, deta: int | None, stream: int = 0) -> None:
+    _check(lib().vx_eos_eta(int(n_zones), ctypes.c_void_p(state or 0), ctypes.c_void_p(deta or 0),
+                            ctypes.c_void_p(stream)), "vx_eos_eta")
+
+
+def vx_eos_chain(n_zones: int, rows: int, deta: int, jac_in: int, jac_out: int, stream: int = 0) -> None:
+    _check(lib().vx_eos_chain(int(n_zones), int(rows), ctypes.c_void_p(deta or 0), ctypes.c_void_p(jac_in or 0),
+                              ctypes.c_void_p(jac_out or 0), ctypes.c_void_p(stream)), "vx_eos_chain")

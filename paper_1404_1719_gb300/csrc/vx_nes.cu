@@ -1,0 +1,832 @@
+// vx_nes.cu -- inelastic neutrino-electron scattering (include/vx_nes.h) and the electron-gas
+// closure (include/vx_eos.h).
+//
+// Work decomposition. One CTA owns one zone at a time (zones pulled from an atomic counter, as in
+// the pair kernel). A bin pair (i >= j: the down-scattering order, eps_i >= eps_j) is one group of
+// lpp lanes of a warp (lpp = n_mu rounded up to a power of two), one lane per cos(omega) node; each
+// lane integrates its (pair, omega) unit over the electron energy, and the group sums the Legendre
+// projections with a fixed shuffle tree (deterministic). The pair's kernel of the other order and
+// the in-scattering kernel follow from time reversal and detailed balance in the contraction.
+//
+// Unit algebra. With t = E - E_min the azimuth-averaged matrix elements are quadratics with
+// non-negative coefficients, <M_X> = a_X + b_X t + c t^2 (a, b, c built in FP64 on the host with
+// the prefactor G2 w_omega 2 pi/(4 |q| eps eps') folded in), so each unit accumulates the three
+// moments Sum W F t^k of the blocking factor F = f(E) (1 - f(E + q0)) (and, for the tangents, of its
+// T and eta derivatives). The electron-energy rule has three panels: Gauss-Legendre below the lower
+// Fermi edge (30 T deep), between the edges, and Gauss-Laguerre above the upper edge. The
+// exponent arguments are anchored at the nearer edge (x2 at the lower, x1 at the upper one), so
+// their rounding stays small where the factors change. On the Laguerre panel, e^x F is formed from
+// the tabulated e^{-x_k} and two per-unit exponentials, with no exponential per node.
+// A zone scale e^{min(eta, 0)} is taken out of the electron occupation, restored in FP64.
+#include "../../include/vx_eos.h"
+#include "../../include/vx_nes.h"
+#include "vx_internal.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+namespace vx {
+vx_status set_error(vx_status s, const char *msg);
+}
+
+namespace {
+
+constexpr int kNesMaxP = 32;     // nodes per panel
+constexpr int kNesMaxMu = 32;
+constexpr int kNesBlock = 128;
+constexpr double kTail = 30.0;   // depth of the lower panel below the lower Fermi edge, in T
+
+vx_status nfail(vx_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    return vx::set_error(s, buf);
+}
+
+#define NES_CU(call)                                                                          \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return nfail(e_ == cudaErrorMemoryAllocation ? VX_ERR_OOM : VX_ERR_CUDA, "%s: %s", #call, \
+                         cudaGetErrorString(e_));                                             \
+    } while (0)
+
+vx_status device_ptr(const void *p, size_t align, const char *name) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nfail(VX_ERR_INVALID_ARG, "%s: not a CUDA pointer", name);
+    }
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+        return nfail(VX_ERR_INVALID_ARG, "%s must be device memory", name);
+    if ((uintptr_t)p % align) return nfail(VX_ERR_INVALID_ARG, "%s must be %zu-byte aligned", name, align);
+    return VX_OK;
+}
+
+// Gauss-Legendre (Newton on P_n) and Gauss-Laguerre nodes and weights, FP64 on the host.
+void gl_nodes(int n, double *x, double *w) {
+    const double pi = 3.14159265358979323846;
+    for (int k = 1; k <= n / 2 + (n & 1); ++k) {
+        double r = std::cos(pi * (k - 0.25) / (n + 0.5)), dP = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double Pm = 1.0, P = r;
+            for (int m = 2; m <= n; ++m) {
+                double Pn = ((2 * m - 1) * r * P - (m - 1) * Pm) / m;
+                Pm = P;
+                P = Pn;
+            }
+            if (n == 1) { P = r; Pm = 1.0; }
+            dP = n * (Pm - r * P) / (1.0 - r * r);
+            const double step = P / dP;
+            r -= step;
+            if (std::fabs(step) <= 1e-17) break;
+        }
+        double Pm = 1.0, P = r;
+        for (int m = 2; m <= n; ++m) {
+            double Pn = ((2 * m - 1) * r * P - (m - 1) * Pm) / m;
+            Pm = P;
+            P = Pn;
+        }
+        if (n == 1) { P = r; Pm = 1.0; }
+        dP = n * (Pm - r * P) / (1.0 - r * r);
+        const double wk = 2.0 / ((1.0 - r * r) * dP * dP);
+        x[n - k] = r; x[k - 1] = -r;
+        w[n - k] = wk; w[k - 1] = wk;
+    }
+    if (n & 1) x[n / 2] = 0.0;
+}
+
+// L_n and L_{n-1} at x (three-term recurrence)
+void lag_eval(int n, double x, double &ln, double &lm) {
+    double p0 = 1.0, p1 = 1.0 - x;
+    for (int k = 1; k < n; ++k) {
+        const double p2 = ((2.0 * k + 1.0 - x) * p1 - k * p0) / (k + 1.0);
+        p0 = p1;
+        p1 = p2;
+    }
+    ln = n ? p1 : 1.0;
+    lm = n ? p0 : 0.0;
+}
+
+// Roots of L_n as the eigenvalues of its Jacobi matrix (diagonal 2k + 1, off-diagonal k): the
+// k-th eigenvalue by bisection on the Sturm count (the number of negative pivots of the LDL^T
+// factorisation of the matrix minus x), inside the Gershgorin bound [0, 4n]; then two Newton steps
+// on L_n. Weights x_k / ((n + 1) L_{n+1}(x_k))^2.
+int sturm_below(int n, double x) {
+    int neg = 0;
+    double d = 1.0 - x;  // a_0 = 1
+    if (d < 0.0) ++neg;
+    for (int k = 1; k < n; ++k) {
+        if (d == 0.0) d = 1e-300;
+        d = (2.0 * k + 1.0 - x) - (double)k * (double)k / d;
+        if (d < 0.0) ++neg;
+    }
+    return neg;
+}
+
+bool lag_nodes(int n, double *x, double *w) {
+    for (int k = 0; k < n; ++k) {
+        double lo = 0.0, hi = 4.0 * n + 2.0;
+        for (int it = 0; it < 200 && hi - lo > 1e-15 * hi; ++it) {
+            const double mid = 0.5 * (lo + hi);
+            if (sturm_below(n, mid) > k) hi = mid;
+            else lo = mid;
+        }
+        double z = 0.5 * (lo + hi);
+        for (int it = 0; it < 2; ++it) {
+            double ln, lm;
+            lag_eval(n, z, ln, lm);
+            const double d = n * (ln - lm) / z;
+            if (d != 0.0) z -= ln / d;
+        }
+        x[k] = z;
+    }
+    for (int k = 0; k < n; ++k) {
+        if (!(x[k] > 0.0) || (k && !(x[k] > x[k - 1]))) return false;
+        double l1, l0;
+        lag_eval(n + 1, x[k], l1, l0);
+        w[k] = x[k] / ((n + 1.0) * (n + 1.0) * l1 * l1);
+    }
+    return true;
+}
+
+}  // namespace
+
+namespace vx {
+
+struct NesCommon {
+    int N, n_mu, n_p, npair, S, lpp, ppw;
+    int species[3];
+    double bI[3], bII[3];
+    double eps[32], w[32];
+    double g2, norm;
+    // panel rules: Gauss-Legendre 1 + tau, 1 - tau, weight; Gauss-Laguerre x, weight, e^{-x}
+    double gu[kNesMaxP], gv[kNesMaxP], gw[kNesMaxP], lx[kNesMaxP], lw[kNesMaxP], lg[kNesMaxP];
+    unsigned char pi_[VX_MAX_PAIRS], pj_[VX_MAX_PAIRS];
+};
+
+// per (pair, omega) record: E_min, q0 (value + remainder), the five coefficients, cos(omega)
+template <typename R>
+struct NesRec {
+    R em, em_lo, q0, q0_lo, aI, bI, aII, bII, c, t;
+};
+
+template <typename R>
+struct NesLaunch {
+    NesCommon c;
+    const NesRec<R> *tab;  // [npair][n_mu]
+    long long Z;
+    const int *off;
+    int n_rays;
+    const double *state, *J, *H;
+    double *j0, *chi0, *j1, *chi1, *phi, *jac;
+    unsigned long long *counter;
+    int *flag;
+};
+
+template <typename R> __device__ __forceinline__ R e2(R x);
+template <> __device__ __forceinline__ float e2<float>(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+template <> __device__ __forceinline__ double e2<double>(double x) { return exp2(x); }
+template <typename R> __device__ __forceinline__ R rc(R x);
+template <> __device__ __forceinline__ float rc<float>(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+template <> __device__ __forceinline__ double rc<double>(double x) { return 1.0 / x; }
+
+// Double-word value h + l (|l| <= ulp(h)/2) and the sums the per-unit set-up needs: Knuth's
+// two-sum of the high parts, the low parts added to the error, renormalised.
+template <typename R>
+struct DW {
+    R h, l;
+};
+template <typename R>
+__device__ __forceinline__ DW<R> dw_add(DW<R> a, DW<R> b) {
+    const R s = a.h + b.h;
+    const R v = s - a.h;
+    const R e = ((a.h - (s - v)) + (b.h - v)) + (a.l + b.l);
+    DW<R> r;
+    r.h = s + e;
+    r.l = e - (r.h - s);
+    return r;
+}
+template <typename R>
+__device__ __forceinline__ DW<R> dw_neg(DW<R> a) {
+    a.h = -a.h;
+    a.l = -a.l;
+    return a;
+}
+
+struct NesZone {
+    double T, eta;
+    int bad;
+};
+
+// Moments of one (pair, omega) unit: F (q = 0), T^2 dF/dT (q = 1), dF/deta (q = 2), each against
+// 1, t, t^2.
+template <typename R, bool ADJ>
+struct NesMom {
+    R m[ADJ ? 3 : 1][3];
+};
+
+template <typename R, bool ADJ, int NP>
+__device__ __forceinline__ void nes_unit(const NesCommon &C, const R *sg, const NesRec<R> &rec, R mu_h, R mu_l,
+                                         R T, R iTl, R one, R esl, NesMom<R, ADJ> &M) {
+    const int np = NP > 0 ? NP : C.n_p;
+    // offsets of the panels' ends relative to the Fermi edges, from double-word sums
+    const DW<R> em = {rec.em, rec.em_lo}, mu = {mu_h, mu_l}, q0w = {rec.q0, rec.q0_lo};
+    const DW<R> emr_w = dw_add(em, dw_neg(mu));        // E_min - mu (mu: the upper edge, q0 >= 0)
+    const DW<R> emq_w = dw_add(emr_w, q0w);            // E_min - (mu - q0) (the lower edge)
+    const R emr = emr_w.h + emr_w.l, emq = emq_w.h + emq_w.l;
+    const R q0 = rec.q0;
+    const R crel = emr > (R)0 ? emr : (R)0;                 // c - mu, c = max(E_min, mu)
+    const R brel = emr > -q0 ? emr : -q0;                    // b - mu, b = max(E_min, mu - q0)
+    const R arel = emr > brel - (R)kTail * T ? emr : brel - (R)kTail * T;  // a - mu
+    const R bq = emq > (R)0 ? emq : (R)0;                    // b - (mu - q0)
+    const R aq = bq - (brel - arel);                         // a - (mu - q0)
+    for (int q = 0; q < (ADJ ? 3 : 1); ++q) M.m[q][0] = M.m[q][1] = M.m[q][2] = (R)0;
+    auto acc = [&](R wF, R t, R r1, R r2, R E) {
+        const R wt = wF * t;
+        M.m[0][0] += wF; M.m[0][1] += wt; M.m[0][2] = fma(wt, t, M.m[0][2]);
+        if (ADJ) {
+            const R dr = r2 - r1;
+            const R we = wF * dr;                                   // dF/deta = F (r2 - r1)
+            const R wT = wF * fma(dr, E, -((R)1 - r2) * q0);        // T^2 dF/dT
+            const R wet = we * t, wTt = wT * t;
+            M.m[2][0] += we; M.m[2][1] += wet; M.m[2][2] = fma(wet, t, M.m[2][2]);
+            M.m[1][0] += wT; M.m[1][1] += wTt; M.m[1][2] = fma(wTt, t, M.m[1][2]);
+        }
+    };
+    const R Em = rec.em;
+    // panels 1 and 2: Gauss-Legendre. x1 = (E - mu)/T, x2 = x1 + q0/T, in log2 units.
+    {
+        const R h1 = (R)0.5 * (brel - arel), h2 = (R)0.5 * (crel - brel);
+        const R X2a = aq * iTl;                    // x2 at a, anchored at the lower edge
+        const R X2b = bq * iTl;                    // x2 at b
+        const R X1c = crel * iTl;                  // x1 at c, anchored at the upper edge
+        const R q0l = q0 * iTl;
+        const R t1 = arel - emr, t2 = brel - emr;  // t at a and at b
+        const R h1l = h1 * iTl, h2l = h2 * iTl;
+        // An empty panel (its ends clipped together at E_min) is skipped: there the exponent
+        // arguments are unbounded, and its nodes carry zero weight anyway.
+        if (h1 > (R)0) {
+#pragma unroll 4
+            for (int k = 0; k < np; ++k) {  // panel 1: [a, b], b the lower edge, X1 <= X2 <= 0
+                const R u = sg[k], wk = sg[2 * kNesMaxP + k];
+                const R X2 = fma(h1l, u, X2a);
+                const R X1 = X2 - q0l;
+                const R e1s = e2<R>(X1 + esl);
+                const R eb = e2<R>(-X2);
+                const R F = rc<R>((one + e1s) * ((R)1 + eb));
+                const R t = fma(h1, u, t1);
+                acc(h1 * wk * F, t, F * ((R)1 + eb) * one, F * (one + e1s), Em + t);
+            }
+        }
+        if (h2 > (R)0) {
+#pragma unroll 4
+            for (int k = 0; k < np; ++k) {  // panel 2: [b, c], c = mu, X1 <= 0 <= X2
+                const R u = sg[k], v = sg[kNesMaxP + k], wk = sg[2 * kNesMaxP + k];
+                const R X2 = fma(h2l, u, X2b);
+                const R X1 = fma(-h2l, v, X1c);
+                const R e1s = e2<R>(X1 + esl);
+                const R eb = e2<R>(-X2);
+                const R F = rc<R>((one + e1s) * ((R)1 + eb));
+                const R t = fma(h2, u, t2);
+                acc(h2 * wk * F, t, F * ((R)1 + eb) * one, F * (one + e1s), Em + t);
+            }
+        }
+    }
+    // panel 3: Gauss-Laguerre above c, E = c + T x: e^x F = 1 / ((one g + A)(1 + B g)), g = e^{-x}.
+    // A overflows (to inf, Fx = 0) only where the unit lies more than the format's range above the
+    // Fermi edge; 1/(1 + B g) is then formed directly rather than as 0 * inf.
+    {
+        const R A = e2<R>(crel * iTl + esl);   // e^{(c - mu)/T} e^{eta_s}
+        const R B = e2<R>(-(crel + q0) * iTl);  // e^{-(c - mu + q0)/T}
+        const R t3 = crel - emr;
+#pragma unroll 4
+        for (int k = 0; k < np; ++k) {
+            const R x = sg[3 * kNesMaxP + k], wk = sg[4 * kNesMaxP + k], g = sg[5 * kNesMaxP + k];
+            const R og = one * g, bg = (R)1 + B * g;
+            const R Fx = rc<R>((og + A) * bg);
+            const R t = fma(T, x, t3);
+            acc(T * wk * Fx, t, Fx * bg * og, ADJ ? rc<R>(bg) : (R)0, Em + t);
+        }
+    }
+}
+
+template <typename R, bool ADJ, int NP>
+__global__ void __launch_bounds__(kNesBlock) k_nes(const __grid_constant__ NesLaunch<R> L) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ NesZone zs;
+    __shared__ long long s_zone;
+    __shared__ R sg[6 * kNesMaxP];
+    const NesCommon &C = L.c;
+    const int N = C.N, N2 = N * N, S = C.S;
+    constexpr int NQ = ADJ ? 3 : 1;
+    // D[q][X][l][i][j] (i >= j filled): the down-scattering kernel and its tangents
+    R *D = reinterpret_cast<R *>(smraw);
+    R *Xf = D + (size_t)NQ * 4 * N2;  // [N][N] e^{-|eps_i - eps_j|/T}
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+    for (int k = tid; k < C.n_p; k += blockDim.x) {
+        sg[k] = (R)C.gu[k];
+        sg[kNesMaxP + k] = (R)C.gv[k];
+        sg[2 * kNesMaxP + k] = (R)C.gw[k];
+        sg[3 * kNesMaxP + k] = (R)C.lx[k];
+        sg[4 * kNesMaxP + k] = (R)C.lw[k];
+        sg[5 * kNesMaxP + k] = (R)C.lg[k];
+    }
+    validate_offsets(L.off, L.n_rays, L.Z, L.flag);
+    const int lpp = C.lpp, ppw = C.ppw, grp = lane / lpp, m = lane % lpp;
+    const bool active = m < C.n_mu;
+    const R L2E = (R)1.4426950408889634;
+    for (;;) {
+        if (tid == 0) {
+            s_zone = (long long)atomicAdd(L.counter, 1ull);
+            const long long z = s_zone;
+            if (z < L.Z) {
+                const double T = L.state[4 * z + 0], eta = L.state[4 * z + 1];
+                zs.T = T;
+                zs.eta = eta;
+                zs.bad = !(T > 0.0) || !isfinite(T) || !isfinite(eta) || fabs(eta) > VX_ETA_MAX;
+            }
+        }
+        __syncthreads();
+        const long long z = s_zone;
+        if (z >= L.Z) break;
+        const double T64 = zs.T, eta64 = zs.eta;
+        if (zs.bad) {
+            const double nan = __longlong_as_double(0x7ff8000000000000ll);
+            for (int e = tid; e < S * N; e += blockDim.x) {
+                const size_t o = (size_t)z * S * N + e;
+                if (L.j0) { L.j0[o] = nan; L.chi0[o] = nan; L.j1[o] = nan; L.chi1[o] = nan; }
+                if (ADJ && L.jac)
+                    for (int q = 0; q < 12; ++q) L.jac[o * 12 + q] = nan;
+            }
+            if (L.phi)
+                for (int e = tid; e < 8 * N2; e += blockDim.x) L.phi[(size_t)z * 8 * N2 + e] = nan;
+            if (tid == 0) atomicOr(L.flag, VX_FLAG_BAD_STATE);
+            __syncthreads();
+            continue;
+        }
+        const double mu64 = eta64 * T64, etas = eta64 < 0.0 ? eta64 : 0.0;
+        const R mu_h = (R)mu64, mu_l = (R)(mu64 - (double)mu_h);
+        const R T = (R)T64, iTl = (R)(1.4426950408889634 / T64);
+        const R one = (R)exp(etas), esl = (R)(etas * 1.4426950408889634);
+        // detailed-balance factors of the zone
+        for (int e = tid; e < N2; e += blockDim.x) {
+            const int i = e / N, j = e % N;
+            Xf[e] = e2<R>((R)(-fabs(C.eps[i] - C.eps[j]) / T64 * 1.4426950408889634));
+        }
+        // quadrature: groups of lpp lanes per bin pair, lanes over cos(omega)
+        const int slots = (C.npair + nwarp * ppw - 1) / (nwarp * ppw);
+        for (int sl = 0; sl < slots; ++sl) {
+            const int p = (sl * nwarp + warp) * ppw + grp;
+            R v[NQ][4];
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) v[q][0] = v[q][1] = v[q][2] = v[q][3] = (R)0;
+            if (active && p < C.npair) {
+                const NesRec<R> rec = L.tab[(size_t)p * C.n_mu + m];
+                NesMom<R, ADJ> M;
+                nes_unit<R, ADJ, NP>(C, sg, rec, mu_h, mu_l, T, iTl, one, esl, M);
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) {
+                    const R kI = fma(rec.aI, M.m[q][0], fma(rec.bI, M.m[q][1], rec.c * M.m[q][2]));
+                    const R kII = fma(rec.aII, M.m[q][0], fma(rec.bII, M.m[q][1], rec.c * M.m[q][2]));
+                    v[q][0] = kI; v[q][1] = kII; v[q][2] = rec.t * kI; v[q][3] = rec.t * kII;
+                }
+            }
+            // sum over the group's lanes (fixed butterfly: deterministic)
+            for (int off = lpp >> 1; off > 0; off >>= 1)
+#pragma unroll
+                for (int q = 0; q < NQ; ++q)
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) v[q][r] += __shfl_xor_sync(0xffffffffu, v[q][r], off);
+            if (m == 0 && p < C.npair) {
+                const int i = C.pi_[p], j = C.pj_[p];
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) {
+                    // [q][X][l]: v = {I l0, II l0, I l1, II l1}
+                    D[((q * 2 + 0) * 2 + 0) * N2 + i * N + j] = v[q][0];
+                    D[((q * 2 + 1) * 2 + 0) * N2 + i * N + j] = v[q][1];
+                    D[((q * 2 + 0) * 2 + 1) * N2 + i * N + j] = v[q][2];
+                    D[((q * 2 + 1) * 2 + 1) * N2 + i * N + j] = v[q][3];
+                }
+            }
+        }
+        __syncthreads();
+        // kernel of a direction: out(i,j) = D(i,j) for i >= j, X D(j,i) above; in(i,j) = X D(i,j)
+        // for i >= j, D(j,i) above. Tangents: dX/dT = X |de|/T^2 (q = 1 holds T^2 dD/dT).
+        auto kern = [&](int q, int X, int l, int dir, int i, int j) -> R {
+            const bool low = i >= j;
+            const int a = low ? i : j, b = low ? j : i;
+            const R d = D[((q * 2 + X) * 2 + l) * N2 + a * N + b];
+            const bool scaled = (dir == 1) != low;  // out above the diagonal, in on and below it
+            if (!scaled || i == j) return d;
+            const R x = Xf[i * N + j];
+            if (q == 1) {
+                const R d0 = D[((0 * 2 + X) * 2 + l) * N2 + a * N + b];
+                return x * fma(d0, (R)fabs(C.eps[i] - C.eps[j]), d);
+            }
+            return x * d;
+        };
+        const double scale = exp(etas), two_pi = 6.283185307179586;
+        for (int e = tid; e < 4 * S * N; e += blockDim.x) {
+            const int o = e / (S * N), s = (e / N) % S, i = e % N;
+            const int l = o >> 1, dir = o & 1;  // j0: in l0, chi0: out l0, j1: in l1, chi1: out l1
+            const R bI = (R)C.bI[s], bII = (R)C.bII[s];
+            const size_t row = ((size_t)z * S + s) * N;
+            double res[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                R acc = (R)0;
+                for (int j = 0; j < N; ++j) {
+                    const R vj = (R)(C.w[j] * (o == 0 ? L.J[row + j] : o == 1 ? 1.0 - L.J[row + j] : L.H[row + j]));
+                    acc = fma(fma(bI, kern(q, 0, l, dir, i, j), bII * kern(q, 1, l, dir, i, j)), vj, acc);
+                }
+                res[q] = (double)acc;
+            }
+            const double cl = (l ? -3.0 : 1.0) * two_pi * C.norm * scale;
+            const size_t oi = row + i;
+            const double fwd = cl * res[0];
+            if (L.j0) {
+                double *dst = o == 0 ? L.j0 : o == 1 ? L.chi0 : o == 2 ? L.j1 : L.chi1;
+                dst[oi] = fwd;
+                if (!isfinite(fwd)) atomicOr(L.flag, VX_FLAG_NONFINITE);
+            }
+            if (ADJ && L.jac) {
+                const double dT = cl * res[1] / (T64 * T64), dE = cl * res[2];
+                L.jac[oi * 12 + o * 3 + 0] = dT;
+                L.jac[oi * 12 + o * 3 + 1] = dE;
+                L.jac[oi * 12 + o * 3 + 2] = 0.0;
+                if (!isfinite(dT) || !isfinite(dE)) atomicOr(L.flag, VX_FLAG_NONFINITE);
+            }
+        }
+        if (L.phi) {  // [X][dir][l][i][j], G2 applied (in the table), zone scale restored
+            for (int e = tid; e < 8 * N2; e += blockDim.x) {
+                const int X = e / (4 * N2), dir = (e / (2 * N2)) & 1, l = (e / N2) & 1, ij = e % N2;
+                L.phi[(size_t)z * 8 * N2 + e] = scale * (double)kern(0, X, l, dir, ij / N, ij % N);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <typename R, bool ADJ>
+const void *nes_kernel(int n_p) {
+    switch (n_p) {
+        case 8: return (const void *)k_nes<R, ADJ, 8>;
+        case 16: return (const void *)k_nes<R, ADJ, 16>;
+        default: return (const void *)k_nes<R, ADJ, 0>;
+    }
+}
+
+template <typename R, bool ADJ>
+cudaError_t nes_launch(const NesLaunch<R> &L, int grid, size_t smem, cudaStream_t s) {
+    switch (L.c.n_p) {
+        case 8: k_nes<R, ADJ, 8><<<grid, kNesBlock, smem, s>>>(L); break;
+        case 16: k_nes<R, ADJ, 16><<<grid, kNesBlock, smem, s>>>(L); break;
+        default: k_nes<R, ADJ, 0><<<grid, kNesBlock, smem, s>>>(L); break;
+    }
+    return cudaGetLastError();
+}
+
+// ---- electron-gas closure -------------------------------------------------------------------
+// eta from the cubic eta^3 + pi^2 eta = q by Newton's method from a bracketing start (the
+// function is increasing and convex for eta >= 0; from above the root Newton converges
+// monotonically), then the derivatives by implicit differentiation.
+__global__ void k_eos_eta(long long Z, double *state, double *deta) {
+    const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (z >= Z) return;
+    const double hbarc = 1.973269804e-11, mu_g = 1.66053906660e-24, p = 9.869604401089358;  // pi^2
+    const double T = state[4 * z + 0], ye = state[4 * z + 2], rho = state[4 * z + 3];
+    double eta = __longlong_as_double(0x7ff8000000000000ll), d0 = eta, d1 = eta, d2 = eta;
+    if (T > 0.0 && ye >= 0.0 && rho >= 0.0 && isfinite(T) && isfinite(ye) && isfinite(rho)) {
+        const double r = hbarc / T;
+        const double q = 3.0 * p * (rho * ye / mu_g) * r * r * r;
+        // start above the root: eta^3 + p eta >= max(eta^3, p eta), so eta0 = max(cbrt(q), q/p) works
+        double e = fmax(cbrt(q), q / p);
+        for (int it = 0; it < 100; ++it) {
+            const double f = fma(e * e, e, p * e) - q, df = fma(3.0 * e, e, p);
+            const double step = f / df;
+            e -= step;
+            if (!(fabs(step) > 1e-16 * fmax(e, 1e-300))) break;
+        }
+        eta = e;
+        const double dedq = 1.0 / fma(3.0 * e, e, p);
+        d0 = dedq * (-3.0 * q / T);
+        d1 = dedq * (ye > 0.0 ? q / ye : 3.0 * p * (rho / mu_g) * r * r * r);
+        d2 = dedq * (rho > 0.0 ? q / rho : 3.0 * p * (ye / mu_g) * r * r * r);
+    }
+    state[4 * z + 1] = eta;
+    if (deta) { deta[3 * z + 0] = d0; deta[3 * z + 1] = d1; deta[3 * z + 2] = d2; }
+}
+
+__global__ void k_eos_chain(long long Z, int rows, const double *deta, const double *jin, double *jout) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= Z * rows) return;
+    const long long z = e / rows;
+    const double dT = jin[3 * e + 0], dE = jin[3 * e + 1];
+    const double a = deta[3 * z + 0], b = deta[3 * z + 1], c = deta[3 * z + 2];
+    jout[3 * e + 0] = fma(dE, a, dT);
+    jout[3 * e + 1] = dE * b;
+    jout[3 * e + 2] = dE * c;
+}
+
+}  // namespace vx
+
+struct vx_nes {
+    int device = 0, nsm = 0;
+    vx::NesCommon c{};
+    int prec = VX_PREC_MIXED;
+    void *d_tab = nullptr;
+    unsigned long long *d_counter = nullptr;
+    int *d_flag = nullptr;
+    size_t smem[2] = {0, 0};
+    int grid[2] = {0, 0};
+};
+
+namespace {
+
+// Builds the (pair, omega) table in FP64: E_min = eps eps' y/(Q + q0), the coefficients of the
+// azimuth-averaged matrix elements in t = E - E_min (all non-negative), with u = eps eps' y/Q,
+// sigma = eps + eps', G = (eps eps')^2 y (2 - y), sigma - Q = 2 eps eps' (2 - y)/(sigma + Q):
+//   a_I = u^2 Q^2 (sigma + Q)(sigma - Q)/(4 Q^2) + u^2 Q (sigma + Q)/2,  a_II = u^2 (sigma - Q)^2/4,
+//   b_I = u^2 sigma^2/Q + u G/Q^2 + u^2 sigma,  b_II = u^2 sigma (sigma - Q)/Q + u G/Q^2,
+//   c = u^2 sigma^2/Q^2 + u G/Q^3,
+// each times G2 w_omega 2 pi/(4 Q eps eps').
+template <typename R>
+std::vector<vx::NesRec<R>> nes_table(const vx::NesCommon &C, const double *tmu, const double *wmu) {
+    const double pi = 3.14159265358979323846;
+    std::vector<vx::NesRec<R>> tab((size_t)C.npair * C.n_mu);
+    for (int p = 0; p < C.npair; ++p) {
+        const double e = C.eps[C.pi_[p]], ep = C.eps[C.pj_[p]];
+        for (int m = 0; m < C.n_mu; ++m) {
+            const double t = tmu[m], y = 1.0 - t, g = e * ep, q0 = e - ep;
+            const double Q = std::sqrt(q0 * q0 + 2.0 * g * y), s = e + ep;
+            const double Em = g * y / (Q + q0), u = g * y / Q, G = g * g * y * (2.0 - y);
+            const double smQ = 2.0 * g * (2.0 - y) / (s + Q);
+            const double pref = C.g2 * wmu[m] * 2.0 * pi / (4.0 * Q * g);
+            const double aI = u * u * (Q * (s + Q)) * (Q * smQ) / (4.0 * Q * Q) + u * u * Q * (s + Q) / 2.0;
+            const double aII = u * u * smQ * smQ / 4.0;
+            const double bI = u * u * s * s / Q + u * G / (Q * Q) + u * u * s;
+            const double bII = u * u * s * smQ / Q + u * G / (Q * Q);
+            const double cc = u * u * s * s / (Q * Q) + u * G / (Q * Q * Q);
+            vx::NesRec<R> &r = tab[(size_t)p * C.n_mu + m];
+            r.em = (R)Em; r.em_lo = (R)(Em - (double)r.em);
+            r.q0 = (R)q0; r.q0_lo = (R)(q0 - (double)r.q0);
+            r.aI = (R)(pref * aI); r.bI = (R)(pref * bI); r.aII = (R)(pref * aII); r.bII = (R)(pref * bII);
+            r.c = (R)(pref * cc); r.t = (R)t;
+        }
+    }
+    return tab;
+}
+
+size_t nes_smem(const vx::NesCommon &C, bool adj, bool dbl) {
+    const size_t r = dbl ? 8 : 4;
+    return ((adj ? 3 : 1) * 4 * (size_t)C.N * C.N + (size_t)C.N * C.N) * r;
+}
+
+vx_status nes_validate_batch(const vx_nes *h, const vx_batch *b) {
+    if (!h) return nfail(VX_ERR_INVALID_ARG, "handle is NULL");
+    if (!b) return nfail(VX_ERR_INVALID_ARG, "batch is NULL");
+    if (b->n_zones < 0 || b->n_rays < 0) return nfail(VX_ERR_INVALID_ARG, "negative batch size");
+    if (b->n_zones == 0) return VX_OK;
+    vx_status s;
+    if (b->ray_offsets) {
+        if (b->n_rays == 0) return nfail(VX_ERR_INVALID_ARG, "n_zones > 0 with no rays");
+        if ((s = device_ptr(b->ray_offsets, 4, "ray_offsets")) != VX_OK) return s;
+    }
+    if ((s = device_ptr(b->state, 8, "state")) != VX_OK) return s;
+    if ((s = device_ptr(b->J, 8, "J")) != VX_OK) return s;
+    if ((s = device_ptr(b->H, 8, "H")) != VX_OK) return s;
+    return VX_OK;
+}
+
+vx_status nes_validate_out(const vx_out *o, bool allow_phi) {
+    vx_status s;
+    const double *a[4] = {o->j0, o->chi0, o->j1, o->chi1};
+    const char *nm[4] = {"out.j0", "out.chi0", "out.j1", "out.chi1"};
+    for (int k = 0; k < 4; ++k)
+        if ((s = device_ptr(a[k], 8, nm[k])) != VX_OK) return s;
+    if (o->phi) {
+        if (!allow_phi) return nfail(VX_ERR_INVALID_ARG, "phi output is not produced by this call");
+        if ((s = device_ptr(o->phi, 8, "out.phi")) != VX_OK) return s;
+    }
+    return VX_OK;
+}
+
+template <typename R>
+vx_status nes_run(vx_nes *h, const vx_batch *b, const vx_out *out, double *jac, cudaStream_t s) {
+    vx::NesLaunch<R> L{};
+    L.c = h->c;
+    L.tab = reinterpret_cast<const vx::NesRec<R> *>(h->d_tab);
+    L.Z = b->n_zones;
+    L.off = b->ray_offsets;
+    L.n_rays = b->n_rays;
+    L.state = b->state; L.J = b->J; L.H = b->H;
+    if (out) { L.j0 = out->j0; L.chi0 = out->chi0; L.j1 = out->j1; L.chi1 = out->chi1; L.phi = out->phi; }
+    L.jac = jac;
+    L.counter = h->d_counter;
+    L.flag = h->d_flag;
+    const bool adj = jac != nullptr;
+    const int grid = (int)std::min<long long>(h->grid[adj], b->n_zones);
+    NES_CU(cudaMemsetAsync(h->d_counter, 0, sizeof(unsigned long long), s));
+    const cudaError_t e = adj ? vx::nes_launch<R, true>(L, grid, h->smem[1], s) : vx::nes_launch<R, false>(L, grid, h->smem[0], s);
+    NES_CU(e);
+    return VX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+vx_status vx_nes_create(const vx_config *cfg, vx_nes **out) {
+    if (!out) return nfail(VX_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!cfg) return nfail(VX_ERR_INVALID_ARG, "config is NULL");
+    if (cfg->n_bins < 2 || cfg->n_bins > VX_MAX_BINS - 1) return nfail(VX_ERR_INVALID_ARG, "n_bins %d outside 2..31", cfg->n_bins);
+    if (!cfg->eps) return nfail(VX_ERR_INVALID_ARG, "eps is NULL");
+    for (int i = 0; i < cfg->n_bins; ++i) {
+        if (!(cfg->eps[i] > 0.0) || !std::isfinite(cfg->eps[i])) return nfail(VX_ERR_INVALID_ARG, "eps[%d] must be finite and > 0", i);
+        if (i && !(cfg->eps[i] > cfg->eps[i - 1])) return nfail(VX_ERR_INVALID_ARG, "eps must be strictly increasing");
+        if (cfg->weights && (!(cfg->weights[i] > 0.0) || !std::isfinite(cfg->weights[i])))
+            return nfail(VX_ERR_INVALID_ARG, "weights[%d] must be finite and > 0", i);
+    }
+    if (cfg->n_mu < 2 || cfg->n_mu > kNesMaxMu) return nfail(VX_ERR_INVALID_ARG, "n_mu %d outside 2..%d", cfg->n_mu, kNesMaxMu);
+    if (cfg->n_e < 6 || cfg->n_e > 3 * kNesMaxP || cfg->n_e % 3)
+        return nfail(VX_ERR_INVALID_ARG, "n_e %d must be a multiple of 3 in 6..%d", cfg->n_e, 3 * kNesMaxP);
+    if (cfg->n_species < 1 || cfg->n_species > 3 || !cfg->species) return nfail(VX_ERR_INVALID_ARG, "n_species must be 1..3");
+    for (int s = 0; s < cfg->n_species; ++s) {
+        if (cfg->species[s] < 0 || cfg->species[s] > 2) return nfail(VX_ERR_INVALID_ARG, "species[%d] is not a vx_species", s);
+        for (int t = 0; t < s; ++t)
+            if (cfg->species[t] == cfg->species[s]) return nfail(VX_ERR_INVALID_ARG, "species listed twice");
+    }
+    if (!std::isfinite(cfg->sin2w) || !std::isfinite(cfg->g2) || !std::isfinite(cfg->norm))
+        return nfail(VX_ERR_INVALID_ARG, "sin2w, g2 and norm must be finite");
+    if (cfg->prec != VX_PREC_MIXED && cfg->prec != VX_PREC_FP64) return nfail(VX_ERR_INVALID_ARG, "unknown precision");
+    if (cfg->flags != 0 || cfg->eta_fp64 != 0.0) return nfail(VX_ERR_INVALID_ARG, "flags and eta_fp64 must be 0 for NES");
+
+    vx_nes *h = new vx_nes();
+    h->prec = cfg->prec;
+    vx::NesCommon &C = h->c;
+    const int N = cfg->n_bins;
+    C.N = N; C.n_mu = cfg->n_mu; C.n_p = cfg->n_e / 3; C.S = cfg->n_species;
+    C.npair = N * (N + 1) / 2;
+    int lpp = 1;
+    while (lpp < C.n_mu) lpp <<= 1;
+    C.lpp = lpp;
+    C.ppw = 32 / lpp;
+    C.g2 = cfg->g2;
+    C.norm = cfg->norm;
+    for (int i = 0; i < N; ++i) {
+        C.eps[i] = cfg->eps[i];
+        if (cfg->weights) C.w[i] = cfg->weights[i];
+        else {
+            const double *e = cfg->eps;
+            const double lo = i ? std::sqrt(e[i - 1] * e[i]) : e[0] * std::sqrt(e[0] / e[1]);
+            const double hi = i < N - 1 ? std::sqrt(e[i] * e[i + 1]) : e[N - 1] * std::sqrt(e[N - 1] / e[N - 2]);
+            C.w[i] = e[i] * e[i] * (hi - lo);
+        }
+    }
+    for (int s = 0; s < C.S; ++s) {
+        const int sp = cfg->species[s];
+        C.species[s] = sp;
+        const double cv = (sp == VX_NU_X ? -0.5 : 0.5) + 2.0 * cfg->sin2w, ca = sp == VX_NU_X ? -0.5 : 0.5;
+        double b1 = (cv + ca) * (cv + ca), b2 = (cv - ca) * (cv - ca);
+        if (sp == VX_NU_EBAR) std::swap(b1, b2);
+        C.bI[s] = b1;
+        C.bII[s] = b2;
+    }
+    {
+        int p = 0;
+        for (int i = 0; i < N; ++i)
+            for (int j = 0; j <= i; ++j) { C.pi_[p] = (unsigned char)i; C.pj_[p] = (unsigned char)j; ++p; }
+    }
+    double tmu[kNesMaxMu], wmu[kNesMaxMu], tg[kNesMaxP], wg[kNesMaxP], xl[kNesMaxP], wl[kNesMaxP];
+    gl_nodes(C.n_mu, tmu, wmu);
+    gl_nodes(C.n_p, tg, wg);
+    if (!lag_nodes(C.n_p, xl, wl)) { delete h; return nfail(VX_ERR_INVALID_ARG, "Gauss-Laguerre nodes did not converge"); }
+    for (int k = 0; k < C.n_p; ++k) {
+        C.gu[k] = 1.0 + tg[k]; C.gv[k] = 1.0 - tg[k]; C.gw[k] = wg[k];
+        C.lx[k] = xl[k]; C.lw[k] = wl[k]; C.lg[k] = std::exp(-xl[k]);
+    }
+    auto cleanup = [&](vx_status st) { vx_nes_destroy(h); return st; };
+    cudaDeviceProp prop;
+    if (cudaGetDevice(&h->device) != cudaSuccess || cudaGetDeviceProperties(&prop, h->device) != cudaSuccess) {
+        delete h;
+        return nfail(VX_ERR_CUDA, "no CUDA device");
+    }
+    h->nsm = prop.multiProcessorCount;
+    const bool dbl = h->prec == VX_PREC_FP64;
+    size_t tb;
+    if (dbl) {
+        auto t = nes_table<double>(C, tmu, wmu);
+        tb = t.size() * sizeof(t[0]);
+        if (cudaMalloc(&h->d_tab, tb) != cudaSuccess || cudaMemcpy(h->d_tab, t.data(), tb, cudaMemcpyHostToDevice) != cudaSuccess)
+            return cleanup(nfail(VX_ERR_OOM, "table upload failed"));
+    } else {
+        auto t = nes_table<float>(C, tmu, wmu);
+        tb = t.size() * sizeof(t[0]);
+        if (cudaMalloc(&h->d_tab, tb) != cudaSuccess || cudaMemcpy(h->d_tab, t.data(), tb, cudaMemcpyHostToDevice) != cudaSuccess)
+            return cleanup(nfail(VX_ERR_OOM, "table upload failed"));
+    }
+    if (cudaMalloc(&h->d_counter, sizeof(unsigned long long)) != cudaSuccess || cudaMalloc(&h->d_flag, sizeof(int)) != cudaSuccess ||
+        cudaMemset(h->d_flag, 0, sizeof(int)) != cudaSuccess)
+        return cleanup(nfail(VX_ERR_OOM, "allocation failed"));
+    for (int adj = 0; adj < 2; ++adj) {
+        h->smem[adj] = nes_smem(C, adj != 0, dbl);
+        const void *fn = dbl ? (adj ? vx::nes_kernel<double, true>(C.n_p) : vx::nes_kernel<double, false>(C.n_p))
+                             : (adj ? vx::nes_kernel<float, true>(C.n_p) : vx::nes_kernel<float, false>(C.n_p));
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem[adj]) != cudaSuccess)
+            return cleanup(nfail(VX_ERR_CUDA, "shared memory attribute"));
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kNesBlock, h->smem[adj]) != cudaSuccess || occ < 1)
+            return cleanup(nfail(VX_ERR_UNSUPPORTED, "NES kernel does not fit on an SM"));
+        h->grid[adj] = occ * h->nsm;
+    }
+    *out = h;
+    return VX_OK;
+}
+
+vx_status vx_nes_eval(vx_nes *h, const vx_batch *b, const vx_out *out, vx_stream stream) {
+    vx_status st = nes_validate_batch(h, b);
+    if (st != VX_OK) return st;
+    if (!out) return nfail(VX_ERR_INVALID_ARG, "out is NULL");
+    if (b->n_zones == 0) return VX_OK;
+    if ((st = nes_validate_out(out, true)) != VX_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    return h->prec == VX_PREC_FP64 ? nes_run<double>(h, b, out, nullptr, s) : nes_run<float>(h, b, out, nullptr, s);
+}
+
+vx_status vx_nes_adjoint(vx_nes *h, const vx_batch *b, double *jac, const vx_out *fwd, vx_stream stream) {
+    vx_status st = nes_validate_batch(h, b);
+    if (st != VX_OK) return st;
+    if (!jac) return nfail(VX_ERR_INVALID_ARG, "jac is NULL");
+    if (b->n_zones == 0) return VX_OK;
+    if ((st = device_ptr(jac, 8, "jac")) != VX_OK) return st;
+    if (fwd && (st = nes_validate_out(fwd, false)) != VX_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    return h->prec == VX_PREC_FP64 ? nes_run<double>(h, b, fwd, jac, s) : nes_run<float>(h, b, fwd, jac, s);
+}
+
+vx_status vx_nes_check(vx_nes *h, vx_stream stream) {
+    if (!h) return nfail(VX_ERR_INVALID_ARG, "handle is NULL");
+    NES_CU(cudaStreamSynchronize((cudaStream_t)stream));
+    int f = 0;
+    NES_CU(cudaMemcpy(&f, h->d_flag, sizeof(int), cudaMemcpyDeviceToHost));
+    if (f) {
+        NES_CU(cudaMemset(h->d_flag, 0, sizeof(int)));
+        return nfail(VX_ERR_NUMERIC, "NES device flag 0x%x (%s%s%s)", f, (f & VX_FLAG_BAD_STATE) ? "invalid zone state; " : "",
+                     (f & VX_FLAG_NONFINITE) ? "non-finite result; " : "", (f & VX_FLAG_BAD_OFFSETS) ? "invalid ray offsets" : "");
+    }
+    return VX_OK;
+}
+
+void vx_nes_destroy(vx_nes *h) {
+    if (!h) return;
+    cudaDeviceSynchronize();
+    cudaFree(h->d_tab);
+    cudaFree(h->d_counter);
+    cudaFree(h->d_flag);
+    delete h;
+}
+
+vx_status vx_eos_eta(long long n_zones, double *state, double *deta, vx_stream stream) {
+    if (n_zones < 0) return nfail(VX_ERR_INVALID_ARG, "n_zones < 0");
+    if (n_zones == 0) return VX_OK;
+    if (!state) return nfail(VX_ERR_INVALID_ARG, "state is NULL");
+    vx_status st;
+    if ((st = device_ptr(state, 8, "state")) != VX_OK) return st;
+    if (deta && (st = device_ptr(deta, 8, "deta")) != VX_OK) return st;
+    vx::k_eos_eta<<<(unsigned)((n_zones + 255) / 256), 256, 0, (cudaStream_t)stream>>>(n_zones, state, deta);
+    NES_CU(cudaGetLastError());
+    return VX_OK;
+}
+
+vx_status vx_eos_chain(long long n_zones, int rows, const double *deta, const double *jac_in, double *jac_out,
+                       vx_stream stream) {
+    if (n_zones < 0 || rows < 0) return nfail(VX_ERR_INVALID_ARG, "negative size");
+    if (n_zones == 0 || rows == 0) return VX_OK;
+    if (!deta || !jac_in || !jac_out) return nfail(VX_ERR_INVALID_ARG, "NULL array");
+    vx_status st;
+    if ((st = device_ptr(deta, 8, "deta")) != VX_OK) return st;
+    if ((st = device_ptr(jac_in, 8, "jac_in")) != VX_OK) return st;
+    if ((st = device_ptr(jac_out, 8, "jac_out")) != VX_OK) return st;
+    const long long n = n_zones * rows;
+    vx::k_eos_chain<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(n_zones, rows, deta, jac_in, jac_out);
+    NES_CU(cudaGetLastError());
+    return VX_OK;
+}
+
+}  // extern "C"
