@@ -229,7 +229,7 @@ __device__ __forceinline__ DW<R> dw_neg(DW<R> a) {
 }
 
 struct NesZone {
-    double T, eta;
+    double T, eta, scale, iT2;  // scale: e^{min(eta, 0)}, the zone scale restored at the end
     int bad;
 };
 
@@ -331,12 +331,15 @@ __global__ void __launch_bounds__(kNesBlock) k_nes(const __grid_constant__ NesLa
     __shared__ NesZone zs;
     __shared__ long long s_zone;
     __shared__ R sg[6 * kNesMaxP];
+    __shared__ R zr[6];  // mu (value, remainder), T, log2(e)/T, e^{eta_s}, eta_s log2(e)
     const NesCommon &C = L.c;
     const int N = C.N, N2 = N * N, S = C.S;
     constexpr int NQ = ADJ ? 3 : 1;
     // D[q][X][l][i][j] (i >= j filled): the down-scattering kernel and its tangents
     R *D = reinterpret_cast<R *>(smraw);
-    R *Xf = D + (size_t)NQ * 4 * N2;  // [N][N] e^{-|eps_i - eps_j|/T}
+    R *Xf = D + (size_t)NQ * 4 * N2;  // [N][N] e^{-|eps_i - eps_j|/T} of the zone
+    R *dE = Xf + N2;                  // [N][N] |eps_i - eps_j|
+    R *vec = dE + N2;                 // [4][S][N] w_j (J_j, 1 - J_j, H_j, H_j) of the zone
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
     for (int k = tid; k < C.n_p; k += blockDim.x) {
         sg[k] = (R)C.gu[k];
@@ -346,6 +349,7 @@ __global__ void __launch_bounds__(kNesBlock) k_nes(const __grid_constant__ NesLa
         sg[4 * kNesMaxP + k] = (R)C.lw[k];
         sg[5 * kNesMaxP + k] = (R)C.lg[k];
     }
+    for (int e = tid; e < N2; e += blockDim.x) dE[e] = (R)fabs(C.eps[e / N] - C.eps[e % N]);
     validate_offsets(L.off, L.n_rays, L.Z, L.flag);
     const int lpp = C.lpp, ppw = C.ppw, grp = lane / lpp, m = lane % lpp;
     const bool active = m < C.n_mu;
@@ -359,12 +363,22 @@ __global__ void __launch_bounds__(kNesBlock) k_nes(const __grid_constant__ NesLa
                 zs.T = T;
                 zs.eta = eta;
                 zs.bad = !(T > 0.0) || !isfinite(T) || !isfinite(eta) || fabs(eta) > VX_ETA_MAX;
+                if (!zs.bad) {  // the zone's scalars, once (FP64 here, R in the loops)
+                    const double mu = eta * T, etas = eta < 0.0 ? eta : 0.0;
+                    zr[0] = (R)mu;
+                    zr[1] = (R)(mu - (double)zr[0]);
+                    zr[2] = (R)T;
+                    zr[3] = (R)(1.4426950408889634 / T);
+                    zs.scale = exp(etas);
+                    zr[4] = (R)zs.scale;
+                    zr[5] = (R)(etas * 1.4426950408889634);
+                    zs.iT2 = 1.0 / (T * T);
+                }
             }
         }
         __syncthreads();
         const long long z = s_zone;
         if (z >= L.Z) break;
-        const double T64 = zs.T, eta64 = zs.eta;
         if (zs.bad) {
             const double nan = __longlong_as_double(0x7ff8000000000000ll);
             for (int e = tid; e < S * N; e += blockDim.x) {
@@ -379,14 +393,13 @@ __global__ void __launch_bounds__(kNesBlock) k_nes(const __grid_constant__ NesLa
             __syncthreads();
             continue;
         }
-        const double mu64 = eta64 * T64, etas = eta64 < 0.0 ? eta64 : 0.0;
-        const R mu_h = (R)mu64, mu_l = (R)(mu64 - (double)mu_h);
-        const R T = (R)T64, iTl = (R)(1.4426950408889634 / T64);
-        const R one = (R)exp(etas), esl = (R)(etas * 1.4426950408889634);
-        // detailed-balance factors of the zone
-        for (int e = tid; e < N2; e += blockDim.x) {
-            const int i = e / N, j = e % N;
-            Xf[e] = e2<R>((R)(-fabs(C.eps[i] - C.eps[j]) / T64 * 1.4426950408889634));
+        const R mu_h = zr[0], mu_l = zr[1], T = zr[2], iTl = zr[3], one = zr[4], esl = zr[5];
+        // detailed-balance factors and contraction vectors of the zone
+        for (int e = tid; e < N2; e += blockDim.x) Xf[e] = e2<R>(-dE[e] * iTl);
+        for (int e = tid; e < 4 * S * N; e += blockDim.x) {
+            const int o = e / (S * N), j = e % N;
+            const double Jj = L.J[(size_t)z * S * N + e % (S * N)], Hj = L.H[(size_t)z * S * N + e % (S * N)];
+            vec[e] = (R)(C.w[j] * (o == 0 ? Jj : o == 1 ? 1.0 - Jj : Hj));
         }
         // quadrature: groups of lpp lanes per bin pair, lanes over cos(omega)
         const int slots = (C.npair + nwarp * ppw - 1) / (nwarp * ppw);
@@ -436,24 +449,23 @@ __global__ void __launch_bounds__(kNesBlock) k_nes(const __grid_constant__ NesLa
             const R x = Xf[i * N + j];
             if (q == 1) {
                 const R d0 = D[((0 * 2 + X) * 2 + l) * N2 + a * N + b];
-                return x * fma(d0, (R)fabs(C.eps[i] - C.eps[j]), d);
+                return x * fma(d0, dE[i * N + j], d);
             }
             return x * d;
         };
-        const double scale = exp(etas), two_pi = 6.283185307179586;
+        const double scale = zs.scale, two_pi = 6.283185307179586;
         for (int e = tid; e < 4 * S * N; e += blockDim.x) {
             const int o = e / (S * N), s = (e / N) % S, i = e % N;
             const int l = o >> 1, dir = o & 1;  // j0: in l0, chi0: out l0, j1: in l1, chi1: out l1
             const R bI = (R)C.bI[s], bII = (R)C.bII[s];
             const size_t row = ((size_t)z * S + s) * N;
+            const R *vo = vec + (size_t)(o * S + s) * N;
             double res[3] = {0.0, 0.0, 0.0};
 #pragma unroll
             for (int q = 0; q < NQ; ++q) {
                 R acc = (R)0;
-                for (int j = 0; j < N; ++j) {
-                    const R vj = (R)(C.w[j] * (o == 0 ? L.J[row + j] : o == 1 ? 1.0 - L.J[row + j] : L.H[row + j]));
-                    acc = fma(fma(bI, kern(q, 0, l, dir, i, j), bII * kern(q, 1, l, dir, i, j)), vj, acc);
-                }
+                for (int j = 0; j < N; ++j)
+                    acc = fma(fma(bI, kern(q, 0, l, dir, i, j), bII * kern(q, 1, l, dir, i, j)), vo[j], acc);
                 res[q] = (double)acc;
             }
             const double cl = (l ? -3.0 : 1.0) * two_pi * C.norm * scale;
@@ -465,11 +477,11 @@ __global__ void __launch_bounds__(kNesBlock) k_nes(const __grid_constant__ NesLa
                 if (!isfinite(fwd)) atomicOr(L.flag, VX_FLAG_NONFINITE);
             }
             if (ADJ && L.jac) {
-                const double dT = cl * res[1] / (T64 * T64), dE = cl * res[2];
+                const double dT = cl * res[1] * zs.iT2, dEta = cl * res[2];
                 L.jac[oi * 12 + o * 3 + 0] = dT;
-                L.jac[oi * 12 + o * 3 + 1] = dE;
+                L.jac[oi * 12 + o * 3 + 1] = dEta;
                 L.jac[oi * 12 + o * 3 + 2] = 0.0;
-                if (!isfinite(dT) || !isfinite(dE)) atomicOr(L.flag, VX_FLAG_NONFINITE);
+                if (!isfinite(dT) || !isfinite(dEta)) atomicOr(L.flag, VX_FLAG_NONFINITE);
             }
         }
         if (L.phi) {  // [X][dir][l][i][j], G2 applied (in the table), zone scale restored
@@ -593,8 +605,8 @@ std::vector<vx::NesRec<R>> nes_table(const vx::NesCommon &C, const double *tmu, 
 }
 
 size_t nes_smem(const vx::NesCommon &C, bool adj, bool dbl) {
-    const size_t r = dbl ? 8 : 4;
-    return ((adj ? 3 : 1) * 4 * (size_t)C.N * C.N + (size_t)C.N * C.N) * r;
+    const size_t r = dbl ? 8 : 4, N2 = (size_t)C.N * C.N;
+    return ((adj ? 3 : 1) * 4 * N2 + 2 * N2 + 4 * (size_t)C.S * C.N) * r;
 }
 
 vx_status nes_validate_batch(const vx_nes *h, const vx_batch *b) {
