@@ -12,8 +12,9 @@
 //    y_k = D_k^{-1} (rhs_k - A_k y_{k-1}), backward delta_k = y_k - G_k delta_{k+1}; a lane holds
 //    rows lane + 32 t of a zone's vector and the column being eliminated is broadcast by shuffle.
 //    The first sweep writes x = delta, later ones add delta to x in FP64.
-//  * k_btd_resid: the FP64 residual r = d - M x from the caller's FP64 blocks, one warp per zone
-//    row block, lanes across a row (coalesced), a fixed butterfly reduction per row.
+//  * k_btd_resid: the FP64 residual r = d - M x from the caller's FP64 blocks, a warp per zone,
+//    four lanes per row and eight rows per pass (coalesced), FMA accumulation and a fixed two-step
+//    shuffle reduction per row.
 // The host runs validate, factor, sweep, then n_refine times (resid, sweep), all on the caller's
 // stream.
 #include "../../include/vx_btd.h"
@@ -35,6 +36,7 @@ namespace {
 
 constexpr int kFactorThreads = 256;
 constexpr int kResidThreads = 256;
+constexpr int kResidSplit = 4;  // CTAs per ray in the residual kernel
 
 vx_status bfail(vx_status s, const char *fmt, ...) {
     char buf[512];
@@ -590,26 +592,56 @@ __global__ void __launch_bounds__(32) k_btd_sweep(const BtdArgs a) {
     stage_wait<0>();
 }
 
-__global__ void __launch_bounds__(kResidThreads) k_btd_resid(const BtdArgs a) {
+// Each ray's zones are split over kResidSplit CTAs (blockIdx.y), a warp per zone. The kernel is
+// bound by the FP64 pipe, not by HBM: every matrix element costs one FP64 FMA and GB300 issues few
+// of them per clock, so the layout minimises FP64 instructions beyond those FMAs. Lane 4 r + c takes
+// row i0 + r of a pass of eight rows and the columns c, c + 4, ... (four lanes read 32 contiguous
+// bytes of a row, eight rows per load instruction), accumulates with FMAs only, and two
+// shuffle-add steps finish the row: about 3 m + 2 FP64 operations per row against 3 m.
+#ifndef VX_RESID_MINB
+#define VX_RESID_MINB 2
+#endif
+constexpr int kResidUnroll = 7;  // column quads per batch of loads in flight
+__global__ void __launch_bounds__(kResidThreads, VX_RESID_MINB) k_btd_resid(const BtdArgs a) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int rr = lane >> 2, cc = lane & 3;
     long long z0, z1;
     if (!ray_range(a, blockIdx.x, z0, z1) || z1 == z0 || a.zbad[z0]) return;
+    const long long len = z1 - z0;
+    const long long q0 = z0 + len * blockIdx.y / gridDim.y, q1 = z0 + len * (blockIdx.y + 1) / gridDim.y;
     const int m = a.m;
     const size_t mm = (size_t)m * m;
-    for (long long k = z0 + warp; k < z1; k += nw) {
+    for (long long k = q0 + warp; k < q1; k += nw) {
         const double *Ak = a.A + k * mm, *Bk = a.B + k * mm, *Ck = a.C + k * mm;
         const double *xm = a.x + (k - 1) * m, *x0 = a.x + k * m, *xp = a.x + (k + 1) * m;
         const bool lo = k > z0, hi = k + 1 < z1;
-        for (int i = 0; i < m; ++i) {
+        for (int i0 = 0; i0 < m; i0 += 8) {
+            const int i = i0 + rr < m ? i0 + rr : m - 1;  // rows past the end repeat the last one
+            const size_t ro = (size_t)i * m;
             double s = 0.0;
-            for (int j = lane; j < m; j += 32) {
-                s = fma(Bk[(size_t)i * m + j], x0[j], s);
-                if (lo) s = fma(Ak[(size_t)i * m + j], xm[j], s);
-                if (hi) s = fma(Ck[(size_t)i * m + j], xp[j], s);
-            }
+            for (int j0 = cc; j0 < m; j0 += 4 * kResidUnroll) {
+                double vb[kResidUnroll], va[kResidUnroll], vc[kResidUnroll];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) a.r[k * m + i] = a.d[k * m + i] - s;
+                for (int u = 0; u < kResidUnroll; ++u) {
+                    const int j = j0 + 4 * u;
+                    const bool in = j < m;
+                    vb[u] = in ? Bk[ro + j] : 0.0;
+                    va[u] = in && lo ? Ak[ro + j] : 0.0;
+                    vc[u] = in && hi ? Ck[ro + j] : 0.0;
+                }
+#pragma unroll
+                for (int u = 0; u < kResidUnroll; ++u) {
+                    const int j = j0 + 4 * u;
+                    if (j < m) {
+                        s = fma(vb[u], x0[j], s);
+                        if (lo) s = fma(va[u], xm[j], s);
+                        if (hi) s = fma(vc[u], xp[j], s);
+                    }
+                }
+            }
+            s += __shfl_xor_sync(0xffffffffu, s, 1);
+            s += __shfl_xor_sync(0xffffffffu, s, 2);
+            if (cc == 0 && i0 + rr < m) a.r[k * m + i] = a.d[k * m + i] - s;
         }
     }
 }
@@ -750,7 +782,7 @@ extern "C" vx_status vx_btd_solve(vx_btd *h, int n_rays, long long n_zones, cons
     BTD_CU(cudaGetLastError());
     for (int it = 1; it <= h->n_refine; ++it) {
         a.rhs = d;
-        k_btd_resid<<<n_rays, kResidThreads, 0, s>>>(a);
+        k_btd_resid<<<dim3(n_rays, kResidSplit), kResidThreads, 0, s>>>(a);
         BTD_CU(cudaGetLastError());
         a.rhs = h->r;
         if (it == h->n_refine)

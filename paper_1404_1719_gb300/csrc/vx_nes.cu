@@ -325,8 +325,13 @@ __device__ __forceinline__ void nes_unit(const NesCommon &C, const R *sg, const 
     }
 }
 
+// Minimum CTAs per SM the register allocation is bounded for (1: no bound).
+#ifndef VX_NES_MINB
+#define VX_NES_MINB 1
+#endif
+
 template <typename R, bool ADJ, int NP>
-__global__ void __launch_bounds__(kNesBlock) k_nes(const __grid_constant__ NesLaunch<R> L) {
+__global__ void __launch_bounds__(kNesBlock, VX_NES_MINB) k_nes(const __grid_constant__ NesLaunch<R> L) {
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ NesZone zs;
     __shared__ long long s_zone;
