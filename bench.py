@@ -45,10 +45,10 @@ def entries(Z, N):
 
 
 # DRAM bytes (read + write) per zone of the forward + tangent kernel, from one ncu capture of the
-# 200-ray case of this workload (dram__bytes_read.sum + dram__bytes_write.sum = 90.2 + 591.4 MB
-# for 80,000 zones); scaled to a launch by the zone count. Set to None whenever the kernel
-# changes, until it has been captured again.
-TRAFFIC_BYTES_PER_ZONE = 8520
+# 200-ray case of this workload (dram__bytes_read.sum + dram__bytes_write.sum = 91.0 + 591.6 MB
+# for 80,000 zones, profiles/k_pair_mixed_tangents_200rays_pipes.md); scaled to a launch by the
+# zone count. Set to None whenever the kernel changes, until it has been captured again.
+TRAFFIC_BYTES_PER_ZONE = 8532
 # rays of the default workload in --mode spectral (410k zones: 17 GB of blocks)
 SPECTRAL_RAYS = 1024
 
@@ -66,17 +66,18 @@ def algorithmic_flops_per_node(adj: bool) -> int:
 
 def formulation_flops_per_node(adj: bool) -> int:
     """FP32 operations per node in the formulation the kernel evaluates (nodes in mirror pairs
-    tau, -tau; tangents from r^2), same counting: forward 14; with tangents 41, since the blocking
-    factor's three moments then follow per (pair, omega) from the energy tangents' (forward 8 per
-    node + tangents 33)."""
-    return 41 if adj else 14
+    tau, -tau; tangents from r^2), same counting: forward 14; with tangents 38: the forward node
+    plus E (2), r^2 and the four blocked products (6), the T and eta integrands (4) and their six
+    moment FMAs (12); the production tangent's moments follow per (pair, omega) unit as
+    q0 M(O) - M(GTa)."""
+    return 38 if adj else 14
 
 
 # Pipe utilisation of the benchmark's kernels from one ncu capture each (see profiles/; set to
 # None whenever the kernel changes, until it has been captured again): the MUFU (XU) issue
 # fraction of the forward + tangent kernel and the FP64-pipe fraction of the plain FP64 kernel.
-MUFU_FRAC_TANGENT = 0.2418   # profiles/k_pair_mixed_tangents_and_k_pair_fp64_pipes_20rays.md
-FP64_FRAC_FP64FWD = 0.9154
+MUFU_FRAC_TANGENT = 0.2530   # profiles/k_pair_mixed_tangents_200rays_pipes.md
+FP64_FRAC_FP64FWD = 0.9154   # profiles/k_pair_mixed_tangents_and_k_pair_fp64_pipes_20rays.md
 # fraction of the workload's zones the plain FP64 comparison leg evaluates, and its timed launches
 FP64_SAMPLE_FRAC, FP64_REPEATS = 0.05, 3
 # timed launches of the precise-mode leg (after two untimed ones)
@@ -723,7 +724,8 @@ def run_ours(args):
                                       "forward + tangent kernel (profiles/)",
                          "traffic": (TRAFFIC_BYTES_PER_ZONE * Z if (TRAFFIC_BYTES_PER_ZONE and args.workload == WORKLOAD
                                                                     and not fwd_only and not split) else None),
-                         "traffic_note": "ncu DRAM read+write of an 80,000-zone capture, scaled by zone count",
+                         "traffic_note": "ncu DRAM read+write of an 80,000-zone capture, scaled by zone count "
+                                         "(profiles/k_pair_mixed_tangents_200rays_pipes.md)",
                          "peak_note": f"FP32 {nsm} SMs x 128 FMA x 2 x {mhz:.0f} MHz (median SM clock in the run); "
                                       f"probe: {pipes['ffma2']:.1f} FP32 lanes/clk/SM with packed FMAs = "
                                       f"{peak_probe:.1f} TFLOP/s at the same clock",

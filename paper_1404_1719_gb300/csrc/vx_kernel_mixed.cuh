@@ -47,6 +47,16 @@
 #ifndef VX_MO_TANG
 #define VX_MO_TANG 1
 #endif
+// Tangent kernel, packed fast loop (not the precise mode): the production tangent's moments as
+// q0 M(O) - M(GTa) (1) instead of their own accumulation (0); GTp = O q0 - GTa on every node, and
+// since f_ebar <= 1/2 in the eta >= 0 frame, GTp >= O Ebar / 2, so the difference cancels only by
+// about q0 / Ebar on the moment's own weights. 2 of 24 FP32 lane operations per node fewer
+// (GB300, workload 4: 625.0 against 658.3 ms on the same box). Loading each unit's record one
+// unit ahead (626.8 ms), pair reciprocals (631.5 ms) and 32-node chunks (631.0 ms) on top of it
+// measured slower.
+#ifndef VX_TP_DIFF
+#define VX_TP_DIFF 1
+#endif
 // Packed loops: the positron energies of a mirror pair as the electron energies with the lanes
 // exchanged (1; Ebar(tau) = E(-tau) bit for bit) or from their own fused multiply-add (0).
 #ifndef VX_ESWAP
@@ -471,6 +481,7 @@ __device__ __forceinline__ void node_loop(const NodeSm *__restrict__ nd, const N
         const float2 z2 = make_float2(0.f, 0.f);
         float2 P2 = z2, M2 = z2, Z2 = z2;
         float2 TAp = z2, TAm = z2, TAz = z2, TPp = z2, TPm = z2, TPz = z2, ETp = z2, ETm = z2, ETz = z2;
+        constexpr bool TPD = ADJ && VX_TP_DIFF && !PREC;
 #pragma unroll 1
         for (int k0 = 0; k0 < NE / 2; k0 += UM / 2) {
 #pragma unroll
@@ -497,7 +508,7 @@ __device__ __forceinline__ void node_loop(const NodeSm *__restrict__ nd, const N
                 } else {
                     r = make_float2(rcpa(d.x), rcpa(d.y));
                 }
-                if (!(ADJ && VX_MO_TANG)) {
+                if (!(ADJ && VX_MO_TANG) || TPD) {
                     P2 = __ffma2_rn(cpm, r, P2);
                     M2 = __ffma2_rn(cmp, r, M2);
                     Z2 = __ffma2_rn(c00, r, Z2);
@@ -510,22 +521,31 @@ __device__ __forceinline__ void node_loop(const NodeSm *__restrict__ nd, const N
                     const float2 s0 = __ffma2_rn(f, r2, r2), p = __fmul2_rn(t, r2);
                     const float2 a1 = __fmul2_rn(e, s0), a2 = __fmul2_rn(f, p);
                     const float2 ga = __ffma2_rn(a1, E2, __fmul2_rn(a2, Eb2));
-                    const float2 gp = __ffma2_rn(s0, E2, __fmul2_rn(p, Eb2));
                     const float2 ge = __ffma2_rn(a1, mone2, a2);  // a2 - a1
                     TAp = __ffma2_rn(cpm, ga, TAp); TAm = __ffma2_rn(cmp, ga, TAm); TAz = __ffma2_rn(c00, ga, TAz);
-                    TPp = __ffma2_rn(cpm, gp, TPp); TPm = __ffma2_rn(cmp, gp, TPm); TPz = __ffma2_rn(c00, gp, TPz);
+                    if (!TPD) {
+                        const float2 gp = __ffma2_rn(s0, E2, __fmul2_rn(p, Eb2));
+                        TPp = __ffma2_rn(cpm, gp, TPp); TPm = __ffma2_rn(cmp, gp, TPm); TPz = __ffma2_rn(c00, gp, TPz);
+                    }
                     ETp = __ffma2_rn(cpm, ge, ETp); ETm = __ffma2_rn(cmp, ge, ETm); ETz = __ffma2_rn(c00, ge, ETz);
                 }
             }
         }
         if (ADJ) {
             ta.p = TAp.x + TAp.y; ta.m = TAm.x + TAm.y; ta.z = TAz.x + TAz.y;
-            tp.p = TPp.x + TPp.y; tp.m = TPm.x + TPm.y; tp.z = TPz.x + TPz.y;
             et.p = ETp.x + ETp.y; et.m = ETm.x + ETm.y; et.z = ETz.x + ETz.y;
         }
-        if (ADJ && VX_MO_TANG) {
+        if (TPD) {
+            // GTp = O (E + Ebar) - GTa; GTa <= (E + Ebar) O max(f_e, f_ebar) and f_ebar <= 1/2 in
+            // the eta >= 0 frame, so the difference keeps at least the positron's share
+            mo.p = P2.x + P2.y; mo.m = M2.x + M2.y; mo.z = Z2.x + Z2.y;
+            const float q0 = 2.f * (h + Em);
+            tp.p = fmaf(q0, mo.p, -ta.p); tp.m = fmaf(q0, mo.m, -ta.m); tp.z = fmaf(q0, mo.z, -ta.z);
+        } else if (ADJ && VX_MO_TANG) {
+            tp.p = TPp.x + TPp.y; tp.m = TPm.x + TPm.y; tp.z = TPz.x + TPz.y;
             mo_from_tangents(mo, ta, tp, h, Em);
         } else {
+            if (ADJ) { tp.p = TPp.x + TPp.y; tp.m = TPm.x + TPm.y; tp.z = TPz.x + TPz.y; }
             mo.p = P2.x + P2.y; mo.m = M2.x + M2.y; mo.z = Z2.x + Z2.y;
         }
     } else if (MIRROR) {

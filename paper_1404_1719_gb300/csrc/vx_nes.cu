@@ -240,42 +240,63 @@ struct NesMom {
     R m[ADJ ? 3 : 1][3];
 };
 
+// Node constants in shared memory, one aligned record per node (a single shared-memory load):
+// Gauss-Legendre 1 + tau, 1 - tau, weight; Gauss-Laguerre x, T w and e^{eta_s} e^{-x} (both set
+// per zone) and e^{-x}.
+template <typename R>
+struct alignas(4 * sizeof(R)) NesGl {
+    R u, v, w, pad;
+};
+template <typename R>
+struct alignas(4 * sizeof(R)) NesLg {
+    R x, wT, og, g;
+};
+
 template <typename R, bool ADJ, int NP>
-__device__ __forceinline__ void nes_unit(const NesCommon &C, const R *sg, const NesRec<R> &rec, R mu_h, R mu_l,
-                                         R T, R iTl, R one, R esl, NesMom<R, ADJ> &M) {
+__device__ __forceinline__ void nes_unit(const NesCommon &C, const NesGl<R> *gl, const NesLg<R> *lg,
+                                         const NesRec<R> &rec, R mu_h, R mu_l, R T, R iTl, R one, R esl,
+                                         NesMom<R, ADJ> &M) {
     const int np = NP > 0 ? NP : C.n_p;
     // offsets of the panels' ends relative to the Fermi edges, from double-word sums
     const DW<R> em = {rec.em, rec.em_lo}, mu = {mu_h, mu_l}, q0w = {rec.q0, rec.q0_lo};
     const DW<R> emr_w = dw_add(em, dw_neg(mu));        // E_min - mu (mu: the upper edge, q0 >= 0)
     const DW<R> emq_w = dw_add(emr_w, q0w);            // E_min - (mu - q0) (the lower edge)
     const R emr = emr_w.h + emr_w.l, emq = emq_w.h + emq_w.l;
-    const R q0 = rec.q0;
+    const R q0 = rec.q0, nq0 = -q0;
     const R crel = emr > (R)0 ? emr : (R)0;                 // c - mu, c = max(E_min, mu)
     const R brel = emr > -q0 ? emr : -q0;                    // b - mu, b = max(E_min, mu - q0)
     const R arel = emr > brel - (R)kTail * T ? emr : brel - (R)kTail * T;  // a - mu
     const R bq = emq > (R)0 ? emq : (R)0;                    // b - (mu - q0)
     const R aq = bq - (brel - arel);                         // a - (mu - q0)
     for (int q = 0; q < (ADJ ? 3 : 1); ++q) M.m[q][0] = M.m[q][1] = M.m[q][2] = (R)0;
-    auto acc = [&](R wF, R t, R r1, R r2, R E) {
+    // wF: weighted blocking factor F; with the tangents dr = r2 - r1 (dF/deta = F dr) and
+    // omr2 = 1 - r2, where r1 = one/(one + e1s) and r2 = 1/(1 + eb) are the two unblocked factors
+    auto acc = [&](R wF, R t, R dr, R omr2, R E) {
         const R wt = wF * t;
         M.m[0][0] += wF; M.m[0][1] += wt; M.m[0][2] = fma(wt, t, M.m[0][2]);
         if (ADJ) {
-            const R dr = r2 - r1;
-            const R we = wF * dr;                                   // dF/deta = F (r2 - r1)
-            const R wT = wF * fma(dr, E, -((R)1 - r2) * q0);        // T^2 dF/dT
+            const R we = wF * dr;                                   // dF/deta
+            const R wT = wF * fma(dr, E, omr2 * nq0);               // T^2 dF/dT
             const R wet = we * t, wTt = wT * t;
             M.m[2][0] += we; M.m[2][1] += wet; M.m[2][2] = fma(wet, t, M.m[2][2]);
             M.m[1][0] += wT; M.m[1][1] += wTt; M.m[1][2] = fma(wTt, t, M.m[1][2]);
         }
     };
-    const R Em = rec.em;
+    // one Gauss-Legendre node: F = 1/(a b), a = one + e1s, b = 1 + eb; r2 - r1 = F (e1s - one eb)
+    // and 1 - r2 = eb/b = eb F a, free of cancellation
+    auto gl_node = [&](R hw, R t, R e1s, R eb) {
+        const R a = one + e1s;
+        const R F = rc<R>(a * ((R)1 + eb));
+        if (ADJ) acc(hw * F, t, F * fma(-one, eb, e1s), (F * a) * eb, rec.em + t);
+        else acc(hw * F, t, (R)0, (R)0, (R)0);
+    };
     // panels 1 and 2: Gauss-Legendre. x1 = (E - mu)/T, x2 = x1 + q0/T, in log2 units.
     {
         const R h1 = (R)0.5 * (brel - arel), h2 = (R)0.5 * (crel - brel);
         const R X2a = aq * iTl;                    // x2 at a, anchored at the lower edge
         const R X2b = bq * iTl;                    // x2 at b
-        const R X1c = crel * iTl;                  // x1 at c, anchored at the upper edge
-        const R q0l = q0 * iTl;
+        const R X1c = crel * iTl + esl;            // x1 at c, anchored at the upper edge, + eta_s
+        const R c1 = esl - q0 * iTl;               // x1 + eta_s = x2 + c1
         const R t1 = arel - emr, t2 = brel - emr;  // t at a and at b
         const R h1l = h1 * iTl, h2l = h2 * iTl;
         // An empty panel (its ends clipped together at E_min) is skipped: there the exponent
@@ -283,44 +304,38 @@ __device__ __forceinline__ void nes_unit(const NesCommon &C, const R *sg, const 
         if (h1 > (R)0) {
 #pragma unroll 4
             for (int k = 0; k < np; ++k) {  // panel 1: [a, b], b the lower edge, X1 <= X2 <= 0
-                const R u = sg[k], wk = sg[2 * kNesMaxP + k];
-                const R X2 = fma(h1l, u, X2a);
-                const R X1 = X2 - q0l;
-                const R e1s = e2<R>(X1 + esl);
-                const R eb = e2<R>(-X2);
-                const R F = rc<R>((one + e1s) * ((R)1 + eb));
-                const R t = fma(h1, u, t1);
-                acc(h1 * wk * F, t, F * ((R)1 + eb) * one, F * (one + e1s), Em + t);
+                const NesGl<R> g = gl[k];
+                const R X2 = fma(h1l, g.u, X2a);
+                gl_node(h1 * g.w, fma(h1, g.u, t1), e2<R>(X2 + c1), e2<R>(-X2));
             }
         }
         if (h2 > (R)0) {
 #pragma unroll 4
             for (int k = 0; k < np; ++k) {  // panel 2: [b, c], c = mu, X1 <= 0 <= X2
-                const R u = sg[k], v = sg[kNesMaxP + k], wk = sg[2 * kNesMaxP + k];
-                const R X2 = fma(h2l, u, X2b);
-                const R X1 = fma(-h2l, v, X1c);
-                const R e1s = e2<R>(X1 + esl);
-                const R eb = e2<R>(-X2);
-                const R F = rc<R>((one + e1s) * ((R)1 + eb));
-                const R t = fma(h2, u, t2);
-                acc(h2 * wk * F, t, F * ((R)1 + eb) * one, F * (one + e1s), Em + t);
+                const NesGl<R> g = gl[k];
+                const R X2 = fma(h2l, g.u, X2b);
+                gl_node(h2 * g.w, fma(h2, g.u, t2), e2<R>(fma(-h2l, g.v, X1c)), e2<R>(-X2));
             }
         }
     }
     // panel 3: Gauss-Laguerre above c, E = c + T x: e^x F = 1 / ((one g + A)(1 + B g)), g = e^{-x}.
-    // A overflows (to inf, Fx = 0) only where the unit lies more than the format's range above the
-    // Fermi edge; 1/(1 + B g) is then formed directly rather than as 0 * inf.
+    // Where A overflows (the unit lies more than the format's range above the Fermi edge) every
+    // node's F is below the format's range: the panel adds nothing.
     {
         const R A = e2<R>(crel * iTl + esl);   // e^{(c - mu)/T} e^{eta_s}
         const R B = e2<R>(-(crel + q0) * iTl);  // e^{-(c - mu + q0)/T}
         const R t3 = crel - emr;
+        if (isfinite(A)) {
 #pragma unroll 4
-        for (int k = 0; k < np; ++k) {
-            const R x = sg[3 * kNesMaxP + k], wk = sg[4 * kNesMaxP + k], g = sg[5 * kNesMaxP + k];
-            const R og = one * g, bg = (R)1 + B * g;
-            const R Fx = rc<R>((og + A) * bg);
-            const R t = fma(T, x, t3);
-            acc(T * wk * Fx, t, Fx * bg * og, ADJ ? rc<R>(bg) : (R)0, Em + t);
+            for (int k = 0; k < np; ++k) {
+                const NesLg<R> g = lg[k];
+                const R Bg = B * g.g, s = g.og + A;
+                const R Fx = rc<R>(s * ((R)1 + Bg));
+                const R t = fma(T, g.x, t3);
+                // r2 = 1/(1 + B g) = Fx s, r1 = og/(og + A): r2 - r1 = Fx (A - og B g), 1 - r2 = B g Fx s
+                if (ADJ) acc(g.wT * Fx, t, Fx * fma(-g.og, Bg, A), (Bg * Fx) * s, rec.em + t);
+                else acc(g.wT * Fx, t, (R)0, (R)0, (R)0);
+            }
         }
     }
 }
@@ -335,7 +350,8 @@ __global__ void __launch_bounds__(kNesBlock, VX_NES_MINB) k_nes(const __grid_con
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ NesZone zs;
     __shared__ long long s_zone;
-    __shared__ R sg[6 * kNesMaxP];
+    __shared__ NesGl<R> sgl[kNesMaxP];
+    __shared__ NesLg<R> slg[kNesMaxP];
     __shared__ R zr[6];  // mu (value, remainder), T, log2(e)/T, e^{eta_s}, eta_s log2(e)
     const NesCommon &C = L.c;
     const int N = C.N, N2 = N * N, S = C.S;
@@ -347,12 +363,12 @@ __global__ void __launch_bounds__(kNesBlock, VX_NES_MINB) k_nes(const __grid_con
     R *vec = dE + N2;                 // [4][S][N] w_j (J_j, 1 - J_j, H_j, H_j) of the zone
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
     for (int k = tid; k < C.n_p; k += blockDim.x) {
-        sg[k] = (R)C.gu[k];
-        sg[kNesMaxP + k] = (R)C.gv[k];
-        sg[2 * kNesMaxP + k] = (R)C.gw[k];
-        sg[3 * kNesMaxP + k] = (R)C.lx[k];
-        sg[4 * kNesMaxP + k] = (R)C.lw[k];
-        sg[5 * kNesMaxP + k] = (R)C.lg[k];
+        sgl[k].u = (R)C.gu[k];
+        sgl[k].v = (R)C.gv[k];
+        sgl[k].w = (R)C.gw[k];
+        sgl[k].pad = (R)0;
+        slg[k].x = (R)C.lx[k];
+        slg[k].g = (R)C.lg[k];
     }
     for (int e = tid; e < N2; e += blockDim.x) dE[e] = (R)fabs(C.eps[e / N] - C.eps[e % N]);
     validate_offsets(L.off, L.n_rays, L.Z, L.flag);
@@ -378,6 +394,10 @@ __global__ void __launch_bounds__(kNesBlock, VX_NES_MINB) k_nes(const __grid_con
                     zr[4] = (R)zs.scale;
                     zr[5] = (R)(etas * 1.4426950408889634);
                     zs.iT2 = 1.0 / (T * T);
+                    for (int k = 0; k < C.n_p; ++k) {  // the Laguerre panel's zone factors
+                        slg[k].wT = (R)(T * C.lw[k]);
+                        slg[k].og = (R)(zs.scale * C.lg[k]);
+                    }
                 }
             }
         }
@@ -416,7 +436,7 @@ __global__ void __launch_bounds__(kNesBlock, VX_NES_MINB) k_nes(const __grid_con
             if (active && p < C.npair) {
                 const NesRec<R> rec = L.tab[(size_t)p * C.n_mu + m];
                 NesMom<R, ADJ> M;
-                nes_unit<R, ADJ, NP>(C, sg, rec, mu_h, mu_l, T, iTl, one, esl, M);
+                nes_unit<R, ADJ, NP>(C, sgl, slg, rec, mu_h, mu_l, T, iTl, one, esl, M);
 #pragma unroll
                 for (int q = 0; q < NQ; ++q) {
                     const R kI = fma(rec.aI, M.m[q][0], fma(rec.bI, M.m[q][1], rec.c * M.m[q][2]));
