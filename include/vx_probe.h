@@ -28,11 +28,14 @@ typedef struct {
     double dfma;   /* FP64 fused multiply-adds per SM per clock                                   */
     double ex2;    /* MUFU ex2.approx.f32 results per SM per clock                                */
     double rcp;    /* MUFU rcp.approx.f32 results per SM per clock                                */
+    double mma_tf32; /* multiply-adds per SM per clock of warp-level mma.sync m16n8k8 TF32 (FP32
+                      * accumulate), the legacy tensor-core path                                   */
+    double mma_bf16; /* the same for mma.sync m16n8k16 BF16                                         */
     double sm_mhz; /* SM clock while the FFMA probe ran (clock64 against the global timer)        */
     int n_sm;      /* SMs of the device                                                           */
 } vx_pipe_rates;
 
-/* Runs the five probes on the current device (about 0.1 s of GPU time; synchronises `stream`)
+/* Runs the seven probes on the current device (about 0.1 s of GPU time; synchronises `stream`)
  * and fills *out. Allocates and frees a few KB of device memory. Errors: VX_ERR_INVALID_ARG
  * (out NULL), VX_ERR_OOM, VX_ERR_CUDA. */
 vx_status vx_probe_pipes(vx_pipe_rates *out, vx_stream stream);

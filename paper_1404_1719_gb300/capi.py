@@ -39,8 +39,8 @@ class vx_out(ctypes.Structure):
 
 class vx_pipe_rates(ctypes.Structure):
     _fields_ = [("ffma", ctypes.c_double), ("ffma2", ctypes.c_double), ("dfma", ctypes.c_double),
-                ("ex2", ctypes.c_double), ("rcp", ctypes.c_double), ("sm_mhz", ctypes.c_double),
-                ("n_sm", ctypes.c_int)]
+                ("ex2", ctypes.c_double), ("rcp", ctypes.c_double), ("mma_tf32", ctypes.c_double),
+                ("mma_bf16", ctypes.c_double), ("sm_mhz", ctypes.c_double), ("n_sm", ctypes.c_int)]
 
 
 class VxError(RuntimeError):

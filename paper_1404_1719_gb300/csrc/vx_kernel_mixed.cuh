@@ -612,13 +612,15 @@ __device__ __forceinline__ void node_loop(const NodeSm *__restrict__ nd, const N
 // (kp, km, k0) and l = 1 (t kp, t km, t k0). (kp, km) are already exchanged for eta < 0.
 struct Coef {
     float kp, km, k0;  // l = 0
-    float lp, lm, l0;  // l = 1
+    float lp, lm, l0;  // l = 1 (precise mode)
+    float t;           // cos(omega): the l = 1 coefficients are t times the l = 0 ones
 };
 
 __device__ __forceinline__ Coef make_coef(float kp, float km, float k0, float t) {
     Coef c;
     c.kp = kp; c.km = km; c.k0 = k0;
     c.lp = t * kp; c.lm = t * km; c.l0 = t * k0;
+    c.t = t;
     return c;
 }
 
@@ -627,18 +629,21 @@ __device__ __forceinline__ Coef make_coef(float kp, float km, float k0, float t)
 // PREC: the l = 1 sums (and, for a quantity whose moments change sign -- SIGNED, the eta
 // tangent -- the l = 0 sums too) go into double-float accumulators; sums of non-negative terms
 // stay FP32, whose rounding is relative to the sum itself.
+// Default mode: the l = 1 terms as cos(omega) times the l = 0 ones, fused into the accumulation.
 template <bool PREC, bool SIGNED = false>
 __device__ __forceinline__ void project(Proj &P, const Mom &M, const Coef &c) {
     const float a = fmaf(c.kp, M.p, fmaf(c.km, M.m, c.k0 * M.z));
     const float b = fmaf(c.km, M.p, fmaf(c.kp, M.m, c.k0 * M.z));
-    const float d = fmaf(c.lp, M.p, fmaf(c.lm, M.m, c.l0 * M.z));
-    const float e = fmaf(c.lm, M.p, fmaf(c.lp, M.m, c.l0 * M.z));
     if (PREC) {
+        const float d = fmaf(c.lp, M.p, fmaf(c.lm, M.m, c.l0 * M.z));
+        const float e = fmaf(c.lm, M.p, fmaf(c.lp, M.m, c.l0 * M.z));
         if (SIGNED) { acc2(P.o0I, P.l0I, a); acc2(P.o0II, P.l0II, b); }
         else { P.o0I += a; P.o0II += b; }
         acc2(P.o1I, P.l1I, d); acc2(P.o1II, P.l1II, e);
     } else {
-        P.o0I += a; P.o0II += b; P.o1I += d; P.o1II += e;
+        P.o0I += a; P.o0II += b;
+        P.o1I = fmaf(c.t, a, P.o1I);
+        P.o1II = fmaf(c.t, b, P.o1II);
     }
 }
 
