@@ -160,14 +160,23 @@ def oracle_sample_rate(b, n_zones: int, jac: bool, spectral: bool = False):
     return entries(n_zones, len(b["eps"])) / dt, out["threads"], dt
 
 
+def sized_sample(run, cap: int, n0: int, target_s: float):
+    """Runs run(n) -> (rate, threads, seconds) on growing samples until one takes at least half of
+    target_s (or the sample reaches cap); a small first sample overestimates the per-unit cost."""
+    n = min(cap, n0)
+    rate, thr, dt = run(n)
+    while dt < 0.5 * target_s and n < cap:
+        n = int(min(cap, max(n + 1, n * target_s / max(dt, 1e-3))))
+        rate, thr, dt = run(n)
+    return rate, thr, dt, n
+
+
 def cpu_baseline(target_s: float = 15.0, workload: int = WORKLOAD, jac: bool = True, spectral: bool = False):
-    b = vx_inputs.make_batch(workload, rays=[0, 1, 2, 3])
-    rate, thr, dt = oracle_sample_rate(b, 16, jac, spectral)
-    n = int(min(len(b["state"]), max(16, 16 * target_s / max(dt, 1e-3))))
-    rate, thr, dt = oracle_sample_rate(b, n, jac, spectral)
+    b = vx_inputs.make_batch(workload, rays=range(16))
+    rate, thr, dt, n = sized_sample(lambda k: oracle_sample_rate(b, k, jac, spectral), len(b["state"]), 64, target_s)
     what = "forward + Jacobian" if jac else ("forward + spectral blocks" if spectral else "forward")
     return {"value": rate, "unit": UNIT, "cores": thr, "kind": "oracle",
-            "sample": f"first {n} zones of workload {workload} (rays 0-3), {what}, FP64, {dt:.1f} s"}
+            "sample": f"first {n} zones of workload {workload} (rays 0-15), {what}, FP64, {dt:.1f} s"}
 
 
 def run_reference(args):
@@ -327,10 +336,16 @@ def run_solve(args):
             "numeric_ok": bool(ok),
         }
         if not args.no_cpu:
-            sub = gen.newton_system([SOLVE_ZONES] * n_rays, n_bins=SOLVE_BINS, seed=rank, rays=range(12))
-            rate, dt = solve_oracle_rate(sub, list(range(12)))
+            sub = gen.newton_system([SOLVE_ZONES] * n_rays, n_bins=SOLVE_BINS, seed=rank, rays=range(64))
+
+            def run_rays(k):
+                r, t = solve_oracle_rate(sub, list(range(k)))
+                return r, 1, t
+
+            rate, _, dt, k = sized_sample(run_rays, 64, 4, 12.0)
             line["cpu_baseline"] = {"value": rate, "unit": "zones/s", "cores": 1, "kind": "oracle",
-                                    "sample": f"rays 0-11 of the workload, banded LU (scipy solve_banded), {dt:.1f} s"}
+                                    "sample": f"rays 0-{k - 1} of the workload, banded LU (scipy solve_banded), "
+                                              f"{dt:.1f} s"}
         print(json.dumps(line))
     if world > 1:
         dist.barrier()
@@ -495,10 +510,8 @@ def run_nes(args):
             "clocks": c, "numeric_ok": bool(ok),
         }
         if not args.no_cpu:
-            bb = vx_inputs.make_batch(WORKLOAD, rays=range(16))
-            _, thr, dt = nes_oracle_rate(bb, 8)
-            n = int(min(len(bb["state"]), max(8, 8 * 15.0 / max(dt, 1e-3))))
-            rate, thr, dt = nes_oracle_rate(bb, n)
+            bb = vx_inputs.make_batch(WORKLOAD, rays=range(48))
+            rate, thr, dt, n = sized_sample(lambda k: nes_oracle_rate(bb, k), len(bb["state"]), 256, 15.0)
             line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": thr, "kind": "oracle",
                                     "sample": f"first {n} zones of workload {WORKLOAD}, NES forward + Jacobian, "
                                               f"FP64, {dt:.1f} s"}

@@ -20,6 +20,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "vx_oracle.c")
 _SRC_NES = os.path.join(_HERE, "vx_nes_oracle.c")
+_SRC_ABS = os.path.join(_HERE, "vx_abs_oracle.c")
 _SO = os.path.join(_HERE, "libvx_oracle.so")
 _lib = None
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -27,13 +28,13 @@ _ip = ctypes.POINTER(ctypes.c_int)
 
 
 def build(force: bool = False) -> str:
-    """Compile vx_oracle.c and vx_nes_oracle.c into libvx_oracle.so (gcc, -O2, OpenMP when
-    available)."""
-    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= max(os.path.getmtime(_SRC),
-                                                                            os.path.getmtime(_SRC_NES)):
+    """Compile vx_oracle.c, vx_nes_oracle.c and vx_abs_oracle.c into libvx_oracle.so (gcc, -O2,
+    OpenMP when available)."""
+    srcs = (_SRC, _SRC_NES, _SRC_ABS)
+    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= max(os.path.getmtime(f) for f in srcs):
         return _SO
     base = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-std=c11",
-            "-o", _SO + ".tmp", _SRC, _SRC_NES, "-lm"]
+            "-o", _SO + ".tmp", *srcs, "-lm"]
     try:
         subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
     except subprocess.CalledProcessError:
@@ -76,6 +77,9 @@ def _load():
                                      ctypes.c_int]
         lib.vxo_nes_eval.restype = ctypes.c_int
         lib.vxo_eos_eta.argtypes = [ctypes.c_long, _dp, _dp, _dp]
+        lib.vxo_abs_eval.argtypes = [ctypes.c_int, _dp, ctypes.c_int, _ip, ctypes.c_double, ctypes.c_longlong, _dp,
+                                     _dp, _dp, _dp, _dp, _dp]
+        lib.vxo_abs_eval.restype = None
         lib.vxo_eos_eta.restype = None
         _lib = lib
     return _lib
@@ -290,3 +294,19 @@ def eos_eta(state):
     eta, deta = np.empty(Z), np.empty((Z, 3))
     _load().vxo_eos_eta(Z, _p(state), _p(eta), _p(deta))
     return eta, deta
+
+
+def abs_evaluate(eps, species, state, g2=1.0, jac=False):
+    """Charged-current absorption and emission rates on free nucleons (vx_abs_oracle.c): j0, chi0,
+    j1, chi1 [Z][S][N] and, with jac=True, the Jacobian [Z][S][N][4][3] (d/dT, d/deta_e, d/dY_e)."""
+    eps = _f64(eps)
+    species = np.ascontiguousarray(species, dtype=np.int32)
+    state = _f64(state)
+    Z, S, N = state.shape[0], len(species), len(eps)
+    out = {k: np.empty((Z, S, N)) for k in ("j0", "chi0", "j1", "chi1")}
+    jc = np.empty((Z, S, N, 4, 3)) if jac else None
+    _load().vxo_abs_eval(N, _p(eps), S, species.ctypes.data_as(_ip), float(g2), Z, _p(state),
+                         *(_p(out[k]) for k in ("j0", "chi0", "j1", "chi1")), _p(jc) if jac else None)
+    if jac:
+        out["jac"] = jc
+    return out
