@@ -49,6 +49,16 @@ def entries(Z, N):
 # for 80,000 zones, profiles/k_pair_mixed_tangents_200rays_pipes.md); scaled to a launch by the
 # zone count. Set to None whenever the kernel changes, until it has been captured again.
 TRAFFIC_BYTES_PER_ZONE = 8532
+def measured_hbm_gbs():
+    """The HBM copy bandwidth measured on this machine's GPUs (MEASURED_PEAKS.json), else the
+    recipe's fallback figure; returns (GB/s, note)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "of measured (MEASURED_PEAKS.json hbm_gbs, a copy)"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "of fallback (6.8 TB/s)"
+
+
 # rays of the default workload in --mode spectral (410k zones: 17 GB of blocks)
 SPECTRAL_RAYS = 1024
 
@@ -523,6 +533,148 @@ def run_nes(args):
     return 0
 
 
+ABS_METRIC = "absorption/emission rate entries/s (zone*species*eps), forward+Jacobian, % HBM peak"
+
+
+def abs_oracle_rate(b, n_zones):
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.abs_evaluate(b["eps"], b["species"], b["state"][:n_zones], jac=True)
+    dt = time.perf_counter() - t0
+    return n_zones * len(b["species"]) * len(b["eps"]) / dt, 1, dt
+
+
+def run_abs(args):
+    """Charged-current absorption and emission on free nucleons: rates + Jacobian of every zone of
+    workload 4's 4096 rays x 400 zones (21 bins, 3 species)."""
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        b = vx_inputs.make_batch(WORKLOAD, rays=range(64))
+        for _ in range(args.warmup):
+            abs_oracle_rate(b, 400)
+        t = [abs_oracle_rate(b, len(b["state"]))[2] for _ in range(args.steps)]
+        ms = 1000 * float(np.mean(t))
+        n = len(b["state"])
+        value = n * len(b["species"]) * len(b["eps"]) / (ms / 1000)
+        print(json.dumps({"impl": "reference", "metric": ABS_METRIC, "value": value, "unit": "entries/s",
+                          "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                          "data": "synthetic",
+                          "config": {"workload": vx_inputs.WORKLOADS[WORKLOAD]["name"] + " absorption+jacobian",
+                                     "zones_per_step": n},
+                          "cpu_baseline": {"value": value, "unit": "entries/s", "cores": 1, "kind": "oracle",
+                                           "sample": f"first {n} zones of workload {WORKLOAD} per step"},
+                          "e2e": {"value": value, "unit": "entries/s", "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0}}))
+        return 0
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    from paper_1404_1719_gb300 import AbsRates, _build, capi
+    _build.build()
+    b = rank_batch(rank, rays=None if args.rays is None else range(args.rays))
+    Z, N, S = b["state"].shape[0], len(b["eps"]), len(b["species"])
+    h_state = torch.from_numpy(np.ascontiguousarray(b["state"])).pin_memory()
+    state = h_state.to(dev)
+    ab = AbsRates(b["eps"], species=b["species"])
+    stream = torch.cuda.current_stream()
+    keys = ("j0", "chi0", "j1", "chi1")
+    out = {k: torch.empty((Z, S, N), dtype=torch.float64, device=dev) for k in keys}
+    jac = torch.empty((Z, S, N, 4, 3), dtype=torch.float64, device=dev)
+    offs = torch.from_numpy(np.asarray(b["ray_offsets"], dtype=np.int32)).to(dev)
+    bt = ab._state_batch(state, offs, None)
+    fwd = capi.vx_out(*(out[k].data_ptr() for k in keys), None)
+
+    def step():
+        capi.vx_abs_adjoint(ab.handle, bt, jac.data_ptr(), fwd, stream.cuda_stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    assert ab.check(), "numeric flag raised during warm-up"
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms_local = e0.elapsed_time(e1) / args.steps
+    ms = max_over_ranks(ms_local, world, dist, dev)
+    ok = ab.check()
+    # end to end through the public API: the state in from pinned host memory, rates and Jacobian back
+    h_out = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in out.items()}
+    h_jac = torch.empty(jac.shape, dtype=jac.dtype, pin_memory=True)
+
+    def step_e2e():
+        state.copy_(h_state, non_blocking=True)
+        res = ab.adjoint(state, forward=True, ray_offsets=offs)
+        for k in keys:
+            h_out[k].copy_(res[k], non_blocking=True)
+        h_jac.copy_(res["jac"], non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+
+    step_e2e()
+    e2e_steps = max(1, min(3, args.steps))
+    t_e2e = time.perf_counter()
+    for _ in range(e2e_steps):
+        step_e2e()
+    ms_e2e = max_over_ranks(1000.0 * (time.perf_counter() - t_e2e) / e2e_steps, world, dist, dev)
+    h2d = h_state.numel() * h_state.element_size()
+    d2h = sum(v.numel() * v.element_size() for v in h_out.values()) + h_jac.numel() * h_jac.element_size()
+    if rank == 0:
+        c = clk.summary()
+        ents = Z * S * N
+        algo_bytes = Z * 32 + ents * 16 * 8  # the state read; four rates and twelve Jacobian entries written
+        achieved = algo_bytes / (ms_local / 1000) / 1e9
+        peak, peak_note = measured_hbm_gbs()
+        line = {
+            "metric": ABS_METRIC, "value": ents * world / (ms / 1000), "unit": "entries/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64 (FP32 occupation factors)", "data": "synthetic",
+            "config": {"workload": vx_inputs.WORKLOADS[WORKLOAD]["name"] + " absorption/emission forward+jacobian"
+                                   + ("" if args.rays is None else f" [first {args.rays} rays]"),
+                       "zones": Z, "bins": N, "species": S,
+                       "l2": "each step writes %.1f GB (> L2), which evicts the %.2f GB state between steps"
+                             % (ents * 16 * 8 / 1e9, Z * 32 / 1e9)},
+            "e2e": {"value": ents * world / (ms_e2e / 1000), "unit": "entries/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e,
+                    "call": "AbsRates.adjoint with the state copied in from and the outputs back to pinned host "
+                            "tensors every step"},
+            "gpu_launches": args.steps,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "bytes_per_step": algo_bytes, "traffic": None,
+                         "peak_note": peak_note,
+                         "bound_note": "streaming kernel; every output entry also costs about 25 FP64 "
+                                       "operations, which bound it on GB300's FP64 pipe before HBM",
+                         "kernel": "k_abs<mixed, tangents>"},
+            "clocks": c, "numeric_ok": bool(ok),
+        }
+        if not args.no_cpu:  # the oracle is fast here: the sample can grow to the whole workload
+            rate, thr, dt, n = sized_sample(lambda k: abs_oracle_rate(b, k), len(b["state"]), 20000, 15.0)
+            line["cpu_baseline"] = {"value": rate, "unit": "entries/s", "cores": thr, "kind": "oracle",
+                                    "sample": f"first {n} zones of workload {WORKLOAD}, absorption + Jacobian, "
+                                              f"FP64, {dt:.1f} s"}
+        print(json.dumps(line))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    ab.close()
+    return 0
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -782,11 +934,12 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU-baseline leg")
     ap.add_argument("--workload", type=int, default=WORKLOAD, choices=sorted(vx_inputs.WORKLOADS),
                     help="synthetic workload (default 4: 4096 rays x 400 zones)")
-    ap.add_argument("--mode", choices=["fwd+jac", "fwd", "spectral", "solve", "nes"], default="fwd+jac",
+    ap.add_argument("--mode", choices=["fwd+jac", "fwd", "spectral", "solve", "nes", "abs"], default="fwd+jac",
                     help="step = forward + Jacobian pass (default), forward rates only, forward + the "
                          "derivatives with respect to the spectra (blocks and J/H VJP), the per-ray "
-                         "block-tridiagonal Newton solve, or the inelastic neutrino-electron scattering "
-                         "kernel (forward + Jacobian)")
+                         "block-tridiagonal Newton solve, the inelastic neutrino-electron scattering "
+                         "kernel (forward + Jacobian), or the absorption and emission rates on nucleons "
+                         "(forward + Jacobian)")
     ap.add_argument("--quad", choices=["standard", "split"], default="standard",
                     help="discrete rule in electron energy: standard, or split at the Fermi edge (VX_QUAD_SPLIT)")
     ap.add_argument("--rays", type=int, default=None,
@@ -796,6 +949,8 @@ def main():
         return run_solve(args)
     if args.mode == "nes":
         return run_nes(args)
+    if args.mode == "abs":
+        return run_abs(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -30,11 +30,15 @@ extern "C" {
  * Errors: VX_ERR_INVALID_ARG (n_zones < 0, NULL or non-device state with n_zones > 0). */
 vx_status vx_eos_eta(long long n_zones, double *state, double *deta, vx_stream stream);
 
-/* Chain rule for jacobians laid out [Z][rows][3] with columns d/dT (at fixed eta_e), d/deta_e and a
- * third column that is ignored (the rate kernels' [Z][S][N][4][3] has rows = 4 S N and Y_e there):
- * writes jac_out [Z][rows][3] = (d/dT, d/dY_e, d/drho) at fixed (rho, Y_e), (T, rho) and (T, Y_e):
- *   d/dT|_{rho,Ye} = d/dT|_eta + d/deta * deta/dT,  d/dY_e = d/deta * deta/dY_e,
- *   d/drho = d/deta * deta/drho,  with deta from vx_eos_eta. jac_out may equal jac_in.
+/* Chain rule for jacobians laid out [Z][rows][3] with columns d/dT (at fixed eta_e), d/deta_e and
+ * d/dY_e at fixed (T, eta_e, rho) (the rate kernels' [Z][S][N][4][3] has rows = 4 S N; that
+ * column is zero for the pair and scattering kernels, whose rates depend on Y_e only through
+ * eta_e): writes jac_out [Z][rows][3] = (d/dT, d/dY_e, d/drho) at fixed (rho, Y_e), (T, rho) and
+ * (T, Y_e):
+ *   d/dT|_{rho,Ye} = d/dT|_eta + d/deta * deta/dT,  d/dY_e = d/dY_e|_eta + d/deta * deta/dY_e,
+ *   d/drho = d/deta * deta/drho,  with deta from vx_eos_eta. A rate with its own dependence on rho
+ *   at fixed eta_e (the absorption rates of vx_abs.h: rate / rho) needs that term added by the
+ *   caller. jac_out may equal jac_in.
  * Errors: VX_ERR_INVALID_ARG (negative sizes, NULL or non-device arrays with work to do). */
 vx_status vx_eos_chain(long long n_zones, int rows, const double *deta, const double *jac_in, double *jac_out,
                        vx_stream stream);

@@ -12,7 +12,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libvx_rates.so")
 SOURCES = ["vx_rates.cu", "vx_mixed_fwd_b2.cu", "vx_mixed_fwd_b3.cu", "vx_mixed_adj_b2.cu", "vx_mixed_adj_b3.cu",
            "vx_mixed_fwd_b2p.cu", "vx_mixed_fwd_b3p.cu", "vx_mixed_adj_b2p.cu", "vx_mixed_adj_b3p.cu",
-           "vx_fp64.cu", "vx_btd.cu", "vx_probe.cu", "vx_nes.cu"]
+           "vx_fp64.cu", "vx_btd.cu", "vx_probe.cu", "vx_nes.cu", "vx_abs.cu"]
 HEADERS = ["vx_internal.h", "vx_kernel_mixed.cuh", "vx_mixed_inst.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
@@ -28,7 +28,7 @@ def _stale() -> bool:
         return True
     t = os.path.getmtime(LIB)
     deps = [os.path.join(CSRC, f) for f in SOURCES + HEADERS] + [os.path.join(INCLUDE, h)
-                                                                  for h in ("vx_rates.h", "vx_btd.h", "vx_probe.h", "vx_nes.h", "vx_eos.h")]
+                                                                  for h in ("vx_rates.h", "vx_btd.h", "vx_probe.h", "vx_nes.h", "vx_eos.h", "vx_abs.h")]
     return any(os.path.getmtime(d) > t for d in deps)
 
 

@@ -54,7 +54,8 @@ SYMBOLS = ("vx_rates_create", "vx_rates_eval", "vx_rates_adjoint", "vx_rates_che
            "vx_rates_eval_noalloc", "vx_rates_spectral", "vx_rates_eval_host", "vx_rates_adjoint_host",
            "vx_rates_spectral_host", "vx_btd_create", "vx_btd_solve", "vx_btd_check", "vx_btd_destroy",
            "vx_probe_pipes", "vx_nes_create", "vx_nes_eval", "vx_nes_adjoint", "vx_nes_check", "vx_nes_destroy",
-           "vx_eos_eta", "vx_eos_chain")
+           "vx_eos_eta", "vx_eos_chain", "vx_abs_create", "vx_abs_eval", "vx_abs_adjoint", "vx_abs_check",
+           "vx_abs_destroy")
 
 _lib = None
 
@@ -121,6 +122,17 @@ def lib(path: str | None = None):
     L.vx_nes_check.restype = ctypes.c_int
     L.vx_nes_destroy.argtypes = [ctypes.c_void_p]
     L.vx_nes_destroy.restype = None
+    L.vx_abs_create.argtypes = [ctypes.POINTER(vx_config), ctypes.POINTER(ctypes.c_void_p)]
+    L.vx_abs_create.restype = ctypes.c_int
+    L.vx_abs_eval.argtypes = [ctypes.c_void_p, ctypes.POINTER(vx_batch), ctypes.POINTER(vx_out), ctypes.c_void_p]
+    L.vx_abs_eval.restype = ctypes.c_int
+    L.vx_abs_adjoint.argtypes = [ctypes.c_void_p, ctypes.POINTER(vx_batch), ctypes.c_void_p, ctypes.POINTER(vx_out),
+                                 ctypes.c_void_p]
+    L.vx_abs_adjoint.restype = ctypes.c_int
+    L.vx_abs_check.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    L.vx_abs_check.restype = ctypes.c_int
+    L.vx_abs_destroy.argtypes = [ctypes.c_void_p]
+    L.vx_abs_destroy.restype = None
     L.vx_eos_eta.argtypes = [ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     L.vx_eos_eta.restype = ctypes.c_int
     L.vx_eos_chain.argtypes = [ctypes.c_longlong, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -274,6 +286,34 @@ def vx_nes_check(h, stream: int = 0) -> int:
 
 def vx_nes_destroy(h) -> None:
     lib().vx_nes_destroy(h)
+
+
+def vx_abs_create(cfg: vx_config) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(lib().vx_abs_create(ctypes.byref(cfg), ctypes.byref(h)), "vx_abs_create")
+    return h
+
+
+def vx_abs_eval(h, batch: vx_batch, out: vx_out, stream: int = 0) -> None:
+    _check(lib().vx_abs_eval(h, ctypes.byref(batch), ctypes.byref(out), ctypes.c_void_p(stream)), "vx_abs_eval")
+
+
+def vx_abs_adjoint(h, batch: vx_batch, jac: int | None, fwd: vx_out | None, stream: int = 0) -> None:
+    _check(lib().vx_abs_adjoint(h, ctypes.byref(batch), ctypes.c_void_p(jac or 0),
+                                ctypes.byref(fwd) if fwd is not None else None, ctypes.c_void_p(stream)),
+           "vx_abs_adjoint")
+
+
+def vx_abs_check(h, stream: int = 0) -> int:
+    """VX_OK or VX_ERR_NUMERIC (other failures raise)."""
+    st = lib().vx_abs_check(h, ctypes.c_void_p(stream))
+    if st not in (VX_OK, VX_ERR_NUMERIC):
+        raise VxError(st, "vx_abs_check")
+    return st
+
+
+def vx_abs_destroy(h) -> None:
+    lib().vx_abs_destroy(h)
 
 
 def vx_eos_eta(n_zones: int, state: int, deta: int | None, stream: int = 0) -> None:

@@ -1,0 +1,353 @@
+// vx_abs.cu -- charged-current absorption and emission on free nucleons (include/vx_abs.h).
+//
+// A streaming kernel: every (zone, species, bin) entry is independent and costs a few dozen
+// arithmetic operations against 32 B (rates) or 128 B (rates and Jacobian) of output. A block
+// takes a contiguous range of entries per iteration of a grid-stride loop, so a warp's stores
+// are contiguous; the zone quantities its entries share (1/T, the nucleon densities, the state
+// check) are formed once per zone into shared memory by the block's first threads. The lepton
+// energy E and the prefactor (g2/pi)(1 + 3 gA^2) E^2 of every (species, bin) are formed on the
+// host in FP64 and passed by value.
+// Forms: FP64 (library exp, true division) and mixed, where the occupation's exponential is
+// 2^-y with the integer part of y an exact FP64 power of two and the fraction through MUFU ex2,
+// and 1/(1 + e^-|x|) (between 1/2 and 1) through the FP32 reciprocal; the exponent argument x and
+// every product stay FP64, so the relative error is about 2^-21 over the FP64 normal range (and
+// the exponential follows FP64 into its subnormal range).
+#include "../../include/vx_abs.h"
+#include "vx_internal.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+
+namespace vx {
+vx_status set_error(vx_status s, const char *msg);
+}
+
+namespace {
+
+constexpr double kQ = 1.29333236;            // m_n - m_p, MeV
+constexpr double kGA = 1.2754;               // axial coupling
+constexpr double kMu = 1.66053906660e-24;    // atomic mass unit, g
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kAbsBlock = 256;
+constexpr int kZoneSlots = kAbsBlock + 2;    // zones a block's range of entries can touch (S N >= 1)
+
+vx_status afail(vx_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    return vx::set_error(s, buf);
+}
+
+#define ABS_CU(call)                                                                          \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return afail(e_ == cudaErrorMemoryAllocation ? VX_ERR_OOM : VX_ERR_CUDA, "%s: %s", #call, \
+                         cudaGetErrorString(e_));                                             \
+    } while (0)
+
+vx_status device_ptr(const void *p, size_t align, const char *name) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return afail(VX_ERR_INVALID_ARG, "%s: not a CUDA pointer", name);
+    }
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+        return afail(VX_ERR_INVALID_ARG, "%s must be device memory", name);
+    if ((uintptr_t)p % align) return afail(VX_ERR_INVALID_ARG, "%s must be %zu-byte aligned", name, align);
+    return VX_OK;
+}
+
+// Per (species, bin): lepton energy and prefactor (0 where the reaction is closed); per species
+// whether the lepton is a positron.
+struct AbsConst {
+    int N, S;
+    int anti[3];
+    double E[3][VX_MAX_BINS];
+    double K[3][VX_MAX_BINS];
+};
+
+struct AbsLaunch {
+    AbsConst c;
+    long long Z;
+    const int *off;
+    int n_rays;
+    const double *state;
+    double *j0, *chi0, *j1, *chi1, *jac;
+    int *flag;
+};
+
+__device__ __forceinline__ float ex2f(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcpf(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Occupation 1/(1 + e^x) and 1 - it, without cancellation.
+template <bool F64>
+__device__ __forceinline__ void occupation(double x, double &f, double &omf) {
+    const double ax = fabs(x);
+    double e, r;  // e = e^-|x|, r = 1/(1 + e)
+    if (F64) {
+        e = exp(-ax);
+        r = 1.0 / (1.0 + e);
+    } else {
+        const double y = ax * 1.4426950408889634;  // |x| log2(e)
+        const double n = floor(y);
+        const double fr = (double)ex2f(-(float)(y - n));
+        if (n <= 1022.0)
+            e = fr * __longlong_as_double((long long)(1023 - (int)n) << 52);
+        else if (n <= 1100.0)  // into the subnormal range: two exact powers of two
+            e = fr * 0x1p-511 * __longlong_as_double((long long)(1023 - ((int)n - 511)) << 52);
+        else
+            e = 0.0;
+        r = (double)rcpf((float)(1.0 + e));
+    }
+    if (x > 0.0) {
+        f = e * r;
+        omf = r;
+    } else {
+        f = r;
+        omf = e * r;
+    }
+}
+
+template <bool F64, bool ADJ>
+__global__ void __launch_bounds__(kAbsBlock) k_abs(const __grid_constant__ AbsLaunch L) {
+    __shared__ double ziT[kZoneSlots], zeta[kZoneSlots], znb[kZoneSlots], zYe[kZoneSlots];
+    __shared__ int zbad[kZoneSlots];
+    const AbsConst &C = L.c;
+    const int SN = C.S * C.N;
+    const long long total = L.Z * SN;
+    vx::validate_offsets(L.off, L.n_rays, L.Z, L.flag);
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < total; base += (long long)gridDim.x * blockDim.x) {
+        const long long z0 = base / SN;
+        const long long zlast = min(total - 1, base + (long long)blockDim.x - 1) / SN;
+        const int nz = (int)(zlast - z0 + 1);
+        for (int k = threadIdx.x; k < nz; k += blockDim.x) {
+            const double *st = L.state + 4 * (z0 + k);
+            const double T = st[0], eta = st[1], Ye = st[2], rho = st[3];
+            const bool bad = !(T > 0.0) || !isfinite(T) || !isfinite(eta) || !(Ye >= 0.0 && Ye <= 1.0) ||
+                             !(rho >= 0.0) || !isfinite(rho);
+            zbad[k] = bad;
+            ziT[k] = bad ? 0.0 : 1.0 / T;
+            zeta[k] = eta;
+            zYe[k] = Ye;
+            znb[k] = rho * (1e-39 / kMu);  // baryons per fm^3
+            if (bad) atomicOr(L.flag, VX_FLAG_BAD_STATE);
+        }
+        __syncthreads();
+        const long long e = base + threadIdx.x;
+        if (e < total) {
+            const int k = (int)(e / SN - z0), r = (int)(e % SN), s = r / C.N, i = r % C.N;
+            double j = 0.0, chi = 0.0, d[2][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
+            const double K = C.K[s][i];
+            if (zbad[k]) {
+                j = chi = __longlong_as_double(0x7ff8000000000000ll);
+            } else if (K > 0.0) {
+                const bool anti = C.anti[s] != 0;
+                const double E = C.E[s][i], iT = ziT[k], nb = znb[k], Ye = zYe[k];
+                const double nn = nb * (1.0 - Ye), np = nb * Ye;
+                const double nin = anti ? np : nn, nout = anti ? nn : np;
+                const double x = fma(E, iT, anti ? zeta[k] : -zeta[k]);
+                double f, omf;
+                occupation<F64>(x, f, omf);
+                j = K * nout * f;
+                chi = K * nin * omf;
+                if (ADJ) {
+                    // df/dx = -f (1 - f); dx/dT = -E/T^2; dx/deta = -1 (electron), +1 (positron)
+                    const double g = f * omf, gT = g * E * iT * iT, ge = anti ? -g : g;
+                    d[0][0] = K * nout * gT;   d[0][1] = K * nout * ge;   d[0][2] = K * (anti ? -nb : nb) * f;
+                    d[1][0] = -K * nin * gT;   d[1][1] = -K * nin * ge;   d[1][2] = K * (anti ? nb : -nb) * omf;
+                }
+            }
+            if (L.j0) {
+                L.j0[e] = j;
+                L.chi0[e] = chi;
+                L.j1[e] = zbad[k] ? j : 0.0;
+                L.chi1[e] = zbad[k] ? j : 0.0;
+            }
+            if (ADJ && L.jac) {
+                double *J = L.jac + e * 12;
+                const double zero = zbad[k] ? j : 0.0;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    J[c] = zbad[k] ? j : d[0][c];
+                    J[3 + c] = zbad[k] ? j : d[1][c];
+                    J[6 + c] = zero;
+                    J[9 + c] = zero;
+                }
+            }
+            if (!zbad[k] && !(isfinite(j) && isfinite(chi))) atomicOr(L.flag, VX_FLAG_NONFINITE);
+        }
+        __syncthreads();
+    }
+}
+
+template <bool F64>
+const void *abs_kernel(bool adj) {
+    return adj ? (const void *)k_abs<F64, true> : (const void *)k_abs<F64, false>;
+}
+
+}  // namespace
+
+struct vx_abs {
+    int device = 0, grid = 0;
+    int prec = VX_PREC_MIXED;
+    AbsConst c{};
+    int *d_flag = nullptr;
+};
+
+namespace {
+
+vx_status abs_validate_batch(const vx_abs *h, const vx_batch *b) {
+    if (!h) return afail(VX_ERR_INVALID_ARG, "handle is NULL");
+    if (!b) return afail(VX_ERR_INVALID_ARG, "batch is NULL");
+    if (b->n_zones < 0 || b->n_rays < 0) return afail(VX_ERR_INVALID_ARG, "negative batch size");
+    if (b->n_zones == 0) return VX_OK;
+    vx_status s;
+    if (b->ray_offsets) {
+        if (b->n_rays == 0) return afail(VX_ERR_INVALID_ARG, "n_zones > 0 with no rays");
+        if ((s = device_ptr(b->ray_offsets, 4, "ray_offsets")) != VX_OK) return s;
+    }
+    if (b->n_zones > (1ll << 40)) return afail(VX_ERR_INVALID_ARG, "n_zones too large");
+    return device_ptr(b->state, 8, "state");
+}
+
+vx_status abs_validate_out(const vx_out *o) {
+    vx_status s;
+    const double *a[4] = {o->j0, o->chi0, o->j1, o->chi1};
+    const char *nm[4] = {"out.j0", "out.chi0", "out.j1", "out.chi1"};
+    for (int k = 0; k < 4; ++k)
+        if ((s = device_ptr(a[k], 8, nm[k])) != VX_OK) return s;
+    if (o->phi) return afail(VX_ERR_INVALID_ARG, "out.phi must be NULL: these rates have no kernel to dump");
+    return VX_OK;
+}
+
+vx_status abs_run(vx_abs *h, const vx_batch *b, const vx_out *out, double *jac, cudaStream_t s) {
+    AbsLaunch L{};
+    L.c = h->c;
+    L.Z = b->n_zones;
+    L.off = b->ray_offsets;
+    L.n_rays = b->n_rays;
+    L.state = b->state;
+    if (out) { L.j0 = out->j0; L.chi0 = out->chi0; L.j1 = out->j1; L.chi1 = out->chi1; }
+    L.jac = jac;
+    L.flag = h->d_flag;
+    const long long blocks = (b->n_zones * h->c.S * h->c.N + kAbsBlock - 1) / kAbsBlock;
+    const int grid = (int)std::min<long long>(h->grid, blocks);
+    const bool f64 = h->prec == VX_PREC_FP64, adj = jac != nullptr;
+    if (f64) adj ? k_abs<true, true><<<grid, kAbsBlock, 0, s>>>(L) : k_abs<true, false><<<grid, kAbsBlock, 0, s>>>(L);
+    else adj ? k_abs<false, true><<<grid, kAbsBlock, 0, s>>>(L) : k_abs<false, false><<<grid, kAbsBlock, 0, s>>>(L);
+    ABS_CU(cudaGetLastError());
+    return VX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+vx_status vx_abs_create(const vx_config *cfg, vx_abs **out) {
+    if (!out) return afail(VX_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!cfg) return afail(VX_ERR_INVALID_ARG, "config is NULL");
+    if (cfg->n_bins < 1 || cfg->n_bins > VX_MAX_BINS) return afail(VX_ERR_INVALID_ARG, "n_bins %d outside 1..%d", cfg->n_bins, VX_MAX_BINS);
+    if (!cfg->eps) return afail(VX_ERR_INVALID_ARG, "eps is NULL");
+    for (int i = 0; i < cfg->n_bins; ++i)
+        if (!(cfg->eps[i] > 0.0) || !std::isfinite(cfg->eps[i])) return afail(VX_ERR_INVALID_ARG, "eps[%d] must be finite and > 0", i);
+    if (cfg->n_species < 1 || cfg->n_species > 3 || !cfg->species) return afail(VX_ERR_INVALID_ARG, "n_species must be 1..3");
+    for (int s = 0; s < cfg->n_species; ++s) {
+        if (cfg->species[s] < 0 || cfg->species[s] > 2) return afail(VX_ERR_INVALID_ARG, "species[%d] is not a vx_species", s);
+        for (int t = 0; t < s; ++t)
+            if (cfg->species[t] == cfg->species[s]) return afail(VX_ERR_INVALID_ARG, "species listed twice");
+    }
+    if (!std::isfinite(cfg->g2)) return afail(VX_ERR_INVALID_ARG, "g2 must be finite");
+    if (cfg->prec != VX_PREC_MIXED && cfg->prec != VX_PREC_FP64) return afail(VX_ERR_INVALID_ARG, "unknown precision");
+    if (cfg->flags != 0) return afail(VX_ERR_UNSUPPORTED, "flags must be 0 for the absorption rates");
+
+    vx_abs *h = new vx_abs();
+    h->prec = cfg->prec;
+    AbsConst &C = h->c;
+    C.N = cfg->n_bins;
+    C.S = cfg->n_species;
+    const double pref = cfg->g2 / kPi * (1.0 + 3.0 * kGA * kGA);
+    for (int s = 0; s < C.S; ++s) {
+        const int sp = cfg->species[s];
+        C.anti[s] = sp == VX_NU_EBAR;
+        for (int i = 0; i < C.N; ++i) {
+            const double E = sp == VX_NU_EBAR ? cfg->eps[i] - kQ : cfg->eps[i] + kQ;
+            const bool open = sp != VX_NU_X && E > 0.0;
+            C.E[s][i] = open ? E : 0.0;
+            C.K[s][i] = open ? pref * E * E : 0.0;
+        }
+    }
+    cudaDeviceProp prop;
+    if (cudaGetDevice(&h->device) != cudaSuccess || cudaGetDeviceProperties(&prop, h->device) != cudaSuccess) {
+        delete h;
+        return afail(VX_ERR_CUDA, "no CUDA device");
+    }
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, abs_kernel<false>(true), kAbsBlock, 0) != cudaSuccess || occ < 1)
+        occ = 1;
+    h->grid = occ * prop.multiProcessorCount;
+    if (cudaMalloc(&h->d_flag, sizeof(int)) != cudaSuccess || cudaMemset(h->d_flag, 0, sizeof(int)) != cudaSuccess) {
+        vx_abs_destroy(h);
+        return afail(VX_ERR_OOM, "allocation failed");
+    }
+    *out = h;
+    return VX_OK;
+}
+
+vx_status vx_abs_eval(vx_abs *h, const vx_batch *b, const vx_out *out, vx_stream stream) {
+    vx_status st = abs_validate_batch(h, b);
+    if (st != VX_OK) return st;
+    if (!out) return afail(VX_ERR_INVALID_ARG, "out is NULL");
+    if (b->n_zones == 0) return VX_OK;
+    if ((st = abs_validate_out(out)) != VX_OK) return st;
+    return abs_run(h, b, out, nullptr, (cudaStream_t)stream);
+}
+
+vx_status vx_abs_adjoint(vx_abs *h, const vx_batch *b, double *jac, const vx_out *fwd, vx_stream stream) {
+    vx_status st = abs_validate_batch(h, b);
+    if (st != VX_OK) return st;
+    if (!jac && !fwd) return afail(VX_ERR_INVALID_ARG, "jac and fwd are both NULL");
+    if (b->n_zones == 0) return VX_OK;
+    if (jac && (st = device_ptr(jac, 8, "jac")) != VX_OK) return st;
+    if (fwd && (st = abs_validate_out(fwd)) != VX_OK) return st;
+    return abs_run(h, b, fwd, jac, (cudaStream_t)stream);
+}
+
+vx_status vx_abs_check(vx_abs *h, vx_stream stream) {
+    if (!h) return afail(VX_ERR_INVALID_ARG, "handle is NULL");
+    ABS_CU(cudaStreamSynchronize((cudaStream_t)stream));
+    int f = 0;
+    ABS_CU(cudaMemcpy(&f, h->d_flag, sizeof(int), cudaMemcpyDeviceToHost));
+    if (f) {
+        ABS_CU(cudaMemset(h->d_flag, 0, sizeof(int)));
+        return afail(VX_ERR_NUMERIC, "absorption device flag 0x%x (%s%s%s)", f,
+                     (f & VX_FLAG_BAD_STATE) ? "invalid zone state; " : "",
+                     (f & VX_FLAG_NONFINITE) ? "non-finite result; " : "", (f & VX_FLAG_BAD_OFFSETS) ? "invalid ray offsets" : "");
+    }
+    return VX_OK;
+}
+
+void vx_abs_destroy(vx_abs *h) {
+    if (!h) return;
+    cudaDeviceSynchronize();
+    cudaFree(h->d_flag);
+    delete h;
+}
+
+}  // extern "C"

@@ -684,10 +684,10 @@ __global__ void k_eos_chain(long long Z, int rows, const double *deta, const dou
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= Z * rows) return;
     const long long z = e / rows;
-    const double dT = jin[3 * e + 0], dE = jin[3 * e + 1];
+    const double dT = jin[3 * e + 0], dE = jin[3 * e + 1], dY = jin[3 * e + 2];
     const double a = deta[3 * z + 0], b = deta[3 * z + 1], c = deta[3 * z + 2];
     jout[3 * e + 0] = fma(dE, a, dT);
-    jout[3 * e + 1] = dE * b;
+    jout[3 * e + 1] = fma(dE, b, dY);
     jout[3 * e + 2] = dE * c;
 }
 

@@ -106,7 +106,8 @@ def eos_eta(state, stream=None):
 
 def eos_chain(jac, deta, out=None, stream=None):
     """Derivatives at fixed (rho, Y_e) from a kernel Jacobian [Z][..][3] (d/dT at fixed eta, d/deta,
-    ignored): returns [Z][..][3] = (d/dT, d/dY_e, d/drho)."""
+    d/dY_e at fixed eta): returns [Z][..][3] = (d/dT, d/dY_e, d/drho). A rate with its own
+    dependence on rho at fixed eta (the absorption rates: rate / rho) needs that term added."""
     _dev_f64(jac, "jac")
     _dev_f64(deta, "deta", (jac.shape[0], 3))
     if jac.shape[-1] != 3:

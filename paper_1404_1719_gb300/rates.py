@@ -77,6 +77,15 @@ class PairRates:
                 raise ValueError(f"{name} must be a contiguous CUDA float64 tensor of shape {shape}")
             if t.device != self.device:
                 raise ValueError(f"{name} is on {t.device}, the handle on {self.device}")
+        offs, nr = self._offsets(ray_offsets, Z, stream)
+        b = capi.vx_batch(n_rays=nr, n_zones=Z, ray_offsets=None if offs is None else ctypes.cast(offs.data_ptr(), capi._ip),
+                          state=state.data_ptr(), J=J.data_ptr(), H=H.data_ptr())
+        b._keep = offs
+        return b
+
+    def _offsets(self, ray_offsets, Z, stream=None):
+        """Ray offsets as a device int32 tensor (host offsets are checked here and copied) and the
+        ray count; (None, 1) without offsets."""
         offs = None
         nr = 1
         if ray_offsets is not None:
@@ -94,10 +103,7 @@ class PairRates:
                 if stream is not None:
                     offs.record_stream(stream)
             nr = offs.shape[0] - 1
-        b = capi.vx_batch(n_rays=nr, n_zones=Z, ray_offsets=None if offs is None else ctypes.cast(offs.data_ptr(), capi._ip),
-                          state=state.data_ptr(), J=J.data_ptr(), H=H.data_ptr())
-        b._keep = offs
-        return b
+        return offs, nr
 
     def _check_out(self, name, t, shape, host=False):
         """Caller-supplied output (or seed) tensor: float64, contiguous, the given shape, on the

@@ -1,5 +1,6 @@
 """bench.py's reference arms (the oracle timed on the host cores) run without a GPU and print one
-JSON line in the contract's shape, for the default rate step, the Newton solve and the NES kernel."""
+JSON line in the contract's shape, for the default rate step, the Newton solve, the NES kernel and the
+absorption rates."""
 import json
 import os
 import subprocess
@@ -21,7 +22,7 @@ def run_bench(*args):
     return json.loads(lines[0])
 
 
-@pytest.mark.parametrize("mode", [[], ["--mode", "solve"], ["--mode", "nes"]])
+@pytest.mark.parametrize("mode", [[], ["--mode", "solve"], ["--mode", "nes"], ["--mode", "abs"]])
 def test_reference_arm_line(mode):
     d = run_bench("--impl", "reference", "--steps", "1", "--warmup", "0", *mode)
     for k in KEYS:

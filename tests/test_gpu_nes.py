@@ -191,9 +191,10 @@ def test_eos_closure_and_chain_rule_against_oracle():
         tot = eos_chain(jac, deta).cpu().numpy()
         g = jac.cpu().numpy()
         # the chain rule itself, from the kernel's own columns and the closure's derivatives
-        dT, dE = g[..., 0], g[..., 1]
+        dT, dE, dY = g[..., 0], g[..., 1], g[..., 2]
+        assert np.all(dY == 0.0)  # these rates depend on Y_e only through eta_e
         d = deta.cpu().numpy()[:, None, None, None, :]
-        exp = np.stack([dT + dE * d[..., 0], dE * d[..., 1], dE * d[..., 2]], axis=-1)
+        exp = np.stack([dT + dE * d[..., 0], dY + dE * d[..., 1], dE * d[..., 2]], axis=-1)
         size = np.stack([np.abs(dT) + np.abs(dE * d[..., 0]), np.abs(dE * d[..., 1]), np.abs(dE * d[..., 2])], axis=-1)
         assert np.all(np.abs(tot - exp) <= 1e-14 * size)  # the T column is a sum that can cancel
         assert np.any(tot[..., 1] != 0.0)  # the Y_e column
