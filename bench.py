@@ -657,8 +657,9 @@ def run_abs(args):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "bytes_per_step": algo_bytes, "traffic": None,
                          "peak_note": peak_note,
-                         "bound_note": "streaming kernel; every output entry also costs about 25 FP64 "
-                                       "operations, which bound it on GB300's FP64 pipe before HBM",
+                         "bound_note": "streaming kernel: FP32 occupations on FP32-pair exponent arguments, "
+                                       "Jacobian stores staged through shared memory "
+                                       "(profiles/k_abs_tangents_1024rays.md)",
                          "kernel": "k_abs<mixed, tangents>"},
             "clocks": c, "numeric_ok": bool(ok),
         }

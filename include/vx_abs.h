@@ -36,8 +36,10 @@ extern "C" {
 typedef struct vx_abs vx_abs;
 
 /* Creates a handle. Reads from cfg: n_bins (1..32), eps (host, positive), n_species (1..3),
- * species (host, distinct vx_species values), g2 (the rates' global scale, finite) and prec
- * (VX_PREC_MIXED: FP32 Fermi factors with FP64 prefactors; VX_PREC_FP64: FP64 throughout).
+ * species (host, distinct vx_species values), g2 (the rates' global scale, finite, non-zero
+ * magnitudes of any size) and prec (VX_PREC_MIXED: the exponent argument in FP64, the occupation
+ * factors and products in FP32 with their powers of two carried exactly into the FP64 results,
+ * relative error ~1e-6; the T-derivative needs T >= 1e-15 MeV there. VX_PREC_FP64: FP64 throughout).
  * weights, n_mu, n_e, sin2w, norm and eta_fp64 are not used; flags must be 0.
  * Errors: VX_ERR_INVALID_ARG, VX_ERR_UNSUPPORTED (flags), VX_ERR_OOM, VX_ERR_CUDA. */
 vx_status vx_abs_create(const vx_config *cfg, vx_abs **out);

@@ -2,16 +2,21 @@
 //
 // A streaming kernel: every (zone, species, bin) entry is independent and costs a few dozen
 // arithmetic operations against 32 B (rates) or 128 B (rates and Jacobian) of output. A block
-// takes a contiguous range of entries per iteration of a grid-stride loop, so a warp's stores
+// takes a contiguous range of whole zones per iteration of a grid-stride loop, so a warp's stores
 // are contiguous; the zone quantities its entries share (1/T, the nucleon densities, the state
 // check) are formed once per zone into shared memory by the block's first threads. The lepton
 // energy E and the prefactor (g2/pi)(1 + 3 gA^2) E^2 of every (species, bin) are formed on the
-// host in FP64 and passed by value.
-// Forms: FP64 (library exp, true division) and mixed, where the occupation's exponential is
-// 2^-y with the integer part of y an exact FP64 power of two and the fraction through MUFU ex2,
-// and 1/(1 + e^-|x|) (between 1/2 and 1) through the FP32 reciprocal; the exponent argument x and
-// every product stay FP64, so the relative error is about 2^-21 over the FP64 normal range (and
-// the exponential follows FP64 into its subnormal range).
+// host in FP64 and passed by value. (A block takes whole zones, and a thread the same entry of
+// each: no 64-bit integer division per entry, which would run on the FP64 unit.)
+// Forms: FP64 (library exp, true division, FP64 products) and mixed. GB300 issues FP64 about 75x
+// slower than FP32, so the mixed form runs no FP64 arithmetic per entry. The exponent argument
+// x = E/T -+ eta (up to ~1e3, more than FP32's 24 bits can resolve) is formed as an FP32 pair
+// (double-float: exact products by FMA, two-sum) from pairs of E, 1/T and eta, and so is
+// |x| log2(e) = n + fr with n an integer: the small occupation is (2^-fr r) 2^-n and the large one
+// r = 1/(1 + 2^-fr 2^-n), 2^-fr from MUFU ex2 and r from the FP32 reciprocal. Every product is an
+// FP32 mantissa, and the powers of two (2^-n, and that of the prefactor, so any global scale g2
+// fits) are put into the FP64 result's exponent field with integer operations. Relative error
+// about 2^-21 over the FP64 range.
 #include "../../include/vx_abs.h"
 #include "vx_internal.h"
 
@@ -34,7 +39,8 @@ constexpr double kGA = 1.2754;               // axial coupling
 constexpr double kMu = 1.66053906660e-24;    // atomic mass unit, g
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kAbsBlock = 256;
-constexpr int kZoneSlots = kAbsBlock + 2;    // zones a block's range of entries can touch (S N >= 1)
+constexpr int kZoneSlots = kAbsBlock;        // zones a block takes per iteration (S N >= 1)
+static_assert(kAbsBlock >= 3 * VX_MAX_BINS, "a block must hold a whole zone's entries");
 
 vx_status afail(vx_status s, const char *fmt, ...) {
     char buf[512];
@@ -72,6 +78,10 @@ struct AbsConst {
     int anti[3];
     double E[3][VX_MAX_BINS];
     double K[3][VX_MAX_BINS];
+    float Ef[3][VX_MAX_BINS];  // mixed form: E as an FP32 pair, and K = Kf 2^kK with Kf in [1, 2)
+    float El[3][VX_MAX_BINS];
+    float Kf[3][VX_MAX_BINS];
+    int kK[3][VX_MAX_BINS];
 };
 
 struct AbsLaunch {
@@ -93,6 +103,28 @@ __device__ __forceinline__ float rcpf(float x) {
     float y;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
+}
+
+// v 2^shift as an FP64 value, for v an FP32 value, with integer operations only (no FP64
+// instruction, even predicated off): the FP64 exponent is set from v's bits; results below the
+// FP64 normal range get the subnormal encoding of v's 24-bit significand (truncated), an FP32 zero
+// or subnormal v gives a zero, a non-finite v the same non-finite FP64 value.
+__device__ __forceinline__ double pow2scaled(float v, int shift) {
+    const unsigned u = __float_as_uint(v);
+    const int ev = (int)((u >> 23) & 0xffu);
+    const unsigned long long sign = (unsigned long long)(u >> 31) << 63, m = u & 0x7fffffu;
+    unsigned long long bits;
+    const int e64 = ev - 127 + 1023 + shift;
+    if (ev == 0) bits = sign;
+    else if (ev == 255) bits = sign | 0x7ff0000000000000ull | (m << 29);
+    else if (e64 >= 2047) bits = sign | 0x7ff0000000000000ull;
+    else if (e64 >= 1) bits = sign | ((unsigned long long)e64 << 52) | (m << 29);
+    else {  // subnormal: value = S 2^(e64 + 28) 2^-1074, S the 24-bit significand
+        const unsigned long long S = m | 0x800000ull;
+        const int sh = e64 + 28;
+        bits = sign | (sh >= 0 ? (S << sh) : (sh > -25 ? (S >> -sh) : 0ull));
+    }
+    return __longlong_as_double((long long)bits);
 }
 
 // Occupation 1/(1 + e^x) and 1 - it, without cancellation.
@@ -127,36 +159,51 @@ __device__ __forceinline__ void occupation(double x, double &f, double &omf) {
 template <bool F64, bool ADJ>
 __global__ void __launch_bounds__(kAbsBlock) k_abs(const __grid_constant__ AbsLaunch L) {
     __shared__ double ziT[kZoneSlots], zeta[kZoneSlots], znb[kZoneSlots], zYe[kZoneSlots];
+    __shared__ float znnf[kZoneSlots], znpf[kZoneSlots], znbf[kZoneSlots], ziT2f[kZoneSlots];
+    __shared__ float ziTh[kZoneSlots], ziTl[kZoneSlots], zetah[kZoneSlots], zetal[kZoneSlots];
     __shared__ int zbad[kZoneSlots];
+    // the block's Jacobian entries, staged so that the stores are contiguous (row stride 13: banks)
+    __shared__ double sj[ADJ ? kAbsBlock * 13 : 1];
     const AbsConst &C = L.c;
     const int SN = C.S * C.N;
-    const long long total = L.Z * SN;
+    // a block takes nzb whole zones per iteration; thread t keeps the same (zone, species, bin)
+    // offsets throughout, so no 64-bit division runs per entry
+    const int nzb = SN >= (int)blockDim.x ? 1 : (int)blockDim.x / SN;
+    const int t = threadIdx.x, k = t / SN, r = t - k * SN, s = r / C.N, i = r - s * C.N;
+    const bool act = k < nzb;
     vx::validate_offsets(L.off, L.n_rays, L.Z, L.flag);
-    for (long long base = (long long)blockIdx.x * blockDim.x; base < total; base += (long long)gridDim.x * blockDim.x) {
-        const long long z0 = base / SN;
-        const long long zlast = min(total - 1, base + (long long)blockDim.x - 1) / SN;
-        const int nz = (int)(zlast - z0 + 1);
-        for (int k = threadIdx.x; k < nz; k += blockDim.x) {
-            const double *st = L.state + 4 * (z0 + k);
+    for (long long zb = (long long)blockIdx.x * nzb; zb < L.Z; zb += (long long)gridDim.x * nzb) {
+        const int nz = (int)min((long long)nzb, L.Z - zb);
+        for (int kk = threadIdx.x; kk < nz; kk += blockDim.x) {
+            const double *st = L.state + 4 * (zb + kk);
             const double T = st[0], eta = st[1], Ye = st[2], rho = st[3];
             const bool bad = !(T > 0.0) || !isfinite(T) || !isfinite(eta) || !(Ye >= 0.0 && Ye <= 1.0) ||
                              !(rho >= 0.0) || !isfinite(rho);
-            zbad[k] = bad;
-            ziT[k] = bad ? 0.0 : 1.0 / T;
-            zeta[k] = eta;
-            zYe[k] = Ye;
-            znb[k] = rho * (1e-39 / kMu);  // baryons per fm^3
+            zbad[kk] = bad;
+            ziT[kk] = bad ? 0.0 : 1.0 / T;
+            zeta[kk] = eta;
+            zYe[kk] = Ye;
+            znb[kk] = rho * (1e-39 / kMu);  // baryons per fm^3
+            if (!F64) {
+                znbf[kk] = (float)znb[kk];
+                znnf[kk] = (float)(znb[kk] * (1.0 - Ye));
+                znpf[kk] = (float)(znb[kk] * Ye);
+                ziT2f[kk] = (float)fmin(ziT[kk] * ziT[kk], 1e30);  // T >= 1e-15 MeV for the T-derivative
+                ziTh[kk] = (float)ziT[kk];
+                ziTl[kk] = (float)(ziT[kk] - (double)ziTh[kk]);
+                zetah[kk] = (float)eta;
+                zetal[kk] = (float)(eta - (double)zetah[kk]);
+            }
             if (bad) atomicOr(L.flag, VX_FLAG_BAD_STATE);
         }
         __syncthreads();
-        const long long e = base + threadIdx.x;
-        if (e < total) {
-            const int k = (int)(e / SN - z0), r = (int)(e % SN), s = r / C.N, i = r % C.N;
+        if (act && k < nz) {
+            const long long e = (zb + k) * SN + r;
             double j = 0.0, chi = 0.0, d[2][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
             const double K = C.K[s][i];
             if (zbad[k]) {
                 j = chi = __longlong_as_double(0x7ff8000000000000ll);
-            } else if (K > 0.0) {
+            } else if (K > 0.0 && F64) {
                 const bool anti = C.anti[s] != 0;
                 const double E = C.E[s][i], iT = ziT[k], nb = znb[k], Ye = zYe[k];
                 const double nn = nb * (1.0 - Ye), np = nb * Ye;
@@ -172,6 +219,43 @@ __global__ void __launch_bounds__(kAbsBlock) k_abs(const __grid_constant__ AbsLa
                     d[0][0] = K * nout * gT;   d[0][1] = K * nout * ge;   d[0][2] = K * (anti ? -nb : nb) * f;
                     d[1][0] = -K * nin * gT;   d[1][1] = -K * nin * ge;   d[1][2] = K * (anti ? nb : -nb) * omf;
                 }
+            } else if (C.Kf[s][i] > 0.f) {
+                const bool anti = C.anti[s] != 0;
+                // x = E/T -+ eta as an FP32 pair: E (1/T) exactly by FMA, then a two-sum with -+eta
+                // (explicitly rounded operations: no contraction into FMAs may change the pair)
+                const float Eh = C.Ef[s][i], El = C.El[s][i], ih = ziTh[k], il = ziTl[k];
+                const float ph = __fmul_rn(Eh, ih);
+                const float pl = __fadd_rn(fmaf(Eh, ih, -ph), fmaf(Eh, il, __fmul_rn(El, ih)));
+                const float eh = anti ? zetah[k] : -zetah[k], el = anti ? zetal[k] : -zetal[k];
+                const float sh = __fadd_rn(ph, eh), sv = __fsub_rn(sh, ph);
+                const float xl0 = __fadd_rn(__fadd_rn(__fsub_rn(ph, __fsub_rn(sh, sv)), __fsub_rn(eh, sv)), __fadd_rn(pl, el));
+                const float xh = __fadd_rn(sh, xl0), xl = __fsub_rn(xl0, __fsub_rn(xh, sh));
+                // |x| log2(e) = yh + yl as an FP32 pair, then n = floor(yh) and fr = (yh - n) + yl
+                const float ah = fabsf(xh), al = xh < 0.f ? -xl : xl;
+                const float L2h = 1.44269502162933349609375f, L2l = 1.925963033500011079e-8f;
+                const float yh = __fmul_rn(ah, L2h);
+                const float yl = __fadd_rn(fmaf(ah, L2h, -yh), fmaf(ah, L2l, __fmul_rn(al, L2h)));
+                const bool huge = !(yh <= 2000.f);
+                const float nf = huge ? 2000.f : floorf(yh);
+                const int n = (int)nf;
+                const float ef = ex2f(huge ? 0.f : -__fadd_rn(__fsub_rn(yh, nf), yl));  // 2^-fr
+                const float e32 = n < 126 ? ef * __int_as_float((127 - n) << 23) : 0.f; // e^-|x|
+                const float r = rcpf(1.f + e32), sm = ef * r;  // large occupation; small one = sm 2^-n
+                const bool pos = xh > 0.f;
+                const float f = pos ? sm : r, omf = pos ? r : sm;
+                const int kf = C.kK[s][i] - (pos ? n : 0), ko = C.kK[s][i] - (pos ? 0 : n), kg = C.kK[s][i] - n;
+                const float Kf = C.Kf[s][i], nin = anti ? znpf[k] : znnf[k], nout = anti ? znnf[k] : znpf[k];
+                const float Kout = Kf * nout, Kin = Kf * nin;
+                j = pow2scaled(Kout * f, kf);
+                chi = pow2scaled(Kin * omf, ko);
+                if (ADJ) {
+                    const float g = f * omf, gT = g * (C.Ef[s][i] * ziT2f[k]), ge = anti ? -g : g;
+                    const float Kb = Kf * znbf[k];
+                    d[0][0] = pow2scaled(Kout * gT, kg);  d[0][1] = pow2scaled(Kout * ge, kg);
+                    d[0][2] = pow2scaled(anti ? -Kb * f : Kb * f, kf);
+                    d[1][0] = pow2scaled(-Kin * gT, kg);  d[1][1] = pow2scaled(-Kin * ge, kg);
+                    d[1][2] = pow2scaled(anti ? Kb * omf : -Kb * omf, ko);
+                }
             }
             if (L.j0) {
                 L.j0[e] = j;
@@ -180,7 +264,7 @@ __global__ void __launch_bounds__(kAbsBlock) k_abs(const __grid_constant__ AbsLa
                 L.chi1[e] = zbad[k] ? j : 0.0;
             }
             if (ADJ && L.jac) {
-                double *J = L.jac + e * 12;
+                double *J = sj + t * 13;
                 const double zero = zbad[k] ? j : 0.0;
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
@@ -190,7 +274,21 @@ __global__ void __launch_bounds__(kAbsBlock) k_abs(const __grid_constant__ AbsLa
                     J[9 + c] = zero;
                 }
             }
-            if (!zbad[k] && !(isfinite(j) && isfinite(chi))) atomicOr(L.flag, VX_FLAG_NONFINITE);
+            // (the FP64 class test on the FP64 pipe: in the mixed form on the results' exponent bits)
+            const long long jb = __double_as_longlong(j), cb = __double_as_longlong(chi);
+            const bool fin = F64 ? (isfinite(j) && isfinite(chi))
+                                 : ((jb & 0x7ff0000000000000ll) != 0x7ff0000000000000ll &&
+                                    (cb & 0x7ff0000000000000ll) != 0x7ff0000000000000ll);
+            if (!zbad[k] && !fin) atomicOr(L.flag, VX_FLAG_NONFINITE);
+        }
+        if (ADJ && L.jac) {  // the staged entries of the block's zones: 12 nz SN consecutive doubles
+            __syncthreads();
+            const int nv = 12 * nz * SN;
+            double *dst = L.jac + zb * SN * 12;
+            for (int q = threadIdx.x; q < nv; q += blockDim.x) {
+                const int ent = q / 12;
+                dst[q] = sj[ent * 13 + (q - ent * 12)];
+            }
         }
         __syncthreads();
     }
@@ -246,7 +344,8 @@ vx_status abs_run(vx_abs *h, const vx_batch *b, const vx_out *out, double *jac, 
     if (out) { L.j0 = out->j0; L.chi0 = out->chi0; L.j1 = out->j1; L.chi1 = out->chi1; }
     L.jac = jac;
     L.flag = h->d_flag;
-    const long long blocks = (b->n_zones * h->c.S * h->c.N + kAbsBlock - 1) / kAbsBlock;
+    const int nzb = kAbsBlock / (h->c.S * h->c.N);  // whole zones per block and iteration
+    const long long blocks = (b->n_zones + nzb - 1) / nzb;
     const int grid = (int)std::min<long long>(h->grid, blocks);
     const bool f64 = h->prec == VX_PREC_FP64, adj = jac != nullptr;
     if (f64) adj ? k_abs<true, true><<<grid, kAbsBlock, 0, s>>>(L) : k_abs<true, false><<<grid, kAbsBlock, 0, s>>>(L);
@@ -291,6 +390,12 @@ vx_status vx_abs_create(const vx_config *cfg, vx_abs **out) {
             const bool open = sp != VX_NU_X && E > 0.0;
             C.E[s][i] = open ? E : 0.0;
             C.K[s][i] = open ? pref * E * E : 0.0;
+            int ex = 0;
+            const double m = open && C.K[s][i] > 0.0 ? std::frexp(C.K[s][i], &ex) : 0.0;  // K = m 2^ex, m in [1/2, 1)
+            C.Ef[s][i] = (float)C.E[s][i];
+            C.El[s][i] = (float)(C.E[s][i] - (double)C.Ef[s][i]);
+            C.Kf[s][i] = (float)(2.0 * m);
+            C.kK[s][i] = ex - 1;
         }
     }
     cudaDeviceProp prop;

@@ -57,6 +57,14 @@
 #ifndef VX_TP_DIFF
 #define VX_TP_DIFF 1
 #endif
+// Tangent kernel, fast zones with n_mu a multiple of 16: the nine moment sums per node on the
+// tensor cores through warp-level MMA (1) or as FP32 FMAs (0); see mma_quadrature. Measured on
+// GB300 (workload 4): 861.9 ms against 617.3 ms, although the FMAs it removes are worth ~190 ms (a
+// copy without them ran in 424.1 ms): the TF32 splits cost more instructions than they save (+63 %
+// warp instructions). With the remainder split packed and separate accumulators: 913.4 ms.
+#ifndef VX_ADJ_MMA
+#define VX_ADJ_MMA 0
+#endif
 // Packed loops: the positron energies of a mirror pair as the electron energies with the lanes
 // exchanged (1; Ebar(tau) = E(-tau) bit for bit) or from their own fused multiply-add (0).
 #ifndef VX_ESWAP
@@ -703,6 +711,140 @@ __device__ __forceinline__ double kern2(float bI, float a, float bII, float b) {
     return (double)kh + ((double)kl + ((double)e1 + (double)e2));
 }
 
+// ---- tangent kernel, fast zones: the moment sums on the tensor cores ----------------------------
+// The moments of the three integrands O, GTa, GEt of a (pair, omega) unit are sums over the nodes
+// of integrand x weight, with the weights w(1+tau)^2, w(1-tau)^2, w(1-tau^2) shared by every unit:
+// a product [units x nodes] . [nodes x weights]. A warp takes 16 units at a time (units g and
+// g + 8 in the 4-lane group g) and 8 nodes per MMA step (lane q of the group: mirror node pair
+// k = 4 step + q, i.e. node k and node n_e - 1 - k, whose packed integrands are exactly the lane's
+// A-fragment entries of m16n8k8). FP32 accuracy from TF32 operands: each integrand is split into
+// a high part (its last 13 mantissa bits cleared) and the remainder, each weight into its nearest
+// TF32 value and the remainder, held in B's columns (w_hi, w_lo) for the three weights; two MMAs
+// per integrand (high and remainder rows) then carry every product but remainder x remainder
+// (relative 2^-21). The projections onto l = 0, 1 are linear in the moments, so every lane
+// accumulates its share (its weight column, its two units) over the pair's units and one
+// butterfly reduces the warp per pair: a warp owns whole pairs, no partial pairs remain.
+__device__ __forceinline__ void mma_tf32(float (&d)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3,
+                                         unsigned b0, unsigned b1) {
+    asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// v = hi + lo with hi the TF32 value of v's leading bits and lo the exact remainder, cut to TF32.
+__device__ __forceinline__ void split_tf32(float v, unsigned &hi, unsigned &lo) {
+    hi = __float_as_uint(v) & 0xffffe000u;
+    lo = __float_as_uint(__fsub_rn(v, __uint_as_float(hi))) & 0xffffe000u;
+}
+
+// The packed integrands of one unit on a mirror node pair (lane x: node tau, lane y: node -tau),
+// as in node_loop's packed fast path: O = r, GTa, GEt.
+__device__ __forceinline__ void mma_integrands(float2 B2, float2 Pe2, float2 h2, float2 Em2, float2 uv, float K,
+                                               float2 &r, float2 &ga, float2 &ge) {
+    const float2 one2 = make_float2(1.f, 1.f), mone2 = make_float2(-1.f, -1.f);
+    const float2 x = __ffma2_rn(B2, uv, Pe2);
+    const float2 e = make_float2(ex2a(-x.x), ex2a(-x.y));
+    const float2 f = make_float2(e.y * K, e.x * K);
+    const float2 t = __fadd2_rn(e, one2);
+    const float2 d = __ffma2_rn(t, f, t);
+    r = make_float2(rcpa(d.x), rcpa(d.y));
+    const float2 E2 = __ffma2_rn(h2, uv, Em2);
+    const float2 Eb2 = make_float2(E2.y, E2.x);
+    const float2 r2 = __fmul2_rn(r, r);
+    const float2 s0 = __ffma2_rn(f, r2, r2), p = __fmul2_rn(t, r2);
+    const float2 a1 = __fmul2_rn(e, s0), a2 = __fmul2_rn(f, p);
+    ga = __ffma2_rn(a1, E2, __fmul2_rn(a2, Eb2));
+    ge = __ffma2_rn(a1, mone2, a2);
+}
+
+template <int NE>
+__device__ __forceinline__ void mma_quadrature(const NodeMir *__restrict__ nm, const float (*__restrict__ w8)[8],
+                                               const float4 *__restrict__ tab, int npair, int nmu,
+                                               const uint16_t *__restrict__ pij, float *mats, int N2, int N,
+                                               float il_h, float el_h, float K, bool neg) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int g = lane >> 2, tq = lane & 3;
+    const int pa = warp * npair / nwarp, pb = (warp + 1) * npair / nwarp;
+#pragma unroll 1
+    for (int p = pa; p < pb; ++p) {
+        float acc[4][4];  // [O, GTa, GTp, GEt][l = 0 term I, term II, l = 1 term I, term II]
+#pragma unroll
+        for (int x = 0; x < 4; ++x) acc[x][0] = acc[x][1] = acc[x][2] = acc[x][3] = 0.f;
+#pragma unroll 1
+        for (int m0 = 0; m0 < nmu; m0 += 16) {
+            const int uA = p * nmu + m0 + g, uB = uA + 8;
+            const float4 RA0 = __ldg(tab + 2 * uA), RA1 = __ldg(tab + 2 * uA + 1);
+            const float4 RB0 = __ldg(tab + 2 * uB), RB1 = __ldg(tab + 2 * uB + 1);
+            const float2 BA = make_float2(RA0.x * il_h, RA0.x * il_h), BB = make_float2(RB0.x * il_h, RB0.x * il_h);
+            const float pA = fmaf(RA0.z, il_h, -el_h), pB = fmaf(RB0.z, il_h, -el_h);
+            const float2 PA = make_float2(pA, pA), PB = make_float2(pB, pB);
+            const float2 hA = make_float2(RA0.x, RA0.x), hB = make_float2(RB0.x, RB0.x);
+            const float2 EA = make_float2(RA0.z, RA0.z), EB = make_float2(RB0.z, RB0.z);
+            float D[3][4];
+#pragma unroll
+            for (int x = 0; x < 3; ++x) D[x][0] = D[x][1] = D[x][2] = D[x][3] = 0.f;
+#pragma unroll 2
+            for (int kb = 0; kb < NE / 8; ++kb) {
+                const int k = 4 * kb + tq;
+                const float2 uv = make_float2(nm[k].a.x, nm[k].a.y);
+                const unsigned b0 = __float_as_uint(w8[k][g]), b1 = __float_as_uint(w8[NE - 1 - k][g]);
+                float2 vA[3], vB[3];
+                mma_integrands(BA, PA, hA, EA, uv, K, vA[0], vA[1], vA[2]);
+                mma_integrands(BB, PB, hB, EB, uv, K, vB[0], vB[1], vB[2]);
+#pragma unroll
+                for (int x = 0; x < 3; ++x) {
+                    unsigned h0, l0, h1, l1, h2, l2, h3, l3;
+                    split_tf32(vA[x].x, h0, l0);
+                    split_tf32(vB[x].x, h1, l1);
+                    split_tf32(vA[x].y, h2, l2);
+                    split_tf32(vB[x].y, h3, l3);
+                    mma_tf32(D[x], h0, h1, h2, h3, b0, b1);
+                    mma_tf32(D[x], l0, l1, l2, l3, b0, b1);
+                }
+            }
+            // lane q < 3 holds weight q's moments: columns 2q, 2q + 1 = (w_hi, w_lo) of units A, B
+            if (tq < 3) {
+                // projection coefficients of this lane's weight: term I (kp, km, k0)[q], term II
+                // (km, kp, k0)[q]; eta < 0 exchanges kp and km
+                const bool sw = (tq == 0) != neg, sw2 = (tq == 1) != neg;
+                const float caA = tq == 2 ? RA1.z : (sw ? RA1.x : RA1.y), cbA = tq == 2 ? RA1.z : (sw2 ? RA1.x : RA1.y);
+                const float caB = tq == 2 ? RB1.z : (sw ? RB1.x : RB1.y), cbB = tq == 2 ? RB1.z : (sw2 ? RB1.x : RB1.y);
+                const float q0A = 2.f * (RA0.x + RA0.z), q0B = 2.f * (RB0.x + RB0.z);
+                float MA[4], MB[4];
+                MA[0] = D[0][0] + D[0][1]; MA[1] = D[1][0] + D[1][1]; MA[3] = D[2][0] + D[2][1];
+                MB[0] = D[0][2] + D[0][3]; MB[1] = D[1][2] + D[1][3]; MB[3] = D[2][2] + D[2][3];
+                MA[2] = fmaf(q0A, MA[0], -MA[1]);  // GTp = O q0 - GTa
+                MB[2] = fmaf(q0B, MB[0], -MB[1]);
+#pragma unroll
+                for (int x = 0; x < 4; ++x) {
+                    const float aA = caA * MA[x], bA = cbA * MA[x], aB = caB * MB[x], bB = cbB * MB[x];
+                    acc[x][0] += aA + aB;
+                    acc[x][1] += bA + bB;
+                    acc[x][2] += fmaf(RA1.w, aA, RB1.w * aB);
+                    acc[x][3] += fmaf(RA1.w, bA, RB1.w * bB);
+                }
+            }
+        }
+        // the pair's sums over the warp (fixed butterfly), stored by lane 0
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[x][c] += __shfl_xor_sync(0xffffffffu, acc[x][c], off);
+        if (lane == 0) {
+            const int pi = pij[p] >> 8, pj = pij[p] & 0xff;
+#pragma unroll
+            for (int x = 0; x < 4; ++x) {
+                Proj P;
+                P.zero();
+                P.o0I = acc[x][0]; P.o0II = acc[x][1]; P.o1I = acc[x][2]; P.o1II = acc[x][3];
+                store_proj<false>(mats + (size_t)x * 2 * N2, N2, N, pi, pj, P);
+            }
+        }
+    }
+}
+
 // MINB selects one of two register budgets (2: up to 128 registers; 3: up to 80 for the forward
 // kernel, 96 for the tangent kernel); both are compiled and the autotuner picks per kernel kind
 // and quadrature. SPLIT compiles the split rule in (separate instantiations, so that the standard
@@ -718,6 +860,10 @@ __global__ void __launch_bounds__(MINB == 3 ? (ADJ ? VX_LB3_THREADS_ADJ : VX_TPB
     __shared__ NodeMir s_mir[VX_MAX_NE / 2];
     __shared__ float4 s_half[VX_MAX_NE / 2];  // split rule: 1 + x, 1 - x, w of the n_e/2-node rule
     __shared__ uint16_t s_pij[VX_MAX_PAIRS];
+    // tensor-core moments: per node the weights as (hi, lo) TF32 pairs, columns
+    // (w(1+tau)^2, w(1-tau)^2, w(1-tau^2)) x (hi, lo) and two zero columns
+    constexpr bool MMA = ADJ && !PREC && !SPLIT && NE > 0 && NE % 8 == 0 && VX_ADJ_MMA && VX_F32X2;
+    __shared__ float s_w8[MMA ? VX_MAX_NE : 1][8];
     const Common &C = L.c;
     const int N = C.N, S = C.S, N2 = N * N, npair = C.npair;
     const int nq = ADJ ? 4 : 1;
@@ -741,6 +887,17 @@ __global__ void __launch_bounds__(MINB == 3 ? (ADJ ? VX_LB3_THREADS_ADJ : VX_TPB
         }
     }
     for (int p = tid; p < npair; p += blockDim.x) s_pij[p] = C.pij[p];
+    if (MMA)
+        for (int k = tid; k < C.n_e; k += blockDim.x) {
+            const float w3[3] = {L.n32.cp[k], L.n32.cm[k], L.n32.c0[k]};
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float hi = __uint_as_float((__float_as_uint(w3[c]) + 0x1000u) & 0xffffe000u);  // nearest TF32
+                s_w8[k][2 * c] = hi;
+                s_w8[k][2 * c + 1] = __uint_as_float(__float_as_uint(w3[c] - hi) & 0xffffe000u);
+            }
+            s_w8[k][6] = s_w8[k][7] = 0.f;
+        }
     if (SPLIT)
         for (int k = tid; k < C.n_e / 2; k += blockDim.x)
             s_half[k] = make_float4(L.n32.hp[k], L.n32.hm[k], L.n32.hw[k], 0.f);
@@ -881,13 +1038,16 @@ __global__ void __launch_bounds__(MINB == 3 ? (ADJ ? VX_LB3_THREADS_ADJ : VX_TPB
         const bool deg = zs.deg, neg = zs.neg;
         // One iteration per unit (28 or 29 per thread at N = 21, n_mu = 32): every lane runs the
         // node loop in step; only the flush at a pair boundary diverges.
+        const bool use_mma = MMA && !deg && nmu % 16 == 0;
+        if (use_mma)
+            mma_quadrature<NE>(s_mir, s_w8, L.tab32, npair, nmu, s_pij, mats, N2, N, il_h, el_h, zs.K, neg);
         int p = u0 / nmu, m = u0 - (u0 / nmu) * nmu, mb = m;
         bool first = true;
         Proj PO, PTa, PTp, PEt;
         PO.zero();
         if (ADJ) { PTa.zero(); PTp.zero(); PEt.zero(); }
 #pragma unroll 1
-        for (int u = u0; u < u1; ++u) {
+        for (int u = use_mma ? u1 : u0; u < u1; ++u) {
             {
                 const float4 *rec = L.tab32 + ((size_t)p * nmu + m) * 2;  // a thread's units are consecutive records
                 const float4 R0 = __ldg(rec), R1 = __ldg(rec + 1);
@@ -995,7 +1155,7 @@ __global__ void __launch_bounds__(MINB == 3 ? (ADJ ? VX_LB3_THREADS_ADJ : VX_TPB
         __syncthreads();
         // pairs split between threads: sum their partial projections over the owning threads in
         // order (owner of unit v: ceil((v+1) TB / U) - 1), then store
-        for (int p = tid; p < npair; p += TB) {
+        for (int p = use_mma ? npair : tid; p < npair; p += TB) {
             const int ua = p * nmu, ub = ua + nmu - 1;
             const int ta = ((ua + 1) * TB + U - 1) / U - 1, tb = ((ub + 1) * TB + U - 1) / U - 1;
             if (ta == tb) continue;
