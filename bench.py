@@ -365,6 +365,10 @@ def run_solve(args):
 
 
 NES_METRIC = "NES kernel entries/s (zone*eps*eps'*l), FP32 forward+Jacobian, % FP peak"
+# DRAM bytes (read + write) per zone of the NES forward + Jacobian kernel, from one ncu capture of
+# the 256-ray case of the workload (108.8 + 765.1 MB for 102,400 zones,
+# profiles/k_nes_tangents_20_and_64rays.md); None whenever the kernel changes, until captured again.
+NES_TRAFFIC_BYTES_PER_ZONE = 8534
 NES_N_MU, NES_N_E = 16, 48
 
 
@@ -471,14 +475,9 @@ def run_nes(args):
     h_out = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in out.items()}
     h_jac = torch.empty(jac.shape, dtype=jac.dtype, pin_memory=True)
 
-    def step_e2e():
-        for k in ("state", "J", "H"):
-            d[k].copy_(host[k], non_blocking=True)
-        res = nes.adjoint(d["state"], d["J"], d["H"], forward=True, ray_offsets=b["ray_offsets"])
-        for k in ("j0", "chi0", "j1", "chi1"):
-            h_out[k].copy_(res[k], non_blocking=True)
-        h_jac.copy_(res["jac"], non_blocking=True)
-        torch.cuda.current_stream().synchronize()
+    def step_e2e():  # vx_nes_adjoint_host: chunks copied in, evaluated and copied back, overlapped
+        nes.adjoint_host(host["state"], host["J"], host["H"], forward=True, ray_offsets=b["ray_offsets"],
+                         out=h_out, jac=h_jac)
 
     step_e2e()
     e2e_steps = max(1, min(3, args.steps))
@@ -506,15 +505,15 @@ def run_nes(args):
                        "species": S, "l2": "inputs larger than L2 (J, H: %.2f GB)" % (2 * b["J"].nbytes / 1e9)},
             "e2e": {"value": job_rate(entries(Z, N), world, ms_e2e), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e,
-                    "call": "NesRates.adjoint with the inputs copied in from and the outputs back to pinned host "
-                            "tensors every step"},
+                    "call": "vx_nes_adjoint_host (host buffers, pinned; chunks overlapped with the kernel)"},
             "gpu_launches": args.steps,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                          "flop_per_node": algorithmic_flops_per_node(True), "nodes_per_step": nodes,
                          "nodes_note": "electron-energy nodes the three-panel rule places (empty panels, where "
                                        "the Fermi edges lie below E_min, have none), counted on a 1-in-64 zone "
                                        "sample and scaled",
-                         "traffic": None,
+                         "traffic": NES_TRAFFIC_BYTES_PER_ZONE * Z if NES_TRAFFIC_BYTES_PER_ZONE else None,
+                         "traffic_note": "ncu DRAM read+write of a 102,400-zone capture, scaled by zone count",
                          "peak_note": f"FP32 {nsm} SMs x 128 FMA x 2 x {mhz:.0f} MHz (median SM clock in the run)",
                          "kernel": f"k_nes<float, tangents, {NES_N_E // 3} nodes per panel>"},
             "clocks": c, "numeric_ok": bool(ok),

@@ -68,6 +68,16 @@ vx_status vx_nes_eval(vx_nes *h, const vx_batch *batch, const vx_out *out, vx_st
  * forward rates of the same pass (its phi member must be NULL). Both precisions. */
 vx_status vx_nes_adjoint(vx_nes *h, const vx_batch *batch, double *jac, const vx_out *fwd, vx_stream stream);
 
+/* The same computations on HOST arrays (vx_nes_eval, vx_nes_adjoint with host pointers; host
+ * ray_offsets, validated on the host): the batch goes through the handle's two staging slots of
+ * device memory (640 MiB each, allocated on first use) in chunks of zones, one stream per slot,
+ * so the copies of one chunk overlap the kernel of the next. Host arrays should be pinned for the
+ * copies to be asynchronous. Synchronous: returns when every output is in host memory; the
+ * numeric flag is reported by vx_nes_check as for the device calls. out->phi must be NULL.
+ * Errors: VX_ERR_INVALID_ARG (NULL arrays, invalid offsets), VX_ERR_OOM, VX_ERR_CUDA. */
+vx_status vx_nes_eval_host(vx_nes *h, const vx_batch *host_batch, const vx_out *host_out);
+vx_status vx_nes_adjoint_host(vx_nes *h, const vx_batch *host_batch, double *host_jac, const vx_out *host_fwd);
+
 /* Synchronises `stream`, reads and clears the device numeric flag: VX_OK or VX_ERR_NUMERIC. */
 vx_status vx_nes_check(vx_nes *h, vx_stream stream);
 

@@ -54,7 +54,7 @@ SYMBOLS = ("vx_rates_create", "vx_rates_eval", "vx_rates_adjoint", "vx_rates_che
            "vx_rates_eval_noalloc", "vx_rates_spectral", "vx_rates_eval_host", "vx_rates_adjoint_host",
            "vx_rates_spectral_host", "vx_btd_create", "vx_btd_solve", "vx_btd_check", "vx_btd_destroy",
            "vx_probe_pipes", "vx_nes_create", "vx_nes_eval", "vx_nes_adjoint", "vx_nes_check", "vx_nes_destroy",
-           "vx_eos_eta", "vx_eos_chain", "vx_abs_create", "vx_abs_eval", "vx_abs_adjoint", "vx_abs_check",
+           "vx_eos_eta", "vx_eos_chain", "vx_nes_eval_host", "vx_nes_adjoint_host", "vx_abs_create", "vx_abs_eval", "vx_abs_adjoint", "vx_abs_check",
            "vx_abs_destroy")
 
 _lib = None
@@ -122,6 +122,11 @@ def lib(path: str | None = None):
     L.vx_nes_check.restype = ctypes.c_int
     L.vx_nes_destroy.argtypes = [ctypes.c_void_p]
     L.vx_nes_destroy.restype = None
+    L.vx_nes_eval_host.argtypes = [ctypes.c_void_p, ctypes.POINTER(vx_batch), ctypes.POINTER(vx_out)]
+    L.vx_nes_eval_host.restype = ctypes.c_int
+    L.vx_nes_adjoint_host.argtypes = [ctypes.c_void_p, ctypes.POINTER(vx_batch), ctypes.c_void_p,
+                                      ctypes.POINTER(vx_out)]
+    L.vx_nes_adjoint_host.restype = ctypes.c_int
     L.vx_abs_create.argtypes = [ctypes.POINTER(vx_config), ctypes.POINTER(ctypes.c_void_p)]
     L.vx_abs_create.restype = ctypes.c_int
     L.vx_abs_eval.argtypes = [ctypes.c_void_p, ctypes.POINTER(vx_batch), ctypes.POINTER(vx_out), ctypes.c_void_p]
@@ -286,6 +291,17 @@ def vx_nes_check(h, stream: int = 0) -> int:
 
 def vx_nes_destroy(h) -> None:
     lib().vx_nes_destroy(h)
+
+
+def vx_nes_eval_host(h, batch: vx_batch, out: vx_out) -> None:
+    """Host arrays in and out (see the header); synchronous."""
+    _check(lib().vx_nes_eval_host(h, ctypes.byref(batch), ctypes.byref(out)), "vx_nes_eval_host")
+
+
+def vx_nes_adjoint_host(h, batch: vx_batch, jac: int, fwd: vx_out | None) -> None:
+    """Host arrays in and out (see the header); synchronous."""
+    _check(lib().vx_nes_adjoint_host(h, ctypes.byref(batch), ctypes.c_void_p(jac or 0),
+                                     ctypes.byref(fwd) if fwd is not None else None), "vx_nes_adjoint_host")
 
 
 def vx_abs_create(cfg: vx_config) -> ctypes.c_void_p:

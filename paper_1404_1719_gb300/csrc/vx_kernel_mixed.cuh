@@ -222,8 +222,10 @@ __device__ __forceinline__ void mo_from_tangents(Mom &mo, const Mom &ta, const M
 // Degenerate path, packed on mirror pairs: exact-split electron argument, direct positron argument,
 // tangents from r^2 where the zone scale keeps r^2 in the FP32 range (R2), else first-order products
 // with r (see node_loop), inline or as an out-of-line call (OUTLINE).
-// (UD: unroll cap; the tangent kernel's loop may be unrolled whole.)
-template <int NE, bool ADJ, bool OUTLINE, bool R2, int UD>
+// (UD: unroll cap; the tangent kernel's loop may be unrolled whole. TPD: the production tangent's
+// moments as q0 M(O) - M(GTa), as in the fast path; with the zone scale GTa + GTp = q0 r still holds
+// node by node, and the moments of O are dominated by E above the Fermi edge, where f_e < 1/2.)
+template <int NE, bool ADJ, bool OUTLINE, bool R2, int UD, bool TPD = false>
 struct DegPacked {
     static __device__ __forceinline__ void body(const NodeMir *__restrict__ nm, float B, float Pp, float Bq, float Bl,
                                                 float Pq, float Pl, float h, float Em, float c1, Mom &mo, Mom &ta,
@@ -251,7 +253,7 @@ struct DegPacked {
                 const float2 t = __fadd2_rn(c12, e1);
                 const float2 d = __ffma2_rn(t, e2, t);
                 const float2 r = make_float2(rcpa(d.x), rcpa(d.y));
-                if (!(ADJ && VX_MO_TANG)) {
+                if (!(ADJ && VX_MO_TANG) || TPD) {
                     P2 = __ffma2_rn(cpm, r, P2);
                     M2 = __ffma2_rn(cmp, r, M2);
                     Z2 = __ffma2_rn(c00, r, Z2);
@@ -259,7 +261,7 @@ struct DegPacked {
                 if (ADJ) {
                     const float2 E2 = __ffma2_rn(h2, u2, Em2);
                     const float2 Eb2 = VX_ESWAP ? make_float2(E2.y, E2.x) : __ffma2_rn(h2, v2, Em2);
-                    float2 ga, gp, ge;
+                    float2 ga, gp = z2, ge;
                     if (R2) {
                         // r = 2^sc O with r^2 in the FP32 range (zone scale chosen for it):
                         // (1 - f_e) r = c1 (1 + e2) r^2, (1 - f_ebar) r = t r^2, f_e r = e1 (1 + e2) r^2,
@@ -268,7 +270,7 @@ struct DegPacked {
                         const float2 s0 = __ffma2_rn(e2, r2, r2), p = __fmul2_rn(t, r2);
                         const float2 a1 = __fmul2_rn(e1, s0), a2 = __fmul2_rn(e2, p);
                         ga = __ffma2_rn(a1, E2, __fmul2_rn(a2, Eb2));
-                        gp = __ffma2_rn(__fmul2_rn(c12, s0), E2, __fmul2_rn(p, Eb2));
+                        if (!TPD) gp = __ffma2_rn(__fmul2_rn(c12, s0), E2, __fmul2_rn(p, Eb2));
                         ge = __ffma2_rn(a1, mone2, a2);
                     } else {
                         const float2 qv = __ffma2_rn(e2, r, r);  // (1 + e2) r
@@ -276,23 +278,30 @@ struct DegPacked {
                         const float2 sp = __fmul2_rn(t, r);      // 1 - f_ebar
                         const float2 fe = __fmul2_rn(e1, qv), fp = __fmul2_rn(e2, sp);
                         ga = __fmul2_rn(__ffma2_rn(fe, E2, __fmul2_rn(fp, Eb2)), r);
-                        gp = __fmul2_rn(__ffma2_rn(se, E2, __fmul2_rn(sp, Eb2)), r);
+                        if (!TPD) gp = __fmul2_rn(__ffma2_rn(se, E2, __fmul2_rn(sp, Eb2)), r);
                         ge = __fmul2_rn(__ffma2_rn(fe, mone2, fp), r);
                     }
                     TAp = __ffma2_rn(cpm, ga, TAp); TAm = __ffma2_rn(cmp, ga, TAm); TAz = __ffma2_rn(c00, ga, TAz);
-                    TPp = __ffma2_rn(cpm, gp, TPp); TPm = __ffma2_rn(cmp, gp, TPm); TPz = __ffma2_rn(c00, gp, TPz);
+                    if (!TPD) {
+                        TPp = __ffma2_rn(cpm, gp, TPp); TPm = __ffma2_rn(cmp, gp, TPm); TPz = __ffma2_rn(c00, gp, TPz);
+                    }
                     ETp = __ffma2_rn(cpm, ge, ETp); ETm = __ffma2_rn(cmp, ge, ETm); ETz = __ffma2_rn(c00, ge, ETz);
                 }
             }
         }
         if (ADJ) {
             ta.p = TAp.x + TAp.y; ta.m = TAm.x + TAm.y; ta.z = TAz.x + TAz.y;
-            tp.p = TPp.x + TPp.y; tp.m = TPm.x + TPm.y; tp.z = TPz.x + TPz.y;
             et.p = ETp.x + ETp.y; et.m = ETm.x + ETm.y; et.z = ETz.x + ETz.y;
         }
-        if (ADJ && VX_MO_TANG) {
+        if (ADJ && TPD) {
+            mo.p = P2.x + P2.y; mo.m = M2.x + M2.y; mo.z = Z2.x + Z2.y;
+            const float q0 = 2.f * (h + Em);
+            tp.p = fmaf(q0, mo.p, -ta.p); tp.m = fmaf(q0, mo.m, -ta.m); tp.z = fmaf(q0, mo.z, -ta.z);
+        } else if (ADJ && VX_MO_TANG) {
+            tp.p = TPp.x + TPp.y; tp.m = TPm.x + TPm.y; tp.z = TPz.x + TPz.y;
             mo_from_tangents(mo, ta, tp, h, Em);
         } else {
+            if (ADJ) { tp.p = TPp.x + TPp.y; tp.m = TPm.x + TPm.y; tp.z = TPz.x + TPz.y; }
             mo.p = P2.x + P2.y; mo.m = M2.x + M2.y; mo.z = Z2.x + Z2.y;
         }
     }
@@ -423,7 +432,7 @@ __device__ __forceinline__ void df_diff(float ah, float al, float bh, float bl, 
 // PREC (precise mode): the packed mirror loop forms the electron argument exactly as the
 // degenerate path does (high part on the zone's grid, exact in FP32, remainder through a second
 // ex2), so the blocking factor's relative error no longer grows like |x| 2^-24 with the argument.
-template <int NE, bool ADJ, bool DEG, bool SPLIT, bool PREC>
+template <int NE, bool ADJ, bool DEG, bool SPLIT, bool PREC, bool TPOK = true>
 __device__ __forceinline__ void node_loop(const NodeSm *__restrict__ nd, const NodeMir *__restrict__ nm, int ne,
                                           float B, float Pe,
                                           float Pp, float Bq, float Bl, float Pq, float Pl, float h,
@@ -590,10 +599,11 @@ __device__ __forceinline__ void node_loop(const NodeSm *__restrict__ nd, const N
     } else if (DEG && NE > 0 && VX_F32X2 && (ADJ ? VX_DEG_PACK_ADJ : VX_DEG_PACK_FWD)) {
         constexpr bool OL = (ADJ ? VX_DEG_PACK_ADJ : VX_DEG_PACK_FWD) == 2;
         constexpr int UDG = !ADJ ? VX_UNROLL_DEG_FWD : (SPLIT ? 16 : VX_UNROLL_DEG_ADJ);
+        constexpr bool DTPD = ADJ && TPOK && VX_TP_DIFF;
         if (!ADJ || r2ok)
-            DegPacked<NE, ADJ, OL, ADJ, UDG>::run(nm, B, Pp, Bq, Bl, Pq, Pl, h, Em, c1, mo, ta, tp, et);
+            DegPacked<NE, ADJ, OL, ADJ, UDG, DTPD>::run(nm, B, Pp, Bq, Bl, Pq, Pl, h, Em, c1, mo, ta, tp, et);
         else
-            DegPacked<NE, ADJ, OL, false, UDG>::run(nm, B, Pp, Bq, Bl, Pq, Pl, h, Em, c1, mo, ta, tp, et);
+            DegPacked<NE, ADJ, OL, false, UDG, DTPD>::run(nm, B, Pp, Bq, Bl, Pq, Pl, h, Em, c1, mo, ta, tp, et);
     } else if (NE > 0) {
 #pragma unroll 1
         for (int k0 = 0; k0 < NE; k0 += U) {
@@ -1114,7 +1124,7 @@ __global__ void __launch_bounds__(MINB == 3 ? (ADJ ? VX_LB3_THREADS_ADJ : VX_TPB
                         const float Pe = fmaf(Em, il_h, -el_h);
                         node_loop<NE, ADJ, false, SPLIT, PREC>(s_nodes, s_mir, C.n_e, B, Pe, Pp, Bq, Bl, Pq, Pl, h, Em, 1.f, zs.K, false, mo, ta, tp, et);
                     } else {
-                        node_loop<NE, ADJ, true, SPLIT, false>(s_nodes, s_mir, C.n_e, B, 0.f, Pp, Bq, Bl, Pq, Pl, h, Em, zs.c1, 0.f, zs.r2ok, mo, ta, tp, et);
+                        node_loop<NE, ADJ, true, SPLIT, false, !PREC>(s_nodes, s_mir, C.n_e, B, 0.f, Pp, Bq, Bl, Pq, Pl, h, Em, zs.c1, 0.f, zs.r2ok, mo, ta, tp, et);
                     }
                     const Coef cf = make_coef(kp, km, k0, R1.w);
                     project<PREC>(PO, mo, cf);

@@ -27,6 +27,7 @@
 #include <type_traits>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -702,6 +703,11 @@ struct vx_nes {
     int *d_flag = nullptr;
     size_t smem[2] = {0, 0};
     int grid[2] = {0, 0};
+    // host-buffer calls: two staging slots of device memory, a stream and a work counter each
+    double *hbuf[2] = {nullptr, nullptr};
+    cudaStream_t hst[2] = {nullptr, nullptr};
+    unsigned long long *hcnt = nullptr;
+    size_t hbytes = 0;
 };
 
 namespace {
@@ -775,7 +781,8 @@ vx_status nes_validate_out(const vx_out *o, bool allow_phi) {
 }
 
 template <typename R>
-vx_status nes_run(vx_nes *h, const vx_batch *b, const vx_out *out, double *jac, cudaStream_t s) {
+vx_status nes_run(vx_nes *h, const vx_batch *b, const vx_out *out, double *jac, cudaStream_t s,
+                  unsigned long long *counter = nullptr) {
     vx::NesLaunch<R> L{};
     L.c = h->c;
     L.tab = reinterpret_cast<const vx::NesRec<R> *>(h->d_tab);
@@ -785,19 +792,111 @@ vx_status nes_run(vx_nes *h, const vx_batch *b, const vx_out *out, double *jac, 
     L.state = b->state; L.J = b->J; L.H = b->H;
     if (out) { L.j0 = out->j0; L.chi0 = out->chi0; L.j1 = out->j1; L.chi1 = out->chi1; L.phi = out->phi; }
     L.jac = jac;
-    L.counter = h->d_counter;
+    L.counter = counter ? counter : h->d_counter;
     L.flag = h->d_flag;
     const bool adj = jac != nullptr;
     const int grid = (int)std::min<long long>(h->grid[adj], b->n_zones);
-    NES_CU(cudaMemsetAsync(h->d_counter, 0, sizeof(unsigned long long), s));
+    NES_CU(cudaMemsetAsync(L.counter, 0, sizeof(unsigned long long), s));
     const cudaError_t e = adj ? vx::nes_launch<R, true>(L, grid, h->smem[1], s) : vx::nes_launch<R, false>(L, grid, h->smem[0], s);
     NES_CU(e);
+    return VX_OK;
+}
+
+// Host-buffer calls: the batch in chunks of zones through the handle's two staging slots
+// (640 MiB each, or VX_HOST_SLOT_MB MiB from the environment, allocated on first use); each slot
+// has its own stream and work counter, so the
+// copies of one chunk overlap the kernel of the next. Host arrays should be pinned for the copies
+// to be asynchronous; the call returns when every output is in host memory.
+constexpr size_t kNesHostSlot = 640ull << 20;
+
+vx_status nes_host_run(vx_nes *h, const vx_batch *b, const vx_out *fwd, double *jac) {
+    if (!h) return nfail(VX_ERR_INVALID_ARG, "handle is NULL");
+    if (!b) return nfail(VX_ERR_INVALID_ARG, "batch is NULL");
+    if (b->n_zones < 0 || b->n_rays < 0) return nfail(VX_ERR_INVALID_ARG, "negative batch size");
+    if (b->ray_offsets) {
+        if (b->ray_offsets[0] != 0) return nfail(VX_ERR_INVALID_ARG, "ray_offsets[0] must be 0");
+        for (int r = 0; r < b->n_rays; ++r)
+            if (b->ray_offsets[r + 1] < b->ray_offsets[r])
+                return nfail(VX_ERR_INVALID_ARG, "ray_offsets must be non-decreasing (ray %d)", r);
+        if ((long long)b->ray_offsets[b->n_rays] != b->n_zones)
+            return nfail(VX_ERR_INVALID_ARG, "ray_offsets[n_rays] does not equal n_zones");
+    }
+    if (fwd && (!fwd->j0 || !fwd->chi0 || !fwd->j1 || !fwd->chi1)) return nfail(VX_ERR_INVALID_ARG, "an output array is NULL");
+    if (fwd && fwd->phi) return nfail(VX_ERR_INVALID_ARG, "phi output is not produced by the host-buffer calls");
+    if (b->n_zones == 0) return VX_OK;
+    if (!b->state || !b->J || !b->H) return nfail(VX_ERR_INVALID_ARG, "state, J and H must be host arrays");
+    int cur = 0;
+    NES_CU(cudaGetDevice(&cur));
+    NES_CU(cudaSetDevice(h->device));
+    struct Restore {
+        int d;
+        ~Restore() { cudaSetDevice(d); }
+    } restore{cur};
+    if (!h->hbuf[0]) {
+        h->hbytes = kNesHostSlot;
+        if (const char *mb = getenv("VX_HOST_SLOT_MB")) {  // slot size override, MiB
+            const long long v = atoll(mb);
+            if (v >= 1 && v <= (1ll << 20)) h->hbytes = (size_t)v << 20;
+        }
+        for (int k = 0; k < 2; ++k) {
+            NES_CU(cudaMalloc(&h->hbuf[k], h->hbytes));
+            NES_CU(cudaStreamCreateWithFlags(&h->hst[k], cudaStreamNonBlocking));
+        }
+        NES_CU(cudaMalloc(&h->hcnt, 2 * sizeof(unsigned long long)));
+    }
+    const size_t SN = (size_t)h->c.S * h->c.N;
+    const size_t per = 4 + 2 * SN + (fwd ? 4 * SN : 0) + (jac ? 12 * SN : 0);  // doubles per zone
+    const long long chunk = (long long)(h->hbytes / (per * sizeof(double)));
+    if (chunk < 1) return nfail(VX_ERR_UNSUPPORTED, "one zone does not fit a staging slot");
+    const long long Z = b->n_zones;
+    for (long long c = 0, z0 = 0; z0 < Z; ++c, z0 += chunk) {
+        const long long n = std::min(chunk, Z - z0);
+        const int sl = (int)(c & 1);
+        cudaStream_t s = h->hst[sl];
+        double *p = h->hbuf[sl];
+        auto take = [&](size_t count) { double *q = p; p += count; return q; };
+        double *d_state = take(4 * n), *d_J = take(SN * n), *d_H = take(SN * n);
+        NES_CU(cudaMemcpyAsync(d_state, b->state + 4 * z0, 4 * n * sizeof(double), cudaMemcpyHostToDevice, s));
+        NES_CU(cudaMemcpyAsync(d_J, b->J + SN * z0, SN * n * sizeof(double), cudaMemcpyHostToDevice, s));
+        NES_CU(cudaMemcpyAsync(d_H, b->H + SN * z0, SN * n * sizeof(double), cudaMemcpyHostToDevice, s));
+        const vx_batch db{0, n, nullptr, d_state, d_J, d_H};
+        vx_out dout{};
+        double *d_out = nullptr, *d_jac = nullptr;
+        if (fwd) {
+            d_out = take(4 * SN * n);
+            dout.j0 = d_out; dout.chi0 = d_out + SN * n; dout.j1 = d_out + 2 * SN * n; dout.chi1 = d_out + 3 * SN * n;
+        }
+        if (jac) d_jac = take(12 * SN * n);
+        const vx_status st = h->prec == VX_PREC_FP64 ? nes_run<double>(h, &db, fwd ? &dout : nullptr, d_jac, s, h->hcnt + sl)
+                                                     : nes_run<float>(h, &db, fwd ? &dout : nullptr, d_jac, s, h->hcnt + sl);
+        if (st != VX_OK) return st;
+        if (fwd) {
+            double *dst[4] = {fwd->j0, fwd->chi0, fwd->j1, fwd->chi1};
+            for (int k = 0; k < 4; ++k)
+                NES_CU(cudaMemcpyAsync(dst[k] + SN * z0, d_out + k * SN * n, SN * n * sizeof(double),
+                                       cudaMemcpyDeviceToHost, s));
+        }
+        if (d_jac)
+            NES_CU(cudaMemcpyAsync(jac + 12 * SN * z0, d_jac, 12 * SN * n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    }
+    NES_CU(cudaStreamSynchronize(h->hst[0]));
+    NES_CU(cudaStreamSynchronize(h->hst[1]));
     return VX_OK;
 }
 
 }  // namespace
 
 extern "C" {
+
+vx_status vx_nes_eval_host(vx_nes *h, const vx_batch *host_batch, const vx_out *host_out) {
+    if (!host_out) return nfail(VX_ERR_INVALID_ARG, "out is NULL");
+    return nes_host_run(h, host_batch, host_out, nullptr);
+}
+
+vx_status vx_nes_adjoint_host(vx_nes *h, const vx_batch *host_batch, double *host_jac, const vx_out *host_fwd) {
+    if (!host_jac) return nfail(VX_ERR_INVALID_ARG, "jac is NULL");
+    return nes_host_run(h, host_batch, host_fwd, host_jac);
+}
 
 vx_status vx_nes_create(const vx_config *cfg, vx_nes **out) {
     if (!out) return nfail(VX_ERR_INVALID_ARG, "out is NULL");
@@ -947,6 +1046,11 @@ void vx_nes_destroy(vx_nes *h) {
     cudaFree(h->d_tab);
     cudaFree(h->d_counter);
     cudaFree(h->d_flag);
+    for (int k = 0; k < 2; ++k) {
+        cudaFree(h->hbuf[k]);
+        if (h->hst[k]) cudaStreamDestroy(h->hst[k]);
+    }
+    cudaFree(h->hcnt);
     delete h;
 }
 

@@ -77,7 +77,32 @@ class NesRates(PairRates):
         capi.vx_nes_adjoint(self._h, b, res["jac"].data_ptr(), fwd, self._stream(stream))
         return res
 
+    def evaluate_host(self, state, J, H, ray_offsets=None, out=None) -> dict:
+        """End-to-end call on host arrays (numpy or pinned torch CPU tensors): vx_nes_eval_host
+        copies chunks of zones in, evaluates and copies the rates back, overlapping the copies of
+        one chunk with the kernel of the next. Returns host tensors (pinned unless `out` given)."""
+        b, Z = self._host_batch(state, J, H, ray_offsets)
+        res, o = self._host_out(Z, out)
+        with torch.cuda.device(self.device):
+            capi.vx_nes_eval_host(self._h, b, o)
+        return res
+
+    def adjoint_host(self, state, J, H, forward: bool = True, ray_offsets=None, out=None, jac=None) -> dict:
+        """End-to-end rates and Jacobian on host arrays (vx_nes_adjoint_host)."""
+        b, Z = self._host_batch(state, J, H, ray_offsets)
+        res, o = self._host_out(Z, out) if forward else ({}, None)
+        if jac is not None:
+            self._check_out("jac", jac, (Z, self.S, self.N, 4, 3), host=True)
+        res["jac"] = jac if jac is not None else torch.empty((Z, self.S, self.N, 4, 3), dtype=torch.float64,
+                                                             pin_memory=True)
+        with torch.cuda.device(self.device):
+            capi.vx_nes_adjoint_host(self._h, b, res["jac"].data_ptr(), o)
+        return res
+
     def spectral(self, *a, **k):
+        raise NotImplementedError("spectral derivatives are provided for the pair kernel")
+
+    def spectral_host(self, *a, **k):
         raise NotImplementedError("spectral derivatives are provided for the pair kernel")
 
     def check(self, stream=None) -> bool:

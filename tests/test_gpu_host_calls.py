@@ -1,6 +1,7 @@
-"""Host-buffer calls (vx_rates_eval_host, vx_rates_adjoint_host): the same bits as the device
-calls on a batch of three staging chunks (both slots, a partial last chunk), from pinned and from
-pageable host memory, and their argument checks."""
+"""Host-buffer calls (vx_rates_eval_host, vx_rates_adjoint_host, and the NES kernel's
+vx_nes_eval_host, vx_nes_adjoint_host): the same bits as the device calls on a batch of three
+staging chunks (both slots, a partial last chunk), from pinned and from pageable host memory, and
+their argument checks."""
 import numpy as np
 import pytest
 
@@ -92,4 +93,26 @@ def test_spectral_host_matches_device_call(monkeypatch):
     assert r.check()
     for k in ("blocks", "grad_J", "grad_H") + KEYS:
         assert torch.equal(got[k], ref[k].cpu()), k
+    r.close()
+
+
+def test_nes_host_calls_match_device_calls(monkeypatch):
+    """NES through 8 MiB staging slots: 1,753 zones per chunk at 11 bins, 3 species, so 5,000
+    zones take three chunks."""
+    from paper_1404_1719_gb300 import NesRates, capi
+    monkeypatch.setenv("VX_HOST_SLOT_MB", "8")
+    eps = vx_inputs.energy_centres(11, 1.0, 300.0)
+    st, J, H = vx_inputs.random_zones(5000, 91, n_bins=11)
+    r = NesRates(eps, 8, 24, species=(0, 1, 2))
+    ref = r.adjoint(_dev(st), _dev(J), _dev(H), forward=True)
+    pinned = [torch.from_numpy(x).pin_memory() for x in (st, J, H)]
+    got = r.adjoint_host(*pinned, forward=True, ray_offsets=[0, 1200, 5000])
+    for k in KEYS + ("jac",):
+        assert torch.equal(got[k], ref[k].cpu()), k
+    got2 = r.evaluate_host(st, J, H)  # pageable numpy arrays
+    for k in KEYS:
+        assert torch.equal(got2[k], ref[k].cpu()), k
+    assert r.check()
+    with pytest.raises(capi.VxError):  # offsets that are not a partition, rejected on the host
+        r.adjoint_host(*pinned, ray_offsets=[0, 6000, 5000])
     r.close()
