@@ -176,6 +176,61 @@ __device__ void lu_solve_block(const float *sL, float *sW, int m, int ld) {
     }
 }
 
+// Schur update on the tensor cores (1) or on the FP32 pipe (0). T = A_k G_{k-1} as m16n8k8 TF32
+// MMA tiles with three-term splitting (high x high + high x low + low x high, each operand split
+// into its nearest TF32 value and the remainder: relative error about 2^-22, near FP32's, so each
+// FP64 refinement sweep still gains about cond x 1e-7).
+#ifndef VX_BTD_MMA
+#define VX_BTD_MMA 1
+#endif
+
+__device__ __forceinline__ void btd_mma(float (&d)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3,
+                                        unsigned b0, unsigned b1) {
+    asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+// v = hi + lo, hi the nearest TF32 value, lo the exact remainder rounded to TF32 (error 2^-22 |v|):
+// adding half an ulp of TF32 to the magnitude bits and clearing the last 13 rounds to nearest.
+__device__ __forceinline__ void btd_split(float v, unsigned &hi, unsigned &lo) {
+    hi = (__float_as_uint(v) + 0x1000u) & 0xffffe000u;
+    lo = (__float_as_uint(__fsub_rn(v, __uint_as_float(hi))) + 0x1000u) & 0xffffe000u;
+}
+
+// sT[i][j] = sum_c sA[i][c] sG[c][j] for i, j < m (row stride ld), the m x m product padded to
+// 16-row by 8-column output tiles and 8-deep steps (zero outside m); tiles dealt to the warps
+// round robin. Fragment layout of m16n8k8: lane = 4 g + q holds A rows g and g + 8 at columns q
+// and q + 4 of the step, B rows q and q + 4 at column g, and C rows g, g + 8 at columns 2q, 2q + 1.
+__device__ void schur_mma(const float *__restrict__ sA, const float *__restrict__ sG, float *__restrict__ sT, int m,
+                          int ld) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int g = lane >> 2, q = lane & 3;
+    const int mt = (m + 15) >> 4, nt = (m + 7) >> 3, ks = (m + 7) >> 3;
+    for (int tile = warp; tile < mt * nt; tile += nw) {
+        const int i0 = (tile / nt) * 16, j0 = (tile % nt) * 8;
+        float d[4] = {0.f, 0.f, 0.f, 0.f};
+        const int r0 = i0 + g, r1 = i0 + g + 8, col = j0 + g;
+        for (int k = 0; k < ks; ++k) {
+            const int c0 = 8 * k + q, c1 = c0 + 4;
+            const float a0 = (r0 < m && c0 < m) ? sA[r0 * ld + c0] : 0.f, a1 = (r1 < m && c0 < m) ? sA[r1 * ld + c0] : 0.f;
+            const float a2 = (r0 < m && c1 < m) ? sA[r0 * ld + c1] : 0.f, a3 = (r1 < m && c1 < m) ? sA[r1 * ld + c1] : 0.f;
+            const float b0 = (c0 < m && col < m) ? sG[c0 * ld + col] : 0.f, b1 = (c1 < m && col < m) ? sG[c1 * ld + col] : 0.f;
+            unsigned ah[4], al[4], bh[2], bl[2];
+            btd_split(a0, ah[0], al[0]); btd_split(a1, ah[1], al[1]);
+            btd_split(a2, ah[2], al[2]); btd_split(a3, ah[3], al[3]);
+            btd_split(b0, bh[0], bl[0]); btd_split(b1, bh[1], bl[1]);
+            btd_mma(d, al[0], al[1], al[2], al[3], bh[0], bh[1]);
+            btd_mma(d, ah[0], ah[1], ah[2], ah[3], bl[0], bl[1]);
+            btd_mma(d, ah[0], ah[1], ah[2], ah[3], bh[0], bh[1]);
+        }
+        const int cc = j0 + 2 * q;
+        if (r0 < m && cc < m) sT[r0 * ld + cc] = d[0];
+        if (r0 < m && cc + 1 < m) sT[r0 * ld + cc + 1] = d[1];
+        if (r1 < m && cc < m) sT[r1 * ld + cc] = d[2];
+        if (r1 < m && cc + 1 < m) sT[r1 * ld + cc + 1] = d[3];
+    }
+}
+
 // The factor kernel. Thread (warp w, lane x) of the 8 x 32 CTA holds in registers the elements of
 // D_k in rows w + 8 s (s < RS) and columns x + 32 t (t < CS), RS = ceil(m / 8), CS = ceil(m / 32):
 // B_k is loaded there, the Schur update A_k G_{k-1} is subtracted there (A_k and G_{k-1} from shared
@@ -197,6 +252,7 @@ __global__ void __launch_bounds__(kFactorThreads, 2) k_btd_factor(const BtdArgs 
     float *P = sW + m * ld;      // [m][kPan] the panel columns (by physical row), then L21 and L11
     float *U = P + kPan * m;     // [kPan][m] the panel's pivot rows, trailing columns, then U12
     int *p0 = reinterpret_cast<int *>(U + kPan * m), *pos = p0 + m;
+    float *sT = reinterpret_cast<float *>(pos + m);  // [m][ld] the Schur product A_k G_{k-1} (tensor-core form)
     long long z0, z1;
     if (!ray_range(a, blockIdx.x, z0, z1) || z1 == z0) return;
     if (tid == 0) s_bad = 0;
@@ -219,6 +275,17 @@ __global__ void __launch_bounds__(kFactorThreads, 2) k_btd_factor(const BtdArgs 
             for (int i = warp; i < m; i += 8)
                 for (int c = lane; c < m; c += 32) sA[i * ld + c] = (float)Ak[(size_t)i * m + c];
             __syncthreads();
+#if VX_BTD_MMA
+            schur_mma(sA, sW, sT, m, ld);
+            __syncthreads();
+#pragma unroll
+            for (int s = 0; s < RS; ++s)
+#pragma unroll
+                for (int t = 0; t < CS; ++t) {
+                    const int i = warp + 8 * s, c = lane + 32 * t;
+                    if (i < m && c < m) v[s][t] -= sT[i * ld + c];
+                }
+#else
             for (int c = 0; c < m; ++c) {  // v -= A_k G_{k-1}
                 float ar[RS], gc[CS];
 #pragma unroll
@@ -236,6 +303,7 @@ __global__ void __launch_bounds__(kFactorThreads, 2) k_btd_factor(const BtdArgs 
 #pragma unroll
                     for (int t = 0; t < CS; ++t) v[s][t] = fmaf(-ar[s], gc[t], v[s][t]);
             }
+#endif
             float *At = a.At + k * mm;  // FP32 column-major copy for the solve sweeps
             for (int c = warp; c < m; c += 8)
                 for (int i = lane; i < m; i += 32) At[(size_t)c * m + i] = sA[i * ld + c];
@@ -697,7 +765,8 @@ extern "C" vx_status vx_btd_create(int m, long long max_zones, int n_refine, vx_
     h->ld = m | 1;  // odd row stride: column walks through shared memory hit distinct banks
     h->n_refine = n_refine;
     h->max_zones = max_zones;
-    h->smem = ((size_t)2 * m * h->ld + 2 * (size_t)kPan * m) * sizeof(float) + (size_t)2 * m * sizeof(int);
+    h->smem = ((size_t)2 * m * h->ld + 2 * (size_t)kPan * m) * sizeof(float) + (size_t)2 * m * sizeof(int) +
+              (VX_BTD_MMA ? (size_t)m * h->ld * sizeof(float) : 0);
     h->smem_sweep = ((size_t)2 * ((m * m + 3) & ~3) + m) * sizeof(float);
     const size_t zc = (size_t)(max_zones > 0 ? max_zones : 1), mm = (size_t)m * m;
     cudaError_t e = cudaSuccess;

@@ -109,9 +109,10 @@ def test_nes_host_calls_match_device_calls(monkeypatch):
     got = r.adjoint_host(*pinned, forward=True, ray_offsets=[0, 1200, 5000])
     for k in KEYS + ("jac",):
         assert torch.equal(got[k], ref[k].cpu()), k
+    ref2 = r.evaluate(_dev(st), _dev(J), _dev(H))  # the forward kernel (its own instantiation)
     got2 = r.evaluate_host(st, J, H)  # pageable numpy arrays
     for k in KEYS:
-        assert torch.equal(got2[k], ref[k].cpu()), k
+        assert torch.equal(got2[k], ref2[k].cpu()), k
     assert r.check()
     with pytest.raises(capi.VxError):  # offsets that are not a partition, rejected on the host
         r.adjoint_host(*pinned, ray_offsets=[0, 6000, 5000])
