@@ -102,80 +102,6 @@ __global__ void k_btd_validate(const int *off, int n_rays, long long n_zones, in
     }
 }
 
-// sW <- U^{-1} L^{-1} sW for the m right-hand sides in the columns of sW (rows in pivot order), with
-// the factors of sL in pivot order. Blocks of kSub rows: the block's own triangle first (one thread
-// per column), then the block's update of the rows still to come (rank kSub, a warp per row, lanes
-// along the columns); two CTA barriers per block.
-constexpr int kSub = 8;
-constexpr int kPan = 8;  // columns per LU panel
-__device__ void lu_solve_block(const float *sL, float *sW, int m, int ld) {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5, nt = blockDim.x;
-    for (int j0 = 0; j0 < m; j0 += kSub) {  // forward: unit lower triangle
-        const int jb = m - j0 < kSub ? m - j0 : kSub;
-        for (int c = tid; c < m; c += nt) {
-            float w[kSub];
-#pragma unroll
-            for (int r = 0; r < kSub; ++r) w[r] = r < jb ? sW[(j0 + r) * ld + c] : 0.f;
-#pragma unroll
-            for (int r = 1; r < kSub; ++r)
-#pragma unroll
-                for (int q = 0; q < r; ++q)
-                    if (r < jb) w[r] = fmaf(-sL[(j0 + r) * ld + j0 + q], w[q], w[r]);
-#pragma unroll
-            for (int r = 1; r < kSub; ++r)
-                if (r < jb) sW[(j0 + r) * ld + c] = w[r];
-        }
-        __syncthreads();
-        for (int i = j0 + jb + warp; i < m; i += nw) {
-            float l[kSub];
-#pragma unroll
-            for (int q = 0; q < kSub; ++q) l[q] = q < jb ? sL[i * ld + j0 + q] : 0.f;
-            for (int c = lane; c < m; c += 32) {
-                float acc = sW[i * ld + c];
-#pragma unroll
-                for (int q = 0; q < kSub; ++q)
-                    if (q < jb) acc = fmaf(-l[q], sW[(j0 + q) * ld + c], acc);
-                sW[i * ld + c] = acc;
-            }
-        }
-        __syncthreads();
-    }
-    for (int j1 = m; j1 > 0; j1 -= kSub) {  // backward: upper triangle, rows j0 .. j1-1
-        const int j0 = j1 > kSub ? j1 - kSub : 0, jb = j1 - j0;
-        for (int c = tid; c < m; c += nt) {
-            float w[kSub];
-#pragma unroll
-            for (int r = 0; r < kSub; ++r) w[r] = r < jb ? sW[(j0 + r) * ld + c] : 0.f;
-#pragma unroll
-            for (int r = kSub - 1; r >= 0; --r) {
-                if (r < jb) {
-#pragma unroll
-                    for (int q = r + 1; q < kSub; ++q)
-                        if (q < jb) w[r] = fmaf(-sL[(j0 + r) * ld + j0 + q], w[q], w[r]);
-                    w[r] /= sL[(j0 + r) * ld + j0 + r];
-                }
-            }
-#pragma unroll
-            for (int r = 0; r < kSub; ++r)
-                if (r < jb) sW[(j0 + r) * ld + c] = w[r];
-        }
-        __syncthreads();
-        for (int i = warp; i < j0; i += nw) {
-            float u[kSub];
-#pragma unroll
-            for (int q = 0; q < kSub; ++q) u[q] = q < jb ? sL[i * ld + j0 + q] : 0.f;
-            for (int c = lane; c < m; c += 32) {
-                float acc = sW[i * ld + c];
-#pragma unroll
-                for (int q = 0; q < kSub; ++q)
-                    if (q < jb) acc = fmaf(-u[q], sW[(j0 + q) * ld + c], acc);
-                sW[i * ld + c] = acc;
-            }
-        }
-        __syncthreads();
-    }
-}
-
 // Schur update on the tensor cores (1) or on the FP32 pipe (0). T = A_k G_{k-1} as m16n8k8 TF32
 // MMA tiles with three-term splitting (high x high + high x low + low x high, each operand split
 // into its nearest TF32 value and the remainder: relative error about 2^-22, near FP32's, so each
@@ -231,13 +157,131 @@ __device__ void schur_mma(const float *__restrict__ sA, const float *__restrict_
     }
 }
 
+// sW[r][c] -= sum_{q < jb} sL[r][j0 + q] sW[j0 + q][c] for rows r0 <= r < r1 and all m columns: the
+// rank-jb update of one block of a triangular substitution, as 16 x 8 output tiles of one
+// 8-deep MMA step (three-term split as schur_mma; the multiplier enters negated, the tile of sW
+// as the accumulator). The source rows j0 .. j0 + jb lie outside [r0, r1), so tiles only read
+// what no other tile writes.
+__device__ void block_update_mma(const float *__restrict__ sL, float *__restrict__ sW, int m, int ld, int r0, int r1,
+                                 int j0, int jb) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int g = lane >> 2, q = lane & 3;
+    const int nrt = (r1 - r0 + 15) >> 4, nct = (m + 7) >> 3;
+    for (int tile = warp; tile < nrt * nct; tile += nw) {
+        const int i0 = r0 + (tile / nct) * 16, c0 = (tile % nct) * 8;
+        const int ra = i0 + g, rb = ra + 8, col = c0 + g, cc = c0 + 2 * q;
+        const bool va = ra < r1, vb = rb < r1, k0 = q < jb, k1 = q + 4 < jb;
+        const float a0 = va && k0 ? -sL[ra * ld + j0 + q] : 0.f, a1 = vb && k0 ? -sL[rb * ld + j0 + q] : 0.f;
+        const float a2 = va && k1 ? -sL[ra * ld + j0 + q + 4] : 0.f, a3 = vb && k1 ? -sL[rb * ld + j0 + q + 4] : 0.f;
+        const float b0 = k0 && col < m ? sW[(j0 + q) * ld + col] : 0.f, b1 = k1 && col < m ? sW[(j0 + q + 4) * ld + col] : 0.f;
+        float d[4];
+        d[0] = va && cc < m ? sW[ra * ld + cc] : 0.f;
+        d[1] = va && cc + 1 < m ? sW[ra * ld + cc + 1] : 0.f;
+        d[2] = vb && cc < m ? sW[rb * ld + cc] : 0.f;
+        d[3] = vb && cc + 1 < m ? sW[rb * ld + cc + 1] : 0.f;
+        unsigned ah[4], al[4], bh[2], bl[2];
+        btd_split(a0, ah[0], al[0]); btd_split(a1, ah[1], al[1]);
+        btd_split(a2, ah[2], al[2]); btd_split(a3, ah[3], al[3]);
+        btd_split(b0, bh[0], bl[0]); btd_split(b1, bh[1], bl[1]);
+        btd_mma(d, al[0], al[1], al[2], al[3], bh[0], bh[1]);
+        btd_mma(d, ah[0], ah[1], ah[2], ah[3], bl[0], bl[1]);
+        btd_mma(d, ah[0], ah[1], ah[2], ah[3], bh[0], bh[1]);
+        if (va && cc < m) sW[ra * ld + cc] = d[0];
+        if (va && cc + 1 < m) sW[ra * ld + cc + 1] = d[1];
+        if (vb && cc < m) sW[rb * ld + cc] = d[2];
+        if (vb && cc + 1 < m) sW[rb * ld + cc + 1] = d[3];
+    }
+}
+
+// sW <- U^{-1} L^{-1} sW for the m right-hand sides in the columns of sW (rows in pivot order), with
+// the factors of sL in pivot order. Blocks of kSub rows: the block's own triangle first (one thread
+// per column), then the block's update of the rows still to come (rank kSub: block_update_mma on the
+// tensor cores, else a warp per row with lanes along the columns); two CTA barriers per block.
+constexpr int kSub = 8;
+constexpr int kPan = 8;  // columns per LU panel
+__device__ void lu_solve_block(const float *sL, float *sW, int m, int ld) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5, nt = blockDim.x;
+    for (int j0 = 0; j0 < m; j0 += kSub) {  // forward: unit lower triangle
+        const int jb = m - j0 < kSub ? m - j0 : kSub;
+        for (int c = tid; c < m; c += nt) {
+            float w[kSub];
+#pragma unroll
+            for (int r = 0; r < kSub; ++r) w[r] = r < jb ? sW[(j0 + r) * ld + c] : 0.f;
+#pragma unroll
+            for (int r = 1; r < kSub; ++r)
+#pragma unroll
+                for (int q = 0; q < r; ++q)
+                    if (r < jb) w[r] = fmaf(-sL[(j0 + r) * ld + j0 + q], w[q], w[r]);
+#pragma unroll
+            for (int r = 1; r < kSub; ++r)
+                if (r < jb) sW[(j0 + r) * ld + c] = w[r];
+        }
+        __syncthreads();
+#if VX_BTD_MMA
+        block_update_mma(sL, sW, m, ld, j0 + jb, m, j0, jb);
+#else
+        for (int i = j0 + jb + warp; i < m; i += nw) {
+            float l[kSub];
+#pragma unroll
+            for (int q = 0; q < kSub; ++q) l[q] = q < jb ? sL[i * ld + j0 + q] : 0.f;
+            for (int c = lane; c < m; c += 32) {
+                float acc = sW[i * ld + c];
+#pragma unroll
+                for (int q = 0; q < kSub; ++q)
+                    if (q < jb) acc = fmaf(-l[q], sW[(j0 + q) * ld + c], acc);
+                sW[i * ld + c] = acc;
+            }
+        }
+#endif
+        __syncthreads();
+    }
+    for (int j1 = m; j1 > 0; j1 -= kSub) {  // backward: upper triangle, rows j0 .. j1-1
+        const int j0 = j1 > kSub ? j1 - kSub : 0, jb = j1 - j0;
+        for (int c = tid; c < m; c += nt) {
+            float w[kSub];
+#pragma unroll
+            for (int r = 0; r < kSub; ++r) w[r] = r < jb ? sW[(j0 + r) * ld + c] : 0.f;
+#pragma unroll
+            for (int r = kSub - 1; r >= 0; --r) {
+                if (r < jb) {
+#pragma unroll
+                    for (int q = r + 1; q < kSub; ++q)
+                        if (q < jb) w[r] = fmaf(-sL[(j0 + r) * ld + j0 + q], w[q], w[r]);
+                    w[r] /= sL[(j0 + r) * ld + j0 + r];
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < kSub; ++r)
+                if (r < jb) sW[(j0 + r) * ld + c] = w[r];
+        }
+        __syncthreads();
+#if VX_BTD_MMA
+        block_update_mma(sL, sW, m, ld, 0, j0, j0, jb);
+#else
+        for (int i = warp; i < j0; i += nw) {
+            float u[kSub];
+#pragma unroll
+            for (int q = 0; q < kSub; ++q) u[q] = q < jb ? sL[i * ld + j0 + q] : 0.f;
+            for (int c = lane; c < m; c += 32) {
+                float acc = sW[i * ld + c];
+#pragma unroll
+                for (int q = 0; q < kSub; ++q)
+                    if (q < jb) acc = fmaf(-u[q], sW[(j0 + q) * ld + c], acc);
+                sW[i * ld + c] = acc;
+            }
+        }
+#endif
+        __syncthreads();
+    }
+}
+
 // The factor kernel. Thread (warp w, lane x) of the 8 x 32 CTA holds in registers the elements of
 // D_k in rows w + 8 s (s < RS) and columns x + 32 t (t < CS), RS = ceil(m / 8), CS = ceil(m / 32):
 // B_k is loaded there, the Schur update A_k G_{k-1} is subtracted there (A_k and G_{k-1} from shared
 // memory, RS + CS loads per RS x CS FMAs), and the LU runs there, in panels of kPan columns:
 // (1) the panel columns of the rows not yet pivots go to shared memory; (2) warp 0 factors the
-// panel alone (partial pivoting: largest magnitude, lowest position on ties; no CTA barrier inside
-// the panel); (3) the panel's pivot rows publish their trailing columns and every thread takes the
+// panel alone, in registers (partial pivoting: largest magnitude, lowest physical row on ties; no
+// CTA barrier inside the panel); (3) the panel's pivot rows publish their trailing columns and every thread takes the
 // factored panel columns back; (4) U12 = L11^{-1} U by one thread per trailing column; (5) the pivot
 // rows take U12 and every other row gets the rank-kPan update in registers. Rows are never moved:
 // the pivot order is an index vector. Five CTA barriers per panel. At the end the factors are
@@ -308,11 +352,14 @@ __global__ void __launch_bounds__(kFactorThreads, 2) k_btd_factor(const BtdArgs 
             for (int c = warp; c < m; c += 8)
                 for (int i = lane; i < m; i += 32) At[(size_t)c * m + i] = sA[i * ld + c];
         }
-        for (int q = tid; q < m; q += kFactorThreads) p0[q] = q;
         __syncthreads();
         // LU in registers, in panels of kPan columns
-        int *cur = p0;      // position -> physical row; written only by warp 0 inside a panel
+        int *cur = p0;      // position -> physical row, set by warp 0 as the pivots are chosen
         unsigned done = 0u;  // bit s: my row warp + 8 s has been a pivot
+        unsigned live = 0u;  // warp 0, bit t: row lane + 32 t is not yet a pivot
+#pragma unroll
+        for (int t = 0; t < CS; ++t)
+            if (lane + 32 * t < m) live |= 1u << t;
         for (int j0 = 0; j0 < m; j0 += kPan) {
             const int jb = m - j0 < kPan ? m - j0 : kPan;
             // (1) the panel columns of the rows not yet pivots go to P[row][0 .. jb)
@@ -327,46 +374,66 @@ __global__ void __launch_bounds__(kFactorThreads, 2) k_btd_factor(const BtdArgs 
                     }
             }
             __syncthreads();
-            // (2) warp 0 factors the panel: partial pivoting over the positions not yet pivots
+            // (2) warp 0 factors the panel in registers (rows lane + 32 t): partial pivoting, the
+            //     largest magnitude by a warp max over the magnitudes' bit patterns, the lowest
+            //     physical row among equal magnitudes by a warp min; no CTA barrier inside the panel
             if (warp == 0) {
-                for (int jj = 0; jj < jb; ++jj) {
-                    const int j = j0 + jj;
-                    float best = -1.f;
-                    int bq = j;
-                    for (int q = j + lane; q < m; q += 32) {
-                        const float x = fabsf(P[cur[q] * kPan + jj]);
-                        if (x > best) {
-                            best = x;
-                            bq = q;
-                        }
-                    }
+                float pr[CS][kPan];
+                const unsigned live0 = live;
 #pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) {
-                        const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-                        const int oq = __shfl_xor_sync(0xffffffffu, bq, o);
-                        if (ob > best || (ob == best && oq < bq)) {
-                            best = ob;
-                            bq = oq;
+                for (int t = 0; t < CS; ++t)
+#pragma unroll
+                    for (int kk = 0; kk < kPan; ++kk)
+                        pr[t][kk] = ((live0 >> t) & 1u) && kk < jb ? P[(lane + 32 * t) * kPan + kk] : 0.f;
+#pragma unroll
+                for (int jj = 0; jj < kPan; ++jj) {
+                    if (jj >= jb) break;
+                    unsigned key = 0u;  // |x| bits + 1 (NaN: 1) for a candidate row, 0 for none
+                    int brow = 0x7fffffff;
+#pragma unroll
+                    for (int t = 0; t < CS; ++t)
+                        if ((live >> t) & 1u) {
+                            const float x = fabsf(pr[t][jj]);
+                            const unsigned kx = x == x ? __float_as_uint(x) + 1u : 1u;
+                            if (kx > key) {
+                                key = kx;
+                                brow = lane + 32 * t;
+                            }
                         }
+                    const unsigned kmax = __reduce_max_sync(0xffffffffu, key);
+                    const int prow = (int)__reduce_min_sync(0xffffffffu, key == kmax ? (unsigned)brow : 0xffffffffu);
+                    const int owner = prow & 31, tp = prow >> 5;
+                    float pv[kPan];
+#pragma unroll
+                    for (int kk = 0; kk < kPan; ++kk) {
+                        float mine = pr[0][kk];
+#pragma unroll
+                        for (int t = 1; t < CS; ++t)
+                            if (tp == t) mine = pr[t][kk];
+                        pv[kk] = kk >= jj ? __shfl_sync(0xffffffffu, mine, owner) : 0.f;
                     }
-                    const int pj = cur[bq];
-                    __syncwarp();
+                    if (lane == owner) live &= ~(1u << tp);
                     if (lane == 0) {
-                        cur[bq] = cur[j];
-                        cur[j] = pj;
-                        if (!(best > 0.f && best < INFINITY)) s_bad = 1;
+                        cur[j0 + jj] = prow;
+                        if (!(fabsf(pv[jj]) > 0.f && fabsf(pv[jj]) < INFINITY)) s_bad = 1;
                     }
-                    __syncwarp();
-                    const float ipiv = 1.f / P[pj * kPan + jj];
-                    for (int q = j + 1 + lane; q < m; q += 32) {
-                        const int r = cur[q];
-                        const float l = P[r * kPan + jj] * ipiv;
-                        P[r * kPan + jj] = l;
-                        for (int kk = jj + 1; kk < jb; ++kk)
-                            P[r * kPan + kk] = fmaf(-l, P[pj * kPan + kk], P[r * kPan + kk]);
-                    }
-                    __syncwarp();
+                    const float ipiv = 1.f / pv[jj];
+#pragma unroll
+                    for (int t = 0; t < CS; ++t)
+                        if ((live >> t) & 1u) {
+                            const float l = pr[t][jj] * ipiv;
+                            pr[t][jj] = l;
+#pragma unroll
+                            for (int kk = jj + 1; kk < kPan; ++kk)
+                                if (kk < jb) pr[t][kk] = fmaf(-l, pv[kk], pr[t][kk]);
+                        }
                 }
+#pragma unroll
+                for (int t = 0; t < CS; ++t)
+                    if ((live0 >> t) & 1u)
+#pragma unroll
+                        for (int kk = 0; kk < kPan; ++kk)
+                            if (kk < jb) P[(lane + 32 * t) * kPan + kk] = pr[t][kk];
             }
             __syncthreads();
             // (3) the panel's pivot rows publish their trailing columns to U[a][c]; the panel
