@@ -123,229 +123,179 @@ __device__ __forceinline__ void btd_split(float v, unsigned &hi, unsigned &lo) {
     lo = (__float_as_uint(__fsub_rn(v, __uint_as_float(hi))) + 0x1000u) & 0xffffe000u;
 }
 
-// sT[i][j] = sum_c sA[i][c] sG[c][j] for i, j < m (row stride ld), the m x m product padded to
-// 16-row by 8-column output tiles and 8-deep steps (zero outside m); tiles dealt to the warps
-// round robin. Fragment layout of m16n8k8: lane = 4 g + q holds A rows g and g + 8 at columns q
-// and q + 4 of the step, B rows q and q + 4 at column g, and C rows g, g + 8 at columns 2q, 2q + 1.
-__device__ void schur_mma(const float *__restrict__ sA, const float *__restrict__ sG, float *__restrict__ sT, int m,
-                          int ld) {
+// D[i][j] (+/-)= sum_{k < K} X[i][xo + k] Y[yo + k][j] for rows r0 <= i < r1 and columns j < n (all
+// three with row stride ld) on the tensor cores: 16 x 16 output blocks dealt to the warps round
+// robin, each two m16n8k8 tiles that share the A fragment (split once for both), 8-deep steps
+// (zero beyond K). ACC: D is the accumulator (else overwritten); NEG: the product is subtracted.
+// Fragment layout of m16n8k8: lane = 4 g + q holds A rows g and g + 8 at columns q and q + 4 of
+// the step, B rows q and q + 4 at column g, and C rows g, g + 8 at columns 2q, 2q + 1. The rows of Y
+// that are read lie outside [r0, r1) whenever Y and D are the same array, so no block reads what
+// another writes.
+template <bool ACC, bool NEG>
+__device__ void mma_rows(const float *X, int xo, const float *Y, int yo, float *D, int ld, int r0, int r1, int n,
+                         int K) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int g = lane >> 2, q = lane & 3;
-    const int mt = (m + 15) >> 4, nt = (m + 7) >> 3, ks = (m + 7) >> 3;
-    for (int tile = warp; tile < mt * nt; tile += nw) {
-        const int i0 = (tile / nt) * 16, j0 = (tile % nt) * 8;
-        float d[4] = {0.f, 0.f, 0.f, 0.f};
-        const int r0 = i0 + g, r1 = i0 + g + 8, col = j0 + g;
+    const int nrb = (r1 - r0 + 15) >> 4, ncb = (n + 15) >> 4, ks = (K + 7) >> 3;
+    for (int blk = warp; blk < nrb * ncb; blk += nw) {
+        const int i0 = r0 + (blk / ncb) * 16, c0 = (blk % ncb) * 16;
+        const int ra = i0 + g, rb = ra + 8;
+        const bool va = ra < r1, vb = rb < r1;
+        float d[2][4];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int cc = c0 + 8 * h + 2 * q;
+            d[h][0] = ACC && va && cc < n ? D[ra * ld + cc] : 0.f;
+            d[h][1] = ACC && va && cc + 1 < n ? D[ra * ld + cc + 1] : 0.f;
+            d[h][2] = ACC && vb && cc < n ? D[rb * ld + cc] : 0.f;
+            d[h][3] = ACC && vb && cc + 1 < n ? D[rb * ld + cc + 1] : 0.f;
+        }
         for (int k = 0; k < ks; ++k) {
-            const int c0 = 8 * k + q, c1 = c0 + 4;
-            const float a0 = (r0 < m && c0 < m) ? sA[r0 * ld + c0] : 0.f, a1 = (r1 < m && c0 < m) ? sA[r1 * ld + c0] : 0.f;
-            const float a2 = (r0 < m && c1 < m) ? sA[r0 * ld + c1] : 0.f, a3 = (r1 < m && c1 < m) ? sA[r1 * ld + c1] : 0.f;
-            const float b0 = (c0 < m && col < m) ? sG[c0 * ld + col] : 0.f, b1 = (c1 < m && col < m) ? sG[c1 * ld + col] : 0.f;
-            unsigned ah[4], al[4], bh[2], bl[2];
+            const int ka = 8 * k + q, kb = ka + 4;
+            const bool ia = ka < K, ib = kb < K;
+            float a0 = va && ia ? X[ra * ld + xo + ka] : 0.f, a1 = vb && ia ? X[rb * ld + xo + ka] : 0.f;
+            float a2 = va && ib ? X[ra * ld + xo + kb] : 0.f, a3 = vb && ib ? X[rb * ld + xo + kb] : 0.f;
+            if (NEG) {
+                a0 = -a0; a1 = -a1; a2 = -a2; a3 = -a3;
+            }
+            unsigned ah[4], al[4];
             btd_split(a0, ah[0], al[0]); btd_split(a1, ah[1], al[1]);
             btd_split(a2, ah[2], al[2]); btd_split(a3, ah[3], al[3]);
-            btd_split(b0, bh[0], bl[0]); btd_split(b1, bh[1], bl[1]);
-            btd_mma(d, al[0], al[1], al[2], al[3], bh[0], bh[1]);
-            btd_mma(d, ah[0], ah[1], ah[2], ah[3], bl[0], bl[1]);
-            btd_mma(d, ah[0], ah[1], ah[2], ah[3], bh[0], bh[1]);
-        }
-        const int cc = j0 + 2 * q;
-        if (r0 < m && cc < m) sT[r0 * ld + cc] = d[0];
-        if (r0 < m && cc + 1 < m) sT[r0 * ld + cc + 1] = d[1];
-        if (r1 < m && cc < m) sT[r1 * ld + cc] = d[2];
-        if (r1 < m && cc + 1 < m) sT[r1 * ld + cc + 1] = d[3];
-    }
-}
-
-// sW[r][c] -= sum_{q < jb} sL[r][j0 + q] sW[j0 + q][c] for rows r0 <= r < r1 and all m columns: the
-// rank-jb update of one block of a triangular substitution, as 16 x 8 output tiles of one
-// 8-deep MMA step (three-term split as schur_mma; the multiplier enters negated, the tile of sW
-// as the accumulator). The source rows j0 .. j0 + jb lie outside [r0, r1), so tiles only read
-// what no other tile writes.
-__device__ void block_update_mma(const float *__restrict__ sL, float *__restrict__ sW, int m, int ld, int r0, int r1,
-                                 int j0, int jb) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int g = lane >> 2, q = lane & 3;
-    const int nrt = (r1 - r0 + 15) >> 4, nct = (m + 7) >> 3;
-    for (int tile = warp; tile < nrt * nct; tile += nw) {
-        const int i0 = r0 + (tile / nct) * 16, c0 = (tile % nct) * 8;
-        const int ra = i0 + g, rb = ra + 8, col = c0 + g, cc = c0 + 2 * q;
-        const bool va = ra < r1, vb = rb < r1, k0 = q < jb, k1 = q + 4 < jb;
-        const float a0 = va && k0 ? -sL[ra * ld + j0 + q] : 0.f, a1 = vb && k0 ? -sL[rb * ld + j0 + q] : 0.f;
-        const float a2 = va && k1 ? -sL[ra * ld + j0 + q + 4] : 0.f, a3 = vb && k1 ? -sL[rb * ld + j0 + q + 4] : 0.f;
-        const float b0 = k0 && col < m ? sW[(j0 + q) * ld + col] : 0.f, b1 = k1 && col < m ? sW[(j0 + q + 4) * ld + col] : 0.f;
-        float d[4];
-        d[0] = va && cc < m ? sW[ra * ld + cc] : 0.f;
-        d[1] = va && cc + 1 < m ? sW[ra * ld + cc + 1] : 0.f;
-        d[2] = vb && cc < m ? sW[rb * ld + cc] : 0.f;
-        d[3] = vb && cc + 1 < m ? sW[rb * ld + cc + 1] : 0.f;
-        unsigned ah[4], al[4], bh[2], bl[2];
-        btd_split(a0, ah[0], al[0]); btd_split(a1, ah[1], al[1]);
-        btd_split(a2, ah[2], al[2]); btd_split(a3, ah[3], al[3]);
-        btd_split(b0, bh[0], bl[0]); btd_split(b1, bh[1], bl[1]);
-        btd_mma(d, al[0], al[1], al[2], al[3], bh[0], bh[1]);
-        btd_mma(d, ah[0], ah[1], ah[2], ah[3], bl[0], bl[1]);
-        btd_mma(d, ah[0], ah[1], ah[2], ah[3], bh[0], bh[1]);
-        if (va && cc < m) sW[ra * ld + cc] = d[0];
-        if (va && cc + 1 < m) sW[ra * ld + cc + 1] = d[1];
-        if (vb && cc < m) sW[rb * ld + cc] = d[2];
-        if (vb && cc + 1 < m) sW[rb * ld + cc + 1] = d[3];
-    }
-}
-
-// sW <- U^{-1} L^{-1} sW for the m right-hand sides in the columns of sW (rows in pivot order), with
-// the factors of sL in pivot order. Blocks of kSub rows: the block's own triangle first (one thread
-// per column), then the block's update of the rows still to come (rank kSub: block_update_mma on the
-// tensor cores, else a warp per row with lanes along the columns); two CTA barriers per block.
-constexpr int kSub = 8;
-constexpr int kPan = 8;  // columns per LU panel
-__device__ void lu_solve_block(const float *sL, float *sW, int m, int ld) {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5, nt = blockDim.x;
-    for (int j0 = 0; j0 < m; j0 += kSub) {  // forward: unit lower triangle
-        const int jb = m - j0 < kSub ? m - j0 : kSub;
-        for (int c = tid; c < m; c += nt) {
-            float w[kSub];
 #pragma unroll
-            for (int r = 0; r < kSub; ++r) w[r] = r < jb ? sW[(j0 + r) * ld + c] : 0.f;
-#pragma unroll
-            for (int r = 1; r < kSub; ++r)
-#pragma unroll
-                for (int q = 0; q < r; ++q)
-                    if (r < jb) w[r] = fmaf(-sL[(j0 + r) * ld + j0 + q], w[q], w[r]);
-#pragma unroll
-            for (int r = 1; r < kSub; ++r)
-                if (r < jb) sW[(j0 + r) * ld + c] = w[r];
-        }
-        __syncthreads();
-#if VX_BTD_MMA
-        block_update_mma(sL, sW, m, ld, j0 + jb, m, j0, jb);
-#else
-        for (int i = j0 + jb + warp; i < m; i += nw) {
-            float l[kSub];
-#pragma unroll
-            for (int q = 0; q < kSub; ++q) l[q] = q < jb ? sL[i * ld + j0 + q] : 0.f;
-            for (int c = lane; c < m; c += 32) {
-                float acc = sW[i * ld + c];
-#pragma unroll
-                for (int q = 0; q < kSub; ++q)
-                    if (q < jb) acc = fmaf(-l[q], sW[(j0 + q) * ld + c], acc);
-                sW[i * ld + c] = acc;
+            for (int h = 0; h < 2; ++h) {
+                const int col = c0 + 8 * h + g;
+                const float b0 = ia && col < n ? Y[(yo + ka) * ld + col] : 0.f;
+                const float b1 = ib && col < n ? Y[(yo + kb) * ld + col] : 0.f;
+                unsigned bh[2], bl[2];
+                btd_split(b0, bh[0], bl[0]); btd_split(b1, bh[1], bl[1]);
+                btd_mma(d[h], al[0], al[1], al[2], al[3], bh[0], bh[1]);
+                btd_mma(d[h], ah[0], ah[1], ah[2], ah[3], bl[0], bl[1]);
+                btd_mma(d[h], ah[0], ah[1], ah[2], ah[3], bh[0], bh[1]);
             }
         }
-#endif
-        __syncthreads();
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int cc = c0 + 8 * h + 2 * q;
+            if (va && cc < n) D[ra * ld + cc] = d[h][0];
+            if (va && cc + 1 < n) D[ra * ld + cc + 1] = d[h][1];
+            if (vb && cc < n) D[rb * ld + cc] = d[h][2];
+            if (vb && cc + 1 < n) D[rb * ld + cc + 1] = d[h][3];
+        }
     }
-    for (int j1 = m; j1 > 0; j1 -= kSub) {  // backward: upper triangle, rows j0 .. j1-1
-        const int j0 = j1 > kSub ? j1 - kSub : 0, jb = j1 - j0;
-        for (int c = tid; c < m; c += nt) {
-            float w[kSub];
+}
+
+// dst[i][c] = (float) M[row(i)][c] for i, c < m, row(i) = rowmap[i] (rowmap NULL: i), thread (warp,
+// lane) taking rows warp + 8 s and columns lane + 32 t: each of NCH chunks of its rows has all its
+// loads in flight before the first conversion (one DRAM round trip per chunk, not one per element).
+template <int RS, int CS, int NCH>
+__device__ __forceinline__ void stage_rows(const double *__restrict__ M, const int *rowmap, float *dst, int m, int ld,
+                                           int warp, int lane) {
+    static_assert(RS % NCH == 0, "rows per thread in equal chunks");
+    constexpr int H = RS / NCH;
 #pragma unroll
-            for (int r = 0; r < kSub; ++r) w[r] = r < jb ? sW[(j0 + r) * ld + c] : 0.f;
+    for (int h = 0; h < NCH; ++h) {
+        double x[H][CS];
 #pragma unroll
-            for (int r = kSub - 1; r >= 0; --r) {
-                if (r < jb) {
+        for (int s = 0; s < H; ++s) {
+            const int i = warp + 8 * (h * H + s);
+            const int r = i < m ? (rowmap ? rowmap[i] : i) : 0;
 #pragma unroll
-                    for (int q = r + 1; q < kSub; ++q)
-                        if (q < jb) w[r] = fmaf(-sL[(j0 + r) * ld + j0 + q], w[q], w[r]);
-                    w[r] /= sL[(j0 + r) * ld + j0 + r];
+            for (int t = 0; t < CS; ++t) {
+                const int c = lane + 32 * t;
+                x[s][t] = (i < m && c < m) ? __ldg(M + (size_t)r * m + c) : 0.0;
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < H; ++s) {
+            const int i = warp + 8 * (h * H + s);
+#pragma unroll
+            for (int t = 0; t < CS; ++t) {
+                const int c = lane + 32 * t;
+                if (i < m && c < m) dst[i * ld + c] = (float)x[s][t];
+            }
+        }
+    }
+}
+
+// stage_rows for two matrices at once (M1 may be NULL): each half of a thread's rows of both has its
+// loads in flight together.
+template <int RS, int CS>
+__device__ __forceinline__ void stage_two(const double *__restrict__ M1, float *d1, const double *__restrict__ M2,
+                                          float *d2, int m, int ld, int warp, int lane) {
+    static_assert(RS % 2 == 0, "rows per thread in two halves");
+    constexpr int H = RS / 2;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        double x1[H][CS], x2[H][CS];
+#pragma unroll
+        for (int s = 0; s < H; ++s) {
+            const int i = warp + 8 * (h * H + s);
+#pragma unroll
+            for (int t = 0; t < CS; ++t) {
+                const int c = lane + 32 * t;
+                const bool in = i < m && c < m;
+                x1[s][t] = in && M1 ? __ldg(M1 + (size_t)i * m + c) : 0.0;
+                x2[s][t] = in ? __ldg(M2 + (size_t)i * m + c) : 0.0;
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < H; ++s) {
+            const int i = warp + 8 * (h * H + s);
+#pragma unroll
+            for (int t = 0; t < CS; ++t) {
+                const int c = lane + 32 * t;
+                if (i < m && c < m) {
+                    if (M1) d1[i * ld + c] = (float)x1[s][t];
+                    d2[i * ld + c] = (float)x2[s][t];
                 }
             }
-#pragma unroll
-            for (int r = 0; r < kSub; ++r)
-                if (r < jb) sW[(j0 + r) * ld + c] = w[r];
         }
-        __syncthreads();
-#if VX_BTD_MMA
-        block_update_mma(sL, sW, m, ld, 0, j0, j0, jb);
-#else
-        for (int i = warp; i < j0; i += nw) {
-            float u[kSub];
-#pragma unroll
-            for (int q = 0; q < kSub; ++q) u[q] = q < jb ? sL[i * ld + j0 + q] : 0.f;
-            for (int c = lane; c < m; c += 32) {
-                float acc = sW[i * ld + c];
-#pragma unroll
-                for (int q = 0; q < kSub; ++q)
-                    if (q < jb) acc = fmaf(-u[q], sW[(j0 + q) * ld + c], acc);
-                sW[i * ld + c] = acc;
-            }
-        }
-#endif
-        __syncthreads();
     }
 }
 
-// The factor kernel. Thread (warp w, lane x) of the 8 x 32 CTA holds in registers the elements of
-// D_k in rows w + 8 s (s < RS) and columns x + 32 t (t < CS), RS = ceil(m / 8), CS = ceil(m / 32):
-// B_k is loaded there, the Schur update A_k G_{k-1} is subtracted there (A_k and G_{k-1} from shared
-// memory, RS + CS loads per RS x CS FMAs), and the LU runs there, in panels of kPan columns:
-// (1) the panel columns of the rows not yet pivots go to shared memory; (2) warp 0 factors the
-// panel alone, in registers (partial pivoting: largest magnitude, lowest physical row on ties; no
-// CTA barrier inside the panel); (3) the panel's pivot rows publish their trailing columns and every thread takes the
-// factored panel columns back; (4) U12 = L11^{-1} U by one thread per trailing column; (5) the pivot
-// rows take U12 and every other row gets the rank-kPan update in registers. Rows are never moved:
-// the pivot order is an index vector. Five CTA barriers per panel. At the end the factors are
-// written to shared memory in pivot order for the substitutions and the column-major copy.
+// The factor kernel, one CTA of eight warps per ray, its zones in order. B_k and A_k are staged
+// in shared memory and D_k = B_k - A_k G_{k-1} is formed there (tensor cores). Then thread (warp w,
+// lane x) takes into registers the elements of D_k and of C_k in rows x + 32 t (t < CS) and columns
+// w + 8 s (s < RS), so that column j lies in warp j mod 8 alone, and Gauss-Jordan elimination with
+// partial pivoting runs on [D_k | C_k] one column at a time, with one CTA barrier per column:
+//  - the warp that holds column j finds the pivot row (the largest magnitude among the rows not
+//    yet pivots, the lowest row on ties) by two warp reductions and publishes the row and the
+//    multipliers of every other row; a row not yet a pivot keeps its multiplier in column j (an
+//    entry of L);
+//  - after the barrier every warp takes the pivot row's values in its columns by shuffle, writes
+//    them to row j of the factor buffer (the pivot row's entries of L, U_jj and its row of U) and
+//    subtracts the multiples from the other rows, in the columns of D past j and in all of C.
+// The factors of D_k are those of LU with partial pivoting; the rows already pivots are
+// eliminated as well, so at the end the C part of pivot row j is U_jj G_k[j] and no substitution
+// is left. Rows are never moved: cur maps pivot positions to physical rows.
 template <int RS, int CS>
-__global__ void __launch_bounds__(kFactorThreads, 2) k_btd_factor(const BtdArgs a) {
+__global__ void __launch_bounds__(kFactorThreads, RS > 12 ? 1 : 2) k_btd_factor(const BtdArgs a) {  // m > 96: one CTA per SM (shared memory)
     extern __shared__ __align__(16) float sm[];
     __shared__ int s_bad;
+    __shared__ int s_r[2];
     const int m = a.m, ld = a.ld, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    float *sA = sm;              // A_k, then the factors of D_k in pivot order
-    float *sW = sA + m * ld;     // G_{k-1}, then P C_k -> G_k
-    float *P = sW + m * ld;      // [m][kPan] the panel columns (by physical row), then L21 and L11
-    float *U = P + kPan * m;     // [kPan][m] the panel's pivot rows, trailing columns, then U12
-    int *p0 = reinterpret_cast<int *>(U + kPan * m), *pos = p0 + m;
-    float *sT = reinterpret_cast<float *>(pos + m);  // [m][ld] the Schur product A_k G_{k-1} (tensor-core form)
+    float *sA = sm;           // A_k, then the factors of D_k in pivot order, a row per column step
+    float *sW = sA + m * ld;  // G_{k-1}, then C_k, then G_k
+    float *sT = sW + m * ld;  // B_k, then D_k
+    float *sL = sT + m * ld;  // [2][m] the multipliers of the current column (two buffers)
+    int *cur = reinterpret_cast<int *>(sL + 2 * m), *pos = cur + m;
     long long z0, z1;
     if (!ray_range(a, blockIdx.x, z0, z1) || z1 == z0) return;
     if (tid == 0) s_bad = 0;
     const size_t mm = (size_t)m * m;
     for (long long k = z0; k < z1; ++k) {
-        const bool prev = k > z0;
-        float v[RS][CS];
-        {
-            const double *Bk = a.B + k * mm;
-#pragma unroll
-            for (int s = 0; s < RS; ++s)
-#pragma unroll
-                for (int t = 0; t < CS; ++t) {
-                    const int i = warp + 8 * s, c = lane + 32 * t;
-                    v[s][t] = (i < m && c < m) ? (float)Bk[(size_t)i * m + c] : 0.f;
-                }
-        }
+        const bool prev = k > z0, next = k + 1 < z1;
+        stage_two<RS, CS>(prev ? a.A + k * mm : nullptr, sA, a.B + k * mm, sT, m, ld, warp, lane);
+        __syncthreads();
         if (prev) {
-            const double *Ak = a.A + k * mm;
-            for (int i = warp; i < m; i += 8)
-                for (int c = lane; c < m; c += 32) sA[i * ld + c] = (float)Ak[(size_t)i * m + c];
-            __syncthreads();
 #if VX_BTD_MMA
-            schur_mma(sA, sW, sT, m, ld);
-            __syncthreads();
-#pragma unroll
-            for (int s = 0; s < RS; ++s)
-#pragma unroll
-                for (int t = 0; t < CS; ++t) {
-                    const int i = warp + 8 * s, c = lane + 32 * t;
-                    if (i < m && c < m) v[s][t] -= sT[i * ld + c];
-                }
+            mma_rows<true, true>(sA, 0, sW, 0, sT, ld, 0, m, m, m);  // sT = B_k - A_k G_{k-1}
 #else
-            for (int c = 0; c < m; ++c) {  // v -= A_k G_{k-1}
-                float ar[RS], gc[CS];
-#pragma unroll
-                for (int s = 0; s < RS; ++s) {
-                    const int i = warp + 8 * s;
-                    ar[s] = i < m ? sA[i * ld + c] : 0.f;
-                }
-#pragma unroll
-                for (int t = 0; t < CS; ++t) {
-                    const int col = lane + 32 * t;
-                    gc[t] = col < m ? sW[c * ld + col] : 0.f;
-                }
-#pragma unroll
-                for (int s = 0; s < RS; ++s)
-#pragma unroll
-                    for (int t = 0; t < CS; ++t) v[s][t] = fmaf(-ar[s], gc[t], v[s][t]);
+            for (int e = tid; e < m * m; e += kFactorThreads) {
+                const int i = e / m, c = e % m;
+                float acc = sT[i * ld + c];
+                for (int q = 0; q < m; ++q) acc = fmaf(-sA[i * ld + q], sW[q * ld + c], acc);
+                sT[i * ld + c] = acc;
             }
 #endif
             float *At = a.At + k * mm;  // FP32 column-major copy for the solve sweeps
@@ -353,197 +303,122 @@ __global__ void __launch_bounds__(kFactorThreads, 2) k_btd_factor(const BtdArgs 
                 for (int i = lane; i < m; i += 32) At[(size_t)c * m + i] = sA[i * ld + c];
         }
         __syncthreads();
-        // LU in registers, in panels of kPan columns
-        int *cur = p0;      // position -> physical row, set by warp 0 as the pivots are chosen
-        unsigned done = 0u;  // bit s: my row warp + 8 s has been a pivot
-        unsigned live = 0u;  // warp 0, bit t: row lane + 32 t is not yet a pivot
+        if (next) stage_rows<RS, CS, 2>(a.C + k * mm, nullptr, sW, m, ld, warp, lane);
+        float v[RS][CS], w[RS][CS];  // D_k and C_k: rows lane + 32 t, columns warp + 8 s
 #pragma unroll
-        for (int t = 0; t < CS; ++t)
-            if (lane + 32 * t < m) live |= 1u << t;
-        for (int j0 = 0; j0 < m; j0 += kPan) {
-            const int jb = m - j0 < kPan ? m - j0 : kPan;
-            // (1) the panel columns of the rows not yet pivots go to P[row][0 .. jb)
+        for (int s = 0; s < RS; ++s)
 #pragma unroll
             for (int t = 0; t < CS; ++t) {
-                const int c = lane + 32 * t;
-                if (c >= j0 && c < j0 + jb)
-#pragma unroll
-                    for (int s = 0; s < RS; ++s) {
-                        const int i = warp + 8 * s;
-                        if (i < m && !((done >> s) & 1u)) P[i * kPan + (c - j0)] = v[s][t];
-                    }
+                const int i = lane + 32 * t, c = warp + 8 * s;
+                v[s][t] = i < m && c < m ? sT[i * ld + c] : 0.f;
             }
-            __syncthreads();
-            // (2) warp 0 factors the panel in registers (rows lane + 32 t): partial pivoting, the
-            //     largest magnitude by a warp max over the magnitudes' bit patterns, the lowest
-            //     physical row among equal magnitudes by a warp min; no CTA barrier inside the panel
-            if (warp == 0) {
-                float pr[CS][kPan];
-                const unsigned live0 = live;
-#pragma unroll
-                for (int t = 0; t < CS; ++t)
-#pragma unroll
-                    for (int kk = 0; kk < kPan; ++kk)
-                        pr[t][kk] = ((live0 >> t) & 1u) && kk < jb ? P[(lane + 32 * t) * kPan + kk] : 0.f;
-#pragma unroll
-                for (int jj = 0; jj < kPan; ++jj) {
-                    if (jj >= jb) break;
-                    unsigned key = 0u;  // |x| bits + 1 (NaN: 1) for a candidate row, 0 for none
-                    int brow = 0x7fffffff;
-#pragma unroll
-                    for (int t = 0; t < CS; ++t)
-                        if ((live >> t) & 1u) {
-                            const float x = fabsf(pr[t][jj]);
-                            const unsigned kx = x == x ? __float_as_uint(x) + 1u : 1u;
-                            if (kx > key) {
-                                key = kx;
-                                brow = lane + 32 * t;
-                            }
-                        }
-                    const unsigned kmax = __reduce_max_sync(0xffffffffu, key);
-                    const int prow = (int)__reduce_min_sync(0xffffffffu, key == kmax ? (unsigned)brow : 0xffffffffu);
-                    const int owner = prow & 31, tp = prow >> 5;
-                    float pv[kPan];
-#pragma unroll
-                    for (int kk = 0; kk < kPan; ++kk) {
-                        float mine = pr[0][kk];
-#pragma unroll
-                        for (int t = 1; t < CS; ++t)
-                            if (tp == t) mine = pr[t][kk];
-                        pv[kk] = kk >= jj ? __shfl_sync(0xffffffffu, mine, owner) : 0.f;
-                    }
-                    if (lane == owner) live &= ~(1u << tp);
-                    if (lane == 0) {
-                        cur[j0 + jj] = prow;
-                        if (!(fabsf(pv[jj]) > 0.f && fabsf(pv[jj]) < INFINITY)) s_bad = 1;
-                    }
-                    const float ipiv = 1.f / pv[jj];
-#pragma unroll
-                    for (int t = 0; t < CS; ++t)
-                        if ((live >> t) & 1u) {
-                            const float l = pr[t][jj] * ipiv;
-                            pr[t][jj] = l;
-#pragma unroll
-                            for (int kk = jj + 1; kk < kPan; ++kk)
-                                if (kk < jb) pr[t][kk] = fmaf(-l, pv[kk], pr[t][kk]);
-                        }
-                }
-#pragma unroll
-                for (int t = 0; t < CS; ++t)
-                    if ((live0 >> t) & 1u)
-#pragma unroll
-                        for (int kk = 0; kk < kPan; ++kk)
-                            if (kk < jb) P[(lane + 32 * t) * kPan + kk] = pr[t][kk];
-            }
-            __syncthreads();
-            // (3) the panel's pivot rows publish their trailing columns to U[a][c]; the panel
-            //     columns come back from P; the panel's pivot rows are now done
-            for (int a = 0; a < jb; ++a) {
-                const int pr = cur[j0 + a];
-                if (warp == (pr & 7)) {
-                    const int sp = pr >> 3;
-#pragma unroll
-                    for (int s = 0; s < RS; ++s)
-                        if (s == sp)
-#pragma unroll
-                            for (int t = 0; t < CS; ++t) {
-                                const int c = lane + 32 * t;
-                                if (c >= j0 + jb && c < m) U[a * m + c] = v[s][t];
-                            }
-                }
-            }
-#pragma unroll
-            for (int t = 0; t < CS; ++t) {
-                const int c = lane + 32 * t;
-                if (c >= j0 && c < j0 + jb)
-#pragma unroll
-                    for (int s = 0; s < RS; ++s) {
-                        const int i = warp + 8 * s;
-                        if (i < m && !((done >> s) & 1u)) v[s][t] = P[i * kPan + (c - j0)];
-                    }
-            }
-            for (int a = 0; a < jb; ++a) {
-                const int pr = cur[j0 + a];
-                if (warp == (pr & 7)) done |= 1u << (pr >> 3);
-            }
-            __syncthreads();
-            // (4) U12 = L11^{-1} U, one thread per trailing column
-            for (int c = j0 + jb + tid; c < m; c += kFactorThreads) {
-                float u[kPan];
-#pragma unroll
-                for (int a = 0; a < kPan; ++a) u[a] = a < jb ? U[a * m + c] : 0.f;
-#pragma unroll
-                for (int a = 1; a < kPan; ++a)
-                    if (a < jb) {
-                        const float *la = P + cur[j0 + a] * kPan;
-#pragma unroll
-                        for (int b = 0; b < a; ++b) u[a] = fmaf(-la[b], u[b], u[a]);
-                    }
-#pragma unroll
-                for (int a = 0; a < kPan; ++a)
-                    if (a < jb) U[a * m + c] = u[a];
-            }
-            __syncthreads();
-            // (5) the pivot rows take U12; the other rows get the rank-jb update
-            for (int a = 0; a < jb; ++a) {
-                const int pr = cur[j0 + a];
-                if (warp == (pr & 7)) {
-                    const int sp = pr >> 3;
-#pragma unroll
-                    for (int s = 0; s < RS; ++s)
-                        if (s == sp)
-#pragma unroll
-                            for (int t = 0; t < CS; ++t) {
-                                const int c = lane + 32 * t;
-                                if (c >= j0 + jb && c < m) v[s][t] = U[a * m + c];
-                            }
-                }
-            }
-#pragma unroll
-            for (int s = 0; s < RS; ++s) {
-                const int i = warp + 8 * s;
-                if (i < m && !((done >> s) & 1u)) {
-                    float l[kPan];
-#pragma unroll
-                    for (int a = 0; a < kPan; ++a) l[a] = a < jb ? P[i * kPan + a] : 0.f;
-#pragma unroll
-                    for (int t = 0; t < CS; ++t) {
-                        const int c = lane + 32 * t;
-                        if (c >= j0 + jb && c < m) {
-                            float acc = v[s][t];
-#pragma unroll
-                            for (int a = 0; a < kPan; ++a)
-                                if (a < jb) acc = fmaf(-l[a], U[a * m + c], acc);
-                            v[s][t] = acc;
-                        }
-                    }
-                }
-            }
-            __syncthreads();
-        }
-        // factors in pivot order (A_k is no longer needed: the barriers above ordered its last reads)
-        for (int q = tid; q < m; q += kFactorThreads) pos[cur[q]] = q;
         __syncthreads();
 #pragma unroll
         for (int s = 0; s < RS; ++s)
 #pragma unroll
             for (int t = 0; t < CS; ++t) {
-                const int i = warp + 8 * s, c = lane + 32 * t;
-                if (i < m && c < m) sA[pos[i] * ld + c] = v[s][t];
+                const int i = lane + 32 * t, c = warp + 8 * s;
+                w[s][t] = next && i < m && c < m ? sW[i * ld + c] : 0.f;
             }
+        unsigned done = 0u;  // bit t: my row lane + 32 t has been a pivot
+#pragma unroll
+        for (int sj = 0; sj < RS; ++sj) {
+            for (int wj = 0; wj < 8; ++wj) {
+                const int j = 8 * sj + wj;
+                if (j >= m) break;
+                const int buf = j & 1;
+                if (warp == wj) {  // column j: the pivot row and the multipliers
+                    unsigned key = 0u;  // |x| bits + 1 (NaN: 1) for a candidate row, 0 for none
+                    unsigned brow = 0xffffffffu;
+#pragma unroll
+                    for (int t = 0; t < CS; ++t) {
+                        const int i = lane + 32 * t;
+                        if (i < m && !((done >> t) & 1u)) {
+                            const float x = fabsf(v[sj][t]);
+                            const unsigned kx = x == x ? __float_as_uint(x) + 1u : 1u;
+                            if (kx > key) {
+                                key = kx;
+                                brow = (unsigned)i;
+                            }
+                        }
+                    }
+                    const unsigned kmax = __reduce_max_sync(0xffffffffu, key);
+                    const int r = (int)__reduce_min_sync(0xffffffffu, key == kmax ? brow : 0xffffffffu);
+                    const int tr = r >> 5;
+                    float mine = v[sj][0];
+#pragma unroll
+                    for (int t = 1; t < CS; ++t)
+                        if (tr == t) mine = v[sj][t];
+                    const float piv = __shfl_sync(0xffffffffu, mine, r & 31), rp = 1.f / piv;
+                    if (lane == 0) {
+                        s_r[buf] = r;
+                        cur[j] = r;
+                        if (!(fabsf(piv) > 0.f && fabsf(piv) < INFINITY)) s_bad = 1;
+                    }
+#pragma unroll
+                    for (int t = 0; t < CS; ++t) {
+                        const int i = lane + 32 * t;
+                        if (i < m) {
+                            const float lv = i != r ? v[sj][t] * rp : 0.f;
+                            sL[buf * m + i] = lv;
+                            if (i != r && !((done >> t) & 1u)) v[sj][t] = lv;  // an entry of L
+                        }
+                    }
+                }
+                __syncthreads();
+                const int r = s_r[buf], rl = r & 31, tr = r >> 5;
+                float lt[CS];
+#pragma unroll
+                for (int t = 0; t < CS; ++t) {
+                    const int i = lane + 32 * t;
+                    lt[t] = i < m ? sL[buf * m + i] : 0.f;
+                }
+                if (lane == rl) done |= 1u << tr;
+#pragma unroll
+                for (int s = 0; s < RS; ++s) {
+                    float vd = v[s][0], vc = w[s][0];
+#pragma unroll
+                    for (int t = 1; t < CS; ++t)
+                        if (tr == t) {
+                            vd = v[s][t];
+                            vc = w[s][t];
+                        }
+                    const float pd = __shfl_sync(0xffffffffu, vd, rl), pc = __shfl_sync(0xffffffffu, vc, rl);
+                    const int c = warp + 8 * s;
+                    if (lane == 0 && c < m) sA[j * ld + c] = pd;  // row j of the factors
+                    if (s > sj || (s == sj && warp > wj)) {   // the columns of D past j
+#pragma unroll
+                        for (int t = 0; t < CS; ++t) v[s][t] = fmaf(-lt[t], pd, v[s][t]);
+                    }
+#pragma unroll
+                    for (int t = 0; t < CS; ++t) w[s][t] = fmaf(-lt[t], pc, w[s][t]);
+                }
+            }
+        }
+        __syncthreads();
+        for (int q = tid; q < m; q += kFactorThreads) pos[cur[q]] = q;
+        __syncthreads();
+        if (next) {  // G_k[p] = (C part of pivot row p) / U_pp
+#pragma unroll
+            for (int t = 0; t < CS; ++t) {
+                const int i = lane + 32 * t;
+                if (i < m) {
+                    const int p = pos[i];
+                    const float ru = 1.f / sA[p * ld + p];
+#pragma unroll
+                    for (int s = 0; s < RS; ++s) {
+                        const int c = warp + 8 * s;
+                        if (c < m) sW[p * ld + c] = w[s][t] * ru;
+                    }
+                }
+            }
+        }
         __syncthreads();
         float *LUt = a.LUt + k * mm;
         for (int c = warp; c < m; c += 8)
             for (int i = lane; i < m; i += 32) LUt[(size_t)c * m + i] = sA[i * ld + c];
         for (int i = tid; i < m; i += kFactorThreads) a.perm[k * m + i] = cur[i];
-        if (k + 1 < z1) {
-            const double *Ck = a.C + k * mm;
-            for (int i = warp; i < m; i += 8) {
-                const double *row = Ck + (size_t)cur[i] * m;
-                for (int c = lane; c < m; c += 32) sW[i * ld + c] = (float)row[c];
-            }
-            __syncthreads();
-            lu_solve_block(sA, sW, m, ld);
+        if (next) {
             float *Gt = a.Gt + k * mm;
             for (int c = warp; c < m; c += 8)
                 for (int i = lane; i < m; i += 32) Gt[(size_t)c * m + i] = sW[i * ld + c];
@@ -832,8 +707,7 @@ extern "C" vx_status vx_btd_create(int m, long long max_zones, int n_refine, vx_
     h->ld = m | 1;  // odd row stride: column walks through shared memory hit distinct banks
     h->n_refine = n_refine;
     h->max_zones = max_zones;
-    h->smem = ((size_t)2 * m * h->ld + 2 * (size_t)kPan * m) * sizeof(float) + (size_t)2 * m * sizeof(int) +
-              (VX_BTD_MMA ? (size_t)m * h->ld * sizeof(float) : 0);
+    h->smem = ((size_t)3 * m * h->ld + 2 * m) * sizeof(float) + (size_t)2 * m * sizeof(int);
     h->smem_sweep = ((size_t)2 * ((m * m + 3) & ~3) + m) * sizeof(float);
     const size_t zc = (size_t)(max_zones > 0 ? max_zones : 1), mm = (size_t)m * m;
     cudaError_t e = cudaSuccess;
