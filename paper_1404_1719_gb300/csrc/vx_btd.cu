@@ -253,18 +253,128 @@ __device__ __forceinline__ void stage_two(const double *__restrict__ M1, float *
     }
 }
 
+// Row stride of the factor rows in shared memory: row j keeps the eight warps' column slots
+// contiguous (warp w's RS slots at w RS, column c at (c mod 8) RS + c / 8), padded to 16 bytes.
+template <int RS>
+__host__ __device__ constexpr int factor_ldu() {
+    return 8 * RS + 4;
+}
+static_assert(factor_ldu<12>() % 4 == 0, "factor rows on 16-byte boundaries");
+
+// Named barriers of the column steps: the warp that publishes column j arrives, the others wait.
+// Steps alternate between barriers 1 and 2: the publishing warp arrives early and goes on to wait
+// at the next step, which on a single barrier could count towards the step still open. With two,
+// every warp reaches the barrier of step j only after waiting at step j - 1 (no warp publishes two
+// steps in a row), so the barrier's previous use, step j - 2, has completed.
+__device__ __forceinline__ void step_arrive(int j) {
+    asm volatile("bar.arrive %0, %1;" ::"r"(1 + (j & 1)), "n"(kFactorThreads) : "memory");
+}
+__device__ __forceinline__ void step_wait(int j) {
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + (j & 1)), "n"(kFactorThreads) : "memory");
+}
+
+// Column j of D_k, in slot S of the calling warp (column warp + 8 S): the pivot row (the largest
+// magnitude among the rows not yet pivots, the lowest row on ties, by two warp reductions) and the
+// multipliers of every other row, published to buffer j mod 2; a row not yet a pivot keeps its
+// multiplier in column j (an entry of L). Ends with the warp's arrival at the step barrier.
+template <int RS, int CS>
+__device__ __forceinline__ void gj_publish(float (&v)[RS][CS], const int S, unsigned done, int j, int m, int lane,
+                                           float *sL, int *s_r, int *cur, int *s_bad) {
+    unsigned key = 0u;  // |x| bits + 1 (NaN: 1) for a candidate row, 0 for none
+    unsigned brow = 0xffffffffu;
+#pragma unroll
+    for (int t = 0; t < CS; ++t) {
+        const int i = lane + 32 * t;
+        if (i < m && !((done >> t) & 1u)) {
+            const float x = fabsf(v[S][t]);
+            const unsigned kx = x == x ? __float_as_uint(x) + 1u : 1u;
+            if (kx > key) {
+                key = kx;
+                brow = (unsigned)i;
+            }
+        }
+    }
+    const unsigned kmax = __reduce_max_sync(0xffffffffu, key);
+    const int r = (int)__reduce_min_sync(0xffffffffu, key == kmax ? brow : 0xffffffffu);
+    const int tr = r >> 5;
+    float mine = v[S][0];
+#pragma unroll
+    for (int t = 1; t < CS; ++t)
+        if (tr == t) mine = v[S][t];
+    const float piv = __shfl_sync(0xffffffffu, mine, r & 31), rp = 1.f / piv;
+    const int buf = j & 1;
+    if (lane == 0) {
+        s_r[buf] = r;
+        cur[j] = r;
+        if (!(fabsf(piv) > 0.f && fabsf(piv) < INFINITY)) *s_bad = 1;
+    }
+#pragma unroll
+    for (int t = 0; t < CS; ++t) {
+        const int i = lane + 32 * t;
+        if (i < m) {
+            const float lv = i != r ? v[S][t] * rp : 0.f;
+            sL[buf * m + i] = lv;
+            if (i != r && !((done >> t) & 1u)) v[S][t] = lv;
+        }
+    }
+    step_arrive(j);
+}
+
+// The elimination of column j (slot sj of warp wj) from the calling warp's part of [D_k | C_k],
+// the pivot row's slot TR known at compile time (the pivot row's values come by shuffle from lane
+// rl): row j of the factors to sU, D's columns past j and all of C's updated with the multipliers
+// lt. If the warp holds column j + 1 (np), that column is updated first and published before the
+// rest (look-ahead).
+template <int RS, int CS, int TR>
+__device__ __forceinline__ void gj_eliminate(float (&v)[RS][CS], float (&w)[RS][CS], const float (&lt)[CS], int rl,
+                                             const int sj, int wj, int warp, int lane, int j, int m, bool np,
+                                             unsigned done, float *sU, float *sL, int *s_r, int *cur, int *s_bad) {
+    float pd[RS];
+#pragma unroll
+    for (int s = 0; s < RS; ++s) pd[s] = __shfl_sync(0xffffffffu, v[s][TR], rl);
+    if (lane == 0) {  // row j of the factors: the pivot row's entries of L, U_jj and its row of U
+        float4 *row = reinterpret_cast<float4 *>(sU + j * factor_ldu<RS>() + warp * RS);
+#pragma unroll
+        for (int q = 0; q < RS / 4; ++q) row[q] = make_float4(pd[4 * q], pd[4 * q + 1], pd[4 * q + 2], pd[4 * q + 3]);
+    }
+    const bool wrap = wj == 7;  // column j + 1 is in slot sj + 1 (else in slot sj)
+    if (np) {
+        if (wrap) {
+            if (sj + 1 < RS) {
+#pragma unroll
+                for (int t = 0; t < CS; ++t) v[sj + 1][t] = fmaf(-lt[t], pd[sj + 1], v[sj + 1][t]);
+                gj_publish<RS, CS>(v, sj + 1 < RS ? sj + 1 : RS - 1, done, j + 1, m, lane, sL, s_r, cur, s_bad);
+            }
+        } else {
+#pragma unroll
+            for (int t = 0; t < CS; ++t) v[sj][t] = fmaf(-lt[t], pd[sj], v[sj][t]);
+            gj_publish<RS, CS>(v, sj, done, j + 1, m, lane, sL, s_r, cur, s_bad);
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < RS; ++s) {
+        const bool past = s > sj || (s == sj && warp > wj);
+        const bool ahead = np && ((s == sj && !wrap) || (s == sj + 1 && wrap));  // done above
+        if (past && !ahead) {
+#pragma unroll
+            for (int t = 0; t < CS; ++t) v[s][t] = fmaf(-lt[t], pd[s], v[s][t]);
+        }
+        const float pc = __shfl_sync(0xffffffffu, w[s][TR], rl);
+#pragma unroll
+        for (int t = 0; t < CS; ++t) w[s][t] = fmaf(-lt[t], pc, w[s][t]);
+    }
+}
+
 // The factor kernel, one CTA of eight warps per ray, its zones in order. B_k and A_k are staged
 // in shared memory and D_k = B_k - A_k G_{k-1} is formed there (tensor cores). Then thread (warp w,
 // lane x) takes into registers the elements of D_k and of C_k in rows x + 32 t (t < CS) and columns
 // w + 8 s (s < RS), so that column j lies in warp j mod 8 alone, and Gauss-Jordan elimination with
-// partial pivoting runs on [D_k | C_k] one column at a time, with one CTA barrier per column:
-//  - the warp that holds column j finds the pivot row (the largest magnitude among the rows not
-//    yet pivots, the lowest row on ties) by two warp reductions and publishes the row and the
-//    multipliers of every other row; a row not yet a pivot keeps its multiplier in column j (an
-//    entry of L);
-//  - after the barrier every warp takes the pivot row's values in its columns by shuffle, writes
-//    them to row j of the factor buffer (the pivot row's entries of L, U_jj and its row of U) and
-//    subtracts the multiples from the other rows, in the columns of D past j and in all of C.
+// partial pivoting runs on [D_k | C_k] one column at a time:
+//  - the warp that holds column j finds the pivot row and publishes it with the multipliers of
+//    every other row (gj_publish), then arrives at the step barrier, at which the other warps wait;
+//  - every warp takes the pivot row's values in its columns by shuffle, writes them to row j of the
+//    factor buffer and subtracts the multiples from the other rows, in the columns of D past j and
+//    in all of C (gj_eliminate); the warp that holds column j + 1 updates and publishes it first.
 // The factors of D_k are those of LU with partial pivoting; the rows already pivots are
 // eliminated as well, so at the end the C part of pivot row j is U_jj G_k[j] and no substitution
 // is left. Rows are never moved: cur maps pivot positions to physical rows.
@@ -273,9 +383,10 @@ __global__ void __launch_bounds__(kFactorThreads, RS > 12 ? 1 : 2) k_btd_factor(
     extern __shared__ __align__(16) float sm[];
     __shared__ int s_bad;
     __shared__ int s_r[2];
+    constexpr int ldu = factor_ldu<RS>();
     const int m = a.m, ld = a.ld, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    float *sA = sm;           // A_k, then the factors of D_k in pivot order, a row per column step
-    float *sW = sA + m * ld;  // G_{k-1}, then C_k, then G_k
+    float *sA = sm;  // A_k, then the factors of D_k in pivot order (row stride ldu, slots by warp)
+    float *sW = sA + m * (ld > ldu ? ld : ldu);  // G_{k-1}, then C_k, then G_k
     float *sT = sW + m * ld;  // B_k, then D_k
     float *sL = sT + m * ld;  // [2][m] the multipliers of the current column (two buffers)
     int *cur = reinterpret_cast<int *>(sL + 2 * m), *pos = cur + m;
@@ -321,51 +432,14 @@ __global__ void __launch_bounds__(kFactorThreads, RS > 12 ? 1 : 2) k_btd_factor(
                 w[s][t] = next && i < m && c < m ? sW[i * ld + c] : 0.f;
             }
         unsigned done = 0u;  // bit t: my row lane + 32 t has been a pivot
+        if (warp == 0) gj_publish<RS, CS>(v, 0, done, 0, m, lane, sL, s_r, cur, &s_bad);
 #pragma unroll
         for (int sj = 0; sj < RS; ++sj) {
             for (int wj = 0; wj < 8; ++wj) {
                 const int j = 8 * sj + wj;
                 if (j >= m) break;
+                if (warp != wj) step_wait(j);  // the warp of column j arrived when it published
                 const int buf = j & 1;
-                if (warp == wj) {  // column j: the pivot row and the multipliers
-                    unsigned key = 0u;  // |x| bits + 1 (NaN: 1) for a candidate row, 0 for none
-                    unsigned brow = 0xffffffffu;
-#pragma unroll
-                    for (int t = 0; t < CS; ++t) {
-                        const int i = lane + 32 * t;
-                        if (i < m && !((done >> t) & 1u)) {
-                            const float x = fabsf(v[sj][t]);
-                            const unsigned kx = x == x ? __float_as_uint(x) + 1u : 1u;
-                            if (kx > key) {
-                                key = kx;
-                                brow = (unsigned)i;
-                            }
-                        }
-                    }
-                    const unsigned kmax = __reduce_max_sync(0xffffffffu, key);
-                    const int r = (int)__reduce_min_sync(0xffffffffu, key == kmax ? brow : 0xffffffffu);
-                    const int tr = r >> 5;
-                    float mine = v[sj][0];
-#pragma unroll
-                    for (int t = 1; t < CS; ++t)
-                        if (tr == t) mine = v[sj][t];
-                    const float piv = __shfl_sync(0xffffffffu, mine, r & 31), rp = 1.f / piv;
-                    if (lane == 0) {
-                        s_r[buf] = r;
-                        cur[j] = r;
-                        if (!(fabsf(piv) > 0.f && fabsf(piv) < INFINITY)) s_bad = 1;
-                    }
-#pragma unroll
-                    for (int t = 0; t < CS; ++t) {
-                        const int i = lane + 32 * t;
-                        if (i < m) {
-                            const float lv = i != r ? v[sj][t] * rp : 0.f;
-                            sL[buf * m + i] = lv;
-                            if (i != r && !((done >> t) & 1u)) v[sj][t] = lv;  // an entry of L
-                        }
-                    }
-                }
-                __syncthreads();
                 const int r = s_r[buf], rl = r & 31, tr = r >> 5;
                 float lt[CS];
 #pragma unroll
@@ -374,25 +448,15 @@ __global__ void __launch_bounds__(kFactorThreads, RS > 12 ? 1 : 2) k_btd_factor(
                     lt[t] = i < m ? sL[buf * m + i] : 0.f;
                 }
                 if (lane == rl) done |= 1u << tr;
-#pragma unroll
-                for (int s = 0; s < RS; ++s) {
-                    float vd = v[s][0], vc = w[s][0];
-#pragma unroll
-                    for (int t = 1; t < CS; ++t)
-                        if (tr == t) {
-                            vd = v[s][t];
-                            vc = w[s][t];
-                        }
-                    const float pd = __shfl_sync(0xffffffffu, vd, rl), pc = __shfl_sync(0xffffffffu, vc, rl);
-                    const int c = warp + 8 * s;
-                    if (lane == 0 && c < m) sA[j * ld + c] = pd;  // row j of the factors
-                    if (s > sj || (s == sj && warp > wj)) {   // the columns of D past j
-#pragma unroll
-                        for (int t = 0; t < CS; ++t) v[s][t] = fmaf(-lt[t], pd, v[s][t]);
-                    }
-#pragma unroll
-                    for (int t = 0; t < CS; ++t) w[s][t] = fmaf(-lt[t], pc, w[s][t]);
-                }
+                const bool np = j + 1 < m && warp == ((j + 1) & 7);
+                if (tr == 0)
+                    gj_eliminate<RS, CS, 0>(v, w, lt, rl, sj, wj, warp, lane, j, m, np, done, sA, sL, s_r, cur, &s_bad);
+                else if (CS > 1 && tr == 1)
+                    gj_eliminate<RS, CS, (CS > 1 ? 1 : 0)>(v, w, lt, rl, sj, wj, warp, lane, j, m, np, done, sA, sL, s_r, cur, &s_bad);
+                else if (CS > 2 && tr == 2)
+                    gj_eliminate<RS, CS, (CS > 2 ? 2 : 0)>(v, w, lt, rl, sj, wj, warp, lane, j, m, np, done, sA, sL, s_r, cur, &s_bad);
+                else if (CS > 3)
+                    gj_eliminate<RS, CS, (CS > 3 ? 3 : 0)>(v, w, lt, rl, sj, wj, warp, lane, j, m, np, done, sA, sL, s_r, cur, &s_bad);
             }
         }
         __syncthreads();
@@ -404,7 +468,7 @@ __global__ void __launch_bounds__(kFactorThreads, RS > 12 ? 1 : 2) k_btd_factor(
                 const int i = lane + 32 * t;
                 if (i < m) {
                     const int p = pos[i];
-                    const float ru = 1.f / sA[p * ld + p];
+                    const float ru = 1.f / sA[p * ldu + (p & 7) * RS + (p >> 3)];
 #pragma unroll
                     for (int s = 0; s < RS; ++s) {
                         const int c = warp + 8 * s;
@@ -416,7 +480,7 @@ __global__ void __launch_bounds__(kFactorThreads, RS > 12 ? 1 : 2) k_btd_factor(
         __syncthreads();
         float *LUt = a.LUt + k * mm;
         for (int c = warp; c < m; c += 8)
-            for (int i = lane; i < m; i += 32) LUt[(size_t)c * m + i] = sA[i * ld + c];
+            for (int i = lane; i < m; i += 32) LUt[(size_t)c * m + i] = sA[i * ldu + (c & 7) * RS + (c >> 3)];
         for (int i = tid; i < m; i += kFactorThreads) a.perm[k * m + i] = cur[i];
         if (next) {
             float *Gt = a.Gt + k * mm;
@@ -707,7 +771,11 @@ extern "C" vx_status vx_btd_create(int m, long long max_zones, int n_refine, vx_
     h->ld = m | 1;  // odd row stride: column walks through shared memory hit distinct banks
     h->n_refine = n_refine;
     h->max_zones = max_zones;
-    h->smem = ((size_t)3 * m * h->ld + 2 * m) * sizeof(float) + (size_t)2 * m * sizeof(int);
+    {
+        const int ldu = m <= 32 ? factor_ldu<4>() : m <= 64 ? factor_ldu<8>() : m <= 96 ? factor_ldu<12>() : factor_ldu<16>();
+        h->smem = ((size_t)m * (h->ld > ldu ? h->ld : ldu) + 2 * (size_t)m * h->ld + 2 * m) * sizeof(float) +
+                  (size_t)2 * m * sizeof(int);
+    }
     h->smem_sweep = ((size_t)2 * ((m * m + 3) & ~3) + m) * sizeof(float);
     const size_t zc = (size_t)(max_zones > 0 ? max_zones : 1), mm = (size_t)m * m;
     cudaError_t e = cudaSuccess;
