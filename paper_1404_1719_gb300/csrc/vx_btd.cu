@@ -273,12 +273,16 @@ __device__ __forceinline__ void step_wait(int j) {
     asm volatile("bar.sync %0, %1;" ::"r"(1 + (j & 1)), "n"(kFactorThreads) : "memory");
 }
 
+// Element (slot s, row slot t) of a register tile stored as pairs of slots (s even: .x, odd: .y),
+// so that two slots update with one packed FP32 FMA.
+#define VX_SLOT(tile, s, t) (((s) & 1) ? (tile)[(s) >> 1][t].y : (tile)[(s) >> 1][t].x)
+
 // Column j of D_k, in slot S of the calling warp (column warp + 8 S): the pivot row (the largest
 // magnitude among the rows not yet pivots, the lowest row on ties, by two warp reductions) and the
 // multipliers of every other row, published to buffer j mod 2; a row not yet a pivot keeps its
 // multiplier in column j (an entry of L). Ends with the warp's arrival at the step barrier.
 template <int RS, int CS>
-__device__ __forceinline__ void gj_publish(float (&v)[RS][CS], const int S, unsigned done, int j, int m, int lane,
+__device__ __forceinline__ void gj_publish(float2 (&v)[RS / 2][CS], const int S, unsigned done, int j, int m, int lane,
                                            float *sL, int *s_r, int *cur, int *s_bad) {
     unsigned key = 0u;  // |x| bits + 1 (NaN: 1) for a candidate row, 0 for none
     unsigned brow = 0xffffffffu;
@@ -286,7 +290,7 @@ __device__ __forceinline__ void gj_publish(float (&v)[RS][CS], const int S, unsi
     for (int t = 0; t < CS; ++t) {
         const int i = lane + 32 * t;
         if (i < m && !((done >> t) & 1u)) {
-            const float x = fabsf(v[S][t]);
+            const float x = fabsf(VX_SLOT(v, S, t));
             const unsigned kx = x == x ? __float_as_uint(x) + 1u : 1u;
             if (kx > key) {
                 key = kx;
@@ -297,10 +301,10 @@ __device__ __forceinline__ void gj_publish(float (&v)[RS][CS], const int S, unsi
     const unsigned kmax = __reduce_max_sync(0xffffffffu, key);
     const int r = (int)__reduce_min_sync(0xffffffffu, key == kmax ? brow : 0xffffffffu);
     const int tr = r >> 5;
-    float mine = v[S][0];
+    float mine = VX_SLOT(v, S, 0);
 #pragma unroll
     for (int t = 1; t < CS; ++t)
-        if (tr == t) mine = v[S][t];
+        if (tr == t) mine = VX_SLOT(v, S, t);
     const float piv = __shfl_sync(0xffffffffu, mine, r & 31), rp = 1.f / piv;
     const int buf = j & 1;
     if (lane == 0) {
@@ -312,9 +316,9 @@ __device__ __forceinline__ void gj_publish(float (&v)[RS][CS], const int S, unsi
     for (int t = 0; t < CS; ++t) {
         const int i = lane + 32 * t;
         if (i < m) {
-            const float lv = i != r ? v[S][t] * rp : 0.f;
+            const float lv = i != r ? VX_SLOT(v, S, t) * rp : 0.f;
             sL[buf * m + i] = lv;
-            if (i != r && !((done >> t) & 1u)) v[S][t] = lv;
+            if (i != r && !((done >> t) & 1u)) VX_SLOT(v, S, t) = lv;
         }
     }
     step_arrive(j);
@@ -326,12 +330,12 @@ __device__ __forceinline__ void gj_publish(float (&v)[RS][CS], const int S, unsi
 // lt. If the warp holds column j + 1 (np), that column is updated first and published before the
 // rest (look-ahead).
 template <int RS, int CS, int TR>
-__device__ __forceinline__ void gj_eliminate(float (&v)[RS][CS], float (&w)[RS][CS], const float (&lt)[CS], int rl,
-                                             const int sj, int wj, int warp, int lane, int j, int m, bool np,
+__device__ __forceinline__ void gj_eliminate(float2 (&v)[RS / 2][CS], float2 (&w)[RS / 2][CS], const float (&lt)[CS],
+                                             int rl, const int sj, int wj, int warp, int lane, int j, int m, bool np,
                                              unsigned done, float *sU, float *sL, int *s_r, int *cur, int *s_bad) {
     float pd[RS];
 #pragma unroll
-    for (int s = 0; s < RS; ++s) pd[s] = __shfl_sync(0xffffffffu, v[s][TR], rl);
+    for (int s = 0; s < RS; ++s) pd[s] = __shfl_sync(0xffffffffu, VX_SLOT(v, s, TR), rl);
     if (lane == 0) {  // row j of the factors: the pivot row's entries of L, U_jj and its row of U
         float4 *row = reinterpret_cast<float4 *>(sU + j * factor_ldu<RS>() + warp * RS);
 #pragma unroll
@@ -342,26 +346,45 @@ __device__ __forceinline__ void gj_eliminate(float (&v)[RS][CS], float (&w)[RS][
         if (wrap) {
             if (sj + 1 < RS) {
 #pragma unroll
-                for (int t = 0; t < CS; ++t) v[sj + 1][t] = fmaf(-lt[t], pd[sj + 1], v[sj + 1][t]);
+                for (int t = 0; t < CS; ++t) VX_SLOT(v, sj + 1, t) = fmaf(-lt[t], pd[sj + 1], VX_SLOT(v, sj + 1, t));
                 gj_publish<RS, CS>(v, sj + 1 < RS ? sj + 1 : RS - 1, done, j + 1, m, lane, sL, s_r, cur, s_bad);
             }
         } else {
 #pragma unroll
-            for (int t = 0; t < CS; ++t) v[sj][t] = fmaf(-lt[t], pd[sj], v[sj][t]);
+            for (int t = 0; t < CS; ++t) VX_SLOT(v, sj, t) = fmaf(-lt[t], pd[sj], VX_SLOT(v, sj, t));
             gj_publish<RS, CS>(v, sj, done, j + 1, m, lane, sL, s_r, cur, s_bad);
         }
     }
+    float2 nlt[CS];
 #pragma unroll
-    for (int s = 0; s < RS; ++s) {
-        const bool past = s > sj || (s == sj && warp > wj);
-        const bool ahead = np && ((s == sj && !wrap) || (s == sj + 1 && wrap));  // done above
-        if (past && !ahead) {
+    for (int t = 0; t < CS; ++t) nlt[t] = make_float2(-lt[t], -lt[t]);
 #pragma unroll
-            for (int t = 0; t < CS; ++t) v[s][t] = fmaf(-lt[t], pd[s], v[s][t]);
+    for (int q = 0; q < RS / 2; ++q) {
+        bool upd[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int s = 2 * q + e;
+            const bool past = s > sj || (s == sj && warp > wj);
+            const bool ahead = np && ((s == sj && !wrap) || (s == sj + 1 && wrap));  // done above
+            upd[e] = past && !ahead;
         }
-        const float pc = __shfl_sync(0xffffffffu, w[s][TR], rl);
+        if (upd[0] && upd[1]) {
+            const float2 p2 = make_float2(pd[2 * q], pd[2 * q + 1]);
 #pragma unroll
-        for (int t = 0; t < CS; ++t) w[s][t] = fmaf(-lt[t], pc, w[s][t]);
+            for (int t = 0; t < CS; ++t) v[q][t] = __ffma2_rn(nlt[t], p2, v[q][t]);
+        } else {
+            if (upd[0]) {
+#pragma unroll
+                for (int t = 0; t < CS; ++t) v[q][t].x = fmaf(-lt[t], pd[2 * q], v[q][t].x);
+            }
+            if (upd[1]) {
+#pragma unroll
+                for (int t = 0; t < CS; ++t) v[q][t].y = fmaf(-lt[t], pd[2 * q + 1], v[q][t].y);
+            }
+        }
+        const float2 c2 = make_float2(__shfl_sync(0xffffffffu, w[q][TR].x, rl), __shfl_sync(0xffffffffu, w[q][TR].y, rl));
+#pragma unroll
+        for (int t = 0; t < CS; ++t) w[q][t] = __ffma2_rn(nlt[t], c2, w[q][t]);
     }
 }
 
@@ -415,13 +438,13 @@ __global__ void __launch_bounds__(kFactorThreads, RS > 12 ? 1 : 2) k_btd_factor(
         }
         __syncthreads();
         if (next) stage_rows<RS, CS, 2>(a.C + k * mm, nullptr, sW, m, ld, warp, lane);
-        float v[RS][CS], w[RS][CS];  // D_k and C_k: rows lane + 32 t, columns warp + 8 s
+        float2 v[RS / 2][CS], w[RS / 2][CS];  // D_k and C_k: rows lane + 32 t, columns warp + 8 s (VX_SLOT)
 #pragma unroll
         for (int s = 0; s < RS; ++s)
 #pragma unroll
             for (int t = 0; t < CS; ++t) {
                 const int i = lane + 32 * t, c = warp + 8 * s;
-                v[s][t] = i < m && c < m ? sT[i * ld + c] : 0.f;
+                VX_SLOT(v, s, t) = i < m && c < m ? sT[i * ld + c] : 0.f;
             }
         __syncthreads();
 #pragma unroll
@@ -429,7 +452,7 @@ __global__ void __launch_bounds__(kFactorThreads, RS > 12 ? 1 : 2) k_btd_factor(
 #pragma unroll
             for (int t = 0; t < CS; ++t) {
                 const int i = lane + 32 * t, c = warp + 8 * s;
-                w[s][t] = next && i < m && c < m ? sW[i * ld + c] : 0.f;
+                VX_SLOT(w, s, t) = next && i < m && c < m ? sW[i * ld + c] : 0.f;
             }
         unsigned done = 0u;  // bit t: my row lane + 32 t has been a pivot
         if (warp == 0) gj_publish<RS, CS>(v, 0, done, 0, m, lane, sL, s_r, cur, &s_bad);
@@ -472,7 +495,7 @@ __global__ void __launch_bounds__(kFactorThreads, RS > 12 ? 1 : 2) k_btd_factor(
 #pragma unroll
                     for (int s = 0; s < RS; ++s) {
                         const int c = warp + 8 * s;
-                        if (c < m) sW[p * ld + c] = w[s][t] * ru;
+                        if (c < m) sW[p * ld + c] = VX_SLOT(w, s, t) * ru;
                     }
                 }
             }
@@ -596,14 +619,20 @@ __global__ void __launch_bounds__(32) k_btd_sweep(const BtdArgs a) {
                 }
             }
         }
-        // upper triangle, last row first
+        // upper triangle, last row first; 1 / U_jj formed ahead, off the chain of steps
+        float rdiag[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int i = lane + 32 * t;
+            rdiag[t] = i < m ? 1.f / S1[i * m + i] : 0.f;
+        }
 #pragma unroll
         for (int tj = 3; tj >= 0; --tj) {
             if (32 * tj >= m) continue;
             const int top = m - 32 * tj < 32 ? m - 32 * tj : 32;
             for (int l = top - 1; l >= 0; --l) {
                 const int j = 32 * tj + l;
-                const float vj = __shfl_sync(0xffffffffu, v[tj], l) / S1[j * m + j];
+                const float vj = __shfl_sync(0xffffffffu, v[tj], l) * __shfl_sync(0xffffffffu, rdiag[tj], l);
                 if (lane == l) v[tj] = vj;
 #pragma unroll
                 for (int t = 0; t <= tj; ++t) {
