@@ -241,19 +241,20 @@ def run_solve(args):
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     n_rays = args.rays or SOLVE_RAYS
+    n_zones = args.zones or SOLVE_ZONES  # zones per ray
     if args.impl == "reference":
         if rank != 0:
             return 0
-        s = gen.newton_system([SOLVE_ZONES] * 2, n_bins=SOLVE_BINS, seed=0)
+        s = gen.newton_system([n_zones] * 2, n_bins=SOLVE_BINS, seed=0)
         for _ in range(args.warmup):
             solve_oracle_rate(s, [0])
         t = [solve_oracle_rate(s, [0, 1])[1] for _ in range(args.steps)]
         ms = 1000 * float(np.mean(t))
-        value = 2 * SOLVE_ZONES / (ms / 1000)
+        value = 2 * n_zones / (ms / 1000)
         print(json.dumps({"impl": "reference", "metric": SOLVE_METRIC, "value": value, "unit": "zones/s",
                           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                          "data": "synthetic", "config": {"workload": f"2 rays x {SOLVE_ZONES} zones, m = 84"},
+                          "data": "synthetic", "config": {"workload": f"2 rays x {n_zones} zones, m = 84"},
                           "cpu_baseline": {"value": value, "unit": "zones/s", "cores": 1, "kind": "oracle",
                                            "sample": "2 rays per step, banded LU (scipy solve_banded)"},
                           "e2e": {"value": value, "unit": "zones/s", "h2d_bytes_per_step": 0,
@@ -265,7 +266,7 @@ def run_solve(args):
     dev = torch.device("cuda", local)
     from paper_1404_1719_gb300 import BlockTridiagSolver, _build
     _build.build()
-    s = gen.newton_system([SOLVE_ZONES] * n_rays, n_bins=SOLVE_BINS, seed=rank)
+    s = gen.newton_system([n_zones] * n_rays, n_bins=SOLVE_BINS, seed=rank)
     m, Z = s["m"], s["d"].shape[0]
     host = {k: torch.from_numpy(np.ascontiguousarray(s[k])).pin_memory() for k in ("offsets", "A", "B", "C", "d")}
     dv = {k: v.to(dev) for k, v in host.items()}
@@ -318,8 +319,8 @@ def run_solve(args):
         mhz = c["sm_mhz"] or 2070.0
         peak = nsm * 128 * 2 * mhz * 1e6 / 1e12
         # FP32 flops of the block factorisation: Schur update A_k G_{k-1} (2 m^3) on every zone but a
-        # ray's first, LU of D_k (2 m^3 / 3) on every zone, G_k = D_k^{-1} C_k by two triangular solves
-        # over m right-hand sides (2 m^3) on every zone but a ray's last; the O(m^2) sweeps and FP64
+        # ray's first, LU of D_k (2 m^3 / 3) on every zone, G_k = D_k^{-1} C_k (m elimination steps over
+        # the m x m right-hand block, 2 m^3) on every zone but a ray's last; the O(m^2) sweeps and FP64
         # residuals are not counted
         flops = (Z - n_rays) * 2.0 * m ** 3 + Z * 2.0 * m ** 3 / 3.0 + (Z - n_rays) * 2.0 * m ** 3
         achieved = flops / (ms_local / 1000) / 1e12
@@ -327,7 +328,7 @@ def run_solve(args):
             "metric": SOLVE_METRIC, "value": job_rate(Z, world, ms), "unit": "zones/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"{n_rays} rays x {SOLVE_ZONES} zones, block-tridiagonal Newton systems, "
+            "config": {"workload": f"{n_rays} rays x {n_zones} zones, block-tridiagonal Newton systems, "
                                    f"m = {m} (J, H of nu_e, nu_ebar x {SOLVE_BINS} bins)",
                        "zones": Z, "m": m, "n_refine": SOLVE_REFINE,
                        "l2": "inputs larger than L2 (A, B, C: %.1f GB)" % (3 * s["A"].nbytes / 1e9)},
@@ -346,7 +347,7 @@ def run_solve(args):
             "numeric_ok": bool(ok),
         }
         if not args.no_cpu:
-            sub = gen.newton_system([SOLVE_ZONES] * n_rays, n_bins=SOLVE_BINS, seed=rank, rays=range(64))
+            sub = gen.newton_system([n_zones] * n_rays, n_bins=SOLVE_BINS, seed=rank, rays=range(64))
 
             def run_rays(k):
                 r, t = solve_oracle_rate(sub, list(range(k)))
@@ -944,6 +945,8 @@ def main():
                     help="discrete rule in electron energy: standard, or split at the Fermi edge (VX_QUAD_SPLIT)")
     ap.add_argument("--rays", type=int, default=None,
                     help="use only the first R rays of the workload (small cases for profiling)")
+    ap.add_argument("--zones", type=int, default=None,
+                    help="--mode solve: zones per ray (default 400; small cases for profiling)")
     args = ap.parse_args()
     if args.mode == "solve":
         return run_solve(args)
