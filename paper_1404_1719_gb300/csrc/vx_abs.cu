@@ -39,8 +39,8 @@ constexpr double kGA = 1.2754;               // axial coupling
 constexpr double kMu = 1.66053906660e-24;    // atomic mass unit, g
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kAbsBlock = 256;
-constexpr int kZoneSlots = kAbsBlock;        // zones a block takes per iteration (S N >= 1)
-static_assert(kAbsBlock >= 3 * VX_MAX_BINS, "a block must hold a whole zone's entries");
+constexpr int kAbsWarps = kAbsBlock / 32;
+constexpr int kZoneSlots = 32;  // zones a warp's 32 consecutive entries can span (S N >= 1)
 
 vx_status afail(vx_status s, const char *fmt, ...) {
     char buf[512];
@@ -158,139 +158,165 @@ __device__ __forceinline__ void occupation(double x, double &f, double &omf) {
 
 template <bool F64, bool ADJ>
 __global__ void __launch_bounds__(kAbsBlock) k_abs(const __grid_constant__ AbsLaunch L) {
-    __shared__ double ziT[kZoneSlots], zeta[kZoneSlots], znb[kZoneSlots], zYe[kZoneSlots];
-    __shared__ float znnf[kZoneSlots], znpf[kZoneSlots], znbf[kZoneSlots], ziT2f[kZoneSlots];
-    __shared__ float ziTh[kZoneSlots], ziTl[kZoneSlots], zetah[kZoneSlots], zetal[kZoneSlots];
-    __shared__ int zbad[kZoneSlots];
-    // the block's Jacobian entries, staged so that the stores are contiguous (row stride 13: banks)
+    // Each warp takes 32 consecutive zones at a time, with no CTA barrier: lane l forms zone l's
+    // scalars in the warp's shared slots (the FP64 set-up with every lane busy), then the warp runs
+    // through the group's entries (zone, species, bin) 32 at a time, staging their Jacobian rows in
+    // its own slice of shared memory (row stride 13: banks) and storing them as one contiguous run.
+    __shared__ double ziT[kAbsWarps][kZoneSlots], zeta[kAbsWarps][kZoneSlots], znb[kAbsWarps][kZoneSlots],
+        zYe[kAbsWarps][kZoneSlots];
+    __shared__ float znnf[kAbsWarps][kZoneSlots], znpf[kAbsWarps][kZoneSlots], znbf[kAbsWarps][kZoneSlots],
+        ziT2f[kAbsWarps][kZoneSlots];
+    __shared__ float ziTh[kAbsWarps][kZoneSlots], ziTl[kAbsWarps][kZoneSlots], zetah[kAbsWarps][kZoneSlots],
+        zetal[kAbsWarps][kZoneSlots];
+    __shared__ int zbad[kAbsWarps][kZoneSlots];
     __shared__ double sj[ADJ ? kAbsBlock * 13 : 1];
     const AbsConst &C = L.c;
     const int SN = C.S * C.N;
-    // a block takes nzb whole zones per iteration; thread t keeps the same (zone, species, bin)
-    // offsets throughout, so no 64-bit division runs per entry
-    const int nzb = SN >= (int)blockDim.x ? 1 : (int)blockDim.x / SN;
-    const int t = threadIdx.x, k = t / SN, r = t - k * SN, s = r / C.N, i = r - s * C.N;
-    const bool act = k < nzb;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double *sjw = sj + (ADJ ? warp * 32 * 13 : 0);
     vx::validate_offsets(L.off, L.n_rays, L.Z, L.flag);
-    for (long long zb = (long long)blockIdx.x * nzb; zb < L.Z; zb += (long long)gridDim.x * nzb) {
-        const int nz = (int)min((long long)nzb, L.Z - zb);
-        for (int kk = threadIdx.x; kk < nz; kk += blockDim.x) {
-            const double *st = L.state + 4 * (zb + kk);
+    // entry q = lane of a group as (zone slot k0, species s0, bin i0), and the step of 32 entries
+    const int k0 = lane / SN, s0 = (lane - k0 * SN) / C.N, i0 = lane - k0 * SN - s0 * C.N;
+    const int dk = 32 / SN, dsi = 32 - dk * SN, ds = dsi / C.N, di = dsi - ds * C.N;
+    for (long long zg = ((long long)blockIdx.x * kAbsWarps + warp) * kZoneSlots; zg < L.Z;
+         zg += (long long)gridDim.x * kAbsWarps * kZoneSlots) {
+        const int nz = (int)min((long long)kZoneSlots, L.Z - zg);
+        if (lane < nz) {
+            const int kk = lane;
+            const double *st = L.state + 4 * (zg + kk);
             const double T = st[0], eta = st[1], Ye = st[2], rho = st[3];
             const bool bad = !(T > 0.0) || !isfinite(T) || !isfinite(eta) || !(Ye >= 0.0 && Ye <= 1.0) ||
                              !(rho >= 0.0) || !isfinite(rho);
-            zbad[kk] = bad;
-            ziT[kk] = bad ? 0.0 : 1.0 / T;
-            zeta[kk] = eta;
-            zYe[kk] = Ye;
-            znb[kk] = rho * (1e-39 / kMu);  // baryons per fm^3
+            zbad[warp][kk] = bad;
+            ziT[warp][kk] = bad ? 0.0 : 1.0 / T;
+            zeta[warp][kk] = eta;
+            zYe[warp][kk] = Ye;
+            znb[warp][kk] = rho * (1e-39 / kMu);  // baryons per fm^3
             if (!F64) {
-                znbf[kk] = (float)znb[kk];
-                znnf[kk] = (float)(znb[kk] * (1.0 - Ye));
-                znpf[kk] = (float)(znb[kk] * Ye);
-                ziT2f[kk] = (float)fmin(ziT[kk] * ziT[kk], 1e30);  // T >= 1e-15 MeV for the T-derivative
-                ziTh[kk] = (float)ziT[kk];
-                ziTl[kk] = (float)(ziT[kk] - (double)ziTh[kk]);
-                zetah[kk] = (float)eta;
-                zetal[kk] = (float)(eta - (double)zetah[kk]);
+                const double nb = znb[warp][kk], iT = ziT[warp][kk];
+                znbf[warp][kk] = (float)nb;
+                znnf[warp][kk] = (float)(nb * (1.0 - Ye));
+                znpf[warp][kk] = (float)(nb * Ye);
+                ziT2f[warp][kk] = (float)fmin(iT * iT, 1e30);  // T >= 1e-15 MeV for the T-derivative
+                ziTh[warp][kk] = (float)iT;
+                ziTl[warp][kk] = (float)(iT - (double)ziTh[warp][kk]);
+                zetah[warp][kk] = (float)eta;
+                zetal[warp][kk] = (float)(eta - (double)zetah[warp][kk]);
             }
             if (bad) atomicOr(L.flag, VX_FLAG_BAD_STATE);
         }
-        __syncthreads();
-        if (act && k < nz) {
-            const long long e = (zb + k) * SN + r;
-            double j = 0.0, chi = 0.0, d[2][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
-            const double K = C.K[s][i];
-            if (zbad[k]) {
-                j = chi = __longlong_as_double(0x7ff8000000000000ll);
-            } else if (K > 0.0 && F64) {
-                const bool anti = C.anti[s] != 0;
-                const double E = C.E[s][i], iT = ziT[k], nb = znb[k], Ye = zYe[k];
-                const double nn = nb * (1.0 - Ye), np = nb * Ye;
-                const double nin = anti ? np : nn, nout = anti ? nn : np;
-                const double x = fma(E, iT, anti ? zeta[k] : -zeta[k]);
-                double f, omf;
-                occupation<F64>(x, f, omf);
-                j = K * nout * f;
-                chi = K * nin * omf;
-                if (ADJ) {
-                    // df/dx = -f (1 - f); dx/dT = -E/T^2; dx/deta = -1 (electron), +1 (positron)
-                    const double g = f * omf, gT = g * E * iT * iT, ge = anti ? -g : g;
-                    d[0][0] = K * nout * gT;   d[0][1] = K * nout * ge;   d[0][2] = K * (anti ? -nb : nb) * f;
-                    d[1][0] = -K * nin * gT;   d[1][1] = -K * nin * ge;   d[1][2] = K * (anti ? nb : -nb) * omf;
+        __syncwarp();
+        const int nE = nz * SN;
+        int k = k0, s = s0, i = i0;
+        for (int c0 = 0; c0 < nE; c0 += 32) {
+            const long long e = zg * SN + c0 + lane;
+            const int last = min(31, nE - 1 - c0);
+            if (c0 + lane < nE) {
+                double j = 0.0, chi = 0.0, d[2][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
+                const double K = C.K[s][i];
+                if (zbad[warp][k]) {
+                    j = chi = __longlong_as_double(0x7ff8000000000000ll);
+                } else if (K > 0.0 && F64) {
+                    const bool anti = C.anti[s] != 0;
+                    const double E = C.E[s][i], iT = ziT[warp][k], nb = znb[warp][k], Ye = zYe[warp][k];
+                    const double nn = nb * (1.0 - Ye), np = nb * Ye;
+                    const double nin = anti ? np : nn, nout = anti ? nn : np;
+                    const double x = fma(E, iT, anti ? zeta[warp][k] : -zeta[warp][k]);
+                    double f, omf;
+                    occupation<F64>(x, f, omf);
+                    j = K * nout * f;
+                    chi = K * nin * omf;
+                    if (ADJ) {
+                        // df/dx = -f (1 - f); dx/dT = -E/T^2; dx/deta = -1 (electron), +1 (positron)
+                        const double g = f * omf, gT = g * E * iT * iT, ge = anti ? -g : g;
+                        d[0][0] = K * nout * gT;   d[0][1] = K * nout * ge;   d[0][2] = K * (anti ? -nb : nb) * f;
+                        d[1][0] = -K * nin * gT;   d[1][1] = -K * nin * ge;   d[1][2] = K * (anti ? nb : -nb) * omf;
+                    }
+                } else if (C.Kf[s][i] > 0.f) {
+                    const bool anti = C.anti[s] != 0;
+                    // x = E/T -+ eta as an FP32 pair: E (1/T) exactly by FMA, then a two-sum with -+eta
+                    // (explicitly rounded operations: no contraction into FMAs may change the pair)
+                    const float Eh = C.Ef[s][i], El = C.El[s][i], ih = ziTh[warp][k], il = ziTl[warp][k];
+                    const float ph = __fmul_rn(Eh, ih);
+                    const float pl = __fadd_rn(fmaf(Eh, ih, -ph), fmaf(Eh, il, __fmul_rn(El, ih)));
+                    const float eh = anti ? zetah[warp][k] : -zetah[warp][k], el = anti ? zetal[warp][k] : -zetal[warp][k];
+                    const float sh = __fadd_rn(ph, eh), sv = __fsub_rn(sh, ph);
+                    const float xl0 = __fadd_rn(__fadd_rn(__fsub_rn(ph, __fsub_rn(sh, sv)), __fsub_rn(eh, sv)), __fadd_rn(pl, el));
+                    const float xh = __fadd_rn(sh, xl0), xl = __fsub_rn(xl0, __fsub_rn(xh, sh));
+                    // |x| log2(e) = yh + yl as an FP32 pair, then n = floor(yh) and fr = (yh - n) + yl
+                    const float ah = fabsf(xh), al = xh < 0.f ? -xl : xl;
+                    const float L2h = 1.44269502162933349609375f, L2l = 1.925963033500011079e-8f;
+                    const float yh = __fmul_rn(ah, L2h);
+                    const float yl = __fadd_rn(fmaf(ah, L2h, -yh), fmaf(ah, L2l, __fmul_rn(al, L2h)));
+                    const bool huge = !(yh <= 2000.f);
+                    const float nf = huge ? 2000.f : floorf(yh);
+                    const int n = (int)nf;
+                    const float ef = ex2f(huge ? 0.f : -__fadd_rn(__fsub_rn(yh, nf), yl));  // 2^-fr
+                    const float e32 = n < 126 ? ef * __int_as_float((127 - n) << 23) : 0.f; // e^-|x|
+                    const float r = rcpf(1.f + e32), sm = ef * r;  // large occupation; small one = sm 2^-n
+                    const bool pos = xh > 0.f;
+                    const float f = pos ? sm : r, omf = pos ? r : sm;
+                    const int kf = C.kK[s][i] - (pos ? n : 0), ko = C.kK[s][i] - (pos ? 0 : n), kg = C.kK[s][i] - n;
+                    const float Kf = C.Kf[s][i], nin = anti ? znpf[warp][k] : znnf[warp][k], nout = anti ? znnf[warp][k] : znpf[warp][k];
+                    const float Kout = Kf * nout, Kin = Kf * nin;
+                    j = pow2scaled(Kout * f, kf);
+                    chi = pow2scaled(Kin * omf, ko);
+                    if (ADJ) {
+                        const float g = f * omf, gT = g * (C.Ef[s][i] * ziT2f[warp][k]), ge = anti ? -g : g;
+                        const float Kb = Kf * znbf[warp][k];
+                        d[0][0] = pow2scaled(Kout * gT, kg);  d[0][1] = pow2scaled(Kout * ge, kg);
+                        d[0][2] = pow2scaled(anti ? -Kb * f : Kb * f, kf);
+                        d[1][0] = pow2scaled(-Kin * gT, kg);  d[1][1] = pow2scaled(-Kin * ge, kg);
+                        d[1][2] = pow2scaled(anti ? Kb * omf : -Kb * omf, ko);
+                    }
                 }
-            } else if (C.Kf[s][i] > 0.f) {
-                const bool anti = C.anti[s] != 0;
-                // x = E/T -+ eta as an FP32 pair: E (1/T) exactly by FMA, then a two-sum with -+eta
-                // (explicitly rounded operations: no contraction into FMAs may change the pair)
-                const float Eh = C.Ef[s][i], El = C.El[s][i], ih = ziTh[k], il = ziTl[k];
-                const float ph = __fmul_rn(Eh, ih);
-                const float pl = __fadd_rn(fmaf(Eh, ih, -ph), fmaf(Eh, il, __fmul_rn(El, ih)));
-                const float eh = anti ? zetah[k] : -zetah[k], el = anti ? zetal[k] : -zetal[k];
-                const float sh = __fadd_rn(ph, eh), sv = __fsub_rn(sh, ph);
-                const float xl0 = __fadd_rn(__fadd_rn(__fsub_rn(ph, __fsub_rn(sh, sv)), __fsub_rn(eh, sv)), __fadd_rn(pl, el));
-                const float xh = __fadd_rn(sh, xl0), xl = __fsub_rn(xl0, __fsub_rn(xh, sh));
-                // |x| log2(e) = yh + yl as an FP32 pair, then n = floor(yh) and fr = (yh - n) + yl
-                const float ah = fabsf(xh), al = xh < 0.f ? -xl : xl;
-                const float L2h = 1.44269502162933349609375f, L2l = 1.925963033500011079e-8f;
-                const float yh = __fmul_rn(ah, L2h);
-                const float yl = __fadd_rn(fmaf(ah, L2h, -yh), fmaf(ah, L2l, __fmul_rn(al, L2h)));
-                const bool huge = !(yh <= 2000.f);
-                const float nf = huge ? 2000.f : floorf(yh);
-                const int n = (int)nf;
-                const float ef = ex2f(huge ? 0.f : -__fadd_rn(__fsub_rn(yh, nf), yl));  // 2^-fr
-                const float e32 = n < 126 ? ef * __int_as_float((127 - n) << 23) : 0.f; // e^-|x|
-                const float r = rcpf(1.f + e32), sm = ef * r;  // large occupation; small one = sm 2^-n
-                const bool pos = xh > 0.f;
-                const float f = pos ? sm : r, omf = pos ? r : sm;
-                const int kf = C.kK[s][i] - (pos ? n : 0), ko = C.kK[s][i] - (pos ? 0 : n), kg = C.kK[s][i] - n;
-                const float Kf = C.Kf[s][i], nin = anti ? znpf[k] : znnf[k], nout = anti ? znnf[k] : znpf[k];
-                const float Kout = Kf * nout, Kin = Kf * nin;
-                j = pow2scaled(Kout * f, kf);
-                chi = pow2scaled(Kin * omf, ko);
-                if (ADJ) {
-                    const float g = f * omf, gT = g * (C.Ef[s][i] * ziT2f[k]), ge = anti ? -g : g;
-                    const float Kb = Kf * znbf[k];
-                    d[0][0] = pow2scaled(Kout * gT, kg);  d[0][1] = pow2scaled(Kout * ge, kg);
-                    d[0][2] = pow2scaled(anti ? -Kb * f : Kb * f, kf);
-                    d[1][0] = pow2scaled(-Kin * gT, kg);  d[1][1] = pow2scaled(-Kin * ge, kg);
-                    d[1][2] = pow2scaled(anti ? Kb * omf : -Kb * omf, ko);
+                if (L.j0) {
+                    L.j0[e] = j;
+                    L.chi0[e] = chi;
+                    L.j1[e] = zbad[warp][k] ? j : 0.0;
+                    L.chi1[e] = zbad[warp][k] ? j : 0.0;
                 }
-            }
-            if (L.j0) {
-                L.j0[e] = j;
-                L.chi0[e] = chi;
-                L.j1[e] = zbad[k] ? j : 0.0;
-                L.chi1[e] = zbad[k] ? j : 0.0;
-            }
-            if (ADJ && L.jac) {
-                double *J = sj + t * 13;
-                const double zero = zbad[k] ? j : 0.0;
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    J[c] = zbad[k] ? j : d[0][c];
-                    J[3 + c] = zbad[k] ? j : d[1][c];
-                    J[6 + c] = zero;
-                    J[9 + c] = zero;
+                if (ADJ && L.jac) {
+                    double *J = sjw + lane * 13;
+                    const double zero = zbad[warp][k] ? j : 0.0;
+    #pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        J[c] = zbad[warp][k] ? j : d[0][c];
+                        J[3 + c] = zbad[warp][k] ? j : d[1][c];
+                        J[6 + c] = zero;
+                        J[9 + c] = zero;
+                    }
                 }
+                // (the FP64 class test on the FP64 pipe: in the mixed form on the results' exponent bits)
+                const long long jb = __double_as_longlong(j), cb = __double_as_longlong(chi);
+                const bool fin = F64 ? (isfinite(j) && isfinite(chi))
+                                     : ((jb & 0x7ff0000000000000ll) != 0x7ff0000000000000ll &&
+                                        (cb & 0x7ff0000000000000ll) != 0x7ff0000000000000ll);
+                if (!zbad[warp][k] && !fin) atomicOr(L.flag, VX_FLAG_NONFINITE);
             }
-            // (the FP64 class test on the FP64 pipe: in the mixed form on the results' exponent bits)
-            const long long jb = __double_as_longlong(j), cb = __double_as_longlong(chi);
-            const bool fin = F64 ? (isfinite(j) && isfinite(chi))
-                                 : ((jb & 0x7ff0000000000000ll) != 0x7ff0000000000000ll &&
-                                    (cb & 0x7ff0000000000000ll) != 0x7ff0000000000000ll);
-            if (!zbad[k] && !fin) atomicOr(L.flag, VX_FLAG_NONFINITE);
+            if (ADJ && L.jac) {  // the chunk's entries: 12 (last + 1) consecutive doubles
+                __syncwarp();
+                const int nv = 12 * (last + 1);
+                double *dst = L.jac + (zg * SN + c0) * 12;
+                for (int q = lane; q < nv; q += 32) {
+                    const int ent = q / 12;
+                    dst[q] = sjw[ent * 13 + (q - ent * 12)];
+                }
+                __syncwarp();
+            }
+            k += dk;  // the next 32 entries
+            i += di;
+            if (i >= C.N) {
+                i -= C.N;
+                ++s;
+            }
+            s += ds;
+            if (s >= C.S) {
+                s -= C.S;
+                ++k;
+            }
         }
-        if (ADJ && L.jac) {  // the staged entries of the block's zones: 12 nz SN consecutive doubles
-            __syncthreads();
-            const int nv = 12 * nz * SN;
-            double *dst = L.jac + zb * SN * 12;
-            for (int q = threadIdx.x; q < nv; q += blockDim.x) {
-                const int ent = q / 12;
-                dst[q] = sj[ent * 13 + (q - ent * 12)];
-            }
-        }
-        __syncthreads();
+        __syncwarp();  // the zone slots are read before the next group's set-up
     }
 }
 
@@ -344,8 +370,7 @@ vx_status abs_run(vx_abs *h, const vx_batch *b, const vx_out *out, double *jac, 
     if (out) { L.j0 = out->j0; L.chi0 = out->chi0; L.j1 = out->j1; L.chi1 = out->chi1; }
     L.jac = jac;
     L.flag = h->d_flag;
-    const int nzb = kAbsBlock / (h->c.S * h->c.N);  // whole zones per block and iteration
-    const long long blocks = (b->n_zones + nzb - 1) / nzb;
+    const long long blocks = (b->n_zones + kAbsWarps * kZoneSlots - 1) / (kAbsWarps * kZoneSlots);  // 32 zones per warp
     const int grid = (int)std::min<long long>(h->grid, blocks);
     const bool f64 = h->prec == VX_PREC_FP64, adj = jac != nullptr;
     if (f64) adj ? k_abs<true, true><<<grid, kAbsBlock, 0, s>>>(L) : k_abs<true, false><<<grid, kAbsBlock, 0, s>>>(L);
