@@ -534,6 +534,10 @@ def run_nes(args):
 
 
 ABS_METRIC = "absorption/emission rate entries/s (zone*species*eps), forward+Jacobian, % HBM peak"
+# DRAM bytes (read + write) per entry (zone, species, bin) of the absorption rates + Jacobian kernel,
+# from one ncu capture of the 1024-ray case of the workload (13.4 + 3241.5 MB for 25.8 M entries,
+# profiles/k_abs_tangents_1024rays.md); None whenever the kernel changes, until captured again.
+ABS_TRAFFIC_BYTES_PER_ENTRY = 126.1
 
 
 def abs_oracle_rate(b, n_zones):
@@ -655,11 +659,12 @@ def run_abs(args):
                             "tensors every step"},
             "gpu_launches": args.steps,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "bytes_per_step": algo_bytes, "traffic": None,
+                         "bytes_per_step": algo_bytes,
+                         "traffic": ABS_TRAFFIC_BYTES_PER_ENTRY * ents if ABS_TRAFFIC_BYTES_PER_ENTRY else None,
                          "peak_note": peak_note,
                          "bound_note": "streaming kernel: FP32 occupations on FP32-pair exponent arguments, "
-                                       "Jacobian stores staged through shared memory "
-                                       "(profiles/k_abs_tangents_1024rays.md)",
+                                       "32 zones per warp, Jacobian rows staged per warp in shared memory "
+                                       "and stored contiguously (profiles/k_abs_tangents_1024rays.md)",
                          "kernel": "k_abs<mixed, tangents>"},
             "clocks": c, "numeric_ok": bool(ok),
         }
