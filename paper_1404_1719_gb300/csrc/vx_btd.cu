@@ -563,13 +563,20 @@ __global__ void __launch_bounds__(32) k_btd_sweep(const BtdArgs a) {
     if (z0 + 1 < z1) warp_stage(S0, a.At + (size_t)(z0 + 1) * mm, mm, lane);
     else asm volatile("cp.async.commit_group;" ::: "memory");
     for (long long k = z0; k < z1; ++k) {
+        // the zone's right-hand side and row permutation are loaded first and used after the
+        // product A_k y_{k-1}, which accumulates apart, so their latency hides behind it
         const double *rhs = a.rhs + k * m;
+        const int *perm = a.perm + k * m;
+        double rv[4];
+        int pv[4];
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
             const int i = lane + 32 * t;
-            v[t] = i < m ? (float)rhs[i] : 0.f;
+            rv[t] = i < m ? rhs[i] : 0.0;
+            pv[t] = i < m ? perm[i] : 0;
+            v[t] = 0.f;
         }
-        if (k > z0) {  // rhs_k - A_k y_{k-1}
+        if (k > z0) {  // A_k y_{k-1}
             stage_wait<1>();  // A_k (the LU factors of D_k are the newer group)
 #pragma unroll
             for (int tc = 0; tc < 4; ++tc) {
@@ -581,7 +588,7 @@ __global__ void __launch_bounds__(32) k_btd_sweep(const BtdArgs a) {
 #pragma unroll
                     for (int t = 0; t < 4; ++t) {
                         const int i = lane + 32 * t;
-                        if (i < m) v[t] = fmaf(-S0[c * m + i], yc, v[t]);
+                        if (i < m) v[t] = fmaf(S0[c * m + i], yc, v[t]);
                     }
                 }
             }
@@ -590,18 +597,17 @@ __global__ void __launch_bounds__(32) k_btd_sweep(const BtdArgs a) {
             else asm volatile("cp.async.commit_group;" ::: "memory");
         }
         stage_wait<1>();  // the LU factors of D_k
-        // row permutation of the factorisation
+        // rhs_k - A_k y_{k-1}, then the row permutation of the factorisation
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
             const int i = lane + 32 * t;
-            if (i < m) sv[i] = v[t];
+            if (i < m) sv[i] = (float)rv[t] - v[t];
         }
         __syncwarp();
-        const int *perm = a.perm + k * m;
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
             const int i = lane + 32 * t;
-            if (i < m) v[t] = sv[perm[i]];
+            if (i < m) v[t] = sv[pv[t]];
         }
         __syncwarp();
         // unit lower triangle
@@ -657,11 +663,17 @@ __global__ void __launch_bounds__(32) k_btd_sweep(const BtdArgs a) {
     float dn[4] = {0.f, 0.f, 0.f, 0.f};
     if (z1 - 2 >= z0) warp_stage(((z1 - 2) & 1) ? S1 : S0, a.Gt + (size_t)(z1 - 2) * mm, mm, lane);
     for (long long k = z1 - 1; k >= z0; --k) {
+        // y_k and x_k are loaded first and used after the product G_k delta_{k+1}
         const float *yk = a.y + k * m;
+        double *xk = a.x + k * m;
+        float yv[4];
+        double xv[4];
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
             const int i = lane + 32 * t;
-            v[t] = i < m ? yk[i] : 0.f;
+            yv[t] = i < m ? yk[i] : 0.f;
+            xv[t] = !FIRST && i < m ? xk[i] : 0.0;
+            v[t] = 0.f;
         }
         if (k + 1 < z1) {
             const float *G = (k & 1) ? S1 : S0;
@@ -678,17 +690,17 @@ __global__ void __launch_bounds__(32) k_btd_sweep(const BtdArgs a) {
 #pragma unroll
                     for (int t = 0; t < 4; ++t) {
                         const int i = lane + 32 * t;
-                        if (i < m) v[t] = fmaf(-G[c * m + i], dc, v[t]);
+                        if (i < m) v[t] = fmaf(G[c * m + i], dc, v[t]);
                     }
                 }
             }
             __syncwarp();
         }
-        double *xk = a.x + k * m;
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
             const int i = lane + 32 * t;
-            if (i < m) xk[i] = FIRST ? (double)v[t] : xk[i] + (double)v[t];
+            v[t] = yv[t] - v[t];  // delta_k = y_k - G_k delta_{k+1}
+            if (i < m) xk[i] = FIRST ? (double)v[t] : xv[t] + (double)v[t];
             dn[t] = v[t];
         }
     }

@@ -47,7 +47,7 @@ def ray_errors(x, ref, offsets):
     return max(errs)
 
 
-@pytest.mark.parametrize("m", [1, 2, 7, 32, 33, 42, 84, 128])
+@pytest.mark.parametrize("m", [1, 2, 7, 32, 33, 42, 63, 64, 65, 84, 96, 97, 128])  # every register-tile size and its edges
 def test_random_systems_against_oracle(m):
     s = gen.random_system([5, 0, 1, 9, 17, 2], m, seed=m)
     x, ok = run(s)
