@@ -13,10 +13,13 @@
  * d(j1, chi1)/dH of the partner spectrum) are part of B_k in such a system; the radial flux terms
  * make A_k and C_k. Rays are independent (sec. 2.2) and are solved in one call.
  *
- * Method (GB300: FP32 on the CUDA cores, FP64 only where accuracy needs it). Block LU along the
- * ray without pivoting across zones: D_0 = B_0, D_k = B_k - A_k G_{k-1} with G_k = D_k^{-1} C_k,
+ * Method (GB300: FP32 arithmetic, FP64 only where accuracy needs it). Block LU along the ray
+ * without pivoting across zones: D_0 = B_0, D_k = B_k - A_k G_{k-1} with G_k = D_k^{-1} C_k,
  * each D_k factored with partial pivoting inside the block. The factorisation is done in FP32 from
- * FP32 copies of the blocks, one CTA per ray. Then the ray is solved with those factors, and
+ * FP32 copies of the blocks, one CTA per ray: the product A_k G_{k-1} on the tensor cores (TF32
+ * with each operand split into two parts, three products: about FP32 accuracy), then Gauss-Jordan
+ * elimination of [D_k | C_k], whose pivot rows and multipliers are the LU factors of D_k and
+ * whose right-hand block ends as G_k. Then the ray is solved with those factors, and
  * n_refine sweeps of iterative refinement follow, each from the FP64 residual d - M x of the
  * caller's FP64 blocks. For a ray whose Schur complements are well conditioned (e.g. block rows
  * diagonally dominant) every sweep gains a factor of about cond x 1e-7, so two sweeps reach FP64
