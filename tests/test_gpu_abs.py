@@ -87,6 +87,28 @@ def test_rates_and_jacobian_against_oracle(name, precision):
     assert np.all(gj[..., 2:, :] == 0.0) and np.all(res["j1"].cpu().numpy() == 0.0)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("species,nbins,nzones", [((0,), 1, 45), ((0,), 5, 101), ((1, 2), 13, 77)])
+def test_few_entries_per_zone(species, nbins, nzones, precision):
+    """Fewer than 32 entries (species x bins) per zone, so that a warp's 32 consecutive entries span
+    several zones and the entry counter carries across zones; zone counts not multiples of 32."""
+    from paper_1404_1719_gb300 import AbsRates
+    sp = np.array(species, np.int32)
+    eps = np.geomspace(0.8, 120.0, nbins) if nbins > 1 else np.array([7.5])
+    st = vx_inputs.make_batch(2)["state"][:nzones]
+    r = AbsRates(eps, species=sp, precision=precision)
+    res = r.adjoint(dev(st), forward=True)
+    assert r.check()
+    r.close()
+    ref = oracle.abs_evaluate(eps, sp, st, jac=True)
+    tol = TOL[precision]
+    for k in ("j0", "chi0"):
+        assert worst(res[k].cpu().numpy(), ref[k]) <= tol, k
+    gj, oj = res["jac"].cpu().numpy(), ref["jac"]
+    for c in range(3):
+        assert worst(np.swapaxes(gj[..., c], 2, 3), np.swapaxes(oj[..., c], 2, 3)) <= tol, c
+
+
 def test_full_size_workload_sampled():
     """The bench's configuration (workload 4, 1.64 M zones, mixed form, forward + Jacobian) against
     the oracle on a sample of zones spread over the whole batch."""
