@@ -57,6 +57,29 @@ def test_random_systems_against_oracle(m):
     assert e <= TOL, f"m={m}: {e:.3e}"
 
 
+@pytest.mark.parametrize("m", [2, 7, 33, 84, 97, 128])
+def test_row_exchanges(m):
+    """The equations of every zone shuffled (one row permutation applied to A_k, B_k, C_k and d_k):
+    the solution is unchanged, but the dominant entries leave the diagonal, so partial pivoting
+    exchanges rows in every block. Checked against the oracle and against the unshuffled solve."""
+    s = gen.random_system([5, 0, 1, 9, 17, 2], m, seed=200 + m)
+    ref = obtd.solve(s["A"], s["B"], s["C"], s["d"], s["offsets"])
+    rng = np.random.default_rng(m)
+    t = {k: s[k].copy() for k in ("A", "B", "C", "d")}
+    for z in range(s["d"].shape[0]):
+        p = rng.permutation(m)
+        if m > 1 and np.all(p == np.arange(m)):
+            p = np.roll(p, 1)
+        for k in ("A", "B", "C", "d"):
+            t[k][z] = t[k][z][p]
+    t.update(offsets=s["offsets"], m=m)
+    x, ok = run(t)
+    assert ok
+    e = ray_errors(x, ref, s["offsets"])
+    assert e <= TOL, f"m={m}: {e:.3e}"
+    assert e <= TOL and ray_errors(x, obtd.solve(t["A"], t["B"], t["C"], t["d"], t["offsets"]), s["offsets"]) <= TOL
+
+
 @pytest.mark.parametrize("pair", [True, False])
 def test_newton_systems_against_oracle(pair):
     s = gen.newton_system([40, 25, 0, 3, 1], n_bins=21, pair=pair, seed=1)
@@ -82,9 +105,18 @@ def test_full_length_rays_sampled():
     assert np.abs(res).max() <= 1e-13 * np.abs(s["d"]).max()
 
 
-def test_without_refinement_is_fp32_accurate():
+@pytest.mark.parametrize("shuffle", [False, True])
+def test_without_refinement_is_fp32_accurate(shuffle):
+    """FP32 accuracy of the factors alone; shuffled: the equations of every zone permuted, so that
+    only a sound pivot choice keeps the FP32 factorisation at this accuracy."""
     s = gen.newton_system([60, 30], n_bins=8, seed=2)
     ref = obtd.solve(s["A"], s["B"], s["C"], s["d"], s["offsets"])
+    if shuffle:
+        rng = np.random.default_rng(5)
+        for z in range(s["d"].shape[0]):
+            p = rng.permutation(s["m"])
+            for k in ("A", "B", "C", "d"):
+                s[k][z] = s[k][z][p]
     x0, ok0 = run(s, n_refine=0)
     x1, ok1 = run(s, n_refine=1)
     x2, ok2 = run(s, n_refine=2)
