@@ -75,7 +75,7 @@ struct BtdArgs {
     const int *off;
     const double *A, *B, *C, *d, *rhs;
     double *x, *r;
-    float *LUt, *Gt, *At, *y;
+    float *Mt, *Gt, *At, *y;  // Mt: the Gauss-Jordan multipliers of D_k, column j at j m, pivot value at (j, perm[j])
     int *perm, *zbad, *flag;
     const int *inval;  // set by k_btd_validate when the offsets are not a partition of the zones
 };
@@ -253,14 +253,6 @@ __device__ __forceinline__ void stage_two(const double *__restrict__ M1, float *
     }
 }
 
-// Row stride of the factor rows in shared memory: row j keeps the eight warps' column slots
-// contiguous (warp w's RS slots at w RS, column c at (c mod 8) RS + c / 8), padded to 16 bytes.
-template <int RS>
-__host__ __device__ constexpr int factor_ldu() {
-    return 8 * RS + 4;
-}
-static_assert(factor_ldu<12>() % 4 == 0, "factor rows on 16-byte boundaries");
-
 // Named barriers of the column steps: the warp that publishes column j arrives, the others wait.
 // Steps alternate between barriers 1 and 2: the publishing warp arrives early and goes on to wait
 // at the next step, which on a single barrier could count towards the step still open. With two,
@@ -279,11 +271,13 @@ __device__ __forceinline__ void step_wait(int j) {
 
 // Column j of D_k, in slot S of the calling warp (column warp + 8 S): the pivot row (the largest
 // magnitude among the rows not yet pivots, the lowest row on ties, by two warp reductions) and the
-// multipliers of every other row, published to buffer j mod 2; a row not yet a pivot keeps its
-// multiplier in column j (an entry of L). Ends with the warp's arrival at the step barrier.
+// multipliers of every other row, published to buffer j mod 2 and stored as column j of the zone's
+// multiplier matrix Mz (the pivot value in the pivot row's place), with 1 / pivot in s_rp[j]. Ends
+// with the warp's arrival at the step barrier.
 template <int RS, int CS>
-__device__ __forceinline__ void gj_publish(float2 (&v)[RS / 2][CS], const int S, unsigned done, int j, int m, int lane,
-                                           float *sL, int *s_r, int *cur, int *s_bad) {
+__device__ __forceinline__ void gj_publish(const float2 (&v)[RS / 2][CS], const int S, unsigned done, int j, int m,
+                                           int lane, float *sL, int *s_r, int *cur, float *s_rp, float *Mz,
+                                           int *s_bad) {
     unsigned key = 0u;  // |x| bits + 1 (NaN: 1) for a candidate row, 0 for none
     unsigned brow = 0xffffffffu;
 #pragma unroll
@@ -310,15 +304,17 @@ __device__ __forceinline__ void gj_publish(float2 (&v)[RS / 2][CS], const int S,
     if (lane == 0) {
         s_r[buf] = r;
         cur[j] = r;
+        s_rp[j] = rp;
         if (!(fabsf(piv) > 0.f && fabsf(piv) < INFINITY)) *s_bad = 1;
     }
+    float *mcol = Mz + (size_t)j * m;
 #pragma unroll
     for (int t = 0; t < CS; ++t) {
         const int i = lane + 32 * t;
         if (i < m) {
             const float lv = i != r ? VX_SLOT(v, S, t) * rp : 0.f;
             sL[buf * m + i] = lv;
-            if (i != r && !((done >> t) & 1u)) VX_SLOT(v, S, t) = lv;
+            mcol[i] = i != r ? lv : piv;
         }
     }
     step_arrive(j);
@@ -326,33 +322,28 @@ __device__ __forceinline__ void gj_publish(float2 (&v)[RS / 2][CS], const int S,
 
 // The elimination of column j (slot sj of warp wj) from the calling warp's part of [D_k | C_k],
 // the pivot row's slot TR known at compile time (the pivot row's values come by shuffle from lane
-// rl): row j of the factors to sU, D's columns past j and all of C's updated with the multipliers
-// lt. If the warp holds column j + 1 (np), that column is updated first and published before the
-// rest (look-ahead).
+// rl): D's columns past j and all of C's updated with the multipliers lt. If the warp holds column
+// j + 1 (np), that column is updated first and published before the rest (look-ahead).
 template <int RS, int CS, int TR>
 __device__ __forceinline__ void gj_eliminate(float2 (&v)[RS / 2][CS], float2 (&w)[RS / 2][CS], const float (&lt)[CS],
                                              int rl, const int sj, int wj, int warp, int lane, int j, int m, bool np,
-                                             unsigned done, float *sU, float *sL, int *s_r, int *cur, int *s_bad) {
+                                             unsigned done, float *sL, int *s_r, int *cur, float *s_rp, float *Mz,
+                                             int *s_bad) {
     float pd[RS];
 #pragma unroll
     for (int s = 0; s < RS; ++s) pd[s] = __shfl_sync(0xffffffffu, VX_SLOT(v, s, TR), rl);
-    if (lane == 0) {  // row j of the factors: the pivot row's entries of L, U_jj and its row of U
-        float4 *row = reinterpret_cast<float4 *>(sU + j * factor_ldu<RS>() + warp * RS);
-#pragma unroll
-        for (int q = 0; q < RS / 4; ++q) row[q] = make_float4(pd[4 * q], pd[4 * q + 1], pd[4 * q + 2], pd[4 * q + 3]);
-    }
     const bool wrap = wj == 7;  // column j + 1 is in slot sj + 1 (else in slot sj)
     if (np) {
         if (wrap) {
             if (sj + 1 < RS) {
 #pragma unroll
                 for (int t = 0; t < CS; ++t) VX_SLOT(v, sj + 1, t) = fmaf(-lt[t], pd[sj + 1], VX_SLOT(v, sj + 1, t));
-                gj_publish<RS, CS>(v, sj + 1 < RS ? sj + 1 : RS - 1, done, j + 1, m, lane, sL, s_r, cur, s_bad);
+                gj_publish<RS, CS>(v, sj + 1 < RS ? sj + 1 : RS - 1, done, j + 1, m, lane, sL, s_r, cur, s_rp, Mz, s_bad);
             }
         } else {
 #pragma unroll
             for (int t = 0; t < CS; ++t) VX_SLOT(v, sj, t) = fmaf(-lt[t], pd[sj], VX_SLOT(v, sj, t));
-            gj_publish<RS, CS>(v, sj, done, j + 1, m, lane, sL, s_r, cur, s_bad);
+            gj_publish<RS, CS>(v, sj, done, j + 1, m, lane, sL, s_r, cur, s_rp, Mz, s_bad);
         }
     }
     float2 nlt[CS];
@@ -395,24 +386,25 @@ __device__ __forceinline__ void gj_eliminate(float2 (&v)[RS / 2][CS], float2 (&w
 // partial pivoting runs on [D_k | C_k] one column at a time:
 //  - the warp that holds column j finds the pivot row and publishes it with the multipliers of
 //    every other row (gj_publish), then arrives at the step barrier, at which the other warps wait;
-//  - every warp takes the pivot row's values in its columns by shuffle, writes them to row j of the
-//    factor buffer and subtracts the multiples from the other rows, in the columns of D past j and
-//    in all of C (gj_eliminate); the warp that holds column j + 1 updates and publishes it first.
-// The factors of D_k are those of LU with partial pivoting; the rows already pivots are
-// eliminated as well, so at the end the C part of pivot row j is U_jj G_k[j] and no substitution
-// is left. Rows are never moved: cur maps pivot positions to physical rows.
+//  - every warp takes the pivot row's values in its columns by shuffle and subtracts the multiples
+//    from the other rows, in the columns of D past j and in all of C (gj_eliminate); the warp that
+//    holds column j + 1 updates and publishes it first.
+// The rows already pivots are eliminated as well, so at the end the C part of pivot row j is
+// U_jj G_k[j] and no substitution is left. Rows are never moved: cur maps pivot positions to
+// physical rows. What the solve sweeps need of D_k is the elimination itself: the multiplier
+// columns (with the pivot values), stored as they are published, and cur.
 template <int RS, int CS>
 __global__ void __launch_bounds__(kFactorThreads, RS > 12 ? 1 : 2) k_btd_factor(const BtdArgs a) {  // m > 96: one CTA per SM (shared memory)
     extern __shared__ __align__(16) float sm[];
     __shared__ int s_bad;
     __shared__ int s_r[2];
-    constexpr int ldu = factor_ldu<RS>();
     const int m = a.m, ld = a.ld, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    float *sA = sm;  // A_k, then the factors of D_k in pivot order (row stride ldu, slots by warp)
-    float *sW = sA + m * (ld > ldu ? ld : ldu);  // G_{k-1}, then C_k, then G_k
+    float *sA = sm;           // A_k
+    float *sW = sA + m * ld;  // G_{k-1}, then C_k, then G_k
     float *sT = sW + m * ld;  // B_k, then D_k
     float *sL = sT + m * ld;  // [2][m] the multipliers of the current column (two buffers)
-    int *cur = reinterpret_cast<int *>(sL + 2 * m), *pos = cur + m;
+    float *s_rp = sL + 2 * m;  // [m] 1 / the pivot of each column
+    int *cur = reinterpret_cast<int *>(s_rp + m), *pos = cur + m;
     long long z0, z1;
     if (!ray_range(a, blockIdx.x, z0, z1) || z1 == z0) return;
     if (tid == 0) s_bad = 0;
@@ -454,8 +446,9 @@ __global__ void __launch_bounds__(kFactorThreads, RS > 12 ? 1 : 2) k_btd_factor(
                 const int i = lane + 32 * t, c = warp + 8 * s;
                 VX_SLOT(w, s, t) = next && i < m && c < m ? sW[i * ld + c] : 0.f;
             }
+        float *Mz = a.Mt + k * mm;  // the zone's multiplier columns
         unsigned done = 0u;  // bit t: my row lane + 32 t has been a pivot
-        if (warp == 0) gj_publish<RS, CS>(v, 0, done, 0, m, lane, sL, s_r, cur, &s_bad);
+        if (warp == 0) gj_publish<RS, CS>(v, 0, done, 0, m, lane, sL, s_r, cur, s_rp, Mz, &s_bad);
 #pragma unroll
         for (int sj = 0; sj < RS; ++sj) {
             for (int wj = 0; wj < 8; ++wj) {
@@ -473,13 +466,13 @@ __global__ void __launch_bounds__(kFactorThreads, RS > 12 ? 1 : 2) k_btd_factor(
                 if (lane == rl) done |= 1u << tr;
                 const bool np = j + 1 < m && warp == ((j + 1) & 7);
                 if (tr == 0)
-                    gj_eliminate<RS, CS, 0>(v, w, lt, rl, sj, wj, warp, lane, j, m, np, done, sA, sL, s_r, cur, &s_bad);
+                    gj_eliminate<RS, CS, 0>(v, w, lt, rl, sj, wj, warp, lane, j, m, np, done, sL, s_r, cur, s_rp, Mz, &s_bad);
                 else if (CS > 1 && tr == 1)
-                    gj_eliminate<RS, CS, (CS > 1 ? 1 : 0)>(v, w, lt, rl, sj, wj, warp, lane, j, m, np, done, sA, sL, s_r, cur, &s_bad);
+                    gj_eliminate<RS, CS, (CS > 1 ? 1 : 0)>(v, w, lt, rl, sj, wj, warp, lane, j, m, np, done, sL, s_r, cur, s_rp, Mz, &s_bad);
                 else if (CS > 2 && tr == 2)
-                    gj_eliminate<RS, CS, (CS > 2 ? 2 : 0)>(v, w, lt, rl, sj, wj, warp, lane, j, m, np, done, sA, sL, s_r, cur, &s_bad);
+                    gj_eliminate<RS, CS, (CS > 2 ? 2 : 0)>(v, w, lt, rl, sj, wj, warp, lane, j, m, np, done, sL, s_r, cur, s_rp, Mz, &s_bad);
                 else if (CS > 3)
-                    gj_eliminate<RS, CS, (CS > 3 ? 3 : 0)>(v, w, lt, rl, sj, wj, warp, lane, j, m, np, done, sA, sL, s_r, cur, &s_bad);
+                    gj_eliminate<RS, CS, (CS > 3 ? 3 : 0)>(v, w, lt, rl, sj, wj, warp, lane, j, m, np, done, sL, s_r, cur, s_rp, Mz, &s_bad);
             }
         }
         __syncthreads();
@@ -491,7 +484,7 @@ __global__ void __launch_bounds__(kFactorThreads, RS > 12 ? 1 : 2) k_btd_factor(
                 const int i = lane + 32 * t;
                 if (i < m) {
                     const int p = pos[i];
-                    const float ru = 1.f / sA[p * ldu + (p & 7) * RS + (p >> 3)];
+                    const float ru = s_rp[p];
 #pragma unroll
                     for (int s = 0; s < RS; ++s) {
                         const int c = warp + 8 * s;
@@ -501,9 +494,6 @@ __global__ void __launch_bounds__(kFactorThreads, RS > 12 ? 1 : 2) k_btd_factor(
             }
         }
         __syncthreads();
-        float *LUt = a.LUt + k * mm;
-        for (int c = warp; c < m; c += 8)
-            for (int i = lane; i < m; i += 32) LUt[(size_t)c * m + i] = sA[i * ldu + (c & 7) * RS + (c >> 3)];
         for (int i = tid; i < m; i += kFactorThreads) a.perm[k * m + i] = cur[i];
         if (next) {
             float *Gt = a.Gt + k * mm;
@@ -559,7 +549,7 @@ __global__ void __launch_bounds__(32) k_btd_sweep(const BtdArgs a) {
     // forward: S0 holds A_k (zones after the first), S1 the LU factors of D_k. Every zone commits
     // two groups in the order they are needed (an empty one where nothing is copied), so
     // wait_group 1 always completes the older of the two in flight.
-    warp_stage(S1, a.LUt + (size_t)z0 * mm, mm, lane);
+    warp_stage(S1, a.Mt + (size_t)z0 * mm, mm, lane);
     if (z0 + 1 < z1) warp_stage(S0, a.At + (size_t)(z0 + 1) * mm, mm, lane);
     else asm volatile("cp.async.commit_group;" ::: "memory");
     for (long long k = z0; k < z1; ++k) {
@@ -596,59 +586,43 @@ __global__ void __launch_bounds__(32) k_btd_sweep(const BtdArgs a) {
             if (k + 1 < z1) warp_stage(S0, a.At + (size_t)(k + 1) * mm, mm, lane);
             else asm volatile("cp.async.commit_group;" ::: "memory");
         }
-        stage_wait<1>();  // the LU factors of D_k
-        // rhs_k - A_k y_{k-1}, then the row permutation of the factorisation
+        stage_wait<1>();  // the multiplier columns of zone k
+        // x = rhs_k - A_k y_{k-1}, rows in physical order
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            const int i = lane + 32 * t;
-            if (i < m) sv[i] = (float)rv[t] - v[t];
-        }
-        __syncwarp();
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            const int i = lane + 32 * t;
-            if (i < m) v[t] = sv[pv[t]];
-        }
-        __syncwarp();
-        // unit lower triangle
+        for (int t = 0; t < 4; ++t) v[t] = (float)rv[t] - v[t];
+        // the factor's elimination replayed on x: at step j every row but cur[j] subtracts its
+        // multiplier times x_{cur[j]} (one chain of m steps)
 #pragma unroll
         for (int tj = 0; tj < 4; ++tj) {
-            if (32 * tj >= m - 1) break;
-            const int lim = m - 1 - 32 * tj < 32 ? m - 1 - 32 * tj : 32;
+            if (32 * tj >= m) break;
+            const int lim = m - 32 * tj < 32 ? m - 32 * tj : 32;
             for (int l = 0; l < lim; ++l) {
                 const int j = 32 * tj + l;
-                const float vj = __shfl_sync(0xffffffffu, v[tj], l);
+                const int rj = __shfl_sync(0xffffffffu, pv[tj], l);  // cur[j]
+                const float m01 = (rj & 32) ? v[1] : v[0], m23 = (rj & 32) ? v[3] : v[2];
+                const float xr = __shfl_sync(0xffffffffu, (rj & 64) ? m23 : m01, rj & 31);
+                const float *col = S1 + j * m;
 #pragma unroll
-                for (int t = tj; t < 4; ++t) {
+                for (int t = 0; t < 4; ++t) {
                     const int i = lane + 32 * t;
-                    if (i > j && i < m) v[t] = fmaf(-S1[j * m + i], vj, v[t]);
+                    if (i < m && i != rj) v[t] = fmaf(-col[i], xr, v[t]);
                 }
             }
         }
-        // upper triangle, last row first; 1 / U_jj formed ahead, off the chain of steps
-        float rdiag[4];
+        // y_j = x_{cur[j]} / pivot_j, in the order of the unknowns
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
             const int i = lane + 32 * t;
-            rdiag[t] = i < m ? 1.f / S1[i * m + i] : 0.f;
-        }
-#pragma unroll
-        for (int tj = 3; tj >= 0; --tj) {
-            if (32 * tj >= m) continue;
-            const int top = m - 32 * tj < 32 ? m - 32 * tj : 32;
-            for (int l = top - 1; l >= 0; --l) {
-                const int j = 32 * tj + l;
-                const float vj = __shfl_sync(0xffffffffu, v[tj], l) * __shfl_sync(0xffffffffu, rdiag[tj], l);
-                if (lane == l) v[tj] = vj;
-#pragma unroll
-                for (int t = 0; t <= tj; ++t) {
-                    const int i = lane + 32 * t;
-                    if (i < j) v[t] = fmaf(-S1[j * m + i], vj, v[t]);
-                }
-            }
+            if (i < m) sv[i] = v[t];
         }
         __syncwarp();
-        if (k + 1 < z1) warp_stage(S1, a.LUt + (size_t)(k + 1) * mm, mm, lane);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int j = lane + 32 * t;
+            if (j < m) v[t] = sv[pv[t]] / S1[j * m + pv[t]];
+        }
+        __syncwarp();
+        if (k + 1 < z1) warp_stage(S1, a.Mt + (size_t)(k + 1) * mm, mm, lane);
         else asm volatile("cp.async.commit_group;" ::: "memory");
         float *yk = a.y + k * m;
 #pragma unroll
@@ -781,14 +755,14 @@ struct vx_btd {
     int m = 0, ld = 0, n_refine = 0;
     long long max_zones = 0;
     size_t smem = 0, smem_sweep = 0;
-    float *LUt = nullptr, *Gt = nullptr, *At = nullptr, *y = nullptr;
+    float *Mt = nullptr, *Gt = nullptr, *At = nullptr, *y = nullptr;
     int *perm = nullptr, *zbad = nullptr, *flag = nullptr;  // flag[0]: numeric flag, flag[1]: offsets invalid
     double *r = nullptr;
 };
 
 static void btd_free(vx_btd *h) {
     if (!h) return;
-    cudaFree(h->LUt);
+    cudaFree(h->Mt);
     cudaFree(h->Gt);
     cudaFree(h->At);
     cudaFree(h->y);
@@ -812,15 +786,11 @@ extern "C" vx_status vx_btd_create(int m, long long max_zones, int n_refine, vx_
     h->ld = m | 1;  // odd row stride: column walks through shared memory hit distinct banks
     h->n_refine = n_refine;
     h->max_zones = max_zones;
-    {
-        const int ldu = m <= 32 ? factor_ldu<4>() : m <= 64 ? factor_ldu<8>() : m <= 96 ? factor_ldu<12>() : factor_ldu<16>();
-        h->smem = ((size_t)m * (h->ld > ldu ? h->ld : ldu) + 2 * (size_t)m * h->ld + 2 * m) * sizeof(float) +
-                  (size_t)2 * m * sizeof(int);
-    }
+    h->smem = ((size_t)3 * m * h->ld + 3 * m) * sizeof(float) + (size_t)2 * m * sizeof(int);
     h->smem_sweep = ((size_t)2 * ((m * m + 3) & ~3) + m) * sizeof(float);
     const size_t zc = (size_t)(max_zones > 0 ? max_zones : 1), mm = (size_t)m * m;
     cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess) e = cudaMalloc(&h->LUt, zc * mm * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&h->Mt, zc * mm * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&h->Gt, zc * mm * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&h->At, zc * mm * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&h->y, zc * m * sizeof(float));
@@ -881,7 +851,7 @@ extern "C" vx_status vx_btd_solve(vx_btd *h, int n_rays, long long n_zones, cons
     a.rhs = d;
     a.x = x;
     a.r = h->r;
-    a.LUt = h->LUt;
+    a.Mt = h->Mt;
     a.Gt = h->Gt;
     a.At = h->At;
     a.y = h->y;
