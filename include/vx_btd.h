@@ -18,8 +18,9 @@
  * each D_k factored with partial pivoting inside the block. The factorisation is done in FP32 from
  * FP32 copies of the blocks, one CTA per ray: the product A_k G_{k-1} on the tensor cores (TF32
  * with each operand split into two parts, three products: about FP32 accuracy), then Gauss-Jordan
- * elimination of [D_k | C_k], whose pivot rows and multipliers are the LU factors of D_k and
- * whose right-hand block ends as G_k. Then the ray is solved with those factors, and
+ * elimination of [D_k | C_k] with partial pivoting, whose right-hand block ends as G_k and whose
+ * multipliers are kept. Then the ray is solved by replaying those eliminations on the right-hand
+ * side, and
  * n_refine sweeps of iterative refinement follow, each from the FP64 residual d - M x of the
  * caller's FP64 blocks. For a ray whose Schur complements are well conditioned (e.g. block rows
  * diagonally dominant) every sweep gains a factor of about cond x 1e-7, so two sweeps reach FP64
