@@ -2,16 +2,17 @@
 //
 // One ray per CTA (or per warp), since a ray's zones are a sequential chain; k_btd_validate first
 // checks that the ray offsets partition the zones (else every kernel returns at once):
-//  * k_btd_factor: block LU along the ray in FP32, the zone's block held in registers across the
-//    CTA. Per zone: load B_k, subtract the Schur term A_k G_{k-1} (G_{k-1} is still in shared memory
-//    from the previous zone), factor D_k with partial pivoting by row indirection, then
-//    G_k = D_k^{-1} C_k by forward and back substitution over the m right-hand sides in blocks of 8
-//    rows. The factors, G_k and an FP32 copy of A_k are written column-major, the row permutation
-//    as an index vector.
-//  * k_btd_sweep: one warp per ray solves M delta = rhs with those factors: forward
-//    y_k = D_k^{-1} (rhs_k - A_k y_{k-1}), backward delta_k = y_k - G_k delta_{k+1}; a lane holds
-//    rows lane + 32 t of a zone's vector and the column being eliminated is broadcast by shuffle.
-//    The first sweep writes x = delta, later ones add delta to x in FP64.
+//  * k_btd_factor: block elimination along the ray in FP32, one CTA per ray. Per zone: stage B_k
+//    and A_k, form D_k = B_k - A_k G_{k-1} on the tensor cores (G_{k-1} is still in shared memory
+//    from the previous zone), then Gauss-Jordan elimination with partial pivoting (row indirection)
+//    on [D_k | C_k] held in registers, which leaves G_k = D_k^{-1} C_k. Each step's multiplier
+//    column, G_k and an FP32 copy of A_k are written column-major, the pivot order as an index
+//    vector.
+//  * k_btd_sweep: one warp per ray solves M delta = rhs with those: forward
+//    y_k = D_k^{-1} (rhs_k - A_k y_{k-1}) by replaying the zone's elimination on the vector,
+//    backward delta_k = y_k - G_k delta_{k+1}; a lane holds rows lane + 32 t of a zone's vector and
+//    the element being eliminated is broadcast by shuffle. The first sweep writes x = delta, later
+//    ones add delta to x in FP64.
 //  * k_btd_resid: the FP64 residual r = d - M x from the caller's FP64 blocks, a warp per zone,
 //    four lanes per row and eight rows per pass (coalesced), FMA accumulation and a fixed two-step
 //    shuffle reduction per row.
@@ -530,8 +531,17 @@ __device__ __forceinline__ void stage_wait() {
 
 // One warp per ray (one warp per CTA). Each zone's FP32 matrices are staged in shared memory
 // (two buffers: the next matrix is in flight while the current one is used) and the vector being
-// eliminated is broadcast by shuffle: rows lane + 32 t of a zone's vector live in lane `lane`.
-template <bool FIRST, bool LAST>
+// eliminated is broadcast by shuffle: rows lane + 32 t (t < NT = ceil(m / 32)) of a zone's vector
+// live in lane `lane`; only the last slot can fall past m.
+template <int NT>
+__device__ __forceinline__ float slot_of(const float (&v)[NT], int t) {
+    float r = v[0];
+#pragma unroll
+    for (int q = 1; q < NT; ++q)
+        if (t == q) r = v[q];
+    return r;
+}
+template <bool FIRST, bool LAST, int NT>
 __global__ void __launch_bounds__(32) k_btd_sweep(const BtdArgs a) {
     extern __shared__ __align__(16) float sbuf[];
     const int lane = threadIdx.x;
@@ -545,7 +555,9 @@ __global__ void __launch_bounds__(32) k_btd_sweep(const BtdArgs a) {
             for (long long e = z0 * m + lane; e < z1 * m; e += 32) a.x[e] = __longlong_as_double(0x7ff8000000000000ll);
         return;
     }
-    float v[4], yp[4] = {0.f, 0.f, 0.f, 0.f};
+    float v[NT], yp[NT];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) yp[t] = 0.f;
     // forward: S0 holds A_k (zones after the first), S1 the LU factors of D_k. Every zone commits
     // two groups in the order they are needed (an empty one where nothing is copied), so
     // wait_group 1 always completes the older of the two in flight.
@@ -557,28 +569,28 @@ __global__ void __launch_bounds__(32) k_btd_sweep(const BtdArgs a) {
         // product A_k y_{k-1}, which accumulates apart, so their latency hides behind it
         const double *rhs = a.rhs + k * m;
         const int *perm = a.perm + k * m;
-        double rv[4];
-        int pv[4];
+        double rv[NT];
+        int pv[NT];
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
+        for (int t = 0; t < NT; ++t) {
             const int i = lane + 32 * t;
-            rv[t] = i < m ? rhs[i] : 0.0;
-            pv[t] = i < m ? perm[i] : 0;
+            rv[t] = t < NT - 1 || i < m ? rhs[i] : 0.0;
+            pv[t] = t < NT - 1 || i < m ? perm[i] : 0;
             v[t] = 0.f;
         }
         if (k > z0) {  // A_k y_{k-1}
             stage_wait<1>();  // A_k (the LU factors of D_k are the newer group)
 #pragma unroll
-            for (int tc = 0; tc < 4; ++tc) {
+            for (int tc = 0; tc < NT; ++tc) {
                 if (32 * tc >= m) break;
                 const int lim = m - 32 * tc < 32 ? m - 32 * tc : 32;
                 for (int l = 0; l < lim; ++l) {
                     const int c = 32 * tc + l;
                     const float yc = __shfl_sync(0xffffffffu, yp[tc], l);
 #pragma unroll
-                    for (int t = 0; t < 4; ++t) {
+                    for (int t = 0; t < NT; ++t) {
                         const int i = lane + 32 * t;
-                        if (i < m) v[t] = fmaf(S0[c * m + i], yc, v[t]);
+                        if (t < NT - 1 || i < m) v[t] = fmaf(S0[c * m + i], yc, v[t]);
                     }
                 }
             }
@@ -589,64 +601,65 @@ __global__ void __launch_bounds__(32) k_btd_sweep(const BtdArgs a) {
         stage_wait<1>();  // the multiplier columns of zone k
         // x = rhs_k - A_k y_{k-1}, rows in physical order
 #pragma unroll
-        for (int t = 0; t < 4; ++t) v[t] = (float)rv[t] - v[t];
+        for (int t = 0; t < NT; ++t) v[t] = (float)rv[t] - v[t];
         // the factor's elimination replayed on x: at step j every row but cur[j] subtracts its
         // multiplier times x_{cur[j]} (one chain of m steps)
 #pragma unroll
-        for (int tj = 0; tj < 4; ++tj) {
+        for (int tj = 0; tj < NT; ++tj) {
             if (32 * tj >= m) break;
             const int lim = m - 32 * tj < 32 ? m - 32 * tj : 32;
             for (int l = 0; l < lim; ++l) {
                 const int j = 32 * tj + l;
                 const int rj = __shfl_sync(0xffffffffu, pv[tj], l);  // cur[j]
-                const float m01 = (rj & 32) ? v[1] : v[0], m23 = (rj & 32) ? v[3] : v[2];
-                const float xr = __shfl_sync(0xffffffffu, (rj & 64) ? m23 : m01, rj & 31);
+                const float xr = __shfl_sync(0xffffffffu, slot_of<NT>(v, rj >> 5), rj & 31);
                 const float *col = S1 + j * m;
 #pragma unroll
-                for (int t = 0; t < 4; ++t) {
+                for (int t = 0; t < NT; ++t) {
                     const int i = lane + 32 * t;
-                    if (i < m && i != rj) v[t] = fmaf(-col[i], xr, v[t]);
+                    if ((t < NT - 1 || i < m) && i != rj) v[t] = fmaf(-col[i], xr, v[t]);
                 }
             }
         }
         // y_j = x_{cur[j]} / pivot_j, in the order of the unknowns
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
+        for (int t = 0; t < NT; ++t) {
             const int i = lane + 32 * t;
-            if (i < m) sv[i] = v[t];
+            if (t < NT - 1 || i < m) sv[i] = v[t];
         }
         __syncwarp();
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
+        for (int t = 0; t < NT; ++t) {
             const int j = lane + 32 * t;
-            if (j < m) v[t] = sv[pv[t]] / S1[j * m + pv[t]];
+            if (t < NT - 1 || j < m) v[t] = sv[pv[t]] / S1[j * m + pv[t]];
         }
         __syncwarp();
         if (k + 1 < z1) warp_stage(S1, a.Mt + (size_t)(k + 1) * mm, mm, lane);
         else asm volatile("cp.async.commit_group;" ::: "memory");
         float *yk = a.y + k * m;
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
+        for (int t = 0; t < NT; ++t) {
             const int i = lane + 32 * t;
-            if (i < m) yk[i] = v[t];
+            if (t < NT - 1 || i < m) yk[i] = v[t];
             yp[t] = v[t];
         }
     }
     stage_wait<0>();
     // backward: delta_k = y_k - G_k delta_{k+1}; x += delta (FP64). G of zone k in buffer k & 1.
-    float dn[4] = {0.f, 0.f, 0.f, 0.f};
+    float dn[NT];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) dn[t] = 0.f;
     if (z1 - 2 >= z0) warp_stage(((z1 - 2) & 1) ? S1 : S0, a.Gt + (size_t)(z1 - 2) * mm, mm, lane);
     for (long long k = z1 - 1; k >= z0; --k) {
         // y_k and x_k are loaded first and used after the product G_k delta_{k+1}
         const float *yk = a.y + k * m;
         double *xk = a.x + k * m;
-        float yv[4];
-        double xv[4];
+        float yv[NT];
+        double xv[NT];
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
+        for (int t = 0; t < NT; ++t) {
             const int i = lane + 32 * t;
-            yv[t] = i < m ? yk[i] : 0.f;
-            xv[t] = !FIRST && i < m ? xk[i] : 0.0;
+            yv[t] = t < NT - 1 || i < m ? yk[i] : 0.f;
+            xv[t] = !FIRST && (t < NT - 1 || i < m) ? xk[i] : 0.0;
             v[t] = 0.f;
         }
         if (k + 1 < z1) {
@@ -655,26 +668,26 @@ __global__ void __launch_bounds__(32) k_btd_sweep(const BtdArgs a) {
             else asm volatile("cp.async.commit_group;" ::: "memory");
             stage_wait<1>();  // G_k (G_{k-1} is the newer group)
 #pragma unroll
-            for (int tc = 0; tc < 4; ++tc) {
+            for (int tc = 0; tc < NT; ++tc) {
                 if (32 * tc >= m) break;
                 const int lim = m - 32 * tc < 32 ? m - 32 * tc : 32;
                 for (int l = 0; l < lim; ++l) {
                     const int c = 32 * tc + l;
                     const float dc = __shfl_sync(0xffffffffu, dn[tc], l);
 #pragma unroll
-                    for (int t = 0; t < 4; ++t) {
+                    for (int t = 0; t < NT; ++t) {
                         const int i = lane + 32 * t;
-                        if (i < m) v[t] = fmaf(G[c * m + i], dc, v[t]);
+                        if (t < NT - 1 || i < m) v[t] = fmaf(G[c * m + i], dc, v[t]);
                     }
                 }
             }
             __syncwarp();
         }
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
+        for (int t = 0; t < NT; ++t) {
             const int i = lane + 32 * t;
             v[t] = yv[t] - v[t];  // delta_k = y_k - G_k delta_{k+1}
-            if (i < m) xk[i] = FIRST ? (double)v[t] : xv[t] + (double)v[t];
+            if (t < NT - 1 || i < m) xk[i] = FIRST ? (double)v[t] : xv[t] + (double)v[t];
             dn[t] = v[t];
         }
     }
@@ -751,6 +764,23 @@ static void launch_factor(int m, int grid, size_t smem, cudaStream_t s, const Bt
     else k_btd_factor<16, 4><<<grid, kFactorThreads, smem, s>>>(a);
 }
 
+// The sweep kernel for NT = ceil(m / 32) row slots per lane.
+template <bool F, bool L>
+static const void *sweep_kernel(int nt) {
+    if (nt <= 1) return (const void *)k_btd_sweep<F, L, 1>;
+    if (nt == 2) return (const void *)k_btd_sweep<F, L, 2>;
+    if (nt == 3) return (const void *)k_btd_sweep<F, L, 3>;
+    return (const void *)k_btd_sweep<F, L, 4>;
+}
+template <bool F, bool L>
+static void launch_sweep(int m, int grid, size_t smem, cudaStream_t s, const BtdArgs &a) {
+    const int nt = (m + 31) / 32;
+    if (nt <= 1) k_btd_sweep<F, L, 1><<<grid, 32, smem, s>>>(a);
+    else if (nt == 2) k_btd_sweep<F, L, 2><<<grid, 32, smem, s>>>(a);
+    else if (nt == 3) k_btd_sweep<F, L, 3><<<grid, 32, smem, s>>>(a);
+    else k_btd_sweep<F, L, 4><<<grid, 32, smem, s>>>(a);
+}
+
 struct vx_btd {
     int m = 0, ld = 0, n_refine = 0;
     long long max_zones = 0;
@@ -801,8 +831,9 @@ extern "C" vx_status vx_btd_create(int m, long long max_zones, int n_refine, vx_
     if (e == cudaSuccess) e = cudaMemset(h->flag, 0, 2 * sizeof(int));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(factor_kernel(m), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem);
-    const void *sweeps[4] = {(const void *)k_btd_sweep<true, true>, (const void *)k_btd_sweep<true, false>,
-                             (const void *)k_btd_sweep<false, true>, (const void *)k_btd_sweep<false, false>};
+    const int nt = (m + 31) / 32;
+    const void *sweeps[4] = {sweep_kernel<true, true>(nt), sweep_kernel<true, false>(nt), sweep_kernel<false, true>(nt),
+                             sweep_kernel<false, false>(nt)};
     for (int i = 0; i < 4 && e == cudaSuccess; ++i)
         e = cudaFuncSetAttribute(sweeps[i], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem_sweep);
     if (e != cudaSuccess) {
@@ -865,9 +896,9 @@ extern "C" vx_status vx_btd_solve(vx_btd *h, int n_rays, long long n_zones, cons
     launch_factor(h->m, n_rays, h->smem, s, a);
     BTD_CU(cudaGetLastError());
     if (h->n_refine == 0)
-        k_btd_sweep<true, true><<<n_rays, 32, h->smem_sweep, s>>>(a);
+        launch_sweep<true, true>(h->m, n_rays, h->smem_sweep, s, a);
     else
-        k_btd_sweep<true, false><<<n_rays, 32, h->smem_sweep, s>>>(a);
+        launch_sweep<true, false>(h->m, n_rays, h->smem_sweep, s, a);
     BTD_CU(cudaGetLastError());
     for (int it = 1; it <= h->n_refine; ++it) {
         a.rhs = d;
@@ -875,9 +906,9 @@ extern "C" vx_status vx_btd_solve(vx_btd *h, int n_rays, long long n_zones, cons
         BTD_CU(cudaGetLastError());
         a.rhs = h->r;
         if (it == h->n_refine)
-            k_btd_sweep<false, true><<<n_rays, 32, h->smem_sweep, s>>>(a);
+            launch_sweep<false, true>(h->m, n_rays, h->smem_sweep, s, a);
         else
-            k_btd_sweep<false, false><<<n_rays, 32, h->smem_sweep, s>>>(a);
+            launch_sweep<false, false>(h->m, n_rays, h->smem_sweep, s, a);
         BTD_CU(cudaGetLastError());
     }
     return VX_OK;
