@@ -284,7 +284,7 @@ __device__ __forceinline__ void gj_publish(const float2 (&v)[RS / 2][CS], const 
 #pragma unroll
     for (int t = 0; t < CS; ++t) {
         const int i = lane + 32 * t;
-        if (i < m && !((done >> t) & 1u)) {
+        if ((t < CS - 1 || i < m) && !((done >> t) & 1u)) {  // CS = ceil(m / 32): only the last slot can fall past m
             const float x = fabsf(VX_SLOT(v, S, t));
             const unsigned kx = x == x ? __float_as_uint(x) + 1u : 1u;
             if (kx > key) {
@@ -312,7 +312,7 @@ __device__ __forceinline__ void gj_publish(const float2 (&v)[RS / 2][CS], const 
 #pragma unroll
     for (int t = 0; t < CS; ++t) {
         const int i = lane + 32 * t;
-        if (i < m) {
+        if (t < CS - 1 || i < m) {
             const float lv = i != r ? VX_SLOT(v, S, t) * rp : 0.f;
             sL[buf * m + i] = lv;
             mcol[i] = i != r ? lv : piv;
@@ -462,7 +462,7 @@ __global__ void __launch_bounds__(kFactorThreads, RS > 12 ? 1 : 2) k_btd_factor(
 #pragma unroll
                 for (int t = 0; t < CS; ++t) {
                     const int i = lane + 32 * t;
-                    lt[t] = i < m ? sL[buf * m + i] : 0.f;
+                    lt[t] = t < CS - 1 || i < m ? sL[buf * m + i] : 0.f;
                 }
                 if (lane == rl) done |= 1u << tr;
                 const bool np = j + 1 < m && warp == ((j + 1) & 7);
